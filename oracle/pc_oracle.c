@@ -1,0 +1,1300 @@
+/*
+ * CPU oracle for the perceptron-predicted, pointwise-relative-error-bounded
+ * compressor of arXiv 2309.09778.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * benchmark's CPU-baseline leg, never by the product path.  It shares no code,
+ * header, table or constant generator with the CUDA library.
+ *
+ * The functions follow the paper's steps in its order:
+ *   Section III   relative -> absolute (log) map with sign factors, Eq. 6-12
+ *   Section IV.A  Lorenzo prediction surface (the SZ prediction formula)
+ *   Section IV.B  three-layer perceptron with leaky ReLU, Lorenzo-aligned init
+ *   Section IV.C  sampled training, 8:2 split, L2 term, several (lr, lambda)
+ *   Section IV.D  data selection from (pre-quantized) true values; balance points
+ *   Section V     Algorithm 1 (compression) and the decompression procedure
+ * Where the paper is silent the stated readings are marked "Reading:".
+ *
+ * Parity status: every function is pinned by the tests against closed forms,
+ * brute force or library routines, except the paper-level compression-ratio
+ * claim (Section VI), which needs the SEG-Y data and SZ2.1: parity unpinned.
+ */
+#include "pc_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------- */
+/* Our own log2 / exp2.  From the mathematics, not from any vendor library:  */
+/*   ln y = 2 atanh(s), s = (y-1)/(y+1), atanh s = sum s^(2j+1)/(2j+1)       */
+/*   2^f  = e^(f ln2)  = sum (f ln2)^i / i!                                  */
+/* Evaluated by Horner's rule with explicit fused multiply-adds.             */
+/* ------------------------------------------------------------------------- */
+
+static const float O_SQRT2_F = 0x1.6a09e6p+0f;   /* RN_f32(sqrt 2) */
+static const float O_2LN2_F = 0x1.715476p+1f;    /* RN_f32(2 / ln 2) */
+static const float O_LN2_F = 0x1.62e430p-1f;     /* RN_f32(ln 2) */
+static const double O_SQRT2_D = 0x1.6a09e667f3bcdp+0;
+static const double O_2LN2_D = 0x1.71547652b82fep+1;
+static const double O_LN2_D = 0x1.62e42fefa39efp-1;
+
+static float f_from_bits(uint32_t b) { float f; memcpy(&f, &b, 4); return f; }
+static uint32_t bits_of_f(float f) { uint32_t b; memcpy(&b, &f, 4); return b; }
+static double d_from_bits(uint64_t b) { double f; memcpy(&f, &b, 8); return f; }
+static uint64_t bits_of_d(double f) { uint64_t b; memcpy(&b, &f, 8); return b; }
+
+/* log2 of a positive normal float. */
+float orc_L32(float y) {
+  uint32_t b = bits_of_f(y);
+  int e = (int)((b >> 23) & 0xFFu) - 127;
+  float m = f_from_bits((b & 0x7FFFFFu) | 0x3F800000u); /* [1, 2) */
+  if (m > O_SQRT2_F) { m = m * 0.5f; e = e + 1; }
+  float s = (m - 1.0f) / (m + 1.0f);
+  float z = s * s;
+  float p = 1.0f / 9.0f;
+  p = fmaf(p, z, 1.0f / 7.0f);
+  p = fmaf(p, z, 1.0f / 5.0f);
+  p = fmaf(p, z, 1.0f / 3.0f);
+  p = fmaf(p, z, 1.0f);
+  float t = s * p;
+  t = t * O_2LN2_F;
+  return (float)e + t;
+}
+
+/* 2^t for finite t (clamped to [-300, 300]). */
+float orc_E32(float t) {
+  if (t > 300.0f) t = 300.0f;
+  if (t < -300.0f) t = -300.0f;
+  float nf = rintf(t);
+  int k = (int)nf;
+  float f = t - nf;
+  float u = f * O_LN2_F;
+  float p = 1.0f / 5040.0f;
+  p = fmaf(p, u, 1.0f / 720.0f);
+  p = fmaf(p, u, 1.0f / 120.0f);
+  p = fmaf(p, u, 1.0f / 24.0f);
+  p = fmaf(p, u, 1.0f / 6.0f);
+  p = fmaf(p, u, 1.0f / 2.0f);
+  p = fmaf(p, u, 1.0f);
+  p = fmaf(p, u, 1.0f);
+  int k1 = k / 3;
+  int k2 = (k - k1) / 2;
+  int k3 = k - k1 - k2;
+  float s1 = f_from_bits((uint32_t)(k1 + 127) << 23);
+  float s2 = f_from_bits((uint32_t)(k2 + 127) << 23);
+  float s3 = f_from_bits((uint32_t)(k3 + 127) << 23);
+  return ((p * s1) * s2) * s3;
+}
+
+/* log2 of a positive double (subnormals are rescaled first). */
+double orc_L64(double y) {
+  if (y < 0x1p-1022) return orc_L64(y * 0x1p64) - 64.0;
+  uint64_t b = bits_of_d(y);
+  int e = (int)((b >> 52) & 0x7FFu) - 1023;
+  double m = d_from_bits((b & 0xFFFFFFFFFFFFFull) | 0x3FF0000000000000ull);
+  if (m > O_SQRT2_D) { m = m * 0.5; e = e + 1; }
+  double s = (m - 1.0) / (m + 1.0);
+  double z = s * s;
+  double p = 1.0 / 21.0;
+  for (int j = 9; j >= 0; j--) p = fma(p, z, 1.0 / (double)(2 * j + 1));
+  double t = s * p;
+  t = t * O_2LN2_D;
+  return (double)e + t;
+}
+
+/* 2^t for finite t (clamped to [-2100, 2100]). */
+double orc_E64(double t) {
+  if (t > 2100.0) t = 2100.0;
+  if (t < -2100.0) t = -2100.0;
+  double nf = rint(t);
+  int k = (int)nf;
+  double f = t - nf;
+  double u = f * O_LN2_D;
+  /* coefficients 1/i! for i = 13 .. 0 */
+  double fact[14];
+  fact[0] = 1.0;
+  for (int i = 1; i < 14; i++) fact[i] = fact[i - 1] * (double)i;
+  double p = 1.0 / fact[13];
+  for (int i = 12; i >= 0; i--) p = fma(p, u, 1.0 / fact[i]);
+  int k1 = k / 3;
+  int k2 = (k - k1) / 2;
+  int k3 = k - k1 - k2;
+  double s1 = d_from_bits((uint64_t)(k1 + 1023) << 52);
+  double s2 = d_from_bits((uint64_t)(k2 + 1023) << 52);
+  double s3 = d_from_bits((uint64_t)(k3 + 1023) << 52);
+  return ((p * s1) * s2) * s3;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Counter-based hash (SplitMix64 finaliser, Steele, Lea & Flood, OOPSLA     */
+/* 2014) and CRC-32 (IEEE 802.3 polynomial, reflected, bitwise).             */
+/* ------------------------------------------------------------------------- */
+uint64_t orc_mix64(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+uint32_t orc_crc32(const uint8_t* p, size_t n) {
+  uint32_t c = 0xFFFFFFFFu;
+  for (size_t i = 0; i < n; i++) {
+    c ^= p[i];
+    for (int k = 0; k < 8; k++) c = (c >> 1) ^ (0xEDB88320u & (0u - (c & 1u)));
+  }
+  return c ^ 0xFFFFFFFFu;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Step a1: global statistics (Algorithm 1 input "max/min of the dataset").  */
+/* abs_min is the non-zero minimum absolute value (Section III.B).           */
+/* Reading: subnormal magnitudes are left out of abs_min (they become        */
+/* balance points); NaN/Inf are rejected.                                    */
+/* ------------------------------------------------------------------------- */
+int orc_stats(const void* x, uint64_t n, int dtype, double* amin, double* amax, int* trivial) {
+  double mn = INFINITY, mx = 0.0;
+  int have = 0;
+  for (uint64_t i = 0; i < n; i++) {
+    double a;
+    if (dtype == ORC_F32) {
+      float v = ((const float*)x)[i];
+      if (!isfinite(v)) return ORC_ERR_NONFINITE;
+      a = fabs((double)v);
+      if (a >= 0x1p-126) { have = 1; if (a < mn) mn = a; }
+    } else if (dtype == ORC_F64) {
+      double v = ((const double*)x)[i];
+      if (!isfinite(v)) return ORC_ERR_NONFINITE;
+      a = fabs(v);
+      if (a >= 0x1p-1022) { have = 1; if (a < mn) mn = a; }
+    } else {
+      return ORC_ERR_DTYPE;
+    }
+    if (a > mx) mx = a;
+  }
+  if (!have) { mn = 1.0; mx = 1.0; }
+  *amin = mn;
+  *amax = mx;
+  *trivial = !have;
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Step a2: constants.                                                        */
+/*   b_a = log2(1 + eb)                                   (Eq. 8, Alg. 1)    */
+/*   factor_pos = abs_min                                  (Eq. 9)            */
+/*   log2 factor_neg = log2(abs_max + e0) + log2 factor_pos                   */
+/*                     + 2 log2(1 + eb) - log2(abs_min - e0)  (Eq. 10/11)     */
+/*   zero image f(e0 * factor_pos)                         (Eq. 12)           */
+/*   sign boundary f((abs_max + e0) factor_pos) + g(eb)    (Section III.B)    */
+/* Reading: e0 is the smallest positive representable value of the dtype.    */
+/* Reading: the log of a product is taken as the sum of logs, and each        */
+/* factor's log is rounded to a whole number K of quantization steps 2 b_a.  */
+/* By Eq. 5 this is the same as using the constant 2^(K 2 b_a) as the factor. */
+/* In code units (one unit = 2 b_a): positive image q = n + Kp, negative      */
+/* image q = n + Kn, zero image Zq, with n = rint(log2|x| / (2 b_a)).         */
+/* ------------------------------------------------------------------------- */
+int orc_make_consts(int dtype, double amin, double amax, int trivial, double eb, orc_consts* c) {
+  if (!(eb > 0.0 && eb < 1.0)) return ORC_ERR_ARG;
+  if (dtype != ORC_F32 && dtype != ORC_F64) return ORC_ERR_DTYPE;
+  memset(c, 0, sizeof(*c));
+  c->dtype = dtype;
+  c->eb = eb;
+  c->abs_min = amin;
+  c->abs_max = amax;
+  c->trivial = trivial;
+  double e0 = dtype == ORC_F32 ? 0x1p-149 : 0x1p-1074;
+  double le0 = dtype == ORC_F32 ? -149.0 : -1074.0;  /* log2 e0, exact */
+  double ba = orc_L64(1.0 + eb);
+  double step = ba + ba;
+  c->step64 = step;
+  double kp = rint(orc_L64(amin) / step);
+  double lfn = ((orc_L64(amax + e0) + orc_L64(amin)) + step) - orc_L64(amin - e0);
+  double kn = rint(lfn / step);
+  double zq = rint(le0 / step) + kp;
+  double s = rint(orc_L64(amax + e0) / step) + kp;
+  double span = (dtype == ORC_F32 ? 151.0 : 1076.0) / step + 2.0;
+  double lim = 1073741824.0; /* 2^30 */
+  if (fabs(kp) + span > lim || fabs(kn) + span > lim || fabs(zq) > lim || fabs(s) > lim)
+    return ORC_ERR_EB_RANGE;
+  c->Kp = (int32_t)kp;
+  c->Kn = (int32_t)kn;
+  c->Zq = (int32_t)zq;
+  c->S = (int32_t)s;
+  c->step32 = (float)step;
+  c->inv32 = 1.0f / c->step32;
+  float ef = (float)eb;
+  if ((double)ef > eb) ef = nextafterf(ef, 0.0f);
+  c->ebdn32 = ef;
+  c->stepd = step;
+  c->invd = 1.0 / step;
+  c->ebdnd = eb;
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Step a4 and its inverse (Eq. 6, 7, 12 and the inverse map, Section III.B).*/
+/* Class of a code: q <= Zq zero, Zq < q <= S positive, q > S negative.       */
+/* Reading: Alg. 1 multiplies a negative value by factor_neg; with Eq. 7 this */
+/* is |x| * factor_neg.  Reading: only +0.0 maps to the zero image; -0.0,     */
+/* subnormals and any point whose code does not reproduce it within the bound */
+/* are forced balance points (stored verbatim).                              */
+/* ------------------------------------------------------------------------- */
+static int o_class(int32_t q, const orc_consts* c) { return q <= c->Zq ? 0 : (q <= c->S ? 1 : 2); }
+
+float orc_recon32(int32_t q, const orc_consts* c) {
+  int cl = o_class(q, c);
+  if (cl == 0) return 0.0f;
+  int32_t n = q - (cl == 1 ? c->Kp : c->Kn);
+  float t = (float)n * c->step32;
+  float a = orc_E32(t);
+  return cl == 1 ? a : -a;
+}
+
+double orc_recon64(int32_t q, const orc_consts* c) {
+  int cl = o_class(q, c);
+  if (cl == 0) return 0.0;
+  int32_t n = q - (cl == 1 ? c->Kp : c->Kn);
+  double t = (double)n * c->stepd;
+  double a = orc_E64(t);
+  return cl == 1 ? a : -a;
+}
+
+void orc_transform32(float x, const orc_consts* c, int32_t* dq, int* ok) {
+  uint32_t b = bits_of_f(x);
+  float a = fabsf(x);
+  if (b == 0u) { *dq = c->Zq; *ok = 1; return; }
+  if (a < 0x1p-126f) { *dq = c->Zq; *ok = 0; return; }
+  float l = orc_L32(a);
+  float nf = rintf(l * c->inv32);
+  int32_t n = (int32_t)nf;
+  int32_t q = n + (x > 0.0f ? c->Kp : c->Kn);
+  *dq = q;
+  if (o_class(q, c) != (x > 0.0f ? 1 : 2)) { *ok = 0; return; }
+  float r = orc_E32((float)n * c->step32);
+  float err = fabsf(r - a);
+  /* err <= eb * |x| decided exactly: the product of two floats is exact in double. */
+  *ok = (double)err <= (double)c->ebdn32 * (double)a;
+}
+
+void orc_transform64(double x, const orc_consts* c, int32_t* dq, int* ok) {
+  uint64_t b = bits_of_d(x);
+  double a = fabs(x);
+  if (b == 0u) { *dq = c->Zq; *ok = 1; return; }
+  if (a < 0x1p-1022) { *dq = c->Zq; *ok = 0; return; }
+  double l = orc_L64(a);
+  double nf = rint(l * c->invd);
+  int32_t n = (int32_t)nf;
+  int32_t q = n + (x > 0.0 ? c->Kp : c->Kn);
+  *dq = q;
+  if (o_class(q, c) != (x > 0.0 ? 1 : 2)) { *ok = 0; return; }
+  double r = orc_E64((double)n * c->stepd);
+  double err = fabs(r - a);
+  /* exact product in binary128 (113-bit significand holds 53 x 53 bits) */
+  _Float128 prod = (_Float128)c->ebdnd * (_Float128)a;
+  *ok = (_Float128)err <= prod;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Blocks, stencils and predictors (Section IV.A, IV.B, IV.D).               */
+/* Blocks tile the field from the origin; edge blocks are truncated.  The    */
+/* block anchor (local origin) is a balance point (Section IV.D.2).  The     */
+/* predictor reads the exact pre-quantized codes of causal in-block          */
+/* neighbours, centred on the anchor; a neighbour outside the block reads 0. */
+/* Reading: the "true values" of the modified selection rule are the          */
+/* pre-quantized codes, which the decoder reproduces exactly, so there is no  */
+/* drift and compression is fully parallel.                                  */
+/* ------------------------------------------------------------------------- */
+#define O_VCLAMP 16777215  /* 2^24 - 1 */
+static const int O_S7[7][3] = {{-1, 0, 0}, {0, -1, 0}, {0, 0, -1}, {-1, -1, 0},
+                               {-1, 0, -1}, {0, -1, -1}, {-1, -1, -1}};
+static const int O_LZ7[7] = {1, 1, 1, -1, -1, -1, 1};
+
+static void o_stencil(int k, int i, int* dz, int* dy, int* dx) {
+  if (k == 7) { *dz = O_S7[i][0]; *dy = O_S7[i][1]; *dx = O_S7[i][2]; return; }
+  /* S13: all (dz,dy,dx) in {-1,0,1}^3 lexicographically before (0,0,0) */
+  int t = 0;
+  for (int a = -1; a <= 1; a++)
+    for (int b = -1; b <= 1; b++)
+      for (int cc = -1; cc <= 1; cc++) {
+        if (a == 0 && b == 0 && cc == 0) return;
+        if (t == i) { *dz = a; *dy = b; *dx = cc; return; }
+        t++;
+      }
+}
+
+/* Lorenzo weights over stencil k: the SZ formula (Section IV.A) with n = 1 in 3-D. */
+static int o_lz_weight(int k, int i) {
+  if (k == 7) return O_LZ7[i];
+  int dz, dy, dx;
+  o_stencil(k, i, &dz, &dy, &dx);
+  if (dz > 0 || dy > 0 || dx > 0) return 0;
+  int cnt = (dz != 0) + (dy != 0) + (dx != 0);
+  return (cnt % 2 == 1) ? 1 : -1;
+}
+
+int orc_lz_weight(int k, int i) { return o_lz_weight(k, i); }
+
+static int64_t o_lorenzo(const int32_t* v7) {
+  int64_t s = 0;
+  for (int i = 0; i < 7; i++) s += (int64_t)O_LZ7[i] * v7[i];
+  return s;
+}
+
+/* Weight blob: W1[h1][k], b1[h1], (W2[h2][h1], b2[h2] if h2 > 0), W3[hl], b3. */
+int orc_mlp_nweights(int k, int h1, int h2) {
+  int hl = h2 > 0 ? h2 : h1;
+  return h1 * k + h1 + (h2 > 0 ? h2 * h1 + h2 : 0) + hl + 1;
+}
+
+#define O_ALPHA 0.0625f /* leaky ReLU slope 2^-4 (Reading: slope unstated) */
+#define O_MAXH 64
+
+/* FP32 perceptron forward on centred integer inputs (Section IV.B, Fig. 3).
+ * u_i = v_i 2^-s; each unit: acc = bias, then acc = fma(w, u_i, acc) in input
+ * order; leaky ReLU on hidden units; linear output o; prediction o 2^s. */
+float orc_mlp_fwd32(const float* w, int k, int h1, int h2, int s_in, const int32_t* v) {
+  float sig = ldexpf(1.0f, -s_in);
+  float u[32];
+  for (int i = 0; i < k; i++) u[i] = (float)v[i] * sig;
+  const float* W1 = w;
+  const float* b1 = W1 + h1 * k;
+  float a1[O_MAXH];
+  for (int j = 0; j < h1; j++) {
+    float acc = b1[j];
+    for (int i = 0; i < k; i++) acc = fmaf(W1[j * k + i], u[i], acc);
+    a1[j] = acc >= 0.0f ? acc : acc * O_ALPHA;
+  }
+  const float* p = b1 + h1;
+  float* hl = a1;
+  int nl = h1;
+  float a2[O_MAXH];
+  if (h2 > 0) {
+    const float* W2 = p;
+    const float* b2 = W2 + h2 * h1;
+    for (int j = 0; j < h2; j++) {
+      float acc = b2[j];
+      for (int i = 0; i < h1; i++) acc = fmaf(W2[j * h1 + i], a1[i], acc);
+      a2[j] = acc >= 0.0f ? acc : acc * O_ALPHA;
+    }
+    p = b2 + h2;
+    hl = a2;
+    nl = h2;
+  }
+  const float* W3 = p;
+  float o = W3[nl];
+  for (int j = 0; j < nl; j++) o = fmaf(W3[j], hl[j], o);
+  return o * ldexpf(1.0f, s_in);
+}
+
+static int32_t o_round_pred(float p) {
+  if (p != p) return 0;
+  if (p > 1073741824.0f) p = 1073741824.0f;
+  if (p < -1073741824.0f) p = -1073741824.0f;
+  return (int32_t)rintf(p);
+}
+
+int32_t orc_mlp_pred32(const float* w, int k, int h1, int h2, int s_in, const int32_t* v) {
+  return o_round_pred(orc_mlp_fwd32(w, k, h1, h2, s_in, v));
+}
+
+static int o_bitlen(uint64_t n) { int b = 0; while (n) { b++; n >>= 1; } return b; }
+
+/* ------------------------------------------------------------------------- */
+/* Step a10: Huffman code lengths (Section IV.A stage 3; Section IV.C).      */
+/* Textbook Huffman: repeatedly join the two lightest nodes.  Total order:   */
+/* (weight, leaf before internal node, leaves by symbol, internal nodes by   */
+/* creation).  A single used symbol gets length 1.  Lengths are then handed   */
+/* out by rank from the per-length counts: the lightest leaf gets the longest */
+/* length.  If the longest exceeds lmax, the counts are first adjusted by the */
+/* procedure of ITU-T T.81 Annex K.3 (move a deepest sibling pair up one      */
+/* level and split a shallower leaf), which keeps the Kraft sum at one.       */
+/* ------------------------------------------------------------------------- */
+typedef struct { uint64_t f; uint32_t s; } o_leaf;
+static int o_cmp_leaf(const void* a, const void* b) {
+  const o_leaf* x = (const o_leaf*)a;
+  const o_leaf* y = (const o_leaf*)b;
+  if (x->f != y->f) return x->f < y->f ? -1 : 1;
+  return x->s < y->s ? -1 : (x->s > y->s ? 1 : 0);
+}
+
+int orc_huffman_lengths(const uint64_t* hist, int nsym, int lmax, uint8_t* len) {
+  memset(len, 0, (size_t)nsym);
+  int n = 0;
+  for (int s = 0; s < nsym; s++) n += hist[s] > 0;
+  if (n == 0) return 0;
+  o_leaf* L = (o_leaf*)malloc(sizeof(o_leaf) * (size_t)n);
+  int t = 0;
+  for (int s = 0; s < nsym; s++)
+    if (hist[s] > 0) { L[t].f = hist[s]; L[t].s = (uint32_t)s; t++; }
+  if (n == 1) { len[L[0].s] = 1; free(L); return 1; }
+  qsort(L, (size_t)n, sizeof(o_leaf), o_cmp_leaf);
+  int nn = 2 * n - 1;
+  uint64_t* w = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)nn);
+  int* parent = (int*)malloc(sizeof(int) * (size_t)nn);
+  int* depth = (int*)malloc(sizeof(int) * (size_t)nn);
+  for (int i = 0; i < n; i++) w[i] = L[i].f;
+  int li = 0, ii = n, next = n;
+  for (int step = 0; step < n - 1; step++) {
+    int pick[2];
+    for (int q = 0; q < 2; q++) {
+      if (li < n && (ii >= next || w[li] <= w[ii])) pick[q] = li++;
+      else pick[q] = ii++;
+    }
+    w[next] = w[pick[0]] + w[pick[1]];
+    parent[pick[0]] = next;
+    parent[pick[1]] = next;
+    next++;
+  }
+  depth[nn - 1] = 0;
+  for (int i = nn - 2; i >= 0; i--) depth[i] = depth[parent[i]] + 1;
+  int maxlen = 0;
+  int* bits = (int*)calloc((size_t)n + 2, sizeof(int));
+  for (int i = 0; i < n; i++) { bits[depth[i]]++; if (depth[i] > maxlen) maxlen = depth[i]; }
+  if (maxlen > lmax) {
+    for (int i = maxlen; i > lmax; i--) {
+      while (bits[i] > 0) {
+        int j = i - 2;
+        while (bits[j] == 0) j--;
+        bits[i] -= 2;
+        bits[i - 1] += 1;
+        bits[j + 1] += 2;
+        bits[j] -= 1;
+      }
+    }
+    maxlen = lmax;
+  }
+  int idx = 0;
+  for (int l = maxlen; l >= 1; l--)
+    for (int c = 0; c < bits[l]; c++) len[L[idx++].s] = (uint8_t)l;
+  free(bits); free(depth); free(parent); free(w); free(L);
+  return n;
+}
+
+/* Canonical code words from lengths: the construction of RFC 1951 Section 3.2.2
+ * (codes of one length are consecutive, in symbol order). */
+void orc_canonical_codes(const uint8_t* len, int nsym, int lmax, uint32_t* code) {
+  uint32_t blc[33] = {0}, nextc[33] = {0};
+  for (int s = 0; s < nsym; s++) if (len[s]) blc[len[s]]++;
+  uint32_t c = 0;
+  blc[0] = 0;
+  for (int b = 1; b <= lmax; b++) { c = (c + blc[b - 1]) << 1; nextc[b] = c; }
+  for (int s = 0; s < nsym; s++) { code[s] = 0; if (len[s]) code[s] = nextc[len[s]]++; }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Container (little-endian).  Header of 256 bytes, then 16-byte aligned      */
+/* sections: weights, codebook (sym | len << 16, by symbol), per-block bit    */
+/* counts (| perceptron flag << 31), per-block balance-point counts (u16),   */
+/* balance-point values (dtype), bitstream (u32 words, MSB first).           */
+/* The factors travel with the stream (Section V).                           */
+/* ------------------------------------------------------------------------- */
+#define O_LMAX 24
+#define O_HDR 256
+static void put32(uint8_t* p, uint32_t v) { for (int i = 0; i < 4; i++) p[i] = (uint8_t)(v >> (8 * i)); }
+static void put64(uint8_t* p, uint64_t v) { for (int i = 0; i < 8; i++) p[i] = (uint8_t)(v >> (8 * i)); }
+static uint32_t get32(const uint8_t* p) { uint32_t v = 0; for (int i = 0; i < 4; i++) v |= (uint32_t)p[i] << (8 * i); return v; }
+static uint64_t get64(const uint8_t* p) { uint64_t v = 0; for (int i = 0; i < 8; i++) v |= (uint64_t)p[i] << (8 * i); return v; }
+static uint64_t al16(uint64_t x) { return (x + 15u) & ~(uint64_t)15u; }
+
+typedef struct {
+  uint64_t nb[3], nblocks, bvol;
+} o_geom;
+
+static int o_geom_make(const uint64_t dims[3], const int block[3], o_geom* g) {
+  uint64_t vol = 1;
+  for (int i = 0; i < 3; i++) {
+    if (block[i] < 1 || dims[i] < 1) return ORC_ERR_ARG;
+    g->nb[i] = (dims[i] + (uint64_t)block[i] - 1) / (uint64_t)block[i];
+    vol *= (uint64_t)block[i];
+  }
+  if (vol > 4096 || vol < 2) return ORC_ERR_ARG;
+  g->bvol = vol;
+  g->nblocks = g->nb[0] * g->nb[1] * g->nb[2];
+  return ORC_OK;
+}
+
+uint64_t orc_compress_bound(const uint64_t dims[3], int dtype, const int block[3], int m, int nweights) {
+  o_geom g;
+  if (o_geom_make(dims, block, &g)) return 0;
+  uint64_t n = dims[0] * dims[1] * dims[2];
+  uint64_t ts = dtype == ORC_F64 ? 8 : 4;
+  uint64_t b = O_HDR;
+  b = al16(b + 4ull * (uint64_t)nweights);
+  b = al16(b + 4ull * (1ull << m));
+  b = al16(b + 4ull * g.nblocks);
+  b = al16(b + 2ull * g.nblocks);
+  b = al16(b + ts * n);
+  b = al16(b + 4ull * ((n * O_LMAX + 31) / 32 + 1));
+  return b;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Algorithm 1: compression.                                                  */
+/* ------------------------------------------------------------------------- */
+int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_params* p,
+                 uint8_t* out, uint64_t cap, uint64_t* out_size, orc_dump* dump) {
+  if (dtype != ORC_F32 && dtype != ORC_F64) return ORC_ERR_DTYPE;
+  if (p->m < 2 || p->m > 16) return ORC_ERR_ARG;
+  int use_nn = p->pred == ORC_PRED_MLP && p->weights != NULL;
+  int k = p->stencil;
+  if (use_nn && (k != 7 && k != 13)) return ORC_ERR_ARG;
+  if (use_nn && (p->h1 < 1 || p->h1 > O_MAXH || p->h2 < 0 || p->h2 > O_MAXH)) return ORC_ERR_ARG;
+  if (use_nn && (p->s_in < 0 || p->s_in > 30)) return ORC_ERR_ARG;
+  o_geom g;
+  if (o_geom_make(dims, p->block, &g)) return ORC_ERR_ARG;
+  uint64_t n = dims[0] * dims[1] * dims[2];
+  size_t ts = dtype == ORC_F64 ? 8 : 4;
+  int nsym = 1 << p->m;
+  int64_t R = (int64_t)1 << (p->m - 1);
+
+  /* a1, a2 */
+  double amin, amax;
+  int trivial;
+  int st = orc_stats(x, n, dtype, &amin, &amax, &trivial);
+  if (st) return st;
+  orc_consts c;
+  st = orc_make_consts(dtype, amin, amax, trivial, p->eb, &c);
+  if (st) return st;
+
+  /* a4: transform every point (Alg. 1, the per-point map) */
+  int32_t* dq = (int32_t*)malloc(sizeof(int32_t) * n);
+  uint8_t* okv = (uint8_t*)malloc(n);
+  for (uint64_t i = 0; i < n; i++) {
+    int ok;
+    if (dtype == ORC_F32) orc_transform32(((const float*)x)[i], &c, &dq[i], &ok);
+    else orc_transform64(((const double*)x)[i], &c, &dq[i], &ok);
+    okv[i] = (uint8_t)ok;
+  }
+
+  /* a5-a9: per block predict, select, quantize, histogram */
+  uint16_t* codes = (uint16_t*)calloc(g.nblocks * g.bvol, sizeof(uint16_t));
+  uint8_t* nnf = (uint8_t*)calloc(g.nblocks, 1);
+  uint16_t* nout = (uint16_t*)calloc(g.nblocks, sizeof(uint16_t));
+  uint64_t* hist = (uint64_t*)calloc((size_t)nsym, sizeof(uint64_t));
+  int32_t* vc = (int32_t*)malloc(sizeof(int32_t) * g.bvol);
+  int64_t* vt = (int64_t*)malloc(sizeof(int64_t) * g.bvol);
+  uint16_t* cz = (uint16_t*)malloc(sizeof(uint16_t) * g.bvol);
+  uint16_t* cn = (uint16_t*)malloc(sizeof(uint16_t) * g.bvol);
+  uint64_t n_out = 0;
+  uint64_t bi = 0;
+  for (uint64_t bz = 0; bz < g.nb[0]; bz++)
+    for (uint64_t by = 0; by < g.nb[1]; by++)
+      for (uint64_t bx = 0; bx < g.nb[2]; bx++, bi++) {
+        uint64_t o0 = bz * p->block[0], o1 = by * p->block[1], o2 = bx * p->block[2];
+        int e0 = (int)((dims[0] - o0) < (uint64_t)p->block[0] ? dims[0] - o0 : (uint64_t)p->block[0]);
+        int e1 = (int)((dims[1] - o1) < (uint64_t)p->block[1] ? dims[1] - o1 : (uint64_t)p->block[1]);
+        int e2 = (int)((dims[2] - o2) < (uint64_t)p->block[2] ? dims[2] - o2 : (uint64_t)p->block[2]);
+        int np = e0 * e1 * e2;
+        uint64_t ia = (o0 * dims[1] + o1) * dims[2] + o2;
+        int32_t da = dq[ia];
+        for (int lz = 0; lz < e0; lz++)
+          for (int ly = 0; ly < e1; ly++)
+            for (int lx = 0; lx < e2; lx++) {
+              int j = (lz * e1 + ly) * e2 + lx;
+              uint64_t ig = ((o0 + lz) * dims[1] + (o1 + ly)) * dims[2] + (o2 + lx);
+              int64_t v = (int64_t)dq[ig] - (int64_t)da;
+              vt[j] = v;
+              vc[j] = (int32_t)(v > O_VCLAMP ? O_VCLAMP : (v < -O_VCLAMP ? -O_VCLAMP : v));
+            }
+        int64_t costz = 0, costn = 0;
+        for (int lz = 0; lz < e0; lz++)
+          for (int ly = 0; ly < e1; ly++)
+            for (int lx = 0; lx < e2; lx++) {
+              int j = (lz * e1 + ly) * e2 + lx;
+              if (j == 0) continue;
+              uint64_t ig = ((o0 + lz) * dims[1] + (o1 + ly)) * dims[2] + (o2 + lx);
+              int32_t in7[7];
+              for (int i = 0; i < 7; i++) {
+                int qz = lz + O_S7[i][0], qy = ly + O_S7[i][1], qx = lx + O_S7[i][2];
+                in7[i] = (qz >= 0 && qy >= 0 && qx >= 0) ? vc[(qz * e1 + qy) * e2 + qx] : 0;
+              }
+              int64_t kz = vt[j] - o_lorenzo(in7);
+              int64_t az = kz < 0 ? -kz : kz;
+              costz += o_bitlen((uint64_t)(az < R ? az : R));
+              cz[j] = (uint16_t)((az <= R - 1 && okv[ig]) ? kz + R : 0);
+              if (use_nn) {
+                int32_t in[13];
+                for (int i = 0; i < k; i++) {
+                  int dz, dy, dx;
+                  o_stencil(k, i, &dz, &dy, &dx);
+                  int qz = lz + dz, qy = ly + dy, qx = lx + dx;
+                  in[i] = (qz >= 0 && qy >= 0 && qx >= 0 && qz < e0 && qy < e1 && qx < e2)
+                              ? vc[(qz * e1 + qy) * e2 + qx] : 0;
+                }
+                int64_t kn = vt[j] - (int64_t)orc_mlp_pred32(p->weights, k, p->h1, p->h2, p->s_in, in);
+                int64_t an = kn < 0 ? -kn : kn;
+                costn += o_bitlen((uint64_t)(an < R ? an : R));
+                cn[j] = (uint16_t)((an <= R - 1 && okv[ig]) ? kn + R : 0);
+              }
+            }
+        /* a7: perceptron only where it is strictly cheaper than Lorenzo */
+        int usen = use_nn && costn < costz;
+        nnf[bi] = (uint8_t)usen;
+        const uint16_t* cs = usen ? cn : cz;
+        int no = 1;  /* the anchor */
+        for (int j = 1; j < np; j++) {
+          codes[bi * g.bvol + j] = cs[j];
+          hist[cs[j]]++;
+          if (cs[j] == 0) no++;
+        }
+        nout[bi] = (uint16_t)no;
+        n_out += (uint64_t)no;
+      }
+
+  /* a10: code lengths and canonical codes */
+  uint8_t* lens = (uint8_t*)malloc((size_t)nsym);
+  uint32_t* cw = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)nsym);
+  int n_used = orc_huffman_lengths(hist, nsym, O_LMAX, lens);
+  orc_canonical_codes(lens, nsym, O_LMAX, cw);
+
+  /* a11: per-block bit counts and total */
+  uint32_t* bbits = (uint32_t*)malloc(sizeof(uint32_t) * g.nblocks);
+  uint64_t tbits = 0;
+  bi = 0;
+  for (uint64_t b = 0; b < g.nblocks; b++) {
+    uint64_t bz = b / (g.nb[1] * g.nb[2]), by = (b / g.nb[2]) % g.nb[1], bx = b % g.nb[2];
+    int e0 = (int)((dims[0] - bz * p->block[0]) < (uint64_t)p->block[0] ? dims[0] - bz * p->block[0] : (uint64_t)p->block[0]);
+    int e1 = (int)((dims[1] - by * p->block[1]) < (uint64_t)p->block[1] ? dims[1] - by * p->block[1] : (uint64_t)p->block[1]);
+    int e2 = (int)((dims[2] - bx * p->block[2]) < (uint64_t)p->block[2] ? dims[2] - bx * p->block[2] : (uint64_t)p->block[2]);
+    int np = e0 * e1 * e2;
+    uint32_t s = 0;
+    for (int j = 1; j < np; j++) s += lens[codes[b * g.bvol + j]];
+    bbits[b] = s;
+    tbits += s;
+  }
+  uint64_t swords = (tbits + 31) / 32;
+
+  /* layout */
+  int nw = use_nn ? orc_mlp_nweights(k, p->h1, p->h2) : 0;
+  uint64_t off_w = O_HDR;
+  uint64_t off_cb = al16(off_w + 4ull * (uint64_t)nw);
+  uint64_t off_bb = al16(off_cb + 4ull * (uint64_t)n_used);
+  uint64_t off_bn = al16(off_bb + 4ull * g.nblocks);
+  uint64_t off_ov = al16(off_bn + 2ull * g.nblocks);
+  uint64_t off_st = al16(off_ov + ts * n_out);
+  uint64_t total = al16(off_st + 4ull * swords);
+  int ret = ORC_OK;
+  if (total > cap) { ret = ORC_ERR_CAPACITY; goto done; }
+  memset(out, 0, total);
+
+  /* header */
+  memcpy(out, "PCMP", 4);
+  put32(out + 4, 1);
+  put32(out + 8, (uint32_t)dtype);
+  put32(out + 12, (uint32_t)(use_nn ? ORC_PRED_MLP : ORC_PRED_LORENZO));
+  put64(out + 16, dims[0]); put64(out + 24, dims[1]); put64(out + 32, dims[2]);
+  put32(out + 40, (uint32_t)p->block[0]); put32(out + 44, (uint32_t)p->block[1]); put32(out + 48, (uint32_t)p->block[2]);
+  put32(out + 52, (uint32_t)(use_nn ? k : 0));
+  put32(out + 56, (uint32_t)(use_nn ? p->h1 : 0));
+  put32(out + 60, (uint32_t)(use_nn ? p->h2 : 0));
+  put32(out + 64, (uint32_t)p->m);
+  put32(out + 68, (uint32_t)(use_nn ? p->s_in : 0));
+  put64(out + 72, bits_of_d(p->eb));
+  put64(out + 80, bits_of_d(amin));
+  put64(out + 88, bits_of_d(amax));
+  put32(out + 96, (uint32_t)(trivial ? 1 : 0));
+  put32(out + 100, (uint32_t)c.Kp); put32(out + 104, (uint32_t)c.Kn);
+  put32(out + 108, (uint32_t)c.Zq); put32(out + 112, (uint32_t)c.S);
+  put32(out + 116, (uint32_t)n_used);
+  if (dtype == ORC_F32) {
+    put64(out + 120, bits_of_f(c.step32)); put64(out + 128, bits_of_f(c.inv32)); put64(out + 136, bits_of_f(c.ebdn32));
+  } else {
+    put64(out + 120, bits_of_d(c.stepd)); put64(out + 128, bits_of_d(c.invd)); put64(out + 136, bits_of_d(c.ebdnd));
+  }
+  put64(out + 144, g.nblocks);
+  put64(out + 152, n_out);
+  put64(out + 160, swords);
+  put64(out + 168, off_w); put64(out + 176, off_cb); put64(out + 184, off_bb);
+  put64(out + 192, off_bn); put64(out + 200, off_ov); put64(out + 208, off_st);
+  put64(out + 216, total);
+  put32(out + 224, (uint32_t)nw);
+  put32(out + 252, orc_crc32(out, 252));
+
+  /* sections */
+  for (int i = 0; i < nw; i++) put32(out + off_w + 4ull * i, bits_of_f(p->weights[i]));
+  {
+    uint64_t t = 0;
+    for (int s = 0; s < nsym; s++)
+      if (lens[s]) { put32(out + off_cb + 4ull * t, (uint32_t)s | ((uint32_t)lens[s] << 16)); t++; }
+  }
+  for (uint64_t b = 0; b < g.nblocks; b++) {
+    put32(out + off_bb + 4ull * b, bbits[b] | ((uint32_t)nnf[b] << 31));
+    out[off_bn + 2ull * b] = (uint8_t)(nout[b] & 0xFF);
+    out[off_bn + 2ull * b + 1] = (uint8_t)(nout[b] >> 8);
+  }
+  {
+    /* a12: balance points (anchor first, then code-0 points in raster order) and bits */
+    uint64_t oi = 0, bp = 0;
+    for (uint64_t b = 0; b < g.nblocks; b++) {
+      uint64_t bz = b / (g.nb[1] * g.nb[2]), by = (b / g.nb[2]) % g.nb[1], bx = b % g.nb[2];
+      uint64_t o0 = bz * p->block[0], o1 = by * p->block[1], o2 = bx * p->block[2];
+      int e0 = (int)((dims[0] - o0) < (uint64_t)p->block[0] ? dims[0] - o0 : (uint64_t)p->block[0]);
+      int e1 = (int)((dims[1] - o1) < (uint64_t)p->block[1] ? dims[1] - o1 : (uint64_t)p->block[1]);
+      int e2 = (int)((dims[2] - o2) < (uint64_t)p->block[2] ? dims[2] - o2 : (uint64_t)p->block[2]);
+      for (int lz = 0; lz < e0; lz++)
+        for (int ly = 0; ly < e1; ly++)
+          for (int lx = 0; lx < e2; lx++) {
+            int j = (lz * e1 + ly) * e2 + lx;
+            uint64_t ig = ((o0 + lz) * dims[1] + (o1 + ly)) * dims[2] + (o2 + lx);
+            uint16_t cd = codes[b * g.bvol + j];
+            if (j == 0 || cd == 0) {
+              memcpy(out + off_ov + ts * oi, (const uint8_t*)x + ts * ig, ts);
+              oi++;
+            }
+            if (j == 0) continue;
+            uint32_t w = cw[cd];
+            int L = lens[cd];
+            for (int q = L - 1; q >= 0; q--, bp++) {
+              if ((w >> q) & 1u) {
+                uint64_t word = bp >> 5;
+                uint32_t bit = 31u - (uint32_t)(bp & 31u);
+                uint8_t* wp = out + off_st + 4ull * word;
+                put32(wp, get32(wp) | (1u << bit));
+              }
+            }
+          }
+    }
+  }
+  *out_size = total;
+
+  if (dump) {
+    if (dump->dq) memcpy(dump->dq, dq, sizeof(int32_t) * n);
+    if (dump->ok) memcpy(dump->ok, okv, n);
+    if (dump->codes) memcpy(dump->codes, codes, sizeof(uint16_t) * g.nblocks * g.bvol);
+    if (dump->nnflag) memcpy(dump->nnflag, nnf, g.nblocks);
+    if (dump->hist) memcpy(dump->hist, hist, sizeof(uint64_t) * (size_t)nsym);
+    if (dump->lens) memcpy(dump->lens, lens, (size_t)nsym);
+  }
+done:
+  free(bbits); free(cw); free(lens); free(cz); free(cn); free(vt); free(vc);
+  free(hist); free(nout); free(nnf); free(codes); free(okv); free(dq);
+  return ret;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Decompression (Section V): rebuild the canonical Huffman decoder, read the */
+/* stream bit by bit, take balance points from their set, otherwise invert   */
+/* the quantization and let the predictor walk the block from its start.     */
+/* ------------------------------------------------------------------------- */
+int orc_read_header(const uint8_t* in, uint64_t in_size, uint64_t dims[3], int* dtype) {
+  if (in_size < O_HDR) return ORC_ERR_CORRUPT;
+  if (memcmp(in, "PCMP", 4) != 0 || get32(in + 4) != 1) return ORC_ERR_CORRUPT;
+  if (get32(in + 252) != orc_crc32(in, 252)) return ORC_ERR_CORRUPT;
+  dims[0] = get64(in + 16); dims[1] = get64(in + 24); dims[2] = get64(in + 32);
+  *dtype = (int)get32(in + 8);
+  return ORC_OK;
+}
+
+int orc_decompress(const uint8_t* in, uint64_t in_size, void* xo, uint64_t cap_elems) {
+  uint64_t dims[3];
+  int dtype;
+  int st = orc_read_header(in, in_size, dims, &dtype);
+  if (st) return st;
+  if (dtype != ORC_F32 && dtype != ORC_F64) return ORC_ERR_CORRUPT;
+  size_t ts = dtype == ORC_F64 ? 8 : 4;
+  int pred = (int)get32(in + 12);
+  int block[3] = {(int)get32(in + 40), (int)get32(in + 44), (int)get32(in + 48)};
+  int k = (int)get32(in + 52), h1 = (int)get32(in + 56), h2 = (int)get32(in + 60);
+  int m = (int)get32(in + 64), s_in = (int)get32(in + 68);
+  orc_consts c;
+  memset(&c, 0, sizeof(c));
+  c.dtype = dtype;
+  c.Kp = (int32_t)get32(in + 100); c.Kn = (int32_t)get32(in + 104);
+  c.Zq = (int32_t)get32(in + 108); c.S = (int32_t)get32(in + 112);
+  uint32_t n_used = get32(in + 116);
+  if (dtype == ORC_F32) {
+    c.step32 = f_from_bits((uint32_t)get64(in + 120));
+    c.inv32 = f_from_bits((uint32_t)get64(in + 128));
+    c.ebdn32 = f_from_bits((uint32_t)get64(in + 136));
+  } else {
+    c.stepd = d_from_bits(get64(in + 120));
+    c.invd = d_from_bits(get64(in + 128));
+    c.ebdnd = d_from_bits(get64(in + 136));
+  }
+  uint64_t nblocks = get64(in + 144), n_out = get64(in + 152), swords = get64(in + 160);
+  uint64_t off_w = get64(in + 168), off_cb = get64(in + 176), off_bb = get64(in + 184);
+  uint64_t off_bn = get64(in + 192), off_ov = get64(in + 200), off_st = get64(in + 208);
+  uint64_t total = get64(in + 216);
+  int nw = (int)get32(in + 224);
+  o_geom g;
+  if (o_geom_make(dims, block, &g)) return ORC_ERR_CORRUPT;
+  if (m < 2 || m > 16 || g.nblocks != nblocks || total > in_size) return ORC_ERR_CORRUPT;
+  if (pred == ORC_PRED_MLP) {
+    if ((k != 7 && k != 13) || h1 < 1 || h1 > O_MAXH || h2 < 0 || h2 > O_MAXH ||
+        nw != orc_mlp_nweights(k, h1, h2) || s_in < 0 || s_in > 30)
+      return ORC_ERR_CORRUPT;
+  } else if (pred != ORC_PRED_LORENZO || nw != 0) {
+    return ORC_ERR_CORRUPT;
+  }
+  if (off_w + 4ull * nw > total || off_cb + 4ull * n_used > total || off_bb + 4ull * nblocks > total ||
+      off_bn + 2ull * nblocks > total || off_ov + ts * n_out > total || off_st + 4ull * swords > total)
+    return ORC_ERR_CORRUPT;
+  uint64_t n = dims[0] * dims[1] * dims[2];
+  if (n > cap_elems) return ORC_ERR_CAPACITY;
+  int nsym = 1 << m;
+  int64_t R = (int64_t)1 << (m - 1);
+  if (n_used > (uint32_t)nsym) return ORC_ERR_CORRUPT;
+
+  float* wts = NULL;
+  if (nw) {
+    wts = (float*)malloc(sizeof(float) * (size_t)nw);
+    for (int i = 0; i < nw; i++) wts[i] = f_from_bits(get32(in + off_w + 4ull * i));
+  }
+  /* canonical decoder tables */
+  uint8_t* lens = (uint8_t*)calloc((size_t)nsym, 1);
+  int ret = ORC_OK;
+  for (uint32_t t = 0; t < n_used; t++) {
+    uint32_t e = get32(in + off_cb + 4ull * t);
+    uint32_t s = e & 0xFFFFu, l = e >> 16;
+    if (s >= (uint32_t)nsym || l < 1 || l > O_LMAX || lens[s]) { ret = ORC_ERR_CORRUPT; break; }
+    lens[s] = (uint8_t)l;
+  }
+  uint32_t cnt[O_LMAX + 1] = {0}, first[O_LMAX + 1] = {0}, offs[O_LMAX + 1] = {0};
+  uint32_t* sorted = (uint32_t*)malloc(sizeof(uint32_t) * (n_used + 1));
+  if (ret == ORC_OK) {
+    for (int s = 0; s < nsym; s++) if (lens[s]) cnt[lens[s]]++;
+    uint32_t cc = 0, o = 0;
+    for (int l = 1; l <= O_LMAX; l++) {
+      cc = (cc + cnt[l - 1]) << 1;
+      first[l] = cc;
+      offs[l] = o;
+      o += cnt[l];
+      if (cnt[l] && (uint64_t)first[l] + cnt[l] > (1ull << l)) ret = ORC_ERR_CORRUPT;
+    }
+    uint32_t fill[O_LMAX + 1];
+    memcpy(fill, offs, sizeof(fill));
+    for (int s = 0; s < nsym; s++) if (lens[s]) sorted[fill[lens[s]]++] = (uint32_t)s;
+  }
+  int32_t* dq = (int32_t*)malloc(sizeof(int32_t) * g.bvol);
+  int32_t* vc = (int32_t*)malloc(sizeof(int32_t) * g.bvol);
+  uint64_t bp = 0, oi = 0;
+  uint64_t sbits = swords * 32ull;
+  for (uint64_t b = 0; b < nblocks && ret == ORC_OK; b++) {
+    uint32_t bw = get32(in + off_bb + 4ull * b);
+    uint32_t nbits = bw & 0x7FFFFFFFu;
+    int usen = (int)(bw >> 31);
+    uint32_t no = (uint32_t)in[off_bn + 2ull * b] | ((uint32_t)in[off_bn + 2ull * b + 1] << 8);
+    if (usen && !wts) { ret = ORC_ERR_CORRUPT; break; }
+    uint64_t bend = bp + nbits;
+    uint64_t oend = oi + no;
+    if (bend > sbits || oend > n_out || no < 1) { ret = ORC_ERR_CORRUPT; break; }
+    uint64_t bz = b / (g.nb[1] * g.nb[2]), by = (b / g.nb[2]) % g.nb[1], bx = b % g.nb[2];
+    uint64_t o0 = bz * block[0], o1 = by * block[1], o2 = bx * block[2];
+    int e0 = (int)((dims[0] - o0) < (uint64_t)block[0] ? dims[0] - o0 : (uint64_t)block[0]);
+    int e1 = (int)((dims[1] - o1) < (uint64_t)block[1] ? dims[1] - o1 : (uint64_t)block[1]);
+    int e2 = (int)((dims[2] - o2) < (uint64_t)block[2] ? dims[2] - o2 : (uint64_t)block[2]);
+    int32_t da = 0;
+    for (int lz = 0; lz < e0 && ret == ORC_OK; lz++)
+      for (int ly = 0; ly < e1 && ret == ORC_OK; ly++)
+        for (int lx = 0; lx < e2 && ret == ORC_OK; lx++) {
+          int j = (lz * e1 + ly) * e2 + lx;
+          uint64_t ig = ((o0 + lz) * dims[1] + (o1 + ly)) * dims[2] + (o2 + lx);
+          uint32_t sym = 0;
+          if (j > 0) {
+            uint32_t code = 0;
+            int found = 0;
+            for (int l = 1; l <= O_LMAX; l++) {
+              if (bp >= bend) break;
+              uint32_t word = get32(in + off_st + 4ull * (bp >> 5));
+              uint32_t bit = (word >> (31u - (uint32_t)(bp & 31u))) & 1u;
+              bp++;
+              code = (code << 1) | bit;
+              if (cnt[l] && code - first[l] < cnt[l]) { sym = sorted[offs[l] + code - first[l]]; found = 1; break; }
+            }
+            if (!found) { ret = ORC_ERR_CORRUPT; break; }
+          }
+          int32_t q;
+          if (j == 0 || sym == 0) {
+            if (oi >= oend) { ret = ORC_ERR_CORRUPT; break; }
+            int ok;
+            if (dtype == ORC_F32) {
+              float v;
+              memcpy(&v, in + off_ov + ts * oi, 4);
+              ((float*)xo)[ig] = v;
+              orc_transform32(v, &c, &q, &ok);
+            } else {
+              double v;
+              memcpy(&v, in + off_ov + ts * oi, 8);
+              ((double*)xo)[ig] = v;
+              orc_transform64(v, &c, &q, &ok);
+            }
+            oi++;
+            if (j == 0) da = q;
+          } else {
+            int32_t in7[7];
+            for (int i = 0; i < 7; i++) {
+              int qz = lz + O_S7[i][0], qy = ly + O_S7[i][1], qx = lx + O_S7[i][2];
+              in7[i] = (qz >= 0 && qy >= 0 && qx >= 0) ? vc[(qz * e1 + qy) * e2 + qx] : 0;
+            }
+            int64_t pr;
+            if (usen) {
+              int32_t inn[13];
+              for (int i = 0; i < k; i++) {
+                int dz, dy, dx;
+                o_stencil(k, i, &dz, &dy, &dx);
+                int qz = lz + dz, qy = ly + dy, qx = lx + dx;
+                inn[i] = (qz >= 0 && qy >= 0 && qx >= 0 && qz < e0 && qy < e1 && qx < e2)
+                             ? vc[(qz * e1 + qy) * e2 + qx] : 0;
+              }
+              pr = orc_mlp_pred32(wts, k, h1, h2, s_in, inn);
+            } else {
+              pr = o_lorenzo(in7);
+            }
+            int64_t qq = (int64_t)da + pr + ((int64_t)sym - R);
+            if (qq > 2147483647LL || qq < -2147483647LL) { ret = ORC_ERR_CORRUPT; break; }
+            q = (int32_t)qq;
+            if (dtype == ORC_F32) ((float*)xo)[ig] = orc_recon32(q, &c);
+            else ((double*)xo)[ig] = orc_recon64(q, &c);
+          }
+          dq[j] = q;
+          int64_t v = (int64_t)q - (int64_t)da;
+          vc[j] = (int32_t)(v > O_VCLAMP ? O_VCLAMP : (v < -O_VCLAMP ? -O_VCLAMP : v));
+        }
+    if (ret == ORC_OK && (bp != bend || oi != oend)) ret = ORC_ERR_CORRUPT;
+  }
+  free(vc); free(dq); free(sorted); free(lens); free(wts);
+  return ret;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Step a3: training (Section IV.C, Section V).                               */
+/* Samples: a non-anchor point is drawn iff the high 32 bits of               */
+/* mix64(seed, linear index) fall below thr32 (10% by default); it goes to    */
+/* validation iff the low 32 bits mod 10 < 2 (the 8:2 split).  Samples are    */
+/* listed in block order, then local raster order.  A sample is used for      */
+/* learning only if the point, its anchor and its in-block stencil            */
+/* neighbours share one non-zero sign class (Reading: the paper trains on    */
+/* sampled blocks; sign and zero jumps are unpredictable balance points).     */
+/* ------------------------------------------------------------------------- */
+int orc_count_samples(const uint64_t dims[3], const int block[3], uint64_t seed, uint32_t thr32,
+                      uint64_t* ntrain, uint64_t* nval) {
+  o_geom g;
+  if (o_geom_make(dims, block, &g)) return ORC_ERR_ARG;
+  uint64_t nt = 0, nv = 0;
+  for (uint64_t b = 0; b < g.nblocks; b++) {
+    uint64_t bz = b / (g.nb[1] * g.nb[2]), by = (b / g.nb[2]) % g.nb[1], bx = b % g.nb[2];
+    uint64_t o0 = bz * block[0], o1 = by * block[1], o2 = bx * block[2];
+    for (uint64_t lz = 0; lz < (uint64_t)block[0] && o0 + lz < dims[0]; lz++)
+      for (uint64_t ly = 0; ly < (uint64_t)block[1] && o1 + ly < dims[1]; ly++)
+        for (uint64_t lx = 0; lx < (uint64_t)block[2] && o2 + lx < dims[2]; lx++) {
+          if (lz == 0 && ly == 0 && lx == 0) continue;
+          uint64_t ig = ((o0 + lz) * dims[1] + (o1 + ly)) * dims[2] + (o2 + lx);
+          uint64_t h = orc_mix64(seed, ig);
+          if ((uint32_t)(h >> 32) >= thr32) continue;
+          if ((uint32_t)h % 10u < 2u) nv++; else nt++;
+        }
+  }
+  *ntrain = nt;
+  *nval = nv;
+  return ORC_OK;
+}
+
+/* Gather: inputs [count][k] (clamped centred codes), target [count], use [count]. */
+int orc_gather_samples(const void* x, const uint64_t dims[3], int dtype, const orc_consts* c,
+                       const int block[3], int k, uint64_t seed, uint32_t thr32,
+                       int32_t* tin, int32_t* ttg, uint8_t* tuse,
+                       int32_t* vin, int32_t* vtg, uint8_t* vuse) {
+  o_geom g;
+  if (o_geom_make(dims, block, &g)) return ORC_ERR_ARG;
+  uint64_t n = dims[0] * dims[1] * dims[2];
+  int32_t* dq = (int32_t*)malloc(sizeof(int32_t) * n);
+  for (uint64_t i = 0; i < n; i++) {
+    int ok;
+    if (dtype == ORC_F32) orc_transform32(((const float*)x)[i], c, &dq[i], &ok);
+    else orc_transform64(((const double*)x)[i], c, &dq[i], &ok);
+  }
+  uint64_t it = 0, iv = 0;
+  for (uint64_t b = 0; b < g.nblocks; b++) {
+    uint64_t bz = b / (g.nb[1] * g.nb[2]), by = (b / g.nb[2]) % g.nb[1], bx = b % g.nb[2];
+    uint64_t o0 = bz * block[0], o1 = by * block[1], o2 = bx * block[2];
+    int e0 = (int)((dims[0] - o0) < (uint64_t)block[0] ? dims[0] - o0 : (uint64_t)block[0]);
+    int e1 = (int)((dims[1] - o1) < (uint64_t)block[1] ? dims[1] - o1 : (uint64_t)block[1]);
+    int e2 = (int)((dims[2] - o2) < (uint64_t)block[2] ? dims[2] - o2 : (uint64_t)block[2]);
+    uint64_t ia = (o0 * dims[1] + o1) * dims[2] + o2;
+    int32_t da = dq[ia];
+    int ca = o_class(da, c);
+    for (int lz = 0; lz < e0; lz++)
+      for (int ly = 0; ly < e1; ly++)
+        for (int lx = 0; lx < e2; lx++) {
+          if (lz == 0 && ly == 0 && lx == 0) continue;
+          uint64_t ig = ((o0 + lz) * dims[1] + (o1 + ly)) * dims[2] + (o2 + lx);
+          uint64_t h = orc_mix64(seed, ig);
+          if ((uint32_t)(h >> 32) >= thr32) continue;
+          int isval = (uint32_t)h % 10u < 2u;
+          int32_t* inp = isval ? vin + (size_t)iv * k : tin + (size_t)it * k;
+          int cp = o_class(dq[ig], c);
+          int use = cp != 0 && cp == ca;
+          for (int i = 0; i < k; i++) {
+            int dz, dy, dx;
+            o_stencil(k, i, &dz, &dy, &dx);
+            int qz = lz + dz, qy = ly + dy, qx = lx + dx;
+            int32_t v = 0;
+            if (qz >= 0 && qy >= 0 && qx >= 0 && qz < e0 && qy < e1 && qx < e2) {
+              uint64_t iq = ((o0 + qz) * dims[1] + (o1 + qy)) * dims[2] + (o2 + qx);
+              int64_t d = (int64_t)dq[iq] - (int64_t)da;
+              v = (int32_t)(d > O_VCLAMP ? O_VCLAMP : (d < -O_VCLAMP ? -O_VCLAMP : d));
+              if (o_class(dq[iq], c) != cp) use = 0;
+            }
+            inp[i] = v;
+          }
+          int64_t d = (int64_t)dq[ig] - (int64_t)da;
+          int32_t tv = (int32_t)(d > O_VCLAMP ? O_VCLAMP : (d < -O_VCLAMP ? -O_VCLAMP : d));
+          if (isval) { vtg[iv] = tv; vuse[iv] = (uint8_t)use; iv++; }
+          else { ttg[it] = tv; tuse[it] = (uint8_t)use; it++; }
+        }
+  }
+  free(dq);
+  return ORC_OK;
+}
+
+/* Input scale: smallest s in [0, 30] with (sum min(t^2, 2^40)) >> 2s < n_used. */
+int orc_input_shift(const int32_t* tg, const uint8_t* use, uint64_t n) {
+  uint64_t s2 = 0, nu = 0;
+  for (uint64_t i = 0; i < n; i++) {
+    if (!use[i]) continue;
+    uint64_t a = (uint64_t)((int64_t)tg[i] < 0 ? -(int64_t)tg[i] : (int64_t)tg[i]);
+    uint64_t q = a * a;
+    if (q > (1ull << 40)) q = 1ull << 40;
+    s2 += q;
+    nu++;
+  }
+  if (nu == 0) return 0;
+  int s = 0;
+  while (s < 30 && (s2 >> (2 * s)) >= nu) s++;
+  return s;
+}
+
+/* Initial weights (Section IV.B): hidden units 0 and 1 take the +/- Lorenzo
+ * weights with zero bias; with two hidden layers the pair is carried through
+ * by [1,-1] and [-1,1]; the output takes (c, -c) with c = 1/(1+alpha)^L so that
+ * the network equals Lorenzo.  Reading: the paper's "two numbers summing to
+ * one" cannot give Lorenzo through a leaky ReLU; this pair does.  Other weights
+ * of hidden layers start at small hash-derived values in [-2^-10, 2^-10); other
+ * output weights and all other biases start at zero. */
+void orc_init_weights(float* w, int k, int h1, int h2, uint64_t seed) {
+  int nw = orc_mlp_nweights(k, h1, h2);
+  for (int i = 0; i < nw; i++) w[i] = 0.0f;
+  uint64_t ctr = 0;
+  float* W1 = w;
+  for (int j = 0; j < h1; j++)
+    for (int i = 0; i < k; i++) {
+      float val;
+      if (j < 2 && h1 >= 2) val = (float)(j == 0 ? o_lz_weight(k, i) : -o_lz_weight(k, i));
+      else val = (float)((int32_t)(orc_mix64(seed, ctr) >> 40) - 8388608) * 0x1p-33f;
+      ctr++;
+      W1[j * k + i] = val;
+    }
+  float* p = W1 + h1 * k + h1;
+  float a1 = 1.0f + O_ALPHA;
+  float cc;
+  if (h2 > 0) {
+    float* W2 = p;
+    for (int j = 0; j < h2; j++)
+      for (int i = 0; i < h1; i++) {
+        float val;
+        if (j < 2) val = (i == j) ? 1.0f : ((i < 2) ? -1.0f : 0.0f);
+        else val = (float)((int32_t)(orc_mix64(seed, ctr) >> 40) - 8388608) * 0x1p-33f;
+        ctr++;
+        W2[j * h1 + i] = val;
+      }
+    p = W2 + h2 * h1 + h2;
+    cc = 1.0f / (a1 * a1);
+  } else {
+    cc = 1.0f / a1;
+  }
+  p[0] = cc;
+  p[1] = -cc;
+}
+
+#define O_BATCH 256
+
+/* Pairwise tree sum over O_BATCH rows: level by level, element 2i + 2i+1. */
+static float o_treesum(float* a) {
+  for (int w = O_BATCH / 2; w >= 1; w /= 2)
+    for (int i = 0; i < w; i++) a[i] = a[2 * i] + a[2 * i + 1];
+  return a[0];
+}
+
+/* Gradient of the minibatch loss
+ *   (1/B) sum_r use_r (o_r - t_r)^2   (+ L2 handled in the update)
+ * with t_r = target_r 2^-s (targets in scaled units), B = rows.  Every
+ * parameter's gradient is a pairwise tree sum of per-row terms (rows >= B
+ * contribute +0). */
+void orc_batch_grad(const float* w, int k, int h1, int h2, int s_in,
+                    const int32_t* in, const int32_t* tg, const uint8_t* use, int B, float* g) {
+  int nw = orc_mlp_nweights(k, h1, h2);
+  int hl = h2 > 0 ? h2 : h1;
+  float sig = ldexpf(1.0f, -s_in);
+  const float* W1 = w;
+  const float* b1 = W1 + h1 * k;
+  const float* W2 = b1 + h1;
+  const float* b2 = W2 + (h2 > 0 ? h2 * h1 : 0);
+  const float* W3 = h2 > 0 ? b2 + h2 : W2;
+  float ginv = 2.0f / (float)B;
+  /* per-row terms for each parameter: [nw][O_BATCH] */
+  float* terms = (float*)calloc((size_t)nw * O_BATCH, sizeof(float));
+  for (int r = 0; r < B; r++) {
+    float u[32], a1[O_MAXH], z1[O_MAXH], a2[O_MAXH], z2[O_MAXH], d2[O_MAXH], d1[O_MAXH];
+    for (int i = 0; i < k; i++) u[i] = (float)in[(size_t)r * k + i] * sig;
+    for (int j = 0; j < h1; j++) {
+      float acc = b1[j];
+      for (int i = 0; i < k; i++) acc = fmaf(W1[j * k + i], u[i], acc);
+      z1[j] = acc;
+      a1[j] = acc >= 0.0f ? acc : acc * O_ALPHA;
+    }
+    const float* hv = a1;
+    if (h2 > 0) {
+      for (int j = 0; j < h2; j++) {
+        float acc = b2[j];
+        for (int i = 0; i < h1; i++) acc = fmaf(W2[j * h1 + i], a1[i], acc);
+        z2[j] = acc;
+        a2[j] = acc >= 0.0f ? acc : acc * O_ALPHA;
+      }
+      hv = a2;
+    }
+    float o = W3[hl];
+    for (int j = 0; j < hl; j++) o = fmaf(W3[j], hv[j], o);
+    float t = (float)tg[r] * sig;
+    float go = use[r] ? (o - t) * ginv : 0.0f;
+    /* output layer */
+    int base3 = (int)(W3 - w);
+    for (int j = 0; j < hl; j++) terms[(size_t)(base3 + j) * O_BATCH + r] = go * hv[j];
+    terms[(size_t)(base3 + hl) * O_BATCH + r] = go;
+    float* dtop;
+    if (h2 > 0) {
+      for (int j = 0; j < h2; j++) {
+        float tt = go * W3[j];
+        d2[j] = z2[j] >= 0.0f ? tt : tt * O_ALPHA;
+      }
+      int baseW2 = (int)(W2 - w), baseb2 = (int)(b2 - w);
+      for (int j = 0; j < h2; j++) {
+        for (int i = 0; i < h1; i++) terms[(size_t)(baseW2 + j * h1 + i) * O_BATCH + r] = d2[j] * a1[i];
+        terms[(size_t)(baseb2 + j) * O_BATCH + r] = d2[j];
+      }
+      for (int i = 0; i < h1; i++) {
+        float s = 0.0f;
+        for (int j = 0; j < h2; j++) s = fmaf(W2[j * h1 + i], d2[j], s);
+        d1[i] = z1[i] >= 0.0f ? s : s * O_ALPHA;
+      }
+      dtop = d1;
+    } else {
+      for (int i = 0; i < h1; i++) {
+        float tt = go * W3[i];
+        d1[i] = z1[i] >= 0.0f ? tt : tt * O_ALPHA;
+      }
+      dtop = d1;
+    }
+    int baseb1 = (int)(b1 - w);
+    for (int j = 0; j < h1; j++) {
+      for (int i = 0; i < k; i++) terms[(size_t)(j * k + i) * O_BATCH + r] = dtop[j] * u[i];
+      terms[(size_t)(baseb1 + j) * O_BATCH + r] = dtop[j];
+    }
+  }
+  for (int q = 0; q < nw; q++) g[q] = o_treesum(terms + (size_t)q * O_BATCH);
+  free(terms);
+}
+
+/* One SGD update: weights w <- w - lr (g + 2 lambda w); biases w <- w - lr g. */
+void orc_sgd_update(float* w, const float* g, int k, int h1, int h2, float lr, float lam) {
+  int nw = orc_mlp_nweights(k, h1, h2);
+  int hl = h2 > 0 ? h2 : h1;
+  float lam2 = lam + lam;
+  for (int q = 0; q < nw; q++) {
+    int isbias;
+    if (q < h1 * k) isbias = 0;
+    else if (q < h1 * k + h1) isbias = 1;
+    else if (h2 > 0 && q < h1 * k + h1 + h2 * h1) isbias = 0;
+    else if (h2 > 0 && q < h1 * k + h1 + h2 * h1 + h2) isbias = 1;
+    else isbias = (q == nw - 1);
+    (void)hl;
+    if (isbias) {
+      float u = lr * g[q];
+      w[q] = w[q] - u;
+    } else {
+      float t = lam2 * w[q];
+      float gt = g[q] + t;
+      float u = lr * gt;
+      w[q] = w[q] - u;
+    }
+  }
+}
+
+/* One epoch of minibatch SGD over the training list, in list order. */
+void orc_train_epoch(float* w, int k, int h1, int h2, int s_in, const int32_t* in, const int32_t* tg,
+                     const uint8_t* use, uint64_t n, float lr, float lam, uint64_t max_steps) {
+  int nw = orc_mlp_nweights(k, h1, h2);
+  float* g = (float*)malloc(sizeof(float) * (size_t)nw);
+  uint64_t steps = 0;
+  for (uint64_t s = 0; s < n && steps < max_steps; s += O_BATCH, steps++) {
+    int B = (int)((n - s) < O_BATCH ? (n - s) : O_BATCH);
+    orc_batch_grad(w, k, h1, h2, s_in, in + s * (uint64_t)k, tg + s, use + s, B, g);
+    orc_sgd_update(w, g, k, h1, h2, lr, lam);
+  }
+  free(g);
+}
+
+/* Validation cost: sum of bitlen(min(|t - pred|, R)) over used samples;
+ * w == NULL scores the Lorenzo predictor. */
+uint64_t orc_val_cost(const float* w, int k, int h1, int h2, int s_in, const int32_t* in,
+                      const int32_t* tg, const uint8_t* use, uint64_t n, int m) {
+  int64_t R = (int64_t)1 << (m - 1);
+  uint64_t cost = 0;
+  for (uint64_t i = 0; i < n; i++) {
+    if (!use[i]) continue;
+    int64_t pr;
+    if (w) {
+      pr = orc_mlp_pred32(w, k, h1, h2, s_in, in + i * (uint64_t)k);
+    } else {
+      pr = 0;
+      for (int j = 0; j < k; j++) pr += (int64_t)o_lz_weight(k, j) * in[i * (uint64_t)k + j];
+    }
+    int64_t d = (int64_t)tg[i] - pr;
+    uint64_t a = (uint64_t)(d < 0 ? -d : d);
+    cost += (uint64_t)o_bitlen(a < (uint64_t)R ? a : (uint64_t)R);
+  }
+  return cost;
+}
+
+/* Full training phase: gather, scale, train nmodels (lr, lambda) pairs from the
+ * same initial weights, score on validation, choose.  Returns the chosen index
+ * (-1 = Lorenzo). */
+int orc_train(const void* x, const uint64_t dims[3], int dtype, double eb, const int block[3],
+              int k, int h1, int h2, int m, uint64_t seed, uint32_t thr32, int nmodels,
+              const float* lrs, const float* lams, float* w_out /* nmodels * nw */,
+              int* s_in_out, uint64_t* costs /* nmodels + 1, last = Lorenzo */) {
+  uint64_t n = dims[0] * dims[1] * dims[2];
+  double amin, amax;
+  int trivial;
+  int st = orc_stats(x, n, dtype, &amin, &amax, &trivial);
+  if (st) return st;
+  orc_consts c;
+  st = orc_make_consts(dtype, amin, amax, trivial, eb, &c);
+  if (st) return st;
+  uint64_t nt, nv;
+  st = orc_count_samples(dims, block, seed, thr32, &nt, &nv);
+  if (st) return st;
+  int32_t* tin = (int32_t*)malloc(sizeof(int32_t) * (nt * k + 1));
+  int32_t* ttg = (int32_t*)malloc(sizeof(int32_t) * (nt + 1));
+  uint8_t* tus = (uint8_t*)malloc(nt + 1);
+  int32_t* vin = (int32_t*)malloc(sizeof(int32_t) * (nv * k + 1));
+  int32_t* vtg = (int32_t*)malloc(sizeof(int32_t) * (nv + 1));
+  uint8_t* vus = (uint8_t*)malloc(nv + 1);
+  orc_gather_samples(x, dims, dtype, &c, block, k, seed, thr32, tin, ttg, tus, vin, vtg, vus);
+  int s_in = orc_input_shift(ttg, tus, nt);
+  *s_in_out = s_in;
+  int nw = orc_mlp_nweights(k, h1, h2);
+  int best = -1;
+  uint64_t lz = orc_val_cost(NULL, k, h1, h2, s_in, vin, vtg, vus, nv, m);
+  costs[nmodels] = lz;
+  uint64_t bestc = lz;
+  for (int h = 0; h < nmodels; h++) {
+    float* w = w_out + (size_t)h * nw;
+    orc_init_weights(w, k, h1, h2, seed ^ 0x5DEECE66DULL);
+    orc_train_epoch(w, k, h1, h2, s_in, tin, ttg, tus, nt, lrs[h], lams[h], ~0ull);
+    costs[h] = orc_val_cost(w, k, h1, h2, s_in, vin, vtg, vus, nv, m);
+    if (costs[h] < bestc) { bestc = costs[h]; best = h; }
+  }
+  free(tin); free(ttg); free(tus); free(vin); free(vtg); free(vus);
+  return best;
+}

@@ -1,0 +1,62 @@
+/*
+ * CPU oracle for the perceptron-predicted, pointwise-relative-error-bounded
+ * compressor (arXiv 2309.09778).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code with
+ * the CUDA path; both sides follow the same written specification.
+ *
+ * Everything here is plain, slow, single-threaded C.  Floating-point work is
+ * IEEE round-to-nearest with FMA contraction disabled at compile time; where a
+ * fused multiply-add is part of the specification it is written as fmaf/fma.
+ */
+#ifndef PC_ORACLE_H
+#define PC_ORACLE_H
+#include <stdint.h>
+#include <stddef.h>
+
+#define ORC_OK 0
+#define ORC_ERR_ARG (-1)
+#define ORC_ERR_DTYPE (-2)
+#define ORC_ERR_NONFINITE (-3)
+#define ORC_ERR_CAPACITY (-4)
+#define ORC_ERR_CORRUPT (-5)
+#define ORC_ERR_EB_RANGE (-8)
+
+#define ORC_F32 0
+#define ORC_F64 1
+
+#define ORC_PRED_LORENZO 0
+#define ORC_PRED_MLP 1
+
+typedef struct {
+  int dtype;
+  double eb, abs_min, abs_max;
+  int trivial;           /* field has no normal value */
+  double step64;         /* 2 b_a in double */
+  float step32, inv32, ebdn32;
+  double stepd, invd, ebdnd;
+  int32_t Kp, Kn, Zq, S;
+} orc_consts;
+
+typedef struct {
+  double eb;
+  int block[3];
+  int pred;              /* ORC_PRED_* */
+  int stencil;           /* 7 or 13 */
+  int h1, h2;            /* hidden widths; h2 == 0: one hidden layer */
+  int m;                 /* code bits; radius R = 2^(m-1) */
+  int s_in;              /* input scale: u = v * 2^-s_in */
+  const float* weights;  /* MLP weight blob, NULL for Lorenzo only */
+} orc_params;
+
+typedef struct {
+  int32_t* dq;           /* [N] integer log codes, field order */
+  uint8_t* ok;           /* [N] per-point bound check */
+  uint16_t* codes;       /* [nblocks * bvol] block-strided codes, slot 0 (anchor) = 0 */
+  uint8_t* nnflag;       /* [nblocks] 1 = block used the perceptron */
+  uint64_t* hist;        /* [2^m] code histogram */
+  uint8_t* lens;         /* [2^m] Huffman code lengths */
+} orc_dump;
+
+#endif

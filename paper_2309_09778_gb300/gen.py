@@ -1,0 +1,97 @@
+"""Seeded synthetic input fields.
+
+This module only draws inputs: it holds none of the compressor's arithmetic and
+is shared, as input bits, by the CPU oracle tests and the CUDA path.
+
+The paper evaluates on SEG-Y seismic volumes (Section VI.A), which are not
+available here.  Smooth Gaussian random fields stand in for them: white noise
+from numpy's Philox counter-based generator, shaped in Fourier space to a power
+spectrum |k|^-beta (k = 0 mode removed), normalised to mean 0 and sd 1.  Values
+are made log-normal in magnitude with an independent sign field, and exact
+zeros fill the regions where a third field lies below a quantile, which gives
+contiguous zero regions like muted seismic zones.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def grf(shape, beta: float, seed: int) -> np.ndarray:
+    """Gaussian random field with power spectrum |k|^-beta, float64, mean 0, sd 1."""
+    shape = tuple(int(s) for s in shape)
+    rng = np.random.Generator(np.random.Philox(seed))
+    white = rng.standard_normal(shape)
+    spec = np.fft.rfftn(white)
+    k2 = np.zeros(spec.shape)
+    for ax, n in enumerate(shape):
+        if ax == len(shape) - 1:
+            f = np.fft.rfftfreq(n)
+        else:
+            f = np.fft.fftfreq(n)
+        sl = [None] * len(shape)
+        sl[ax] = slice(None)
+        k2 = k2 + (f[tuple(sl)] ** 2)
+    with np.errstate(divide="ignore"):
+        amp = np.where(k2 > 0, k2 ** (-beta / 4.0), 0.0)
+    g = np.fft.irfftn(spec * amp, s=shape, axes=tuple(range(len(shape))))
+    g -= g.mean()
+    sd = g.std()
+    if sd > 0:
+        g /= sd
+    return g
+
+
+def signed_lognormal(shape, beta: float, seed: int, log_scale: float = 2.0,
+                     zero_frac: float = 0.05, dtype=np.float32) -> np.ndarray:
+    """|x| = exp(log_scale * G1), sign from G2, exact zeros where G3 < its quantile."""
+    g1 = grf(shape, beta, seed)
+    g2 = grf(shape, beta, seed + 1)
+    x = np.exp(log_scale * g1) * np.where(g2 >= 0, 1.0, -1.0)
+    if zero_frac > 0:
+        g3 = grf(shape, beta, seed + 2)
+        thr = np.quantile(g3, zero_frac)
+        x = np.where(g3 < thr, 0.0, x)
+    return x.astype(dtype)
+
+
+def positive_lognormal(shape, beta: float, seed: int, log_scale: float,
+                       dtype=np.float32) -> np.ndarray:
+    """Density-like positive field exp(log_scale * G)."""
+    return np.exp(log_scale * grf(shape, beta, seed)).astype(dtype)
+
+
+def signed_grf(shape, beta: float, seed: int, dtype=np.float32) -> np.ndarray:
+    """Velocity-like signed field G itself."""
+    return grf(shape, beta, seed).astype(dtype)
+
+
+def wide_range(shape, beta: float, seed: int, decades: float = 8.0,
+               zero_frac: float = 0.01, dtype=np.float64) -> np.ndarray:
+    """|x| = 10^(decades * G1 / max|G1|), mixed sign, exact zeros (float64 workload)."""
+    g1 = grf(shape, beta, seed)
+    g2 = grf(shape, beta, seed + 1)
+    m = np.abs(g1).max()
+    x = np.power(10.0, decades * g1 / (m if m > 0 else 1.0)) * np.where(g2 >= 0, 1.0, -1.0)
+    if zero_frac > 0:
+        g3 = grf(shape, beta, seed + 2)
+        thr = np.quantile(g3, zero_frac)
+        x = np.where(g3 < thr, 0.0, x)
+    return x.astype(dtype)
+
+
+# Named workloads.  Sizes, spectra, value distributions and error bounds follow
+# the evaluation plan: a small 64^3 single-precision case, a 100x500x500 case,
+# a 512^3 density/velocity pair and a 256x384x384 double-precision case.
+WORKLOADS = {
+    "grf64_f32": dict(shape=(64, 64, 64), beta=3.0, seed=0, zero_frac=0.05, eb=1e-2),
+    "grf100x500x500_f32": dict(shape=(100, 500, 500), beta=11.0 / 3.0, seed=0,
+                               zero_frac=0.02, eb=1e-3),
+}
+
+
+def workload(name: str, shape=None) -> tuple[np.ndarray, float]:
+    """Return (field, eb_rel) for a named workload, optionally at a smaller shape."""
+    w = WORKLOADS[name]
+    shp = w["shape"] if shape is None else shape
+    x = signed_lognormal(shp, w["beta"], w["seed"], 2.0, w["zero_frac"])
+    return x, w["eb"]
