@@ -1,0 +1,165 @@
+/*
+ * pc.h - C ABI of the GB300 perceptron-predicted, pointwise-relative-error
+ * bounded lossy compressor (arXiv 2309.09778).
+ *
+ * Method (paper sections):
+ *   Section III (Eq. 6-12)  relative -> absolute map x -> log2(|x| factor), with a
+ *                           positive and a negative factor so that the sign lives
+ *                           in the code and needs no extra storage;
+ *   Section IV.A-B          prediction of each code from its causal in-block
+ *                           neighbours by a three-layer perceptron (leaky ReLU),
+ *                           with the Lorenzo predictor as per-block fallback;
+ *   Section IV.D            data selection from true (pre-quantized) values, which
+ *                           makes prediction parallel; balance points (outliers);
+ *   Section IV.A, V (Alg. 1) linear-scaling quantization, Huffman coding and the
+ *                           bitstream; decompression inverts every step.
+ *
+ * Conventions for every entry point:
+ *   - Device pointers ("d_") are CUDA global memory of the current device; host
+ *     pointers ("h_") are ordinary host memory.  The caller owns every buffer and
+ *     the stream.  No entry point allocates device memory: scratch space comes
+ *     from the caller's workspace (size from the *_workspace_size calls).
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.  Work is stream-ordered; calls that return a host value (sizes)
+ *     synchronize that stream before returning.
+ *   - Fields are C-order (row-major) arrays of dims[0] x dims[1] x dims[2]
+ *     elements, dims[2] fastest.  1-D and 2-D fields use leading dims of 1.
+ *   - Every call returns a status: PC_OK (0) or a negative PC_ERR_* code; no
+ *     call aborts the process.  pc_strerror() names a status.
+ *   - The library fails loudly: there is no CPU fallback for any step.
+ */
+#ifndef PC_H
+#define PC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define PC_OK 0
+#define PC_ERR_ARG (-1)        /* bad argument (sizes, shapes, eb outside (0,1), ...) */
+#define PC_ERR_DTYPE (-2)      /* dtype not PC_F32 / PC_F64 */
+#define PC_ERR_NONFINITE (-3)  /* NaN or Inf in the input field */
+#define PC_ERR_CAPACITY (-4)   /* output or workspace buffer too small */
+#define PC_ERR_CORRUPT (-5)    /* compressed stream fails validation */
+#define PC_ERR_TIMEOUT (-6)    /* a bounded device wait ran out */
+#define PC_ERR_CUDA (-7)       /* a CUDA runtime call failed */
+#define PC_ERR_EB_RANGE (-8)   /* codes would leave +-2^30 (eb too small for the dtype) */
+
+/* element types */
+#define PC_F32 0
+#define PC_F64 1
+
+/* predictor forms */
+#define PC_PRED_LORENZO 0      /* Lorenzo only (Section IV.A) */
+#define PC_PRED_MLP_FP32 1     /* perceptron in FP32 on CUDA cores, Lorenzo per-block fallback */
+
+typedef struct {
+  double eb_rel;          /* pointwise relative bound b_r, 0 < eb_rel < 1 (Eq. 1) */
+  int block[3];           /* compression block shape, product in [2, 4096] (Section IV.C) */
+  int pred;               /* PC_PRED_* */
+  int stencil;            /* perceptron inputs: 7 (3-D Lorenzo set) or 13 (causal half of 3x3x3) */
+  int hidden[2];          /* hidden widths {h1, h2}; h2 = 0 gives the paper's single hidden layer */
+  int m;                  /* code bits, 2..16: codes span 0 .. 2^m - 1 (Section IV.C) */
+  int s_in;               /* input scale: inputs are codes * 2^-s_in (from pc_train) */
+  const float* h_weights; /* host pointer to the perceptron weight blob (pc_mlp_nweights floats):
+                             W1[h1][k], b1[h1], W2[h2][h1], b2[h2], W3[hl], b3 (hl = h2 or h1);
+                             ignored for PC_PRED_LORENZO */
+} pc_params;
+
+/* Number of floats in the weight blob for stencil k and hidden widths h1, h2. */
+int pc_mlp_nweights(int k, int h1, int h2);
+
+/* Upper bound, in bytes, on the compressed size of a field (header, weights,
+ * codebook, block table, balance points, bitstream).  0 on bad arguments. */
+size_t pc_compress_bound(const size_t dims[3], int dtype, const pc_params* p);
+
+/* Device workspace, in bytes, that pc_compress needs for this field. */
+int pc_compress_workspace_size(const size_t dims[3], int dtype, const pc_params* p, size_t* ws_bytes);
+
+/*
+ * Compress a device-resident field (Algorithm 1).
+ *   d_field   [in]  dims[0]*dims[1]*dims[2] elements of dtype, device memory.
+ *   d_out     [out] device buffer of out_cap bytes; receives the container.
+ *   out_size  [out] host size_t: container bytes written.
+ *   d_ws      [scratch] device workspace of ws_bytes >= pc_compress_workspace_size.
+ * The stream is synchronized once, at the end, to read the size and status.
+ * Errors: PC_ERR_ARG, PC_ERR_DTYPE, PC_ERR_NONFINITE, PC_ERR_EB_RANGE,
+ * PC_ERR_CAPACITY (out_cap or ws_bytes too small), PC_ERR_CUDA.
+ */
+int pc_compress(const void* d_field, const size_t dims[3], int dtype, const pc_params* p,
+                void* d_out, size_t out_cap, size_t* out_size,
+                void* d_ws, size_t ws_bytes, void* stream);
+
+/*
+ * Read the fixed 256-byte container header from a host copy (h_hdr, hdr_bytes >= 256):
+ * dims, dtype and the decompression workspace size.  Validates magic, version
+ * and header CRC; PC_ERR_CORRUPT otherwise.
+ */
+int pc_header_info(const void* h_hdr, size_t hdr_bytes, size_t dims_out[3], int* dtype_out,
+                   size_t* ws_bytes);
+
+/*
+ * Decompress a device-resident container (Section V, decompression).
+ *   d_in       [in]  in_size bytes of container, device memory.
+ *   d_field    [out] device buffer of field_cap bytes; receives the field.
+ *   dims_out, dtype_out [out] host.
+ *   d_ws       [scratch] device workspace of ws_bytes (see pc_header_info).
+ * Reads the header and weights to the host first (one small copy and a
+ * stream synchronization), validates everything it reads, and reports a
+ * damaged stream as PC_ERR_CORRUPT without faulting.
+ */
+int pc_decompress(const void* d_in, size_t in_size, void* d_field, size_t field_cap,
+                  size_t dims_out[3], int* dtype_out, void* d_ws, size_t ws_bytes, void* stream);
+
+/*
+ * End-to-end forms with HOST buffers: copy the input host -> device, run the
+ * device call, copy the result device -> host, synchronize.  The caller passes
+ * device staging buffers (nothing is allocated): d_field_stage holds the field
+ * (field bytes), d_out_stage the container (d_out_cap bytes).  h_field and h_out
+ * should be pinned for full copy speed.
+ */
+int pc_compress_host(const void* h_field, const size_t dims[3], int dtype, const pc_params* p,
+                     void* h_out, size_t out_cap, size_t* out_size,
+                     void* d_field_stage, void* d_out_stage, size_t d_out_cap,
+                     void* d_ws, size_t ws_bytes, void* stream);
+int pc_decompress_host(const void* h_in, size_t in_size, void* h_field, size_t field_cap,
+                       size_t dims_out[3], int* dtype_out,
+                       void* d_in_stage, size_t d_in_cap, void* d_field_stage,
+                       void* d_ws, size_t ws_bytes, void* stream);
+
+/*
+ * Training phase (Section IV.C) on the device: sample stencils (rate thr32 / 2^32
+ * of non-anchor points, 10% by default), split 8:2, train nmodels copies of the
+ * Lorenzo-initialised perceptron for one epoch of minibatch SGD (batch 256) with
+ * learning rates lrs[i] and L2 weights lams[i], score each and Lorenzo on the
+ * validation samples by residual bit length, and choose.
+ *   h_weights_out [out] host, nmodels * pc_mlp_nweights floats (every trained model).
+ *   s_in_out      [out] input scale exponent.
+ *   chosen_out    [out] index of the chosen model, -1 if Lorenzo scored best.
+ *   h_costs       [out] host, nmodels + 1 validation costs (last = Lorenzo), may be NULL.
+ * Uses p->block, p->stencil, p->hidden, p->m and p->eb_rel.
+ */
+int pc_train_workspace_size(const size_t dims[3], int dtype, const pc_params* p, unsigned int thr32,
+                            int nmodels, size_t* ws_bytes);
+int pc_train(const void* d_field, const size_t dims[3], int dtype, const pc_params* p,
+             unsigned long long seed, unsigned int thr32, int nmodels,
+             const float* h_lrs, const float* h_lams,
+             float* h_weights_out, int* s_in_out, int* chosen_out, unsigned long long* h_costs,
+             void* d_ws, size_t ws_bytes, void* stream);
+
+/* Diagnostics for tests: offsets (bytes) of the per-point codes (u16, block-strided,
+ * nblocks * block volume), per-block perceptron flags (u8) and the code histogram
+ * (u64, 2^m) inside a compression workspace after pc_compress returns. */
+int pc_compress_workspace_layout(const size_t dims[3], int dtype, const pc_params* p,
+                                 size_t* off_codes, size_t* off_nnflag, size_t* off_hist);
+
+/* Human-readable name of a status code. */
+const char* pc_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PC_H */

@@ -1,0 +1,510 @@
+// C ABI (include/pc.h): argument checks, workspace layout, launch sequence.
+#include <cstring>
+#include <mutex>
+
+#include "pc_kernels.cuh"
+
+using namespace pc;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+int sm_count() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (dev >= 0 && dev < 64 && cache[dev]) return cache[dev];
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (dev >= 0 && dev < 64) cache[dev] = n;
+  return n;
+}
+
+bool shape_supported(const int b[3]) {
+  static const int shapes[][3] = {{8, 8, 8}, {4, 4, 4}, {16, 16, 16}, {1, 16, 32}, {1, 8, 8}, {1, 64, 64}};
+  for (auto& s : shapes)
+    if (s[0] == b[0] && s[1] == b[1] && s[2] == b[2]) return true;
+  return false;
+}
+
+int nweights(int k, int h1, int h2) {
+  const int hl = h2 > 0 ? h2 : h1;
+  return h1 * k + h1 + (h2 > 0 ? h2 * h1 + h2 : 0) + hl + 1;
+}
+
+bool make_geo(const size_t dims[3], const int block[3], Geo& g) {
+  long long vol = 1;
+  for (int i = 0; i < 3; ++i) {
+    if (dims[i] < 1 || block[i] < 1) return false;
+    g.n[i] = (long long)dims[i];
+    g.b[i] = block[i];
+    g.nb[i] = (g.n[i] + block[i] - 1) / block[i];
+    vol *= block[i];
+  }
+  if (vol < 2 || vol > 4096) return false;
+  g.bvol = (int)vol;
+  g.nblocks = g.nb[0] * g.nb[1] * g.nb[2];
+  long long ch = kChunkPts / g.bvol;
+  if (ch < 1) ch = 1;
+  if (ch > 1024) ch = 1024;
+  g.ch = (int)ch;
+  g.nchunks = (g.nblocks + ch - 1) / ch;
+  return true;
+}
+
+int check_params(const size_t dims[3], int dtype, const pc_params* p, Geo& g, int& mode, int& nw) {
+  if (!dims || !p) return PC_ERR_ARG;
+  if (dtype != PC_F32 && dtype != PC_F64) return PC_ERR_DTYPE;
+  if (!(p->eb_rel > 0.0 && p->eb_rel < 1.0)) return PC_ERR_ARG;
+  if (p->m < 2 || p->m > 16) return PC_ERR_ARG;
+  if (!make_geo(dims, p->block, g)) return PC_ERR_ARG;
+  if (!shape_supported(p->block)) return PC_ERR_ARG;
+  mode = p->pred == PC_PRED_MLP_FP32 ? 1 : 0;
+  if (p->pred != PC_PRED_LORENZO && p->pred != PC_PRED_MLP_FP32) return PC_ERR_ARG;
+  nw = 0;
+  if (mode) {
+    if (p->stencil != 7 && p->stencil != 13) return PC_ERR_ARG;
+    if (p->hidden[0] < 2 || p->hidden[0] > kMaxH || p->hidden[1] < 0 || p->hidden[1] > kMaxH) return PC_ERR_ARG;
+    if (p->s_in < 0 || p->s_in > 30 || !p->h_weights) return PC_ERR_ARG;
+    nw = nweights(p->stencil, p->hidden[0], p->hidden[1]);
+    if (nw > kMaxW) return PC_ERR_ARG;
+  }
+  return PC_OK;
+}
+
+struct CompLayout {
+  size_t st, hist, lens, cw, key, w, parent, depth, la, lb, rstart, symord, codes, nnflag, nout, bbits, cbits, cnout,
+      cboff, cooff, total;
+};
+
+CompLayout comp_layout(const Geo& g, int m) {
+  const size_t nsym = (size_t)1 << m;
+  size_t np = 1;
+  while (np < nsym) np <<= 1;
+  CompLayout L;
+  size_t o = 0;
+  L.st = o; o = up(o + sizeof(State));
+  L.hist = o; o = up(o + 8 * nsym);
+  L.lens = o; o = up(o + nsym);
+  L.cw = o; o = up(o + 4 * nsym);
+  L.key = o; o = up(o + 8 * np);
+  L.w = o; o = up(o + 8 * 2 * nsym);
+  L.parent = o; o = up(o + 4 * 2 * nsym);
+  L.depth = o; o = up(o + 4 * 2 * nsym);
+  L.la = o; o = up(o + 4 * nsym);
+  L.lb = o; o = up(o + 4 * nsym);
+  L.rstart = o; o = up(o + 4 * (nsym + 2));
+  L.symord = o; o = up(o + 4 * nsym);
+  L.codes = o; o = up(o + 2 * (size_t)g.nblocks * g.bvol);
+  L.nnflag = o; o = up(o + (size_t)g.nblocks);
+  L.nout = o; o = up(o + 4 * (size_t)g.nblocks);
+  L.bbits = o; o = up(o + 4 * (size_t)g.nblocks);
+  L.cbits = o; o = up(o + 8 * (size_t)g.nchunks);
+  L.cnout = o; o = up(o + 8 * (size_t)g.nchunks);
+  L.cboff = o; o = up(o + 8 * (size_t)g.nchunks);
+  L.cooff = o; o = up(o + 8 * (size_t)g.nchunks);
+  L.total = o;
+  return L;
+}
+
+struct DecLayout {
+  size_t err, lens, sorted, lut, tabs, key, cbits, cnout, cboff, cooff, boff, ooff, codes, total;
+};
+
+DecLayout dec_layout(const Geo& g, int m) {
+  const size_t nsym = (size_t)1 << m;
+  DecLayout L;
+  size_t o = 0;
+  L.err = o; o = up(o + 16);
+  L.lens = o; o = up(o + nsym);
+  L.sorted = o; o = up(o + 2 * nsym);
+  L.lut = o; o = up(o + 4 * 4096);
+  L.tabs = o; o = up(o + 4 * 96);
+  L.key = o; o = up(o + 8 * nsym);
+  L.cbits = o; o = up(o + 8 * (size_t)g.nchunks);
+  L.cnout = o; o = up(o + 8 * (size_t)g.nchunks);
+  L.cboff = o; o = up(o + 8 * (size_t)g.nchunks);
+  L.cooff = o; o = up(o + 8 * (size_t)g.nchunks);
+  L.boff = o; o = up(o + 8 * (size_t)g.nblocks);
+  L.ooff = o; o = up(o + 8 * (size_t)g.nblocks);
+  L.codes = o; o = up(o + 2 * (size_t)g.nblocks * g.bvol);
+  L.total = o;
+  return L;
+}
+
+// CRC-32 (IEEE 802.3, reflected) for header validation on the host.
+uint32_t host_crc32(const uint8_t* p, size_t n) {
+  static uint32_t table[256];
+  static std::once_flag once;
+  std::call_once(once, [] {
+    for (uint32_t i = 0; i < 256; ++i) {
+      uint32_t c = i;
+      for (int k = 0; k < 8; ++k) c = (c & 1u) ? (0xEDB88320u ^ (c >> 1)) : (c >> 1);
+      table[i] = c;
+    }
+  });
+  uint32_t c = 0xFFFFFFFFu;
+  for (size_t i = 0; i < n; ++i) c = table[(c ^ p[i]) & 0xFFu] ^ (c >> 8);
+  return c ^ 0xFFFFFFFFu;
+}
+
+uint32_t rd32(const uint8_t* p) { uint32_t v; memcpy(&v, p, 4); return v; }
+uint64_t rd64(const uint8_t* p) { uint64_t v; memcpy(&v, p, 8); return v; }
+
+// Parsed, validated header.
+struct Hdr {
+  int dtype, pred, m, stencil, h1, h2, s_in, nw, block[3];
+  size_t dims[3];
+  unsigned int n_used;
+  unsigned long long nblocks, n_out, swords, off_cb, off_bb, off_bn, off_ov, off_st, total;
+  int Kp, Kn, Zq, S;
+  unsigned long long step_bits, inv_bits, ebdn_bits;
+};
+
+int parse_header(const uint8_t* h, size_t n, Hdr& H, Geo& g) {
+  if (!h || n < (size_t)kHdr) return PC_ERR_CORRUPT;
+  if (rd32(h) != 0x504D4350u || rd32(h + 4) != 1u) return PC_ERR_CORRUPT;
+  if (rd32(h + 252) != host_crc32(h, 252)) return PC_ERR_CORRUPT;
+  H.dtype = (int)rd32(h + 8);
+  H.pred = (int)rd32(h + 12);
+  for (int i = 0; i < 3; ++i) {
+    H.dims[i] = (size_t)rd64(h + 16 + 8 * i);
+    H.block[i] = (int)rd32(h + 40 + 4 * i);
+  }
+  H.stencil = (int)rd32(h + 52);
+  H.h1 = (int)rd32(h + 56);
+  H.h2 = (int)rd32(h + 60);
+  H.m = (int)rd32(h + 64);
+  H.s_in = (int)rd32(h + 68);
+  H.Kp = (int)rd32(h + 100);
+  H.Kn = (int)rd32(h + 104);
+  H.Zq = (int)rd32(h + 108);
+  H.S = (int)rd32(h + 112);
+  H.n_used = rd32(h + 116);
+  H.step_bits = rd64(h + 120);
+  H.inv_bits = rd64(h + 128);
+  H.ebdn_bits = rd64(h + 136);
+  H.nblocks = rd64(h + 144);
+  H.n_out = rd64(h + 152);
+  H.swords = rd64(h + 160);
+  H.off_cb = rd64(h + 176);
+  H.off_bb = rd64(h + 184);
+  H.off_bn = rd64(h + 192);
+  H.off_ov = rd64(h + 200);
+  H.off_st = rd64(h + 208);
+  H.total = rd64(h + 216);
+  H.nw = (int)rd32(h + 224);
+  if (H.dtype != PC_F32 && H.dtype != PC_F64) return PC_ERR_CORRUPT;
+  if (H.m < 2 || H.m > 16) return PC_ERR_CORRUPT;
+  for (int i = 0; i < 3; ++i)
+    if (H.dims[i] < 1 || H.dims[i] > (1ull << 40)) return PC_ERR_CORRUPT;
+  if (!make_geo(H.dims, H.block, g) || !shape_supported(H.block)) return PC_ERR_CORRUPT;
+  if ((unsigned long long)g.nblocks != H.nblocks) return PC_ERR_CORRUPT;
+  if (H.n_used > (1u << H.m)) return PC_ERR_CORRUPT;
+  if (H.pred == 1) {
+    if ((H.stencil != 7 && H.stencil != 13) || H.h1 < 2 || H.h1 > kMaxH || H.h2 < 0 || H.h2 > kMaxH ||
+        H.s_in < 0 || H.s_in > 30 || H.nw != nweights(H.stencil, H.h1, H.h2) || H.nw > kMaxW)
+      return PC_ERR_CORRUPT;
+  } else if (H.pred != 0 || H.nw != 0) {
+    return PC_ERR_CORRUPT;
+  }
+  const unsigned long long npts = (unsigned long long)H.dims[0] * H.dims[1] * H.dims[2];
+  if (H.n_out > npts || H.swords > (npts * kLmax + 31) / 32 + 1) return PC_ERR_CORRUPT;
+  const unsigned long long ts = H.dtype == PC_F64 ? 8 : 4;
+  const unsigned long long ocb = al16(kHdr + 4ull * H.nw);
+  const unsigned long long obb = al16(ocb + 4ull * H.n_used);
+  const unsigned long long obn = al16(obb + 4ull * H.nblocks);
+  const unsigned long long oov = al16(obn + 2ull * H.nblocks);
+  const unsigned long long ost = al16(oov + ts * H.n_out);
+  const unsigned long long tot = al16(ost + 4ull * H.swords);
+  if (H.off_cb != ocb || H.off_bb != obb || H.off_bn != obn || H.off_ov != oov || H.off_st != ost || H.total != tot)
+    return PC_ERR_CORRUPT;
+  return PC_OK;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? PC_OK : PC_ERR_CUDA; }
+
+}  // namespace
+
+extern "C" {
+
+int pc_mlp_nweights(int k, int h1, int h2) { return nweights(k, h1, h2); }
+
+size_t pc_compress_bound(const size_t dims[3], int dtype, const pc_params* p) {
+  Geo g;
+  int mode, nw;
+  if (check_params(dims, dtype, p, g, mode, nw) != PC_OK) return 0;
+  const unsigned long long n = (unsigned long long)dims[0] * dims[1] * dims[2];
+  const unsigned long long ts = dtype == PC_F64 ? 8 : 4;
+  unsigned long long b = kHdr;
+  b = al16(b + 4ull * nw);
+  b = al16(b + 4ull * (1ull << p->m));
+  b = al16(b + 4ull * g.nblocks);
+  b = al16(b + 2ull * g.nblocks);
+  b = al16(b + ts * n);
+  b = al16(b + 4ull * ((n * kLmax + 31) / 32 + 1));
+  return (size_t)b;
+}
+
+int pc_compress_workspace_size(const size_t dims[3], int dtype, const pc_params* p, size_t* ws) {
+  Geo g;
+  int mode, nw;
+  int st = check_params(dims, dtype, p, g, mode, nw);
+  if (st) return st;
+  if (!ws) return PC_ERR_ARG;
+  *ws = comp_layout(g, p->m).total;
+  return PC_OK;
+}
+
+int pc_compress_workspace_layout(const size_t dims[3], int dtype, const pc_params* p, size_t* off_codes,
+                                 size_t* off_nnflag, size_t* off_hist) {
+  Geo g;
+  int mode, nw;
+  int st = check_params(dims, dtype, p, g, mode, nw);
+  if (st) return st;
+  CompLayout L = comp_layout(g, p->m);
+  if (off_codes) *off_codes = L.codes;
+  if (off_nnflag) *off_nnflag = L.nnflag;
+  if (off_hist) *off_hist = L.hist;
+  return PC_OK;
+}
+
+int pc_compress(const void* d_field, const size_t dims[3], int dtype, const pc_params* p, void* d_out,
+                size_t out_cap, size_t* out_size, void* d_ws, size_t ws_bytes, void* stream) {
+  Geo g;
+  int mode, nw;
+  int st = check_params(dims, dtype, p, g, mode, nw);
+  if (st) return st;
+  if (!d_field || !d_out || !out_size || !d_ws) return PC_ERR_ARG;
+  CompLayout L = comp_layout(g, p->m);
+  if (ws_bytes < L.total) return PC_ERR_CAPACITY;
+  HdrInfo hi;
+  hi.dtype = dtype;
+  hi.pred = mode;
+  hi.stencil = p->stencil;
+  hi.h1 = p->hidden[0];
+  hi.h2 = p->hidden[1];
+  hi.m = p->m;
+  hi.s_in = p->s_in;
+  hi.nw = nw;
+  hi.eb = p->eb_rel;
+  hi.off_cb = al16(kHdr + 4ull * nw);
+  hi.cap = out_cap;
+  if (out_cap < hi.off_cb + 16) return PC_ERR_CAPACITY;
+  static thread_local Mlp mlp;
+  memset(&mlp, 0, sizeof(Mlp));
+  if (mode) {
+    mlp.k = p->stencil;
+    mlp.h1 = p->hidden[0];
+    mlp.h2 = p->hidden[1];
+    mlp.s_in = p->s_in;
+    memcpy(mlp.w, p->h_weights, sizeof(float) * (size_t)nw);
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int nsm = sm_count();
+  if (nsm <= 0) return PC_ERR_CUDA;
+  uint8_t* ws = static_cast<uint8_t*>(d_ws);
+  uint8_t* out = static_cast<uint8_t*>(d_out);
+  State* stp = reinterpret_cast<State*>(ws + L.st);
+  auto* hist = reinterpret_cast<unsigned long long*>(ws + L.hist);
+  auto* codes = reinterpret_cast<uint16_t*>(ws + L.codes);
+  auto* nnflag = reinterpret_cast<uint8_t*>(ws + L.nnflag);
+  auto* nout = reinterpret_cast<uint32_t*>(ws + L.nout);
+  auto* lens = reinterpret_cast<uint8_t*>(ws + L.lens);
+  auto* cw = reinterpret_cast<uint32_t*>(ws + L.cw);
+  HuffScratch hs;
+  hs.key = reinterpret_cast<unsigned long long*>(ws + L.key);
+  hs.w = reinterpret_cast<unsigned long long*>(ws + L.w);
+  hs.parent = reinterpret_cast<int*>(ws + L.parent);
+  hs.depth = reinterpret_cast<int*>(ws + L.depth);
+  hs.la = reinterpret_cast<int*>(ws + L.la);
+  hs.lb = reinterpret_cast<int*>(ws + L.lb);
+  hs.rstart = reinterpret_cast<int*>(ws + L.rstart);
+  hs.symord = reinterpret_cast<unsigned int*>(ws + L.symord);
+  const unsigned long long n = (unsigned long long)dims[0] * dims[1] * dims[2];
+  const int nsym = 1 << p->m;
+  int r;
+  if (dtype == PC_F32) {
+    r = launch_stats_consts<float>(d_field, n, stp, hist, nsym, p->eb_rel, nsm, s);
+    if (!r) r = launch_compress<float>(d_field, g, stp, codes, nnflag, nout, hist, p->m, mode, mlp, nsm, s);
+  } else {
+    r = launch_stats_consts<double>(d_field, n, stp, hist, nsym, p->eb_rel, nsm, s);
+    if (!r) r = launch_compress<double>(d_field, g, stp, codes, nnflag, nout, hist, p->m, mode, mlp, nsm, s);
+  }
+  if (!r) r = launch_codebook(hist, p->m, lens, cw, stp, hs, out, g, hi, s);
+  if (!r) {
+    auto* bbits = reinterpret_cast<uint32_t*>(ws + L.bbits);
+    auto* cb = reinterpret_cast<unsigned long long*>(ws + L.cbits);
+    auto* cn = reinterpret_cast<unsigned long long*>(ws + L.cnout);
+    auto* cbo = reinterpret_cast<unsigned long long*>(ws + L.cboff);
+    auto* coo = reinterpret_cast<unsigned long long*>(ws + L.cooff);
+    if (dtype == PC_F32)
+      r = launch_pack<float>(static_cast<const float*>(d_field), g, codes, nnflag, nout, lens, cw, bbits, cb, cn, cbo,
+                             coo, stp, out, hi, mlp, s);
+    else
+      r = launch_pack<double>(static_cast<const double*>(d_field), g, codes, nnflag, nout, lens, cw, bbits, cb, cn,
+                              cbo, coo, stp, out, hi, mlp, s);
+  }
+  if (r) return r;
+  State hst;
+  if (cudaMemcpyAsync(&hst, stp, sizeof(State), cudaMemcpyDeviceToHost, s) != cudaSuccess) return PC_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
+  if (hst.err) return hst.err;
+  *out_size = (size_t)hst.out_size;
+  return PC_OK;
+}
+
+int pc_header_info(const void* h_hdr, size_t hdr_bytes, size_t dims_out[3], int* dtype_out, size_t* ws_bytes) {
+  Hdr H;
+  Geo g;
+  int st = parse_header(static_cast<const uint8_t*>(h_hdr), hdr_bytes, H, g);
+  if (st) return st;
+  if (dims_out)
+    for (int i = 0; i < 3; ++i) dims_out[i] = H.dims[i];
+  if (dtype_out) *dtype_out = H.dtype;
+  if (ws_bytes) *ws_bytes = dec_layout(g, H.m).total;
+  return PC_OK;
+}
+
+int pc_decompress(const void* d_in, size_t in_size, void* d_field, size_t field_cap, size_t dims_out[3],
+                  int* dtype_out, void* d_ws, size_t ws_bytes, void* stream) {
+  if (!d_in || !d_field || !d_ws) return PC_ERR_ARG;
+  if (in_size < (size_t)kHdr) return PC_ERR_CORRUPT;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint8_t hbuf[kHdr];
+  if (cudaMemcpyAsync(hbuf, d_in, kHdr, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PC_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
+  Hdr H;
+  Geo g;
+  int st = parse_header(hbuf, kHdr, H, g);
+  if (st) return st;
+  if (H.total > in_size) return PC_ERR_CORRUPT;
+  const size_t ts = H.dtype == PC_F64 ? 8 : 4;
+  const size_t n = H.dims[0] * H.dims[1] * H.dims[2];
+  if (field_cap < n * ts) return PC_ERR_CAPACITY;
+  DecLayout L = dec_layout(g, H.m);
+  if (ws_bytes < L.total) return PC_ERR_CAPACITY;
+  static thread_local Mlp mlp;
+  memset(&mlp, 0, sizeof(Mlp));
+  if (H.pred == 1) {
+    mlp.k = H.stencil;
+    mlp.h1 = H.h1;
+    mlp.h2 = H.h2;
+    mlp.s_in = H.s_in;
+    if (cudaMemcpyAsync(mlp.w, static_cast<const uint8_t*>(d_in) + kHdr, 4ull * H.nw, cudaMemcpyDeviceToHost, s) !=
+        cudaSuccess)
+      return PC_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
+  }
+  if (dims_out)
+    for (int i = 0; i < 3; ++i) dims_out[i] = H.dims[i];
+  if (dtype_out) *dtype_out = H.dtype;
+  uint8_t* ws = static_cast<uint8_t*>(d_ws);
+  DecScratch ds;
+  ds.err = reinterpret_cast<int*>(ws + L.err);
+  ds.lens = ws + L.lens;
+  ds.sorted = reinterpret_cast<uint16_t*>(ws + L.sorted);
+  ds.lut = reinterpret_cast<unsigned int*>(ws + L.lut);
+  ds.tabs = reinterpret_cast<unsigned int*>(ws + L.tabs);
+  ds.key = reinterpret_cast<unsigned long long*>(ws + L.key);
+  ds.chunk_bits = reinterpret_cast<unsigned long long*>(ws + L.cbits);
+  ds.chunk_nout = reinterpret_cast<unsigned long long*>(ws + L.cnout);
+  ds.chunk_boff = reinterpret_cast<unsigned long long*>(ws + L.cboff);
+  ds.chunk_ooff = reinterpret_cast<unsigned long long*>(ws + L.cooff);
+  ds.boff = reinterpret_cast<unsigned long long*>(ws + L.boff);
+  ds.ooff = reinterpret_cast<unsigned long long*>(ws + L.ooff);
+  ds.codes = reinterpret_cast<uint16_t*>(ws + L.codes);
+  DecInfo di;
+  di.dtype = H.dtype;
+  di.m = H.m;
+  di.stencil = H.pred == 1 ? H.stencil : 7;
+  di.h1 = H.h1;
+  di.h2 = H.h2;
+  di.s_in = H.s_in;
+  di.usenn_any = H.pred == 1;
+  di.n_used = H.n_used;
+  di.n_out = H.n_out;
+  di.swords = H.swords;
+  di.off_cb = H.off_cb;
+  di.off_bb = H.off_bb;
+  di.off_bn = H.off_bn;
+  di.off_ov = H.off_ov;
+  di.off_st = H.off_st;
+  di.in_size = in_size;
+  di.Kp = H.Kp;
+  di.Kn = H.Kn;
+  di.Zq = H.Zq;
+  di.S = H.S;
+  di.step_bits = H.step_bits;
+  di.inv_bits = H.inv_bits;
+  di.ebdn_bits = H.ebdn_bits;
+  if (cudaMemsetAsync(ds.err, 0, sizeof(int), s) != cudaSuccess) return PC_ERR_CUDA;
+  const int nsm = sm_count();
+  if (nsm <= 0) return PC_ERR_CUDA;
+  const uint8_t* in = static_cast<const uint8_t*>(d_in);
+  int r = H.dtype == PC_F32 ? launch_decompress<float>(in, g, di, ds, mlp, static_cast<float*>(d_field), nsm, s)
+                            : launch_decompress<double>(in, g, di, ds, mlp, static_cast<double*>(d_field), nsm, s);
+  if (r) return r;
+  int err = 0;
+  if (cudaMemcpyAsync(&err, ds.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return PC_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
+  return err ? err : PC_OK;
+}
+
+int pc_compress_host(const void* h_field, const size_t dims[3], int dtype, const pc_params* p, void* h_out,
+                     size_t out_cap, size_t* out_size, void* d_field_stage, void* d_out_stage, size_t d_out_cap,
+                     void* d_ws, size_t ws_bytes, void* stream) {
+  if (!h_field || !h_out || !d_field_stage || !d_out_stage || !dims || !out_size) return PC_ERR_ARG;
+  if (dtype != PC_F32 && dtype != PC_F64) return PC_ERR_DTYPE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = dims[0] * dims[1] * dims[2] * (dtype == PC_F64 ? 8 : 4);
+  if (cudaMemcpyAsync(d_field_stage, h_field, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return PC_ERR_CUDA;
+  size_t sz = 0;
+  int st = pc_compress(d_field_stage, dims, dtype, p, d_out_stage, d_out_cap, &sz, d_ws, ws_bytes, stream);
+  if (st) return st;
+  if (sz > out_cap) return PC_ERR_CAPACITY;
+  if (cudaMemcpyAsync(h_out, d_out_stage, sz, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PC_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
+  *out_size = sz;
+  return PC_OK;
+}
+
+int pc_decompress_host(const void* h_in, size_t in_size, void* h_field, size_t field_cap, size_t dims_out[3],
+                       int* dtype_out, void* d_in_stage, size_t d_in_cap, void* d_field_stage, void* d_ws,
+                       size_t ws_bytes, void* stream) {
+  if (!h_in || !h_field || !d_in_stage || !d_field_stage) return PC_ERR_ARG;
+  if (in_size > d_in_cap) return PC_ERR_CAPACITY;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(d_in_stage, h_in, in_size, cudaMemcpyHostToDevice, s) != cudaSuccess) return PC_ERR_CUDA;
+  size_t dims[3];
+  int dt = 0;
+  int st = pc_decompress(d_in_stage, in_size, d_field_stage, field_cap, dims, &dt, d_ws, ws_bytes, stream);
+  if (st) return st;
+  const size_t bytes = dims[0] * dims[1] * dims[2] * (dt == PC_F64 ? 8 : 4);
+  if (bytes > field_cap) return PC_ERR_CAPACITY;
+  if (cudaMemcpyAsync(h_field, d_field_stage, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PC_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
+  if (dims_out)
+    for (int i = 0; i < 3; ++i) dims_out[i] = dims[i];
+  if (dtype_out) *dtype_out = dt;
+  return PC_OK;
+}
+
+const char* pc_strerror(int status) {
+  switch (status) {
+    case PC_OK: return "ok";
+    case PC_ERR_ARG: return "bad argument";
+    case PC_ERR_DTYPE: return "unsupported dtype";
+    case PC_ERR_NONFINITE: return "NaN or Inf in the input";
+    case PC_ERR_CAPACITY: return "output or workspace buffer too small";
+    case PC_ERR_CORRUPT: return "corrupt compressed stream";
+    case PC_ERR_TIMEOUT: return "bounded device wait ran out";
+    case PC_ERR_CUDA: return "CUDA runtime error";
+    case PC_ERR_EB_RANGE: return "error bound too small for the dtype";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,405 @@
+// Compression kernels: statistics (a1), constants (a2), and the fused
+// transform / predict / select / quantize / histogram pass (a4-a9).
+#include "pc_kernels.cuh"
+
+namespace pc {
+
+// ---------------------------------------------------------------------------
+// a0: reset the per-call state and the histogram.
+// ---------------------------------------------------------------------------
+__global__ void k_init(State* st, unsigned long long* hist, int nsym) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    State z;
+    memset(&z, 0, sizeof(z));
+    z.amin_bits = ~0ull;
+    *st = z;
+  }
+  for (; i < nsym; i += gridDim.x * blockDim.x) hist[i] = 0ull;
+}
+
+// ---------------------------------------------------------------------------
+// a1: abs_min over normal magnitudes, abs_max over all, non-finite flag
+// (Algorithm 1 input; Section III.B defines min as the non-zero minimum
+// absolute value).  Magnitude bit patterns order like unsigned integers, so
+// the reduction is exact and order-free.
+// ---------------------------------------------------------------------------
+template <typename T> struct Bits;
+template <> struct Bits<float> {
+  using U = unsigned int;
+  static __device__ __forceinline__ U mag(float v) { return __float_as_uint(v) & 0x7FFFFFFFu; }
+  static constexpr U kInf = 0x7F800000u, kMinNormal = 0x00800000u;
+};
+template <> struct Bits<double> {
+  using U = unsigned long long;
+  static __device__ __forceinline__ U mag(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+  }
+  static constexpr U kInf = 0x7FF0000000000000ull, kMinNormal = 0x0010000000000000ull;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_stats(const T* __restrict__ x, unsigned long long n, State* st) {
+  using B = Bits<T>;
+  unsigned long long mn = ~0ull, mx = 0ull;
+  unsigned int bad = 0, have = 0;
+  unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    auto a = B::mag(__ldg(&x[i]));
+    bad |= (a >= B::kInf);
+    if (a >= B::kMinNormal && a < B::kInf) {
+      have = 1;
+      mn = min(mn, (unsigned long long)a);
+    }
+    mx = max(mx, (unsigned long long)a);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = min(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
+    mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+    bad |= __shfl_xor_sync(0xFFFFFFFFu, bad, o);
+    have |= __shfl_xor_sync(0xFFFFFFFFu, have, o);
+  }
+  __shared__ unsigned long long s_mn[8], s_mx[8];
+  __shared__ unsigned int s_bad[8], s_have[8];
+  int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { s_mn[w] = mn; s_mx[w] = mx; s_bad[w] = bad; s_have[w] = have; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+      mn = min(mn, s_mn[i]); mx = max(mx, s_mx[i]); bad |= s_bad[i]; have |= s_have[i];
+    }
+    if (have) atomicMin(&st->amin_bits, mn);
+    atomicMax(&st->amax_bits, mx);
+    if (bad) atomicOr(&st->nonfinite, 1u);
+    if (have) atomicOr(&st->have_normal, 1u);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a2: constants (Eq. 8-12), one thread, double precision:
+//   b_a = log2(1 + eb), step = 2 b_a;
+//   Kp = rint(log2 abs_min / step)                       (factor_pos = abs_min)
+//   log2 factor_neg = log2(abs_max + e0) + log2 abs_min + step - log2(abs_min - e0)
+//   Kn = rint(log2 factor_neg / step)
+//   Zq = rint(log2 e0 / step) + Kp                       (zero image, Eq. 12)
+//   S  = rint(log2(abs_max + e0) / step) + Kp            (sign boundary)
+// with e0 the smallest positive value of the dtype.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_consts(State* st, double eb) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  State& c = *st;
+  constexpr bool f32 = sizeof(T) == 4;
+  if (c.nonfinite) { c.err = PC_ERR_NONFINITE; return; }
+  double amin, amax;
+  if (c.have_normal) {
+    if (f32) {
+      amin = (double)__uint_as_float((unsigned int)c.amin_bits);
+      amax = (double)__uint_as_float((unsigned int)c.amax_bits);
+    } else {
+      amin = __longlong_as_double((long long)c.amin_bits);
+      amax = __longlong_as_double((long long)c.amax_bits);
+    }
+    c.trivial = 0;
+  } else {
+    amin = 1.0; amax = 1.0; c.trivial = 1;
+  }
+  c.amin = amin;
+  c.amax = amax;
+  const double e0 = f32 ? 0x1p-149 : 0x1p-1074;
+  const double le0 = f32 ? -149.0 : -1074.0;
+  double ba = dev_log2d(__dadd_rn(1.0, eb));
+  double step = __dadd_rn(ba, ba);
+  double lmax = dev_log2d(__dadd_rn(amax, e0));
+  double lmin = dev_log2d(amin);
+  double kp = rint(__ddiv_rn(lmin, step));
+  double lfn = __dsub_rn(__dadd_rn(__dadd_rn(lmax, lmin), step), dev_log2d(__dsub_rn(amin, e0)));
+  double kn = rint(__ddiv_rn(lfn, step));
+  double zq = __dadd_rn(rint(__ddiv_rn(le0, step)), kp);
+  double s = __dadd_rn(rint(__ddiv_rn(lmax, step)), kp);
+  double span = __dadd_rn(__ddiv_rn(f32 ? 151.0 : 1076.0, step), 2.0);
+  const double lim = 1073741824.0;
+  if (__dadd_rn(fabs(kp), span) > lim || __dadd_rn(fabs(kn), span) > lim || fabs(zq) > lim || fabs(s) > lim) {
+    c.err = PC_ERR_EB_RANGE;
+    return;
+  }
+  c.Kp = (int)kp; c.Kn = (int)kn; c.Zq = (int)zq; c.S = (int)s;
+  c.step32 = __double2float_rn(step);
+  c.inv32 = __fdiv_rn(1.0f, c.step32);
+  float ef = __double2float_rn(eb);
+  if ((double)ef > eb) ef = nextafterf(ef, 0.0f);
+  c.ebdn32 = ef;
+  c.stepd = step;
+  c.invd = __ddiv_rn(1.0, step);
+  c.ebdnd = eb;
+}
+
+// ---------------------------------------------------------------------------
+// a4-a9: fused transform, prediction, block select, quantization, histogram.
+//
+// A CTA of 256 threads handles a brick of G consecutive blocks along x (G
+// chosen so a brick holds at most 4096 points); each block is owned by a team
+// of 256/G threads.  The brick is read with consecutive threads on consecutive
+// x, transformed on the fly, and kept on chip as codes (dq), clamped
+// anchor-centred inputs (vc) and bound flags (ok).  Codes go out block-strided
+// in padded raster order (index (lz*B1 + ly)*B2 + lx); the histogram is kept
+// in shared memory for a window of codes around R and flushed once per CTA.
+// ---------------------------------------------------------------------------
+constexpr int kHistWin = 4096;
+
+template <int BV>
+struct BrickShape {
+  static constexpr int G = BV <= 512 ? 8 : (BV <= 1024 ? 4 : (BV <= 2048 ? 2 : 1));
+  static constexpr int TS = 256 / G;
+  static constexpr int PPT = (BV + TS - 1) / TS;
+};
+
+template <typename T, int B0, int B1, int B2, int MODE, int K, int H1, int H2>
+__global__ void __launch_bounds__(256) k_compress(const T* __restrict__ x, Geo g, const State* __restrict__ st,
+                                                   uint16_t* __restrict__ codes, uint8_t* __restrict__ nnflag,
+                                                   uint32_t* __restrict__ nout, unsigned long long* __restrict__ hist,
+                                                   int m, const __grid_constant__ Mlp mlp) {
+  constexpr int BV = B0 * B1 * B2;
+  using BS = BrickShape<BV>;
+  constexpr int G = BS::G, TS = BS::TS, PPT = BS::PPT;
+  extern __shared__ __align__(16) unsigned char smem[];
+  int* s_dq = reinterpret_cast<int*>(smem);                       // G*BV
+  int* s_vc = s_dq + G * BV;                                      // G*BV
+  unsigned int* s_hist = reinterpret_cast<unsigned int*>(s_vc + G * BV);  // kHistWin
+  uint16_t* s_cz = reinterpret_cast<uint16_t*>(s_hist + kHistWin);        // G*BV
+  uint16_t* s_cn = s_cz + G * BV;                                         // G*BV (MLP only)
+  uint8_t* s_ok = reinterpret_cast<uint8_t*>(s_cn + (MODE ? G * BV : 0)); // G*BV
+  __shared__ int s_cost[G][2];
+  __shared__ int s_nz[G];
+
+  const State c = *st;
+  if (c.err) return;
+  const int tid = threadIdx.x;
+  const int R = 1 << (m - 1);
+  const int hbase = R - kHistWin / 2 > 0 ? R - kHistWin / 2 : 0;
+  for (int i = tid; i < kHistWin; i += 256) s_hist[i] = 0u;
+  const float sig = MODE ? __uint_as_float((unsigned int)(127 - mlp.s_in) << 23) : 1.0f;
+  const float unsig = MODE ? __uint_as_float((unsigned int)(127 + mlp.s_in) << 23) : 1.0f;
+
+  const long long nbx = (g.nb[2] + G - 1) / G;
+  const long long nbricks = g.nb[0] * g.nb[1] * nbx;
+  for (long long brick = blockIdx.x; brick < nbricks; brick += gridDim.x) {
+    const long long bxg = brick % nbx;
+    const long long byz = brick / nbx;
+    const long long by = byz % g.nb[1];
+    const long long bz = byz / g.nb[1];
+    const long long z0 = bz * B0, y0 = by * B1, x0 = bxg * G * B2;
+    const int e0 = (int)min((long long)B0, g.n[0] - z0);
+    const int e1 = (int)min((long long)B1, g.n[1] - y0);
+    const int W = (int)min((long long)(G * B2), g.n[2] - x0);
+    // load + transform (a4)
+    const bool full = (e0 == B0) && (e1 == B1) && (W == G * B2);
+    if (full) {
+#pragma unroll 4
+      for (int e = tid; e < B0 * B1 * G * B2; e += 256) {
+        const int r = e / (G * B2), col = e % (G * B2);
+        const int z = r / B1, y = r % B1;
+        const T v = __ldg(&x[((z0 + z) * g.n[1] + (y0 + y)) * g.n[2] + x0 + col]);
+        bool ok;
+        const int q = Num<T>::transform(v, c, ok);
+        const int si = (col / B2) * BV + (z * B1 + y) * B2 + (col % B2);
+        s_dq[si] = q;
+        s_ok[si] = ok;
+      }
+    } else {
+      for (int e = tid; e < e0 * e1 * W; e += 256) {
+        const int r = e / W, col = e - r * W;
+        const int z = r / e1, y = r - z * e1;
+        const T v = __ldg(&x[((z0 + z) * g.n[1] + (y0 + y)) * g.n[2] + x0 + col]);
+        bool ok;
+        const int q = Num<T>::transform(v, c, ok);
+        const int si = (col / B2) * BV + (z * B1 + y) * B2 + (col % B2);
+        s_dq[si] = q;
+        s_ok[si] = ok;
+      }
+    }
+    if (tid < G) { s_cost[tid][0] = 0; s_cost[tid][1] = 0; s_nz[tid] = 0; }
+    __syncthreads();
+    const int team = tid / TS, t = tid % TS;
+    const long long bx = bxg * G + team;
+    const bool bvalid = bx < g.nb[2];
+    const int e2 = bvalid ? (int)min((long long)B2, g.n[2] - bx * B2) : 0;
+    int* dq = s_dq + team * BV;
+    int* vc = s_vc + team * BV;
+    // a5: anchor-centred, clamped inputs
+    if (bvalid) {
+      const int da = dq[0];
+#pragma unroll
+      for (int i = 0; i < PPT; ++i) {
+        const int j = t + i * TS;
+        if (j < BV) vc[j] = clampv((long long)dq[j] - da);
+      }
+    }
+    __syncthreads();
+    // a6-a8: predict, quantize, cost
+    int cz = 0, cn = 0;
+    if (bvalid) {
+      const int da = dq[0];
+#pragma unroll 1
+      for (int i = 0; i < PPT; ++i) {
+        const int j = t + i * TS;
+        if (j >= BV) break;
+        const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+        const bool valid = lz < e0 && ly < e1 && lx < e2 && j != 0;
+        uint16_t codez = 0, coden = 0;
+        if (valid) {
+          const long long v = (long long)dq[j] - da;
+          const bool okp = s_ok[team * BV + j];
+          int lzp = 0;
+#pragma unroll
+          for (int s = 0; s < 7; ++s) {
+            const int qz = lz + s7_dz(s), qy = ly + s7_dy(s), qx = lx + s7_dx(s);
+            const int vv = (qz >= 0 && qy >= 0 && qx >= 0) ? vc[(qz * B1 + qy) * B2 + qx] : 0;
+            lzp += lz_w(7, s) * vv;
+          }
+          const long long kz = v - lzp;
+          const long long az = kz < 0 ? -kz : kz;
+          cz += bitlen_u((unsigned int)(az < R ? az : R));
+          codez = (az <= R - 1 && okp) ? (uint16_t)(kz + R) : 0;
+          if constexpr (MODE != 0) {
+            int in[K > 0 ? K : 13];
+            const int kk = K > 0 ? K : mlp.k;
+#pragma unroll
+            for (int s = 0; s < (K > 0 ? K : 13); ++s) {
+              if (s < kk) {
+                const int qz = lz + st_dz(kk, s), qy = ly + st_dy(kk, s), qx = lx + st_dx(kk, s);
+                in[s] = (qz >= 0 && qy >= 0 && qx >= 0 && qz < e0 && qy < e1 && qx < e2)
+                            ? vc[(qz * B1 + qy) * B2 + qx] : 0;
+              }
+            }
+            float p;
+            if constexpr (K > 0) p = mlp_fwd<K, H1, H2>(mlp, in, sig, unsig);
+            else p = mlp_fwd_rt(mlp, in, sig, unsig);
+            const long long kn = v - (long long)round_pred(p);
+            const long long an = kn < 0 ? -kn : kn;
+            cn += bitlen_u((unsigned int)(an < R ? an : R));
+            coden = (an <= R - 1 && okp) ? (uint16_t)(kn + R) : 0;
+          }
+        }
+        s_cz[team * BV + j] = codez;
+        if constexpr (MODE != 0) s_cn[team * BV + j] = coden;
+      }
+      atomicAdd(&s_cost[team][0], cz);
+      if (MODE) atomicAdd(&s_cost[team][1], cn);
+    }
+    __syncthreads();
+    // a7 select, a8 emit, a9 histogram
+    if (bvalid) {
+      const long long b = (bz * g.nb[1] + by) * g.nb[2] + bx;
+      const bool usen = MODE != 0 && s_cost[team][1] < s_cost[team][0];
+      const uint16_t* src = usen ? s_cn + team * BV : s_cz + team * BV;
+      int nz = 0;
+#pragma unroll
+      for (int i = 0; i < PPT; ++i) {
+        const int j = t + i * TS;
+        if (j < BV) {
+          const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+          const bool valid = lz < e0 && ly < e1 && lx < e2 && j != 0;
+          const uint16_t cd = src[j];
+          codes[b * BV + j] = cd;
+          if (valid) {
+            nz += cd == 0;
+            const int hi = (int)cd - hbase;
+            if (hi >= 0 && hi < kHistWin) atomicAdd(&s_hist[hi], 1u);
+            else atomicAdd(&hist[cd], 1ull);
+          }
+        }
+      }
+      atomicAdd(&s_nz[team], nz);
+      __syncwarp();
+    }
+    __syncthreads();
+    if (bvalid && t == 0) {
+      const long long b = (bz * g.nb[1] + by) * g.nb[2] + bx;
+      nnflag[b] = (MODE != 0 && s_cost[team][1] < s_cost[team][0]) ? 1 : 0;
+      nout[b] = 1u + (unsigned int)s_nz[team];
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < kHistWin; i += 256) {
+    const unsigned int h = s_hist[i];
+    if (h && hbase + i < (1 << m)) atomicAdd(&hist[hbase + i], (unsigned long long)h);
+  }
+}
+
+template <int BV>
+size_t compress_smem(int mode) {
+  constexpr int G = BrickShape<BV>::G;
+  return (size_t)G * BV * 4 * 2 + kHistWin * 4 + (size_t)G * BV * 2 * (mode ? 2 : 1) + (size_t)G * BV;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (called from the API layer).
+// ---------------------------------------------------------------------------
+template <typename T>
+int launch_stats_consts(const void* x, unsigned long long n, State* st, unsigned long long* hist, int nsym,
+                        double eb, int nsm, cudaStream_t s) {
+  k_init<<<64, 256, 0, s>>>(st, hist, nsym);
+  k_stats<T><<<nsm * 8, 256, 0, s>>>(static_cast<const T*>(x), n, st);
+  k_consts<T><<<1, 32, 0, s>>>(st, eb);
+  return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
+}
+template int launch_stats_consts<float>(const void*, unsigned long long, State*, unsigned long long*, int, double,
+                                        int, cudaStream_t);
+template int launch_stats_consts<double>(const void*, unsigned long long, State*, unsigned long long*, int, double,
+                                         int, cudaStream_t);
+
+template <typename T, int B0, int B1, int B2, int MODE, int K, int H1, int H2>
+static int launch_c(const void* x, const Geo& g, const State* st, uint16_t* codes, uint8_t* nnflag, uint32_t* nout,
+                    unsigned long long* hist, int m, const Mlp& mlp, int nsm, cudaStream_t s) {
+  constexpr int BV = B0 * B1 * B2;
+  auto kern = k_compress<T, B0, B1, B2, MODE, K, H1, H2>;
+  size_t sm = compress_smem<BV>(MODE);
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+    return PC_ERR_CUDA;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm);
+  if (per_sm < 1) per_sm = 1;
+  constexpr int G = BrickShape<BV>::G;
+  long long nbricks = g.nb[0] * g.nb[1] * ((g.nb[2] + G - 1) / G);
+  long long grid = (long long)nsm * per_sm;
+  if (grid > nbricks) grid = nbricks;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned int)grid, 256, sm, s>>>(static_cast<const T*>(x), g, st, codes, nnflag, nout, hist, m, mlp);
+  return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
+}
+
+template <typename T, int B0, int B1, int B2>
+static int launch_c_shape(const void* x, const Geo& g, const State* st, uint16_t* codes, uint8_t* nnflag,
+                          uint32_t* nout, unsigned long long* hist, int m, int mode, const Mlp& mlp, int nsm,
+                          cudaStream_t s) {
+  if (mode == 0) return launch_c<T, B0, B1, B2, 0, 0, 0, 0>(x, g, st, codes, nnflag, nout, hist, m, mlp, nsm, s);
+  if (mlp.k == 7 && mlp.h1 == 16 && mlp.h2 == 16)
+    return launch_c<T, B0, B1, B2, 1, 7, 16, 16>(x, g, st, codes, nnflag, nout, hist, m, mlp, nsm, s);
+  if (mlp.k == 13 && mlp.h1 == 32 && mlp.h2 == 32)
+    return launch_c<T, B0, B1, B2, 1, 13, 32, 32>(x, g, st, codes, nnflag, nout, hist, m, mlp, nsm, s);
+  return launch_c<T, B0, B1, B2, 1, 0, 0, 0>(x, g, st, codes, nnflag, nout, hist, m, mlp, nsm, s);
+}
+
+template <typename T>
+int launch_compress(const void* x, const Geo& g, const State* st, uint16_t* codes, uint8_t* nnflag, uint32_t* nout,
+                    unsigned long long* hist, int m, int mode, const Mlp& mlp, int nsm, cudaStream_t s) {
+  const int b0 = g.b[0], b1 = g.b[1], b2 = g.b[2];
+#define PC_SHAPE(A, B, C) \
+  if (b0 == A && b1 == B && b2 == C) return launch_c_shape<T, A, B, C>(x, g, st, codes, nnflag, nout, hist, m, mode, mlp, nsm, s);
+  PC_SHAPE(8, 8, 8)
+  PC_SHAPE(4, 4, 4)
+  PC_SHAPE(16, 16, 16)
+  PC_SHAPE(1, 16, 32)
+  PC_SHAPE(1, 8, 8)
+  PC_SHAPE(1, 64, 64)
+#undef PC_SHAPE
+  return PC_ERR_ARG;
+}
+template int launch_compress<float>(const void*, const Geo&, const State*, uint16_t*, uint8_t*, uint32_t*,
+                                    unsigned long long*, int, int, const Mlp&, int, cudaStream_t);
+template int launch_compress<double>(const void*, const Geo&, const State*, uint16_t*, uint8_t*, uint32_t*,
+                                     unsigned long long*, int, int, const Mlp&, int, cudaStream_t);
+
+}  // namespace pc

@@ -1,0 +1,550 @@
+// a13: the inverse path (Section V, decompression).
+//
+// k_dec_tables rebuilds the canonical decoder from the stored (symbol, length)
+// list and validates it; k_dec_chunksum / k_dec_chunkscan / k_dec_blockoff
+// turn the block table into per-block bit and balance-point offsets;
+// k_huff_decode decodes one block per thread (12-bit first-level table,
+// canonical search for longer words), checking every read against the block's
+// stated bit count; k_recon rebuilds each block along wavefronts of its causal
+// stencil with the same predictor and inverse map as the compressor, then
+// writes the brick with coalesced stores.  A damaged stream sets the error
+// word and never leads to an out-of-bounds access.
+#include "pc_kernels.cuh"
+
+namespace pc {
+
+constexpr int kLutBits = 12;
+
+__device__ void cta_bitonic_d(unsigned long long* a, int np) {
+  for (int k = 2; k <= np; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const unsigned long long x = a[i], y = a[ixj];
+          const bool up = (i & k) == 0;
+          if ((x > y) == up) { a[i] = y; a[ixj] = x; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_dec_tables(const uint8_t* __restrict__ in, DecInfo di, DecScratch ds) {
+  __shared__ unsigned int s_cnt[32];
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nsym = 1 << di.m;
+  const int n = (int)di.n_used;
+  if (tid < 32) s_cnt[tid] = 0;
+  if (tid == 0) s_bad = 0;
+  for (int i = tid; i < nsym; i += nt) ds.lens[i] = 0;
+  for (int i = tid; i < (1 << kLutBits); i += nt) ds.lut[i] = 0;
+  __syncthreads();
+  int np = 1;
+  while (np < n) np <<= 1;
+  for (int p = tid; p < np; p += nt) {
+    if (p < n) {
+      const unsigned int e = *reinterpret_cast<const unsigned int*>(in + di.off_cb + 4ull * p);
+      const unsigned int sym = e & 0xFFFFu, len = e >> 16;
+      bool bad = sym >= (unsigned int)nsym || len < 1 || len > (unsigned int)kLmax;
+      if (p > 0) {
+        const unsigned int prev = (*reinterpret_cast<const unsigned int*>(in + di.off_cb + 4ull * (p - 1))) & 0xFFFFu;
+        bad |= sym <= prev;
+      }
+      if (bad) { s_bad = 1; ds.key[p] = ~0ull; continue; }
+      ds.lens[sym] = (uint8_t)len;
+      ds.key[p] = ((unsigned long long)len << 16) | sym;
+      atomicAdd(&s_cnt[len], 1u);
+    } else {
+      ds.key[p] = ~0ull;
+    }
+  }
+  __syncthreads();
+  if (s_bad) { if (tid == 0) atomicExch(ds.err, PC_ERR_CORRUPT); return; }
+  cta_bitonic_d(ds.key, np);
+  if (tid == 0) {
+    unsigned int code = 0, off = 0;
+    bool bad = false;
+    for (int l = 1; l <= kLmax; ++l) {
+      const unsigned int prevc = l > 1 ? s_cnt[l - 1] : 0u;
+      code = (code + prevc) << 1;
+      off += prevc;
+      ds.tabs[l] = code;            // first code of length l
+      ds.tabs[32 + l] = s_cnt[l];   // count
+      ds.tabs[64 + l] = off;        // offset into the sorted list
+      if (s_cnt[l] && (unsigned long long)code + s_cnt[l] > (1ull << l)) bad = true;
+    }
+    if (bad) atomicExch(ds.err, PC_ERR_CORRUPT);
+  }
+  __syncthreads();
+  for (int p = tid; p < n; p += nt) {
+    const unsigned int l = (unsigned int)(ds.key[p] >> 16), sym = (unsigned int)(ds.key[p] & 0xFFFFull);
+    ds.sorted[p] = (uint16_t)sym;
+    if (l <= (unsigned int)kLutBits) {
+      const unsigned int code = ds.tabs[l] + ((unsigned int)p - ds.tabs[64 + l]);
+      const unsigned int lo = code << (kLutBits - l), hi = (code + 1) << (kLutBits - l);
+      for (unsigned int t = lo; t < hi && t < (1u << kLutBits); ++t) ds.lut[t] = (sym << 8) | l;
+    }
+  }
+}
+
+__device__ __forceinline__ void dec_block_coords(const Geo& g, long long b, long long& bz, long long& by,
+                                                 long long& bx, int& e0, int& e1, int& e2) {
+  bx = b % g.nb[2];
+  const long long t = b / g.nb[2];
+  by = t % g.nb[1];
+  bz = t / g.nb[1];
+  e0 = (int)min((long long)g.b[0], g.n[0] - bz * g.b[0]);
+  e1 = (int)min((long long)g.b[1], g.n[1] - by * g.b[1]);
+  e2 = (int)min((long long)g.b[2], g.n[2] - bx * g.b[2]);
+}
+
+__global__ void __launch_bounds__(256) k_dec_chunksum(Geo g, const uint8_t* __restrict__ in, DecInfo di,
+                                                      DecScratch ds) {
+  __shared__ unsigned long long s_b[8], s_o[8];
+  const long long c = blockIdx.x;
+  const long long b0 = c * g.ch, b1 = min(g.nblocks, b0 + g.ch);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned long long wb = 0, wo = 0;
+  bool bad = false;
+  for (long long b = b0 + threadIdx.x; b < b1; b += 256) {
+    long long bz, by, bx;
+    int e0, e1, e2;
+    dec_block_coords(g, b, bz, by, bx, e0, e1, e2);
+    const unsigned int npts = (unsigned int)(e0 * e1 * e2);
+    const unsigned int bits = *reinterpret_cast<const unsigned int*>(in + di.off_bb + 4ull * b) & 0x7FFFFFFFu;
+    const unsigned int no = *reinterpret_cast<const uint16_t*>(in + di.off_bn + 2ull * b);
+    if (no < 1 || no > npts || bits > (npts - 1) * (unsigned int)kLmax) bad = true;
+    wb += bits;
+    wo += no;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    wb += __shfl_xor_sync(0xFFFFFFFFu, wb, o);
+    wo += __shfl_xor_sync(0xFFFFFFFFu, wo, o);
+  }
+  if (bad) atomicExch(ds.err, PC_ERR_CORRUPT);
+  if (lane == 0) { s_b[wid] = wb; s_o[wid] = wo; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tb = 0, to = 0;
+    for (int i = 0; i < 8; ++i) { tb += s_b[i]; to += s_o[i]; }
+    ds.chunk_bits[c] = tb;
+    ds.chunk_nout[c] = to;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_dec_chunkscan(Geo g, DecInfo di, DecScratch ds) {
+  __shared__ unsigned long long s_w[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long nc = g.nchunks;
+  const long long per = (nc + nt - 1) / nt;
+  const long long lo = min(nc, tid * per), hi = min(nc, lo + per);
+  unsigned long long sb = 0, so = 0;
+  for (long long i = lo; i < hi; ++i) { sb += ds.chunk_bits[i]; so += ds.chunk_nout[i]; }
+  unsigned long long tb, to;
+  unsigned long long pb = cta_exscan<unsigned long long>(sb, s_w, tb);
+  unsigned long long po = cta_exscan<unsigned long long>(so, s_w, to);
+  for (long long i = lo; i < hi; ++i) {
+    ds.chunk_boff[i] = pb;
+    ds.chunk_ooff[i] = po;
+    pb += ds.chunk_bits[i];
+    po += ds.chunk_nout[i];
+  }
+  if (tid == 0 && ((tb + 31) / 32 != di.swords || to != di.n_out)) atomicExch(ds.err, PC_ERR_CORRUPT);
+}
+
+__global__ void __launch_bounds__(256) k_dec_blockoff(Geo g, const uint8_t* __restrict__ in, DecInfo di,
+                                                      DecScratch ds) {
+  __shared__ unsigned int s_w[32];
+  const long long c = blockIdx.x;
+  const long long b0 = c * g.ch, b1 = min(g.nblocks, b0 + g.ch);
+  const int nb = (int)(b1 - b0);
+  const int tid = threadIdx.x;
+  const int per = (nb + 255) / 256;
+  const int lo = min(nb, tid * per), hi = min(nb, lo + per);
+  unsigned int sb = 0, so = 0;
+  for (int i = lo; i < hi; ++i) {
+    sb += *reinterpret_cast<const unsigned int*>(in + di.off_bb + 4ull * (b0 + i)) & 0x7FFFFFFFu;
+    so += *reinterpret_cast<const uint16_t*>(in + di.off_bn + 2ull * (b0 + i));
+  }
+  unsigned int tb, to;
+  unsigned int pb = cta_exscan<unsigned int>(sb, s_w, tb);
+  unsigned int po = cta_exscan<unsigned int>(so, s_w, to);
+  const unsigned long long cb = ds.chunk_boff[c], co = ds.chunk_ooff[c];
+  for (int i = lo; i < hi; ++i) {
+    ds.boff[b0 + i] = cb + pb;
+    ds.ooff[b0 + i] = co + po;
+    pb += *reinterpret_cast<const unsigned int*>(in + di.off_bb + 4ull * (b0 + i)) & 0x7FFFFFFFu;
+    po += *reinterpret_cast<const uint16_t*>(in + di.off_bn + 2ull * (b0 + i));
+  }
+}
+
+// One thread per block: canonical Huffman decode into block-strided codes.
+__global__ void __launch_bounds__(128) k_huff_decode(Geo g, const uint8_t* __restrict__ in, DecInfo di,
+                                                     DecScratch ds) {
+  __shared__ unsigned int s_lut[1 << kLutBits];
+  __shared__ unsigned int s_tab[96];
+  for (int i = threadIdx.x; i < (1 << kLutBits); i += blockDim.x) s_lut[i] = ds.lut[i];
+  for (int i = threadIdx.x; i < 96; i += blockDim.x) s_tab[i] = ds.tabs[i];
+  __syncthreads();
+  if (*ds.err) return;
+  const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= g.nblocks) return;
+  long long bz, by, bx;
+  int e0, e1, e2;
+  dec_block_coords(g, b, bz, by, bx, e0, e1, e2);
+  const bool full = e0 == g.b[0] && e1 == g.b[1] && e2 == g.b[2];
+  const unsigned int nbits = *reinterpret_cast<const unsigned int*>(in + di.off_bb + 4ull * b) & 0x7FFFFFFFu;
+  const uint32_t* stream = reinterpret_cast<const uint32_t*>(in + di.off_st);
+  const unsigned long long start = ds.boff[b];
+  unsigned long long wpos = start >> 5;
+  unsigned long long buf = 0;
+  int nb = 0;
+  // fill: keep at least 33 valid bits, MSB-aligned in buf
+  auto refill = [&]() {
+    while (nb <= 32) {
+      const unsigned int wv = wpos < di.swords ? __ldg(&stream[wpos]) : 0u;
+      ++wpos;
+      buf |= (unsigned long long)wv << (32 - nb);
+      nb += 32;
+    }
+  };
+  refill();
+  {
+    const int skip = (int)(start & 31ull);
+    buf <<= skip;
+    nb -= skip;
+  }
+  unsigned int used = 0;
+  bool bad = false;
+  uint16_t* out = ds.codes + b * g.bvol;
+  const int b12 = g.b[1] * g.b[2];
+  const int m = di.m;
+  for (int j = 0; j < g.bvol; ++j) {
+    bool valid = j != 0;
+    if (!full && valid) {
+      const int lz = j / b12, r = j - lz * b12, ly = r / g.b[2], lx = r - ly * g.b[2];
+      valid = lz < e0 && ly < e1 && lx < e2;
+    }
+    unsigned int sym = 0;
+    if (valid && !bad) {
+      refill();
+      const unsigned int peek = (unsigned int)(buf >> 40);  // 24 bits
+      const unsigned int e = s_lut[peek >> (kLmax - kLutBits)];
+      unsigned int len = e & 0xFFu;
+      if (len) {
+        sym = e >> 8;
+      } else {
+        len = 0;
+        for (int l = kLutBits + 1; l <= kLmax; ++l) {
+          const unsigned int code = peek >> (kLmax - l);
+          const unsigned int d = code - s_tab[l];
+          if (s_tab[32 + l] && d < s_tab[32 + l]) {
+            sym = ds.sorted[s_tab[64 + l] + d];
+            len = (unsigned int)l;
+            break;
+          }
+        }
+        if (!len) bad = true;
+      }
+      used += len;
+      if (used > nbits) bad = true;
+      buf <<= len;
+      nb -= (int)len;
+      if (sym >= (1u << m)) bad = true;
+    }
+    out[j] = (uint16_t)(bad ? 0 : sym);
+  }
+  if (bad || used != nbits) atomicExch(ds.err, PC_ERR_CORRUPT);
+}
+
+// ---------------------------------------------------------------------------
+// Wavefront reconstruction.  Schedule s(p) = z + y + x for the 7-point
+// stencil and 4z + 2y + x for the 13-point one: every causal neighbour has a
+// smaller s, so all points of one wave are independent.
+// ---------------------------------------------------------------------------
+template <int BV>
+struct DecShape {
+  static constexpr int G = BV <= 512 ? 8 : (BV <= 1024 ? 4 : (BV <= 2048 ? 2 : 1));
+  static constexpr int TS = 256 / G;
+};
+
+template <typename T, int B0, int B1, int B2, int MODE, int K, int H1, int H2>
+__global__ void __launch_bounds__(256) k_recon(Geo g, const uint8_t* __restrict__ in, DecInfo di, DecScratch ds,
+                                               T* __restrict__ xo, const __grid_constant__ Mlp mlp) {
+  constexpr int BV = B0 * B1 * B2;
+  constexpr int G = DecShape<BV>::G, TS = DecShape<BV>::TS;
+  constexpr int SZ = (B0 - 1) * 4 + (B1 - 1) * 2 + (B2 - 1) + 1;  // waves for the wider schedule
+  extern __shared__ __align__(16) unsigned char smem[];
+  int* s_dq = reinterpret_cast<int*>(smem);                  // G*BV
+  int* s_vc = s_dq + G * BV;                                 // G*BV
+  T* s_x = reinterpret_cast<T*>(s_vc + G * BV);              // G*BV
+  uint16_t* s_cd = reinterpret_cast<uint16_t*>(s_x + G * BV);  // G*BV
+  uint16_t* s_rk = s_cd + G * BV;                            // G*BV outlier ranks
+  uint16_t* s_list = s_rk + G * BV;                          // BV wave order
+  __shared__ int s_ws[SZ + 2];
+  __shared__ int s_fill[SZ + 2];
+  __shared__ unsigned int s_tsum[G][TS / 32 > 0 ? TS / 32 : 1];
+  __shared__ int s_bad;
+
+  State c;
+  c.Kp = di.Kp; c.Kn = di.Kn; c.Zq = di.Zq; c.S = di.S;
+  if (sizeof(T) == 4) {
+    c.step32 = __uint_as_float((unsigned int)di.step_bits);
+    c.inv32 = __uint_as_float((unsigned int)di.inv_bits);
+    c.ebdn32 = __uint_as_float((unsigned int)di.ebdn_bits);
+  } else {
+    c.stepd = __longlong_as_double((long long)di.step_bits);
+    c.invd = __longlong_as_double((long long)di.inv_bits);
+    c.ebdnd = __longlong_as_double((long long)di.ebdn_bits);
+  }
+  const int tid = threadIdx.x;
+  const bool s13 = di.stencil == 13;
+  // wave order for the full block shape (order inside a wave is free)
+  for (int i = tid; i < SZ + 2; i += 256) { s_ws[i] = 0; s_fill[i] = 0; }
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  for (int j = tid; j < BV; j += 256) {
+    const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+    const int s = s13 ? 4 * lz + 2 * ly + lx : lz + ly + lx;
+    atomicAdd(&s_ws[s + 1], 1);
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int s = 1; s < SZ + 2; ++s) s_ws[s] += s_ws[s - 1];
+  __syncthreads();
+  for (int j = tid; j < BV; j += 256) {
+    const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+    const int s = s13 ? 4 * lz + 2 * ly + lx : lz + ly + lx;
+    s_list[s_ws[s] + atomicAdd(&s_fill[s], 1)] = (uint16_t)j;
+  }
+  const int nwave = s13 ? SZ : (B0 - 1) + (B1 - 1) + (B2 - 1) + 1;
+  if (*ds.err) return;
+  const int R = 1 << (di.m - 1);
+  const float sig = MODE ? __uint_as_float((unsigned int)(127 - mlp.s_in) << 23) : 1.0f;
+  const float unsig = MODE ? __uint_as_float((unsigned int)(127 + mlp.s_in) << 23) : 1.0f;
+  const T* ov = reinterpret_cast<const T*>(in + di.off_ov);
+  const long long nbx = (g.nb[2] + G - 1) / G;
+  const long long nbricks = g.nb[0] * g.nb[1] * nbx;
+  const int team = tid / TS, t = tid % TS;
+  for (long long brick = blockIdx.x; brick < nbricks; brick += gridDim.x) {
+    const long long bxg = brick % nbx;
+    const long long byz = brick / nbx;
+    const long long by = byz % g.nb[1];
+    const long long bz = byz / g.nb[1];
+    const long long z0 = bz * B0, y0 = by * B1, x0 = bxg * G * B2;
+    const int e0 = (int)min((long long)B0, g.n[0] - z0);
+    const int e1 = (int)min((long long)B1, g.n[1] - y0);
+    const int W = (int)min((long long)(G * B2), g.n[2] - x0);
+    const long long bx = bxg * G + team;
+    const bool bvalid = bx < g.nb[2];
+    const int e2 = bvalid ? (int)min((long long)B2, g.n[2] - bx * B2) : 0;
+    const long long b = (bz * g.nb[1] + by) * g.nb[2] + bx;
+    int* dq = s_dq + team * BV;
+    int* vc = s_vc + team * BV;
+    T* xs = s_x + team * BV;
+    uint16_t* cd = s_cd + team * BV;
+    uint16_t* rk = s_rk + team * BV;
+    // codes and the exclusive rank of each balance point in raster order
+    unsigned int nzero = 0;
+    if (bvalid) {
+      constexpr int SEG = (BV + TS - 1) / TS;
+      unsigned int cnt = 0;
+      for (int q = 0; q < SEG; ++q) {
+        const int j = t * SEG + q;
+        if (j < BV) {
+          const uint16_t v = ds.codes[b * BV + j];
+          cd[j] = v;
+          const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+          cnt += (j != 0 && lz < e0 && ly < e1 && lx < e2 && v == 0);
+        }
+      }
+      // team exclusive scan of cnt
+      const int lane = t & 31, wv = t >> 5;
+      unsigned int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (TS > 32) {
+        if (lane == 31) s_tsum[team][wv] = incl;
+      }
+      if (TS > 32) __syncthreads(); else __syncwarp();
+      unsigned int base = 0;
+      if (TS > 32)
+        for (int q = 0; q < wv; ++q) base += s_tsum[team][q];
+      unsigned int run = base + incl - cnt;
+      for (int q = 0; q < SEG; ++q) {
+        const int j = t * SEG + q;
+        if (j < BV) {
+          rk[j] = (uint16_t)run;
+          const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+          run += (j != 0 && lz < e0 && ly < e1 && lx < e2 && cd[j] == 0);
+        }
+      }
+      unsigned int tot = incl;
+      if (TS > 32) {
+        tot = 0;
+        for (int q = 0; q < TS / 32; ++q) tot += s_tsum[team][q];
+      } else {
+        tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+      }
+      nzero = tot;
+    } else if (TS > 32) {
+      __syncthreads();
+    }
+    __syncthreads();
+    const unsigned int no = bvalid ? *reinterpret_cast<const uint16_t*>(in + di.off_bn + 2ull * b) : 1u;
+    const bool usen = bvalid && ((*reinterpret_cast<const unsigned int*>(in + di.off_bb + 4ull * b)) >> 31);
+    const unsigned long long obase = bvalid ? ds.ooff[b] : 0ull;
+    if (bvalid && nzero + 1u != no && t == 0) s_bad = 1;
+    if (usen && !MODE && t == 0) s_bad = 1;
+    // anchor
+    if (bvalid && t == 0) {
+      const T xa = ov[obase < di.n_out ? obase : 0];
+      bool okk;
+      const int q = Num<T>::transform(xa, c, okk);
+      dq[0] = q;
+      vc[0] = 0;
+      xs[0] = xa;
+    }
+    if (TS > 32) __syncthreads(); else __syncwarp();
+    const int da = bvalid ? dq[0] : 0;
+    for (int s = 1; s < nwave; ++s) {
+      if (bvalid) {
+        for (int idx = s_ws[s] + t; idx < s_ws[s + 1]; idx += TS) {
+          const int j = s_list[idx];
+          const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+          if (!(lz < e0 && ly < e1 && lx < e2)) continue;
+          const unsigned int code = cd[j];
+          int q;
+          if (code == 0) {
+            unsigned long long oi = obase + 1ull + rk[j];
+            if (oi >= obase + no || oi >= di.n_out) { s_bad = 1; oi = obase; }
+            const T xv = ov[oi];
+            bool okk;
+            q = Num<T>::transform(xv, c, okk);
+            xs[j] = xv;
+          } else {
+            long long pr = 0;
+            bool done = false;
+            if constexpr (MODE != 0) {
+              if (usen) {
+                int inp[K > 0 ? K : 13];
+                const int kk = K > 0 ? K : mlp.k;
+#pragma unroll
+                for (int si = 0; si < (K > 0 ? K : 13); ++si) {
+                  if (si < kk) {
+                    const int qz = lz + st_dz(kk, si), qy = ly + st_dy(kk, si), qx = lx + st_dx(kk, si);
+                    inp[si] = (qz >= 0 && qy >= 0 && qx >= 0 && qz < e0 && qy < e1 && qx < e2)
+                                  ? vc[(qz * B1 + qy) * B2 + qx] : 0;
+                  }
+                }
+                float p;
+                if constexpr (K > 0) p = mlp_fwd<K, H1, H2>(mlp, inp, sig, unsig);
+                else p = mlp_fwd_rt(mlp, inp, sig, unsig);
+                pr = round_pred(p);
+                done = true;
+              }
+            }
+            if (!done) {
+              int acc = 0;
+#pragma unroll
+              for (int si = 0; si < 7; ++si) {
+                const int qz = lz + s7_dz(si), qy = ly + s7_dy(si), qx = lx + s7_dx(si);
+                acc += lz_w(7, si) * ((qz >= 0 && qy >= 0 && qx >= 0) ? vc[(qz * B1 + qy) * B2 + qx] : 0);
+              }
+              pr = acc;
+            }
+            const long long qq = (long long)da + pr + ((long long)code - R);
+            if (qq > 2147483647LL || qq < -2147483647LL) { s_bad = 1; q = 0; }
+            else q = (int)qq;
+            xs[j] = Num<T>::recon(q, c);
+          }
+          dq[j] = q;
+          vc[j] = clampv((long long)q - da);
+        }
+      }
+      if (TS > 32) __syncthreads(); else __syncwarp();
+    }
+    __syncthreads();
+    // coalesced brick store
+    for (int e = tid; e < e0 * e1 * W; e += 256) {
+      const int r = e / W, col = e - r * W;
+      const int z = r / e1, y = r - z * e1;
+      xo[((z0 + z) * g.n[1] + (y0 + y)) * g.n[2] + x0 + col] = s_x[(col / B2) * BV + (z * B1 + y) * B2 + (col % B2)];
+    }
+    __syncthreads();
+  }
+  if (s_bad && tid == 0) atomicExch(ds.err, PC_ERR_CORRUPT);
+}
+
+template <int BV>
+size_t recon_smem(size_t ts) {
+  constexpr int G = DecShape<BV>::G;
+  return (size_t)G * BV * (4 + 4 + ts + 2 + 2) + (size_t)BV * 2 + 16;
+}
+
+template <typename T, int B0, int B1, int B2, int MODE, int K, int H1, int H2>
+static int launch_r(const uint8_t* in, const Geo& g, const DecInfo& di, const DecScratch& ds, const Mlp& mlp, T* out,
+                    int nsm, cudaStream_t s) {
+  constexpr int BV = B0 * B1 * B2;
+  auto kern = k_recon<T, B0, B1, B2, MODE, K, H1, H2>;
+  const size_t sm = recon_smem<BV>(sizeof(T));
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+    return PC_ERR_CUDA;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm);
+  if (per_sm < 1) per_sm = 1;
+  constexpr int G = DecShape<BV>::G;
+  const long long nbricks = g.nb[0] * g.nb[1] * ((g.nb[2] + G - 1) / G);
+  long long grid = (long long)nsm * per_sm;
+  if (grid > nbricks) grid = nbricks;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned int)grid, 256, sm, s>>>(g, in, di, ds, out, mlp);
+  return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
+}
+
+template <typename T, int B0, int B1, int B2>
+static int launch_r_shape(const uint8_t* in, const Geo& g, const DecInfo& di, const DecScratch& ds, const Mlp& mlp,
+                          T* out, int nsm, cudaStream_t s) {
+  if (!di.usenn_any) return launch_r<T, B0, B1, B2, 0, 0, 0, 0>(in, g, di, ds, mlp, out, nsm, s);
+  if (mlp.k == 7 && mlp.h1 == 16 && mlp.h2 == 16)
+    return launch_r<T, B0, B1, B2, 1, 7, 16, 16>(in, g, di, ds, mlp, out, nsm, s);
+  if (mlp.k == 13 && mlp.h1 == 32 && mlp.h2 == 32)
+    return launch_r<T, B0, B1, B2, 1, 13, 32, 32>(in, g, di, ds, mlp, out, nsm, s);
+  return launch_r<T, B0, B1, B2, 1, 0, 0, 0>(in, g, di, ds, mlp, out, nsm, s);
+}
+
+template <typename T>
+int launch_decompress(const uint8_t* in, const Geo& g, const DecInfo& di, const DecScratch& ds, const Mlp& mlp,
+                      T* out, int nsm, cudaStream_t s) {
+  k_dec_tables<<<1, 1024, 0, s>>>(in, di, ds);
+  const unsigned int nc = (unsigned int)g.nchunks;
+  k_dec_chunksum<<<nc, 256, 0, s>>>(g, in, di, ds);
+  k_dec_chunkscan<<<1, 1024, 0, s>>>(g, di, ds);
+  k_dec_blockoff<<<nc, 256, 0, s>>>(g, in, di, ds);
+  k_huff_decode<<<(unsigned int)((g.nblocks + 127) / 128), 128, 0, s>>>(g, in, di, ds);
+  if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
+  const int b0 = g.b[0], b1 = g.b[1], b2 = g.b[2];
+#define PC_SHAPE(A, B, C) \
+  if (b0 == A && b1 == B && b2 == C) return launch_r_shape<T, A, B, C>(in, g, di, ds, mlp, out, nsm, s);
+  PC_SHAPE(8, 8, 8)
+  PC_SHAPE(4, 4, 4)
+  PC_SHAPE(16, 16, 16)
+  PC_SHAPE(1, 16, 32)
+  PC_SHAPE(1, 8, 8)
+  PC_SHAPE(1, 64, 64)
+#undef PC_SHAPE
+  return PC_ERR_ARG;
+}
+template int launch_decompress<float>(const uint8_t*, const Geo&, const DecInfo&, const DecScratch&, const Mlp&,
+                                      float*, int, cudaStream_t);
+template int launch_decompress<double>(const uint8_t*, const Geo&, const DecInfo&, const DecScratch&, const Mlp&,
+                                       double*, int, cudaStream_t);
+
+}  // namespace pc

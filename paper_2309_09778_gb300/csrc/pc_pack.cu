@@ -1,0 +1,336 @@
+// a11-a12: per-block code-length sums, their prefix scan, the container
+// header, and bit-packing of the code words and balance points.
+//
+// Blocks are grouped in chunks of about 16K points.  k_blockbits sums each
+// block's code lengths and writes the block table; k_chunkscan scans the chunk
+// totals in one CTA, fixes the section offsets, writes the header (with its
+// CRC-32) and the weights, and zeroes the stream words that two chunks share;
+// k_pack assembles each chunk's bits in shared memory (code words MSB first)
+// and writes whole words, using atomicOr only on the two boundary words.
+#include "pc_kernels.cuh"
+
+namespace pc {
+
+__device__ __forceinline__ void block_coords(const Geo& g, long long b, long long& bz, long long& by, long long& bx,
+                                             int& e0, int& e1, int& e2) {
+  bx = b % g.nb[2];
+  const long long t = b / g.nb[2];
+  by = t % g.nb[1];
+  bz = t / g.nb[1];
+  e0 = (int)min((long long)g.b[0], g.n[0] - bz * g.b[0]);
+  e1 = (int)min((long long)g.b[1], g.n[1] - by * g.b[1]);
+  e2 = (int)min((long long)g.b[2], g.n[2] - bx * g.b[2]);
+}
+
+// padded raster index j of a block -> does it hold a non-anchor point?
+__device__ __forceinline__ bool slot_valid(const Geo& g, int j, int e0, int e1, int e2, bool full) {
+  if (j == 0) return false;
+  if (full) return true;
+  const int b12 = g.b[1] * g.b[2];
+  const int lz = j / b12, r = j - lz * b12, ly = r / g.b[2], lx = r - ly * g.b[2];
+  return lz < e0 && ly < e1 && lx < e2;
+}
+
+__global__ void __launch_bounds__(256) k_blockbits(Geo g, const uint16_t* __restrict__ codes,
+                                                   const uint8_t* __restrict__ nnflag,
+                                                   const uint32_t* __restrict__ nout, const uint8_t* __restrict__ lens,
+                                                   uint32_t* __restrict__ bbits, unsigned long long* chunk_bits,
+                                                   unsigned long long* chunk_nout, const State* __restrict__ st,
+                                                   uint8_t* out) {
+  __shared__ unsigned long long s_b[8], s_o[8];
+  if (st->err) return;
+  const long long c = blockIdx.x;
+  const long long b0 = c * g.ch, b1 = min(g.nblocks, b0 + g.ch);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned long long off_bb = st->off_bb, off_bn = st->off_bn;
+  unsigned long long wb = 0, wo = 0;
+  for (long long b = b0 + wid; b < b1; b += 8) {
+    long long bz, by, bx;
+    int e0, e1, e2;
+    block_coords(g, b, bz, by, bx, e0, e1, e2);
+    const bool full = e0 == g.b[0] && e1 == g.b[1] && e2 == g.b[2];
+    unsigned int s = 0;
+    const uint16_t* cb = codes + b * g.bvol;
+    if (full && (g.bvol & 255) == 0) {
+      for (int j8 = lane; j8 < g.bvol / 8; j8 += 32) {
+        const uint4 v = *reinterpret_cast<const uint4*>(cb + 8 * j8);
+        const unsigned int u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = 8 * j8 + 2 * q;
+          s += (j != 0 ? lens[u[q] & 0xFFFFu] : 0u) + lens[u[q] >> 16];
+        }
+      }
+    } else {
+      for (int j = lane; j < g.bvol; j += 32)
+        if (slot_valid(g, j, e0, e1, e2, full)) s += lens[cb[j]];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    if (lane == 0) {
+      bbits[b] = s;
+      const unsigned int no = nout[b];
+      st_u32(out + off_bb + 4ull * b, s | ((unsigned int)nnflag[b] << 31));
+      *reinterpret_cast<uint16_t*>(out + off_bn + 2ull * b) = (uint16_t)no;
+      wb += s;
+      wo += no;
+    }
+  }
+  if (lane == 0) { s_b[wid] = wb; s_o[wid] = wo; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tb = 0, to = 0;
+    for (int i = 0; i < 8; ++i) { tb += s_b[i]; to += s_o[i]; }
+    chunk_bits[c] = tb;
+    chunk_nout[c] = to;
+  }
+}
+
+__constant__ unsigned int c_dummy;  // keeps the constant bank non-empty for toolchains that warn
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_chunkscan(Geo g, const unsigned long long* __restrict__ chunk_bits,
+                                                    const unsigned long long* __restrict__ chunk_nout,
+                                                    unsigned long long* chunk_boff, unsigned long long* chunk_ooff,
+                                                    State* st, uint8_t* out, HdrInfo hi,
+                                                    const __grid_constant__ Mlp mlp) {
+  __shared__ unsigned long long s_w[32];
+  __shared__ unsigned int s_crc[256];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (st->err) return;
+  const long long nc = g.nchunks;
+  const long long per = (nc + nt - 1) / nt;
+  const long long lo = min(nc, tid * per), hi2 = min(nc, lo + per);
+  unsigned long long sb = 0, so = 0;
+  for (long long i = lo; i < hi2; ++i) { sb += chunk_bits[i]; so += chunk_nout[i]; }
+  unsigned long long tb, to;
+  unsigned long long pb = cta_exscan<unsigned long long>(sb, s_w, tb);
+  unsigned long long po = cta_exscan<unsigned long long>(so, s_w, to);
+  for (long long i = lo; i < hi2; ++i) {
+    chunk_boff[i] = pb;
+    chunk_ooff[i] = po;
+    pb += chunk_bits[i];
+    po += chunk_nout[i];
+  }
+  const unsigned long long ts = sizeof(T);
+  const unsigned long long swords = (tb + 31) / 32;
+  const unsigned long long off_bb = st->off_bb, off_bn = st->off_bn;
+  const unsigned long long off_ov = al16(off_bn + 2ull * (unsigned long long)g.nblocks);
+  const unsigned long long off_st = al16(off_ov + ts * to);
+  const unsigned long long total = al16(off_st + 4ull * swords);
+  __syncthreads();
+  if (total > hi.cap) {
+    if (tid == 0) st->err = PC_ERR_CAPACITY;
+    return;
+  }
+  if (tid == 0) {
+    st->n_out = to;
+    st->total_bits = tb;
+    st->swords = swords;
+    st->off_ov = off_ov;
+    st->off_st = off_st;
+    st->total = total;
+    st->out_size = total;
+  }
+  // zero the stream words shared between chunks, the section pads and the stream tail
+  uint32_t* stream = reinterpret_cast<uint32_t*>(out + off_st);
+  for (long long i = lo; i < hi2; ++i) {
+    const unsigned long long bits = chunk_bits[i];
+    if (bits) {
+      const unsigned long long s0 = chunk_boff[i];
+      stream[s0 >> 5] = 0u;
+      stream[(s0 + bits - 1) >> 5] = 0u;
+    }
+  }
+  for (unsigned long long i = off_bb + 4ull * g.nblocks + tid; i < off_bn; i += nt) out[i] = 0;
+  for (unsigned long long i = off_bn + 2ull * g.nblocks + tid; i < off_ov; i += nt) out[i] = 0;
+  for (unsigned long long i = off_ov + ts * to + tid; i < off_st; i += nt) out[i] = 0;
+  for (unsigned long long i = off_st + 4ull * swords + tid; i < total; i += nt) out[i] = 0;
+  // weights and their pad
+  for (int i = tid; i < hi.nw; i += nt) st_u32(out + kHdr + 4ull * i, __float_as_uint(mlp.w[i]));
+  for (unsigned long long i = kHdr + 4ull * hi.nw + tid; i < hi.off_cb; i += nt) out[i] = 0;
+  // header
+  if (tid < 256) {
+    unsigned int cr = (unsigned int)tid;
+    for (int k = 0; k < 8; ++k) cr = (cr >> 1) ^ (0xEDB88320u & (0u - (cr & 1u)));
+    s_crc[tid] = cr;
+  }
+  if (tid < 64) st_u32(out + 4 * tid, 0u);
+  __syncthreads();
+  if (tid == 0) {
+    const State& c = *st;
+    const bool nn = hi.pred != 0;
+    st_u32(out + 0, 0x504D4350u);  // "PCMP"
+    st_u32(out + 4, 1u);
+    st_u32(out + 8, (unsigned int)hi.dtype);
+    st_u32(out + 12, nn ? 1u : 0u);
+    st_u64(out + 16, (unsigned long long)g.n[0]);
+    st_u64(out + 24, (unsigned long long)g.n[1]);
+    st_u64(out + 32, (unsigned long long)g.n[2]);
+    st_u32(out + 40, (unsigned int)g.b[0]);
+    st_u32(out + 44, (unsigned int)g.b[1]);
+    st_u32(out + 48, (unsigned int)g.b[2]);
+    st_u32(out + 52, nn ? (unsigned int)hi.stencil : 0u);
+    st_u32(out + 56, nn ? (unsigned int)hi.h1 : 0u);
+    st_u32(out + 60, nn ? (unsigned int)hi.h2 : 0u);
+    st_u32(out + 64, (unsigned int)hi.m);
+    st_u32(out + 68, nn ? (unsigned int)hi.s_in : 0u);
+    st_u64(out + 72, (unsigned long long)__double_as_longlong(hi.eb));
+    st_u64(out + 80, (unsigned long long)__double_as_longlong(c.amin));
+    st_u64(out + 88, (unsigned long long)__double_as_longlong(c.amax));
+    st_u32(out + 96, (unsigned int)c.trivial);
+    st_u32(out + 100, (unsigned int)c.Kp);
+    st_u32(out + 104, (unsigned int)c.Kn);
+    st_u32(out + 108, (unsigned int)c.Zq);
+    st_u32(out + 112, (unsigned int)c.S);
+    st_u32(out + 116, c.n_used);
+    if (sizeof(T) == 4) {
+      st_u64(out + 120, __float_as_uint(c.step32));
+      st_u64(out + 128, __float_as_uint(c.inv32));
+      st_u64(out + 136, __float_as_uint(c.ebdn32));
+    } else {
+      st_u64(out + 120, (unsigned long long)__double_as_longlong(c.stepd));
+      st_u64(out + 128, (unsigned long long)__double_as_longlong(c.invd));
+      st_u64(out + 136, (unsigned long long)__double_as_longlong(c.ebdnd));
+    }
+    st_u64(out + 144, (unsigned long long)g.nblocks);
+    st_u64(out + 152, to);
+    st_u64(out + 160, swords);
+    st_u64(out + 168, (unsigned long long)kHdr);
+    st_u64(out + 176, hi.off_cb);
+    st_u64(out + 184, off_bb);
+    st_u64(out + 192, off_bn);
+    st_u64(out + 200, off_ov);
+    st_u64(out + 208, off_st);
+    st_u64(out + 216, total);
+    st_u32(out + 224, (unsigned int)hi.nw);
+    unsigned int crc = 0xFFFFFFFFu;
+    for (int i = 0; i < 252; ++i) crc = s_crc[(crc ^ out[i]) & 0xFFu] ^ (crc >> 8);
+    st_u32(out + 252, crc ^ 0xFFFFFFFFu);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pack(Geo g, const T* __restrict__ x, const uint16_t* __restrict__ codes,
+                                              const uint32_t* __restrict__ nout, const uint32_t* __restrict__ bbits,
+                                              const uint8_t* __restrict__ lens, const uint32_t* __restrict__ cw,
+                                              const unsigned long long* __restrict__ chunk_bits,
+                                              const unsigned long long* __restrict__ chunk_boff,
+                                              const unsigned long long* __restrict__ chunk_ooff,
+                                              const State* __restrict__ st, uint8_t* out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned int s_w[32];
+  if (st->err) return;
+  const long long c = blockIdx.x;
+  const long long b0 = c * g.ch, b1 = min(g.nblocks, b0 + g.ch);
+  const int nb = (int)(b1 - b0);
+  unsigned int* s_boff = reinterpret_cast<unsigned int*>(smem);    // [ch]
+  unsigned int* s_ooff = s_boff + g.ch;                            // [ch]
+  unsigned int* s_words = s_ooff + g.ch;                           // chunk bit buffer
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // per-block offsets inside the chunk
+  const int per = (nb + 255) / 256;
+  const int lo = min(nb, tid * per), hi = min(nb, lo + per);
+  unsigned int sb = 0, so = 0;
+  for (int i = lo; i < hi; ++i) { sb += bbits[b0 + i]; so += nout[b0 + i]; }
+  unsigned int tb, to;
+  unsigned int pb = cta_exscan<unsigned int>(sb, s_w, tb);
+  unsigned int po = cta_exscan<unsigned int>(so, s_w, to);
+  for (int i = lo; i < hi; ++i) {
+    s_boff[i] = pb;
+    s_ooff[i] = po;
+    pb += bbits[b0 + i];
+    po += nout[b0 + i];
+  }
+  const unsigned long long S = chunk_boff[c];
+  const unsigned long long CB = chunk_bits[c];
+  const int sh = (int)(S & 31ull);
+  const int nwords = (int)((sh + CB + 31) >> 5);
+  for (int i = tid; i < nwords; i += 256) s_words[i] = 0u;
+  __syncthreads();
+  const unsigned long long off_ov = st->off_ov, off_st = st->off_st;
+  T* ov = reinterpret_cast<T*>(out + off_ov);
+  const unsigned long long obase = chunk_ooff[c];
+  for (int i = wid; i < nb; i += 8) {
+    const long long b = b0 + i;
+    long long bz, by, bx;
+    int e0, e1, e2;
+    block_coords(g, b, bz, by, bx, e0, e1, e2);
+    const bool full = e0 == g.b[0] && e1 == g.b[1] && e2 == g.b[2];
+    const long long z0 = bz * g.b[0], y0 = by * g.b[1], x0 = bx * g.b[2];
+    unsigned int pos = (unsigned int)sh + s_boff[i];
+    unsigned long long op = obase + s_ooff[i];
+    if (lane == 0) ov[op] = x[(z0 * g.n[1] + y0) * g.n[2] + x0];
+    op += 1;
+    const uint16_t* cb = codes + b * g.bvol;
+    const int b12 = g.b[1] * g.b[2];
+    for (int j0 = 0; j0 < g.bvol; j0 += 32) {
+      const int j = j0 + lane;
+      const bool valid = j < g.bvol && slot_valid(g, j, e0, e1, e2, full);
+      const unsigned int cd = valid ? cb[j] : 0u;
+      const unsigned int L = valid ? lens[cd] : 0u;
+      unsigned int incl = L;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const unsigned int tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+      if (L) {
+        const unsigned int p = pos + incl - L;
+        const unsigned int wv = cw[cd];
+        const unsigned int wi = p >> 5, bo = p & 31u;
+        if (bo + L <= 32u) {
+          atomicOr(&s_words[wi], wv << (32u - bo - L));
+        } else {
+          atomicOr(&s_words[wi], wv >> (bo + L - 32u));
+          atomicOr(&s_words[wi + 1], wv << (64u - bo - L));
+        }
+      }
+      pos += tot;
+      const bool isout = valid && cd == 0u;
+      const unsigned int bal = __ballot_sync(0xFFFFFFFFu, isout);
+      if (isout) {
+        const int lz = j / b12, r = j - lz * b12, ly = r / g.b[2], lx = r - ly * g.b[2];
+        ov[op + __popc(bal & ((1u << lane) - 1u))] = x[((z0 + lz) * g.n[1] + (y0 + ly)) * g.n[2] + x0 + lx];
+      }
+      op += __popc(bal);
+    }
+  }
+  __syncthreads();
+  if (CB == 0) return;
+  uint32_t* stream = reinterpret_cast<uint32_t*>(out + off_st);
+  const unsigned long long W0 = S >> 5;
+  for (int wi = tid; wi < nwords; wi += 256) {
+    const unsigned long long gw = W0 + wi;
+    const bool inside = gw * 32ull >= S && gw * 32ull + 32ull <= S + CB;
+    if (inside) stream[gw] = s_words[wi];
+    else atomicOr(&stream[gw], s_words[wi]);
+  }
+}
+
+template <typename T>
+int launch_pack(const T* x, const Geo& g, const uint16_t* codes, const uint8_t* nnflag, const uint32_t* nout,
+                const uint8_t* lens, const uint32_t* cw, uint32_t* bbits, unsigned long long* chunk_bits,
+                unsigned long long* chunk_nout, unsigned long long* chunk_boff, unsigned long long* chunk_ooff,
+                State* st, uint8_t* out, const HdrInfo& hi, const Mlp& mlp, cudaStream_t s) {
+  const unsigned int nc = (unsigned int)g.nchunks;
+  k_blockbits<<<nc, 256, 0, s>>>(g, codes, nnflag, nout, lens, bbits, chunk_bits, chunk_nout, st, out);
+  k_chunkscan<T><<<1, 1024, 0, s>>>(g, chunk_bits, chunk_nout, chunk_boff, chunk_ooff, st, out, hi, mlp);
+  const size_t words = ((size_t)g.ch * (size_t)(g.bvol > 1 ? g.bvol - 1 : 1) * kLmax + 31) / 32 + 2;
+  const size_t smem = (size_t)g.ch * 8 + words * 4;
+  if (cudaFuncSetAttribute(k_pack<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return PC_ERR_CUDA;
+  k_pack<T><<<nc, 256, smem, s>>>(g, x, codes, nout, bbits, lens, cw, chunk_bits, chunk_boff, chunk_ooff, st, out);
+  return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
+}
+template int launch_pack<float>(const float*, const Geo&, const uint16_t*, const uint8_t*, const uint32_t*,
+                                const uint8_t*, const uint32_t*, uint32_t*, unsigned long long*, unsigned long long*,
+                                unsigned long long*, unsigned long long*, State*, uint8_t*, const HdrInfo&, const Mlp&,
+                                cudaStream_t);
+template int launch_pack<double>(const double*, const Geo&, const uint16_t*, const uint8_t*, const uint32_t*,
+                                 const uint8_t*, const uint32_t*, uint32_t*, unsigned long long*, unsigned long long*,
+                                 unsigned long long*, unsigned long long*, State*, uint8_t*, const HdrInfo&,
+                                 const Mlp&, cudaStream_t);
+
+}  // namespace pc
