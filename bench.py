@@ -1,0 +1,304 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 compressor on one 100x500x500 float32 field.
+
+One step = pc_compress + pc_decompress of the field (the whole hot path:
+statistics, constants, transform, prediction, quantization, histogram,
+codebook, packing, and the inverse path).  The field is a seeded synthetic
+log-normal signed Gaussian random field (power spectrum k^-11/3, 2% exact
+zeros) standing in for the paper's SEG-Y volumes, eb_rel = 1e-3, 8x8x8 blocks.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same field instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "compress/decompress GB/s and bits/value at eb_rel, % of HBM roofline, vs FP32 plain"
+SHAPE = (100, 500, 500)
+EB = 1e-3
+BLOCK = (8, 8, 8)
+SAMPLE = (40, 200, 200)  # oracle sample: a corner sub-volume of the same field
+
+
+def field():
+    from paper_2309_09778_gb300 import gen
+    return gen.signed_lognormal(SHAPE, 11.0 / 3.0, 0, 2.0, 0.02)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if "Active" in r[3 + i]
+                          and "Not" not in r[3 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def cpu_oracle_rate(x: np.ndarray, steps: int, predictor):
+    """Time the oracle's compress + decompress on the bounded sample."""
+    from oracle import oracle as O
+    sub = np.ascontiguousarray(x[: SAMPLE[0], : SAMPLE[1], : SAMPLE[2]])
+    w, s_in = predictor[0], predictor[1]
+    t = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        st, blob = O.compress(sub, EB, block=BLOCK, weights=w, s_in=s_in)
+        st2, y = O.decompress(blob)
+        t.append(time.perf_counter() - t0)
+        assert st == 0 and st2 == 0
+    return sub.nbytes, t
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    x = field()
+    pred = device_free_predictor(x)
+    nbytes, t = cpu_oracle_rate(x, max(1, args.steps), pred)
+    v = nbytes * len(t) / sum(t) / 1e9
+    sample = f"sub-volume {SAMPLE[0]}x{SAMPLE[1]}x{SAMPLE[2]} of the workload field, compress+decompress per step"
+    line = {"metric": METRIC, "value": v, "unit": "GB/s", "impl": "reference", "n_gpus": args.gpus,
+            "steps": len(t), "warmup": 0, "ms_per_step": 1e3 * sum(t) / len(t), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "grf100x500x500_f32", "eb_rel": EB, "block": list(BLOCK),
+                       "predictor": pred[2]},
+            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def device_free_predictor(x):
+    """(weights, s_in, name) used by both arms; Lorenzo until a trained model is supplied."""
+    return None, 0, "lorenzo"
+
+
+# algorithmic bytes per launch of each stage ("kernels and their rooflines")
+def algorithmic_bytes(stage: str, n: int, ts: int, comp_bytes: int) -> int:
+    return {"stats": n * ts, "compress": n * ts, "pack": comp_bytes, "huff_decode": comp_bytes,
+            "recon": n * ts, "blockbits": 0, "codebook": 0}.get(stage, 0)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2309_09778_gb300.pc as pc
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    x = field()
+    w, s_in, pname = device_free_predictor(x)
+    params = pc.make_params(EB, BLOCK, pred=pc.PC_PRED_LORENZO if w is None else pc.PC_PRED_MLP_FP32,
+                            stencil=7, hidden=(16, 16), s_in=s_in, weights=w)
+    n = x.size
+    nbytes = x.nbytes
+    d = torch.from_numpy(x).to(dev)
+    cap = pc.pc_compress_bound(SHAPE, pc.PC_F32, params)
+    out = torch.empty(cap, dtype=torch.uint8, device=dev)
+    wsc = torch.empty(pc.pc_compress_workspace_size(SHAPE, pc.PC_F32, params), dtype=torch.uint8, device=dev)
+    y = torch.empty_like(d)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+    size = pc.pc_compress(d, params, out, wsc)
+    _, _, wsb = pc.pc_header_info(out[:256].cpu().numpy().tobytes())
+    wsd = torch.empty(wsb, dtype=torch.uint8, device=dev)
+
+    def step(timing):
+        flush.zero_()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        sz = pc.pc_compress(d, params, out, wsc, stream)
+        e1.record(stream)
+        pc.pc_decompress(out, sz, y, wsd, stream)
+        e2.record(stream)
+        timing.append((e0, e1, e2))
+        return sz
+
+    for _ in range(args.warmup):
+        step([])
+    torch.cuda.synchronize()
+    ok = bool(((y.double() - d.double()).abs() <= EB * d.double().abs()).all().item())
+    clocks = ClockSampler(local)
+    clocks.start()
+    pc.pc_profile_enable(True)
+    pc.pc_profile_read()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev = []
+    for _ in range(args.steps):
+        size = step(ev)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - t0
+    prof = pc.pc_profile_read()
+    pc.pc_profile_enable(False)
+    clk = clocks.stop()
+    tc = sum(a.elapsed_time(b) for a, b, _ in ev) / len(ev)
+    td = sum(b.elapsed_time(c) for _, b, c in ev) / len(ev)
+    t_step = tc + td
+    if dist:
+        tt = torch.tensor([t_step, tc, td], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step, tc, td = tt.tolist()
+
+    # end to end through the host-buffer entry points (pinned host memory)
+    h_field = torch.from_numpy(x).pin_memory()
+    h_out = torch.empty(cap, dtype=torch.uint8).pin_memory()
+    h_y = torch.empty(SHAPE, dtype=torch.float32).pin_memory()
+    dstage = torch.empty_like(d)
+    hf, ho, hy = h_field.numpy(), h_out.numpy(), h_y.numpy()
+    for _ in range(2):
+        sz = pc.pc_compress_host(hf, params, ho, dstage, out, wsc)
+        pc.pc_decompress_host(ho, sz, hy, out, dstage, wsd)
+    te = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        sz = pc.pc_compress_host(hf, params, ho, dstage, out, wsc)
+        pc.pc_decompress_host(ho, sz, hy, out, dstage, wsd)
+        te.append(time.perf_counter() - t1)
+    e2e_ok = np.array_equal(hy.view(np.uint32), y.cpu().numpy().view(np.uint32))
+
+    # plain FP32: a device copy of the field at HBM speed
+    dst = torch.empty_like(d)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
+    c0.record(stream)
+    for _ in range(5):
+        dst.copy_(d)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    copy_gbs = 2 * nbytes * 5 / (c0.elapsed_time(c1) * 1e6)
+
+    peak, peak_kind = peaks()
+    stages = {k: v for k, v in prof.items() if v[1] > 0}
+    total_dev = sum(v[0] for v in stages.values())
+    dom = max(stages, key=lambda k: stages[k][0])
+    dom_ms = stages[dom][0] / stages[dom][1]
+    alg = algorithmic_bytes(dom, n, 4, size)
+    achieved = alg / (dom_ms * 1e6) if alg else None
+    bpv = 8.0 * size / n
+    launches = sum(v[1] for v in stages.values())
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            nb, t = cpu_oracle_rate(x, 1, (w, s_in, pname))
+            cpu = {"value": nb / t[0] / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                   "sample": f"{SAMPLE[0]}x{SAMPLE[1]}x{SAMPLE[2]} corner sub-volume, compress+decompress, "
+                             f"{t[0]:.1f} s"}
+        line = {
+            "metric": METRIC, "value": world * nbytes / (t_step * 1e6), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "grf100x500x500_f32: 100x500x500 float32 signed log-normal GRF, k^-11/3, "
+                                   "2% zeros", "eb_rel": EB, "block": list(BLOCK), "predictor": pname,
+                       "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "compress_gbs": nbytes / (tc * 1e6), "decompress_gbs": nbytes / (td * 1e6),
+            "bits_per_value": bpv, "bound_held": ok,
+            "vs_fp32_plain": {"bits_per_value": 32.0, "ratio": 32.0 / bpv, "device_copy_gbs": copy_gbs},
+            "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "peak_source": peak_kind, "algorithmic_bytes_per_launch": alg,
+                         "avg_launch_ms": dom_ms},
+            "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+            "cpu_baseline": cpu,
+            "e2e": {"value": nbytes / statistics.median(te) / 1e9, "unit": "GB/s",
+                    "h2d_bytes_per_step": nbytes + size, "d2h_bytes_per_step": size + nbytes,
+                    "matches_device_path": e2e_ok},
+            "clocks": clk, "gpu_launches": launches, "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

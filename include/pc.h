@@ -156,6 +156,19 @@ int pc_train(const void* d_field, const size_t dims[3], int dtype, const pc_para
 int pc_compress_workspace_layout(const size_t dims[3], int dtype, const pc_params* p,
                                  size_t* off_codes, size_t* off_nnflag, size_t* off_hist);
 
+/*
+ * Per-kernel timing (tracing).  pc_profile_enable(1) makes every following
+ * pc_compress / pc_decompress record a CUDA event pair around each of its
+ * kernel launches on the call's stream; the durations are added up per stage
+ * once the call has synchronized.  pc_profile_read copies up to n stage sums
+ * (milliseconds of device time) and launch counts, then clears them; it
+ * returns the number of stages.  pc_profile_stage_name names stage i.
+ * Events are created once per process on first enable (no device memory).
+ */
+int pc_profile_enable(int on);
+int pc_profile_read(double* ms, long long* launches, int n);
+const char* pc_profile_stage_name(int i);
+
 /* Human-readable name of a status code. */
 const char* pc_strerror(int status);
 

@@ -90,9 +90,9 @@ def lib():
             L.orc_mlp_pred32.restype = C.c_int32
             L.orc_mlp_pred32.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]
             L.orc_huffman_lengths.restype = C.c_int
-            L.orc_huffman_lengths.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p]
-            L.orc_canonical_codes.restype = None
-            L.orc_canonical_codes.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+            L.orc_huffman_lengths.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
+            L.orc_canonical_codes.restype = C.c_int
+            L.orc_canonical_codes.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
             L.orc_compress_bound.restype = C.c_uint64
             L.orc_compress_bound.argtypes = [u64p, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int]
             L.orc_compress.restype = C.c_int
@@ -225,17 +225,27 @@ def mlp_pred32(w: np.ndarray, k, h1, h2, s_in, v) -> int:
     return lib().orc_mlp_pred32(_p(w), k, h1, h2, s_in, _p(v))
 
 
-def huffman_lengths(hist: np.ndarray, lmax: int = LMAX) -> np.ndarray:
+def huffman_lengths(hist: np.ndarray, lmax: int = LMAX, with_order: bool = False):
+    """Code lengths per symbol; with_order also returns the code order (most frequent first)."""
     h = np.ascontiguousarray(hist, np.uint64)
     out = np.zeros(h.size, np.uint8)
-    lib().orc_huffman_lengths(_p(h), h.size, lmax, _p(out))
+    order = np.zeros(max(h.size, 1), np.uint32)
+    n = lib().orc_huffman_lengths(_p(h), h.size, lmax, _p(out), _p(order))
+    if with_order:
+        return out, order[:n].copy()
     return out
 
 
-def canonical_codes(lens: np.ndarray, lmax: int = LMAX) -> np.ndarray:
+def canonical_codes(lens: np.ndarray, order=None) -> np.ndarray:
+    """Code words along `order` (default: by length, then symbol, as in RFC 1951)."""
     ln = np.ascontiguousarray(lens, np.uint8)
+    if order is None:
+        used = np.flatnonzero(ln)
+        order = used[np.lexsort((used, ln[used]))]
+    order = np.ascontiguousarray(order, np.uint32)
     out = np.zeros(ln.size, np.uint32)
-    lib().orc_canonical_codes(_p(ln), ln.size, lmax, _p(out))
+    st = lib().orc_canonical_codes(_p(order), order.size, _p(ln), _p(out))
+    assert st == 0, "lengths must not decrease along the order"
     return out
 
 

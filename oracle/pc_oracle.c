@@ -402,6 +402,9 @@ static int o_bitlen(uint64_t n) { int b = 0; while (n) { b++; n >>= 1; } return 
 
 /* ------------------------------------------------------------------------- */
 /* Step a10: Huffman code lengths (Section IV.A stage 3; Section IV.C).      */
+/* The code order handed to the canonical construction is the reverse of    */
+/* the sorted leaf list (most frequent first), as an ordered symbol list in */
+/* the style of ITU-T T.81 Annex C (BITS/HUFFVAL).                          */
 /* Textbook Huffman: repeatedly join the two lightest nodes.  Total order:   */
 /* (weight, leaf before internal node, leaves by symbol, internal nodes by   */
 /* creation).  A single used symbol gets length 1.  Lengths are then handed   */
@@ -418,7 +421,7 @@ static int o_cmp_leaf(const void* a, const void* b) {
   return x->s < y->s ? -1 : (x->s > y->s ? 1 : 0);
 }
 
-int orc_huffman_lengths(const uint64_t* hist, int nsym, int lmax, uint8_t* len) {
+int orc_huffman_lengths(const uint64_t* hist, int nsym, int lmax, uint8_t* len, uint32_t* order) {
   memset(len, 0, (size_t)nsym);
   int n = 0;
   for (int s = 0; s < nsym; s++) n += hist[s] > 0;
@@ -427,7 +430,7 @@ int orc_huffman_lengths(const uint64_t* hist, int nsym, int lmax, uint8_t* len) 
   int t = 0;
   for (int s = 0; s < nsym; s++)
     if (hist[s] > 0) { L[t].f = hist[s]; L[t].s = (uint32_t)s; t++; }
-  if (n == 1) { len[L[0].s] = 1; free(L); return 1; }
+  if (n == 1) { len[L[0].s] = 1; if (order) order[0] = L[0].s; free(L); return 1; }
   qsort(L, (size_t)n, sizeof(o_leaf), o_cmp_leaf);
   int nn = 2 * n - 1;
   uint64_t* w = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)nn);
@@ -467,19 +470,28 @@ int orc_huffman_lengths(const uint64_t* hist, int nsym, int lmax, uint8_t* len) 
   int idx = 0;
   for (int l = maxlen; l >= 1; l--)
     for (int c = 0; c < bits[l]; c++) len[L[idx++].s] = (uint8_t)l;
+  if (order)
+    for (int i = 0; i < n; i++) order[i] = L[n - 1 - i].s;
   free(bits); free(depth); free(parent); free(w); free(L);
   return n;
 }
 
-/* Canonical code words from lengths: the construction of RFC 1951 Section 3.2.2
- * (codes of one length are consecutive, in symbol order). */
-void orc_canonical_codes(const uint8_t* len, int nsym, int lmax, uint32_t* code) {
-  uint32_t blc[33] = {0}, nextc[33] = {0};
-  for (int s = 0; s < nsym; s++) if (len[s]) blc[len[s]]++;
+/* Canonical code words along a given symbol order whose lengths never
+ * decrease: the first code is all zeros and each next code is the previous
+ * plus one, shifted left by the growth in length.  This is the construction
+ * of RFC 1951 Section 3.2.2 (there the order is by length, then symbol) and
+ * of ITU-T T.81 Annex C (there the order is HUFFVAL). */
+int orc_canonical_codes(const uint32_t* order, int n, const uint8_t* len, uint32_t* code) {
   uint32_t c = 0;
-  blc[0] = 0;
-  for (int b = 1; b <= lmax; b++) { c = (c + blc[b - 1]) << 1; nextc[b] = c; }
-  for (int s = 0; s < nsym; s++) { code[s] = 0; if (len[s]) code[s] = nextc[len[s]]++; }
+  int prev = 0;
+  for (int i = 0; i < n; i++) {
+    int l = len[order[i]];
+    if (l < prev || l < 1) return ORC_ERR_ARG;
+    if (i > 0) c = (c + 1u) << (l - prev);
+    code[order[i]] = c;
+    prev = l;
+  }
+  return ORC_OK;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -644,9 +656,10 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
 
   /* a10: code lengths and canonical codes */
   uint8_t* lens = (uint8_t*)malloc((size_t)nsym);
-  uint32_t* cw = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)nsym);
-  int n_used = orc_huffman_lengths(hist, nsym, O_LMAX, lens);
-  orc_canonical_codes(lens, nsym, O_LMAX, cw);
+  uint32_t* cw = (uint32_t*)calloc((size_t)nsym, sizeof(uint32_t));
+  uint32_t* order = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)nsym);
+  int n_used = orc_huffman_lengths(hist, nsym, O_LMAX, lens, order);
+  orc_canonical_codes(order, n_used, lens, cw);
 
   /* a11: per-block bit counts and total */
   uint32_t* bbits = (uint32_t*)malloc(sizeof(uint32_t) * g.nblocks);
@@ -713,11 +726,8 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
 
   /* sections */
   for (int i = 0; i < nw; i++) put32(out + off_w + 4ull * i, bits_of_f(p->weights[i]));
-  {
-    uint64_t t = 0;
-    for (int s = 0; s < nsym; s++)
-      if (lens[s]) { put32(out + off_cb + 4ull * t, (uint32_t)s | ((uint32_t)lens[s] << 16)); t++; }
-  }
+  for (int t = 0; t < n_used; t++)
+    put32(out + off_cb + 4ull * (uint64_t)t, order[t] | ((uint32_t)lens[order[t]] << 16));
   for (uint64_t b = 0; b < g.nblocks; b++) {
     put32(out + off_bb + 4ull * b, bbits[b] | ((uint32_t)nnf[b] << 31));
     out[off_bn + 2ull * b] = (uint8_t)(nout[b] & 0xFF);
@@ -767,7 +777,7 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
     if (dump->lens) memcpy(dump->lens, lens, (size_t)nsym);
   }
 done:
-  free(bbits); free(cw); free(lens); free(cz); free(cn); free(vt); free(vc);
+  free(order); free(bbits); free(cw); free(lens); free(cz); free(cn); free(vt); free(vc);
   free(hist); free(nout); free(nnf); free(codes); free(okv); free(dq);
   return ret;
 }
@@ -841,19 +851,22 @@ int orc_decompress(const uint8_t* in, uint64_t in_size, void* xo, uint64_t cap_e
     wts = (float*)malloc(sizeof(float) * (size_t)nw);
     for (int i = 0; i < nw; i++) wts[i] = f_from_bits(get32(in + off_w + 4ull * i));
   }
-  /* canonical decoder tables */
+  /* canonical decoder tables: the stored list is the code order */
   uint8_t* lens = (uint8_t*)calloc((size_t)nsym, 1);
   int ret = ORC_OK;
+  uint32_t cnt[O_LMAX + 1] = {0}, first[O_LMAX + 1] = {0}, offs[O_LMAX + 1] = {0};
+  uint32_t* sorted = (uint32_t*)malloc(sizeof(uint32_t) * (n_used + 1));
+  uint32_t prevl = 0;
   for (uint32_t t = 0; t < n_used; t++) {
     uint32_t e = get32(in + off_cb + 4ull * t);
     uint32_t s = e & 0xFFFFu, l = e >> 16;
-    if (s >= (uint32_t)nsym || l < 1 || l > O_LMAX || lens[s]) { ret = ORC_ERR_CORRUPT; break; }
+    if (s >= (uint32_t)nsym || l < 1 || l > O_LMAX || lens[s] || l < prevl) { ret = ORC_ERR_CORRUPT; break; }
     lens[s] = (uint8_t)l;
+    sorted[t] = s;
+    cnt[l]++;
+    prevl = l;
   }
-  uint32_t cnt[O_LMAX + 1] = {0}, first[O_LMAX + 1] = {0}, offs[O_LMAX + 1] = {0};
-  uint32_t* sorted = (uint32_t*)malloc(sizeof(uint32_t) * (n_used + 1));
   if (ret == ORC_OK) {
-    for (int s = 0; s < nsym; s++) if (lens[s]) cnt[lens[s]]++;
     uint32_t cc = 0, o = 0;
     for (int l = 1; l <= O_LMAX; l++) {
       cc = (cc + cnt[l - 1]) << 1;
@@ -862,9 +875,6 @@ int orc_decompress(const uint8_t* in, uint64_t in_size, void* xo, uint64_t cap_e
       o += cnt[l];
       if (cnt[l] && (uint64_t)first[l] + cnt[l] > (1ull << l)) ret = ORC_ERR_CORRUPT;
     }
-    uint32_t fill[O_LMAX + 1];
-    memcpy(fill, offs, sizeof(fill));
-    for (int s = 0; s < nsym; s++) if (lens[s]) sorted[fill[lens[s]]++] = (uint32_t)s;
   }
   int32_t* dq = (int32_t*)malloc(sizeof(int32_t) * g.bvol);
   int32_t* vc = (int32_t*)malloc(sizeof(int32_t) * g.bvol);

@@ -3,6 +3,7 @@
 #include <mutex>
 
 #include "pc_kernels.cuh"
+#include "pc_profile.cuh"
 
 using namespace pc;
 
@@ -224,8 +225,6 @@ int parse_header(const uint8_t* h, size_t n, Hdr& H, Geo& g) {
   return PC_OK;
 }
 
-int cuda_status(cudaError_t e) { return e == cudaSuccess ? PC_OK : PC_ERR_CUDA; }
-
 }  // namespace
 
 extern "C" {
@@ -351,6 +350,7 @@ int pc_compress(const void* d_field, const size_t dims[3], int dtype, const pc_p
   State hst;
   if (cudaMemcpyAsync(&hst, stp, sizeof(State), cudaMemcpyDeviceToHost, s) != cudaSuccess) return PC_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
+  prof_collect();
   if (hst.err) return hst.err;
   *out_size = (size_t)hst.out_size;
   return PC_OK;
@@ -450,6 +450,7 @@ int pc_decompress(const void* d_in, size_t in_size, void* d_field, size_t field_
   int err = 0;
   if (cudaMemcpyAsync(&err, ds.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return PC_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
+  prof_collect();
   return err ? err : PC_OK;
 }
 

@@ -11,28 +11,149 @@
 // rest of the list; the result is the sequential algorithm's tree exactly.
 // Lengths are then handed out by rank from the per-length counts (the lightest
 // leaf gets the longest length), with the ITU-T T.81 Annex K.3 adjustment when
-// a length exceeds 24, and canonical code words follow RFC 1951 Section 3.2.2.
+// a length exceeds 24.  Code words are assigned along the symbol list ordered
+// most frequent first (the sorted leaves reversed), where lengths never
+// decrease: consecutive codes per length, as in RFC 1951 Section 3.2.2 and
+// ITU-T T.81 Annex C.  Leaves are sorted by a stable radix sort on counts.
 #include "pc_kernels.cuh"
+#include "pc_profile.cuh"
 
 namespace pc {
 
 constexpr int kCbThreads = 1024;
-constexpr int kCbSmemN = 4096;  // node arrays live in shared memory up to this many leaves
+constexpr int kCbSmemN = 12288;  // merge rounds run in shared memory up to this many leaves
+constexpr size_t kCbSmem = (size_t)kCbSmemN * 16;  // w (u32, 2n) + parent (u16, 2n) + two lists (u16, n)
 
-__device__ void cta_bitonic(unsigned long long* a, int np) {
-  for (int k = 2; k <= np; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < np; i += blockDim.x) {
-        const int ixj = i ^ j;
-        if (ixj > i) {
-          const unsigned long long x = a[i], y = a[ixj];
-          const bool up = (i & k) == 0;
-          if ((x > y) == up) { a[i] = y; a[ixj] = x; }
-        }
+// Stable LSD radix sort (8-bit digits) of (key, val) pairs by key, one CTA of
+// 32 warps.  Each warp owns a contiguous tile; per-warp digit counts give
+// every (warp, digit) its output offset; inside a warp equal digits are
+// ranked in lane order with __match_any_sync, so the sort is stable.
+__device__ void cta_radix_sort(unsigned int* k0, uint16_t* v0, unsigned int* k1, uint16_t* v1, int n, int npass,
+                               unsigned int* s_hist /* [32][256] */, unsigned int* s_tot /* [256] */,
+                               unsigned long long* s_scan, unsigned int*& kout, uint16_t*& vout) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int T = (n + 31) / 32;
+  const int lo = min(n, wid * T), hi = min(n, lo + T);
+  unsigned int* ki = k0;
+  uint16_t* vi = v0;
+  unsigned int* ko = k1;
+  uint16_t* vo = v1;
+  for (int pass = 0; pass < npass; ++pass) {
+    const int sh = 8 * pass;
+    for (int i = tid; i < 32 * 256; i += blockDim.x) s_hist[i] = 0u;
+    __syncthreads();
+    for (int i = lo + lane; i < hi; i += 32) atomicAdd(&s_hist[wid * 256 + ((ki[i] >> sh) & 255u)], 1u);
+    __syncthreads();
+    unsigned long long col = 0;
+    if (tid < 256)
+      for (int w = 0; w < 32; ++w) col += s_hist[w * 256 + tid];
+    unsigned long long tot;
+    const unsigned long long base = cta_exscan<unsigned long long>(tid < 256 ? col : 0ull, s_scan, tot);
+    if (tid < 256) {
+      unsigned int run = (unsigned int)base;
+      for (int w = 0; w < 32; ++w) {
+        const unsigned int c = s_hist[w * 256 + tid];
+        s_hist[w * 256 + tid] = run;
+        run += c;
       }
-      __syncthreads();
     }
+    __syncthreads();
+    for (int c0 = lo; c0 < hi; c0 += 32) {
+      const int i = c0 + lane;
+      const bool valid = i < hi;
+      const unsigned int key = valid ? ki[i] : 0u;
+      const unsigned int d = valid ? ((key >> sh) & 255u) : 256u + (unsigned int)lane;
+      const unsigned int peers = __match_any_sync(0xFFFFFFFFu, d);
+      const unsigned int rank = __popc(peers & ((1u << lane) - 1u));
+      if (valid) {
+        const unsigned int pos = s_hist[wid * 256 + d] + rank;
+        ko[pos] = key;
+        vo[pos] = vi[i];
+      }
+      __syncwarp();
+      if (valid && lane == 31 - __clz(peers)) s_hist[wid * 256 + d] += __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    unsigned int* tk = ki; ki = ko; ko = tk;
+    uint16_t* tv = vi; vi = vo; vo = tv;
   }
+  kout = ki;
+  vout = vi;
+  (void)s_tot;
+}
+
+// Parallel Huffman merge rounds on a list of node ids (leaves 0..n-1 already
+// sorted by weight).  Returns the number of rounds; node ids n.. are internal.
+template <typename Id>
+__device__ int huff_rounds(unsigned int* w, Id* parent, Id* la, Id* lb, int* rstart, int n,
+                           unsigned long long* s_scan) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < n; i += nt) la[i] = (Id)i;
+  __syncthreads();
+  int len = n, next = n, round = 0;
+  while (len > 1) {
+    const unsigned int t1 = w[la[0]] + w[la[1]];
+    int c = 0;
+    for (int i = tid; i < len / 2; i += nt) c += w[la[2 * i + 1]] <= t1;
+    unsigned long long jt;
+    cta_exscan<unsigned long long>((unsigned long long)c, s_scan, jt);
+    const int j = (int)jt;
+    for (int i = tid; i < j; i += nt) {
+      const int a = la[2 * i], b = la[2 * i + 1];
+      w[next + i] = w[a] + w[b];
+      parent[a] = (Id)(next + i);
+      parent[b] = (Id)(next + i);
+    }
+    if (tid == 0) rstart[round] = next;
+    __syncthreads();
+    const int lenR = len - 2 * j;
+    for (int a = tid; a < lenR; a += nt) {
+      const Id id = la[2 * j + a];
+      const unsigned int wa = w[id];
+      int l0 = 0, h0 = j;
+      while (l0 < h0) {
+        const int mid = (l0 + h0) >> 1;
+        if (w[next + mid] < wa) l0 = mid + 1; else h0 = mid;
+      }
+      lb[a + l0] = id;
+    }
+    for (int bi = tid; bi < j; bi += nt) {
+      const unsigned int wb = w[next + bi];
+      int l0 = 0, h0 = lenR;
+      while (l0 < h0) {
+        const int mid = (l0 + h0) >> 1;
+        if (w[la[2 * j + mid]] <= wb) l0 = mid + 1; else h0 = mid;
+      }
+      lb[bi + l0] = (Id)(next + bi);
+    }
+    __syncthreads();
+    Id* tmp = la; la = lb; lb = tmp;
+    len = lenR + j;
+    next += j;
+    ++round;
+  }
+  return round;
+}
+
+// Depth of every leaf; counts per depth into s_bits.
+template <typename Id>
+__device__ void huff_depths(const Id* parent, Id* depth, const int* rstart, int n, int rounds, int* s_bits) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int next = 2 * n - 1, root = next - 1;
+  if (tid == 0) depth[root] = 0;
+  __syncthreads();
+  for (int r = rounds - 1; r >= 0; --r) {
+    const int a = rstart[r], b = (r + 1 < rounds) ? rstart[r + 1] : next;
+    for (int id = a + tid; id < b; id += nt)
+      if (id != root) depth[id] = (Id)(depth[parent[id]] + 1);
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += nt) {
+    const int d = (int)depth[parent[i]] + 1;
+    atomicAdd(&s_bits[d < 127 ? d : 127], 1);
+  }
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(kCbThreads) k_codebook(const unsigned long long* __restrict__ hist, int m,
@@ -42,39 +163,42 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const unsigned long lon
   extern __shared__ __align__(16) unsigned char arena[];
   __shared__ unsigned long long s_scan[32];
   __shared__ int s_bits[128];
-  __shared__ unsigned int s_first[32], s_offs[32], s_lstart[32];
+  __shared__ unsigned int s_first[32], s_offs[32], s_lstart[32], s_tot[256];
   __shared__ int s_u[4];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nsym = 1 << m;
   if (st->err) return;
   for (int i = tid; i < nsym; i += nt) { lens[i] = 0; cw[i] = 0; }
-  // compaction: used symbols in symbol order
+  // compaction: used symbols in symbol order, with their counts
   const int per = (nsym + nt - 1) / nt;
   const int lo = min(nsym, tid * per), hi = min(nsym, lo + per);
-  unsigned long long cnt = 0;
-  for (int s = lo; s < hi; ++s) cnt += hist[s] > 0;
+  unsigned long long cnt = 0, mx = 0;
+  for (int s = lo; s < hi; ++s) { cnt += hist[s] > 0; mx = max(mx, hist[s]); }
   unsigned long long tot;
-  unsigned long long pre = cta_exscan<unsigned long long>(cnt, s_scan, tot);
+  const unsigned long long pre = cta_exscan<unsigned long long>(cnt, s_scan, tot);
   const int n = (int)tot;
-  // node arrays: shared memory for small alphabets, workspace otherwise
-  const bool small = n <= kCbSmemN;
-  unsigned long long* key = small ? reinterpret_cast<unsigned long long*>(arena) : hs.key;
-  unsigned long long* w = small ? key + kCbSmemN : hs.w;
-  int* parent = small ? reinterpret_cast<int*>(w + 2 * kCbSmemN) : hs.parent;
-  int* la = small ? parent + 2 * kCbSmemN : hs.la;
-  int* lb = small ? la + kCbSmemN : hs.lb;
-  int* depth = la;  // reuses la/lb (2n ints) once the rounds are done
-  int* rstart = hs.rstart;
+  unsigned int* k0 = reinterpret_cast<unsigned int*>(hs.key);
+  unsigned int* k1 = k0 + nsym;
+  uint16_t* v0 = reinterpret_cast<uint16_t*>(hs.symord);
+  uint16_t* v1 = v0 + nsym;
   {
     int p = (int)pre;
     for (int s = lo; s < hi; ++s) {
       const unsigned long long h = hist[s];
-      if (h > 0) {
-        hs.symord[p] = (unsigned int)s;
-        key[p] = (h << 16) | (unsigned long long)s;
-        ++p;
-      }
+      if (h > 0) { k0[p] = (unsigned int)h; v0[p] = (uint16_t)s; ++p; }
     }
+  }
+  // largest count -> number of radix passes
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+  if ((tid & 31) == 0) s_scan[tid >> 5] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long m2 = 0;
+    for (int i = 0; i < 32; ++i) m2 = max(m2, s_scan[i]);
+    int np = 0;
+    while (np < 4 && (m2 >> (8 * np)) != 0) ++np;
+    s_u[1] = np;
   }
   const unsigned long long off_bb = al16(off_cb + 4ull * (unsigned long long)n);
   const unsigned long long off_bn = al16(off_bb + 4ull * nblocks);
@@ -89,7 +213,7 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const unsigned long lon
   if (st->err) return;
   if (n <= 1) {
     if (n == 1 && tid == 0) {
-      const unsigned int s = hs.symord[0];
+      const unsigned int s = v0[0];
       lens[s] = 1;
       cw[s] = 0;
       st_u32(out + off_cb, s | (1u << 16));
@@ -97,73 +221,31 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const unsigned long lon
     for (unsigned long long i = off_cb + 4ull * n + tid; i < off_bb; i += nt) out[i] = 0;
     return;
   }
-  int np = 1;
-  while (np < n) np <<= 1;
-  for (int i = n + tid; i < np; i += nt) key[i] = ~0ull;
-  __syncthreads();
-  cta_bitonic(key, np);
-  // leaves: sorted by (freq, symbol)
-  for (int i = tid; i < n; i += nt) { w[i] = key[i] >> 16; la[i] = i; }
-  __syncthreads();
-  int len = n, next = n, round = 0;
-  while (len > 1) {
-    const unsigned long long t1 = w[la[0]] + w[la[1]];
-    int c = 0;
-    for (int i = tid; i < len / 2; i += nt) c += w[la[2 * i + 1]] <= t1;
-    unsigned long long jt;
-    cta_exscan<unsigned long long>((unsigned long long)c, s_scan, jt);
-    const int j = (int)jt;
-    for (int i = tid; i < j; i += nt) {
-      const int a = la[2 * i], b = la[2 * i + 1];
-      w[next + i] = w[a] + w[b];
-      parent[a] = next + i;
-      parent[b] = next + i;
-    }
-    if (tid == 0) rstart[round] = next;
-    __syncthreads();
-    const int lenR = len - 2 * j;
-    for (int a = tid; a < lenR; a += nt) {
-      const int id = la[2 * j + a];
-      const unsigned long long wa = w[id];
-      int l0 = 0, h0 = j;
-      while (l0 < h0) {
-        const int mid = (l0 + h0) >> 1;
-        if (w[next + mid] < wa) l0 = mid + 1; else h0 = mid;
-      }
-      lb[a + l0] = id;
-    }
-    for (int bi = tid; bi < j; bi += nt) {
-      const unsigned long long wb = w[next + bi];
-      int l0 = 0, h0 = lenR;
-      while (l0 < h0) {
-        const int mid = (l0 + h0) >> 1;
-        if (w[la[2 * j + mid]] <= wb) l0 = mid + 1; else h0 = mid;
-      }
-      lb[bi + l0] = next + bi;
-    }
-    __syncthreads();
-    int* tmp = la; la = lb; lb = tmp;
-    len = lenR + j;
-    next += j;
-    ++round;
-  }
-  // depth: the root is the single node of the last round; parents come later
-  const int root = next - 1;
-  depth = small ? parent + 2 * kCbSmemN : hs.depth;  // shared: the la/lb region, 2 * kCbSmemN ints
-  if (tid == 0) depth[root] = 0;
+  // leaves sorted by (count, symbol): stable sort by count of the symbol-ordered list
+  unsigned int* ks;
+  uint16_t* vs;
+  cta_radix_sort(k0, v0, k1, v1, n, s_u[1], reinterpret_cast<unsigned int*>(arena), s_tot, s_scan, ks, vs);
   for (int i = tid; i < 128; i += nt) s_bits[i] = 0;
-  __syncthreads();
-  for (int r = round - 1; r >= 0; --r) {
-    const int a = rstart[r], b = (r + 1 < round) ? rstart[r + 1] : next;
-    for (int id = a + tid; id < b; id += nt)
-      if (id != root) depth[id] = depth[parent[id]] + 1;
+  int rounds;
+  if (n <= kCbSmemN) {
+    unsigned int* w = reinterpret_cast<unsigned int*>(arena);
+    uint16_t* parent = reinterpret_cast<uint16_t*>(w + 2 * kCbSmemN);
+    uint16_t* la = parent + 2 * kCbSmemN;
+    uint16_t* lb = la + kCbSmemN;
+    for (int i = tid; i < n; i += nt) w[i] = ks[i];
     __syncthreads();
+    rounds = huff_rounds<uint16_t>(w, parent, la, lb, hs.rstart, n, s_scan);
+    huff_depths<uint16_t>(parent, la, hs.rstart, n, rounds, s_bits);
+  } else {
+    unsigned int* w = reinterpret_cast<unsigned int*>(hs.w);
+    for (int i = tid; i < n; i += nt) w[i] = ks[i];
+    __syncthreads();
+    rounds = huff_rounds<unsigned int>(w, reinterpret_cast<unsigned int*>(hs.parent),
+                                       reinterpret_cast<unsigned int*>(hs.la), reinterpret_cast<unsigned int*>(hs.lb),
+                                       hs.rstart, n, s_scan);
+    huff_depths<unsigned int>(reinterpret_cast<unsigned int*>(hs.parent), reinterpret_cast<unsigned int*>(hs.depth),
+                              hs.rstart, n, rounds, s_bits);
   }
-  for (int i = tid; i < n; i += nt) {
-    const int d = depth[parent[i]] + 1;
-    atomicAdd(&s_bits[d < 127 ? d : 127], 1);
-  }
-  __syncthreads();
   if (tid == 0) {
     int maxlen = 0;
     for (int l = 1; l < 128; ++l)
@@ -185,49 +267,37 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const unsigned long lon
     unsigned int cum = 0;
     for (int l = maxlen; l >= 1; --l) { s_lstart[l] = cum; cum += (unsigned int)s_bits[l]; }
     unsigned int code = 0, off = 0;
-    s_first[0] = 0;
-    s_offs[0] = 0;
     for (int l = 1; l <= kLmax; ++l) {
-      code = (code + (unsigned int)(l > 1 ? s_bits[l - 1] : 0)) << 1;
+      const unsigned int prevc = l > 1 ? (unsigned int)s_bits[l - 1] : 0u;
+      code = (code + prevc) << 1;
+      off += prevc;
       s_first[l] = code;
-      off += (unsigned int)(l > 1 ? s_bits[l - 1] : 0);
       s_offs[l] = off;
     }
   }
   __syncthreads();
   const int maxlen = s_u[0];
-  // lengths by rank; second sort key (length, symbol) goes into w
-  unsigned long long* key2 = w;
-  for (int i = tid; i < np; i += nt) {
-    if (i < n) {
-      int l = maxlen;
-      while (l > 1 && !((unsigned int)i >= s_lstart[l] && (unsigned int)i < s_lstart[l] + (unsigned int)s_bits[l])) --l;
-      const unsigned int sym = (unsigned int)(key[i] & 0xFFFFull);
-      lens[sym] = (uint8_t)l;
-      key2[i] = ((unsigned long long)l << 16) | sym;
-    } else {
-      key2[i] = ~0ull;
-    }
-  }
-  __syncthreads();
-  cta_bitonic(key2, np);
-  for (int p = tid; p < n; p += nt) {
-    const unsigned int l = (unsigned int)(key2[p] >> 16), sym = (unsigned int)(key2[p] & 0xFFFFull);
-    cw[sym] = s_first[l] + ((unsigned int)p - s_offs[l]);
-  }
-  __syncthreads();
-  for (int p = tid; p < n; p += nt) {
-    const unsigned int sym = hs.symord[p];
-    st_u32(out + off_cb + 4ull * p, sym | ((unsigned int)lens[sym] << 16));
+  // canonical order: most frequent first (the sorted leaf list reversed);
+  // lengths by rank (leaf 0, the lightest, gets the longest length)
+  for (int i = tid; i < n; i += nt) {
+    const int leaf = n - 1 - i;
+    int l = maxlen;
+    while (l > 1 && !((unsigned int)leaf >= s_lstart[l] && (unsigned int)leaf < s_lstart[l] + (unsigned int)s_bits[l]))
+      --l;
+    const unsigned int sym = vs[leaf];
+    lens[sym] = (uint8_t)l;
+    cw[sym] = s_first[l] + ((unsigned int)i - s_offs[l]);
+    st_u32(out + off_cb + 4ull * i, sym | ((unsigned int)l << 16));
   }
   for (unsigned long long i = off_cb + 4ull * n + tid; i < off_bb; i += nt) out[i] = 0;
 }
 
 int launch_codebook(const unsigned long long* hist, int m, uint8_t* lens, uint32_t* cw, State* st,
                     const HuffScratch& hs, uint8_t* out, const Geo& g, const HdrInfo& hi, cudaStream_t s) {
-  const size_t smem = (size_t)kCbSmemN * 8 * 3 + (size_t)kCbSmemN * 4 * 4;  // key, w (2x), parent (2x), la, lb
+  const size_t smem = kCbSmem;
   if (cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return PC_ERR_CUDA;
+  ProfScope p(kStCodebook, s);
   k_codebook<<<1, kCbThreads, smem, s>>>(hist, m, lens, cw, st, hs, out, (unsigned long long)g.nblocks, hi.off_cb,
                                          hi.cap);
   return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;

@@ -1,6 +1,7 @@
 // Compression kernels: statistics (a1), constants (a2), and the fused
 // transform / predict / select / quantize / histogram pass (a4-a9).
 #include "pc_kernels.cuh"
+#include "pc_profile.cuh"
 
 namespace pc {
 
@@ -43,16 +44,31 @@ __global__ void __launch_bounds__(256) k_stats(const T* __restrict__ x, unsigned
   using B = Bits<T>;
   unsigned long long mn = ~0ull, mx = 0ull;
   unsigned int bad = 0, have = 0;
-  unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    auto a = B::mag(__ldg(&x[i]));
+  auto acc = [&](T v) {
+    const auto a = B::mag(v);
     bad |= (a >= B::kInf);
     if (a >= B::kMinNormal && a < B::kInf) {
       have = 1;
       mn = min(mn, (unsigned long long)a);
     }
     mx = max(mx, (unsigned long long)a);
+  };
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long tid0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  // 16-byte vector loads over the aligned body, scalar loads for the tail
+  constexpr int V = 16 / sizeof(T);
+  const bool aligned = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
+  const unsigned long long nv = aligned ? n / V : 0;
+  const uint4* xv = reinterpret_cast<const uint4*>(x);
+#pragma unroll 4
+  for (unsigned long long i = tid0; i < nv; i += stride) {
+    const uint4 u = __ldg(&xv[i]);
+    T t[V];
+    memcpy(t, &u, 16);
+#pragma unroll
+    for (int q = 0; q < V; ++q) acc(t[q]);
   }
+  for (unsigned long long i = nv * V + tid0; i < n; i += stride) acc(__ldg(&x[i]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     mn = min(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
@@ -88,33 +104,53 @@ __global__ void __launch_bounds__(256) k_stats(const T* __restrict__ x, unsigned
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_consts(State* st, double eb) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  // four independent logarithms on four threads, combined by thread 0
+  __shared__ double s_l[4];
+  __shared__ double s_ab[2];
+  __shared__ int s_stop;
   State& c = *st;
   constexpr bool f32 = sizeof(T) == 4;
-  if (c.nonfinite) { c.err = PC_ERR_NONFINITE; return; }
-  double amin, amax;
-  if (c.have_normal) {
-    if (f32) {
-      amin = (double)__uint_as_float((unsigned int)c.amin_bits);
-      amax = (double)__uint_as_float((unsigned int)c.amax_bits);
-    } else {
-      amin = __longlong_as_double((long long)c.amin_bits);
-      amax = __longlong_as_double((long long)c.amax_bits);
-    }
-    c.trivial = 0;
-  } else {
-    amin = 1.0; amax = 1.0; c.trivial = 1;
-  }
-  c.amin = amin;
-  c.amax = amax;
   const double e0 = f32 ? 0x1p-149 : 0x1p-1074;
+  const int t = threadIdx.x;
+  if (t == 0) {
+    s_stop = 0;
+    if (c.nonfinite) {
+      c.err = PC_ERR_NONFINITE;
+      s_stop = 1;
+    }
+    double amin, amax;
+    if (c.have_normal) {
+      if (f32) {
+        amin = (double)__uint_as_float((unsigned int)c.amin_bits);
+        amax = (double)__uint_as_float((unsigned int)c.amax_bits);
+      } else {
+        amin = __longlong_as_double((long long)c.amin_bits);
+        amax = __longlong_as_double((long long)c.amax_bits);
+      }
+      c.trivial = 0;
+    } else {
+      amin = 1.0; amax = 1.0; c.trivial = 1;
+    }
+    c.amin = amin;
+    c.amax = amax;
+    s_ab[0] = amin;
+    s_ab[1] = amax;
+  }
+  __syncthreads();
+  if (s_stop) return;
+  if (t < 4) {
+    const double amin = s_ab[0], amax = s_ab[1];
+    const double arg = t == 0 ? __dadd_rn(1.0, eb) : (t == 1 ? __dadd_rn(amax, e0) : (t == 2 ? amin : __dsub_rn(amin, e0)));
+    s_l[t] = dev_log2d(arg);
+  }
+  __syncthreads();
+  if (t != 0) return;
   const double le0 = f32 ? -149.0 : -1074.0;
-  double ba = dev_log2d(__dadd_rn(1.0, eb));
-  double step = __dadd_rn(ba, ba);
-  double lmax = dev_log2d(__dadd_rn(amax, e0));
-  double lmin = dev_log2d(amin);
+  const double ba = s_l[0];
+  const double step = __dadd_rn(ba, ba);
+  const double lmax = s_l[1], lmin = s_l[2];
   double kp = rint(__ddiv_rn(lmin, step));
-  double lfn = __dsub_rn(__dadd_rn(__dadd_rn(lmax, lmin), step), dev_log2d(__dsub_rn(amin, e0)));
+  double lfn = __dsub_rn(__dadd_rn(__dadd_rn(lmax, lmin), step), s_l[3]);
   double kn = rint(__ddiv_rn(lfn, step));
   double zq = __dadd_rn(rint(__ddiv_rn(le0, step)), kp);
   double s = __dadd_rn(rint(__ddiv_rn(lmax, step)), kp);
@@ -340,9 +376,9 @@ size_t compress_smem(int mode) {
 template <typename T>
 int launch_stats_consts(const void* x, unsigned long long n, State* st, unsigned long long* hist, int nsym,
                         double eb, int nsm, cudaStream_t s) {
-  k_init<<<64, 256, 0, s>>>(st, hist, nsym);
-  k_stats<T><<<nsm * 8, 256, 0, s>>>(static_cast<const T*>(x), n, st);
-  k_consts<T><<<1, 32, 0, s>>>(st, eb);
+  { ProfScope p(kStInit, s); k_init<<<64, 256, 0, s>>>(st, hist, nsym); }
+  { ProfScope p(kStStats, s); k_stats<T><<<nsm * 8, 256, 0, s>>>(static_cast<const T*>(x), n, st); }
+  { ProfScope p(kStConsts, s); k_consts<T><<<1, 32, 0, s>>>(st, eb); }
   return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
 template int launch_stats_consts<float>(const void*, unsigned long long, State*, unsigned long long*, int, double,
@@ -366,7 +402,10 @@ static int launch_c(const void* x, const Geo& g, const State* st, uint16_t* code
   long long grid = (long long)nsm * per_sm;
   if (grid > nbricks) grid = nbricks;
   if (grid < 1) grid = 1;
-  kern<<<(unsigned int)grid, 256, sm, s>>>(static_cast<const T*>(x), g, st, codes, nnflag, nout, hist, m, mlp);
+  {
+    ProfScope p(kStCompress, s);
+    kern<<<(unsigned int)grid, 256, sm, s>>>(static_cast<const T*>(x), g, st, codes, nnflag, nout, hist, m, mlp);
+  }
   return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
 

@@ -10,60 +10,45 @@
 // writes the brick with coalesced stores.  A damaged stream sets the error
 // word and never leads to an out-of-bounds access.
 #include "pc_kernels.cuh"
+#include "pc_profile.cuh"
 
 namespace pc {
 
 constexpr int kLutBits = 12;
 
-__device__ void cta_bitonic_d(unsigned long long* a, int np) {
-  for (int k = 2; k <= np; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < np; i += blockDim.x) {
-        const int ixj = i ^ j;
-        if (ixj > i) {
-          const unsigned long long x = a[i], y = a[ixj];
-          const bool up = (i & k) == 0;
-          if ((x > y) == up) { a[i] = y; a[ixj] = x; }
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
+// The stored list is the code order (lengths never decrease along it), so the
+// decoder tables follow from one pass: the symbol at list position p has code
+// first[len] + (p - offset[len]).
 __global__ void __launch_bounds__(1024) k_dec_tables(const uint8_t* __restrict__ in, DecInfo di, DecScratch ds) {
   __shared__ unsigned int s_cnt[32];
+  __shared__ unsigned int s_seen[2048];  // one bit per symbol (m <= 16)
   __shared__ int s_bad;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nsym = 1 << di.m;
   const int n = (int)di.n_used;
   if (tid < 32) s_cnt[tid] = 0;
   if (tid == 0) s_bad = 0;
+  for (int i = tid; i < 2048; i += nt) s_seen[i] = 0u;
   for (int i = tid; i < nsym; i += nt) ds.lens[i] = 0;
   for (int i = tid; i < (1 << kLutBits); i += nt) ds.lut[i] = 0;
   __syncthreads();
-  int np = 1;
-  while (np < n) np <<= 1;
-  for (int p = tid; p < np; p += nt) {
-    if (p < n) {
-      const unsigned int e = *reinterpret_cast<const unsigned int*>(in + di.off_cb + 4ull * p);
-      const unsigned int sym = e & 0xFFFFu, len = e >> 16;
-      bool bad = sym >= (unsigned int)nsym || len < 1 || len > (unsigned int)kLmax;
-      if (p > 0) {
-        const unsigned int prev = (*reinterpret_cast<const unsigned int*>(in + di.off_cb + 4ull * (p - 1))) & 0xFFFFu;
-        bad |= sym <= prev;
-      }
-      if (bad) { s_bad = 1; ds.key[p] = ~0ull; continue; }
-      ds.lens[sym] = (uint8_t)len;
-      ds.key[p] = ((unsigned long long)len << 16) | sym;
-      atomicAdd(&s_cnt[len], 1u);
-    } else {
-      ds.key[p] = ~0ull;
+  const unsigned int* ent = reinterpret_cast<const unsigned int*>(in + di.off_cb);
+  for (int p = tid; p < n; p += nt) {
+    const unsigned int e = ent[p];
+    const unsigned int sym = e & 0xFFFFu, len = e >> 16;
+    bool bad = sym >= (unsigned int)nsym || len < 1 || len > (unsigned int)kLmax;
+    if (p > 0) bad |= len < (ent[p - 1] >> 16);
+    if (!bad) {
+      const unsigned int bit = 1u << (sym & 31u);
+      bad |= (atomicOr(&s_seen[sym >> 5], bit) & bit) != 0u;
     }
+    if (bad) { s_bad = 1; continue; }
+    ds.lens[sym] = (uint8_t)len;
+    ds.sorted[p] = (uint16_t)sym;
+    atomicAdd(&s_cnt[len], 1u);
   }
   __syncthreads();
   if (s_bad) { if (tid == 0) atomicExch(ds.err, PC_ERR_CORRUPT); return; }
-  cta_bitonic_d(ds.key, np);
   if (tid == 0) {
     unsigned int code = 0, off = 0;
     bool bad = false;
@@ -73,15 +58,15 @@ __global__ void __launch_bounds__(1024) k_dec_tables(const uint8_t* __restrict__
       off += prevc;
       ds.tabs[l] = code;            // first code of length l
       ds.tabs[32 + l] = s_cnt[l];   // count
-      ds.tabs[64 + l] = off;        // offset into the sorted list
+      ds.tabs[64 + l] = off;        // list position of the first code of length l
       if (s_cnt[l] && (unsigned long long)code + s_cnt[l] > (1ull << l)) bad = true;
     }
     if (bad) atomicExch(ds.err, PC_ERR_CORRUPT);
   }
   __syncthreads();
   for (int p = tid; p < n; p += nt) {
-    const unsigned int l = (unsigned int)(ds.key[p] >> 16), sym = (unsigned int)(ds.key[p] & 0xFFFFull);
-    ds.sorted[p] = (uint16_t)sym;
+    const unsigned int e = ent[p];
+    const unsigned int l = e >> 16, sym = e & 0xFFFFu;
     if (l <= (unsigned int)kLutBits) {
       const unsigned int code = ds.tabs[l] + ((unsigned int)p - ds.tabs[64 + l]);
       const unsigned int lo = code << (kLutBits - l), hi = (code + 1) << (kLutBits - l);
@@ -183,14 +168,24 @@ __global__ void __launch_bounds__(256) k_dec_blockoff(Geo g, const uint8_t* __re
 }
 
 // One thread per block: canonical Huffman decode into block-strided codes.
+// Codes of up to 12 bits resolve in one shared-memory table lookup; longer
+// ones by comparing the 24-bit window against each length's code range.
+// Eight decoded codes are packed and written with one 16-byte store.
+constexpr int kSortedSmem = 16384;
+
 __global__ void __launch_bounds__(128) k_huff_decode(Geo g, const uint8_t* __restrict__ in, DecInfo di,
                                                      DecScratch ds) {
   __shared__ unsigned int s_lut[1 << kLutBits];
   __shared__ unsigned int s_tab[96];
+  extern __shared__ uint16_t s_sorted[];
+  const bool small = di.n_used <= (unsigned int)kSortedSmem;
   for (int i = threadIdx.x; i < (1 << kLutBits); i += blockDim.x) s_lut[i] = ds.lut[i];
   for (int i = threadIdx.x; i < 96; i += blockDim.x) s_tab[i] = ds.tabs[i];
+  if (small)
+    for (int i = threadIdx.x; i < (int)di.n_used; i += blockDim.x) s_sorted[i] = ds.sorted[i];
   __syncthreads();
   if (*ds.err) return;
+  const uint16_t* sorted = small ? s_sorted : ds.sorted;
   const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= g.nblocks) return;
   long long bz, by, bx;
@@ -203,60 +198,70 @@ __global__ void __launch_bounds__(128) k_huff_decode(Geo g, const uint8_t* __res
   unsigned long long wpos = start >> 5;
   unsigned long long buf = 0;
   int nb = 0;
-  // fill: keep at least 33 valid bits, MSB-aligned in buf
-  auto refill = [&]() {
-    while (nb <= 32) {
-      const unsigned int wv = wpos < di.swords ? __ldg(&stream[wpos]) : 0u;
-      ++wpos;
-      buf |= (unsigned long long)wv << (32 - nb);
-      nb += 32;
-    }
-  };
-  refill();
+  while (nb <= 32) {
+    const unsigned int wv = wpos < di.swords ? __ldg(&stream[wpos]) : 0u;
+    ++wpos;
+    buf |= (unsigned long long)wv << (32 - nb);
+    nb += 32;
+  }
   {
     const int skip = (int)(start & 31ull);
     buf <<= skip;
     nb -= skip;
   }
+  // left-justified end of the code range of each length 13..24
+  unsigned int lim[kLmax - kLutBits];
+#pragma unroll
+  for (int q = 0; q < kLmax - kLutBits; ++q) {
+    const int l = kLutBits + 1 + q;
+    lim[q] = (s_tab[l] + s_tab[32 + l]) << (kLmax - l);
+  }
   unsigned int used = 0;
   bool bad = false;
-  uint16_t* out = ds.codes + b * g.bvol;
+  uint4* out = reinterpret_cast<uint4*>(ds.codes + b * g.bvol);
   const int b12 = g.b[1] * g.b[2];
-  const int m = di.m;
-  for (int j = 0; j < g.bvol; ++j) {
-    bool valid = j != 0;
-    if (!full && valid) {
-      const int lz = j / b12, r = j - lz * b12, ly = r / g.b[2], lx = r - ly * g.b[2];
-      valid = lz < e0 && ly < e1 && lx < e2;
-    }
-    unsigned int sym = 0;
-    if (valid && !bad) {
-      refill();
-      const unsigned int peek = (unsigned int)(buf >> 40);  // 24 bits
-      const unsigned int e = s_lut[peek >> (kLmax - kLutBits)];
-      unsigned int len = e & 0xFFu;
-      if (len) {
-        sym = e >> 8;
-      } else {
-        len = 0;
-        for (int l = kLutBits + 1; l <= kLmax; ++l) {
-          const unsigned int code = peek >> (kLmax - l);
-          const unsigned int d = code - s_tab[l];
-          if (s_tab[32 + l] && d < s_tab[32 + l]) {
-            sym = ds.sorted[s_tab[64 + l] + d];
-            len = (unsigned int)l;
-            break;
-          }
-        }
-        if (!len) bad = true;
+  const unsigned int nsym = 1u << di.m;
+  for (int j0 = 0; j0 < g.bvol; j0 += 8) {
+    unsigned int pk[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int j = j0 + q;
+      bool valid = j != 0;
+      if (!full && valid) {
+        const int lz = j / b12, r = j - lz * b12, ly = r / g.b[2], lx = r - ly * g.b[2];
+        valid = lz < e0 && ly < e1 && lx < e2;
       }
-      used += len;
-      if (used > nbits) bad = true;
-      buf <<= len;
-      nb -= (int)len;
-      if (sym >= (1u << m)) bad = true;
+      if (valid && !bad) {
+        if (nb <= 32) {
+          const unsigned int wv = wpos < di.swords ? __ldg(&stream[wpos]) : 0u;
+          ++wpos;
+          buf |= (unsigned long long)wv << (32 - nb);
+          nb += 32;
+        }
+        const unsigned int peek = (unsigned int)(buf >> 40);  // next 24 bits
+        const unsigned int e = s_lut[peek >> (kLmax - kLutBits)];
+        unsigned int len = e & 0xFFu, sym = e >> 8;
+        if (!len) {
+          // canonical code ranges tile the 24-bit window space in order of
+          // length: the length is 13 plus the number of longer-code limits
+          // the window has reached
+          unsigned int l = kLutBits + 1;
+#pragma unroll
+          for (int q = 0; q < kLmax - kLutBits - 1; ++q) l += peek >= lim[q];
+          if (peek >= lim[kLmax - kLutBits - 1]) bad = true;
+          const unsigned int d = (peek >> (kLmax - l)) - s_tab[l];
+          if (d >= s_tab[32 + l]) bad = true;
+          sym = bad ? 0u : sorted[s_tab[64 + l] + d];
+          len = l;
+        }
+        used += len;
+        if (used > nbits || sym >= nsym) bad = true;
+        buf <<= len;
+        nb -= (int)len;
+        if (!bad) pk[q >> 1] |= sym << (16 * (q & 1));
+      }
     }
-    out[j] = (uint16_t)(bad ? 0 : sym);
+    out[j0 >> 3] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
   }
   if (bad || used != nbits) atomicExch(ds.err, PC_ERR_CORRUPT);
 }
@@ -505,7 +510,7 @@ static int launch_r(const uint8_t* in, const Geo& g, const DecInfo& di, const De
   long long grid = (long long)nsm * per_sm;
   if (grid > nbricks) grid = nbricks;
   if (grid < 1) grid = 1;
-  kern<<<(unsigned int)grid, 256, sm, s>>>(g, in, di, ds, out, mlp);
+  { ProfScope p(kStRecon, s); kern<<<(unsigned int)grid, 256, sm, s>>>(g, in, di, ds, out, mlp); }
   return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
 
@@ -523,12 +528,16 @@ static int launch_r_shape(const uint8_t* in, const Geo& g, const DecInfo& di, co
 template <typename T>
 int launch_decompress(const uint8_t* in, const Geo& g, const DecInfo& di, const DecScratch& ds, const Mlp& mlp,
                       T* out, int nsm, cudaStream_t s) {
-  k_dec_tables<<<1, 1024, 0, s>>>(in, di, ds);
+  { ProfScope p(kStDecTables, s); k_dec_tables<<<1, 1024, 0, s>>>(in, di, ds); }
   const unsigned int nc = (unsigned int)g.nchunks;
-  k_dec_chunksum<<<nc, 256, 0, s>>>(g, in, di, ds);
-  k_dec_chunkscan<<<1, 1024, 0, s>>>(g, di, ds);
-  k_dec_blockoff<<<nc, 256, 0, s>>>(g, in, di, ds);
-  k_huff_decode<<<(unsigned int)((g.nblocks + 127) / 128), 128, 0, s>>>(g, in, di, ds);
+  {
+    ProfScope p(kStDecScan, s);
+    k_dec_chunksum<<<nc, 256, 0, s>>>(g, in, di, ds);
+    k_dec_chunkscan<<<1, 1024, 0, s>>>(g, di, ds);
+    k_dec_blockoff<<<nc, 256, 0, s>>>(g, in, di, ds);
+  }
+  const size_t sm_sorted = di.n_used <= (unsigned int)kSortedSmem ? 2ull * di.n_used : 0ull;
+  { ProfScope p(kStHuffDecode, s); k_huff_decode<<<(unsigned int)((g.nblocks + 127) / 128), 128, sm_sorted, s>>>(g, in, di, ds); }
   if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
   const int b0 = g.b[0], b1 = g.b[1], b2 = g.b[2];
 #define PC_SHAPE(A, B, C) \

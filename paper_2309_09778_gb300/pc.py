@@ -24,7 +24,8 @@ STATUS = {0: "PC_OK", -1: "PC_ERR_ARG", -2: "PC_ERR_DTYPE", -3: "PC_ERR_NONFINIT
           -5: "PC_ERR_CORRUPT", -6: "PC_ERR_TIMEOUT", -7: "PC_ERR_CUDA", -8: "PC_ERR_EB_RANGE"}
 SYMBOLS = ["pc_mlp_nweights", "pc_compress_bound", "pc_compress_workspace_size", "pc_compress",
            "pc_header_info", "pc_decompress", "pc_compress_host", "pc_decompress_host",
-           "pc_train_workspace_size", "pc_train", "pc_compress_workspace_layout", "pc_strerror"]
+           "pc_train_workspace_size", "pc_train", "pc_compress_workspace_layout", "pc_profile_enable",
+           "pc_profile_read", "pc_profile_stage_name", "pc_strerror"]
 
 
 class PcError(RuntimeError):
@@ -74,6 +75,12 @@ def lib():
                 L.pc_train.restype = C.c_int
                 L.pc_train.argtypes = [vp, szp, C.c_int, P, C.c_ulonglong, C.c_uint, C.c_int, vp, vp, vp,
                                        C.POINTER(C.c_int), C.POINTER(C.c_int), vp, vp, sz, vp]
+            L.pc_profile_enable.restype = C.c_int
+            L.pc_profile_enable.argtypes = [C.c_int]
+            L.pc_profile_read.restype = C.c_int
+            L.pc_profile_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]
+            L.pc_profile_stage_name.restype = C.c_char_p
+            L.pc_profile_stage_name.argtypes = [C.c_int]
             L.pc_strerror.restype = C.c_char_p
             L.pc_strerror.argtypes = [C.c_int]
             _lib = L
@@ -232,6 +239,18 @@ def pc_train(field, params: pc_params, seed: int, thr32: int, lrs, lams, ws, str
                         _stream_ptr(stream))
     _check(st, "pc_train")
     return W, s_in.value, chosen.value, costs
+
+
+def pc_profile_enable(on: bool) -> None:
+    _check(lib().pc_profile_enable(1 if on else 0), "pc_profile_enable")
+
+
+def pc_profile_read() -> dict:
+    """Per-stage device milliseconds and launch counts since the last read."""
+    ms = (C.c_double * 32)()
+    n = (C.c_longlong * 32)()
+    k = lib().pc_profile_read(ms, n, 32)
+    return {lib().pc_profile_stage_name(i).decode(): (ms[i], n[i]) for i in range(k)}
 
 
 def pc_strerror(status: int) -> str:

@@ -92,7 +92,8 @@ def test_bitstream_is_concatenated_codewords(O):
     st, blob, d = O.compress(x, 1e-2, dump=True)
     h = parse(blob)
     lens = d["lens"]
-    codes_cw = O.canonical_codes(lens)
+    cb = np.frombuffer(blob, np.uint32, h["n_used"], h["off"][1])
+    codes_cw = O.canonical_codes(lens, cb & 0xFFFF)
     # expected bit string, written independently of the oracle's packer
     bits = []
     shape, block = x.shape, (8, 8, 8)
@@ -114,10 +115,10 @@ def test_bitstream_is_concatenated_codewords(O):
     got = "".join(format(int(w), "032b") for w in words)
     assert got[: len(allbits)] == allbits
     assert set(got[len(allbits):]) <= {"0"}
-    # codebook section lists (symbol, length) by symbol
-    cb = np.frombuffer(blob, np.uint32, h["n_used"], h["off"][1])
-    assert np.array_equal(cb & 0xFFFF, np.flatnonzero(lens))
-    assert np.array_equal(cb >> 16, lens[lens > 0])
+    # codebook section lists (symbol, length) in code order: most frequent first
+    _, order = O.huffman_lengths(d["hist"], with_order=True)
+    assert np.array_equal(cb & 0xFFFF, order)
+    assert np.array_equal(cb >> 16, lens[order])
     # total size is a multiple of 16 and equals the stored size
     assert len(blob) % 16 == 0 and struct.unpack_from("<Q", blob, 216)[0] == len(blob)
 

@@ -111,11 +111,30 @@ def read_rfc_golden():
 
 
 def test_canonical_rfc1951_example(O):
+    """The ordered construction with RFC 1951's order (length, then symbol)
+    reproduces the RFC's worked example."""
     rows = read_rfc_golden()
     lens = np.array([r[1] for r in rows], np.uint8)
     codes = O.canonical_codes(lens)
     for (sym, ln, code), got in zip(rows, codes.tolist()):
         assert format(got, f"0{ln}b") == code, sym
+
+
+def test_code_order_is_most_frequent_first(O):
+    """The compressor's code order lists symbols by descending frequency
+    (ties: larger symbol first), lengths never decrease along it, and the
+    ordered construction then yields a prefix-free code."""
+    rng = np.random.default_rng(4)
+    hist = np.zeros(512, np.uint64)
+    hist[rng.choice(512, 200, replace=False)] = rng.integers(1, 50, 200)
+    lens, order = O.huffman_lengths(hist, with_order=True)
+    f = hist[order].astype(np.int64)
+    assert np.all((np.diff(f) < 0) | ((np.diff(f) == 0) & (np.diff(order.astype(np.int64)) < 0)))
+    assert np.all(np.diff(lens[order].astype(int)) >= 0)
+    codes = O.canonical_codes(lens, order)
+    words = sorted(format(int(codes[s]), f"0{int(lens[s])}b") for s in order)
+    for a, b in zip(words, words[1:]):
+        assert not b.startswith(a)
 
 
 def test_canonical_prefix_free(O):
