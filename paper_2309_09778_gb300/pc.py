@@ -23,7 +23,7 @@ PC_PRED_LORENZO, PC_PRED_MLP_FP32 = 0, 1
 STATUS = {0: "PC_OK", -1: "PC_ERR_ARG", -2: "PC_ERR_DTYPE", -3: "PC_ERR_NONFINITE", -4: "PC_ERR_CAPACITY",
           -5: "PC_ERR_CORRUPT", -6: "PC_ERR_TIMEOUT", -7: "PC_ERR_CUDA", -8: "PC_ERR_EB_RANGE"}
 SYMBOLS = ["pc_mlp_nweights", "pc_compress_bound", "pc_compress_workspace_size", "pc_compress",
-           "pc_header_info", "pc_decompress", "pc_compress_host", "pc_decompress_host",
+           "pc_header_info", "pc_decompress", "pc_decompress_noalloc", "pc_compress_host", "pc_decompress_host",
            "pc_train_workspace_size", "pc_train", "pc_compress_workspace_layout", "pc_profile_enable",
            "pc_profile_read", "pc_profile_stage_name", "pc_strerror"]
 
@@ -65,6 +65,8 @@ def lib():
             L.pc_header_info.argtypes = [vp, sz, szp, C.POINTER(C.c_int), szp]
             L.pc_decompress.restype = C.c_int
             L.pc_decompress.argtypes = [vp, sz, vp, sz, szp, C.POINTER(C.c_int), vp, sz, vp]
+            L.pc_decompress_noalloc.restype = C.c_int
+            L.pc_decompress_noalloc.argtypes = [vp, sz, vp, sz, szp, C.POINTER(C.c_int), vp]
             L.pc_compress_host.restype = C.c_int
             L.pc_compress_host.argtypes = [vp, szp, C.c_int, P, vp, sz, szp, vp, vp, sz, vp, sz, vp]
             L.pc_decompress_host.restype = C.c_int
@@ -189,6 +191,16 @@ def pc_decompress(blob, in_size: int, out, ws, stream=None):
                              out.numel() * out.element_size(), dims, C.byref(dt), C.c_void_p(ws.data_ptr()),
                              ws.numel(), _stream_ptr(stream))
     _check(st, "pc_decompress")
+    return tuple(dims), dt.value
+
+
+def pc_decompress_noalloc(blob, in_size: int, out, stream=None):
+    """Decompress without a caller workspace (fixed built-in scratch, see include/pc.h)."""
+    dims = (C.c_size_t * 3)()
+    dt = C.c_int()
+    st = lib().pc_decompress_noalloc(C.c_void_p(blob.data_ptr()), int(in_size), C.c_void_p(out.data_ptr()),
+                                     out.numel() * out.element_size(), dims, C.byref(dt), _stream_ptr(stream))
+    _check(st, "pc_decompress_noalloc")
     return tuple(dims), dt.value
 
 
