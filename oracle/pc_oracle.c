@@ -26,15 +26,24 @@
 #include <string.h>
 
 /* ------------------------------------------------------------------------- */
-/* Our own log2 / exp2.  From the mathematics, not from any vendor library:  */
-/*   ln y = 2 atanh(s), s = (y-1)/(y+1), atanh s = sum s^(2j+1)/(2j+1)       */
-/*   2^f  = e^(f ln2)  = sum (f ln2)^i / i!                                  */
-/* Evaluated by Horner's rule with explicit fused multiply-adds.             */
+/* Our own log2 / exp2.  From the mathematics, not from any vendor library.  */
+/*                                                                           */
+/* Single precision follows the table-driven method of P. T. P. Tang        */
+/* ("Table-driven implementation of the logarithm function in IEEE           */
+/* floating-point arithmetic", ACM TOMS 16(4), 1990; "... exponential        */
+/* function ...", ACM TOMS 15(2), 1989):                                     */
+/*   log2 y = e + log2 m, m in [1,2) split as m = c_i (1 + r): i = top 7     */
+/*   mantissa bits, c_0 = 1, c_i = 1 + (i + 1/2)/128, RCP_i = (float)(1/c_i) */
+/*   (double division, then rounding), r = fma(m, RCP_i, -1), and             */
+/*   log2 m = LOGR_i + log2(1 + r) with LOGR_i = (float)(-log2 RCP_i) from     */
+/*   our double log2; log2(1 + r) = r (c1 + r (c2 + r (c3 + r c4))),         */
+/*   c_k = (-1)^(k+1) / (k ln 2) rounded to float.                           */
+/*   2^t = 2^k 2^(j/32) 2^f with 32k + j = rint(32 t), |f| <= 1/64;           */
+/*   2^f = 1 + u + u^2/2 + u^3/6 + u^4/24, u = f ln 2; EXP_j = (float)2^(j/32)*/
+/*   from our double exp2.                                                   */
+/* Double precision sums the atanh and Taylor series directly.              */
 /* ------------------------------------------------------------------------- */
 
-static const float O_SQRT2_F = 0x1.6a09e6p+0f;   /* RN_f32(sqrt 2) */
-static const float O_2LN2_F = 0x1.715476p+1f;    /* RN_f32(2 / ln 2) */
-static const float O_LN2_F = 0x1.62e430p-1f;     /* RN_f32(ln 2) */
 static const double O_SQRT2_D = 0x1.6a09e667f3bcdp+0;
 static const double O_2LN2_D = 0x1.71547652b82fep+1;
 static const double O_LN2_D = 0x1.62e42fefa39efp-1;
@@ -44,50 +53,71 @@ static uint32_t bits_of_f(float f) { uint32_t b; memcpy(&b, &f, 4); return b; }
 static double d_from_bits(uint64_t b) { double f; memcpy(&f, &b, 8); return f; }
 static uint64_t bits_of_d(double f) { uint64_t b; memcpy(&b, &f, 8); return b; }
 
+double orc_L64(double y);
+double orc_E64(double t);
+
+static float o_rcp[128], o_logr[128], o_exp[32];
+static float o_lc[4];
+static int o_tab_ready = 0;
+
+static void o_tables(void) {
+  if (o_tab_ready) return;
+  for (int i = 0; i < 128; i++) {
+    double c = i == 0 ? 1.0 : 1.0 + ((double)i + 0.5) / 128.0;
+    o_rcp[i] = (float)(1.0 / c);
+    o_logr[i] = (float)(-orc_L64((double)o_rcp[i]));
+  }
+  for (int j = 0; j < 32; j++) o_exp[j] = (float)orc_E64((double)j / 32.0);
+  double ln2 = O_LN2_D;
+  o_lc[0] = (float)(1.0 / ln2);
+  o_lc[1] = (float)(-1.0 / (2.0 * ln2));
+  o_lc[2] = (float)(1.0 / (3.0 * ln2));
+  o_lc[3] = (float)(-1.0 / (4.0 * ln2));
+  o_tab_ready = 1;
+}
+
 /* log2 of a positive normal float. */
 float orc_L32(float y) {
+  o_tables();
   uint32_t b = bits_of_f(y);
   int e = (int)((b >> 23) & 0xFFu) - 127;
+  int i = (int)((b >> 16) & 0x7Fu);
   float m = f_from_bits((b & 0x7FFFFFu) | 0x3F800000u); /* [1, 2) */
-  if (m > O_SQRT2_F) { m = m * 0.5f; e = e + 1; }
-  float s = (m - 1.0f) / (m + 1.0f);
-  float z = s * s;
-  float p = 1.0f / 9.0f;
-  p = fmaf(p, z, 1.0f / 7.0f);
-  p = fmaf(p, z, 1.0f / 5.0f);
-  p = fmaf(p, z, 1.0f / 3.0f);
-  p = fmaf(p, z, 1.0f);
-  float t = s * p;
-  t = t * O_2LN2_F;
+  float r = fmaf(m, o_rcp[i], -1.0f);
+  float p = fmaf(o_lc[3], r, o_lc[2]);
+  p = fmaf(p, r, o_lc[1]);
+  p = fmaf(p, r, o_lc[0]);
+  p = p * r;
+  float t = o_logr[i] + p;
   return (float)e + t;
 }
 
 /* 2^t for finite t (clamped to [-300, 300]). */
 float orc_E32(float t) {
+  o_tables();
   if (t > 300.0f) t = 300.0f;
   if (t < -300.0f) t = -300.0f;
-  float nf = rintf(t);
-  int k = (int)nf;
-  float f = t - nf;
-  float u = f * O_LN2_F;
-  float p = 1.0f / 5040.0f;
-  p = fmaf(p, u, 1.0f / 720.0f);
-  p = fmaf(p, u, 1.0f / 120.0f);
-  p = fmaf(p, u, 1.0f / 24.0f);
-  p = fmaf(p, u, 1.0f / 6.0f);
-  p = fmaf(p, u, 1.0f / 2.0f);
+  float nf = rintf(t * 32.0f);
+  int N = (int)nf;
+  int j = N & 31;
+  int k = (N - j) / 32;
+  float f = t - nf * 0.03125f;
+  float u = f * 0x1.62e430p-1f;
+  float p = fmaf(1.0f / 24.0f, u, 1.0f / 6.0f);
+  p = fmaf(p, u, 0.5f);
   p = fmaf(p, u, 1.0f);
   p = fmaf(p, u, 1.0f);
+  float v = o_exp[j] * p;
   int k1 = k / 3;
   int k2 = (k - k1) / 2;
   int k3 = k - k1 - k2;
   float s1 = f_from_bits((uint32_t)(k1 + 127) << 23);
   float s2 = f_from_bits((uint32_t)(k2 + 127) << 23);
   float s3 = f_from_bits((uint32_t)(k3 + 127) << 23);
-  return ((p * s1) * s2) * s3;
+  return ((v * s1) * s2) * s3;
 }
 
-/* log2 of a positive double (subnormals are rescaled first). */
+/* log2 of a positive double (subnormals are rescaled first): atanh series. */
 double orc_L64(double y) {
   if (y < 0x1p-1022) return orc_L64(y * 0x1p64) - 64.0;
   uint64_t b = bits_of_d(y);

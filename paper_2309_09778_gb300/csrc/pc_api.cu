@@ -1,4 +1,5 @@
 // C ABI (include/pc.h): argument checks, workspace layout, launch sequence.
+#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -76,7 +77,7 @@ int check_params(const size_t dims[3], int dtype, const pc_params* p, Geo& g, in
 }
 
 struct CompLayout {
-  size_t st, hist, lens, cw, key, w, parent, depth, la, lb, rstart, symord, codes, nnflag, nout, bbits, cbits, cnout,
+  size_t st, tabs, hist, lens, cw, key, w, parent, depth, la, lb, rstart, symord, codes, nnflag, nout, bbits, cbits, cnout,
       cboff, cooff, total;
 };
 
@@ -87,6 +88,7 @@ CompLayout comp_layout(const Geo& g, int m) {
   CompLayout L;
   size_t o = 0;
   L.st = o; o = up(o + sizeof(State));
+  L.tabs = o; o = up(o + sizeof(Tabs));
   L.hist = o; o = up(o + 8 * nsym);
   L.lens = o; o = up(o + nsym);
   L.cw = o; o = up(o + 4 * nsym);
@@ -111,7 +113,7 @@ CompLayout comp_layout(const Geo& g, int m) {
 }
 
 struct DecLayout {
-  size_t err, lens, sorted, lut, tabs, key, cbits, cnout, cboff, cooff, boff, ooff, codes, total;
+  size_t err, ftab, lens, sorted, lut, tabs, key, cbits, cnout, cboff, cooff, boff, ooff, codes, total;
 };
 
 DecLayout dec_layout(const Geo& g, int m) {
@@ -119,6 +121,7 @@ DecLayout dec_layout(const Geo& g, int m) {
   DecLayout L;
   size_t o = 0;
   L.err = o; o = up(o + 16);
+  L.ftab = o; o = up(o + sizeof(Tabs));
   L.lens = o; o = up(o + nsym);
   L.sorted = o; o = up(o + 2 * nsym);
   L.lut = o; o = up(o + 4 * 4096);
@@ -225,9 +228,148 @@ int parse_header(const uint8_t* h, size_t n, Hdr& H, Geo& g) {
   return PC_OK;
 }
 
+struct TrainLayout {
+  size_t st, tabs, hist, cnt_t, cnt_v, off_t, off_v, tin, ttg, tus, vin, vtg, vus, w, lrs, lams, costs, ctl, total;
+  unsigned long long cap_t, cap_v;
+};
+
+bool train_shape_ok(int k, int h1, int h2) {
+  return (k == 7 && h1 == 16 && h2 == 16) || (k == 13 && h1 == 32 && h2 == 32) || (k == 7 && h1 == 8 && h2 == 8) ||
+         (k == 7 && h1 == 2 && h2 == 0) || (k == 13 && h1 == 16 && h2 == 16);
+}
+
+// Sample counts are drawn by a hash, so the buffers hold the expected count
+// plus eight standard deviations (a larger draw is reported, not written).
+TrainLayout train_layout(const Geo& g, int m, int k, int nw, unsigned int thr32, int nmodels) {
+  const double p = (double)thr32 / 4294967296.0;
+  const double n = (double)(g.n[0] * g.n[1] * g.n[2] - g.nblocks);
+  const double mt = n * p * 0.8, mv = n * p * 0.2;
+  TrainLayout L;
+  L.cap_t = (unsigned long long)(mt + 8.0 * sqrt(mt + 1.0) + 256.0);
+  L.cap_v = (unsigned long long)(mv + 8.0 * sqrt(mv + 1.0) + 256.0);
+  const size_t nsym = (size_t)1 << m;
+  size_t o = 0;
+  L.st = o; o = up(o + sizeof(State));
+  L.tabs = o; o = up(o + sizeof(Tabs));
+  L.hist = o; o = up(o + 8 * nsym);
+  L.cnt_t = o; o = up(o + 4 * (size_t)g.nblocks);
+  L.cnt_v = o; o = up(o + 4 * (size_t)g.nblocks);
+  L.off_t = o; o = up(o + 8 * (size_t)g.nblocks);
+  L.off_v = o; o = up(o + 8 * (size_t)g.nblocks);
+  L.tin = o; o = up(o + 4 * (size_t)k * L.cap_t);
+  L.ttg = o; o = up(o + 4 * (size_t)L.cap_t);
+  L.tus = o; o = up(o + (size_t)L.cap_t);
+  L.vin = o; o = up(o + 4 * (size_t)k * L.cap_v);
+  L.vtg = o; o = up(o + 4 * (size_t)L.cap_v);
+  L.vus = o; o = up(o + (size_t)L.cap_v);
+  L.w = o; o = up(o + 4 * (size_t)nw * nmodels);
+  L.lrs = o; o = up(o + 4 * (size_t)nmodels);
+  L.lams = o; o = up(o + 4 * (size_t)nmodels);
+  L.costs = o; o = up(o + 8 * (size_t)(nmodels + 1));
+  L.ctl = o; o = up(o + train_ctl_bytes());
+  L.total = o;
+  return L;
+}
+
+int train_check(const size_t dims[3], int dtype, const pc_params* p, int nmodels, Geo& g, int& nw) {
+  if (!dims || !p) return PC_ERR_ARG;
+  if (dtype != PC_F32 && dtype != PC_F64) return PC_ERR_DTYPE;
+  if (!(p->eb_rel > 0.0 && p->eb_rel < 1.0) || p->m < 2 || p->m > 16) return PC_ERR_ARG;
+  if (!make_geo(dims, p->block, g) || nmodels < 1 || nmodels > 64) return PC_ERR_ARG;
+  if (!train_shape_ok(p->stencil, p->hidden[0], p->hidden[1])) return PC_ERR_ARG;
+  nw = nweights(p->stencil, p->hidden[0], p->hidden[1]);
+  return PC_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int pc_train_workspace_size(const size_t dims[3], int dtype, const pc_params* p, unsigned int thr32, int nmodels,
+                            size_t* ws_bytes) {
+  Geo g;
+  int nw;
+  int st = train_check(dims, dtype, p, nmodels, g, nw);
+  if (st) return st;
+  if (!ws_bytes) return PC_ERR_ARG;
+  *ws_bytes = train_layout(g, p->m, p->stencil, nw, thr32, nmodels).total;
+  return PC_OK;
+}
+
+int pc_train(const void* d_field, const size_t dims[3], int dtype, const pc_params* p, unsigned long long seed,
+             unsigned int thr32, int nmodels, const float* h_lrs, const float* h_lams, float* h_weights_out,
+             int* s_in_out, int* chosen_out, unsigned long long* h_costs, void* d_ws, size_t ws_bytes,
+             void* stream) {
+  Geo g;
+  int nw;
+  int st = train_check(dims, dtype, p, nmodels, g, nw);
+  if (st) return st;
+  if (!d_field || !h_lrs || !h_lams || !h_weights_out || !s_in_out || !chosen_out || !d_ws) return PC_ERR_ARG;
+  TrainLayout L = train_layout(g, p->m, p->stencil, nw, thr32, nmodels);
+  if (ws_bytes < L.total) return PC_ERR_CAPACITY;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int nsm = sm_count();
+  if (nsm <= 0) return PC_ERR_CUDA;
+  uint8_t* ws = static_cast<uint8_t*>(d_ws);
+  State* stp = reinterpret_cast<State*>(ws + L.st);
+  Tabs* tabs = reinterpret_cast<Tabs*>(ws + L.tabs);
+  auto* hist = reinterpret_cast<unsigned long long*>(ws + L.hist);
+  TrainBufs tb;
+  tb.cnt_t = reinterpret_cast<unsigned int*>(ws + L.cnt_t);
+  tb.cnt_v = reinterpret_cast<unsigned int*>(ws + L.cnt_v);
+  tb.off_t = reinterpret_cast<unsigned long long*>(ws + L.off_t);
+  tb.off_v = reinterpret_cast<unsigned long long*>(ws + L.off_v);
+  tb.tin = reinterpret_cast<int*>(ws + L.tin);
+  tb.ttg = reinterpret_cast<int*>(ws + L.ttg);
+  tb.tus = ws + L.tus;
+  tb.vin = reinterpret_cast<int*>(ws + L.vin);
+  tb.vtg = reinterpret_cast<int*>(ws + L.vtg);
+  tb.vus = ws + L.vus;
+  tb.w = reinterpret_cast<float*>(ws + L.w);
+  tb.lrs = reinterpret_cast<const float*>(ws + L.lrs);
+  tb.lams = reinterpret_cast<const float*>(ws + L.lams);
+  tb.costs = reinterpret_cast<unsigned long long*>(ws + L.costs);
+  tb.ctl = ws + L.ctl;
+  tb.cap_t = L.cap_t;
+  tb.cap_v = L.cap_v;
+  if (cudaMemcpyAsync(ws + L.lrs, h_lrs, 4ull * nmodels, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(ws + L.lams, h_lams, 4ull * nmodels, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return PC_ERR_CUDA;
+  const unsigned long long n = (unsigned long long)dims[0] * dims[1] * dims[2];
+  const int nsym = 1 << p->m;
+  int r;
+  if (dtype == PC_F32) {
+    r = launch_stats_consts<float>(d_field, n, stp, tabs, hist, nsym, p->eb_rel, nsm, s);
+    if (!r) r = launch_train<float>(static_cast<const float*>(d_field), g, stp, tabs, tb, p->stencil, p->hidden[0],
+                                   p->hidden[1], p->m, nmodels, seed, thr32, s);
+  } else {
+    r = launch_stats_consts<double>(d_field, n, stp, tabs, hist, nsym, p->eb_rel, nsm, s);
+    if (!r) r = launch_train<double>(static_cast<const double*>(d_field), g, stp, tabs, tb, p->stencil, p->hidden[0],
+                                    p->hidden[1], p->m, nmodels, seed, thr32, s);
+  }
+  if (r) return r;
+  unsigned long long ctl[8];
+  int herr = 0;
+  if (cudaMemcpyAsync(ctl, tb.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&herr, &stp->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(h_weights_out, tb.w, 4ull * nw * nmodels, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return PC_ERR_CUDA;
+  unsigned long long costs[65];
+  if (cudaMemcpyAsync(costs, tb.costs, 8ull * (nmodels + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return PC_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
+  prof_collect();
+  if (herr) return herr;
+  // TrainCtl: ntrain, nval, s2, nused, then {s_in, chosen, err, pad}
+  if (ctl[0] > L.cap_t || ctl[1] > L.cap_v) return PC_ERR_CAPACITY;
+  int tail[4];
+  memcpy(tail, &ctl[4], sizeof(tail));
+  *s_in_out = tail[0];
+  *chosen_out = tail[1];
+  if (h_costs) memcpy(h_costs, costs, 8ull * (nmodels + 1));
+  return PC_OK;
+}
+
 
 int pc_mlp_nweights(int k, int h1, int h2) { return nweights(k, h1, h2); }
 
@@ -307,6 +449,7 @@ int pc_compress(const void* d_field, const size_t dims[3], int dtype, const pc_p
   uint8_t* ws = static_cast<uint8_t*>(d_ws);
   uint8_t* out = static_cast<uint8_t*>(d_out);
   State* stp = reinterpret_cast<State*>(ws + L.st);
+  Tabs* tabs = reinterpret_cast<Tabs*>(ws + L.tabs);
   auto* hist = reinterpret_cast<unsigned long long*>(ws + L.hist);
   auto* codes = reinterpret_cast<uint16_t*>(ws + L.codes);
   auto* nnflag = reinterpret_cast<uint8_t*>(ws + L.nnflag);
@@ -326,11 +469,11 @@ int pc_compress(const void* d_field, const size_t dims[3], int dtype, const pc_p
   const int nsym = 1 << p->m;
   int r;
   if (dtype == PC_F32) {
-    r = launch_stats_consts<float>(d_field, n, stp, hist, nsym, p->eb_rel, nsm, s);
-    if (!r) r = launch_compress<float>(d_field, g, stp, codes, nnflag, nout, hist, p->m, mode, mlp, nsm, s);
+    r = launch_stats_consts<float>(d_field, n, stp, tabs, hist, nsym, p->eb_rel, nsm, s);
+    if (!r) r = launch_compress<float>(d_field, g, stp, tabs, codes, nnflag, nout, hist, p->m, mode, mlp, nsm, s);
   } else {
-    r = launch_stats_consts<double>(d_field, n, stp, hist, nsym, p->eb_rel, nsm, s);
-    if (!r) r = launch_compress<double>(d_field, g, stp, codes, nnflag, nout, hist, p->m, mode, mlp, nsm, s);
+    r = launch_stats_consts<double>(d_field, n, stp, tabs, hist, nsym, p->eb_rel, nsm, s);
+    if (!r) r = launch_compress<double>(d_field, g, stp, tabs, codes, nnflag, nout, hist, p->m, mode, mlp, nsm, s);
   }
   if (!r) r = launch_codebook(hist, p->m, lens, cw, stp, hs, out, g, hi, s);
   if (!r) {
@@ -404,6 +547,7 @@ int pc_decompress(const void* d_in, size_t in_size, void* d_field, size_t field_
   uint8_t* ws = static_cast<uint8_t*>(d_ws);
   DecScratch ds;
   ds.err = reinterpret_cast<int*>(ws + L.err);
+  ds.ftab = reinterpret_cast<Tabs*>(ws + L.ftab);
   ds.lens = ws + L.lens;
   ds.sorted = reinterpret_cast<uint16_t*>(ws + L.sorted);
   ds.lut = reinterpret_cast<unsigned int*>(ws + L.lut);

@@ -168,24 +168,38 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const unsigned long lon
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nsym = 1 << m;
   if (st->err) return;
-  for (int i = tid; i < nsym; i += nt) { lens[i] = 0; cw[i] = 0; }
-  // compaction: used symbols in symbol order, with their counts
-  const int per = (nsym + nt - 1) / nt;
-  const int lo = min(nsym, tid * per), hi = min(nsym, lo + per);
+  // Only entries of used symbols are ever read, so the length and code
+  // tables are not cleared.  Compaction: used symbols in symbol order, with
+  // their counts; each warp reads a contiguous range 32 symbols at a time.
+  const int lane = tid & 31, wid = tid >> 5, nwarp = nt >> 5;
+  const int per = (nsym + nwarp - 1) / nwarp;
+  const int lo = min(nsym, wid * per), hi = min(nsym, lo + per);
   unsigned long long cnt = 0, mx = 0;
-  for (int s = lo; s < hi; ++s) { cnt += hist[s] > 0; mx = max(mx, hist[s]); }
+  for (int s0 = lo; s0 < hi; s0 += 32) {
+    const int s = s0 + lane;
+    const unsigned long long h = s < hi ? hist[s] : 0ull;
+    mx = max(mx, h);
+    cnt += __popc(__ballot_sync(0xFFFFFFFFu, h > 0));
+  }
   unsigned long long tot;
-  const unsigned long long pre = cta_exscan<unsigned long long>(cnt, s_scan, tot);
+  const unsigned long long pre = cta_exscan<unsigned long long>(lane == 0 ? cnt : 0ull, s_scan, tot);
   const int n = (int)tot;
   unsigned int* k0 = reinterpret_cast<unsigned int*>(hs.key);
   unsigned int* k1 = k0 + nsym;
   uint16_t* v0 = reinterpret_cast<uint16_t*>(hs.symord);
   uint16_t* v1 = v0 + nsym;
   {
-    int p = (int)pre;
-    for (int s = lo; s < hi; ++s) {
-      const unsigned long long h = hist[s];
-      if (h > 0) { k0[p] = (unsigned int)h; v0[p] = (uint16_t)s; ++p; }
+    int p = (int)__shfl_sync(0xFFFFFFFFu, pre, 0);
+    for (int s0 = lo; s0 < hi; s0 += 32) {
+      const int s = s0 + lane;
+      const unsigned long long h = s < hi ? hist[s] : 0ull;
+      const unsigned int bal = __ballot_sync(0xFFFFFFFFu, h > 0);
+      if (h > 0) {
+        const int q = p + __popc(bal & ((1u << lane) - 1u));
+        k0[q] = (unsigned int)h;
+        v0[q] = (uint16_t)s;
+      }
+      p += __popc(bal);
     }
   }
   // largest count -> number of radix passes
@@ -215,7 +229,7 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const unsigned long lon
     if (n == 1 && tid == 0) {
       const unsigned int s = v0[0];
       lens[s] = 1;
-      cw[s] = 0;
+      cw[s] = 1u << 24;
       st_u32(out + off_cb, s | (1u << 16));
     }
     for (unsigned long long i = off_cb + 4ull * n + tid; i < off_bb; i += nt) out[i] = 0;
@@ -286,7 +300,7 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const unsigned long lon
       --l;
     const unsigned int sym = vs[leaf];
     lens[sym] = (uint8_t)l;
-    cw[sym] = s_first[l] + ((unsigned int)i - s_offs[l]);
+    cw[sym] = (s_first[l] + ((unsigned int)i - s_offs[l])) | ((unsigned int)l << 24);
     st_u32(out + off_cb + 4ull * i, sym | ((unsigned int)l << 16));
   }
   for (unsigned long long i = off_cb + 4ull * n + tid; i < off_bb; i += nt) out[i] = 0;

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(256) k_stats(const T* __restrict__ x, unsigned
 // with e0 the smallest positive value of the dtype.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_consts(State* st, double eb) {
+__global__ void k_consts(State* st, double eb, Tabs* tabs) {
   // four independent logarithms on four threads, combined by thread 0
   __shared__ double s_l[4];
   __shared__ double s_ab[2];
@@ -138,6 +138,10 @@ __global__ void k_consts(State* st, double eb) {
   }
   __syncthreads();
   if (s_stop) return;
+  build_tabs_entry(tabs, t);
+  build_tabs_entry(tabs, t + 32);
+  build_tabs_entry(tabs, t + 64);
+  build_tabs_entry(tabs, t + 96);
   if (t < 4) {
     const double amin = s_ab[0], amax = s_ab[1];
     const double arg = t == 0 ? __dadd_rn(1.0, eb) : (t == 1 ? __dadd_rn(amax, e0) : (t == 2 ? amin : __dsub_rn(amin, e0)));
@@ -177,49 +181,69 @@ __global__ void k_consts(State* st, double eb) {
 // A CTA of 256 threads handles a brick of G consecutive blocks along x (G
 // chosen so a brick holds at most 4096 points); each block is owned by a team
 // of 256/G threads.  The brick is read with consecutive threads on consecutive
-// x, transformed on the fly, and kept on chip as codes (dq), clamped
-// anchor-centred inputs (vc) and bound flags (ok).  Codes go out block-strided
-// in padded raster order (index (lz*B1 + ly)*B2 + lx); the histogram is kept
-// in shared memory for a window of codes around R and flushed once per CTA.
+// x (16-byte loads when rows allow), transformed on the fly and kept on chip:
+// each point's code with its bound flag (2 q + ok), and the clamped
+// anchor-centred inputs in a zero-bordered padded block, so that stencil
+// gathers need no bounds checks (a neighbour outside the block reads 0).
+// Codes go out block-strided in padded raster order (index (lz*B1 + ly)*B2 +
+// lx) with 16-byte stores; the histogram is kept in shared memory for a
+// window of codes around R and flushed once per CTA.
 // ---------------------------------------------------------------------------
-constexpr int kHistWin = 4096;
+constexpr int kHistWin = 2048;
 
-template <int BV>
-struct BrickShape {
-  static constexpr int G = BV <= 512 ? 8 : (BV <= 1024 ? 4 : (BV <= 2048 ? 2 : 1));
-  static constexpr int TS = 256 / G;
-  static constexpr int PPT = (BV + TS - 1) / TS;
-};
+template <int BV, int MODE, int PV>
+constexpr size_t compress_smem_bytes() {
+  constexpr int G = BrickShape<BV>::G;
+  return sizeof(Tabs) + (size_t)G * BV * 4 + (size_t)((G * PV + 3) & ~3) * 4 + (size_t)G * BV * 2 * (MODE ? 2 : 1) +
+         (size_t)kHistWin * 4;
+}
 
 template <typename T, int B0, int B1, int B2, int MODE, int K, int H1, int H2>
 __global__ void __launch_bounds__(256) k_compress(const T* __restrict__ x, Geo g, const State* __restrict__ st,
-                                                   uint16_t* __restrict__ codes, uint8_t* __restrict__ nnflag,
-                                                   uint32_t* __restrict__ nout, unsigned long long* __restrict__ hist,
-                                                   int m, const __grid_constant__ Mlp mlp) {
+                                                   const Tabs* __restrict__ tabs, uint16_t* __restrict__ codes,
+                                                   uint8_t* __restrict__ nnflag, uint32_t* __restrict__ nout,
+                                                   unsigned long long* __restrict__ hist, int m,
+                                                   const __grid_constant__ Mlp mlp) {
   constexpr int BV = B0 * B1 * B2;
   using BS = BrickShape<BV>;
   constexpr int G = BS::G, TS = BS::TS, PPT = BS::PPT;
+  constexpr bool WIDE = MODE != 0 && (K == 13 || K == 0);
+  using PD = Pad<B0, B1, B2, WIDE>;
+  constexpr int VW = (16 / (int)sizeof(T));
+  constexpr bool VEC_OK = (B2 * G) % VW == 0;
   extern __shared__ __align__(16) unsigned char smem[];
-  int* s_dq = reinterpret_cast<int*>(smem);                       // G*BV
-  int* s_vc = s_dq + G * BV;                                      // G*BV
-  unsigned int* s_hist = reinterpret_cast<unsigned int*>(s_vc + G * BV);  // kHistWin
-  uint16_t* s_cz = reinterpret_cast<uint16_t*>(s_hist + kHistWin);        // G*BV
-  uint16_t* s_cn = s_cz + G * BV;                                         // G*BV (MLP only)
-  uint8_t* s_ok = reinterpret_cast<uint8_t*>(s_cn + (MODE ? G * BV : 0)); // G*BV
+  Tabs& tb = *reinterpret_cast<Tabs*>(smem);
+  int* s_dq = reinterpret_cast<int*>(smem + sizeof(Tabs));             // G*BV: 2 q + ok
+  int* s_vp = s_dq + G * BV;                                           // G*PV padded inputs
+  uint16_t* s_cz = reinterpret_cast<uint16_t*>(s_vp + ((G * PD::PV + 3) & ~3));  // G*BV
+  uint16_t* s_cn = s_cz + G * BV;                                      // G*BV (perceptron only)
+  unsigned int* s_hist = reinterpret_cast<unsigned int*>(s_cn + (MODE ? G * BV : 0));
   __shared__ int s_cost[G][2];
   __shared__ int s_nz[G];
+  __shared__ int s_da[G];
 
-  const State c = *st;
-  if (c.err) return;
+  if (st->err) return;
+  State c;
+  c.Kp = st->Kp; c.Kn = st->Kn; c.Zq = st->Zq; c.S = st->S;
+  c.step32 = st->step32; c.inv32 = st->inv32; c.ebdn32 = st->ebdn32;
+  c.stepd = st->stepd; c.invd = st->invd; c.ebdnd = st->ebdnd;
   const int tid = threadIdx.x;
+  for (int i = tid; i < (int)(sizeof(Tabs) / 4); i += 256)
+    reinterpret_cast<float*>(&tb)[i] = reinterpret_cast<const float*>(tabs)[i];
+  for (int i = tid; i < G * PD::PV; i += 256) s_vp[i] = 0;
+  for (int i = tid; i < kHistWin; i += 256) s_hist[i] = 0u;
   const int R = 1 << (m - 1);
   const int hbase = R - kHistWin / 2 > 0 ? R - kHistWin / 2 : 0;
-  for (int i = tid; i < kHistWin; i += 256) s_hist[i] = 0u;
   const float sig = MODE ? __uint_as_float((unsigned int)(127 - mlp.s_in) << 23) : 1.0f;
   const float unsig = MODE ? __uint_as_float((unsigned int)(127 + mlp.s_in) << 23) : 1.0f;
+  const bool vec_rows = VEC_OK && (g.n[2] % VW == 0) && ((reinterpret_cast<uintptr_t>(x) & 15u) == 0);
+  __syncthreads();
 
   const long long nbx = (g.nb[2] + G - 1) / G;
   const long long nbricks = g.nb[0] * g.nb[1] * nbx;
+  const int team = tid / TS, t = tid % TS;
+  int* dq = s_dq + team * BV;
+  int* vp = s_vp + team * PD::PV;
   for (long long brick = blockIdx.x; brick < nbricks; brick += gridDim.x) {
     const long long bxg = brick % nbx;
     const long long byz = brick / nbx;
@@ -229,132 +253,183 @@ __global__ void __launch_bounds__(256) k_compress(const T* __restrict__ x, Geo g
     const int e0 = (int)min((long long)B0, g.n[0] - z0);
     const int e1 = (int)min((long long)B1, g.n[1] - y0);
     const int W = (int)min((long long)(G * B2), g.n[2] - x0);
-    // load + transform (a4)
-    const bool full = (e0 == B0) && (e1 == B1) && (W == G * B2);
-    if (full) {
-#pragma unroll 4
-      for (int e = tid; e < B0 * B1 * G * B2; e += 256) {
-        const int r = e / (G * B2), col = e % (G * B2);
-        const int z = r / B1, y = r % B1;
-        const T v = __ldg(&x[((z0 + z) * g.n[1] + (y0 + y)) * g.n[2] + x0 + col]);
-        bool ok;
-        const int q = Num<T>::transform(v, c, ok);
-        const int si = (col / B2) * BV + (z * B1 + y) * B2 + (col % B2);
-        s_dq[si] = q;
-        s_ok[si] = ok;
+    // a4: load the brick into registers (16-byte loads where rows allow), the
+    // G block anchors first; then transform every point and write its code
+    // (2 q + ok) and its anchor-centred clamped input in the padded block.
+    constexpr int EPT = (G * BV + 255) / 256;  // elements per thread, <= 16
+    constexpr int RW = G * B2 / VW;               // 16-byte vectors per brick row
+    constexpr int NV = B0 * B1 * RW;
+    const bool fullb = e0 == B0 && e1 == B1 && W == G * B2;
+    const bool vecb = fullb && vec_rows;
+    const long long n12 = g.n[1] * g.n[2];
+    const T* base = x + z0 * n12 + y0 * g.n[2] + x0;
+    T vals[EPT];
+    if (vecb) {
+#pragma unroll
+      for (int it = 0; it < (NV + 255) / 256; ++it) {
+        const int e = tid + 256 * it;
+        if (e < NV) {
+          const int r = e / RW, cv = e % RW;
+          const uint4 u = __ldg(reinterpret_cast<const uint4*>(base + (r / B1) * n12 + (r % B1) * g.n[2]) + cv);
+          memcpy(&vals[it * VW], &u, 16);
+        }
       }
     } else {
-      for (int e = tid; e < e0 * e1 * W; e += 256) {
-        const int r = e / W, col = e - r * W;
-        const int z = r / e1, y = r - z * e1;
-        const T v = __ldg(&x[((z0 + z) * g.n[1] + (y0 + y)) * g.n[2] + x0 + col]);
-        bool ok;
-        const int q = Num<T>::transform(v, c, ok);
-        const int si = (col / B2) * BV + (z * B1 + y) * B2 + (col % B2);
-        s_dq[si] = q;
-        s_ok[si] = ok;
+      const int tot = e0 * e1 * W;
+#pragma unroll
+      for (int i = 0; i < EPT; ++i) {
+        const int e = tid + 256 * i;
+        if (e < tot) {
+          const int r = e / W, col = e - r * W;
+          vals[i] = __ldg(&base[(r / e1) * n12 + (r % e1) * g.n[2] + col]);
+        }
+      }
+      // truncated blocks: padded cells outside the block read 0
+      for (int i = tid; i < G * BV; i += 256) {
+        const int gb = i / BV, j = i % BV;
+        const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+        const int e2b = (int)min((long long)B2, g.n[2] - (bxg * G + gb) * B2);
+        if (!(lz < e0 && ly < e1 && lx < e2b)) s_vp[gb * PD::PV + PD::at(lz, ly, lx)] = 0;
       }
     }
-    if (tid < G) { s_cost[tid][0] = 0; s_cost[tid][1] = 0; s_nz[tid] = 0; }
+    if (tid < G) {
+      int qa = 0;
+      if (bxg * G + tid < g.nb[2]) {
+        bool okk;
+        qa = Num<T>::transform(__ldg(&base[tid * B2]), c, tb, okk);
+      }
+      s_da[tid] = qa;
+      s_cost[tid][0] = 0; s_cost[tid][1] = 0; s_nz[tid] = 0;
+    }
     __syncthreads();
-    const int team = tid / TS, t = tid % TS;
+    auto emit = [&](T v, int row, int col) {
+      const int gb = col / B2, lx = col % B2;
+      const int lz = row / B1, ly = row % B1;
+      bool ok;
+      const int q = Num<T>::transform(v, c, tb, ok);
+      s_dq[gb * BV + row * B2 + lx] = 2 * q + (ok ? 1 : 0);
+      s_vp[gb * PD::PV + PD::at(lz, ly, lx)] = clampd(q, s_da[gb]);
+    };
+    if (vecb) {
+#pragma unroll
+      for (int it = 0; it < (NV + 255) / 256; ++it) {
+        const int e = tid + 256 * it;
+        if (e < NV) {
+          const int r = e / RW, cv = e % RW;
+#pragma unroll
+          for (int q = 0; q < VW; ++q) emit(vals[it * VW + q], r, cv * VW + q);
+        }
+      }
+    } else {
+      const int tot = e0 * e1 * W;
+#pragma unroll
+      for (int i = 0; i < EPT; ++i) {
+        const int e = tid + 256 * i;
+        if (e < tot) {
+          const int r = e / W, col = e - r * W;
+          emit(vals[i], (r / e1) * B1 + (r % e1), col);
+        }
+      }
+    }
+    __syncthreads();
     const long long bx = bxg * G + team;
     const bool bvalid = bx < g.nb[2];
     const int e2 = bvalid ? (int)min((long long)B2, g.n[2] - bx * B2) : 0;
-    int* dq = s_dq + team * BV;
-    int* vc = s_vc + team * BV;
-    // a5: anchor-centred, clamped inputs
+    const bool bfull = e0 == B0 && e1 == B1 && e2 == B2;
+    const int da = s_da[team];
+    // a6-a8: predict, quantize, cost (and, for Lorenzo only, a9 histogram)
+    const long long b = (bz * g.nb[1] + by) * g.nb[2] + bx;
+    int cz = 0, cn = 0, nz = 0;
     if (bvalid) {
-      const int da = dq[0];
-#pragma unroll
-      for (int i = 0; i < PPT; ++i) {
-        const int j = t + i * TS;
-        if (j < BV) vc[j] = clampv((long long)dq[j] - da);
-      }
-    }
-    __syncthreads();
-    // a6-a8: predict, quantize, cost
-    int cz = 0, cn = 0;
-    if (bvalid) {
-      const int da = dq[0];
-#pragma unroll 1
+#pragma unroll(MODE ? 1 : PPT)
       for (int i = 0; i < PPT; ++i) {
         const int j = t + i * TS;
         if (j >= BV) break;
         const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
-        const bool valid = lz < e0 && ly < e1 && lx < e2 && j != 0;
+        const bool valid = (bfull || (lz < e0 && ly < e1 && lx < e2)) && j != 0;
         uint16_t codez = 0, coden = 0;
         if (valid) {
-          const long long v = (long long)dq[j] - da;
-          const bool okp = s_ok[team * BV + j];
+          const int pd = dq[j];
+          const bool okp = pd & 1;
+          const int v = (pd >> 1) - da;                          // |v| < 2^31
+          const int vk = v > (1 << 30) ? (1 << 30) : (v < -(1 << 30) ? -(1 << 30) : v);
+          const int pj = PD::at(lz, ly, lx);
           int lzp = 0;
 #pragma unroll
-          for (int s = 0; s < 7; ++s) {
-            const int qz = lz + s7_dz(s), qy = ly + s7_dy(s), qx = lx + s7_dx(s);
-            const int vv = (qz >= 0 && qy >= 0 && qx >= 0) ? vc[(qz * B1 + qy) * B2 + qx] : 0;
-            lzp += lz_w(7, s) * vv;
-          }
-          const long long kz = v - lzp;
-          const long long az = kz < 0 ? -kz : kz;
+          for (int q = 0; q < 7; ++q) lzp += lz_w(7, q) * vp[pj + PD::off(s7_dz(q), s7_dy(q), s7_dx(q))];
+          const int kz = vk - lzp;
+          const int az = kz < 0 ? -kz : kz;
           cz += bitlen_u((unsigned int)(az < R ? az : R));
           codez = (az <= R - 1 && okp) ? (uint16_t)(kz + R) : 0;
           if constexpr (MODE != 0) {
-            int in[K > 0 ? K : 13];
+            constexpr int KK = K > 0 ? K : 13;
+            int in[KK];
             const int kk = K > 0 ? K : mlp.k;
 #pragma unroll
-            for (int s = 0; s < (K > 0 ? K : 13); ++s) {
-              if (s < kk) {
-                const int qz = lz + st_dz(kk, s), qy = ly + st_dy(kk, s), qx = lx + st_dx(kk, s);
-                in[s] = (qz >= 0 && qy >= 0 && qx >= 0 && qz < e0 && qy < e1 && qx < e2)
-                            ? vc[(qz * B1 + qy) * B2 + qx] : 0;
-              }
-            }
-            float p;
-            if constexpr (K > 0) p = mlp_fwd<K, H1, H2>(mlp, in, sig, unsig);
-            else p = mlp_fwd_rt(mlp, in, sig, unsig);
-            const long long kn = v - (long long)round_pred(p);
+            for (int q = 0; q < KK; ++q)
+              in[q] = q < kk ? vp[pj + PD::off(st_dz(kk, q), st_dy(kk, q), st_dx(kk, q))] : 0;
+            float pv;
+            if constexpr (K > 0) pv = mlp_fwd<K, H1, H2>(mlp, in, sig, unsig);
+            else pv = mlp_fwd_rt(mlp, in, sig, unsig);
+            const long long kn = (long long)vk - (long long)round_pred(pv);
             const long long an = kn < 0 ? -kn : kn;
             cn += bitlen_u((unsigned int)(an < R ? an : R));
             coden = (an <= R - 1 && okp) ? (uint16_t)(kn + R) : 0;
+          } else {
+            nz += codez == 0;
+            const int hi = (int)codez - hbase;
+            if (hi >= 0 && hi < kHistWin) atomicAdd(&s_hist[hi], 1u);
+            else atomicAdd(&hist[codez], 1ull);
           }
         }
         s_cz[team * BV + j] = codez;
         if constexpr (MODE != 0) s_cn[team * BV + j] = coden;
       }
-      atomicAdd(&s_cost[team][0], cz);
-      if (MODE) atomicAdd(&s_cost[team][1], cn);
     }
+    // team sums
+    int tcz = team_sum<TS>(cz, &s_cost[team][0]);
+    int tcn = MODE ? team_sum<TS>(cn, &s_cost[team][1]) : 0;
+    int tnz = MODE ? 0 : team_sum<TS>(nz, &s_nz[team]);
     __syncthreads();
-    // a7 select, a8 emit, a9 histogram
+    if constexpr (TS != 32) {
+      tcz = s_cost[team][0];
+      tcn = s_cost[team][1];
+      tnz = s_nz[team];
+    }
+    // a7 select, a8 emit, a9 histogram of the chosen codes
     if (bvalid) {
-      const long long b = (bz * g.nb[1] + by) * g.nb[2] + bx;
-      const bool usen = MODE != 0 && s_cost[team][1] < s_cost[team][0];
+      const bool usen = MODE != 0 && tcn < tcz;
       const uint16_t* src = usen ? s_cn + team * BV : s_cz + team * BV;
-      int nz = 0;
-#pragma unroll
-      for (int i = 0; i < PPT; ++i) {
-        const int j = t + i * TS;
-        if (j < BV) {
-          const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
-          const bool valid = lz < e0 && ly < e1 && lx < e2 && j != 0;
-          const uint16_t cd = src[j];
-          codes[b * BV + j] = cd;
-          if (valid) {
-            nz += cd == 0;
-            const int hi = (int)cd - hbase;
-            if (hi >= 0 && hi < kHistWin) atomicAdd(&s_hist[hi], 1u);
-            else atomicAdd(&hist[cd], 1ull);
+      if constexpr (MODE != 0) {
+        int nzz = 0;
+#pragma unroll 4
+        for (int i = 0; i < PPT; ++i) {
+          const int j = t + i * TS;
+          if (j < BV) {
+            const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+            const bool valid = (bfull || (lz < e0 && ly < e1 && lx < e2)) && j != 0;
+            if (valid) {
+              const uint16_t cd = src[j];
+              nzz += cd == 0;
+              const int hi = (int)cd - hbase;
+              if (hi >= 0 && hi < kHistWin) atomicAdd(&s_hist[hi], 1u);
+              else atomicAdd(&hist[cd], 1ull);
+            }
           }
         }
+        tnz = team_sum<TS>(nzz, &s_nz[team]);
       }
-      atomicAdd(&s_nz[team], nz);
-      __syncwarp();
+      uint4* dst = reinterpret_cast<uint4*>(codes + b * BV);
+      const uint4* sv = reinterpret_cast<const uint4*>(src);
+      for (int i = t; i < BV / 8; i += TS) dst[i] = sv[i];
     }
-    __syncthreads();
+    if constexpr (MODE != 0 && TS != 32) {
+      __syncthreads();
+      tnz = s_nz[team];
+    }
     if (bvalid && t == 0) {
-      const long long b = (bz * g.nb[1] + by) * g.nb[2] + bx;
-      nnflag[b] = (MODE != 0 && s_cost[team][1] < s_cost[team][0]) ? 1 : 0;
-      nout[b] = 1u + (unsigned int)s_nz[team];
+      nnflag[b] = (MODE != 0 && tcn < tcz) ? 1 : 0;
+      nout[b] = 1u + (unsigned int)tnz;
     }
     __syncthreads();
   }
@@ -364,34 +439,29 @@ __global__ void __launch_bounds__(256) k_compress(const T* __restrict__ x, Geo g
   }
 }
 
-template <int BV>
-size_t compress_smem(int mode) {
-  constexpr int G = BrickShape<BV>::G;
-  return (size_t)G * BV * 4 * 2 + kHistWin * 4 + (size_t)G * BV * 2 * (mode ? 2 : 1) + (size_t)G * BV;
-}
-
 // ---------------------------------------------------------------------------
 // Host-side launchers (called from the API layer).
 // ---------------------------------------------------------------------------
 template <typename T>
-int launch_stats_consts(const void* x, unsigned long long n, State* st, unsigned long long* hist, int nsym,
-                        double eb, int nsm, cudaStream_t s) {
+int launch_stats_consts(const void* x, unsigned long long n, State* st, Tabs* tabs, unsigned long long* hist,
+                        int nsym, double eb, int nsm, cudaStream_t s) {
   { ProfScope p(kStInit, s); k_init<<<64, 256, 0, s>>>(st, hist, nsym); }
   { ProfScope p(kStStats, s); k_stats<T><<<nsm * 8, 256, 0, s>>>(static_cast<const T*>(x), n, st); }
-  { ProfScope p(kStConsts, s); k_consts<T><<<1, 32, 0, s>>>(st, eb); }
+  { ProfScope p(kStConsts, s); k_consts<T><<<1, 32, 0, s>>>(st, eb, tabs); }
   return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
-template int launch_stats_consts<float>(const void*, unsigned long long, State*, unsigned long long*, int, double,
-                                        int, cudaStream_t);
-template int launch_stats_consts<double>(const void*, unsigned long long, State*, unsigned long long*, int, double,
-                                         int, cudaStream_t);
+template int launch_stats_consts<float>(const void*, unsigned long long, State*, Tabs*, unsigned long long*, int,
+                                        double, int, cudaStream_t);
+template int launch_stats_consts<double>(const void*, unsigned long long, State*, Tabs*, unsigned long long*, int,
+                                         double, int, cudaStream_t);
 
 template <typename T, int B0, int B1, int B2, int MODE, int K, int H1, int H2>
-static int launch_c(const void* x, const Geo& g, const State* st, uint16_t* codes, uint8_t* nnflag, uint32_t* nout,
-                    unsigned long long* hist, int m, const Mlp& mlp, int nsm, cudaStream_t s) {
+static int launch_c(const void* x, const Geo& g, const State* st, const Tabs* tabs, uint16_t* codes, uint8_t* nnflag,
+                    uint32_t* nout, unsigned long long* hist, int m, const Mlp& mlp, int nsm, cudaStream_t s) {
   constexpr int BV = B0 * B1 * B2;
+  constexpr bool WIDE = MODE != 0 && (K == 13 || K == 0);
   auto kern = k_compress<T, B0, B1, B2, MODE, K, H1, H2>;
-  size_t sm = compress_smem<BV>(MODE);
+  const size_t sm = compress_smem_bytes<BV, MODE, Pad<B0, B1, B2, WIDE>::PV>();
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
     return PC_ERR_CUDA;
   int per_sm = 0;
@@ -404,29 +474,31 @@ static int launch_c(const void* x, const Geo& g, const State* st, uint16_t* code
   if (grid < 1) grid = 1;
   {
     ProfScope p(kStCompress, s);
-    kern<<<(unsigned int)grid, 256, sm, s>>>(static_cast<const T*>(x), g, st, codes, nnflag, nout, hist, m, mlp);
+    kern<<<(unsigned int)grid, 256, sm, s>>>(static_cast<const T*>(x), g, st, tabs, codes, nnflag, nout, hist, m, mlp);
   }
   return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
 
 template <typename T, int B0, int B1, int B2>
-static int launch_c_shape(const void* x, const Geo& g, const State* st, uint16_t* codes, uint8_t* nnflag,
-                          uint32_t* nout, unsigned long long* hist, int m, int mode, const Mlp& mlp, int nsm,
-                          cudaStream_t s) {
-  if (mode == 0) return launch_c<T, B0, B1, B2, 0, 0, 0, 0>(x, g, st, codes, nnflag, nout, hist, m, mlp, nsm, s);
+static int launch_c_shape(const void* x, const Geo& g, const State* st, const Tabs* tabs, uint16_t* codes,
+                          uint8_t* nnflag, uint32_t* nout, unsigned long long* hist, int m, int mode, const Mlp& mlp,
+                          int nsm, cudaStream_t s) {
+  if (mode == 0)
+    return launch_c<T, B0, B1, B2, 0, 0, 0, 0>(x, g, st, tabs, codes, nnflag, nout, hist, m, mlp, nsm, s);
   if (mlp.k == 7 && mlp.h1 == 16 && mlp.h2 == 16)
-    return launch_c<T, B0, B1, B2, 1, 7, 16, 16>(x, g, st, codes, nnflag, nout, hist, m, mlp, nsm, s);
+    return launch_c<T, B0, B1, B2, 1, 7, 16, 16>(x, g, st, tabs, codes, nnflag, nout, hist, m, mlp, nsm, s);
   if (mlp.k == 13 && mlp.h1 == 32 && mlp.h2 == 32)
-    return launch_c<T, B0, B1, B2, 1, 13, 32, 32>(x, g, st, codes, nnflag, nout, hist, m, mlp, nsm, s);
-  return launch_c<T, B0, B1, B2, 1, 0, 0, 0>(x, g, st, codes, nnflag, nout, hist, m, mlp, nsm, s);
+    return launch_c<T, B0, B1, B2, 1, 13, 32, 32>(x, g, st, tabs, codes, nnflag, nout, hist, m, mlp, nsm, s);
+  return launch_c<T, B0, B1, B2, 1, 0, 0, 0>(x, g, st, tabs, codes, nnflag, nout, hist, m, mlp, nsm, s);
 }
 
 template <typename T>
-int launch_compress(const void* x, const Geo& g, const State* st, uint16_t* codes, uint8_t* nnflag, uint32_t* nout,
-                    unsigned long long* hist, int m, int mode, const Mlp& mlp, int nsm, cudaStream_t s) {
+int launch_compress(const void* x, const Geo& g, const State* st, const Tabs* tabs, uint16_t* codes, uint8_t* nnflag,
+                    uint32_t* nout, unsigned long long* hist, int m, int mode, const Mlp& mlp, int nsm,
+                    cudaStream_t s) {
   const int b0 = g.b[0], b1 = g.b[1], b2 = g.b[2];
 #define PC_SHAPE(A, B, C) \
-  if (b0 == A && b1 == B && b2 == C) return launch_c_shape<T, A, B, C>(x, g, st, codes, nnflag, nout, hist, m, mode, mlp, nsm, s);
+  if (b0 == A && b1 == B && b2 == C) return launch_c_shape<T, A, B, C>(x, g, st, tabs, codes, nnflag, nout, hist, m, mode, mlp, nsm, s);
   PC_SHAPE(8, 8, 8)
   PC_SHAPE(4, 4, 4)
   PC_SHAPE(16, 16, 16)
@@ -436,9 +508,9 @@ int launch_compress(const void* x, const Geo& g, const State* st, uint16_t* code
 #undef PC_SHAPE
   return PC_ERR_ARG;
 }
-template int launch_compress<float>(const void*, const Geo&, const State*, uint16_t*, uint8_t*, uint32_t*,
-                                    unsigned long long*, int, int, const Mlp&, int, cudaStream_t);
-template int launch_compress<double>(const void*, const Geo&, const State*, uint16_t*, uint8_t*, uint32_t*,
-                                     unsigned long long*, int, int, const Mlp&, int, cudaStream_t);
+template int launch_compress<float>(const void*, const Geo&, const State*, const Tabs*, uint16_t*, uint8_t*,
+                                    uint32_t*, unsigned long long*, int, int, const Mlp&, int, cudaStream_t);
+template int launch_compress<double>(const void*, const Geo&, const State*, const Tabs*, uint16_t*, uint8_t*,
+                                     uint32_t*, unsigned long long*, int, int, const Mlp&, int, cudaStream_t);
 
 }  // namespace pc

@@ -28,6 +28,7 @@ __global__ void __launch_bounds__(1024) k_dec_tables(const uint8_t* __restrict__
   const int n = (int)di.n_used;
   if (tid < 32) s_cnt[tid] = 0;
   if (tid == 0) s_bad = 0;
+  if (tid < 128) build_tabs_entry(ds.ftab, tid);
   for (int i = tid; i < 2048; i += nt) s_seen[i] = 0u;
   for (int i = tid; i < nsym; i += nt) ds.lens[i] = 0;
   for (int i = tid; i < (1 << kLutBits); i += nt) ds.lut[i] = 0;
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(256) k_dec_blockoff(Geo g, const uint8_t* __re
 // Eight decoded codes are packed and written with one 16-byte store.
 constexpr int kSortedSmem = 16384;
 
-__global__ void __launch_bounds__(128) k_huff_decode(Geo g, const uint8_t* __restrict__ in, DecInfo di,
+__global__ void __launch_bounds__(256) k_huff_decode(Geo g, const uint8_t* __restrict__ in, DecInfo di,
                                                      DecScratch ds) {
   __shared__ unsigned int s_lut[1 << kLutBits];
   __shared__ unsigned int s_tab[96];
@@ -193,17 +194,31 @@ __global__ void __launch_bounds__(128) k_huff_decode(Geo g, const uint8_t* __res
   dec_block_coords(g, b, bz, by, bx, e0, e1, e2);
   const bool full = e0 == g.b[0] && e1 == g.b[1] && e2 == g.b[2];
   const unsigned int nbits = *reinterpret_cast<const unsigned int*>(in + di.off_bb + 4ull * b) & 0x7FFFFFFFu;
-  const uint32_t* stream = reinterpret_cast<const uint32_t*>(in + di.off_st);
+  // The stream section starts 16-byte aligned and the container is padded to
+  // 16 bytes, so every 16-byte chunk that holds a stream word lies inside it.
+  const uint4* s4 = reinterpret_cast<const uint4*>(in + di.off_st);
+  const unsigned long long nq = (di.swords + 3) / 4;
   const unsigned long long start = ds.boff[b];
-  unsigned long long wpos = start >> 5;
+  unsigned long long qi = start >> 7;
+  int wi = (int)((start >> 5) & 3ull);
+  const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+  uint4 cur = qi < nq ? __ldg(&s4[qi]) : zero4;
+  uint4 nxt = qi + 1 < nq ? __ldg(&s4[qi + 1]) : zero4;
+  auto next_word = [&]() -> unsigned int {
+    const unsigned int w = wi == 0 ? cur.x : (wi == 1 ? cur.y : (wi == 2 ? cur.z : cur.w));
+    if (++wi == 4) {
+      wi = 0;
+      ++qi;
+      cur = nxt;
+      nxt = qi + 1 < nq ? __ldg(&s4[qi + 1]) : zero4;
+    }
+    return w;
+  };
   unsigned long long buf = 0;
   int nb = 0;
-  while (nb <= 32) {
-    const unsigned int wv = wpos < di.swords ? __ldg(&stream[wpos]) : 0u;
-    ++wpos;
-    buf |= (unsigned long long)wv << (32 - nb);
-    nb += 32;
-  }
+  buf = (unsigned long long)next_word() << 32;
+  buf |= next_word();
+  nb = 64;
   {
     const int skip = (int)(start & 31ull);
     buf <<= skip;
@@ -233,9 +248,7 @@ __global__ void __launch_bounds__(128) k_huff_decode(Geo g, const uint8_t* __res
       }
       if (valid && !bad) {
         if (nb <= 32) {
-          const unsigned int wv = wpos < di.swords ? __ldg(&stream[wpos]) : 0u;
-          ++wpos;
-          buf |= (unsigned long long)wv << (32 - nb);
+          buf |= (unsigned long long)next_word() << (32 - nb);
           nb += 32;
         }
         const unsigned int peek = (unsigned int)(buf >> 40);  // next 24 bits
@@ -247,7 +260,7 @@ __global__ void __launch_bounds__(128) k_huff_decode(Geo g, const uint8_t* __res
           // the window has reached
           unsigned int l = kLutBits + 1;
 #pragma unroll
-          for (int q = 0; q < kLmax - kLutBits - 1; ++q) l += peek >= lim[q];
+          for (int q2 = 0; q2 < kLmax - kLutBits - 1; ++q2) l += peek >= lim[q2];
           if (peek >= lim[kLmax - kLutBits - 1]) bad = true;
           const unsigned int d = (peek >> (kLmax - l)) - s_tab[l];
           if (d >= s_tab[32 + l]) bad = true;
@@ -269,30 +282,40 @@ __global__ void __launch_bounds__(128) k_huff_decode(Geo g, const uint8_t* __res
 // ---------------------------------------------------------------------------
 // Wavefront reconstruction.  Schedule s(p) = z + y + x for the 7-point
 // stencil and 4z + 2y + x for the 13-point one: every causal neighbour has a
-// smaller s, so all points of one wave are independent.
+// smaller s, so all points of one wave are independent.  Blocks are rebuilt in
+// bricks (as in compression) in zero-bordered padded arrays, and the brick is
+// written back with coalesced (16-byte where rows allow) stores.
 // ---------------------------------------------------------------------------
-template <int BV>
-struct DecShape {
-  static constexpr int G = BV <= 512 ? 8 : (BV <= 1024 ? 4 : (BV <= 2048 ? 2 : 1));
-  static constexpr int TS = 256 / G;
-};
+template <int BV, int PV, int TSZ>
+constexpr size_t recon_smem_bytes() {
+  constexpr int G = BrickShape<BV>::G;
+  return sizeof(Tabs) + (size_t)((G * PV + 3) & ~3) * 4 + (size_t)G * BV * TSZ + (size_t)G * BV * 2 * 2 +
+         (size_t)BV * 2 + 16;
+}
 
 template <typename T, int B0, int B1, int B2, int MODE, int K, int H1, int H2>
 __global__ void __launch_bounds__(256) k_recon(Geo g, const uint8_t* __restrict__ in, DecInfo di, DecScratch ds,
                                                T* __restrict__ xo, const __grid_constant__ Mlp mlp) {
   constexpr int BV = B0 * B1 * B2;
-  constexpr int G = DecShape<BV>::G, TS = DecShape<BV>::TS;
-  constexpr int SZ = (B0 - 1) * 4 + (B1 - 1) * 2 + (B2 - 1) + 1;  // waves for the wider schedule
+  using BS = BrickShape<BV>;
+  constexpr int G = BS::G, TS = BS::TS, NWT = TS / 32;
+  constexpr bool WIDE = MODE != 0 && (K == 13 || K == 0);
+  using PD = Pad<B0, B1, B2, WIDE>;
+  constexpr int VPR = (G * PD::PV + 3) & ~3;
+  constexpr int SZ = (B0 - 1) * 4 + (B1 - 1) * 2 + (B2 - 1) + 1;  // waves of the wider schedule
+  constexpr int VW = 16 / (int)sizeof(T);
+  constexpr bool VEC_OK = (B2 * G) % VW == 0;
   extern __shared__ __align__(16) unsigned char smem[];
-  int* s_dq = reinterpret_cast<int*>(smem);                  // G*BV
-  int* s_vc = s_dq + G * BV;                                 // G*BV
-  T* s_x = reinterpret_cast<T*>(s_vc + G * BV);              // G*BV
-  uint16_t* s_cd = reinterpret_cast<uint16_t*>(s_x + G * BV);  // G*BV
-  uint16_t* s_rk = s_cd + G * BV;                            // G*BV outlier ranks
-  uint16_t* s_list = s_rk + G * BV;                          // BV wave order
+  Tabs& tb = *reinterpret_cast<Tabs*>(smem);
+  int* s_vp = reinterpret_cast<int*>(smem + sizeof(Tabs));          // G*PV padded centred codes
+  T* s_x = reinterpret_cast<T*>(s_vp + VPR);                        // G*BV
+  uint16_t* s_cd = reinterpret_cast<uint16_t*>(s_x + G * BV);       // G*BV
+  uint16_t* s_rk = s_cd + G * BV;                                   // G*BV balance-point ranks
+  uint16_t* s_list = s_rk + G * BV;                                 // BV wave order
   __shared__ int s_ws[SZ + 2];
   __shared__ int s_fill[SZ + 2];
-  __shared__ unsigned int s_tsum[G][TS / 32 > 0 ? TS / 32 : 1];
+  __shared__ unsigned int s_wt[G][NWT];
+  __shared__ int s_da[G];
   __shared__ int s_bad;
 
   State c;
@@ -306,35 +329,43 @@ __global__ void __launch_bounds__(256) k_recon(Geo g, const uint8_t* __restrict_
     c.invd = __longlong_as_double((long long)di.inv_bits);
     c.ebdnd = __longlong_as_double((long long)di.ebdn_bits);
   }
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
   const bool s13 = di.stencil == 13;
-  // wave order for the full block shape (order inside a wave is free)
+  for (int i = tid; i < (int)(sizeof(Tabs) / 4); i += 256)
+    reinterpret_cast<float*>(&tb)[i] = reinterpret_cast<const float*>(ds.ftab)[i];
+  for (int i = tid; i < VPR; i += 256) s_vp[i] = 0;
   for (int i = tid; i < SZ + 2; i += 256) { s_ws[i] = 0; s_fill[i] = 0; }
   if (tid == 0) s_bad = 0;
   __syncthreads();
   for (int j = tid; j < BV; j += 256) {
     const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
-    const int s = s13 ? 4 * lz + 2 * ly + lx : lz + ly + lx;
-    atomicAdd(&s_ws[s + 1], 1);
+    atomicAdd(&s_ws[(s13 ? 4 * lz + 2 * ly + lx : lz + ly + lx) + 1], 1);
   }
   __syncthreads();
   if (tid == 0)
-    for (int s = 1; s < SZ + 2; ++s) s_ws[s] += s_ws[s - 1];
+    for (int i = 1; i < SZ + 2; ++i) s_ws[i] += s_ws[i - 1];
   __syncthreads();
   for (int j = tid; j < BV; j += 256) {
     const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
-    const int s = s13 ? 4 * lz + 2 * ly + lx : lz + ly + lx;
-    s_list[s_ws[s] + atomicAdd(&s_fill[s], 1)] = (uint16_t)j;
+    const int sv = s13 ? 4 * lz + 2 * ly + lx : lz + ly + lx;
+    s_list[s_ws[sv] + atomicAdd(&s_fill[sv], 1)] = (uint16_t)j;
   }
   const int nwave = s13 ? SZ : (B0 - 1) + (B1 - 1) + (B2 - 1) + 1;
+  __syncthreads();
   if (*ds.err) return;
   const int R = 1 << (di.m - 1);
   const float sig = MODE ? __uint_as_float((unsigned int)(127 - mlp.s_in) << 23) : 1.0f;
   const float unsig = MODE ? __uint_as_float((unsigned int)(127 + mlp.s_in) << 23) : 1.0f;
   const T* ov = reinterpret_cast<const T*>(in + di.off_ov);
+  const bool vec_rows = VEC_OK && (g.n[2] % VW == 0) && ((reinterpret_cast<uintptr_t>(xo) & 15u) == 0);
   const long long nbx = (g.nb[2] + G - 1) / G;
   const long long nbricks = g.nb[0] * g.nb[1] * nbx;
-  const int team = tid / TS, t = tid % TS;
+  const int team = tid / TS, t = tid % TS, wt = t >> 5;
+  int* vp = s_vp + team * PD::PV;
+  T* xs = s_x + team * BV;
+  uint16_t* cd = s_cd + team * BV;
+  uint16_t* rk = s_rk + team * BV;
+  bool bad = false;
   for (long long brick = blockIdx.x; brick < nbricks; brick += gridDim.x) {
     const long long bxg = brick % nbx;
     const long long byz = brick / nbx;
@@ -347,108 +378,86 @@ __global__ void __launch_bounds__(256) k_recon(Geo g, const uint8_t* __restrict_
     const long long bx = bxg * G + team;
     const bool bvalid = bx < g.nb[2];
     const int e2 = bvalid ? (int)min((long long)B2, g.n[2] - bx * B2) : 0;
+    const bool bfull = e0 == B0 && e1 == B1 && e2 == B2;
     const long long b = (bz * g.nb[1] + by) * g.nb[2] + bx;
-    int* dq = s_dq + team * BV;
-    int* vc = s_vc + team * BV;
-    T* xs = s_x + team * BV;
-    uint16_t* cd = s_cd + team * BV;
-    uint16_t* rk = s_rk + team * BV;
-    // codes and the exclusive rank of each balance point in raster order
-    unsigned int nzero = 0;
+    // codes, padded border for truncated blocks, and balance-point ranks
+    unsigned int run = 0;
     if (bvalid) {
-      constexpr int SEG = (BV + TS - 1) / TS;
-      unsigned int cnt = 0;
-      for (int q = 0; q < SEG; ++q) {
-        const int j = t * SEG + q;
-        if (j < BV) {
-          const uint16_t v = ds.codes[b * BV + j];
-          cd[j] = v;
+      const uint4* src = reinterpret_cast<const uint4*>(ds.codes + b * BV);
+      for (int i = t; i < BV / 8; i += TS) reinterpret_cast<uint4*>(cd)[i] = src[i];
+      if (!bfull) {
+        for (int j = t; j < BV; j += TS) {
           const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
-          cnt += (j != 0 && lz < e0 && ly < e1 && lx < e2 && v == 0);
+          if (!(lz < e0 && ly < e1 && lx < e2)) vp[PD::at(lz, ly, lx)] = 0;
         }
       }
-      // team exclusive scan of cnt
-      const int lane = t & 31, wv = t >> 5;
-      unsigned int incl = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += y;
+    }
+    if (TS == 32) __syncwarp(); else __syncthreads();
+    constexpr int SEG = BV / NWT;  // contiguous codes per warp of the team
+    if (bvalid) {
+      for (int j0 = wt * SEG; j0 < (wt + 1) * SEG; j0 += 32) {
+        const int j = j0 + lane;
+        const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+        const bool f = j != 0 && (bfull || (lz < e0 && ly < e1 && lx < e2)) && cd[j] == 0;
+        const unsigned int bal = __ballot_sync(0xFFFFFFFFu, f);
+        rk[j] = (uint16_t)(run + __popc(bal & ((1u << lane) - 1u)));
+        run += __popc(bal);
       }
-      if (TS > 32) {
-        if (lane == 31) s_tsum[team][wv] = incl;
-      }
-      if (TS > 32) __syncthreads(); else __syncwarp();
-      unsigned int base = 0;
-      if (TS > 32)
-        for (int q = 0; q < wv; ++q) base += s_tsum[team][q];
-      unsigned int run = base + incl - cnt;
-      for (int q = 0; q < SEG; ++q) {
-        const int j = t * SEG + q;
-        if (j < BV) {
-          rk[j] = (uint16_t)run;
-          const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
-          run += (j != 0 && lz < e0 && ly < e1 && lx < e2 && cd[j] == 0);
-        }
-      }
-      unsigned int tot = incl;
-      if (TS > 32) {
-        tot = 0;
-        for (int q = 0; q < TS / 32; ++q) tot += s_tsum[team][q];
-      } else {
-        tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
-      }
-      nzero = tot;
-    } else if (TS > 32) {
-      __syncthreads();
+      if (NWT > 1 && lane == 0) s_wt[team][wt] = run;
     }
     __syncthreads();
+    unsigned int nzero = run;
+    if (NWT > 1 && bvalid) {
+      unsigned int base = 0, tot = 0;
+      for (int q = 0; q < NWT; ++q) {
+        if (q < wt) base += s_wt[team][q];
+        tot += s_wt[team][q];
+      }
+      if (base)
+        for (int j0 = wt * SEG; j0 < (wt + 1) * SEG; j0 += 32) rk[j0 + lane] += (uint16_t)base;
+      nzero = tot;
+    }
     const unsigned int no = bvalid ? *reinterpret_cast<const uint16_t*>(in + di.off_bn + 2ull * b) : 1u;
     const bool usen = bvalid && ((*reinterpret_cast<const unsigned int*>(in + di.off_bb + 4ull * b)) >> 31);
     const unsigned long long obase = bvalid ? ds.ooff[b] : 0ull;
-    if (bvalid && nzero + 1u != no && t == 0) s_bad = 1;
-    if (usen && !MODE && t == 0) s_bad = 1;
+    if (bvalid && (nzero + 1u != no || (usen && !MODE))) bad = true;
     // anchor
     if (bvalid && t == 0) {
       const T xa = ov[obase < di.n_out ? obase : 0];
       bool okk;
-      const int q = Num<T>::transform(xa, c, okk);
-      dq[0] = q;
-      vc[0] = 0;
+      s_da[team] = Num<T>::transform(xa, c, tb, okk);
+      vp[PD::at(0, 0, 0)] = 0;
       xs[0] = xa;
     }
-    if (TS > 32) __syncthreads(); else __syncwarp();
-    const int da = bvalid ? dq[0] : 0;
-    for (int s = 1; s < nwave; ++s) {
+    __syncthreads();
+    const int da = s_da[team];
+    for (int sw = 1; sw < nwave; ++sw) {
       if (bvalid) {
-        for (int idx = s_ws[s] + t; idx < s_ws[s + 1]; idx += TS) {
+        for (int idx = s_ws[sw] + t; idx < s_ws[sw + 1]; idx += TS) {
           const int j = s_list[idx];
           const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
-          if (!(lz < e0 && ly < e1 && lx < e2)) continue;
+          if (!bfull && !(lz < e0 && ly < e1 && lx < e2)) continue;
+          const int pj = PD::at(lz, ly, lx);
           const unsigned int code = cd[j];
           int q;
           if (code == 0) {
             unsigned long long oi = obase + 1ull + rk[j];
-            if (oi >= obase + no || oi >= di.n_out) { s_bad = 1; oi = obase; }
+            if (oi >= obase + no || oi >= di.n_out) { bad = true; oi = obase; }
             const T xv = ov[oi];
             bool okk;
-            q = Num<T>::transform(xv, c, okk);
+            q = Num<T>::transform(xv, c, tb, okk);
             xs[j] = xv;
           } else {
             long long pr = 0;
             bool done = false;
             if constexpr (MODE != 0) {
               if (usen) {
-                int inp[K > 0 ? K : 13];
+                constexpr int KK = K > 0 ? K : 13;
+                int inp[KK];
                 const int kk = K > 0 ? K : mlp.k;
 #pragma unroll
-                for (int si = 0; si < (K > 0 ? K : 13); ++si) {
-                  if (si < kk) {
-                    const int qz = lz + st_dz(kk, si), qy = ly + st_dy(kk, si), qx = lx + st_dx(kk, si);
-                    inp[si] = (qz >= 0 && qy >= 0 && qx >= 0 && qz < e0 && qy < e1 && qx < e2)
-                                  ? vc[(qz * B1 + qy) * B2 + qx] : 0;
-                  }
-                }
+                for (int si = 0; si < KK; ++si)
+                  inp[si] = si < kk ? vp[pj + PD::off(st_dz(kk, si), st_dy(kk, si), st_dx(kk, si))] : 0;
                 float p;
                 if constexpr (K > 0) p = mlp_fwd<K, H1, H2>(mlp, inp, sig, unsig);
                 else p = mlp_fwd_rt(mlp, inp, sig, unsig);
@@ -459,53 +468,63 @@ __global__ void __launch_bounds__(256) k_recon(Geo g, const uint8_t* __restrict_
             if (!done) {
               int acc = 0;
 #pragma unroll
-              for (int si = 0; si < 7; ++si) {
-                const int qz = lz + s7_dz(si), qy = ly + s7_dy(si), qx = lx + s7_dx(si);
-                acc += lz_w(7, si) * ((qz >= 0 && qy >= 0 && qx >= 0) ? vc[(qz * B1 + qy) * B2 + qx] : 0);
-              }
+              for (int si = 0; si < 7; ++si) acc += lz_w(7, si) * vp[pj + PD::off(s7_dz(si), s7_dy(si), s7_dx(si))];
               pr = acc;
             }
             const long long qq = (long long)da + pr + ((long long)code - R);
-            if (qq > 2147483647LL || qq < -2147483647LL) { s_bad = 1; q = 0; }
+            if (qq > 2147483647LL || qq < -2147483647LL) { bad = true; q = 0; }
             else q = (int)qq;
-            xs[j] = Num<T>::recon(q, c);
+            xs[j] = Num<T>::recon(q, c, tb);
           }
-          dq[j] = q;
-          vc[j] = clampv((long long)q - da);
+          vp[pj] = clampv((long long)q - da);
         }
       }
-      if (TS > 32) __syncthreads(); else __syncwarp();
+      if (TS == 32) __syncwarp(); else __syncthreads();
     }
     __syncthreads();
     // coalesced brick store
-    for (int e = tid; e < e0 * e1 * W; e += 256) {
-      const int r = e / W, col = e - r * W;
-      const int z = r / e1, y = r - z * e1;
-      xo[((z0 + z) * g.n[1] + (y0 + y)) * g.n[2] + x0 + col] = s_x[(col / B2) * BV + (z * B1 + y) * B2 + (col % B2)];
+    if (e0 == B0 && e1 == B1 && W == G * B2 && vec_rows) {
+      constexpr int RW = G * B2 / VW;
+      for (int e = tid; e < B0 * B1 * RW; e += 256) {
+        const int r = e / RW, cv = e % RW;
+        const int z = r / B1, y = r % B1;
+        T v[VW];
+#pragma unroll
+        for (int q = 0; q < VW; ++q) {
+          const int col = cv * VW + q;
+          v[q] = s_x[(col / B2) * BV + (z * B1 + y) * B2 + (col % B2)];
+        }
+        uint4 u;
+        memcpy(&u, v, 16);
+        reinterpret_cast<uint4*>(xo + ((z0 + z) * g.n[1] + (y0 + y)) * g.n[2] + x0)[cv] = u;
+      }
+    } else {
+      for (int e = tid; e < e0 * e1 * W; e += 256) {
+        const int r = e / W, col = e - r * W;
+        const int z = r / e1, y = r - z * e1;
+        xo[((z0 + z) * g.n[1] + (y0 + y)) * g.n[2] + x0 + col] = s_x[(col / B2) * BV + (z * B1 + y) * B2 + (col % B2)];
+      }
     }
     __syncthreads();
   }
+  if (bad) s_bad = 1;
+  __syncthreads();
   if (s_bad && tid == 0) atomicExch(ds.err, PC_ERR_CORRUPT);
-}
-
-template <int BV>
-size_t recon_smem(size_t ts) {
-  constexpr int G = DecShape<BV>::G;
-  return (size_t)G * BV * (4 + 4 + ts + 2 + 2) + (size_t)BV * 2 + 16;
 }
 
 template <typename T, int B0, int B1, int B2, int MODE, int K, int H1, int H2>
 static int launch_r(const uint8_t* in, const Geo& g, const DecInfo& di, const DecScratch& ds, const Mlp& mlp, T* out,
                     int nsm, cudaStream_t s) {
   constexpr int BV = B0 * B1 * B2;
+  constexpr bool WIDE = MODE != 0 && (K == 13 || K == 0);
   auto kern = k_recon<T, B0, B1, B2, MODE, K, H1, H2>;
-  const size_t sm = recon_smem<BV>(sizeof(T));
+  const size_t sm = recon_smem_bytes<BV, Pad<B0, B1, B2, WIDE>::PV, (int)sizeof(T)>();
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
     return PC_ERR_CUDA;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm);
   if (per_sm < 1) per_sm = 1;
-  constexpr int G = DecShape<BV>::G;
+  constexpr int G = BrickShape<BV>::G;
   const long long nbricks = g.nb[0] * g.nb[1] * ((g.nb[2] + G - 1) / G);
   long long grid = (long long)nsm * per_sm;
   if (grid > nbricks) grid = nbricks;
@@ -537,7 +556,7 @@ int launch_decompress(const uint8_t* in, const Geo& g, const DecInfo& di, const 
     k_dec_blockoff<<<nc, 256, 0, s>>>(g, in, di, ds);
   }
   const size_t sm_sorted = di.n_used <= (unsigned int)kSortedSmem ? 2ull * di.n_used : 0ull;
-  { ProfScope p(kStHuffDecode, s); k_huff_decode<<<(unsigned int)((g.nblocks + 127) / 128), 128, sm_sorted, s>>>(g, in, di, ds); }
+  { ProfScope p(kStHuffDecode, s); k_huff_decode<<<(unsigned int)((g.nblocks + 255) / 256), 256, sm_sorted, s>>>(g, in, di, ds); }
   if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
   const int b0 = g.b[0], b1 = g.b[1], b2 = g.b[2];
 #define PC_SHAPE(A, B, C) \

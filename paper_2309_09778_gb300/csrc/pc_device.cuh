@@ -50,52 +50,82 @@ struct Mlp {
 };
 
 // ---------------------------------------------------------------------------
-// log2 and 2^t.  Series from the mathematics: ln y = 2 atanh((y-1)/(y+1)) with
-// atanh s = s + s^3/3 + s^5/5 + ...; 2^f = exp(f ln 2) by its Taylor series.
-// Both run Horner's rule with fused multiply-adds.
+// log2 and 2^t, from the mathematics (no vendor math routines).
+//
+// Single precision uses P. T. P. Tang's table-driven method (ACM TOMS 16(4),
+// 1990 for the logarithm; ACM TOMS 15(2), 1989 for the exponential):
+//   log2 y = e + LOGR_i + log2(1 + r),  r = fma(m, RCP_i, -1),
+//     i = top 7 mantissa bits, c_0 = 1, c_i = 1 + (i + 1/2)/128,
+//     RCP_i = float(1/c_i), LOGR_i = float(-log2 RCP_i),
+//     log2(1 + r) = r (c1 + r (c2 + r (c3 + r c4))), c_k = (-1)^(k+1)/(k ln 2);
+//   2^t = 2^k EXP_j 2^f,  32 k + j = rint(32 t),  2^f = 1 + u + u^2/2 + u^3/6 + u^4/24,
+//     u = f ln 2, EXP_j = float(2^(j/32)).
+// The tables are generated on the device from the double-precision series
+// below (build_tabs) once per call.  Double precision sums the atanh and
+// Taylor series directly.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float dev_log2f(float y) {
-  const float sqrt2 = 0x1.6a09e6p+0f;   // sqrt(2) rounded to float
-  const float two_over_ln2 = 0x1.715476p+1f;
-  unsigned int b = __float_as_uint(y);
-  int e = (int)((b >> 23) & 0xFFu) - 127;
-  float m = __uint_as_float((b & 0x7FFFFFu) | 0x3F800000u);
-  if (m > sqrt2) {
-    m = __fmul_rn(m, 0.5f);
-    e += 1;
-  }
-  float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
-  float z = __fmul_rn(s, s);
-  float p = 1.0f / 9.0f;
-  p = __fmaf_rn(p, z, 1.0f / 7.0f);
-  p = __fmaf_rn(p, z, 1.0f / 5.0f);
-  p = __fmaf_rn(p, z, 1.0f / 3.0f);
-  p = __fmaf_rn(p, z, 1.0f);
-  float t = __fmul_rn(__fmul_rn(s, p), two_over_ln2);
-  return __fadd_rn(__int2float_rn(e), t);
-}
+struct Tabs {
+  float rcp[128];
+  float logr[128];
+  float ex[32];
+  float lc[4];
+};
 
 __device__ __forceinline__ float pow2_scale_f(int k) { return __uint_as_float((unsigned int)(k + 127) << 23); }
 
-__device__ __forceinline__ float dev_exp2f(float t) {
-  const float ln2 = 0x1.62e430p-1f;
+// Exact integer <-> float helpers without conversion instructions: adding
+// 1.5 * 2^23 puts rint(u) (round to nearest even, as IEEE addition rounds)
+// in the low mantissa bits for |u| < 2^22, and the inverse turns a small
+// integer into its float exactly.  Outside that range the conversion
+// instructions are used; both give the same values.
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+__device__ __forceinline__ float rint_to_int(float u, int& n) {
+  if (fabsf(u) < 4194304.0f) {
+    const float t = __fadd_rn(u, kMagic);
+    n = __float_as_int(t) - 0x4B400000;
+    return __fsub_rn(t, kMagic);
+  }
+  const float r = rintf(u);
+  n = __float2int_rn(r);
+  return r;
+}
+__device__ __forceinline__ float small_int_to_float(int n) {
+  if (n > -4194304 && n < 4194304) return __fsub_rn(__int_as_float(n + 0x4B400000), kMagic);
+  return __int2float_rn(n);
+}
+
+__device__ __forceinline__ float dev_log2f(float y, const Tabs& tb) {
+  const unsigned int b = __float_as_uint(y);
+  const int e = (int)((b >> 23) & 0xFFu) - 127;
+  const int i = (int)((b >> 16) & 0x7Fu);
+  const float m = __uint_as_float((b & 0x7FFFFFu) | 0x3F800000u);
+  const float r = __fmaf_rn(m, tb.rcp[i], -1.0f);
+  float p = __fmaf_rn(tb.lc[3], r, tb.lc[2]);
+  p = __fmaf_rn(p, r, tb.lc[1]);
+  p = __fmaf_rn(p, r, tb.lc[0]);
+  p = __fmul_rn(p, r);
+  const float t = __fadd_rn(tb.logr[i], p);
+  return __fadd_rn(__fsub_rn(__int_as_float(e + 0x4B400000), kMagic), t);
+}
+
+__device__ __forceinline__ float dev_exp2f(float t, const Tabs& tb) {
   t = fminf(fmaxf(t, -300.0f), 300.0f);
-  float nf = rintf(t);
-  int k = __float2int_rn(nf);
-  float f = __fsub_rn(t, nf);
-  float u = __fmul_rn(f, ln2);
-  float p = 1.0f / 5040.0f;
-  p = __fmaf_rn(p, u, 1.0f / 720.0f);
-  p = __fmaf_rn(p, u, 1.0f / 120.0f);
-  p = __fmaf_rn(p, u, 1.0f / 24.0f);
-  p = __fmaf_rn(p, u, 1.0f / 6.0f);
+  const float t32 = __fadd_rn(__fmul_rn(t, 32.0f), kMagic);   // |32 t| <= 9600
+  const int N = __float_as_int(t32) - 0x4B400000;
+  const float nf = __fsub_rn(t32, kMagic);
+  const int j = N & 31;
+  const int k = (N - j) / 32;
+  const float f = __fsub_rn(t, __fmul_rn(nf, 0.03125f));
+  const float u = __fmul_rn(f, 0x1.62e430p-1f);
+  float p = __fmaf_rn(1.0f / 24.0f, u, 1.0f / 6.0f);
   p = __fmaf_rn(p, u, 0.5f);
   p = __fmaf_rn(p, u, 1.0f);
   p = __fmaf_rn(p, u, 1.0f);
-  int k1 = k / 3;
-  int k2 = (k - k1) / 2;
-  int k3 = k - k1 - k2;
-  return __fmul_rn(__fmul_rn(__fmul_rn(p, pow2_scale_f(k1)), pow2_scale_f(k2)), pow2_scale_f(k3));
+  const float v = __fmul_rn(tb.ex[j], p);
+  const int k1 = k / 3;
+  const int k2 = (k - k1) / 2;
+  const int k3 = k - k1 - k2;
+  return __fmul_rn(__fmul_rn(__fmul_rn(v, pow2_scale_f(k1)), pow2_scale_f(k2)), pow2_scale_f(k3));
 }
 
 __device__ __forceinline__ double pow2_scale_d(int k) {
@@ -148,6 +178,24 @@ __device__ inline double dev_exp2d(double t) {
   return __dmul_rn(__dmul_rn(__dmul_rn(p, pow2_scale_d(k1)), pow2_scale_d(k2)), pow2_scale_d(k3));
 }
 
+// Table generation: entry i is computed by thread i of the calling block.
+__device__ inline void build_tabs_entry(Tabs* tb, int i) {
+  if (i < 128) {
+    const double c = i == 0 ? 1.0 : 1.0 + ((double)i + 0.5) / 128.0;
+    const float r = __double2float_rn(__ddiv_rn(1.0, c));
+    tb->rcp[i] = r;
+    tb->logr[i] = __double2float_rn(-dev_log2d((double)r));
+  }
+  if (i < 32) tb->ex[i] = __double2float_rn(dev_exp2d((double)i / 32.0));
+  if (i < 4) {
+    const double ln2 = 0x1.62e42fefa39efp-1;
+    const double v = i == 0 ? __ddiv_rn(1.0, ln2)
+                            : (i == 1 ? __ddiv_rn(-1.0, 2.0 * ln2)
+                                      : (i == 2 ? __ddiv_rn(1.0, 3.0 * ln2) : __ddiv_rn(-1.0, 4.0 * ln2)));
+    tb->lc[i] = __double2float_rn(v);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Transform (Eq. 6, 7, 12) and its inverse.  Code classes: q <= Zq is zero,
 // Zq < q <= S positive, q > S negative.
@@ -157,42 +205,41 @@ __device__ __forceinline__ int code_class(int q, const State& c) { return q <= c
 template <typename T> struct Num;
 
 template <> struct Num<float> {
-  static __device__ __forceinline__ float recon(int q, const State& c) {
-    int cl = code_class(q, c);
+  static __device__ __forceinline__ float recon(int q, const State& c, const Tabs& tb) {
+    const int cl = code_class(q, c);
     if (cl == 0) return 0.0f;
-    int n = q - (cl == 1 ? c.Kp : c.Kn);
-    float a = dev_exp2f(__fmul_rn(__int2float_rn(n), c.step32));
+    const int n = q - (cl == 1 ? c.Kp : c.Kn);
+    const float a = dev_exp2f(__fmul_rn(small_int_to_float(n), c.step32), tb);
     return cl == 1 ? a : -a;
   }
   // code of x and whether it reproduces x within the bound
-  static __device__ __forceinline__ int transform(float x, const State& c, bool& ok) {
-    unsigned int b = __float_as_uint(x);
-    float a = fabsf(x);
+  static __device__ __forceinline__ int transform(float x, const State& c, const Tabs& tb, bool& ok) {
+    const unsigned int b = __float_as_uint(x);
+    const float a = fabsf(x);
     if (b == 0u) { ok = true; return c.Zq; }
     if (a < 0x1p-126f) { ok = false; return c.Zq; }
-    float l = dev_log2f(a);
-    float nf = rintf(__fmul_rn(l, c.inv32));
-    int n = __float2int_rn(nf);
-    bool pos = x > 0.0f;
-    int q = n + (pos ? c.Kp : c.Kn);
+    const float l = dev_log2f(a, tb);
+    int n;
+    const float nf = rint_to_int(__fmul_rn(l, c.inv32), n);
+    const bool pos = x > 0.0f;
+    const int q = n + (pos ? c.Kp : c.Kn);
     if (code_class(q, c) != (pos ? 1 : 2)) { ok = false; return q; }
-    float r = dev_exp2f(__fmul_rn(__int2float_rn(n), c.step32));
-    float err = fabsf(__fsub_rn(r, a));
+    const float r = dev_exp2f(__fmul_rn(nf, c.step32), tb);
+    const float err = fabsf(__fsub_rn(r, a));
     ok = err <= __fmul_rd(c.ebdn32, a);  // exact: a <= RD(p) iff a <= p for a float a
     return q;
   }
-  static __device__ __forceinline__ bool is_normal_mag(float a) { return a >= 0x1p-126f; }
 };
 
 template <> struct Num<double> {
-  static __device__ __forceinline__ double recon(int q, const State& c) {
+  static __device__ __forceinline__ double recon(int q, const State& c, const Tabs&) {
     int cl = code_class(q, c);
     if (cl == 0) return 0.0;
     int n = q - (cl == 1 ? c.Kp : c.Kn);
     double a = dev_exp2d(__dmul_rn((double)n, c.stepd));
     return cl == 1 ? a : -a;
   }
-  static __device__ __forceinline__ int transform(double x, const State& c, bool& ok) {
+  static __device__ __forceinline__ int transform(double x, const State& c, const Tabs&, bool& ok) {
     unsigned long long b = (unsigned long long)__double_as_longlong(x);
     double a = fabs(x);
     if (b == 0ull) { ok = true; return c.Zq; }
@@ -233,6 +280,8 @@ __host__ __device__ constexpr int lz_w(int k, int i) {
 __device__ __forceinline__ int clampv(long long v) {
   return (int)(v > kVclamp ? kVclamp : (v < -kVclamp ? -kVclamp : v));
 }
+// the same clamp for a difference of two codes, both within +-2^30
+__device__ __forceinline__ int clampd(int q, int da) { return min(max(q - da, -kVclamp), kVclamp); }
 
 __device__ __forceinline__ int bitlen_u(unsigned int a) { return 32 - __clz(a); }
 

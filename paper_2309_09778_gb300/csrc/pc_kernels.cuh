@@ -15,6 +15,39 @@ struct Geo {
   long long nchunks;
 };
 
+// Bricks: a CTA of 256 threads handles G consecutive blocks along x, one
+// team of 256/G threads per block, at most 4096 points per brick.
+template <int BV>
+struct BrickShape {
+  static constexpr int G = BV <= 512 ? 8 : (BV <= 1024 ? 4 : (BV <= 2048 ? 2 : 1));
+  static constexpr int TS = 256 / G;
+  static constexpr int PPT = (BV + TS - 1) / TS;
+};
+
+template <int B0, int B1, int B2, bool WIDE>
+struct Pad {
+  static constexpr int P1 = B1 + (WIDE ? 2 : 1);
+  static constexpr int P2 = B2 + (WIDE ? 2 : 1);
+  static constexpr int PV = (B0 + 1) * P1 * P2;
+  static __device__ __forceinline__ int at(int lz, int ly, int lx) { return ((lz + 1) * P1 + (ly + 1)) * P2 + (lx + 1); }
+  static constexpr int off(int dz, int dy, int dx) { return (dz * P1 + dy) * P2 + dx; }
+};
+
+// Block with a zero border: stencil neighbours outside the block read 0
+// without bounds checks.  WIDE adds the +1 border in y and x that the
+// 13-point stencil reaches.
+template <int TS>
+__device__ __forceinline__ int team_sum(int v, int* slot) {
+  if constexpr (TS == 32) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+  } else {
+    atomicAdd(slot, v);
+    return 0;  // caller reads *slot after a barrier
+  }
+}
+
 // Values the header needs that only the host knows.
 struct HdrInfo {
   int dtype, pred, stencil, h1, h2, m, s_in, nw;
@@ -72,11 +105,12 @@ __device__ __forceinline__ void st_u64(uint8_t* p, unsigned long long v) {
 __host__ __device__ inline unsigned long long al16(unsigned long long x) { return (x + 15ull) & ~15ull; }
 
 template <typename T>
-int launch_stats_consts(const void* x, unsigned long long n, State* st, unsigned long long* hist, int nsym,
-                        double eb, int nsm, cudaStream_t s);
+int launch_stats_consts(const void* x, unsigned long long n, State* st, Tabs* tabs, unsigned long long* hist,
+                        int nsym, double eb, int nsm, cudaStream_t s);
 template <typename T>
-int launch_compress(const void* x, const Geo& g, const State* st, uint16_t* codes, uint8_t* nnflag, uint32_t* nout,
-                    unsigned long long* hist, int m, int mode, const Mlp& mlp, int nsm, cudaStream_t s);
+int launch_compress(const void* x, const Geo& g, const State* st, const Tabs* tabs, uint16_t* codes, uint8_t* nnflag,
+                    uint32_t* nout, unsigned long long* hist, int m, int mode, const Mlp& mlp, int nsm,
+                    cudaStream_t s);
 int launch_codebook(const unsigned long long* hist, int m, uint8_t* lens, uint32_t* cw, State* st,
                     const HuffScratch& hs, uint8_t* out, const Geo& g, const HdrInfo& hi, cudaStream_t s);
 template <typename T>
@@ -107,8 +141,26 @@ struct DecScratch {
   unsigned long long* boff;    // [nblocks]
   unsigned long long* ooff;    // [nblocks]
   uint16_t* codes;             // [nblocks * bvol]
+  Tabs* ftab;                  // log2 / 2^t tables
   int* err;                    // device error word
 };
+// Training buffers (all in the caller's workspace).
+struct TrainBufs {
+  unsigned int *cnt_t, *cnt_v;
+  unsigned long long *off_t, *off_v;
+  int *tin, *ttg, *vin, *vtg;
+  uint8_t *tus, *vus;
+  float* w;
+  const float *lrs, *lams;
+  unsigned long long* costs;
+  void* ctl;
+  unsigned long long cap_t, cap_v;
+};
+size_t train_ctl_bytes();
+template <typename T>
+int launch_train(const T* x, const Geo& g, const State* st, const Tabs* tabs, const TrainBufs& tb, int k, int h1,
+                 int h2, int m, int nmodels, unsigned long long seed, unsigned int thr32, cudaStream_t s);
+
 template <typename T>
 int launch_decompress(const uint8_t* in, const Geo& g, const DecInfo& di, const DecScratch& ds, const Mlp& mlp,
                       T* out, int nsm, cudaStream_t s);

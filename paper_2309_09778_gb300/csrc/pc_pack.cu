@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(1024) k_chunkscan(Geo g, const unsigned long l
 template <typename T>
 __global__ void __launch_bounds__(256) k_pack(Geo g, const T* __restrict__ x, const uint16_t* __restrict__ codes,
                                               const uint32_t* __restrict__ nout, const uint32_t* __restrict__ bbits,
-                                              const uint8_t* __restrict__ lens, const uint32_t* __restrict__ cw,
+                                              const uint32_t* __restrict__ cwl,
                                               const unsigned long long* __restrict__ chunk_bits,
                                               const unsigned long long* __restrict__ chunk_boff,
                                               const unsigned long long* __restrict__ chunk_ooff,
@@ -251,6 +251,7 @@ __global__ void __launch_bounds__(256) k_pack(Geo g, const T* __restrict__ x, co
   const unsigned long long off_ov = st->off_ov, off_st = st->off_st;
   T* ov = reinterpret_cast<T*>(out + off_ov);
   const unsigned long long obase = chunk_ooff[c];
+  const int b12 = g.b[1] * g.b[2];
   for (int i = wid; i < nb; i += 8) {
     const long long b = b0 + i;
     long long bz, by, bx;
@@ -263,38 +264,59 @@ __global__ void __launch_bounds__(256) k_pack(Geo g, const T* __restrict__ x, co
     if (lane == 0) ov[op] = x[(z0 * g.n[1] + y0) * g.n[2] + x0];
     op += 1;
     const uint16_t* cb = codes + b * g.bvol;
-    const int b12 = g.b[1] * g.b[2];
-    for (int j0 = 0; j0 < g.bvol; j0 += 32) {
-      const int j = j0 + lane;
-      const bool valid = j < g.bvol && slot_valid(g, j, e0, e1, e2, full);
-      const unsigned int cd = valid ? cb[j] : 0u;
-      const unsigned int L = valid ? lens[cd] : 0u;
-      unsigned int incl = L;
+    // each lane packs 8 consecutive codes (one 16-byte load)
+    for (int j0 = 0; j0 < g.bvol; j0 += 256) {
+      const int jl = j0 + 8 * lane;
+      unsigned int cd[8];
+      if (jl + 8 <= g.bvol) {
+        const uint4 v = *reinterpret_cast<const uint4*>(cb + jl);
+        cd[0] = v.x & 0xFFFFu; cd[1] = v.x >> 16; cd[2] = v.y & 0xFFFFu; cd[3] = v.y >> 16;
+        cd[4] = v.z & 0xFFFFu; cd[5] = v.z >> 16; cd[6] = v.w & 0xFFFFu; cd[7] = v.w >> 16;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) cd[q] = 0u;
+      }
+      unsigned int ent[8];
+      unsigned int lbits = 0, louts = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int j = jl + q;
+        const bool valid = j < g.bvol && slot_valid(g, j, e0, e1, e2, full);
+        ent[q] = valid ? cwl[cd[q]] : 0u;   // (length << 24) | code word
+        lbits += ent[q] >> 24;
+        louts += (valid && cd[q] == 0u) ? 1u : 0u;
+      }
+      unsigned int ib = lbits, io = louts;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += y;
+        const unsigned int yb = __shfl_up_sync(0xFFFFFFFFu, ib, o);
+        const unsigned int yo = __shfl_up_sync(0xFFFFFFFFu, io, o);
+        if (lane >= o) { ib += yb; io += yo; }
       }
-      const unsigned int tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
-      if (L) {
-        const unsigned int p = pos + incl - L;
-        const unsigned int wv = cw[cd];
-        const unsigned int wi = p >> 5, bo = p & 31u;
-        if (bo + L <= 32u) {
-          atomicOr(&s_words[wi], wv << (32u - bo - L));
-        } else {
-          atomicOr(&s_words[wi], wv >> (bo + L - 32u));
-          atomicOr(&s_words[wi + 1], wv << (64u - bo - L));
+      unsigned int p = pos + ib - lbits;
+      unsigned long long o2 = op + (io - louts);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const unsigned int L = ent[q] >> 24, wv = ent[q] & 0xFFFFFFu;
+        if (L) {
+          const unsigned int wi = p >> 5, bo = p & 31u;
+          if (bo + L <= 32u) {
+            atomicOr(&s_words[wi], wv << (32u - bo - L));
+          } else {
+            atomicOr(&s_words[wi], wv >> (bo + L - 32u));
+            atomicOr(&s_words[wi + 1], wv << (64u - bo - L));
+          }
+          p += L;
+        }
+        const int j = jl + q;
+        if (j < g.bvol && cd[q] == 0u && slot_valid(g, j, e0, e1, e2, full)) {
+          const int lz = j / b12, r = j - lz * b12, ly = r / g.b[2], lx = r - ly * g.b[2];
+          ov[o2] = x[((z0 + lz) * g.n[1] + (y0 + ly)) * g.n[2] + x0 + lx];
+          ++o2;
         }
       }
-      pos += tot;
-      const bool isout = valid && cd == 0u;
-      const unsigned int bal = __ballot_sync(0xFFFFFFFFu, isout);
-      if (isout) {
-        const int lz = j / b12, r = j - lz * b12, ly = r / g.b[2], lx = r - ly * g.b[2];
-        ov[op + __popc(bal & ((1u << lane) - 1u))] = x[((z0 + lz) * g.n[1] + (y0 + ly)) * g.n[2] + x0 + lx];
-      }
-      op += __popc(bal);
+      pos += __shfl_sync(0xFFFFFFFFu, ib, 31);
+      op += __shfl_sync(0xFFFFFFFFu, io, 31);
     }
   }
   __syncthreads();
@@ -321,7 +343,7 @@ int launch_pack(const T* x, const Geo& g, const uint16_t* codes, const uint8_t* 
   const size_t smem = (size_t)g.ch * 8 + words * 4;
   if (cudaFuncSetAttribute(k_pack<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return PC_ERR_CUDA;
-  { ProfScope p(kStPack, s); k_pack<T><<<nc, 256, smem, s>>>(g, x, codes, nout, bbits, lens, cw, chunk_bits, chunk_boff, chunk_ooff, st, out); }
+  { ProfScope p(kStPack, s); k_pack<T><<<nc, 256, smem, s>>>(g, x, codes, nout, bbits, cw, chunk_bits, chunk_boff, chunk_ooff, st, out); }
   return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
 template int launch_pack<float>(const float*, const Geo&, const uint16_t*, const uint8_t*, const uint32_t*,

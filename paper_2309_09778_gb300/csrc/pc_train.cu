@@ -1,0 +1,448 @@
+// a3: the training phase (Section IV.C) on the device.
+//
+//   k_samp_count   per block: how many points the hash draws for training /
+//                  validation (non-anchor points, local raster order);
+//   k_samp_scan    exclusive scans of those counts (one CTA);
+//   k_samp_gather  per block: transform, stencil inputs, target and the
+//                  "one sign class" use flag of every drawn point, written
+//                  in block order;
+//   k_in_shift     input scale s (sum of min(t^2, 2^40) over used samples);
+//   k_init_w       Lorenzo-equal initial weights (Section IV.B);
+//   k_train        one CTA per (lr, lambda) model: one epoch of minibatch SGD,
+//                  every gradient a pairwise tree sum over the 256 rows
+//                  (xor butterfly in each warp, then warp pairs);
+//   k_val          residual bit cost of every model and of Lorenzo on the
+//                  validation samples;
+//   k_choose       the cheapest model (Lorenzo unless strictly beaten).
+#include "pc_kernels.cuh"
+#include "pc_profile.cuh"
+
+namespace pc {
+
+__device__ __forceinline__ unsigned long long dev_mix64(unsigned long long seed, unsigned long long i) {
+  // SplitMix64 output function on state seed + (i + 1) * golden gamma
+  unsigned long long z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+struct TrainCtl {
+  unsigned long long ntrain, nval, s2;
+  unsigned long long nused;
+  int s_in, chosen, err, pad;
+};
+
+// one warp per block
+__global__ void __launch_bounds__(256) k_samp_count(Geo g, unsigned long long seed, unsigned int thr32,
+                                                    unsigned int* cnt_t, unsigned int* cnt_v) {
+  const long long b = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= g.nblocks) return;
+  const long long bx = b % g.nb[2], t = b / g.nb[2], by = t % g.nb[1], bz = t / g.nb[1];
+  const int e0 = (int)min((long long)g.b[0], g.n[0] - bz * g.b[0]);
+  const int e1 = (int)min((long long)g.b[1], g.n[1] - by * g.b[1]);
+  const int e2 = (int)min((long long)g.b[2], g.n[2] - bx * g.b[2]);
+  unsigned int ct = 0, cv = 0;
+  for (int j = lane; j < e0 * e1 * e2; j += 32) {
+    if (j == 0) continue;
+    const int lz = j / (e1 * e2), r = j % (e1 * e2), ly = r / e2, lx = r % e2;
+    const unsigned long long lin =
+        ((unsigned long long)(bz * g.b[0] + lz) * g.n[1] + (by * g.b[1] + ly)) * g.n[2] + bx * g.b[2] + lx;
+    const unsigned long long h = dev_mix64(seed, lin);
+    if ((unsigned int)(h >> 32) < thr32) {
+      if ((unsigned int)h % 10u < 2u) ++cv; else ++ct;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ct += __shfl_xor_sync(0xFFFFFFFFu, ct, o);
+    cv += __shfl_xor_sync(0xFFFFFFFFu, cv, o);
+  }
+  if (lane == 0) { cnt_t[b] = ct; cnt_v[b] = cv; }
+}
+
+// exclusive scans of both count arrays, one CTA (in place: counts -> offsets)
+__global__ void __launch_bounds__(1024) k_samp_scan(long long nblocks, unsigned int* cnt_t, unsigned int* cnt_v,
+                                                    unsigned long long* off_t, unsigned long long* off_v,
+                                                    TrainCtl* ctl) {
+  __shared__ unsigned long long s_w[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long per = (nblocks + nt - 1) / nt;
+  const long long lo = min(nblocks, tid * per), hi = min(nblocks, lo + per);
+  unsigned long long a = 0, bsum = 0;
+  for (long long i = lo; i < hi; ++i) { a += cnt_t[i]; bsum += cnt_v[i]; }
+  unsigned long long ta, tb;
+  unsigned long long pa = cta_exscan<unsigned long long>(a, s_w, ta);
+  unsigned long long pb = cta_exscan<unsigned long long>(bsum, s_w, tb);
+  for (long long i = lo; i < hi; ++i) {
+    off_t[i] = pa;
+    off_v[i] = pb;
+    pa += cnt_t[i];
+    pb += cnt_v[i];
+  }
+  if (tid == 0) { ctl->ntrain = ta; ctl->nval = tb; }
+}
+
+// one warp per block; per-warp shared memory holds the block's codes
+template <typename T>
+__global__ void __launch_bounds__(128) k_samp_gather(const T* __restrict__ x, Geo g, const State* __restrict__ st,
+                                                     const Tabs* __restrict__ tabs, unsigned long long seed,
+                                                     unsigned int thr32, int k, const unsigned long long* off_t,
+                                                     const unsigned long long* off_v, int* tin, int* ttg,
+                                                     uint8_t* tus, int* vin, int* vtg, uint8_t* vus,
+                                                     const TrainCtl* ctl, unsigned long long cap_t,
+                                                     unsigned long long cap_v) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Tabs& tb = *reinterpret_cast<Tabs*>(smem);
+  int* s_dq = reinterpret_cast<int*>(smem + sizeof(Tabs)) + (threadIdx.x >> 5) * g.bvol;
+  for (int i = threadIdx.x; i < (int)(sizeof(Tabs) / 4); i += blockDim.x)
+    reinterpret_cast<float*>(&tb)[i] = reinterpret_cast<const float*>(tabs)[i];
+  __syncthreads();
+  if (st->err || ctl->ntrain > cap_t || ctl->nval > cap_v) return;
+  State c;
+  c.Kp = st->Kp; c.Kn = st->Kn; c.Zq = st->Zq; c.S = st->S;
+  c.step32 = st->step32; c.inv32 = st->inv32; c.ebdn32 = st->ebdn32;
+  c.stepd = st->stepd; c.invd = st->invd; c.ebdnd = st->ebdnd;
+  const long long b = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= g.nblocks) return;
+  const long long bx = b % g.nb[2], t = b / g.nb[2], by = t % g.nb[1], bz = t / g.nb[1];
+  const int e0 = (int)min((long long)g.b[0], g.n[0] - bz * g.b[0]);
+  const int e1 = (int)min((long long)g.b[1], g.n[1] - by * g.b[1]);
+  const int e2 = (int)min((long long)g.b[2], g.n[2] - bx * g.b[2]);
+  const int np = e0 * e1 * e2;
+  const long long z0 = bz * g.b[0], y0 = by * g.b[1], x0 = bx * g.b[2];
+  for (int j = lane; j < np; j += 32) {
+    const int lz = j / (e1 * e2), r = j % (e1 * e2), ly = r / e2, lx = r % e2;
+    bool okk;
+    s_dq[j] = Num<T>::transform(x[((z0 + lz) * g.n[1] + (y0 + ly)) * g.n[2] + x0 + lx], c, tb, okk);
+  }
+  __syncwarp();
+  const int da = s_dq[0];
+  const int ca = code_class(da, c);
+  unsigned long long ot = off_t[b], ovv = off_v[b];
+  for (int j0 = 0; j0 < np; j0 += 32) {
+    const int j = j0 + lane;
+    bool selt = false, selv = false;
+    unsigned long long h = 0;
+    int lz = 0, ly = 0, lx = 0;
+    if (j < np && j != 0) {
+      lz = j / (e1 * e2);
+      const int r = j % (e1 * e2);
+      ly = r / e2;
+      lx = r % e2;
+      const unsigned long long lin = ((unsigned long long)(z0 + lz) * g.n[1] + (y0 + ly)) * g.n[2] + x0 + lx;
+      h = dev_mix64(seed, lin);
+      if ((unsigned int)(h >> 32) < thr32) {
+        if ((unsigned int)h % 10u < 2u) selv = true; else selt = true;
+      }
+    }
+    const unsigned int bt = __ballot_sync(0xFFFFFFFFu, selt), bv = __ballot_sync(0xFFFFFFFFu, selv);
+    if (selt || selv) {
+      const unsigned long long slot = selt ? ot + __popc(bt & ((1u << lane) - 1u)) : ovv + __popc(bv & ((1u << lane) - 1u));
+      int* inp = selt ? tin + slot * (unsigned long long)k : vin + slot * (unsigned long long)k;
+      const int cp = code_class(s_dq[j], c);
+      bool use = cp != 0 && cp == ca;
+      for (int i = 0; i < k; ++i) {
+        const int qz = lz + st_dz(k, i), qy = ly + st_dy(k, i), qx = lx + st_dx(k, i);
+        int v = 0;
+        if (qz >= 0 && qy >= 0 && qx >= 0 && qz < e0 && qy < e1 && qx < e2) {
+          const int q = s_dq[(qz * e1 + qy) * e2 + qx];
+          v = clampd(q, da);
+          if (code_class(q, c) != cp) use = false;
+        }
+        inp[i] = v;
+      }
+      const int tv = clampd(s_dq[j], da);
+      if (selt) { ttg[slot] = tv; tus[slot] = use ? 1 : 0; }
+      else { vtg[slot] = tv; vus[slot] = use ? 1 : 0; }
+    }
+    ot += __popc(bt);
+    ovv += __popc(bv);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_in_shift(const int* __restrict__ ttg, const uint8_t* __restrict__ tus,
+                                                  TrainCtl* ctl) {
+  const unsigned long long n = ctl->ntrain;
+  unsigned long long s2 = 0, nu = 0;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    if (!tus[i]) continue;
+    const long long t = ttg[i];
+    const unsigned long long a = (unsigned long long)(t < 0 ? -t : t);
+    unsigned long long q = a * a;
+    if (q > (1ull << 40)) q = 1ull << 40;
+    s2 += q;
+    ++nu;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s2 += __shfl_xor_sync(0xFFFFFFFFu, s2, o);
+    nu += __shfl_xor_sync(0xFFFFFFFFu, nu, o);
+  }
+  if ((threadIdx.x & 31) == 0 && (s2 || nu)) {
+    atomicAdd(&ctl->s2, s2);
+    atomicAdd(&ctl->nused, nu);
+  }
+}
+
+// initial weights (Section IV.B): Lorenzo pair in hidden units 0 and 1, carried
+// through the second hidden layer by [1,-1], [-1,1]; output (c, -c) with
+// c = 1/(1+alpha)^L; other hidden-layer weights from the hash, others zero.
+__global__ void k_init_w(float* w, int nmodels, int k, int h1, int h2, unsigned long long seed, TrainCtl* ctl) {
+  const int nw = h1 * k + h1 + (h2 > 0 ? h2 * h1 + h2 : 0) + (h2 > 0 ? h2 : h1) + 1;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p == 0) {
+    const unsigned long long s2 = ctl->s2, nu = ctl->nused;
+    int s = 0;
+    if (nu) while (s < 30 && (s2 >> (2 * s)) >= nu) ++s;
+    ctl->s_in = s;
+  }
+  if (p >= nw) return;
+  auto noise = [&](unsigned long long ctr) {
+    return __fmul_rn((float)((int)(dev_mix64(seed, ctr) >> 40) - 8388608), 0x1p-33f);
+  };
+  float v = 0.0f;
+  const float a1 = __fadd_rn(1.0f, kAlpha);
+  if (p < h1 * k) {
+    const int j = p / k, i = p % k;
+    if (j < 2 && h1 >= 2) v = (float)(j == 0 ? lz_w(k, i) : -lz_w(k, i));
+    else v = noise((unsigned long long)p);
+  } else if (h2 > 0 && p >= h1 * k + h1 && p < h1 * k + h1 + h2 * h1) {
+    const int q = p - (h1 * k + h1), j = q / h1, i = q % h1;
+    if (j < 2) v = (i == j) ? 1.0f : ((i < 2) ? -1.0f : 0.0f);
+    else v = noise((unsigned long long)(h1 * k + q));
+  } else {
+    const int p3 = h1 * k + h1 + (h2 > 0 ? h2 * h1 + h2 : 0);
+    const float cc = h2 > 0 ? __fdiv_rn(1.0f, __fmul_rn(a1, a1)) : __fdiv_rn(1.0f, a1);
+    if (p == p3) v = cc;
+    else if (p == p3 + 1) v = -cc;
+  }
+  for (int m = 0; m < nmodels; ++m) w[(size_t)m * nw + p] = v;
+}
+
+// Pairwise tree over the block's 256 rows: xor butterfly inside each warp
+// (lane 0 ends with ((r0+r1)+(r2+r3))+...), then the eight warp sums pairwise.
+__device__ __forceinline__ float warp_tree(float v) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) v = __fadd_rn(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+  return v;
+}
+
+template <int K, int H1, int H2>
+__global__ void __launch_bounds__(256) k_train(const int* __restrict__ tin, const int* __restrict__ ttg,
+                                               const uint8_t* __restrict__ tus, float* __restrict__ wbuf,
+                                               const float* __restrict__ lrs, const float* __restrict__ lams,
+                                               const TrainCtl* __restrict__ ctl) {
+  constexpr int HL = H2 > 0 ? H2 : H1;
+  constexpr int NW = H1 * K + H1 + (H2 > 0 ? H2 * H1 + H2 : 0) + HL + 1;
+  constexpr int OB1 = H1 * K, OW2 = OB1 + H1, OB2 = OW2 + H2 * H1, OW3 = H2 > 0 ? OB2 + H2 : OW2;
+  extern __shared__ __align__(16) float sm[];
+  float* w = sm;            // NW
+  float* part = sm + NW;    // 8 * NW warp sums
+  const int model = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  float* wm = wbuf + (size_t)model * NW;
+  for (int p = tid; p < NW; p += 256) w[p] = wm[p];
+  const float lr = lrs[model], lam2 = __fadd_rn(lams[model], lams[model]);
+  const int s_in = ctl->s_in;
+  const float sig = __uint_as_float((unsigned int)(127 - s_in) << 23);
+  const unsigned long long n = ctl->ntrain;
+  __syncthreads();
+  for (unsigned long long s0 = 0; s0 < n; s0 += 256) {
+    const int B = (int)((n - s0) < 256ull ? (n - s0) : 256ull);
+    const bool row = tid < B;
+    float u[K], z1[H1], a1[H1], z2[H2 > 0 ? H2 : 1], a2[H2 > 0 ? H2 : 1], d1[H1], d2[H2 > 0 ? H2 : 1];
+    float go = 0.0f;
+    if (row) {
+      const unsigned long long r = s0 + tid;
+#pragma unroll
+      for (int i = 0; i < K; ++i) u[i] = __fmul_rn(small_int_to_float(tin[r * K + i]), sig);
+#pragma unroll
+      for (int j = 0; j < H1; ++j) {
+        float acc = w[OB1 + j];
+#pragma unroll
+        for (int i = 0; i < K; ++i) acc = __fmaf_rn(w[j * K + i], u[i], acc);
+        z1[j] = acc;
+        a1[j] = acc >= 0.0f ? acc : __fmul_rn(acc, kAlpha);
+      }
+      if constexpr (H2 > 0) {
+#pragma unroll
+        for (int j = 0; j < H2; ++j) {
+          float acc = w[OB2 + j];
+#pragma unroll
+          for (int i = 0; i < H1; ++i) acc = __fmaf_rn(w[OW2 + j * H1 + i], a1[i], acc);
+          z2[j] = acc;
+          a2[j] = acc >= 0.0f ? acc : __fmul_rn(acc, kAlpha);
+        }
+      }
+      float o = w[OW3 + HL];
+#pragma unroll
+      for (int j = 0; j < HL; ++j) o = __fmaf_rn(w[OW3 + j], H2 > 0 ? a2[j] : a1[j], o);
+      const float tt = __fmul_rn(small_int_to_float(ttg[r]), sig);
+      const float ginv = __fdiv_rn(2.0f, (float)B);
+      go = tus[r] ? __fmul_rn(__fsub_rn(o, tt), ginv) : 0.0f;
+      if constexpr (H2 > 0) {
+#pragma unroll
+        for (int j = 0; j < H2; ++j) {
+          const float q = __fmul_rn(go, w[OW3 + j]);
+          d2[j] = z2[j] >= 0.0f ? q : __fmul_rn(q, kAlpha);
+        }
+#pragma unroll
+        for (int i = 0; i < H1; ++i) {
+          float sacc = 0.0f;
+#pragma unroll
+          for (int j = 0; j < H2; ++j) sacc = __fmaf_rn(w[OW2 + j * H1 + i], d2[j], sacc);
+          d1[i] = z1[i] >= 0.0f ? sacc : __fmul_rn(sacc, kAlpha);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < H1; ++i) {
+          const float q = __fmul_rn(go, w[OW3 + i]);
+          d1[i] = z1[i] >= 0.0f ? q : __fmul_rn(q, kAlpha);
+        }
+      }
+    }
+    // per-parameter row terms, tree-summed; rows >= B contribute +0
+    auto put = [&](int p, float term) {
+      const float sum = warp_tree(row ? term : 0.0f);
+      if (lane == 0) part[wid * NW + p] = sum;
+    };
+#pragma unroll
+    for (int j = 0; j < H1; ++j) {
+#pragma unroll
+      for (int i = 0; i < K; ++i) put(j * K + i, __fmul_rn(d1[j], u[i]));
+      put(OB1 + j, d1[j]);
+    }
+    if constexpr (H2 > 0) {
+#pragma unroll
+      for (int j = 0; j < H2; ++j) {
+#pragma unroll
+        for (int i = 0; i < H1; ++i) put(OW2 + j * H1 + i, __fmul_rn(d2[j], a1[i]));
+        put(OB2 + j, d2[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < HL; ++j) put(OW3 + j, __fmul_rn(go, H2 > 0 ? a2[j] : a1[j]));
+    put(OW3 + HL, go);
+    __syncthreads();
+    for (int p = tid; p < NW; p += 256) {
+      const float* q = part + p;
+      const float g = __fadd_rn(__fadd_rn(__fadd_rn(q[0], q[NW]), __fadd_rn(q[2 * NW], q[3 * NW])),
+                                __fadd_rn(__fadd_rn(q[4 * NW], q[5 * NW]), __fadd_rn(q[6 * NW], q[7 * NW])));
+      const bool bias = (p >= OB1 && p < OB1 + H1) || (H2 > 0 && p >= OB2 && p < OB2 + H2) || p == NW - 1;
+      if (bias) {
+        w[p] = __fsub_rn(w[p], __fmul_rn(lr, g));
+      } else {
+        const float gt = __fadd_rn(g, __fmul_rn(lam2, w[p]));
+        w[p] = __fsub_rn(w[p], __fmul_rn(lr, gt));
+      }
+    }
+    __syncthreads();
+  }
+  for (int p = tid; p < NW; p += 256) wm[p] = w[p];
+}
+
+// validation cost; blockIdx.y = model (nmodels = Lorenzo)
+template <int K, int H1, int H2>
+__global__ void __launch_bounds__(256) k_val(const int* __restrict__ vin, const int* __restrict__ vtg,
+                                             const uint8_t* __restrict__ vus, const float* __restrict__ wbuf,
+                                             int nmodels, int m, const TrainCtl* __restrict__ ctl,
+                                             unsigned long long* costs) {
+  constexpr int NW = H1 * K + H1 + (H2 > 0 ? H2 * H1 + H2 : 0) + (H2 > 0 ? H2 : H1) + 1;
+  __shared__ Mlp s_m;
+  const int model = blockIdx.y;
+  const bool lz = model == nmodels;
+  if (!lz)
+    for (int p = threadIdx.x; p < NW; p += blockDim.x) s_m.w[p] = wbuf[(size_t)model * NW + p];
+  if (threadIdx.x == 0) { s_m.k = K; s_m.h1 = H1; s_m.h2 = H2; s_m.s_in = ctl->s_in; }
+  __syncthreads();
+  const int s_in = ctl->s_in;
+  const float sig = __uint_as_float((unsigned int)(127 - s_in) << 23);
+  const float unsig = __uint_as_float((unsigned int)(127 + s_in) << 23);
+  const long long R = 1ll << (m - 1);
+  const unsigned long long n = ctl->nval;
+  unsigned long long cost = 0;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    if (!vus[i]) continue;
+    int in[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) in[q] = vin[i * K + q];
+    long long pr = 0;
+    if (lz) {
+#pragma unroll
+      for (int q = 0; q < K; ++q) pr += (long long)lz_w(K, q) * in[q];
+    } else {
+      pr = round_pred(mlp_fwd<K, H1, H2>(s_m, in, sig, unsig));
+    }
+    const long long d = (long long)vtg[i] - pr;
+    const unsigned long long a = (unsigned long long)(d < 0 ? -d : d);
+    cost += (unsigned long long)bitlen_u((unsigned int)(a < (unsigned long long)R ? a : (unsigned long long)R));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cost += __shfl_xor_sync(0xFFFFFFFFu, cost, o);
+  if ((threadIdx.x & 31) == 0 && cost) atomicAdd(&costs[model], cost);
+}
+
+__global__ void k_choose(const unsigned long long* costs, int nmodels, TrainCtl* ctl) {
+  unsigned long long best = costs[nmodels];
+  int bi = -1;
+  for (int h = 0; h < nmodels; ++h)
+    if (costs[h] < best) { best = costs[h]; bi = h; }
+  ctl->chosen = bi;
+}
+
+template <int K, int H1, int H2>
+static int launch_train_models(const TrainBufs& tb, int nmodels, int m, cudaStream_t s) {
+  constexpr int NW = H1 * K + H1 + (H2 > 0 ? H2 * H1 + H2 : 0) + (H2 > 0 ? H2 : H1) + 1;
+  const size_t sm = (size_t)NW * 9 * sizeof(float);
+  auto kt = k_train<K, H1, H2>;
+  if (cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return PC_ERR_CUDA;
+  {
+    ProfScope p(kStTrain, s);
+    kt<<<nmodels, 256, sm, s>>>(tb.tin, tb.ttg, tb.tus, tb.w, tb.lrs, tb.lams, reinterpret_cast<const TrainCtl*>(tb.ctl));
+  }
+  dim3 gv(152, nmodels + 1);
+  k_val<K, H1, H2><<<gv, 256, 0, s>>>(tb.vin, tb.vtg, tb.vus, tb.w, nmodels, m,
+                                      reinterpret_cast<const TrainCtl*>(tb.ctl), tb.costs);
+  k_choose<<<1, 1, 0, s>>>(tb.costs, nmodels, reinterpret_cast<TrainCtl*>(tb.ctl));
+  return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
+}
+
+size_t train_ctl_bytes() { return sizeof(TrainCtl); }
+
+template <typename T>
+int launch_train(const T* x, const Geo& g, const State* st, const Tabs* tabs, const TrainBufs& tb, int k, int h1,
+                 int h2, int m, int nmodels, unsigned long long seed, unsigned int thr32, cudaStream_t s) {
+  TrainCtl* ctl = reinterpret_cast<TrainCtl*>(tb.ctl);
+  if (cudaMemsetAsync(ctl, 0, sizeof(TrainCtl), s) != cudaSuccess) return PC_ERR_CUDA;
+  if (cudaMemsetAsync(tb.costs, 0, sizeof(unsigned long long) * (nmodels + 1), s) != cudaSuccess) return PC_ERR_CUDA;
+  const unsigned int nb8 = (unsigned int)((g.nblocks + 7) / 8);
+  k_samp_count<<<nb8, 256, 0, s>>>(g, seed, thr32, tb.cnt_t, tb.cnt_v);
+  k_samp_scan<<<1, 1024, 0, s>>>(g.nblocks, tb.cnt_t, tb.cnt_v, tb.off_t, tb.off_v, ctl);
+  const size_t gsm = sizeof(Tabs) + 4ull * g.bvol * 4;
+  if (cudaFuncSetAttribute(k_samp_gather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm) != cudaSuccess)
+    return PC_ERR_CUDA;
+  k_samp_gather<T><<<(unsigned int)((g.nblocks + 3) / 4), 128, gsm, s>>>(
+      x, g, st, tabs, seed, thr32, k, tb.off_t, tb.off_v, tb.tin, tb.ttg, tb.tus, tb.vin, tb.vtg, tb.vus, ctl,
+      tb.cap_t, tb.cap_v);
+  k_in_shift<<<304, 256, 0, s>>>(tb.ttg, tb.tus, ctl);
+  const int nw = h1 * k + h1 + (h2 > 0 ? h2 * h1 + h2 : 0) + (h2 > 0 ? h2 : h1) + 1;
+  k_init_w<<<(nw + 255) / 256, 256, 0, s>>>(tb.w, nmodels, k, h1, h2, seed ^ 0x5DEECE66Dull, ctl);
+  if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
+  if (k == 7 && h1 == 16 && h2 == 16) return launch_train_models<7, 16, 16>(tb, nmodels, m, s);
+  if (k == 13 && h1 == 32 && h2 == 32) return launch_train_models<13, 32, 32>(tb, nmodels, m, s);
+  if (k == 7 && h1 == 8 && h2 == 8) return launch_train_models<7, 8, 8>(tb, nmodels, m, s);
+  if (k == 7 && h1 == 2 && h2 == 0) return launch_train_models<7, 2, 0>(tb, nmodels, m, s);
+  if (k == 13 && h1 == 16 && h2 == 16) return launch_train_models<13, 16, 16>(tb, nmodels, m, s);
+  return PC_ERR_ARG;
+}
+template int launch_train<float>(const float*, const Geo&, const State*, const Tabs*, const TrainBufs&, int, int, int,
+                                 int, int, unsigned long long, unsigned int, cudaStream_t);
+template int launch_train<double>(const double*, const Geo&, const State*, const Tabs*, const TrainBufs&, int, int,
+                                  int, int, int, unsigned long long, unsigned int, cudaStream_t);
+
+}  // namespace pc
