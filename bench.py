@@ -32,6 +32,7 @@ SHAPE = (100, 500, 500)
 EB = 1e-3
 BLOCK = (8, 8, 8)
 SAMPLE = (40, 200, 200)  # oracle sample: a corner sub-volume of the same field
+THR32 = int(0.1 * 2 ** 32)  # 10% of points drawn for training (Section IV.C)
 
 
 def field():
@@ -98,10 +99,19 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def cpu_oracle_rate(x: np.ndarray, steps: int, predictor):
+def oracle_predictor(sub: np.ndarray):
+    """The oracle's own training phase on the sample (10% sampling, the 16-model grid)."""
+    from oracle import oracle as O
+    best, W, s_in, costs = O.train(sub, EB, block=BLOCK, k=7, h1=16, h2=16, seed=0, thr32=THR32)
+    return (W[best], s_in, "mlp_fp32_s7_16x16") if best >= 0 else (None, 0, "lorenzo")
+
+
+def cpu_oracle_rate(x: np.ndarray, steps: int, predictor=None):
     """Time the oracle's compress + decompress on the bounded sample."""
     from oracle import oracle as O
     sub = np.ascontiguousarray(x[: SAMPLE[0], : SAMPLE[1], : SAMPLE[2]])
+    if predictor is None:
+        predictor = oracle_predictor(sub)
     w, s_in = predictor[0], predictor[1]
     t = []
     for _ in range(steps):
@@ -110,30 +120,24 @@ def cpu_oracle_rate(x: np.ndarray, steps: int, predictor):
         st2, y = O.decompress(blob)
         t.append(time.perf_counter() - t0)
         assert st == 0 and st2 == 0
-    return sub.nbytes, t
+    return sub.nbytes, t, predictor[2]
 
 
 def run_reference(args, rank: int):
     if rank != 0:
         return
     x = field()
-    pred = device_free_predictor(x)
-    nbytes, t = cpu_oracle_rate(x, max(1, args.steps), pred)
+    nbytes, t, pname = cpu_oracle_rate(x, max(1, args.steps))
     v = nbytes * len(t) / sum(t) / 1e9
     sample = f"sub-volume {SAMPLE[0]}x{SAMPLE[1]}x{SAMPLE[2]} of the workload field, compress+decompress per step"
     line = {"metric": METRIC, "value": v, "unit": "GB/s", "impl": "reference", "n_gpus": args.gpus,
             "steps": len(t), "warmup": 0, "ms_per_step": 1e3 * sum(t) / len(t), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "grf100x500x500_f32", "eb_rel": EB, "block": list(BLOCK),
-                       "predictor": pred[2]},
+                       "predictor": pname, "training": "oracle training phase on the sample, untimed"},
             "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
-
-
-def device_free_predictor(x):
-    """(weights, s_in, name) used by both arms; Lorenzo until a trained model is supplied."""
-    return None, 0, "lorenzo"
 
 
 # algorithmic bytes per launch of each stage (see DESIGN.md, "kernels and their rooflines")
@@ -145,7 +149,7 @@ def algorithmic_bytes(stage: str, n: int, ts: int, comp_bytes: int) -> int:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -169,12 +173,26 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     x = field()
-    w, s_in, pname = device_free_predictor(x)
-    params = pc.make_params(EB, BLOCK, pred=pc.PC_PRED_LORENZO if w is None else pc.PC_PRED_MLP_FP32,
-                            stencil=7, hidden=(16, 16), s_in=s_in, weights=w)
     n = x.size
     nbytes = x.nbytes
     d = torch.from_numpy(x).to(dev)
+    # training phase (Section IV.C / V): on the device, before compression, timed separately
+    tparams = pc.make_params(EB, BLOCK, pred=pc.PC_PRED_MLP_FP32, stencil=7, hidden=(16, 16))
+    lrs, lams = pc.default_grid()
+    tws = torch.empty(pc.pc_train_workspace_size(SHAPE, pc.PC_F32, tparams, THR32, lrs.size), dtype=torch.uint8,
+                      device=dev)
+    pc.pc_train(d, tparams, 0, THR32, lrs, lams, tws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    W, s_in, chosen, tcosts = pc.pc_train(d, tparams, 0, THR32, lrs, lams, tws)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del tws
+    w = W[chosen] if chosen >= 0 else None
+    pname = "mlp_fp32_s7_16x16" if w is not None else "lorenzo"
+    params = pc.make_params(EB, BLOCK, pred=pc.PC_PRED_LORENZO if w is None else pc.PC_PRED_MLP_FP32,
+                            stencil=7, hidden=(16, 16), s_in=s_in, weights=w)
+    lz_size = pc.compress(d, pc.make_params(EB, BLOCK)).numel()
     cap = pc.pc_compress_bound(SHAPE, pc.PC_F32, params)
     out = torch.empty(cap, dtype=torch.uint8, device=dev)
     wsc = torch.empty(pc.pc_compress_workspace_size(SHAPE, pc.PC_F32, params), dtype=torch.uint8, device=dev)
@@ -269,10 +287,10 @@ def main():
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            nb, t = cpu_oracle_rate(x, 1, (w, s_in, pname))
+            nb, t, opn = cpu_oracle_rate(x, 1)
             cpu = {"value": nb / t[0] / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                   "sample": f"{SAMPLE[0]}x{SAMPLE[1]}x{SAMPLE[2]} corner sub-volume, compress+decompress, "
-                             f"{t[0]:.1f} s"}
+                   "sample": f"{SAMPLE[0]}x{SAMPLE[1]}x{SAMPLE[2]} corner sub-volume, compress+decompress with "
+                             f"the oracle's own trained {opn} predictor, {t[0]:.1f} s"}
         line = {
             "metric": METRIC, "value": world * nbytes / (t_step * 1e6), "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
@@ -282,6 +300,10 @@ def main():
                        "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
             "compress_gbs": nbytes / (tc * 1e6), "decompress_gbs": nbytes / (td * 1e6),
             "bits_per_value": bpv, "bound_held": ok,
+            "training": {"seconds": train_s, "models": int(lrs.size), "chosen": int(chosen), "s_in": int(s_in),
+                         "samples_rate": THR32 / 2 ** 32, "val_cost_chosen": int(tcosts[chosen]) if chosen >= 0 else None,
+                         "val_cost_lorenzo": int(tcosts[-1])},
+            "bits_per_value_lorenzo_only": 8.0 * lz_size / n,
             "vs_fp32_plain": {"bits_per_value": 32.0, "ratio": 32.0 / bpv, "device_copy_gbs": copy_gbs},
             "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": None,

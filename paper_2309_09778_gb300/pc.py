@@ -28,6 +28,19 @@ SYMBOLS = ["pc_mlp_nweights", "pc_compress_bound", "pc_compress_workspace_size",
            "pc_profile_read", "pc_profile_stage_name", "pc_strerror"]
 
 
+# (lr, lambda) grid trained side by side in the training phase (Section IV.C
+# trains several hyperparameter sets concurrently and keeps the best); the
+# paper gives no values, these are ours.
+DEFAULT_LRS = (3e-3, 1e-2, 3e-2, 1e-1)
+DEFAULT_LAMS = (0.0, 1e-5, 1e-4, 1e-3)
+
+
+def default_grid():
+    lrs = np.array([lr for lr in DEFAULT_LRS for _ in DEFAULT_LAMS], np.float32)
+    lams = np.array([lm for _ in DEFAULT_LRS for lm in DEFAULT_LAMS], np.float32)
+    return lrs, lams
+
+
 class PcError(RuntimeError):
     def __init__(self, status: int, where: str):
         super().__init__(f"{where}: {STATUS.get(status, status)}")
