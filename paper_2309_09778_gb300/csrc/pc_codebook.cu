@@ -21,8 +21,8 @@
 namespace pc {
 
 constexpr int kCbThreads = 1024;
-constexpr int kCbSmemN = 12288;  // merge rounds run in shared memory up to this many leaves
-constexpr size_t kCbSmem = (size_t)kCbSmemN * 16;  // w (u32, 2n) + parent (u16, 2n) + two lists (u16, n)
+constexpr int kCbSmemN = 12288;  // merge rounds run in shared memory once the list is this short
+constexpr size_t kCbSmem = (size_t)kCbSmemN * 16;  // two lists of packed (weight, id) nodes
 
 // Stable LSD radix sort (8-bit digits) of (key, val) pairs by key, one CTA of
 // 32 warps.  Each warp owns a contiguous tile; per-warp digit counts give
@@ -83,62 +83,61 @@ __device__ void cta_radix_sort(unsigned int* k0, uint16_t* v0, unsigned int* k1,
   (void)s_tot;
 }
 
-// Parallel Huffman merge rounds on a list of node ids (leaves 0..n-1 already
-// sorted by weight).  Returns the number of rounds; node ids n.. are internal.
-template <typename Id>
-__device__ int huff_rounds(unsigned int* w, Id* parent, Id* la, Id* lb, int* rstart, int n,
-                           unsigned long long* s_scan) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < n; i += nt) la[i] = (Id)i;
-  __syncthreads();
-  int len = n, next = n, round = 0;
-  while (len > 1) {
-    const unsigned int t1 = w[la[0]] + w[la[1]];
-    int c = 0;
-    for (int i = tid; i < len / 2; i += nt) c += w[la[2 * i + 1]] <= t1;
-    unsigned long long jt;
-    cta_exscan<unsigned long long>((unsigned long long)c, s_scan, jt);
-    const int j = (int)jt;
-    for (int i = tid; i < j; i += nt) {
-      const int a = la[2 * i], b = la[2 * i + 1];
-      w[next + i] = w[a] + w[b];
-      parent[a] = (Id)(next + i);
-      parent[b] = (Id)(next + i);
-    }
-    if (tid == 0) rstart[round] = next;
-    __syncthreads();
-    const int lenR = len - 2 * j;
-    for (int a = tid; a < lenR; a += nt) {
-      const Id id = la[2 * j + a];
-      const unsigned int wa = w[id];
-      int l0 = 0, h0 = j;
-      while (l0 < h0) {
-        const int mid = (l0 + h0) >> 1;
-        if (w[next + mid] < wa) l0 = mid + 1; else h0 = mid;
-      }
-      lb[a + l0] = id;
-    }
-    for (int bi = tid; bi < j; bi += nt) {
-      const unsigned int wb = w[next + bi];
-      int l0 = 0, h0 = lenR;
-      while (l0 < h0) {
-        const int mid = (l0 + h0) >> 1;
-        if (w[la[2 * j + mid]] <= wb) l0 = mid + 1; else h0 = mid;
-      }
-      lb[bi + l0] = (Id)(next + bi);
-    }
-    __syncthreads();
-    Id* tmp = la; la = lb; lb = tmp;
-    len = lenR + j;
-    next += j;
-    ++round;
-  }
-  return round;
+// One merge round on a sorted list of packed nodes (weight << 32 | id),
+// leaves first in (weight, symbol) order.  Joins every pair (L2i, L2i+1)
+// whose second element weighs at most t1 = w(L0) + w(L1) (all of them precede
+// t1 in the total order), records the new nodes' parents, and merges the new
+// nodes (already sorted) with the rest of the list into `out`: an old node
+// goes first on equal weight.  Each thread finds where its share of the
+// output starts by a co-rank search, then merges sequentially.
+__device__ __forceinline__ unsigned long long nn_node(const unsigned long long* in, int i, int next) {
+  const unsigned long long a = in[2 * i], b = in[2 * i + 1];
+  return (((a >> 32) + (b >> 32)) << 32) | (unsigned long long)(next + i);
 }
 
-// Depth of every leaf; counts per depth into s_bits.
-template <typename Id>
-__device__ void huff_depths(const Id* parent, Id* depth, const int* rstart, int n, int rounds, int* s_bits) {
+__device__ int huff_round(const unsigned long long* in, unsigned long long* out, int len, int next,
+                          unsigned int* parent, unsigned long long* s_scan, int& njoin) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const unsigned long long t1 = (in[0] >> 32) + (in[1] >> 32);
+  int c = 0;
+  for (int i = tid; i < len / 2; i += nt) c += (in[2 * i + 1] >> 32) <= t1;
+  unsigned long long jt;
+  cta_exscan<unsigned long long>((unsigned long long)c, s_scan, jt);
+  const int j = (int)jt;
+  for (int i = tid; i < j; i += nt) {
+    parent[(unsigned int)in[2 * i]] = (unsigned int)(next + i);
+    parent[(unsigned int)in[2 * i + 1]] = (unsigned int)(next + i);
+  }
+  const unsigned long long* R = in + 2 * j;
+  const int lenR = len - 2 * j;
+  const int total = lenR + j;
+  const int per = (total + nt - 1) / nt;
+  const int k0 = min(total, tid * per), k1 = min(total, k0 + per);
+  if (k0 < k1) {
+    // co-rank: a elements of R and b = k0 - a of N precede output position k0
+    int lo = max(0, k0 - j), hi = min(k0, lenR);
+    while (lo < hi) {
+      const int a = (lo + hi) >> 1;  // try taking a elements of R
+      const int b = k0 - a;
+      // R[a] must come after N[b-1]: w(N[b-1]) < w(R[a]) (ties put R first)
+      if (b > 0 && a < lenR && (nn_node(in, b - 1, next) >> 32) >= (R[a] >> 32)) lo = a + 1;
+      else hi = a;
+    }
+    int a = lo, b = k0 - lo;
+    for (int k = k0; k < k1; ++k) {
+      const bool takeR = b >= j || (a < lenR && (R[a] >> 32) <= (nn_node(in, b, next) >> 32));
+      out[k] = takeR ? R[a] : nn_node(in, b, next);
+      if (takeR) ++a; else ++b;
+    }
+  }
+  __syncthreads();
+  njoin = j;
+  return total;
+}
+
+// Depth of every leaf from the parent links; counts per depth into s_bits.
+__device__ void huff_depths(const unsigned int* parent, unsigned short* depth, const int* rstart, int n, int rounds,
+                            int* s_bits) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int next = 2 * n - 1, root = next - 1;
   if (tid == 0) depth[root] = 0;
@@ -146,7 +145,7 @@ __device__ void huff_depths(const Id* parent, Id* depth, const int* rstart, int 
   for (int r = rounds - 1; r >= 0; --r) {
     const int a = rstart[r], b = (r + 1 < rounds) ? rstart[r + 1] : next;
     for (int id = a + tid; id < b; id += nt)
-      if (id != root) depth[id] = (Id)(depth[parent[id]] + 1);
+      if (id != root) depth[id] = (unsigned short)(depth[parent[id]] + 1);
     __syncthreads();
   }
   for (int i = tid; i < n; i += nt) {
@@ -163,23 +162,31 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const unsigned long lon
   extern __shared__ __align__(16) unsigned char arena[];
   __shared__ unsigned long long s_scan[32];
   __shared__ int s_bits[128];
-  __shared__ unsigned int s_first[32], s_offs[32], s_lstart[32], s_tot[256];
+  __shared__ unsigned int s_first[32], s_offs[32], s_lend[32], s_tot[256];
   __shared__ int s_u[4];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nsym = 1 << m;
   if (st->err) return;
   // Only entries of used symbols are ever read, so the length and code
   // tables are not cleared.  Compaction: used symbols in symbol order, with
-  // their counts; each warp reads a contiguous range 32 symbols at a time.
+  // their counts; each warp reads a contiguous range, 8 loads in flight.
   const int lane = tid & 31, wid = tid >> 5, nwarp = nt >> 5;
   const int per = (nsym + nwarp - 1) / nwarp;
   const int lo = min(nsym, wid * per), hi = min(nsym, lo + per);
+  constexpr int U = 8;
   unsigned long long cnt = 0, mx = 0;
-  for (int s0 = lo; s0 < hi; s0 += 32) {
-    const int s = s0 + lane;
-    const unsigned long long h = s < hi ? hist[s] : 0ull;
-    mx = max(mx, h);
-    cnt += __popc(__ballot_sync(0xFFFFFFFFu, h > 0));
+  for (int s0 = lo; s0 < hi; s0 += 32 * U) {
+    unsigned long long h[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int s = s0 + 32 * u + lane;
+      h[u] = s < hi ? hist[s] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      mx = max(mx, h[u]);
+      cnt += __popc(__ballot_sync(0xFFFFFFFFu, h[u] > 0));
+    }
   }
   unsigned long long tot;
   const unsigned long long pre = cta_exscan<unsigned long long>(lane == 0 ? cnt : 0ull, s_scan, tot);
@@ -190,16 +197,23 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const unsigned long lon
   uint16_t* v1 = v0 + nsym;
   {
     int p = (int)__shfl_sync(0xFFFFFFFFu, pre, 0);
-    for (int s0 = lo; s0 < hi; s0 += 32) {
-      const int s = s0 + lane;
-      const unsigned long long h = s < hi ? hist[s] : 0ull;
-      const unsigned int bal = __ballot_sync(0xFFFFFFFFu, h > 0);
-      if (h > 0) {
-        const int q = p + __popc(bal & ((1u << lane) - 1u));
-        k0[q] = (unsigned int)h;
-        v0[q] = (uint16_t)s;
+    for (int s0 = lo; s0 < hi; s0 += 32 * U) {
+      unsigned long long h[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int s = s0 + 32 * u + lane;
+        h[u] = s < hi ? hist[s] : 0ull;
       }
-      p += __popc(bal);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const unsigned int bal = __ballot_sync(0xFFFFFFFFu, h[u] > 0);
+        if (h[u] > 0) {
+          const int q = p + __popc(bal & ((1u << lane) - 1u));
+          k0[q] = (unsigned int)h[u];
+          v0[q] = (uint16_t)(s0 + 32 * u + lane);
+        }
+        p += __popc(bal);
+      }
     }
   }
   // largest count -> number of radix passes
@@ -240,25 +254,46 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const unsigned long lon
   uint16_t* vs;
   cta_radix_sort(k0, v0, k1, v1, n, s_u[1], reinterpret_cast<unsigned int*>(arena), s_tot, s_scan, ks, vs);
   for (int i = tid; i < 128; i += nt) s_bits[i] = 0;
-  int rounds;
-  if (n <= kCbSmemN) {
-    unsigned int* w = reinterpret_cast<unsigned int*>(arena);
-    uint16_t* parent = reinterpret_cast<uint16_t*>(w + 2 * kCbSmemN);
-    uint16_t* la = parent + 2 * kCbSmemN;
-    uint16_t* lb = la + kCbSmemN;
-    for (int i = tid; i < n; i += nt) w[i] = ks[i];
+  // merge rounds: in the workspace while the list is long, in shared memory after
+  unsigned long long* ga = reinterpret_cast<unsigned long long*>(hs.w);
+  unsigned long long* gb = ga + nsym;
+  unsigned long long* sa = reinterpret_cast<unsigned long long*>(arena);
+  unsigned long long* sb = sa + kCbSmemN;
+  unsigned int* parent = reinterpret_cast<unsigned int*>(hs.parent);
+  const bool start_smem = n <= kCbSmemN;
+  unsigned long long* la = start_smem ? sa : ga;
+  unsigned long long* lb = start_smem ? sb : gb;
+  for (int i = tid; i < n; i += nt) la[i] = ((unsigned long long)ks[i] << 32) | (unsigned long long)i;
+  __syncthreads();
+  int len = n, next = n, rounds = 0;
+  bool in_smem = start_smem;
+  while (len > 1) {
+    if (tid == 0) hs.rstart[rounds] = next;
+    int j;
+    len = huff_round(la, lb, len, next, parent, s_scan, j);
+    next += j;
+    ++rounds;
+    if (!in_smem && len <= kCbSmemN) {
+      for (int i = tid; i < len; i += nt) sa[i] = lb[i];
+      __syncthreads();
+      la = sa;
+      lb = sb;
+      in_smem = true;
+    } else {
+      unsigned long long* t = la; la = lb; lb = t;
+    }
+  }
+  __syncthreads();
+  const int nnode = 2 * n - 1;
+  if ((size_t)nnode * 6 <= kCbSmem) {
+    // walk the tree in shared memory: parent links copied in, depths beside them
+    unsigned int* sp = reinterpret_cast<unsigned int*>(arena);
+    unsigned short* sd = reinterpret_cast<unsigned short*>(sp + nnode);
+    for (int i = tid; i < nnode - 1; i += nt) sp[i] = parent[i];
     __syncthreads();
-    rounds = huff_rounds<uint16_t>(w, parent, la, lb, hs.rstart, n, s_scan);
-    huff_depths<uint16_t>(parent, la, hs.rstart, n, rounds, s_bits);
+    huff_depths(sp, sd, hs.rstart, n, rounds, s_bits);
   } else {
-    unsigned int* w = reinterpret_cast<unsigned int*>(hs.w);
-    for (int i = tid; i < n; i += nt) w[i] = ks[i];
-    __syncthreads();
-    rounds = huff_rounds<unsigned int>(w, reinterpret_cast<unsigned int*>(hs.parent),
-                                       reinterpret_cast<unsigned int*>(hs.la), reinterpret_cast<unsigned int*>(hs.lb),
-                                       hs.rstart, n, s_scan);
-    huff_depths<unsigned int>(reinterpret_cast<unsigned int*>(hs.parent), reinterpret_cast<unsigned int*>(hs.depth),
-                              hs.rstart, n, rounds, s_bits);
+    huff_depths(parent, reinterpret_cast<unsigned short*>(hs.depth), hs.rstart, n, rounds, s_bits);
   }
   if (tid == 0) {
     int maxlen = 0;
@@ -278,8 +313,14 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const unsigned long lon
       maxlen = kLmax;
     }
     s_u[0] = maxlen;
+    // leaves (ascending count) take lengths from the longest down: leaf ranks
+    // below s_lend[l] have length >= l
     unsigned int cum = 0;
-    for (int l = maxlen; l >= 1; --l) { s_lstart[l] = cum; cum += (unsigned int)s_bits[l]; }
+    for (int l = 31; l >= 1; --l) {
+      if (l <= maxlen) cum += (unsigned int)s_bits[l];
+      s_lend[l] = cum;
+    }
+    s_lend[0] = cum;
     unsigned int code = 0, off = 0;
     for (int l = 1; l <= kLmax; ++l) {
       const unsigned int prevc = l > 1 ? (unsigned int)s_bits[l - 1] : 0u;
@@ -291,13 +332,16 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const unsigned long lon
   }
   __syncthreads();
   const int maxlen = s_u[0];
-  // canonical order: most frequent first (the sorted leaf list reversed);
-  // lengths by rank (leaf 0, the lightest, gets the longest length)
+  // canonical order: most frequent first (the sorted leaf list reversed)
   for (int i = tid; i < n; i += nt) {
-    const int leaf = n - 1 - i;
-    int l = maxlen;
-    while (l > 1 && !((unsigned int)leaf >= s_lstart[l] && (unsigned int)leaf < s_lstart[l] + (unsigned int)s_bits[l]))
-      --l;
+    const unsigned int leaf = (unsigned int)(n - 1 - i);
+    // length = largest l with leaf < s_lend[l] (s_lend decreases with l)
+    int lo2 = 1, hi2 = maxlen;
+    while (lo2 < hi2) {
+      const int mid = (lo2 + hi2 + 1) >> 1;
+      if (leaf < s_lend[mid]) lo2 = mid; else hi2 = mid - 1;
+    }
+    const int l = lo2;
     const unsigned int sym = vs[leaf];
     lens[sym] = (uint8_t)l;
     cw[sym] = (s_first[l] + ((unsigned int)i - s_offs[l])) | ((unsigned int)l << 24);

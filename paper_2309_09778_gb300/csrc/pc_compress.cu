@@ -199,7 +199,7 @@ constexpr size_t compress_smem_bytes() {
 }
 
 template <typename T, int B0, int B1, int B2, int MODE, int K, int H1, int H2>
-__global__ void __launch_bounds__(256) k_compress(const T* __restrict__ x, Geo g, const State* __restrict__ st,
+__global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restrict__ x, Geo g, const State* __restrict__ st,
                                                    const Tabs* __restrict__ tabs, uint16_t* __restrict__ codes,
                                                    uint8_t* __restrict__ nnflag, uint32_t* __restrict__ nout,
                                                    unsigned long long* __restrict__ hist, int m,

@@ -177,11 +177,21 @@ constexpr int kSortedSmem = 16384;
 __global__ void __launch_bounds__(256) k_huff_decode(Geo g, const uint8_t* __restrict__ in, DecInfo di,
                                                      DecScratch ds) {
   __shared__ unsigned int s_lut[1 << kLutBits];
-  __shared__ unsigned int s_tab[96];
+  __shared__ unsigned int s_lim[16];    // left-justified end of the code range of lengths 13..28
+  __shared__ unsigned int s_first[32], s_cnt[32], s_offs[32];  // per length: first code, count, list position
   extern __shared__ uint16_t s_sorted[];
   const bool small = di.n_used <= (unsigned int)kSortedSmem;
   for (int i = threadIdx.x; i < (1 << kLutBits); i += blockDim.x) s_lut[i] = ds.lut[i];
-  for (int i = threadIdx.x; i < 96; i += blockDim.x) s_tab[i] = ds.tabs[i];
+  if (threadIdx.x < 32) {
+    const int l = threadIdx.x;
+    s_first[l] = ds.tabs[l];
+    s_cnt[l] = ds.tabs[32 + l];
+    s_offs[l] = ds.tabs[64 + l];
+  }
+  if (threadIdx.x < 16) {
+    const int l = kLutBits + 1 + threadIdx.x;
+    s_lim[threadIdx.x] = l <= kLmax ? (ds.tabs[l] + ds.tabs[32 + l]) << (kLmax - l) : 0xFFFFFFFFu;
+  }
   if (small)
     for (int i = threadIdx.x; i < (int)di.n_used; i += blockDim.x) s_sorted[i] = ds.sorted[i];
   __syncthreads();
@@ -200,42 +210,66 @@ __global__ void __launch_bounds__(256) k_huff_decode(Geo g, const uint8_t* __res
   const unsigned long long nq = (di.swords + 3) / 4;
   const unsigned long long start = ds.boff[b];
   unsigned long long qi = start >> 7;
-  int wi = (int)((start >> 5) & 3ull);
   const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
-  uint4 cur = qi < nq ? __ldg(&s4[qi]) : zero4;
-  uint4 nxt = qi + 1 < nq ? __ldg(&s4[qi + 1]) : zero4;
-  auto next_word = [&]() -> unsigned int {
-    const unsigned int w = wi == 0 ? cur.x : (wi == 1 ? cur.y : (wi == 2 ? cur.z : cur.w));
-    if (++wi == 4) {
-      wi = 0;
+  uint4 q4 = qi < nq ? __ldg(&s4[qi]) : zero4;           // word queue: q4.x is next
+  uint4 nx4 = qi + 1 < nq ? __ldg(&s4[qi + 1]) : zero4;  // prefetched chunk
+  int qn = 4;
+  auto pop = [&]() -> unsigned int {
+    const unsigned int w = q4.x;
+    q4.x = q4.y; q4.y = q4.z; q4.z = q4.w;
+    if (--qn == 0) {
+      q4 = nx4;
       ++qi;
-      cur = nxt;
-      nxt = qi + 1 < nq ? __ldg(&s4[qi + 1]) : zero4;
+      nx4 = qi + 1 < nq ? __ldg(&s4[qi + 1]) : zero4;
+      qn = 4;
     }
     return w;
   };
-  unsigned long long buf = 0;
-  int nb = 0;
-  buf = (unsigned long long)next_word() << 32;
-  buf |= next_word();
-  nb = 64;
+  for (int k = (int)((start >> 5) & 3ull); k > 0; --k) pop();
+  unsigned long long buf = (unsigned long long)pop() << 32;
+  buf |= pop();
+  int nb = 64;
   {
     const int skip = (int)(start & 31ull);
     buf <<= skip;
     nb -= skip;
   }
-  // left-justified end of the code range of each length 13..24
-  unsigned int lim[kLmax - kLutBits];
-#pragma unroll
-  for (int q = 0; q < kLmax - kLutBits; ++q) {
-    const int l = kLutBits + 1 + q;
-    lim[q] = (s_tab[l] + s_tab[32 + l]) << (kLmax - l);
-  }
   unsigned int used = 0;
   bool bad = false;
+  const unsigned int nsym = 1u << di.m, nused = di.n_used;
+  // one canonical decode step
+  auto step = [&]() -> unsigned int {
+    if (nb <= 32) {
+      buf |= (unsigned long long)pop() << (32 - nb);
+      nb += 32;
+    }
+    const unsigned int peek = (unsigned int)(buf >> 40);  // next 24 bits
+    const unsigned int e = s_lut[peek >> (kLmax - kLutBits)];
+    // long words: lengths 13..24 by binary search over the left-justified
+    // range ends (canonical ranges tile the window space in length order)
+    int q = 0;
+    q += peek >= s_lim[q + 7] ? 8 : 0;
+    q += peek >= s_lim[q + 3] ? 4 : 0;
+    q += peek >= s_lim[q + 1] ? 2 : 0;
+    q += peek >= s_lim[q] ? 1 : 0;
+    const int l = kLutBits + 1 + q;
+    const int lc = l <= kLmax ? l : kLmax;
+    const unsigned int d = (peek >> (kLmax - lc)) - s_first[lc];
+    const bool inr = l <= kLmax && d < s_cnt[lc];
+    const unsigned int idx = s_offs[lc] + (inr ? d : 0u);
+    const unsigned int slong = sorted[idx < nused ? idx : 0u];
+    const unsigned int elen = e & 0xFFu;
+    const unsigned int len = elen ? elen : (unsigned int)lc;
+    const unsigned int sym = elen ? (e >> 8) : slong;
+    if (!elen && !inr) bad = true;
+    used += len;
+    if (used > nbits || sym >= nsym) bad = true;
+    buf <<= len;
+    nb -= (int)len;
+    return sym;
+  };
   uint4* out = reinterpret_cast<uint4*>(ds.codes + b * g.bvol);
   const int b12 = g.b[1] * g.b[2];
-  const unsigned int nsym = 1u << di.m;
   for (int j0 = 0; j0 < g.bvol; j0 += 8) {
     unsigned int pk[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
@@ -247,30 +281,7 @@ __global__ void __launch_bounds__(256) k_huff_decode(Geo g, const uint8_t* __res
         valid = lz < e0 && ly < e1 && lx < e2;
       }
       if (valid && !bad) {
-        if (nb <= 32) {
-          buf |= (unsigned long long)next_word() << (32 - nb);
-          nb += 32;
-        }
-        const unsigned int peek = (unsigned int)(buf >> 40);  // next 24 bits
-        const unsigned int e = s_lut[peek >> (kLmax - kLutBits)];
-        unsigned int len = e & 0xFFu, sym = e >> 8;
-        if (!len) {
-          // canonical code ranges tile the 24-bit window space in order of
-          // length: the length is 13 plus the number of longer-code limits
-          // the window has reached
-          unsigned int l = kLutBits + 1;
-#pragma unroll
-          for (int q2 = 0; q2 < kLmax - kLutBits - 1; ++q2) l += peek >= lim[q2];
-          if (peek >= lim[kLmax - kLutBits - 1]) bad = true;
-          const unsigned int d = (peek >> (kLmax - l)) - s_tab[l];
-          if (d >= s_tab[32 + l]) bad = true;
-          sym = bad ? 0u : sorted[s_tab[64 + l] + d];
-          len = l;
-        }
-        used += len;
-        if (used > nbits || sym >= nsym) bad = true;
-        buf <<= len;
-        nb -= (int)len;
+        const unsigned int sym = step();
         if (!bad) pk[q >> 1] |= sym << (16 * (q & 1));
       }
     }
@@ -294,7 +305,7 @@ constexpr size_t recon_smem_bytes() {
 }
 
 template <typename T, int B0, int B1, int B2, int MODE, int K, int H1, int H2>
-__global__ void __launch_bounds__(256) k_recon(Geo g, const uint8_t* __restrict__ in, DecInfo di, DecScratch ds,
+__global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_t* __restrict__ in, DecInfo di, DecScratch ds,
                                                T* __restrict__ xo, const __grid_constant__ Mlp mlp) {
   constexpr int BV = B0 * B1 * B2;
   using BS = BrickShape<BV>;
