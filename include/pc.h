@@ -86,7 +86,9 @@ int pc_compress_workspace_size(const size_t dims[3], int dtype, const pc_params*
  *   out_size  [out] host size_t: container bytes written.
  *   d_ws      [scratch] device workspace of ws_bytes >= pc_compress_workspace_size.
  * The stream is synchronized once, at the end, to read the size and status.
- * Errors: PC_ERR_ARG, PC_ERR_DTYPE, PC_ERR_NONFINITE, PC_ERR_EB_RANGE,
+ * A field holds at most 2^32 - 1 points (code counts are 32-bit); larger
+ * fields are compressed as independent partitions by the caller.
+ * Errors: PC_ERR_ARG (also for more than 2^32 - 1 points), PC_ERR_DTYPE, PC_ERR_NONFINITE, PC_ERR_EB_RANGE,
  * PC_ERR_CAPACITY (out_cap or ws_bytes too small), PC_ERR_CUDA.
  */
 int pc_compress(const void* d_field, const size_t dims[3], int dtype, const pc_params* p,

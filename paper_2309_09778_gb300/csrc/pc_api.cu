@@ -39,13 +39,17 @@ int nweights(int k, int h1, int h2) {
 bool make_geo(const size_t dims[3], const int block[3], Geo& g) {
   long long vol = 1;
   for (int i = 0; i < 3; ++i) {
-    if (dims[i] < 1 || block[i] < 1) return false;
+    if (dims[i] < 1 || dims[i] > 0xFFFFFFFFull || block[i] < 1) return false;
     g.n[i] = (long long)dims[i];
     g.b[i] = block[i];
     g.nb[i] = (g.n[i] + block[i] - 1) / block[i];
     vol *= block[i];
   }
   if (vol < 2 || vol > 4096) return false;
+  // Huffman weights are 32-bit counts of points
+  if ((unsigned long long)g.n[0] * (unsigned long long)g.n[1] > 0xFFFFFFFFull ||
+      (unsigned long long)g.n[0] * (unsigned long long)g.n[1] * (unsigned long long)g.n[2] > 0xFFFFFFFFull)
+    return false;
   g.bvol = (int)vol;
   g.nblocks = g.nb[0] * g.nb[1] * g.nb[2];
   long long ch = kChunkPts / g.bvol;

@@ -215,3 +215,51 @@ def test_host_buffer_entry_points(pc, O):
     pc.pc_decompress_host(hout[:n], n, hy, dout, dfield, ws2)
     st, yo = O.decompress(want)
     assert same_bits(hy, yo.reshape(x.shape))
+
+
+def lattice_field(nb, nlev, seed, eb, B=64):
+    """2-D field (1, nb0*B, nb1*B) whose Lorenzo residual codes inside each
+    B x B block are chosen exactly: Fibonacci counts (1, 1, 2, 3, 5, ...) for
+    nlev distinct residuals, zero elsewhere.  Values sit on the quantization
+    lattice 2^(d * 2 log2(1+eb)) with d the per-block 2-D prefix sums of the
+    residuals (first row and column of every block zero), so the histogram
+    has the Fibonacci shape that drives a Huffman tree deepest."""
+    rng = np.random.default_rng(seed)
+    f = [1, 1]
+    while len(f) < nlev:
+        f.append(f[-1] + f[-2])
+    vals = np.concatenate([np.full(c, (k // 2 + 1) * (1 if k % 2 else -1)) for k, c in enumerate(f)])
+    nin = nb[0] * nb[1] * (B - 1) ** 2
+    r = np.concatenate([vals, np.zeros(nin - vals.size, np.int64)])
+    rng.shuffle(r)
+    r = r.reshape(nb[0], nb[1], B - 1, B - 1)
+    d = np.zeros((nb[0], nb[1], B, B), np.int64)
+    d[:, :, 1:, 1:] = r.cumsum(axis=2).cumsum(axis=3)
+    d = d.transpose(0, 2, 1, 3).reshape(1, nb[0] * B, nb[1] * B)
+    return np.exp2(d * 2 * np.log2(1 + eb)).astype(np.float32)
+
+
+def test_length_limit_on_fibonacci_histogram(pc, O):
+    """Huffman depth beyond 24 bits: the T.81 Annex K.3 limit must act the same way."""
+    x = lattice_field((15, 15), 28, 5, 1e-3)
+    st, want, d = O.compress(x, 1e-3, block=(1, 64, 64), dump=True)
+    assert st == 0
+    assert int(O.huffman_lengths(d["hist"], 64).max()) > 24 and int(d["lens"].max()) == 24
+    got, y = run_gpu(pc, x, 1e-3, (1, 64, 64))
+    assert_same(got, want)
+    st, yo = O.decompress(want)
+    assert same_bits(y, yo.reshape(x.shape))
+
+
+def test_many_used_symbols(pc, O):
+    """White log-normal noise: tens of thousands of used symbols, so the
+    codebook sorts and merges in the workspace before shared memory."""
+    rng = np.random.default_rng(3)
+    x = (np.exp2(rng.normal(0, 6.4, (48, 64, 64))) * np.where(rng.random((48, 64, 64)) < 0.5, -1, 1)).astype(np.float32)
+    st, want, d = O.compress(x, 1e-3, block=(8, 8, 8), dump=True)
+    assert st == 0 and int((d["hist"] > 0).sum()) > 40000
+    got, y = run_gpu(pc, x, 1e-3, (8, 8, 8))
+    assert_same(got, want)
+    st, yo = O.decompress(want)
+    assert same_bits(y, yo.reshape(x.shape))
+    check_roundtrip(x, y, 1e-3)
