@@ -14,12 +14,12 @@
 // a length exceeds 24.  Code words are assigned along the symbol list ordered
 // most frequent first (the sorted leaves reversed), where lengths never
 // decrease: consecutive codes per length, as in RFC 1951 Section 3.2.2 and
-// ITU-T T.81 Annex C.  Leaves are sorted by a stable radix sort on counts.
+// ITU-T T.81 Annex C.  Leaves are sorted by count with a stable radix sort
+// (in shared memory when they fit, else in the workspace).
 //
 // Node weights are held in 32 bits: the field has fewer than 2^32 points,
 // which the entry points check.  Everything that fits runs in shared memory;
-// for many used symbols the sort and the first (long) merge rounds run in
-// the workspace, staged through shared memory in tiles.
+// for many used symbols the sort and the merge queues live in the workspace.
 #include "pc_kernels.cuh"
 #include "pc_profile.cuh"
 
@@ -27,10 +27,7 @@ namespace pc {
 
 constexpr int kCbThreads = 1024;
 constexpr size_t kCbSmem = 196608;  // dynamic shared memory arena
-constexpr int kCbListN = 12288;     // merge lists (two of packed u64 nodes) in shared memory up to this length
-constexpr int kCbTile = 12288;      // long rounds: output tile staged through shared memory
-constexpr int kCbSortN = 13568;     // radix sort in shared memory up to this many leaves (12 B each + 32 KB counts)
-constexpr int kRadixU = 4;          // 32-key chunks a warp loads before it ranks them
+constexpr int kCbQueueN = 24576;    // merge queues (leaf and internal weights, u32) in shared memory up to this n
 
 // Smallest x in [lo, hi] with pred(x), for pred false then true over the
 // range (pred(hi) is taken as true and never evaluated).  All lanes of the
@@ -52,12 +49,89 @@ __device__ __forceinline__ int warp_first_true(int lo, int hi, P pred) {
   return lo;
 }
 
-// Stable LSD radix sort (8-bit digits) of (key, val) pairs by key, one CTA of
-// 32 warps: input (kin, vin), result in (kout, vout), two temporaries for the
+// Stable sort, by key, of (key, val) pairs held in shared memory: LSD radix
+// with 4-bit digits, one counting pass per digit of the largest key.
+//
+// A counting pass: thread t owns the contiguous run [t E, t E + E) of the
+// input and counts its digits (in 4-bit fields of one register, E < 16); the
+// counts go to column t of a digit-major table, whose exclusive scan in
+// (digit, thread) order gives each (digit, thread) its first output slot.
+// The pass is stable without any ranking across threads.
+constexpr int kSegN = 13568;  // pairs sorted in shared memory at once (E <= 14 with 1024 threads)
+
+// One stable counting pass of ki/vi[0, n) into ko/vo by digit(key) in 0..15.
+template <typename DF>
+__device__ void count_pass(const unsigned int* ki, const uint16_t* vi, unsigned int* ko, uint16_t* vo, int n, DF digit,
+                           unsigned short* s_cnt, unsigned long long* s_scan) {
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int E = (n + nt - 1) / nt;
+  const int lo = min(n, t * E), hi = min(n, lo + E);
+  unsigned long long c = 0;
+  for (int i = lo; i < hi; ++i) c += 1ull << (4 * digit(ki[i]));
+#pragma unroll
+  for (int d = 0; d < 16; ++d) s_cnt[d * nt + t] = (unsigned short)((c >> (4 * d)) & 15u);
+  __syncthreads();
+  // this thread's 16 consecutive table entries, as two 16-byte words
+  uint4* row = reinterpret_cast<uint4*>(s_cnt + 16 * t);
+  uint4 w0 = row[0], w1 = row[1];
+  unsigned int e[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+  unsigned int sum = 0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) sum += (e[u] & 0xFFFFu) + (e[u] >> 16);
+  unsigned long long tot;
+  unsigned int run = (unsigned int)cta_exscan<unsigned long long>(sum, s_scan, tot);
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const unsigned int lo16 = run;
+    run += e[u] & 0xFFFFu;
+    const unsigned int hi16 = run;
+    run += e[u] >> 16;
+    e[u] = lo16 | (hi16 << 16);
+  }
+  row[0] = make_uint4(e[0], e[1], e[2], e[3]);
+  row[1] = make_uint4(e[4], e[5], e[6], e[7]);
+  __syncthreads();
+  for (int i = lo; i < hi; ++i) {
+    const unsigned int key = ki[i];
+    const int d = digit(key);
+    const unsigned int pos = s_cnt[d * nt + t];
+    s_cnt[d * nt + t] = (unsigned short)(pos + 1u);
+    ko[pos] = key;
+    vo[pos] = vi[i];
+  }
+  __syncthreads();
+}
+
+// Sorts k0/v0[0, n) (k1/v1 is the other buffer) on npass 4-bit digits and
+// writes the result to (kout, vout) in global memory.
+__device__ void smem_sort(unsigned int* k0, uint16_t* v0, unsigned int* k1, uint16_t* v1, int n, int npass,
+                          unsigned int* kout, uint16_t* vout, unsigned short* s_cnt, unsigned long long* s_scan) {
+  int cur = 0;
+#pragma unroll 1
+  for (int pass = 0; pass < npass; ++pass) {
+    const int sh = 4 * pass;
+    auto dig = [=](unsigned int k) { return (int)((k >> sh) & 15u); };
+    if (cur) count_pass(k1, v1, k0, v0, n, dig, s_cnt, s_scan);
+    else count_pass(k0, v0, k1, v1, n, dig, s_cnt, s_scan);
+    cur ^= 1;
+  }
+  const unsigned int* rk = cur ? k1 : k0;
+  const uint16_t* rv = cur ? v1 : v0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    kout[i] = rk[i];
+    vout[i] = rv[i];
+  }
+  __syncthreads();
+}
+
+constexpr int kRadixU8 = 4;  // 32-key chunks a warp loads before it ranks them
+
+// Stable LSD radix sort (8-bit digits) of (key, val) pairs by key in global
+// memory, one CTA of 32 warps: input (kin, vin), result in (kout, vout), two temporaries for the
 // passes in between.  Each warp owns a contiguous tile; per-warp digit counts
 // give every (warp, digit) its output offset; inside a warp equal digits are
 // ranked in lane order with __match_any_sync, so the sort is stable.
-__device__ void cta_radix_sort(const unsigned int* kin, const uint16_t* vin, unsigned int* ka, uint16_t* va,
+__device__ void cta_radix_sort8(const unsigned int* kin, const uint16_t* vin, unsigned int* ka, uint16_t* va,
                                unsigned int* kb, uint16_t* vb, unsigned int* kout, uint16_t* vout, int n, int npass,
                                unsigned int* s_hist /* [32][256] */, unsigned long long* s_scan) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -71,15 +145,15 @@ __device__ void cta_radix_sort(const unsigned int* kin, const uint16_t* vin, uns
     const int sh = 8 * pass;
     for (int i = tid; i < 32 * 256; i += blockDim.x) s_hist[i] = 0u;
     __syncthreads();
-    for (int c0 = lo; c0 < hi; c0 += 32 * kRadixU) {
-      unsigned int key[kRadixU];
+    for (int c0 = lo; c0 < hi; c0 += 32 * kRadixU8) {
+      unsigned int key[kRadixU8];
 #pragma unroll
-      for (int u = 0; u < kRadixU; ++u) {
+      for (int u = 0; u < kRadixU8; ++u) {
         const int i = c0 + 32 * u + lane;
         key[u] = i < hi ? ki[i] : 0u;
       }
 #pragma unroll
-      for (int u = 0; u < kRadixU; ++u)
+      for (int u = 0; u < kRadixU8; ++u)
         if (c0 + 32 * u + lane < hi) atomicAdd(&s_hist[wid * 256 + ((key[u] >> sh) & 255u)], 1u);
     }
     __syncthreads();
@@ -97,17 +171,17 @@ __device__ void cta_radix_sort(const unsigned int* kin, const uint16_t* vin, uns
       }
     }
     __syncthreads();
-    for (int c0 = lo; c0 < hi; c0 += 32 * kRadixU) {
-      unsigned int key[kRadixU];
-      uint16_t val[kRadixU];
+    for (int c0 = lo; c0 < hi; c0 += 32 * kRadixU8) {
+      unsigned int key[kRadixU8];
+      uint16_t val[kRadixU8];
 #pragma unroll
-      for (int u = 0; u < kRadixU; ++u) {
+      for (int u = 0; u < kRadixU8; ++u) {
         const int i = c0 + 32 * u + lane;
         key[u] = i < hi ? ki[i] : 0u;
         val[u] = i < hi ? vi[i] : (uint16_t)0;
       }
 #pragma unroll
-      for (int u = 0; u < kRadixU; ++u) {
+      for (int u = 0; u < kRadixU8; ++u) {
         const bool valid = c0 + 32 * u + lane < hi;
         const unsigned int d = valid ? ((key[u] >> sh) & 255u) : 256u + (unsigned int)lane;
         const unsigned int peers = __match_any_sync(0xFFFFFFFFu, d);
@@ -128,109 +202,139 @@ __device__ void cta_radix_sort(const unsigned int* kin, const uint16_t* vin, uns
   }
 }
 
-// Merge rounds on a sorted list of packed nodes (weight << 32 | id), leaves
-// first in (weight, symbol) order.  A round joins every pair (L2i, L2i+1)
-// whose second element weighs at most t1 = w(L0) + w(L1) (all of them precede
-// t1 in the total order; the list is sorted, so they are a prefix of the
-// pairs), records the new nodes' parents, and merges the new nodes (already
-// sorted) with the rest R of the list: an old node goes first on equal
-// weight.  Output position k is reached after taking a nodes of R and k - a
-// new ones, with a found by a co-rank search; each thread then merges its
-// share sequentially.
-__device__ __forceinline__ unsigned long long nn_node(const unsigned long long* in, int i, int next) {
-  const unsigned long long a = in[2 * i], b = in[2 * i + 1];
-  return (((a >> 32) + (b >> 32)) << 32) | (unsigned long long)(next + i);
-}
+// Merge rounds on two queues: the leaves A (weights sorted by (count,
+// symbol), ids 0..n-1) and the internal nodes B (ids n, n+1, ... in order of
+// creation).  Huffman's rule creates internal nodes in non-decreasing weight,
+// so B stays sorted, and the available nodes in the total order are the merge
+// of the unconsumed parts A[p..] and B[q..nb) with a leaf first on equal
+// weight.  A round joins L0+L1 into t1 and, with it, every following pair
+// (L2i, L2i+1) whose second element weighs at most t1: with c nodes of weight
+// <= t1 available, that is j = c/2 pairs, made of the first 2j nodes of the
+// merge (x of them leaves).  Only those 2j nodes are touched, so the rounds
+// do O(n) work in all.  The weights fit 32 bits (fewer than 2^32 points).
+struct TwoQ {
+  int p, q, nb, j, x, cA, cB;
+};
 
-__device__ __forceinline__ unsigned int wt(unsigned long long v) { return (unsigned int)(v >> 32); }
-
-// Number of pairs joined in this round, found by warp 0 and shared.
-__device__ __forceinline__ int round_joins(const unsigned long long* in, int len, int* s_j) {
-  if (threadIdx.x < 32) {
-    const unsigned long long t1 = (unsigned long long)wt(in[0]) + wt(in[1]);
-    const int j = warp_first_true(0, len / 2, [&](int i) { return (unsigned long long)wt(in[2 * i + 1]) > t1; });
-    if (threadIdx.x == 0) *s_j = j;
+// Warp 0: the round's j and x from the queue heads; result in *s.
+__device__ void two_queue_plan(const unsigned int* A, const unsigned int* B, int n, TwoQ* s) {
+  if (threadIdx.x >= 32) return;
+  const int p = s->p, q = s->q, nb = s->nb;
+  // the first two nodes of the merge
+  unsigned int w[2];
+  int pa = p, qb = q;
+  for (int r = 0; r < 2; ++r) {
+    const bool leaf = pa < n && (qb >= nb || A[pa] <= B[qb]);
+    w[r] = leaf ? A[pa] : B[qb];
+    if (leaf) ++pa; else ++qb;
   }
-  __syncthreads();
-  return *s_j;
-}
-
-__device__ __forceinline__ void set_parents(const unsigned long long* in, int j, int next, unsigned int* parent) {
-  for (int i = threadIdx.x; i < j; i += blockDim.x) {
-    parent[(unsigned int)in[2 * i]] = (unsigned int)(next + i);
-    parent[(unsigned int)in[2 * i + 1]] = (unsigned int)(next + i);
+  const unsigned int t1 = w[0] + w[1];
+  const int cA = warp_first_true(p, n, [&](int i) { return A[i] > t1; }) - p;
+  const int cB = warp_first_true(q, nb, [&](int i) { return B[i] > t1; }) - q;
+  const int j = (cA + cB) / 2;
+  const int k = 2 * j;
+  // x leaves among the first k: B[y-1] must strictly precede A[x] (leaf first on ties)
+  const int x = warp_first_true(max(0, k - cB), min(k, cA), [&](int xx) {
+    const int y = k - xx;
+    return !(y > 0 && xx < cA && B[q + y - 1] >= A[p + xx]);
+  });
+  if (threadIdx.x == 0) {
+    s->j = j;
+    s->x = x;
+    s->cA = cA;
+    s->cB = cB;
   }
 }
 
-// Merge of R[0, nR) and N[0, nN) (N given by the callable) into out[k0, k1)
-// for this thread's share of [0, nR + nN); sequential from its co-rank.
-template <typename NF>
-__device__ __forceinline__ void merge_share(const unsigned long long* R, int nR, NF N, int nN, unsigned long long* out) {
-  const int total = nR + nN;
-  const int per = (total + (int)blockDim.x - 1) / (int)blockDim.x;
-  const int k0 = min(total, (int)threadIdx.x * per), k1 = min(total, k0 + per);
-  if (k0 >= k1) return;
-  // smallest a such that N[k0-a-1] (if any) precedes R[a] (if any): w(N) < w(R)
-  int lo = max(0, k0 - nN), hi = min(k0, nR);
+// All threads: create this round's j nodes from the first 2j nodes of the
+// merge of A[p, p+x) and B[q, q+2j-x); each thread takes a run of pairs,
+// finds where it starts by a co-rank search and merges sequentially.
+__device__ void two_queue_join(const unsigned int* A, unsigned int* B, int n, const TwoQ& s, unsigned int* parent,
+                               int t, int nt) {
+  const int j = s.j, x = s.x, y = 2 * j - s.x;
+  const unsigned int* Ax = A + s.p;
+  const unsigned int* By = B + s.q;
+  const int per = (j + nt - 1) / nt;
+  const int i0 = min(j, t * per), i1 = min(j, i0 + per);
+  if (i0 >= i1) return;
+  const int k0 = 2 * i0;
+  int lo = max(0, k0 - y), hi = min(k0, x);
   while (lo < hi) {
     const int a = (lo + hi) >> 1;
     const int b = k0 - a;
-    if (b > 0 && a < nR && wt(N(b - 1)) >= wt(R[a])) lo = a + 1;
+    if (b > 0 && a < x && By[b - 1] >= Ax[a]) lo = a + 1;
     else hi = a;
   }
   int a = lo, b = k0 - lo;
-  for (int k = k0; k < k1; ++k) {
-    const bool takeR = b >= nN || (a < nR && wt(R[a]) <= wt(N(b)));
-    out[k] = takeR ? R[a] : N(b);
-    if (takeR) ++a; else ++b;
+  const unsigned int base = (unsigned int)(n + s.nb);
+  for (int i = i0; i < i1; ++i) {
+    unsigned int wsum = 0;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const bool leaf = b >= y || (a < x && Ax[a] <= By[b]);
+      const unsigned int id = leaf ? (unsigned int)(s.p + a) : (unsigned int)(n + s.q + b);
+      wsum += leaf ? Ax[a] : By[b];
+      parent[id] = base + (unsigned int)i;
+      if (leaf) ++a; else ++b;
+    }
+    B[s.nb + i] = wsum;
   }
 }
 
-// One round with both lists in shared memory.
-__device__ int huff_round_smem(const unsigned long long* in, unsigned long long* out, int len, int next,
-                               unsigned int* parent, int* s_j, int& njoin) {
-  const int j = round_joins(in, len, s_j);
-  set_parents(in, j, next, parent);
-  merge_share(in + 2 * j, len - 2 * j, [&](int b) { return nn_node(in, b, next); }, j, out);
-  __syncthreads();
-  njoin = j;
-  return len - j;
-}
+// Returns the number of rounds; rstart[r] is the first node id made in round r.
+// Warp 0 runs rounds of at most kWarpJoin pairs on its own (no block-wide
+// barrier); a larger round is joined by the whole block.
+constexpr int kWarpJoin = 256;
 
-// One round with the lists in the workspace: the output is cut into tiles of
-// kCbTile; one warp per tile boundary finds its co-rank, then each tile's
-// nodes are loaded into shared memory (coalesced) and merged there.
-__device__ int huff_round_global(const unsigned long long* in, unsigned long long* out, int len, int next,
-                                 unsigned int* parent, unsigned long long* sR, unsigned long long* sN, int* s_j,
-                                 int* s_cr, int& njoin) {
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
-  const int j = round_joins(in, len, s_j);
-  set_parents(in, j, next, parent);
-  const unsigned long long* R = in + 2 * j;
-  const int lenR = len - 2 * j;
-  const int total = lenR + j;
-  const int ntile = (total + kCbTile - 1) / kCbTile;  // <= 6 for 2^16 symbols
-  if (wid <= ntile) {
-    const int k = min(total, wid * kCbTile);
-    const int a = warp_first_true(max(0, k - j), min(k, lenR), [&](int a) {
-      const int b = k - a;
-      return !(b > 0 && a < lenR && wt(nn_node(in, b - 1, next)) >= wt(R[a]));
-    });
-    if (lane == 0) s_cr[wid] = a;
+__device__ int huff_two_queue(const unsigned int* A, unsigned int* B, int n, unsigned int* parent, int* rstart,
+                              TwoQ* s, int* s_flag) {
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    s->p = 0;
+    s->q = 0;
+    s->nb = 0;
+    s_flag[0] = 0;  // done
+    s_flag[1] = 0;  // rounds
   }
   __syncthreads();
-  for (int t = 0; t < ntile; ++t) {
-    const int k0 = t * kCbTile, k1 = min(total, k0 + kCbTile);
-    const int a0 = s_cr[t], a1 = s_cr[t + 1];
-    const int b0 = k0 - a0, b1 = k1 - a1;
-    for (int i = tid; i < a1 - a0; i += nt) sR[i] = R[a0 + i];
-    for (int i = tid; i < b1 - b0; i += nt) sN[i] = nn_node(in, b0 + i, next);
+  while (true) {
+    if (tid < 32) {
+      while (true) {
+        if ((n - s->p) + (s->nb - s->q) <= 1) {
+          if (tid == 0) s_flag[0] = 1;
+          break;
+        }
+        two_queue_plan(A, B, n, s);
+        __syncwarp();
+        const TwoQ c = *s;
+        if (c.j > kWarpJoin) break;
+        if (tid == 0) rstart[s_flag[1]] = n + c.nb;
+        two_queue_join(A, B, n, c, parent, tid, 32);
+        __syncwarp();
+        if (tid == 0) {
+          s->p = c.p + c.x;
+          s->q = c.q + 2 * c.j - c.x;
+          s->nb = c.nb + c.j;
+          s_flag[1] += 1;
+        }
+        __syncwarp();
+      }
+    }
     __syncthreads();
-    merge_share(sR, a1 - a0, [&](int b) { return sN[b]; }, b1 - b0, out + k0);
+    if (s_flag[0]) break;
+    const TwoQ c = *s;
+    if (tid == 0) rstart[s_flag[1]] = n + c.nb;
+    two_queue_join(A, B, n, c, parent, tid, blockDim.x);
+    __syncthreads();
+    if (tid == 0) {
+      s->p = c.p + c.x;
+      s->q = c.q + 2 * c.j - c.x;
+      s->nb = c.nb + c.j;
+      s_flag[1] += 1;
+    }
     __syncthreads();
   }
-  njoin = j;
-  return total;
+  return s_flag[1];
 }
 
 // Depth of every leaf from the parent links, walked from the root down one
@@ -303,8 +407,8 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const unsigned long lon
   extern __shared__ __align__(16) unsigned char arena[];
   __shared__ unsigned long long s_scan[32];
   __shared__ int s_bits[128];
-  __shared__ unsigned int s_first[32], s_offs[32], s_lend[32];
-  __shared__ int s_u[4], s_cr[40];
+  __shared__ unsigned int s_lend[32];
+  __shared__ int s_u[4];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nsym = 1 << m;
   if (st->err) return;
@@ -357,7 +461,7 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const unsigned long lon
       }
     }
   }
-  // largest count -> number of radix passes
+  // largest count -> number of 4-bit radix passes
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
   if ((tid & 31) == 0) s_scan[tid >> 5] = mx;
@@ -366,7 +470,7 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const unsigned long lon
     unsigned long long m2 = 0;
     for (int i = 0; i < 32; ++i) m2 = max(m2, s_scan[i]);
     int np = 0;
-    while (np < 4 && (m2 >> (8 * np)) != 0) ++np;
+    while (np < 8 && (m2 >> (4 * np)) != 0) ++np;
     s_u[1] = np;
   }
   const unsigned long long off_bb = al16(off_cb + 4ull * (unsigned long long)n);
@@ -391,56 +495,44 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const unsigned long lon
     return;
   }
   // leaves sorted by (count, symbol): stable sort by count of the symbol-ordered list
-  unsigned int* ks = reinterpret_cast<unsigned int*>(hs.la);
-  uint16_t* vs = reinterpret_cast<uint16_t*>(hs.lb);
+  unsigned int* ks;
+  uint16_t* vs;
   {
-    unsigned int* s_hist = reinterpret_cast<unsigned int*>(arena);
-    unsigned int *ka, *kb;
-    uint16_t *va, *vb;
-    if (n <= kCbSortN) {
-      ka = s_hist + 32 * 256;
-      kb = ka + kCbSortN;
-      va = reinterpret_cast<uint16_t*>(kb + kCbSortN);
-      vb = va + kCbSortN;
+    unsigned short* s_cnt = reinterpret_cast<unsigned short*>(arena);
+    unsigned int* sk0 = reinterpret_cast<unsigned int*>(arena + 16 * kCbThreads * sizeof(unsigned short));
+    unsigned int* sk1 = sk0 + kSegN;
+    uint16_t* sv0 = reinterpret_cast<uint16_t*>(sk1 + kSegN);
+    uint16_t* sv1 = sv0 + kSegN;
+    ks = reinterpret_cast<unsigned int*>(hs.la);
+    vs = reinterpret_cast<uint16_t*>(hs.lb);
+    if (n <= kSegN) {
+      for (int i = tid; i < n; i += nt) {
+        sk0[i] = kc[i];
+        sv0[i] = vc[i];
+      }
+      __syncthreads();
+      smem_sort(sk0, sv0, sk1, sv1, n, s_u[1], ks, vs, s_cnt, s_scan);
     } else {
-      ka = kc + nsym;
-      va = vc + nsym;
-      kb = reinterpret_cast<unsigned int*>(hs.depth);
-      vb = reinterpret_cast<uint16_t*>(kb + nsym);
+      // in the workspace, 8-bit digits
+      unsigned int* qk = reinterpret_cast<unsigned int*>(hs.depth);
+      uint16_t* qv = reinterpret_cast<uint16_t*>(qk + nsym);
+      cta_radix_sort8(kc, vc, kc + nsym, vc + nsym, qk, qv, ks, vs, n, (s_u[1] + 1) / 2,
+                      reinterpret_cast<unsigned int*>(arena), s_scan);
     }
-    cta_radix_sort(kc, vc, ka, va, kb, vb, ks, vs, n, s_u[1], s_hist, s_scan);
   }
   for (int i = tid; i < 128; i += nt) s_bits[i] = 0;
-  // merge rounds: in the workspace while the list is long, in shared memory after
-  unsigned long long* ga = reinterpret_cast<unsigned long long*>(hs.w);
-  unsigned long long* gb = ga + nsym;
-  unsigned long long* sa = reinterpret_cast<unsigned long long*>(arena);
-  unsigned long long* sb = sa + kCbListN;
+  // merge rounds on the two queues: in shared memory when both fit
   unsigned int* parent = reinterpret_cast<unsigned int*>(hs.parent);
-  bool in_smem = n <= kCbListN;
-  unsigned long long* la = in_smem ? sa : ga;
-  unsigned long long* lb = in_smem ? sb : gb;
-  for (int i = tid; i < n; i += nt) la[i] = ((unsigned long long)ks[i] << 32) | (unsigned long long)i;
-  __syncthreads();
-  int len = n, next = n, rounds = 0;
-  while (len > 1) {
-    if (tid == 0) hs.rstart[rounds] = next;
-    int j;
-    if (in_smem) len = huff_round_smem(la, lb, len, next, parent, &s_u[2], j);
-    else len = huff_round_global(la, lb, len, next, parent, sa, sb, &s_u[2], s_cr, j);
-    next += j;
-    ++rounds;
-    if (!in_smem && len <= kCbListN) {
-      for (int i = tid; i < len; i += nt) sa[i] = lb[i];
-      __syncthreads();
-      la = sa;
-      lb = sb;
-      in_smem = true;
-    } else {
-      unsigned long long* t = la; la = lb; lb = t;
-    }
+  const unsigned int* qa = ks;
+  unsigned int* qb = reinterpret_cast<unsigned int*>(hs.w);
+  if (n <= kCbQueueN) {
+    unsigned int* sA = reinterpret_cast<unsigned int*>(arena);
+    for (int i = tid; i < n; i += nt) sA[i] = ks[i];
+    qa = sA;
+    qb = sA + kCbQueueN;
   }
-  __syncthreads();
+  __shared__ TwoQ s_q;
+  const int rounds = huff_two_queue(qa, qb, n, parent, hs.rstart, &s_q, &s_u[2]);
   const int nnode = 2 * n - 1;
   if ((size_t)nnode * 6 <= kCbSmem) {
     // walk the tree in shared memory: parent links copied in, depths beside them
@@ -475,39 +567,40 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const unsigned long lon
       const unsigned int prevc = l > 1 ? (unsigned int)s_bits[l - 1] : 0u;
       code = (code + prevc) << 1;
       off += prevc;
-      s_first[l] = code;
-      s_offs[l] = off;
+      st->cb_first[l] = code;
+      st->cb_offs[l] = off;
     }
   }
   __syncthreads();
   const int maxlen = s_u[0];
-  // canonical order: most frequent first (the sorted leaf list reversed)
-  constexpr int UA = 4;
-  for (int i0 = 0; i0 < n; i0 += nt * UA) {
-    unsigned int sym[UA];
-#pragma unroll
-    for (int u = 0; u < UA; ++u) {
-      const int i = i0 + u * nt + tid;
-      sym[u] = i < n ? vs[n - 1 - i] : 0u;
+  // canonical order: most frequent first (the sorted leaf list reversed);
+  // the code tables indexed by symbol are filled by k_cb_assign
+  for (int i = tid; i < n; i += nt) {
+    const unsigned int leaf = (unsigned int)(n - 1 - i);
+    // length = largest l with leaf < s_lend[l] (s_lend decreases with l)
+    int lo2 = 1, hi2 = maxlen;
+    while (lo2 < hi2) {
+      const int mid = (lo2 + hi2 + 1) >> 1;
+      if (leaf < s_lend[mid]) lo2 = mid; else hi2 = mid - 1;
     }
-#pragma unroll
-    for (int u = 0; u < UA; ++u) {
-      const int i = i0 + u * nt + tid;
-      if (i >= n) break;
-      const unsigned int leaf = (unsigned int)(n - 1 - i);
-      // length = largest l with leaf < s_lend[l] (s_lend decreases with l)
-      int lo2 = 1, hi2 = maxlen;
-      while (lo2 < hi2) {
-        const int mid = (lo2 + hi2 + 1) >> 1;
-        if (leaf < s_lend[mid]) lo2 = mid; else hi2 = mid - 1;
-      }
-      const int l = lo2;
-      lens[sym[u]] = (uint8_t)l;
-      cw[sym[u]] = (s_first[l] + ((unsigned int)i - s_offs[l])) | ((unsigned int)l << 24);
-      st_u32(out + off_cb + 4ull * i, sym[u] | ((unsigned int)l << 16));
-    }
+    st_u32(out + off_cb + 4ull * i, (unsigned int)vs[leaf] | ((unsigned int)lo2 << 16));
   }
   for (unsigned long long i = off_cb + 4ull * n + tid; i < off_bb; i += nt) out[i] = 0;
+}
+
+// Length and code word of every used symbol, from the ordered codebook
+// section: entry i of length l has code cb_first[l] + (i - cb_offs[l]).
+// Many CTAs, so the writes scattered by symbol spread over the GPU.
+__global__ void __launch_bounds__(256) k_cb_assign(const uint8_t* __restrict__ out, uint8_t* lens, uint32_t* cw,
+                                                   const State* __restrict__ st) {
+  if (st->err) return;
+  const unsigned int n = st->n_used;
+  const unsigned int i = blockIdx.x * 256u + threadIdx.x;
+  if (n <= 1 || i >= n) return;
+  const unsigned int e = *reinterpret_cast<const unsigned int*>(out + st->off_cb + 4ull * i);
+  const unsigned int sym = e & 0xFFFFu, l = e >> 16;
+  lens[sym] = (uint8_t)l;
+  cw[sym] = (st->cb_first[l] + (i - st->cb_offs[l])) | (l << 24);
 }
 
 int launch_codebook(const unsigned long long* hist, int m, uint8_t* lens, uint32_t* cw, State* st,
@@ -518,6 +611,7 @@ int launch_codebook(const unsigned long long* hist, int m, uint8_t* lens, uint32
   ProfScope p(kStCodebook, s);
   k_codebook<<<1, kCbThreads, smem, s>>>(hist, m, lens, cw, st, hs, out, (unsigned long long)g.nblocks, hi.off_cb,
                                          hi.cap);
+  k_cb_assign<<<((1u << m) + 255u) / 256u, 256, 0, s>>>(out, lens, cw, st);
   return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
 

@@ -42,6 +42,8 @@ struct State {
   unsigned long long out_size;
   unsigned int ticket;
   unsigned int pad2[15];
+  // a10: first canonical code and first codebook index of every length
+  unsigned int cb_first[32], cb_offs[32];
 };
 
 struct Mlp {
