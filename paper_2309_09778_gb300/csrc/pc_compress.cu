@@ -340,7 +340,64 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restr
     // a6-a8: predict, quantize, cost (and, for Lorenzo only, a9 histogram)
     const long long b = (bz * g.nb[1] + by) * g.nb[2] + bx;
     int cz = 0, cn = 0, nz = 0;
-    if (bvalid) {
+    if constexpr (MODE != 0 && K > 0) {
+      // two points per step through the packed perceptron forward
+      if (bvalid) {
+#pragma unroll 1
+        for (int i = 0; i < PPT; i += 2) {
+          int inp[2][K];
+          int vks[2], js[2];
+          bool oks[2], vals[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int j = t + (i + u) * TS;
+            const bool inr = i + u < PPT && j < BV;
+            js[u] = inr ? j : -1;
+            const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+            const bool valid = inr && (bfull || (lz < e0 && ly < e1 && lx < e2)) && j != 0;
+            vals[u] = valid;
+            uint16_t codez = 0;
+            int vk = 0;
+            bool okp = false;
+            if (valid) {
+              const int pd = dq[j];
+              okp = pd & 1;
+              const int v = (pd >> 1) - da;
+              vk = v > (1 << 30) ? (1 << 30) : (v < -(1 << 30) ? -(1 << 30) : v);
+              const int pj = PD::at(lz, ly, lx);
+              int lzp = 0;
+#pragma unroll
+              for (int q = 0; q < 7; ++q) lzp += lz_w(7, q) * vp[pj + PD::off(s7_dz(q), s7_dy(q), s7_dx(q))];
+              const int kz = vk - lzp;
+              const int az = kz < 0 ? -kz : kz;
+              cz += bitlen_u((unsigned int)(az < R ? az : R));
+              codez = (az <= R - 1 && okp) ? (uint16_t)(kz + R) : 0;
+#pragma unroll
+              for (int q = 0; q < K; ++q) inp[u][q] = vp[pj + PD::off(st_dz(K, q), st_dy(K, q), st_dx(K, q))];
+            } else {
+#pragma unroll
+              for (int q = 0; q < K; ++q) inp[u][q] = 0;
+            }
+            vks[u] = vk;
+            oks[u] = okp;
+            if (inr) s_cz[team * BV + j] = codez;
+          }
+          float pv[2];
+          mlp_fwd2<K, H1, H2>(mlp, inp[0], inp[1], sig, unsig, pv[0], pv[1]);
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            uint16_t coden = 0;
+            if (vals[u]) {
+              const long long kn = (long long)vks[u] - (long long)round_pred(pv[u]);
+              const long long an = kn < 0 ? -kn : kn;
+              cn += bitlen_u((unsigned int)(an < R ? an : R));
+              coden = (an <= R - 1 && oks[u]) ? (uint16_t)(kn + R) : 0;
+            }
+            if (js[u] >= 0) s_cn[team * BV + js[u]] = coden;
+          }
+        }
+      }
+    } else if (bvalid) {
 #pragma unroll(MODE ? 1 : PPT)
       for (int i = 0; i < PPT; ++i) {
         const int j = t + i * TS;

@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(256) k_huff_decode(Geo g, const uint8_t* __res
 template <int BV, int PV, int TSZ>
 constexpr size_t recon_smem_bytes() {
   constexpr int G = BrickShape<BV>::G;
-  return sizeof(Tabs) + (size_t)((G * PV + 3) & ~3) * 4 + (size_t)G * BV * TSZ + (size_t)G * BV * 2 * 2 +
+  return sizeof(Tabs) + (size_t)((G * PV + 3) & ~3) * 4 + (size_t)G * BV * TSZ * 2 + (size_t)G * BV * 2 * 2 +
          (size_t)BV * 2 + 16;
 }
 
@@ -320,7 +320,8 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
   Tabs& tb = *reinterpret_cast<Tabs*>(smem);
   int* s_vp = reinterpret_cast<int*>(smem + sizeof(Tabs));          // G*PV padded centred codes
   T* s_x = reinterpret_cast<T*>(s_vp + VPR);                        // G*BV
-  uint16_t* s_cd = reinterpret_cast<uint16_t*>(s_x + G * BV);       // G*BV
+  T* s_ov = s_x + G * BV;                                           // G*BV balance points of each block
+  uint16_t* s_cd = reinterpret_cast<uint16_t*>(s_ov + G * BV);      // G*BV
   uint16_t* s_rk = s_cd + G * BV;                                   // G*BV balance-point ranks
   uint16_t* s_list = s_rk + G * BV;                                 // BV wave order
   __shared__ int s_ws[SZ + 2];
@@ -328,6 +329,8 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
   __shared__ unsigned int s_wt[G][NWT];
   __shared__ int s_da[G];
   __shared__ int s_bad;
+  __shared__ int s_usen[G], s_no[G], s_e2[G];
+  __shared__ unsigned long long s_obase[G];
 
   State c;
   c.Kp = di.Kp; c.Kn = di.Kn; c.Zq = di.Zq; c.S = di.S;
@@ -432,6 +435,19 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
     const bool usen = bvalid && ((*reinterpret_cast<const unsigned int*>(in + di.off_bb + 4ull * b)) >> 31);
     const unsigned long long obase = bvalid ? ds.ooff[b] : 0ull;
     if (bvalid && (nzero + 1u != no || (usen && !MODE))) bad = true;
+    if (t == 0) {
+      s_usen[team] = usen;
+      s_no[team] = (int)no;
+      s_e2[team] = e2;
+      s_obase[team] = obase;
+    }
+    // the block's balance points (stored contiguously) into shared memory
+    T* ovs = s_ov + team * BV;
+    if (bvalid) {
+      const unsigned long long nv = min((unsigned long long)min(no, (unsigned int)BV),
+                                        obase < di.n_out ? di.n_out - obase : 0ull);
+      for (int r = t; r < (int)nv; r += TS) ovs[r] = ov[obase + r];
+    }
     // anchor
     if (bvalid && t == 0) {
       const T xa = ov[obase < di.n_out ? obase : 0];
@@ -442,6 +458,81 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
     }
     __syncthreads();
     const int da = s_da[team];
+    if constexpr (MODE != 0 && K > 0) {
+      // Each wave of all G blocks at once, flattened over the CTA, two points
+      // per thread through the packed perceptron forward.
+      for (int sw = 1; sw < nwave; ++sw) {
+        const int w0 = s_ws[sw], S = s_ws[sw + 1] - w0;
+        const int tot = G * S, half = (tot + 1) >> 1;
+        for (int pr2 = tid; pr2 < half; pr2 += 256) {
+          int inp[2][K];
+          int jj[2], gbs[2], pjs[2];
+          unsigned int cds[2];
+          bool act[2], need[2];
+          long long lzp[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int f = pr2 + u * half;
+            act[u] = false;
+            need[u] = false;
+            lzp[u] = 0;
+            cds[u] = 0;
+            const int gb = f < tot ? f / S : 0;
+            const int j = f < tot ? s_list[w0 + f - gb * S] : 0;
+            const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+            const int e2g = s_e2[gb];
+            const bool fullg = e0 == B0 && e1 == B1 && e2g == B2;
+            const bool valid = f < tot && e2g > 0 && (fullg || (lz < e0 && ly < e1 && lx < e2g));
+            const int pj = PD::at(lz, ly, lx);
+            const int* vpg = s_vp + gb * PD::PV;
+            jj[u] = j;
+            gbs[u] = gb;
+            pjs[u] = pj;
+            if (valid) {
+              act[u] = true;
+              const unsigned int code = s_cd[gb * BV + j];
+              cds[u] = code;
+              if (code == 0) {
+                const unsigned long long ob = s_obase[gb];
+                unsigned int r = 1u + s_rk[gb * BV + j];
+                if (r >= (unsigned int)s_no[gb] || ob + r >= di.n_out) { bad = true; r = 0; }
+                const T xv = s_ov[gb * BV + r];
+                bool okk;
+                const int q = Num<T>::transform(xv, c, tb, okk);
+                s_x[gb * BV + j] = xv;
+                s_vp[gb * PD::PV + pj] = clampv((long long)q - s_da[gb]);
+                act[u] = false;
+              } else if (s_usen[gb]) {
+                need[u] = true;
+              } else {
+                int acc = 0;
+#pragma unroll
+                for (int si = 0; si < 7; ++si) acc += lz_w(7, si) * vpg[pj + PD::off(s7_dz(si), s7_dy(si), s7_dx(si))];
+                lzp[u] = acc;
+              }
+            }
+#pragma unroll
+            for (int si = 0; si < K; ++si)
+              inp[u][si] = need[u] ? vpg[pj + PD::off(st_dz(K, si), st_dy(K, si), st_dx(K, si))] : 0;
+          }
+          float pv[2] = {0.0f, 0.0f};
+          if (need[0] || need[1]) mlp_fwd2<K, H1, H2>(mlp, inp[0], inp[1], sig, unsig, pv[0], pv[1]);
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            if (!act[u]) continue;
+            const long long prd = need[u] ? (long long)round_pred(pv[u]) : lzp[u];
+            const int gb = gbs[u];
+            const long long qq = (long long)s_da[gb] + prd + ((long long)cds[u] - R);
+            int q;
+            if (qq > 2147483647LL || qq < -2147483647LL) { bad = true; q = 0; }
+            else q = (int)qq;
+            s_x[gb * BV + jj[u]] = Num<T>::recon(q, c, tb);
+            s_vp[gb * PD::PV + pjs[u]] = clampv((long long)q - s_da[gb]);
+          }
+        }
+        __syncthreads();
+      }
+    } else
     for (int sw = 1; sw < nwave; ++sw) {
       if (bvalid) {
         for (int idx = s_ws[sw] + t; idx < s_ws[sw + 1]; idx += TS) {
@@ -452,9 +543,9 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
           const unsigned int code = cd[j];
           int q;
           if (code == 0) {
-            unsigned long long oi = obase + 1ull + rk[j];
-            if (oi >= obase + no || oi >= di.n_out) { bad = true; oi = obase; }
-            const T xv = ov[oi];
+            unsigned int r = 1u + rk[j];
+            if (r >= no || obase + r >= di.n_out) { bad = true; r = 0; }
+            const T xv = ovs[r];
             bool okk;
             q = Num<T>::transform(xv, c, tb, okk);
             xs[j] = xv;

@@ -326,6 +326,58 @@ __device__ __forceinline__ float mlp_fwd(const Mlp& m, const int* v, float sig, 
   }
 }
 
+// Two points at once through the same perceptron, on the packed two-lane
+// fp32 operations (__ffma2_rn, __fmul2_rn): each lane performs the correctly
+// rounded IEEE operation of the scalar form, so both results equal
+// mlp_fwd's bit for bit while the instruction count nearly halves.  The
+// leaky ReLU is max(v, alpha v), the same value as the scalar select for
+// every v (alpha > 0; a zero keeps its sign).
+__device__ __forceinline__ float2 f2_leaky(float2 v) {
+  const float2 m = __fmul2_rn(v, make_float2(kAlpha, kAlpha));
+  return make_float2(fmaxf(v.x, m.x), fmaxf(v.y, m.y));
+}
+
+template <int K, int H1, int H2>
+__device__ __forceinline__ void mlp_fwd2(const Mlp& m, const int* va, const int* vb, float sig, float unsig, float& pa,
+                                         float& pb) {
+  auto W = [&](int idx) { return make_float2(m.w[idx], m.w[idx]); };
+  float2 u[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+    u[i] = make_float2(__fmul_rn(__int2float_rn(va[i]), sig), __fmul_rn(__int2float_rn(vb[i]), sig));
+  float2 a1[H1];
+#pragma unroll
+  for (int j = 0; j < H1; ++j) {
+    float2 acc = W(H1 * K + j);
+#pragma unroll
+    for (int i = 0; i < K; ++i) acc = __ffma2_rn(W(j * K + i), u[i], acc);
+    a1[j] = f2_leaky(acc);
+  }
+  constexpr int P2 = H1 * K + H1;
+  float2 o;
+  if constexpr (H2 > 0) {
+    float2 a2[H2];
+#pragma unroll
+    for (int j = 0; j < H2; ++j) {
+      float2 acc = W(P2 + H2 * H1 + j);
+#pragma unroll
+      for (int i = 0; i < H1; ++i) acc = __ffma2_rn(W(P2 + j * H1 + i), a1[i], acc);
+      a2[j] = f2_leaky(acc);
+    }
+    constexpr int P3 = P2 + H2 * H1 + H2;
+    o = W(P3 + H2);
+#pragma unroll
+    for (int j = 0; j < H2; ++j) o = __ffma2_rn(W(P3 + j), a2[j], o);
+  } else {
+    o = W(P2 + H1);
+#pragma unroll
+    for (int j = 0; j < H1; ++j) o = __ffma2_rn(W(P2 + j), a1[j], o);
+  }
+  o = __fmul2_rn(o, make_float2(unsig, unsig));
+  pa = o.x;
+  pb = o.y;
+}
+
 // Runtime-shaped forward for widths without a compiled instance.
 __device__ __forceinline__ float mlp_fwd_rt(const Mlp& m, const int* v, float sig, float unsig) {
   const int K = m.k, H1 = m.h1, H2 = m.h2;
