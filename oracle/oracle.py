@@ -21,7 +21,7 @@ _lock = threading.Lock()
 _lib = None
 
 F32, F64 = 0, 1
-PRED_LORENZO, PRED_MLP = 0, 1
+PRED_LORENZO, PRED_MLP, PRED_MLP_BF16 = 0, 1, 2
 ERR = {0: "ok", -1: "arg", -2: "dtype", -3: "nonfinite", -4: "capacity", -5: "corrupt", -8: "eb_range"}
 LMAX = 24
 BATCH = 256
@@ -51,7 +51,7 @@ class Consts(C.Structure):
 class Params(C.Structure):
     _fields_ = [("eb", C.c_double), ("block", C.c_int * 3), ("pred", C.c_int), ("stencil", C.c_int),
                 ("h1", C.c_int), ("h2", C.c_int), ("m", C.c_int), ("s_in", C.c_int),
-                ("weights", C.c_void_p)]
+                ("weights", C.c_void_p), ("qnet", C.c_void_p)]
 
 
 class Dump(C.Structure):
@@ -126,6 +126,14 @@ def lib():
             L.orc_train.argtypes = [C.c_void_p, u64p, C.c_int, C.c_double, C.POINTER(C.c_int), C.c_int, C.c_int,
                                     C.c_int, C.c_int, C.c_uint64, C.c_uint32, C.c_int, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.POINTER(C.c_int), C.c_void_p]
+            L.orc_qnet_len.restype = C.c_int; L.orc_qnet_len.argtypes = [C.c_int] * 3
+            L.orc_mlp_pred_q.restype = C.c_int32; L.orc_mlp_pred_q.argtypes = [C.c_void_p, C.c_void_p]
+            L.orc_qnet_build.restype = C.c_int
+            L.orc_qnet_build.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                         C.c_uint64, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p]
+            L.orc_quantize.restype = C.c_int
+            L.orc_quantize.argtypes = [C.c_void_p, u64p, C.c_int, C.c_double, C.POINTER(C.c_int), C.c_int, C.c_int,
+                                       C.c_int, C.c_uint64, C.c_uint32, C.c_void_p, C.c_int, C.c_void_p]
             _lib = L
     return _lib
 
@@ -225,6 +233,48 @@ def mlp_pred32(w: np.ndarray, k, h1, h2, s_in, v) -> int:
     return lib().orc_mlp_pred32(_p(w), k, h1, h2, s_in, _p(v))
 
 
+# ------------------------------------------------ fixed-point (BF16) perceptron
+def qnet_len(k: int, h1: int, h2: int) -> int:
+    return lib().orc_qnet_len(k, h1, h2)
+
+
+def mlp_pred_q(q: np.ndarray, v) -> int:
+    """Prediction of the fixed-point network q (int64 layout of orc_qnet_len)."""
+    q = np.ascontiguousarray(q, np.int64)
+    v = np.ascontiguousarray(v, np.int32)
+    return lib().orc_mlp_pred_q(_p(q), _p(v))
+
+
+def qnet_build(w, k, h1, h2, s_in, tin, tuse, vin=None, vuse=None) -> np.ndarray:
+    """Quantize FP32 weights with shifts chosen from the given (used) sample inputs."""
+    w = np.ascontiguousarray(w, np.float32)
+    tin = np.ascontiguousarray(tin, np.int32).reshape(-1)
+    tuse = np.ascontiguousarray(tuse, np.uint8)
+    if vin is None:
+        vin = np.zeros(k, np.int32); vuse = np.zeros(1, np.uint8); nv = 0
+    else:
+        vin = np.ascontiguousarray(vin, np.int32).reshape(-1); vuse = np.ascontiguousarray(vuse, np.uint8)
+        nv = vuse.size
+    q = np.zeros(qnet_len(k, h1, h2), np.int64)
+    st = lib().orc_qnet_build(_p(w), k, h1, h2, s_in, _p(tin), _p(tuse), tuse.size, _p(vin), _p(vuse), nv, _p(q))
+    assert st == 0
+    return q
+
+
+def quantize(x: np.ndarray, eb: float, w, s_in: int, block=(8, 8, 8), k=7, h1=16, h2=16, seed=0,
+             thr32=None) -> np.ndarray:
+    """Fixed-point form of the trained perceptron w, shifts from the training phase's samples."""
+    x = np.ascontiguousarray(x)
+    if thr32 is None:
+        thr32 = int(0.1 * 2 ** 32)
+    w = np.ascontiguousarray(w, np.float32)
+    q = np.zeros(qnet_len(k, h1, h2), np.int64)
+    b = (C.c_int * 3)(*block)
+    st = lib().orc_quantize(_p(x), _dims(x), _dtype_code(x), eb, b, k, h1, h2, seed, thr32, _p(w), s_in, _p(q))
+    assert st == 0, st
+    return q
+
+
 def huffman_lengths(hist: np.ndarray, lmax: int = LMAX, with_order: bool = False):
     """Code lengths per symbol; with_order also returns the code order (most frequent first)."""
     h = np.ascontiguousarray(hist, np.uint64)
@@ -249,7 +299,7 @@ def canonical_codes(lens: np.ndarray, order=None) -> np.ndarray:
     return out
 
 
-def _params(eb, block, pred, stencil, h1, h2, m, s_in, w):
+def _params(eb, block, pred, stencil, h1, h2, m, s_in, w, q=None):
     p = Params()
     p.eb = eb
     p.block[:] = list(block)
@@ -257,6 +307,7 @@ def _params(eb, block, pred, stencil, h1, h2, m, s_in, w):
     p.stencil = stencil
     p.h1, p.h2, p.m, p.s_in = h1, h2, m, s_in
     p.weights = None if w is None else w.ctypes.data
+    p.qnet = None if q is None else q.ctypes.data
     return p
 
 
@@ -267,16 +318,22 @@ def compress_bound(shape3, dtype: int, block, m: int = 16, nweights: int = 0) ->
 
 
 def compress(x: np.ndarray, eb: float, block=(8, 8, 8), weights=None, stencil=7, h1=16, h2=16,
-             m: int = 16, s_in: int = 0, dump: bool = False):
-    """Compress with the oracle.  Returns (status, bytes[, dump dict])."""
+             m: int = 16, s_in: int = 0, dump: bool = False, qnet=None):
+    """Compress with the oracle.  Returns (status, bytes[, dump dict]).  `qnet` selects the
+    fixed-point (BF16) perceptron form instead of the FP32 weights."""
     x = np.ascontiguousarray(x)
     dims = _dims(x)
     dt = _dtype_code(x)
     w = None if weights is None else np.ascontiguousarray(weights, np.float32)
+    q = None if qnet is None else np.ascontiguousarray(qnet, np.int64)
     nw = 0 if w is None else w.size
     if w is not None:
         assert nw == mlp_nweights(stencil, h1, h2)
-    p = _params(eb, block, PRED_MLP if w is not None else PRED_LORENZO, stencil, h1, h2, m, s_in, w)
+    if q is not None:
+        assert q.size == qnet_len(stencil, h1, h2)
+        nw = 2 * q.size
+    pred = PRED_MLP_BF16 if q is not None else (PRED_MLP if w is not None else PRED_LORENZO)
+    p = _params(eb, block, pred, stencil, h1, h2, m, s_in, w, q)
     cap = compress_bound(tuple(dims), dt, block, m, nw)
     out = np.zeros(cap, np.uint8)
     size = C.c_uint64()

@@ -428,6 +428,210 @@ int32_t orc_mlp_pred32(const float* w, int k, int h1, int h2, int s_in, const in
   return o_round_pred(orc_mlp_fwd32(w, k, h1, h2, s_in, v));
 }
 
+/* ------------------------------------------------------------------------- */
+/* Fixed-point (BF16) form of the perceptron (Section IV.B network, the      */
+/* precision form evaluated on bf16 tensor-core operands).                    */
+/*                                                                           */
+/* Reading (the paper fixes no inference precision): every weight of layer l */
+/* is an integer |Wq| <= 255 times 2^-e_l, so it is exactly a bf16 value;    */
+/* the stencil inputs are the centred codes clamped to +-(2^16 - 1); the      */
+/* hidden activations are integers clamped to +-(2^15 - 1).  Each layer's    */
+/* sum of products is therefore an exact integer, computed here in int64.   */
+/* (A tensor-core evaluation splits inputs and activations into signed      */
+/* 8-bit limbs, so each partial sum stays below 2^24 and FP32 accumulation  */
+/* is exact in any order and MMA shape.)  Per layer:                         */
+/*   A = sum Wq x + Bq;   leaky(A) = A >= 0 ? A : A / 16   (slope 2^-4)      */
+/*   hidden:  Hq = clamp(rne(leaky(A) 2^-t), +-(2^15 - 1))                   */
+/*   output:  pred = clamp(rne(A 2^-F), +-2^30),  F = sum e - sum t          */
+/* rne = round to nearest, ties to even.  Units: A_1 counts 2^-(e1 + s_in),  */
+/* so B1 = rint(b1 2^(e1 + s_in)); each later layer's bias takes the units   */
+/* of its sum (orc_quantize).                                                */
+/* qnet (int64): k, h1, h2, s_in, e1, e2, e3, t1, t2, then W1[h1][k], B1[h1], */
+/* and for h2 > 0: W2[h2][h1], B2[h2], W3[h2], B3; for h2 = 0: W2[h1], B2    */
+/* (e3 = t2 = 0).                                                             */
+/* ------------------------------------------------------------------------- */
+#define O_QHDR 9
+#define O_QIN 65535
+#define O_QH 32767
+
+int orc_qnet_len(int k, int h1, int h2) {
+  return O_QHDR + h1 * k + h1 + (h2 ? h2 * h1 + h2 + h2 + 1 : h1 + 1);
+}
+
+/* rne(x 2^-s) for integer x */
+static int64_t o_rne_shift(int64_t x, int s) {
+  if (s <= 0) return x * ((int64_t)1 << (-s));
+  if (s >= 62) return 0;
+  int64_t d = (int64_t)1 << s;
+  int64_t q = x / d, r = x % d;
+  if (r < 0) { q -= 1; r += d; }
+  int64_t h = d >> 1;
+  if (r > h || (r == h && (q & 1))) q += 1;
+  return q;
+}
+
+static int64_t o_leaky_requant(int64_t a, int t) {
+  int64_t h = a >= 0 ? o_rne_shift(a, t) : o_rne_shift(a, t + 4);
+  return h > O_QH ? O_QH : (h < -O_QH ? -O_QH : h);
+}
+
+/* 16 |leaky(A)|: the activation magnitude that sets the shift t */
+static int64_t o_leaky16(int64_t a) { return a >= 0 ? 16 * a : -a; }
+
+/* hidden activations of layer 1 (and 2), writing the integer pre-activations */
+static void o_q_hidden(const int64_t* q, const int32_t* v, int64_t* a1, int64_t* h1q, int64_t* a2, int64_t* h2q) {
+  int k = (int)q[0], h1 = (int)q[1], h2 = (int)q[2];
+  int t1 = (int)q[7], t2 = (int)q[8];
+  const int64_t* W1 = q + O_QHDR;
+  const int64_t* B1 = W1 + h1 * k;
+  int64_t x[13];
+  for (int i = 0; i < k; i++) x[i] = v[i] > O_QIN ? O_QIN : (v[i] < -O_QIN ? -O_QIN : v[i]);
+  for (int j = 0; j < h1; j++) {
+    int64_t acc = 0;
+    for (int i = 0; i < k; i++) acc += W1[j * k + i] * x[i];
+    a1[j] = acc + B1[j];
+    h1q[j] = o_leaky_requant(a1[j], t1);
+  }
+  if (h2 && a2) {
+    const int64_t* W2 = B1 + h1;
+    const int64_t* B2 = W2 + h2 * h1;
+    for (int j = 0; j < h2; j++) {
+      int64_t acc = 0;
+      for (int i = 0; i < h1; i++) acc += W2[j * h1 + i] * h1q[i];
+      a2[j] = acc + B2[j];
+      h2q[j] = o_leaky_requant(a2[j], t2);
+    }
+  }
+}
+
+int32_t orc_mlp_pred_q(const int64_t* q, const int32_t* v) {
+  int k = (int)q[0], h1 = (int)q[1], h2 = (int)q[2];
+  int e1 = (int)q[4], e2 = (int)q[5], e3 = (int)q[6], t1 = (int)q[7], t2 = (int)q[8];
+  int64_t a1[O_MAXH], h1q[O_MAXH], a2[O_MAXH], h2q[O_MAXH];
+  o_q_hidden(q, v, a1, h1q, a2, h2q);
+  const int64_t* B1 = q + O_QHDR + h1 * k;
+  int64_t acc;
+  int F;
+  if (h2) {
+    const int64_t* W3 = B1 + h1 + h2 * h1 + h2;
+    acc = W3[h2];
+    int64_t s = 0;
+    for (int j = 0; j < h2; j++) s += W3[j] * h2q[j];
+    acc += s;
+    F = e1 + e2 + e3 - t1 - t2;
+  } else {
+    const int64_t* W2 = B1 + h1;
+    int64_t s = 0;
+    for (int j = 0; j < h1; j++) s += W2[j] * h1q[j];
+    acc = s + W2[h1];
+    F = e1 + e2 - t1;
+  }
+  int64_t p = o_rne_shift(acc, F);
+  if (p > 1073741824LL) p = 1073741824LL;
+  if (p < -1073741824LL) p = -1073741824LL;
+  return (int32_t)p;
+}
+
+/* Largest e with max|w| 2^e <= 255 (0 for all-zero weights), kept in [-30, 30]. */
+static int o_wexp(const float* w, int n, int stride, int rows, int cols) {
+  float m = 0.0f;
+  for (int r = 0; r < rows; r++)
+    for (int c = 0; c < cols; c++) {
+      float a = fabsf(w[r * stride + c]);
+      if (a > m) m = a;
+    }
+  (void)n;
+  if (m == 0.0f) return 0;
+  int E;
+  float fr = frexpf(m, &E);
+  int e = fr <= 255.0f / 256.0f ? 8 - E : 7 - E;
+  return e < -30 ? -30 : (e > 30 ? 30 : e);
+}
+
+static int64_t o_qw(float w, int e) { return (int64_t)rintf(ldexpf(w, e)); }
+
+static int64_t o_qb(float b, int E) {
+  double v = rint(ldexp((double)b, E));
+  const double lim = 1099511627776.0; /* 2^40 */
+  return (int64_t)(v > lim ? lim : (v < -lim ? -lim : v));
+}
+
+/* Smallest t in [-24, 40] with M 2^-t <= 16 (2^15 - 1), M = max 16|leaky(A)|. */
+static int o_shift_for(int64_t M) {
+  if (M <= 0) return 0;
+  const int64_t lim = 16 * (int64_t)O_QH;
+  for (int t = -24; t < 40; t++) {
+    if (t >= 0 ? (M <= (lim << t)) : ((M << (-t)) <= lim)) return t;
+  }
+  return 40;
+}
+
+/* Quantize FP32 weights w (orc_mlp layout) with input scale s_in into qnet,
+ * choosing the activation shifts from the used training and validation
+ * samples (inputs tin/vin as gathered for training). */
+int orc_qnet_build(const float* w, int k, int h1, int h2, int s_in, const int32_t* tin, const uint8_t* tus,
+                   uint64_t nt, const int32_t* vin, const uint8_t* vus, uint64_t nv, int64_t* q) {
+  int hl = h2 ? h2 : h1;
+  const float* W1 = w;
+  const float* b1 = W1 + h1 * k;
+  const float* W2 = b1 + h1;
+  const float* b2 = h2 ? W2 + h2 * h1 : NULL;
+  const float* W3 = h2 ? b2 + h2 : W2;
+  const float* b3 = W3 + hl;
+  int e1 = o_wexp(W1, h1 * k, k, h1, k);
+  int e2 = h2 ? o_wexp(W2, h2 * h1, h1, h2, h1) : o_wexp(W2, h1, h1, 1, h1);
+  int e3 = h2 ? o_wexp(W3, h2, h2, 1, h2) : 0;
+  q[0] = k; q[1] = h1; q[2] = h2; q[3] = s_in;
+  q[4] = e1; q[5] = e2; q[6] = e3; q[7] = 0; q[8] = 0;
+  int64_t* QW1 = q + O_QHDR;
+  int64_t* QB1 = QW1 + h1 * k;
+  for (int j = 0; j < h1 * k; j++) QW1[j] = o_qw(W1[j], e1);
+  for (int j = 0; j < h1; j++) QB1[j] = o_qb(b1[j], e1 + s_in);
+  int64_t* QW2 = QB1 + h1;
+  int64_t* QB2 = h2 ? QW2 + h2 * h1 : QW2 + h1;
+  int64_t* QW3 = h2 ? QB2 + h2 : NULL;
+  int64_t* QB3 = h2 ? QW3 + h2 : NULL;
+  /* layer-2 weights (integers) are needed for the layer-2 scan */
+  if (h2) for (int j = 0; j < h2 * h1; j++) QW2[j] = o_qw(W2[j], e2);
+  else for (int j = 0; j < h1; j++) QW2[j] = o_qw(W2[j], e2);
+  int64_t a1[O_MAXH], h1q[O_MAXH], a2[O_MAXH], h2q[O_MAXH];
+  /* t1 from the layer-1 pre-activations */
+  int64_t M = 0;
+  for (int pass = 0; pass < 2; pass++) {
+    const int32_t* in = pass ? vin : tin;
+    const uint8_t* us = pass ? vus : tus;
+    uint64_t cnt = pass ? nv : nt;
+    for (uint64_t s = 0; s < cnt; s++) {
+      if (!us[s]) continue;
+      o_q_hidden(q, in + s * (uint64_t)k, a1, h1q, NULL, NULL);
+      for (int j = 0; j < h1; j++) if (o_leaky16(a1[j]) > M) M = o_leaky16(a1[j]);
+    }
+  }
+  int t1 = o_shift_for(M);
+  q[7] = t1;
+  if (h2) {
+    for (int j = 0; j < h2; j++) QB2[j] = o_qb(b2[j], e1 + e2 + s_in - t1);
+    M = 0;
+    for (int pass = 0; pass < 2; pass++) {
+      const int32_t* in = pass ? vin : tin;
+      const uint8_t* us = pass ? vus : tus;
+      uint64_t cnt = pass ? nv : nt;
+      for (uint64_t s = 0; s < cnt; s++) {
+        if (!us[s]) continue;
+        o_q_hidden(q, in + s * (uint64_t)k, a1, h1q, a2, h2q);
+        for (int j = 0; j < h2; j++) if (o_leaky16(a2[j]) > M) M = o_leaky16(a2[j]);
+      }
+    }
+    int t2 = o_shift_for(M);
+    q[8] = t2;
+    for (int j = 0; j < h2; j++) QW3[j] = o_qw(W3[j], e3);
+    QB3[0] = o_qb(b3[0], e1 + e2 + e3 + s_in - t1 - t2);
+  } else {
+    QB2[0] = o_qb(b3[0], e1 + e2 + s_in - t1);
+  }
+  return ORC_OK;
+}
+
 static int o_bitlen(uint64_t n) { int b = 0; while (n) { b++; n >>= 1; } return b; }
 
 /* ------------------------------------------------------------------------- */
@@ -578,8 +782,11 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
                  uint8_t* out, uint64_t cap, uint64_t* out_size, orc_dump* dump) {
   if (dtype != ORC_F32 && dtype != ORC_F64) return ORC_ERR_DTYPE;
   if (p->m < 2 || p->m > 16) return ORC_ERR_ARG;
-  int use_nn = p->pred == ORC_PRED_MLP && p->weights != NULL;
+  int use_q = p->pred == ORC_PRED_MLP_BF16 && p->qnet != NULL;
+  int use_nn = (p->pred == ORC_PRED_MLP && p->weights != NULL) || use_q;
   int k = p->stencil;
+  if (use_q && (p->qnet[0] != k || p->qnet[1] != p->h1 || p->qnet[2] != p->h2 || p->qnet[3] != p->s_in))
+    return ORC_ERR_ARG;
   if (use_nn && (k != 7 && k != 13)) return ORC_ERR_ARG;
   if (use_nn && (p->h1 < 1 || p->h1 > O_MAXH || p->h2 < 0 || p->h2 > O_MAXH)) return ORC_ERR_ARG;
   if (use_nn && (p->s_in < 0 || p->s_in > 30)) return ORC_ERR_ARG;
@@ -664,7 +871,9 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
                   in[i] = (qz >= 0 && qy >= 0 && qx >= 0 && qz < e0 && qy < e1 && qx < e2)
                               ? vc[(qz * e1 + qy) * e2 + qx] : 0;
                 }
-                int64_t kn = vt[j] - (int64_t)orc_mlp_pred32(p->weights, k, p->h1, p->h2, p->s_in, in);
+                int64_t pr = use_q ? (int64_t)orc_mlp_pred_q(p->qnet, in)
+                                   : (int64_t)orc_mlp_pred32(p->weights, k, p->h1, p->h2, p->s_in, in);
+                int64_t kn = vt[j] - pr;
                 int64_t an = kn < 0 ? -kn : kn;
                 costn += o_bitlen((uint64_t)(an < R ? an : R));
                 cn[j] = (uint16_t)((an <= R - 1 && okv[ig]) ? kn + R : 0);
@@ -709,9 +918,10 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
   uint64_t swords = (tbits + 31) / 32;
 
   /* layout */
-  int nw = use_nn ? orc_mlp_nweights(k, p->h1, p->h2) : 0;
+  /* weights section: FP32 blob, or the int64 fixed-point network */
+  int nw = use_q ? orc_qnet_len(k, p->h1, p->h2) : (use_nn ? orc_mlp_nweights(k, p->h1, p->h2) : 0);
   uint64_t off_w = O_HDR;
-  uint64_t off_cb = al16(off_w + 4ull * (uint64_t)nw);
+  uint64_t off_cb = al16(off_w + (use_q ? 8ull : 4ull) * (uint64_t)nw);
   uint64_t off_bb = al16(off_cb + 4ull * (uint64_t)n_used);
   uint64_t off_bn = al16(off_bb + 4ull * g.nblocks);
   uint64_t off_ov = al16(off_bn + 2ull * g.nblocks);
@@ -725,7 +935,7 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
   memcpy(out, "PCMP", 4);
   put32(out + 4, 1);
   put32(out + 8, (uint32_t)dtype);
-  put32(out + 12, (uint32_t)(use_nn ? ORC_PRED_MLP : ORC_PRED_LORENZO));
+  put32(out + 12, (uint32_t)(use_q ? ORC_PRED_MLP_BF16 : (use_nn ? ORC_PRED_MLP : ORC_PRED_LORENZO)));
   put64(out + 16, dims[0]); put64(out + 24, dims[1]); put64(out + 32, dims[2]);
   put32(out + 40, (uint32_t)p->block[0]); put32(out + 44, (uint32_t)p->block[1]); put32(out + 48, (uint32_t)p->block[2]);
   put32(out + 52, (uint32_t)(use_nn ? k : 0));
@@ -755,7 +965,8 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
   put32(out + 252, orc_crc32(out, 252));
 
   /* sections */
-  for (int i = 0; i < nw; i++) put32(out + off_w + 4ull * i, bits_of_f(p->weights[i]));
+  if (use_q) for (int i = 0; i < nw; i++) put64(out + off_w + 8ull * i, (uint64_t)p->qnet[i]);
+  else for (int i = 0; i < nw; i++) put32(out + off_w + 4ull * i, bits_of_f(p->weights[i]));
   for (int t = 0; t < n_used; t++)
     put32(out + off_cb + 4ull * (uint64_t)t, order[t] | ((uint32_t)lens[order[t]] << 16));
   for (uint64_t b = 0; b < g.nblocks; b++) {
@@ -860,14 +1071,15 @@ int orc_decompress(const uint8_t* in, uint64_t in_size, void* xo, uint64_t cap_e
   o_geom g;
   if (o_geom_make(dims, block, &g)) return ORC_ERR_CORRUPT;
   if (m < 2 || m > 16 || g.nblocks != nblocks || total > in_size) return ORC_ERR_CORRUPT;
-  if (pred == ORC_PRED_MLP) {
-    if ((k != 7 && k != 13) || h1 < 1 || h1 > O_MAXH || h2 < 0 || h2 > O_MAXH ||
-        nw != orc_mlp_nweights(k, h1, h2) || s_in < 0 || s_in > 30)
+  int wsz = pred == ORC_PRED_MLP_BF16 ? 8 : 4;
+  if (pred == ORC_PRED_MLP || pred == ORC_PRED_MLP_BF16) {
+    if ((k != 7 && k != 13) || h1 < 1 || h1 > O_MAXH || h2 < 0 || h2 > O_MAXH || s_in < 0 || s_in > 30 ||
+        nw != (pred == ORC_PRED_MLP ? orc_mlp_nweights(k, h1, h2) : orc_qnet_len(k, h1, h2)))
       return ORC_ERR_CORRUPT;
   } else if (pred != ORC_PRED_LORENZO || nw != 0) {
     return ORC_ERR_CORRUPT;
   }
-  if (off_w + 4ull * nw > total || off_cb + 4ull * n_used > total || off_bb + 4ull * nblocks > total ||
+  if (off_w + (uint64_t)wsz * nw > total || off_cb + 4ull * n_used > total || off_bb + 4ull * nblocks > total ||
       off_bn + 2ull * nblocks > total || off_ov + ts * n_out > total || off_st + 4ull * swords > total)
     return ORC_ERR_CORRUPT;
   uint64_t n = dims[0] * dims[1] * dims[2];
@@ -877,9 +1089,28 @@ int orc_decompress(const uint8_t* in, uint64_t in_size, void* xo, uint64_t cap_e
   if (n_used > (uint32_t)nsym) return ORC_ERR_CORRUPT;
 
   float* wts = NULL;
-  if (nw) {
+  int64_t* qn = NULL;
+  if (nw && pred == ORC_PRED_MLP) {
     wts = (float*)malloc(sizeof(float) * (size_t)nw);
     for (int i = 0; i < nw; i++) wts[i] = f_from_bits(get32(in + off_w + 4ull * i));
+  }
+  if (nw && pred == ORC_PRED_MLP_BF16) {
+    /* the fixed-point network: shapes must match the header, shifts and
+     * integers must lie in their stated ranges */
+    qn = (int64_t*)malloc(sizeof(int64_t) * (size_t)nw);
+    for (int i = 0; i < nw; i++) qn[i] = (int64_t)get64(in + off_w + 8ull * i);
+    int bad = qn[0] != k || qn[1] != h1 || qn[2] != h2 || qn[3] != s_in;
+    for (int i = 4; i < 7; i++) bad |= qn[i] < -30 || qn[i] > 30;
+    for (int i = 7; i < 9; i++) bad |= qn[i] < -24 || qn[i] > 40;
+    int li = O_QHDR;
+    int lay[3][2] = {{h1, k}, {h2 ? h2 : 1, h1}, {h2 ? 1 : 0, h2}};
+    for (int l = 0; l < 3 && !bad; l++) {
+      for (int r = 0; r < lay[l][0]; r++) {
+        for (int c2 = 0; c2 < lay[l][1]; c2++, li++) bad |= qn[li] < -255 || qn[li] > 255;
+      }
+      for (int r = 0; r < lay[l][0]; r++, li++) bad |= qn[li] < -1099511627776LL || qn[li] > 1099511627776LL;
+    }
+    if (bad || li != nw) { free(qn); return ORC_ERR_CORRUPT; }
   }
   /* canonical decoder tables: the stored list is the code order */
   uint8_t* lens = (uint8_t*)calloc((size_t)nsym, 1);
@@ -915,7 +1146,7 @@ int orc_decompress(const uint8_t* in, uint64_t in_size, void* xo, uint64_t cap_e
     uint32_t nbits = bw & 0x7FFFFFFFu;
     int usen = (int)(bw >> 31);
     uint32_t no = (uint32_t)in[off_bn + 2ull * b] | ((uint32_t)in[off_bn + 2ull * b + 1] << 8);
-    if (usen && !wts) { ret = ORC_ERR_CORRUPT; break; }
+    if (usen && !wts && !qn) { ret = ORC_ERR_CORRUPT; break; }
     uint64_t bend = bp + nbits;
     uint64_t oend = oi + no;
     if (bend > sbits || oend > n_out || no < 1) { ret = ORC_ERR_CORRUPT; break; }
@@ -977,7 +1208,7 @@ int orc_decompress(const uint8_t* in, uint64_t in_size, void* xo, uint64_t cap_e
                 inn[i] = (qz >= 0 && qy >= 0 && qx >= 0 && qz < e0 && qy < e1 && qx < e2)
                              ? vc[(qz * e1 + qy) * e2 + qx] : 0;
               }
-              pr = orc_mlp_pred32(wts, k, h1, h2, s_in, inn);
+              pr = qn ? orc_mlp_pred_q(qn, inn) : orc_mlp_pred32(wts, k, h1, h2, s_in, inn);
             } else {
               pr = o_lorenzo(in7);
             }
@@ -993,7 +1224,7 @@ int orc_decompress(const uint8_t* in, uint64_t in_size, void* xo, uint64_t cap_e
         }
     if (ret == ORC_OK && (bp != bend || oi != oend)) ret = ORC_ERR_CORRUPT;
   }
-  free(vc); free(dq); free(sorted); free(lens); free(wts);
+  free(vc); free(dq); free(sorted); free(lens); free(wts); free(qn);
   return ret;
 }
 
@@ -1337,4 +1568,31 @@ int orc_train(const void* x, const uint64_t dims[3], int dtype, double eb, const
   }
   free(tin); free(ttg); free(tus); free(vin); free(vtg); free(vus);
   return best;
+}
+
+/* Fixed-point form of a trained perceptron: gather the training phase's
+ * samples again (same seed and rate) and build the qnet from weights w. */
+int orc_quantize(const void* x, const uint64_t dims[3], int dtype, double eb, const int block[3],
+                 int k, int h1, int h2, uint64_t seed, uint32_t thr32, const float* w, int s_in, int64_t* qnet) {
+  uint64_t n = dims[0] * dims[1] * dims[2];
+  double amin, amax;
+  int trivial;
+  int st = orc_stats(x, n, dtype, &amin, &amax, &trivial);
+  if (st) return st;
+  orc_consts c;
+  st = orc_make_consts(dtype, amin, amax, trivial, eb, &c);
+  if (st) return st;
+  uint64_t nt, nv;
+  st = orc_count_samples(dims, block, seed, thr32, &nt, &nv);
+  if (st) return st;
+  int32_t* tin = (int32_t*)malloc(sizeof(int32_t) * (nt * k + 1));
+  int32_t* ttg = (int32_t*)malloc(sizeof(int32_t) * (nt + 1));
+  uint8_t* tus = (uint8_t*)malloc(nt + 1);
+  int32_t* vin = (int32_t*)malloc(sizeof(int32_t) * (nv * k + 1));
+  int32_t* vtg = (int32_t*)malloc(sizeof(int32_t) * (nv + 1));
+  uint8_t* vus = (uint8_t*)malloc(nv + 1);
+  orc_gather_samples(x, dims, dtype, &c, block, k, seed, thr32, tin, ttg, tus, vin, vtg, vus);
+  st = orc_qnet_build(w, k, h1, h2, s_in, tin, tus, nt, vin, vus, nv, qnet);
+  free(tin); free(ttg); free(tus); free(vin); free(vtg); free(vus);
+  return st;
 }

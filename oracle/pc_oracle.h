@@ -28,6 +28,7 @@
 
 #define ORC_PRED_LORENZO 0
 #define ORC_PRED_MLP 1
+#define ORC_PRED_MLP_BF16 2  /* fixed-point perceptron on bf16 tensor-core operands */
 
 typedef struct {
   int dtype;
@@ -48,6 +49,7 @@ typedef struct {
   int m;                 /* code bits; radius R = 2^(m-1) */
   int s_in;              /* input scale: u = v * 2^-s_in */
   const float* weights;  /* MLP weight blob, NULL for Lorenzo only */
+  const int64_t* qnet;   /* fixed-point network (ORC_PRED_MLP_BF16), see orc_qnet_len */
 } orc_params;
 
 typedef struct {
