@@ -55,6 +55,7 @@ extern "C" {
 /* predictor forms */
 #define PC_PRED_LORENZO 0      /* Lorenzo only (Section IV.A) */
 #define PC_PRED_MLP_FP32 1     /* perceptron in FP32 on CUDA cores, Lorenzo per-block fallback */
+#define PC_PRED_MLP_BF16 2     /* fixed-point perceptron on bf16 tensor cores (pc_quantize), Lorenzo fallback */
 
 typedef struct {
   double eb_rel;          /* pointwise relative bound b_r, 0 < eb_rel < 1 (Eq. 1) */
@@ -66,11 +67,49 @@ typedef struct {
   int s_in;               /* input scale: inputs are codes * 2^-s_in (from pc_train) */
   const float* h_weights; /* host pointer to the perceptron weight blob (pc_mlp_nweights floats):
                              W1[h1][k], b1[h1], W2[h2][h1], b2[h2], W3[hl], b3 (hl = h2 or h1);
-                             ignored for PC_PRED_LORENZO */
+                             used by PC_PRED_MLP_FP32 */
+  const long long* h_qnet;/* host pointer to the fixed-point network (pc_qnet_len int64, from
+                             pc_quantize); used by PC_PRED_MLP_BF16 */
 } pc_params;
 
 /* Number of floats in the weight blob for stencil k and hidden widths h1, h2. */
 int pc_mlp_nweights(int k, int h1, int h2);
+
+/*
+ * Fixed-point (BF16) form of the perceptron of Section IV.B, evaluated on
+ * bf16 tensor cores with FP32 accumulation and bit-reproducible by
+ * construction.  The network is an int64 array of pc_qnet_len(k, h1, h2)
+ * entries: k, h1, h2, s_in, e1, e2, e3, t1, t2, then W1[h1][k], B1[h1],
+ * W2[h2][h1], B2[h2], W3[h2], B3.
+ *  - Weights of layer l are integers |W| <= 255 standing for W 2^-e_l.
+ *  - Stencil inputs are the centred codes clamped to +-(2^16 - 1).
+ *  - Each hidden layer computes A = sum W x + B (exact integer), then
+ *    leaky(A) = A >= 0 ? A : A / 16, then H = clamp(rne(leaky(A) 2^-t), +-(2^15 - 1)).
+ *  - The output is pred = clamp(rne(A 2^-F), +-2^30), F = e1 + e2 + e3 - t1 - t2;
+ *    rne rounds to nearest, ties to even.
+ * Supported shapes: (k, h1, h2) = (7, 16, 16) and (13, 32, 32).
+ * The network travels in the container's weights section, and decompression
+ * checks its ranges (PC_ERR_CORRUPT).
+ */
+int pc_qnet_len(int k, int h1, int h2);
+
+/*
+ * Build the fixed-point network from trained FP32 weights p->h_weights with
+ * input scale p->s_in (from pc_train), on the device.
+ *  - Weight exponents: e_l is the largest e with max|W_l| 2^e <= 255, kept in
+ *    [-30, 30]; W = rint(W_f32 2^e).
+ *  - Biases: rint of the f32 bias in the units of its layer's sum, clamped to +-2^40.
+ *  - Shifts: each hidden layer's t is the smallest t in [-24, 40] with
+ *    max 16 |leaky(A)| 2^-t <= 16 (2^15 - 1). The maximum is over the used
+ *    training and validation samples, drawn as by pc_train with the same seed
+ *    and thr32.
+ * Arguments:
+ *   h_qnet_out [out] host, pc_qnet_len(p->stencil, p->hidden[0], p->hidden[1]) int64.
+ *   d_ws       workspace of pc_train_workspace_size(dims, dtype, p, thr32, 1) bytes.
+ * Errors: PC_ERR_ARG (unsupported shape, missing weights), PC_ERR_CAPACITY, PC_ERR_CUDA.
+ */
+int pc_quantize(const void* d_field, const size_t dims[3], int dtype, const pc_params* p, unsigned long long seed,
+                unsigned int thr32, long long* h_qnet_out, void* d_ws, size_t ws_bytes, void* stream);
 
 /* Upper bound, in bytes, on the compressed size of a field (header, weights,
  * codebook, block table, balance points, bitstream).  0 on bad arguments. */

@@ -4,6 +4,7 @@
 #include <mutex>
 
 #include "pc_kernels.cuh"
+#include "pc_qmlp.cuh"
 #include "pc_profile.cuh"
 
 using namespace pc;
@@ -60,6 +61,8 @@ bool make_geo(const size_t dims[3], const int block[3], Geo& g) {
   return true;
 }
 
+bool qshape_ok(int k, int h1, int h2) { return (k == 7 && h1 == 16 && h2 == 16) || (k == 13 && h1 == 32 && h2 == 32); }
+
 int check_params(const size_t dims[3], int dtype, const pc_params* p, Geo& g, int& mode, int& nw) {
   if (!dims || !p) return PC_ERR_ARG;
   if (dtype != PC_F32 && dtype != PC_F64) return PC_ERR_DTYPE;
@@ -67,10 +70,15 @@ int check_params(const size_t dims[3], int dtype, const pc_params* p, Geo& g, in
   if (p->m < 2 || p->m > 16) return PC_ERR_ARG;
   if (!make_geo(dims, p->block, g)) return PC_ERR_ARG;
   if (!shape_supported(p->block)) return PC_ERR_ARG;
-  mode = p->pred == PC_PRED_MLP_FP32 ? 1 : 0;
-  if (p->pred != PC_PRED_LORENZO && p->pred != PC_PRED_MLP_FP32) return PC_ERR_ARG;
+  mode = p->pred == PC_PRED_MLP_FP32 ? 1 : (p->pred == PC_PRED_MLP_BF16 ? 2 : 0);
+  if (p->pred != PC_PRED_LORENZO && p->pred != PC_PRED_MLP_FP32 && p->pred != PC_PRED_MLP_BF16) return PC_ERR_ARG;
   nw = 0;
-  if (mode) {
+  if (mode == 2) {
+    if (!qshape_ok(p->stencil, p->hidden[0], p->hidden[1]) || p->s_in < 0 || p->s_in > 30 || !p->h_qnet)
+      return PC_ERR_ARG;
+    if (!qnet_valid(p->h_qnet, p->stencil, p->hidden[0], p->hidden[1], p->s_in)) return PC_ERR_ARG;
+    nw = qnet_len(p->stencil, p->hidden[0], p->hidden[1]);
+  } else if (mode) {
     if (p->stencil != 7 && p->stencil != 13) return PC_ERR_ARG;
     if (p->hidden[0] < 2 || p->hidden[0] > kMaxH || p->hidden[1] < 0 || p->hidden[1] > kMaxH) return PC_ERR_ARG;
     if (p->s_in < 0 || p->s_in > 30 || !p->h_weights) return PC_ERR_ARG;
@@ -215,13 +223,16 @@ int parse_header(const uint8_t* h, size_t n, Hdr& H, Geo& g) {
     if ((H.stencil != 7 && H.stencil != 13) || H.h1 < 2 || H.h1 > kMaxH || H.h2 < 0 || H.h2 > kMaxH ||
         H.s_in < 0 || H.s_in > 30 || H.nw != nweights(H.stencil, H.h1, H.h2) || H.nw > kMaxW)
       return PC_ERR_CORRUPT;
+  } else if (H.pred == 2) {
+    if (!qshape_ok(H.stencil, H.h1, H.h2) || H.s_in < 0 || H.s_in > 30 || H.nw != qnet_len(H.stencil, H.h1, H.h2))
+      return PC_ERR_CORRUPT;
   } else if (H.pred != 0 || H.nw != 0) {
     return PC_ERR_CORRUPT;
   }
   const unsigned long long npts = (unsigned long long)H.dims[0] * H.dims[1] * H.dims[2];
   if (H.n_out > npts || H.swords > (npts * kLmax + 31) / 32 + 1) return PC_ERR_CORRUPT;
   const unsigned long long ts = H.dtype == PC_F64 ? 8 : 4;
-  const unsigned long long ocb = al16(kHdr + 4ull * H.nw);
+  const unsigned long long ocb = al16(kHdr + (H.pred == 2 ? 8ull : 4ull) * H.nw);
   const unsigned long long obb = al16(ocb + 4ull * H.n_used);
   const unsigned long long obn = al16(obb + 4ull * H.nblocks);
   const unsigned long long oov = al16(obn + 2ull * H.nblocks);
@@ -233,7 +244,8 @@ int parse_header(const uint8_t* h, size_t n, Hdr& H, Geo& g) {
 }
 
 struct TrainLayout {
-  size_t st, tabs, hist, cnt_t, cnt_v, off_t, off_v, tin, ttg, tus, vin, vtg, vus, w, lrs, lams, costs, ctl, total;
+  size_t st, tabs, hist, cnt_t, cnt_v, off_t, off_v, tin, ttg, tus, vin, vtg, vus, w, lrs, lams, costs, ctl, qnet, qmax,
+      total;
   unsigned long long cap_t, cap_v;
 };
 
@@ -271,6 +283,8 @@ TrainLayout train_layout(const Geo& g, int m, int k, int nw, unsigned int thr32,
   L.lams = o; o = up(o + 4 * (size_t)nmodels);
   L.costs = o; o = up(o + 8 * (size_t)(nmodels + 1));
   L.ctl = o; o = up(o + train_ctl_bytes());
+  L.qnet = o; o = up(o + 8 * (size_t)qnet_len(13, 32, 32));
+  L.qmax = o; o = up(o + 16);
   L.total = o;
   return L;
 }
@@ -375,6 +389,72 @@ int pc_train(const void* d_field, const size_t dims[3], int dtype, const pc_para
 }
 
 
+int pc_quantize(const void* d_field, const size_t dims[3], int dtype, const pc_params* p, unsigned long long seed,
+                unsigned int thr32, long long* h_qnet_out, void* d_ws, size_t ws_bytes, void* stream) {
+  Geo g;
+  int nw;
+  int st = train_check(dims, dtype, p, 1, g, nw);
+  if (st) return st;
+  if (!d_field || !p->h_weights || !h_qnet_out || !d_ws || p->s_in < 0 || p->s_in > 30) return PC_ERR_ARG;
+  if (!qshape_ok(p->stencil, p->hidden[0], p->hidden[1])) return PC_ERR_ARG;
+  TrainLayout L = train_layout(g, p->m, p->stencil, nw, thr32, 1);
+  if (ws_bytes < L.total) return PC_ERR_CAPACITY;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int nsm = sm_count();
+  if (nsm <= 0) return PC_ERR_CUDA;
+  uint8_t* ws = static_cast<uint8_t*>(d_ws);
+  State* stp = reinterpret_cast<State*>(ws + L.st);
+  Tabs* tabs = reinterpret_cast<Tabs*>(ws + L.tabs);
+  auto* hist = reinterpret_cast<unsigned long long*>(ws + L.hist);
+  TrainBufs tb;
+  tb.cnt_t = reinterpret_cast<unsigned int*>(ws + L.cnt_t);
+  tb.cnt_v = reinterpret_cast<unsigned int*>(ws + L.cnt_v);
+  tb.off_t = reinterpret_cast<unsigned long long*>(ws + L.off_t);
+  tb.off_v = reinterpret_cast<unsigned long long*>(ws + L.off_v);
+  tb.tin = reinterpret_cast<int*>(ws + L.tin);
+  tb.ttg = reinterpret_cast<int*>(ws + L.ttg);
+  tb.tus = ws + L.tus;
+  tb.vin = reinterpret_cast<int*>(ws + L.vin);
+  tb.vtg = reinterpret_cast<int*>(ws + L.vtg);
+  tb.vus = ws + L.vus;
+  tb.w = reinterpret_cast<float*>(ws + L.w);
+  tb.lrs = nullptr;
+  tb.lams = nullptr;
+  tb.costs = reinterpret_cast<unsigned long long*>(ws + L.costs);
+  tb.ctl = ws + L.ctl;
+  tb.cap_t = L.cap_t;
+  tb.cap_v = L.cap_v;
+  auto* q = reinterpret_cast<long long*>(ws + L.qnet);
+  auto* qmax = reinterpret_cast<unsigned long long*>(ws + L.qmax);
+  if (cudaMemcpyAsync(tb.w, p->h_weights, 4ull * nw, cudaMemcpyHostToDevice, s) != cudaSuccess) return PC_ERR_CUDA;
+  const unsigned long long n = (unsigned long long)dims[0] * dims[1] * dims[2];
+  const int nsym = 1 << p->m;
+  int r;
+  if (dtype == PC_F32) {
+    r = launch_stats_consts<float>(d_field, n, stp, tabs, hist, nsym, p->eb_rel, nsm, s);
+    if (!r) r = launch_quantize<float>(static_cast<const float*>(d_field), g, stp, tabs, tb, p->stencil, p->hidden[0],
+                                      p->hidden[1], p->s_in, seed, thr32, q, qmax, s);
+  } else {
+    r = launch_stats_consts<double>(d_field, n, stp, tabs, hist, nsym, p->eb_rel, nsm, s);
+    if (!r) r = launch_quantize<double>(static_cast<const double*>(d_field), g, stp, tabs, tb, p->stencil,
+                                       p->hidden[0], p->hidden[1], p->s_in, seed, thr32, q, qmax, s);
+  }
+  if (r) return r;
+  const int len = qnet_len(p->stencil, p->hidden[0], p->hidden[1]);
+  unsigned long long ctl[8];
+  int herr = 0;
+  if (cudaMemcpyAsync(ctl, tb.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&herr, &stp->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(h_qnet_out, q, 8ull * len, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return PC_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
+  if (herr) return herr;
+  if (ctl[0] > L.cap_t || ctl[1] > L.cap_v) return PC_ERR_CAPACITY;
+  return qnet_valid(h_qnet_out, p->stencil, p->hidden[0], p->hidden[1], p->s_in) ? PC_OK : PC_ERR_ARG;
+}
+
+int pc_qnet_len(int k, int h1, int h2) { return qnet_len(k, h1, h2); }
+
 int pc_mlp_nweights(int k, int h1, int h2) { return nweights(k, h1, h2); }
 
 size_t pc_compress_bound(const size_t dims[3], int dtype, const pc_params* p) {
@@ -384,7 +464,7 @@ size_t pc_compress_bound(const size_t dims[3], int dtype, const pc_params* p) {
   const unsigned long long n = (unsigned long long)dims[0] * dims[1] * dims[2];
   const unsigned long long ts = dtype == PC_F64 ? 8 : 4;
   unsigned long long b = kHdr;
-  b = al16(b + 4ull * nw);
+  b = al16(b + (mode == 2 ? 8ull : 4ull) * nw);
   b = al16(b + 4ull * (1ull << p->m));
   b = al16(b + 4ull * g.nblocks);
   b = al16(b + 2ull * g.nblocks);
@@ -434,8 +514,9 @@ int pc_compress(const void* d_field, const size_t dims[3], int dtype, const pc_p
   hi.m = p->m;
   hi.s_in = p->s_in;
   hi.nw = nw;
+  hi.wsz = mode == 2 ? 8 : 4;
   hi.eb = p->eb_rel;
-  hi.off_cb = al16(kHdr + 4ull * nw);
+  hi.off_cb = al16(kHdr + (unsigned long long)hi.wsz * nw);
   hi.cap = out_cap;
   if (out_cap < hi.off_cb + 16) return PC_ERR_CAPACITY;
   static thread_local Mlp mlp;
@@ -445,9 +526,18 @@ int pc_compress(const void* d_field, const size_t dims[3], int dtype, const pc_p
     mlp.h1 = p->hidden[0];
     mlp.h2 = p->hidden[1];
     mlp.s_in = p->s_in;
-    memcpy(mlp.w, p->h_weights, sizeof(float) * (size_t)nw);
+    if (mode == 1) memcpy(mlp.w, p->h_weights, sizeof(float) * (size_t)nw);
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the fixed-point network goes straight into the container's weights
+  // section, where the kernels read it
+  const long long* qnet = nullptr;
+  if (mode == 2) {
+    if (cudaMemcpyAsync(static_cast<uint8_t*>(d_out) + kHdr, p->h_qnet, 8ull * nw, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+      return PC_ERR_CUDA;
+    qnet = reinterpret_cast<const long long*>(static_cast<uint8_t*>(d_out) + kHdr);
+  }
   const int nsm = sm_count();
   if (nsm <= 0) return PC_ERR_CUDA;
   uint8_t* ws = static_cast<uint8_t*>(d_ws);
@@ -474,10 +564,11 @@ int pc_compress(const void* d_field, const size_t dims[3], int dtype, const pc_p
   int r;
   if (dtype == PC_F32) {
     r = launch_stats_consts<float>(d_field, n, stp, tabs, hist, nsym, p->eb_rel, nsm, s);
-    if (!r) r = launch_compress<float>(d_field, g, stp, tabs, codes, nnflag, nout, hist, p->m, mode, mlp, nsm, s);
+    if (!r) r = launch_compress<float>(d_field, g, stp, tabs, codes, nnflag, nout, hist, p->m, mode, mlp, qnet, nsm, s);
   } else {
     r = launch_stats_consts<double>(d_field, n, stp, tabs, hist, nsym, p->eb_rel, nsm, s);
-    if (!r) r = launch_compress<double>(d_field, g, stp, tabs, codes, nnflag, nout, hist, p->m, mode, mlp, nsm, s);
+    if (!r) r = launch_compress<double>(d_field, g, stp, tabs, codes, nnflag, nout, hist, p->m, mode, mlp, qnet, nsm,
+                                        s);
   }
   if (!r) r = launch_codebook(hist, p->m, lens, cw, stp, hs, out, g, hi, s);
   if (!r) {
@@ -535,11 +626,13 @@ int pc_decompress(const void* d_in, size_t in_size, void* d_field, size_t field_
   if (ws_bytes < L.total) return PC_ERR_CAPACITY;
   static thread_local Mlp mlp;
   memset(&mlp, 0, sizeof(Mlp));
-  if (H.pred == 1) {
+  if (H.pred == 1 || H.pred == 2) {
     mlp.k = H.stencil;
     mlp.h1 = H.h1;
     mlp.h2 = H.h2;
     mlp.s_in = H.s_in;
+  }
+  if (H.pred == 1) {
     if (cudaMemcpyAsync(mlp.w, static_cast<const uint8_t*>(d_in) + kHdr, 4ull * H.nw, cudaMemcpyDeviceToHost, s) !=
         cudaSuccess)
       return PC_ERR_CUDA;
@@ -567,11 +660,14 @@ int pc_decompress(const void* d_in, size_t in_size, void* d_field, size_t field_
   DecInfo di;
   di.dtype = H.dtype;
   di.m = H.m;
-  di.stencil = H.pred == 1 ? H.stencil : 7;
+  di.stencil = H.pred != 0 ? H.stencil : 7;
   di.h1 = H.h1;
   di.h2 = H.h2;
   di.s_in = H.s_in;
-  di.usenn_any = H.pred == 1;
+  di.usenn_any = H.pred != 0;
+  di.qmode = H.pred == 2;
+  // the fixed-point network is read in place from the container
+  di.qnet = H.pred == 2 ? reinterpret_cast<const long long*>(static_cast<const uint8_t*>(d_in) + kHdr) : nullptr;
   di.n_used = H.n_used;
   di.n_out = H.n_out;
   di.swords = H.swords;

@@ -1,6 +1,7 @@
 // Compression kernels: statistics (a1), constants (a2), and the fused
 // transform / predict / select / quantize / histogram pass (a4-a9).
 #include "pc_kernels.cuh"
+#include "pc_qmlp.cuh"
 #include "pc_profile.cuh"
 
 namespace pc {
@@ -191,11 +192,23 @@ __global__ void k_consts(State* st, double eb, Tabs* tabs) {
 // ---------------------------------------------------------------------------
 constexpr int kHistWin = 2048;
 
-template <int BV, int MODE, int PV>
+// Extra shared memory of the fixed-point form: B fragments, biases, and one
+// prediction per point of the brick.
+template <int BV, int MODE, int K, int H1, int H2>
+constexpr size_t qnet_smem_bytes() {
+  if constexpr (MODE == 2) {
+    using S = QShape<K, H1, H2>;
+    return (size_t)S::NFRAG * 4 + (size_t)S::NBIAS * 8 + (size_t)BrickShape<BV>::G * BV * 4;
+  } else {
+    return 0;
+  }
+}
+
+template <int BV, int MODE, int PV, int K, int H1, int H2>
 constexpr size_t compress_smem_bytes() {
   constexpr int G = BrickShape<BV>::G;
   return sizeof(Tabs) + (size_t)G * BV * 4 + (size_t)((G * PV + 3) & ~3) * 4 + (size_t)G * BV * 2 * (MODE ? 2 : 1) +
-         (size_t)kHistWin * 4;
+         (size_t)kHistWin * 4 + qnet_smem_bytes<BV, MODE, K, H1, H2>();
 }
 
 template <typename T, int B0, int B1, int B2, int MODE, int K, int H1, int H2>
@@ -203,7 +216,8 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restr
                                                    const Tabs* __restrict__ tabs, uint16_t* __restrict__ codes,
                                                    uint8_t* __restrict__ nnflag, uint32_t* __restrict__ nout,
                                                    unsigned long long* __restrict__ hist, int m,
-                                                   const __grid_constant__ Mlp mlp) {
+                                                   const __grid_constant__ Mlp mlp,
+                                                   const long long* __restrict__ qnet) {
   constexpr int BV = B0 * B1 * B2;
   using BS = BrickShape<BV>;
   constexpr int G = BS::G, TS = BS::TS, PPT = BS::PPT;
@@ -218,6 +232,13 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restr
   uint16_t* s_cz = reinterpret_cast<uint16_t*>(s_vp + ((G * PD::PV + 3) & ~3));  // G*BV
   uint16_t* s_cn = s_cz + G * BV;                                      // G*BV (perceptron only)
   unsigned int* s_hist = reinterpret_cast<unsigned int*>(s_cn + (MODE ? G * BV : 0));
+  // fixed-point form: B fragments, biases, per-point predictions
+  constexpr int QK = MODE == 2 ? K : 7, QH1 = MODE == 2 ? H1 : 16, QH2 = MODE == 2 ? H2 : 16;
+  using QS = QShape<QK, QH1, QH2>;
+  uint32_t* s_frag = reinterpret_cast<uint32_t*>(s_hist + kHistWin);
+  long long* s_qbias = reinterpret_cast<long long*>(s_frag + (MODE == 2 ? QS::NFRAG : 0));
+  int* s_pred = reinterpret_cast<int*>(s_qbias + (MODE == 2 ? QS::NBIAS : 0));
+  __shared__ QSc s_qsc;
   __shared__ int s_cost[G][2];
   __shared__ int s_nz[G];
   __shared__ int s_da[G];
@@ -237,6 +258,7 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restr
   const float sig = MODE ? __uint_as_float((unsigned int)(127 - mlp.s_in) << 23) : 1.0f;
   const float unsig = MODE ? __uint_as_float((unsigned int)(127 + mlp.s_in) << 23) : 1.0f;
   const bool vec_rows = VEC_OK && (g.n[2] % VW == 0) && ((reinterpret_cast<uintptr_t>(x) & 15u) == 0);
+  if constexpr (MODE == 2) qnet_stage<QK, QH1, QH2>(qnet, s_frag, s_qbias, &s_qsc);
   __syncthreads();
 
   const long long nbx = (g.nb[2] + G - 1) / G;
@@ -332,6 +354,49 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restr
       }
     }
     __syncthreads();
+    if constexpr (MODE == 2) {
+      // a6, fixed-point form: tiles of 16 points on the tensor cores
+      const int wid = tid >> 5, lane = tid & 31;
+      const QSc qsc = s_qsc;
+      // this thread's layer-1 columns: stencil offset (or none) and limb
+      int qoff[QS::KC1][4], qhi[QS::KC1][4];  // stencil offset; limb 1 hi, 0 lo, 2 padding
+#pragma unroll
+      for (int kc = 0; kc < QS::KC1; ++kc)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          int in, hi;
+          qcol<QK>(kc, e, in, hi);
+          qoff[kc][e] = in < 0 ? 0 : PD::off(st_dz(QK, in), st_dy(QK, in), st_dx(QK, in));
+          qhi[kc][e] = in < 0 ? 2 : hi;  // 2: padding column
+        }
+      for (int tile = wid; tile < G * BV / 16; tile += 8) {
+        const int f0 = tile * 16;
+        const int gb = f0 / BV;
+        const int* vpg = s_vp + gb * PD::PV;
+        int lv[2][QS::KC1][4];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int j = f0 - gb * BV + (lane >> 2) + 8 * r;
+          const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+          const int pj = PD::at(lz, ly, lx);
+#pragma unroll
+          for (int kc = 0; kc < QS::KC1; ++kc)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              int v = qhi[kc][e] == 2 ? 0 : vpg[pj + qoff[kc][e]];
+              v = v > kQIn ? kQIn : (v < -kQIn ? -kQIn : v);
+              lv[r][kc][e] = qlimb(v, qhi[kc][e]);
+            }
+        }
+        int p0, p1;
+        qnet_tile<QK, QH1, QH2>(s_frag, s_qbias, qsc, lv, p0, p1);
+        if ((lane & 3) == 0) {
+          s_pred[f0 + (lane >> 2)] = p0;
+          s_pred[f0 + (lane >> 2) + 8] = p1;
+        }
+      }
+      __syncthreads();
+    }
     const long long bx = bxg * G + team;
     const bool bvalid = bx < g.nb[2];
     const int e2 = bvalid ? (int)min((long long)B2, g.n[2] - bx * B2) : 0;
@@ -340,7 +405,7 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restr
     // a6-a8: predict, quantize, cost (and, for Lorenzo only, a9 histogram)
     const long long b = (bz * g.nb[1] + by) * g.nb[2] + bx;
     int cz = 0, cn = 0, nz = 0;
-    if constexpr (MODE != 0 && K > 0) {
+    if constexpr (MODE == 1 && K > 0) {
       // two points per step through the packed perceptron forward
       if (bvalid) {
 #pragma unroll 1
@@ -419,16 +484,22 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restr
           cz += bitlen_u((unsigned int)(az < R ? az : R));
           codez = (az <= R - 1 && okp) ? (uint16_t)(kz + R) : 0;
           if constexpr (MODE != 0) {
-            constexpr int KK = K > 0 ? K : 13;
-            int in[KK];
-            const int kk = K > 0 ? K : mlp.k;
+            long long prd;
+            if constexpr (MODE == 2) {
+              prd = s_pred[team * BV + j];
+            } else {
+              constexpr int KK = K > 0 ? K : 13;
+              int in[KK];
+              const int kk = K > 0 ? K : mlp.k;
 #pragma unroll
-            for (int q = 0; q < KK; ++q)
-              in[q] = q < kk ? vp[pj + PD::off(st_dz(kk, q), st_dy(kk, q), st_dx(kk, q))] : 0;
-            float pv;
-            if constexpr (K > 0) pv = mlp_fwd<K, H1, H2>(mlp, in, sig, unsig);
-            else pv = mlp_fwd_rt(mlp, in, sig, unsig);
-            const long long kn = (long long)vk - (long long)round_pred(pv);
+              for (int q = 0; q < KK; ++q)
+                in[q] = q < kk ? vp[pj + PD::off(st_dz(kk, q), st_dy(kk, q), st_dx(kk, q))] : 0;
+              float pv;
+              if constexpr (K > 0) pv = mlp_fwd<K, H1, H2>(mlp, in, sig, unsig);
+              else pv = mlp_fwd_rt(mlp, in, sig, unsig);
+              prd = round_pred(pv);
+            }
+            const long long kn = (long long)vk - prd;
             const long long an = kn < 0 ? -kn : kn;
             cn += bitlen_u((unsigned int)(an < R ? an : R));
             coden = (an <= R - 1 && okp) ? (uint16_t)(kn + R) : 0;
@@ -514,11 +585,12 @@ template int launch_stats_consts<double>(const void*, unsigned long long, State*
 
 template <typename T, int B0, int B1, int B2, int MODE, int K, int H1, int H2>
 static int launch_c(const void* x, const Geo& g, const State* st, const Tabs* tabs, uint16_t* codes, uint8_t* nnflag,
-                    uint32_t* nout, unsigned long long* hist, int m, const Mlp& mlp, int nsm, cudaStream_t s) {
+                    uint32_t* nout, unsigned long long* hist, int m, const Mlp& mlp, const long long* qnet, int nsm,
+                    cudaStream_t s) {
   constexpr int BV = B0 * B1 * B2;
   constexpr bool WIDE = MODE != 0 && (K == 13 || K == 0);
   auto kern = k_compress<T, B0, B1, B2, MODE, K, H1, H2>;
-  const size_t sm = compress_smem_bytes<BV, MODE, Pad<B0, B1, B2, WIDE>::PV>();
+  const size_t sm = compress_smem_bytes<BV, MODE, Pad<B0, B1, B2, WIDE>::PV, K, H1, H2>();
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
     return PC_ERR_CUDA;
   int per_sm = 0;
@@ -531,7 +603,8 @@ static int launch_c(const void* x, const Geo& g, const State* st, const Tabs* ta
   if (grid < 1) grid = 1;
   {
     ProfScope p(kStCompress, s);
-    kern<<<(unsigned int)grid, 256, sm, s>>>(static_cast<const T*>(x), g, st, tabs, codes, nnflag, nout, hist, m, mlp);
+    kern<<<(unsigned int)grid, 256, sm, s>>>(static_cast<const T*>(x), g, st, tabs, codes, nnflag, nout, hist, m, mlp,
+                                             qnet);
   }
   return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
@@ -539,23 +612,30 @@ static int launch_c(const void* x, const Geo& g, const State* st, const Tabs* ta
 template <typename T, int B0, int B1, int B2>
 static int launch_c_shape(const void* x, const Geo& g, const State* st, const Tabs* tabs, uint16_t* codes,
                           uint8_t* nnflag, uint32_t* nout, unsigned long long* hist, int m, int mode, const Mlp& mlp,
-                          int nsm, cudaStream_t s) {
+                          const long long* qnet, int nsm, cudaStream_t s) {
   if (mode == 0)
-    return launch_c<T, B0, B1, B2, 0, 0, 0, 0>(x, g, st, tabs, codes, nnflag, nout, hist, m, mlp, nsm, s);
+    return launch_c<T, B0, B1, B2, 0, 0, 0, 0>(x, g, st, tabs, codes, nnflag, nout, hist, m, mlp, qnet, nsm, s);
+  if (mode == 2) {
+    if (mlp.k == 7 && mlp.h1 == 16 && mlp.h2 == 16)
+      return launch_c<T, B0, B1, B2, 2, 7, 16, 16>(x, g, st, tabs, codes, nnflag, nout, hist, m, mlp, qnet, nsm, s);
+    if (mlp.k == 13 && mlp.h1 == 32 && mlp.h2 == 32)
+      return launch_c<T, B0, B1, B2, 2, 13, 32, 32>(x, g, st, tabs, codes, nnflag, nout, hist, m, mlp, qnet, nsm, s);
+    return PC_ERR_ARG;
+  }
   if (mlp.k == 7 && mlp.h1 == 16 && mlp.h2 == 16)
-    return launch_c<T, B0, B1, B2, 1, 7, 16, 16>(x, g, st, tabs, codes, nnflag, nout, hist, m, mlp, nsm, s);
+    return launch_c<T, B0, B1, B2, 1, 7, 16, 16>(x, g, st, tabs, codes, nnflag, nout, hist, m, mlp, qnet, nsm, s);
   if (mlp.k == 13 && mlp.h1 == 32 && mlp.h2 == 32)
-    return launch_c<T, B0, B1, B2, 1, 13, 32, 32>(x, g, st, tabs, codes, nnflag, nout, hist, m, mlp, nsm, s);
-  return launch_c<T, B0, B1, B2, 1, 0, 0, 0>(x, g, st, tabs, codes, nnflag, nout, hist, m, mlp, nsm, s);
+    return launch_c<T, B0, B1, B2, 1, 13, 32, 32>(x, g, st, tabs, codes, nnflag, nout, hist, m, mlp, qnet, nsm, s);
+  return launch_c<T, B0, B1, B2, 1, 0, 0, 0>(x, g, st, tabs, codes, nnflag, nout, hist, m, mlp, qnet, nsm, s);
 }
 
 template <typename T>
 int launch_compress(const void* x, const Geo& g, const State* st, const Tabs* tabs, uint16_t* codes, uint8_t* nnflag,
-                    uint32_t* nout, unsigned long long* hist, int m, int mode, const Mlp& mlp, int nsm,
-                    cudaStream_t s) {
+                    uint32_t* nout, unsigned long long* hist, int m, int mode, const Mlp& mlp,
+                    const long long* qnet, int nsm, cudaStream_t s) {
   const int b0 = g.b[0], b1 = g.b[1], b2 = g.b[2];
 #define PC_SHAPE(A, B, C) \
-  if (b0 == A && b1 == B && b2 == C) return launch_c_shape<T, A, B, C>(x, g, st, tabs, codes, nnflag, nout, hist, m, mode, mlp, nsm, s);
+  if (b0 == A && b1 == B && b2 == C) return launch_c_shape<T, A, B, C>(x, g, st, tabs, codes, nnflag, nout, hist, m, mode, mlp, qnet, nsm, s);
   PC_SHAPE(8, 8, 8)
   PC_SHAPE(4, 4, 4)
   PC_SHAPE(16, 16, 16)
@@ -566,8 +646,10 @@ int launch_compress(const void* x, const Geo& g, const State* st, const Tabs* ta
   return PC_ERR_ARG;
 }
 template int launch_compress<float>(const void*, const Geo&, const State*, const Tabs*, uint16_t*, uint8_t*,
-                                    uint32_t*, unsigned long long*, int, int, const Mlp&, int, cudaStream_t);
+                                    uint32_t*, unsigned long long*, int, int, const Mlp&, const long long*, int,
+                                    cudaStream_t);
 template int launch_compress<double>(const void*, const Geo&, const State*, const Tabs*, uint16_t*, uint8_t*,
-                                     uint32_t*, unsigned long long*, int, int, const Mlp&, int, cudaStream_t);
+                                     uint32_t*, unsigned long long*, int, int, const Mlp&, const long long*, int,
+                                     cudaStream_t);
 
 }  // namespace pc

@@ -10,6 +10,7 @@
 // writes the brick with coalesced stores.  A damaged stream sets the error
 // word and never leads to an out-of-bounds access.
 #include "pc_kernels.cuh"
+#include "pc_qmlp.cuh"
 #include "pc_profile.cuh"
 
 namespace pc {
@@ -297,10 +298,12 @@ __global__ void __launch_bounds__(256) k_huff_decode(Geo g, const uint8_t* __res
 // bricks (as in compression) in zero-bordered padded arrays, and the brick is
 // written back with coalesced (16-byte where rows allow) stores.
 // ---------------------------------------------------------------------------
-template <int BV, int PV, int TSZ>
+template <int BV, int PV, int TSZ, int MODE, int K, int H1, int H2>
 constexpr size_t recon_smem_bytes() {
   constexpr int G = BrickShape<BV>::G;
-  return sizeof(Tabs) + (size_t)((G * PV + 3) & ~3) * 4 + (size_t)G * BV * TSZ * 2 + (size_t)G * BV * 2 * 2 +
+  size_t q = 0;
+  if constexpr (MODE == 2) q = ((size_t)QShape<K, H1, H2>::NFRAG * 4 + (size_t)QShape<K, H1, H2>::NBIAS * 8 + 15) & ~(size_t)15;
+  return sizeof(Tabs) + q + (size_t)((G * PV + 3) & ~3) * 4 + (size_t)G * BV * TSZ * 2 + (size_t)G * BV * 2 * 2 +
          (size_t)BV * 2 + 16;
 }
 
@@ -318,7 +321,14 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
   constexpr bool VEC_OK = (B2 * G) % VW == 0;
   extern __shared__ __align__(16) unsigned char smem[];
   Tabs& tb = *reinterpret_cast<Tabs*>(smem);
-  int* s_vp = reinterpret_cast<int*>(smem + sizeof(Tabs));          // G*PV padded centred codes
+  constexpr int QK = MODE == 2 ? K : 7, QH1 = MODE == 2 ? H1 : 16, QH2 = MODE == 2 ? H2 : 16;
+  using QS = QShape<QK, QH1, QH2>;
+  // whole 16-byte units, so that the arrays after it keep their 16-byte alignment
+  constexpr size_t QBYTES = MODE == 2 ? (((size_t)QS::NFRAG * 4 + (size_t)QS::NBIAS * 8 + 15) & ~(size_t)15) : 0;
+  uint32_t* s_frag = reinterpret_cast<uint32_t*>(smem + sizeof(Tabs));   // fixed-point form only
+  long long* s_qbias = reinterpret_cast<long long*>(s_frag + (MODE == 2 ? QS::NFRAG : 0));
+  __shared__ QSc s_qsc;
+  int* s_vp = reinterpret_cast<int*>(smem + sizeof(Tabs) + QBYTES);  // G*PV padded centred codes
   T* s_x = reinterpret_cast<T*>(s_vp + VPR);                        // G*BV
   T* s_ov = s_x + G * BV;                                           // G*BV balance points of each block
   uint16_t* s_cd = reinterpret_cast<uint16_t*>(s_ov + G * BV);      // G*BV
@@ -350,6 +360,7 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
   for (int i = tid; i < VPR; i += 256) s_vp[i] = 0;
   for (int i = tid; i < SZ + 2; i += 256) { s_ws[i] = 0; s_fill[i] = 0; }
   if (tid == 0) s_bad = 0;
+  if constexpr (MODE == 2) qnet_stage<QK, QH1, QH2>(di.qnet, s_frag, s_qbias, &s_qsc);
   __syncthreads();
   for (int j = tid; j < BV; j += 256) {
     const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
@@ -458,7 +469,92 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
     }
     __syncthreads();
     const int da = s_da[team];
-    if constexpr (MODE != 0 && K > 0) {
+    if constexpr (MODE == 2) {
+      // Each wave of all G blocks at once, in tiles of 16 points on the tensor
+      // cores; the lanes holding a tile's predictions finish its points.
+      const int wid = tid >> 5;
+      const QSc qsc = s_qsc;
+      int qoff[QS::KC1][4], qhi[QS::KC1][4];  // stencil offset; limb 1 hi, 0 lo, 2 padding
+#pragma unroll
+      for (int kc = 0; kc < QS::KC1; ++kc)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          int in, hi;
+          qcol<QK>(kc, e, in, hi);
+          qoff[kc][e] = in < 0 ? 0 : PD::off(st_dz(QK, in), st_dy(QK, in), st_dx(QK, in));
+          qhi[kc][e] = in < 0 ? 2 : hi;  // 2: padding column
+        }
+      for (int sw = 1; sw < nwave; ++sw) {
+        const int w0 = s_ws[sw], S = s_ws[sw + 1] - w0;
+        const int tot = G * S;
+        for (int tile = wid; tile * 16 < tot; tile += 8) {
+          int lv[2][QS::KC1][4];
+          int fs[2];
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const int f = tile * 16 + (lane >> 2) + 8 * r;
+            fs[r] = f;
+            const int gb = f < tot ? f / S : 0;
+            const int j = f < tot ? s_list[w0 + f - gb * S] : 0;
+            const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+            const int pj = PD::at(lz, ly, lx);
+            const int* vpg = s_vp + gb * PD::PV;
+#pragma unroll
+            for (int kc = 0; kc < QS::KC1; ++kc)
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                int v = qhi[kc][e] == 2 ? 0 : vpg[pj + qoff[kc][e]];
+                v = v > kQIn ? kQIn : (v < -kQIn ? -kQIn : v);
+                lv[r][kc][e] = qlimb(v, qhi[kc][e]);
+              }
+          }
+          int pq[2];
+          qnet_tile<QK, QH1, QH2>(s_frag, s_qbias, qsc, lv, pq[0], pq[1]);
+          if ((lane & 3) == 0) {
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+              const int f = fs[r];
+              if (f >= tot) continue;
+              const int gb = f / S;
+              const int j = s_list[w0 + f - gb * S];
+              const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+              const int e2g = s_e2[gb];
+              const bool fullg = e0 == B0 && e1 == B1 && e2g == B2;
+              if (!(e2g > 0 && (fullg || (lz < e0 && ly < e1 && lx < e2g)))) continue;
+              const int pj = PD::at(lz, ly, lx);
+              const unsigned int code = s_cd[gb * BV + j];
+              int q;
+              if (code == 0) {
+                const unsigned long long ob = s_obase[gb];
+                unsigned int rr = 1u + s_rk[gb * BV + j];
+                if (rr >= (unsigned int)s_no[gb] || ob + rr >= di.n_out) { bad = true; rr = 0; }
+                const T xv = s_ov[gb * BV + rr];
+                bool okk;
+                q = Num<T>::transform(xv, c, tb, okk);
+                s_x[gb * BV + j] = xv;
+              } else {
+                long long prd;
+                if (s_usen[gb]) {
+                  prd = pq[r];
+                } else {
+                  const int* vpg = s_vp + gb * PD::PV;
+                  int acc = 0;
+#pragma unroll
+                  for (int si = 0; si < 7; ++si) acc += lz_w(7, si) * vpg[pj + PD::off(s7_dz(si), s7_dy(si), s7_dx(si))];
+                  prd = acc;
+                }
+                const long long qq = (long long)s_da[gb] + prd + ((long long)code - R);
+                if (qq > 2147483647LL || qq < -2147483647LL) { bad = true; q = 0; }
+                else q = (int)qq;
+                s_x[gb * BV + j] = Num<T>::recon(q, c, tb);
+              }
+              s_vp[gb * PD::PV + pj] = clampv((long long)q - s_da[gb]);
+            }
+          }
+        }
+        __syncthreads();
+      }
+    } else if constexpr (MODE != 0 && K > 0) {
       // Each wave of all G blocks at once, flattened over the CTA, two points
       // per thread through the packed perceptron forward.
       for (int sw = 1; sw < nwave; ++sw) {
@@ -620,7 +716,7 @@ static int launch_r(const uint8_t* in, const Geo& g, const DecInfo& di, const De
   constexpr int BV = B0 * B1 * B2;
   constexpr bool WIDE = MODE != 0 && (K == 13 || K == 0);
   auto kern = k_recon<T, B0, B1, B2, MODE, K, H1, H2>;
-  const size_t sm = recon_smem_bytes<BV, Pad<B0, B1, B2, WIDE>::PV, (int)sizeof(T)>();
+  const size_t sm = recon_smem_bytes<BV, Pad<B0, B1, B2, WIDE>::PV, (int)sizeof(T), MODE, K, H1, H2>();
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
     return PC_ERR_CUDA;
   int per_sm = 0;
@@ -639,6 +735,13 @@ template <typename T, int B0, int B1, int B2>
 static int launch_r_shape(const uint8_t* in, const Geo& g, const DecInfo& di, const DecScratch& ds, const Mlp& mlp,
                           T* out, int nsm, cudaStream_t s) {
   if (!di.usenn_any) return launch_r<T, B0, B1, B2, 0, 0, 0, 0>(in, g, di, ds, mlp, out, nsm, s);
+  if (di.qmode) {
+    if (mlp.k == 7 && mlp.h1 == 16 && mlp.h2 == 16)
+      return launch_r<T, B0, B1, B2, 2, 7, 16, 16>(in, g, di, ds, mlp, out, nsm, s);
+    if (mlp.k == 13 && mlp.h1 == 32 && mlp.h2 == 32)
+      return launch_r<T, B0, B1, B2, 2, 13, 32, 32>(in, g, di, ds, mlp, out, nsm, s);
+    return PC_ERR_ARG;
+  }
   if (mlp.k == 7 && mlp.h1 == 16 && mlp.h2 == 16)
     return launch_r<T, B0, B1, B2, 1, 7, 16, 16>(in, g, di, ds, mlp, out, nsm, s);
   if (mlp.k == 13 && mlp.h1 == 32 && mlp.h2 == 32)
@@ -646,9 +749,16 @@ static int launch_r_shape(const uint8_t* in, const Geo& g, const DecInfo& di, co
   return launch_r<T, B0, B1, B2, 1, 0, 0, 0>(in, g, di, ds, mlp, out, nsm, s);
 }
 
+// The fixed-point network read from the container must lie in its stated
+// ranges (exact tensor-core sums, shifts inside 64 bits).
+__global__ void k_qcheck(DecInfo di, int* err) {
+  if (threadIdx.x == 0 && !qnet_valid(di.qnet, di.stencil, di.h1, di.h2, di.s_in)) atomicExch(err, PC_ERR_CORRUPT);
+}
+
 template <typename T>
 int launch_decompress(const uint8_t* in, const Geo& g, const DecInfo& di, const DecScratch& ds, const Mlp& mlp,
                       T* out, int nsm, cudaStream_t s) {
+  if (di.qmode) k_qcheck<<<1, 32, 0, s>>>(di, ds.err);
   { ProfScope p(kStDecTables, s); k_dec_tables<<<1, 1024, 0, s>>>(in, di, ds); }
   const unsigned int nc = (unsigned int)g.nchunks;
   {

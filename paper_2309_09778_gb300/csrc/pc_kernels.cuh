@@ -51,8 +51,9 @@ __device__ __forceinline__ int team_sum(int v, int* slot) {
 // Values the header needs that only the host knows.
 struct HdrInfo {
   int dtype, pred, stencil, h1, h2, m, s_in, nw;
+  int wsz;                    // bytes per weights-section entry: 4 (f32 weights) or 8 (int64 fixed-point network)
   double eb;
-  unsigned long long off_cb;  // = al16(256 + 4 nw)
+  unsigned long long off_cb;  // = al16(256 + wsz nw)
   unsigned long long cap;     // output capacity in bytes
 };
 
@@ -109,8 +110,8 @@ int launch_stats_consts(const void* x, unsigned long long n, State* st, Tabs* ta
                         int nsym, double eb, int nsm, cudaStream_t s);
 template <typename T>
 int launch_compress(const void* x, const Geo& g, const State* st, const Tabs* tabs, uint16_t* codes, uint8_t* nnflag,
-                    uint32_t* nout, unsigned long long* hist, int m, int mode, const Mlp& mlp, int nsm,
-                    cudaStream_t s);
+                    uint32_t* nout, unsigned long long* hist, int m, int mode, const Mlp& mlp,
+                    const long long* qnet, int nsm, cudaStream_t s);
 int launch_codebook(const unsigned long long* hist, int m, uint8_t* lens, uint32_t* cw, State* st,
                     const HuffScratch& hs, uint8_t* out, const Geo& g, const HdrInfo& hi, cudaStream_t s);
 template <typename T>
@@ -121,7 +122,8 @@ int launch_pack(const T* x, const Geo& g, const uint16_t* codes, const uint8_t* 
 
 // Decompression.
 struct DecInfo {
-  int dtype, m, stencil, h1, h2, s_in, usenn_any;
+  int dtype, m, stencil, h1, h2, s_in, usenn_any, qmode;
+  const long long* qnet;  // fixed-point network in the container (qmode), else null
   unsigned int n_used;
   unsigned long long n_out, swords;
   unsigned long long off_cb, off_bb, off_bn, off_ov, off_st, in_size;
@@ -160,6 +162,11 @@ size_t train_ctl_bytes();
 template <typename T>
 int launch_train(const T* x, const Geo& g, const State* st, const Tabs* tabs, const TrainBufs& tb, int k, int h1,
                  int h2, int m, int nmodels, unsigned long long seed, unsigned int thr32, cudaStream_t s);
+
+template <typename T>
+int launch_quantize(const T* x, const Geo& g, const State* st, const Tabs* tabs, const TrainBufs& tb, int k, int h1,
+                    int h2, int s_in, unsigned long long seed, unsigned int thr32, long long* q,
+                    unsigned long long* qmax, cudaStream_t s);
 
 template <typename T>
 int launch_decompress(const uint8_t* in, const Geo& g, const DecInfo& di, const DecScratch& ds, const Mlp& mlp,

@@ -147,8 +147,10 @@ __global__ void __launch_bounds__(1024) k_chunkscan(Geo g, const unsigned long l
   for (unsigned long long i = off_ov + ts * to + tid; i < off_st; i += nt) out[i] = 0;
   for (unsigned long long i = off_st + 4ull * swords + tid; i < total; i += nt) out[i] = 0;
   // weights and their pad
-  for (int i = tid; i < hi.nw; i += nt) st_u32(out + kHdr + 4ull * i, __float_as_uint(mlp.w[i]));
-  for (unsigned long long i = kHdr + 4ull * hi.nw + tid; i < hi.off_cb; i += nt) out[i] = 0;
+  // the f32 weights; the fixed-point network was placed there by the host
+  if (hi.pred == 1)
+    for (int i = tid; i < hi.nw; i += nt) st_u32(out + kHdr + 4ull * i, __float_as_uint(mlp.w[i]));
+  for (unsigned long long i = kHdr + (unsigned long long)hi.wsz * hi.nw + tid; i < hi.off_cb; i += nt) out[i] = 0;
   // header
   if (tid < 256) {
     unsigned int cr = (unsigned int)tid;
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(1024) k_chunkscan(Geo g, const unsigned long l
     st_u32(out + 0, 0x504D4350u);  // "PCMP"
     st_u32(out + 4, 1u);
     st_u32(out + 8, (unsigned int)hi.dtype);
-    st_u32(out + 12, nn ? 1u : 0u);
+    st_u32(out + 12, (unsigned int)hi.pred);
     st_u64(out + 16, (unsigned long long)g.n[0]);
     st_u64(out + 24, (unsigned long long)g.n[1]);
     st_u64(out + 32, (unsigned long long)g.n[2]);

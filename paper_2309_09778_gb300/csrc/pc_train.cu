@@ -16,6 +16,7 @@
 //   k_choose       the cheapest model (Lorenzo unless strictly beaten).
 #include "pc_kernels.cuh"
 #include "pc_profile.cuh"
+#include "pc_qmlp.cuh"
 
 namespace pc {
 
@@ -440,6 +441,170 @@ int launch_train(const T* x, const Geo& g, const State* st, const Tabs* tabs, co
   if (k == 13 && h1 == 16 && h2 == 16) return launch_train_models<13, 16, 16>(tb, nmodels, m, s);
   return PC_ERR_ARG;
 }
+// ---------------------------------------------------------------------------
+// Fixed-point (BF16) form of a trained perceptron.  Weights of layer l become
+// integers |Wq| <= 255 times 2^-e_l, with e_l the largest exponent such that
+// max|W_l| 2^e_l <= 255 (kept in [-30, 30]); biases become integers in the
+// units of their layer's sums (clamped to +-2^40); each hidden layer's shift
+// t is the smallest t in [-24, 40] with max 16 |leaky(A)| 2^-t <= 16 (2^15 -
+// 1) over the used training and validation samples (0 when every A is 0).
+// ---------------------------------------------------------------------------
+__device__ int q_wexp(float m) {
+  if (m == 0.0f) return 0;
+  int E;
+  const float fr = frexpf(m, &E);
+  const int e = fr <= 255.0f / 256.0f ? 8 - E : 7 - E;
+  return e < -30 ? -30 : (e > 30 ? 30 : e);
+}
+__device__ long long q_w(float w, int e) { return (long long)rintf(ldexpf(w, e)); }
+__device__ long long q_b(float b, int E) {
+  const double v = rint(ldexp((double)b, E));
+  const double lim = 1099511627776.0;
+  return (long long)(v > lim ? lim : (v < -lim ? -lim : v));
+}
+
+// one CTA: exponents, integer weights, layer-1 biases, header of the network
+__global__ void __launch_bounds__(256) k_qweights(const float* __restrict__ w, int k, int h1, int h2, const TrainCtl* ctl,
+                                                  long long* q, unsigned long long* qmax) {
+  __shared__ unsigned int s_m[3];
+  const int tid = threadIdx.x;
+  if (tid < 3) s_m[tid] = 0u;
+  __syncthreads();
+  const float* W1 = w;
+  const float* W2 = W1 + h1 * k + h1;
+  const float* W3 = W2 + h2 * h1 + h2;
+  for (int i = tid; i < h1 * k; i += 256) atomicMax(&s_m[0], __float_as_uint(fabsf(W1[i])));
+  for (int i = tid; i < h2 * h1; i += 256) atomicMax(&s_m[1], __float_as_uint(fabsf(W2[i])));
+  for (int i = tid; i < h2; i += 256) atomicMax(&s_m[2], __float_as_uint(fabsf(W3[i])));
+  __syncthreads();
+  const int s_in = ctl->s_in;
+  const int e1 = q_wexp(__uint_as_float(s_m[0])), e2 = q_wexp(__uint_as_float(s_m[1])),
+            e3 = q_wexp(__uint_as_float(s_m[2]));
+  long long* QW1 = q + kQHdr;
+  long long* QB1 = QW1 + h1 * k;
+  long long* QW2 = QB1 + h1;
+  long long* QW3 = QW2 + h2 * h1 + h2;
+  for (int i = tid; i < h1 * k; i += 256) QW1[i] = q_w(W1[i], e1);
+  for (int i = tid; i < h1; i += 256) QB1[i] = q_b(W1[h1 * k + i], e1 + s_in);
+  for (int i = tid; i < h2 * h1; i += 256) QW2[i] = q_w(W2[i], e2);
+  for (int i = tid; i < h2; i += 256) QW3[i] = q_w(W3[i], e3);
+  if (tid == 0) {
+    q[0] = k; q[1] = h1; q[2] = h2; q[3] = s_in;
+    q[4] = e1; q[5] = e2; q[6] = e3; q[7] = 0; q[8] = 0;
+    qmax[0] = 0ull;
+    qmax[1] = 0ull;
+  }
+}
+
+// max 16 |leaky(A)| of hidden layer L (1 or 2) over the used samples
+template <int L>
+__global__ void __launch_bounds__(256) k_qscan(const int* __restrict__ tin, const uint8_t* __restrict__ tus,
+                                               const int* __restrict__ vin, const uint8_t* __restrict__ vus,
+                                               const TrainCtl* ctl, const long long* __restrict__ q,
+                                               unsigned long long* qmax) {
+  const int k = (int)q[0], h1 = (int)q[1], h2 = (int)q[2], t1 = (int)q[7];
+  const long long* W1 = q + kQHdr;
+  const long long* B1 = W1 + h1 * k;
+  const long long* W2 = B1 + h1;
+  const long long* B2 = W2 + h2 * h1;
+  const unsigned long long nt = ctl->ntrain, nv = ctl->nval;
+  unsigned long long m = 0;
+  for (unsigned long long i = blockIdx.x * 256ull + threadIdx.x; i < nt + nv; i += gridDim.x * 256ull) {
+    const bool isv = i >= nt;
+    const unsigned long long si = isv ? i - nt : i;
+    if (!(isv ? vus[si] : tus[si])) continue;
+    const int* in = (isv ? vin : tin) + si * (unsigned long long)k;
+    int x[13];
+    for (int c = 0; c < k; ++c) x[c] = in[c] > kQIn ? kQIn : (in[c] < -kQIn ? -kQIn : in[c]);
+    int h1q[kMaxH];
+    for (int j = 0; j < h1; ++j) {
+      int acc = 0;
+      for (int c = 0; c < k; ++c) acc += (int)W1[j * k + c] * x[c];
+      const long long a = (long long)acc + B1[j];
+      if (L == 1) {
+        const unsigned long long l16 = (unsigned long long)(a >= 0 ? 16 * a : -a);
+        m = l16 > m ? l16 : m;
+      } else {
+        h1q[j] = leaky_requant(a, t1);
+      }
+    }
+    if (L == 2) {
+      for (int j = 0; j < h2; ++j) {
+        int acc = 0;
+        for (int c = 0; c < h1; ++c) acc += (int)W2[j * h1 + c] * h1q[c];
+        const long long a = (long long)acc + B2[j];
+        const unsigned long long l16 = (unsigned long long)(a >= 0 ? 16 * a : -a);
+        m = l16 > m ? l16 : m;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, m, o);
+    m = y > m ? y : m;
+  }
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(&qmax[L - 1], m);
+}
+
+// shift of hidden layer L from its maximum; then the next layer's biases
+template <int L>
+__global__ void k_qshift(const float* __restrict__ w, long long* q, const unsigned long long* qmax) {
+  if (threadIdx.x != 0) return;
+  const int k = (int)q[0], h1 = (int)q[1], h2 = (int)q[2], s_in = (int)q[3];
+  const int e1 = (int)q[4], e2 = (int)q[5], e3 = (int)q[6];
+  const unsigned long long M = qmax[L - 1];
+  int t = 0;
+  if (M) {
+    const unsigned long long lim = 16ull * (unsigned long long)kQAct;
+    t = 40;
+    for (int c = -24; c < 40; ++c) {
+      if (c >= 0 ? (M <= (lim << c)) : ((M << (-c)) <= lim)) { t = c; break; }
+    }
+  }
+  const float* b2 = w + h1 * k + h1 + h2 * h1;
+  const float* b3 = b2 + h2 + h2;
+  long long* QB2 = q + kQHdr + h1 * k + h1 + h2 * h1;
+  long long* QB3 = QB2 + h2 + h2;
+  if (L == 1) {
+    q[7] = t;
+    for (int j = 0; j < h2; ++j) QB2[j] = q_b(b2[j], e1 + e2 + s_in - t);
+  } else {
+    q[8] = t;
+    QB3[0] = q_b(b3[0], e1 + e2 + e3 + s_in - (int)q[7] - t);
+  }
+}
+
+template <typename T>
+int launch_quantize(const T* x, const Geo& g, const State* st, const Tabs* tabs, const TrainBufs& tb, int k, int h1,
+                    int h2, int s_in, unsigned long long seed, unsigned int thr32, long long* q,
+                    unsigned long long* qmax, cudaStream_t s) {
+  TrainCtl* ctl = reinterpret_cast<TrainCtl*>(tb.ctl);
+  if (cudaMemsetAsync(ctl, 0, sizeof(TrainCtl), s) != cudaSuccess) return PC_ERR_CUDA;
+  const unsigned int nb8 = (unsigned int)((g.nblocks + 7) / 8);
+  k_samp_count<<<nb8, 256, 0, s>>>(g, seed, thr32, tb.cnt_t, tb.cnt_v);
+  k_samp_scan<<<1, 1024, 0, s>>>(g.nblocks, tb.cnt_t, tb.cnt_v, tb.off_t, tb.off_v, ctl);
+  const size_t gsm = sizeof(Tabs) + 4ull * g.bvol * 4;
+  if (cudaFuncSetAttribute(k_samp_gather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm) != cudaSuccess)
+    return PC_ERR_CUDA;
+  k_samp_gather<T><<<(unsigned int)((g.nblocks + 3) / 4), 128, gsm, s>>>(
+      x, g, st, tabs, seed, thr32, k, tb.off_t, tb.off_v, tb.tin, tb.ttg, tb.tus, tb.vin, tb.vtg, tb.vus, ctl,
+      tb.cap_t, tb.cap_v);
+  // the input scale is the caller's (the one the weights were trained with)
+  if (cudaMemcpyAsync(&ctl->s_in, &s_in, sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess) return PC_ERR_CUDA;
+  k_qweights<<<1, 256, 0, s>>>(tb.w, k, h1, h2, ctl, q, qmax);
+  k_qscan<1><<<304, 256, 0, s>>>(tb.tin, tb.tus, tb.vin, tb.vus, ctl, q, qmax);
+  k_qshift<1><<<1, 32, 0, s>>>(tb.w, q, qmax);
+  k_qscan<2><<<304, 256, 0, s>>>(tb.tin, tb.tus, tb.vin, tb.vus, ctl, q, qmax);
+  k_qshift<2><<<1, 32, 0, s>>>(tb.w, q, qmax);
+  return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
+}
+template int launch_quantize<float>(const float*, const Geo&, const State*, const Tabs*, const TrainBufs&, int, int,
+                                    int, int, unsigned long long, unsigned int, long long*, unsigned long long*,
+                                    cudaStream_t);
+template int launch_quantize<double>(const double*, const Geo&, const State*, const Tabs*, const TrainBufs&, int, int,
+                                     int, int, unsigned long long, unsigned int, long long*, unsigned long long*,
+                                     cudaStream_t);
+
 template int launch_train<float>(const float*, const Geo&, const State*, const Tabs*, const TrainBufs&, int, int, int,
                                  int, int, unsigned long long, unsigned int, cudaStream_t);
 template int launch_train<double>(const double*, const Geo&, const State*, const Tabs*, const TrainBufs&, int, int,

@@ -19,7 +19,7 @@ _lib = None
 _lock = threading.Lock()
 
 PC_F32, PC_F64 = 0, 1
-PC_PRED_LORENZO, PC_PRED_MLP_FP32 = 0, 1
+PC_PRED_LORENZO, PC_PRED_MLP_FP32, PC_PRED_MLP_BF16 = 0, 1, 2
 STATUS = {0: "PC_OK", -1: "PC_ERR_ARG", -2: "PC_ERR_DTYPE", -3: "PC_ERR_NONFINITE", -4: "PC_ERR_CAPACITY",
           -5: "PC_ERR_CORRUPT", -6: "PC_ERR_TIMEOUT", -7: "PC_ERR_CUDA", -8: "PC_ERR_EB_RANGE"}
 SYMBOLS = ["pc_mlp_nweights", "pc_compress_bound", "pc_compress_workspace_size", "pc_compress",
@@ -49,7 +49,8 @@ class PcError(RuntimeError):
 
 class pc_params(C.Structure):
     _fields_ = [("eb_rel", C.c_double), ("block", C.c_int * 3), ("pred", C.c_int), ("stencil", C.c_int),
-                ("hidden", C.c_int * 2), ("m", C.c_int), ("s_in", C.c_int), ("h_weights", C.c_void_p)]
+                ("hidden", C.c_int * 2), ("m", C.c_int), ("s_in", C.c_int), ("h_weights", C.c_void_p),
+                ("h_qnet", C.c_void_p)]
 
 
 def lib():
@@ -90,6 +91,11 @@ def lib():
                 L.pc_train.restype = C.c_int
                 L.pc_train.argtypes = [vp, szp, C.c_int, P, C.c_ulonglong, C.c_uint, C.c_int, vp, vp, vp,
                                        C.POINTER(C.c_int), C.POINTER(C.c_int), vp, vp, sz, vp]
+            if hasattr(L, "pc_quantize"):
+                L.pc_qnet_len.restype = C.c_int
+                L.pc_qnet_len.argtypes = [C.c_int, C.c_int, C.c_int]
+                L.pc_quantize.restype = C.c_int
+                L.pc_quantize.argtypes = [vp, szp, C.c_int, P, C.c_ulonglong, C.c_uint, vp, vp, sz, vp]
             L.pc_profile_enable.restype = C.c_int
             L.pc_profile_enable.argtypes = [C.c_int]
             L.pc_profile_read.restype = C.c_int
@@ -135,8 +141,8 @@ def _stream_ptr(stream):
 
 
 def make_params(eb_rel: float, block=(8, 8, 8), pred: int = PC_PRED_LORENZO, stencil: int = 7,
-                hidden=(16, 16), m: int = 16, s_in: int = 0, weights=None):
-    """Fill a pc_params struct; the weights array is kept alive on the struct."""
+                hidden=(16, 16), m: int = 16, s_in: int = 0, weights=None, qnet=None):
+    """Fill a pc_params struct; the weights and network arrays are kept alive on the struct."""
     p = pc_params()
     p.eb_rel = float(eb_rel)
     p.block[:] = [int(b) for b in block]
@@ -151,6 +157,12 @@ def make_params(eb_rel: float, block=(8, 8, 8), pred: int = PC_PRED_LORENZO, ste
         p.h_weights = w.ctypes.data
     else:
         p.h_weights = None
+    if qnet is not None:
+        q = np.ascontiguousarray(np.asarray(qnet, dtype=np.int64))
+        p._q = q
+        p.h_qnet = q.ctypes.data
+    else:
+        p.h_qnet = None
     return p
 
 
@@ -264,6 +276,20 @@ def pc_train(field, params: pc_params, seed: int, thr32: int, lrs, lams, ws, str
                         _stream_ptr(stream))
     _check(st, "pc_train")
     return W, s_in.value, chosen.value, costs
+
+
+def pc_qnet_len(k: int, h1: int, h2: int) -> int:
+    return lib().pc_qnet_len(k, h1, h2)
+
+
+def pc_quantize(field, params: pc_params, seed: int, thr32: int, ws, stream=None) -> np.ndarray:
+    """Fixed-point (BF16) network from params' FP32 weights and s_in; returns int64 [pc_qnet_len]."""
+    q = np.zeros(pc_qnet_len(params.stencil, params.hidden[0], params.hidden[1]), np.int64)
+    st = lib().pc_quantize(C.c_void_p(field.data_ptr()), _dims3(field.shape), _dtype_of(field), C.byref(params),
+                           int(seed), int(thr32), q.ctypes.data_as(C.c_void_p), C.c_void_p(ws.data_ptr()),
+                           ws.numel(), _stream_ptr(stream))
+    _check(st, "pc_quantize")
+    return q
 
 
 def pc_profile_enable(on: bool) -> None:
