@@ -192,6 +192,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form", default="fp32", choices=["bf16", "fp32"],
+                    help="perceptron form of the timed step (the other form is timed beside it)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -226,11 +228,25 @@ def main():
     W, s_in, chosen, tcosts = pc.pc_train(d, tparams, 0, THR32, lrs, lams, tws)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    del tws
     w = W[chosen] if chosen >= 0 else None
-    pname = "mlp_fp32_s7_16x16" if w is not None else "lorenzo"
-    params = pc.make_params(EB, BLOCK, pred=pc.PC_PRED_LORENZO if w is None else pc.PC_PRED_MLP_FP32,
-                            stencil=7, hidden=(16, 16), s_in=s_in, weights=w)
+    # fixed-point (BF16 tensor-core) form of the chosen perceptron, from the same samples
+    q = None
+    quant_s = None
+    p32 = pc.make_params(EB, BLOCK, pred=pc.PC_PRED_MLP_FP32, stencil=7, hidden=(16, 16), s_in=s_in, weights=w)
+    if w is not None:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        q = pc.pc_quantize(d, p32, 0, THR32, tws)
+        torch.cuda.synchronize()
+        quant_s = time.perf_counter() - t0
+    del tws
+    pbf = pc.make_params(EB, BLOCK, pred=pc.PC_PRED_MLP_BF16, stencil=7, hidden=(16, 16), s_in=s_in, qnet=q)
+    if w is None:
+        pname, params = "lorenzo", pc.make_params(EB, BLOCK)
+    elif args.form == "bf16":
+        pname, params = "mlp_bf16_tensorcore_s7_16x16", pbf
+    else:
+        pname, params = "mlp_fp32_s7_16x16", p32
     lz_size = pc.compress(d, pc.make_params(EB, BLOCK)).numel()
     cap = pc.pc_compress_bound(SHAPE, pc.PC_F32, params)
     out = torch.empty(cap, dtype=torch.uint8, device=dev)
@@ -303,6 +319,32 @@ def main():
         te.append(time.perf_counter() - t1)
     e2e_ok = np.array_equal(hy.view(np.uint32), y.cpu().numpy().view(np.uint32))
 
+    # the other perceptron form on the same field, for the FP32 vs BF16 comparison
+    forms = {}
+    if w is not None:
+        for fname, fp in (("bf16", pbf), ("fp32", p32)):
+            ws2 = torch.empty(pc.pc_compress_workspace_size(SHAPE, pc.PC_F32, fp), dtype=torch.uint8, device=dev)
+            o2 = torch.empty(pc.pc_compress_bound(SHAPE, pc.PC_F32, fp), dtype=torch.uint8, device=dev)
+            tcs, tds = [], []
+            for it in range(3 + min(args.steps, 40)):
+                flush.zero_()
+                a, b, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                a.record(stream)
+                sz2 = pc.pc_compress(d, fp, o2, ws2, stream)
+                b.record(stream)
+                pc.pc_decompress(o2, sz2, y, wsd, stream)
+                c2.record(stream)
+                torch.cuda.synchronize()
+                if it >= 3:
+                    tcs.append(a.elapsed_time(b))
+                    tds.append(b.elapsed_time(c2))
+            okf = bool(((y.double() - d.double()).abs() <= EB * d.double().abs()).all().item())
+            forms[fname] = {"compress_gbs": nbytes / (statistics.median(tcs) * 1e6),
+                            "decompress_gbs": nbytes / (statistics.median(tds) * 1e6),
+                            "bits_per_value": 8.0 * sz2 / n, "bound_held": okf}
+            del ws2, o2
+        forms["bf16_size_vs_fp32"] = forms["bf16"]["bits_per_value"] / forms["fp32"]["bits_per_value"] - 1.0
+
     # plain FP32: a device copy of the field at HBM speed
     dst = torch.empty_like(d)
     c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -321,7 +363,7 @@ def main():
     blob = out[:size].cpu().numpy().tobytes()
     nnflag, free_pts = block_census(blob, SHAPE, BLOCK)
     nn_pts = int(free_pts[nnflag].sum())
-    fpp = perceptron_flops_per_point(7, 16, 16) if w is not None else 0
+    fpp = perceptron_flops_per_point(7, 16, 16) if (w is not None and args.form == "fp32") else 0
     bpv = 8.0 * size / n
     launches = sum(v[1] * KERNELS_PER_STAGE.get(k, 1) for k, v in stages.items())
 
@@ -342,7 +384,9 @@ def main():
                        "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
             "compress_gbs": nbytes / (tc * 1e6), "decompress_gbs": nbytes / (td * 1e6),
             "bits_per_value": bpv, "bound_held": ok,
-            "training": {"seconds": train_s, "models": int(lrs.size), "chosen": int(chosen), "s_in": int(s_in),
+            "perceptron_forms": forms,
+            "training": {"seconds": train_s, "quantize_seconds": quant_s, "models": int(lrs.size),
+                         "chosen": int(chosen), "s_in": int(s_in),
                          "samples_rate": THR32 / 2 ** 32, "val_cost_chosen": int(tcosts[chosen]) if chosen >= 0 else None,
                          "val_cost_lorenzo": int(tcosts[-1])},
             "bits_per_value_lorenzo_only": 8.0 * lz_size / n,

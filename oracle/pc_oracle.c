@@ -437,15 +437,16 @@ int32_t orc_mlp_pred32(const float* w, int k, int h1, int h2, int s_in, const in
 /* the stencil inputs are the centred codes clamped to +-(2^16 - 1); the      */
 /* hidden activations are integers clamped to +-(2^15 - 1).  Each layer's    */
 /* sum of products is therefore an exact integer, computed here in int64.   */
-/* (A tensor-core evaluation splits inputs and activations into signed      */
-/* 8-bit limbs, so each partial sum stays below 2^24 and FP32 accumulation  */
-/* is exact in any order and MMA shape.)  Per layer:                         */
+/* (A tensor-core evaluation splits inputs and activations into 8-bit limbs, */
+/* x = 256 hi + lo with 0 <= lo < 256, so each partial sum stays below 2^24  */
+/* and FP32 accumulation is exact in any order and MMA shape.)  Per layer:   */
 /*   A = sum Wq x + Bq;   leaky(A) = A >= 0 ? A : A / 16   (slope 2^-4)      */
-/*   hidden:  Hq = clamp(rne(leaky(A) 2^-t), +-(2^15 - 1))                   */
+/*   hidden:  Hq = clamp(rhu(leaky(A) 2^-t), +-(2^15 - 1)),  t >= 0          */
 /*   output:  pred = clamp(rne(A 2^-F), +-2^30),  F = sum e - sum t          */
-/* rne = round to nearest, ties to even.  Units: A_1 counts 2^-(e1 + s_in),  */
-/* so B1 = rint(b1 2^(e1 + s_in)); each later layer's bias takes the units   */
-/* of its sum (orc_quantize).                                                */
+/* rhu = round half up, floor(y + 1/2); rne = round to nearest, ties to even.*/
+/* Units: A_1 counts 2^-(e1 + s_in), so B1 = rint(b1 2^(e1 + s_in)); each    */
+/* later layer's bias takes the units of its sum (orc_quantize); biases are  */
+/* clamped to +-2^30, so every hidden sum fits 32 bits.                      */
 /* qnet (int64): k, h1, h2, s_in, e1, e2, e3, t1, t2, then W1[h1][k], B1[h1], */
 /* and for h2 > 0: W2[h2][h1], B2[h2], W3[h2], B3; for h2 = 0: W2[h1], B2    */
 /* (e3 = t2 = 0).                                                             */
@@ -470,8 +471,18 @@ static int64_t o_rne_shift(int64_t x, int s) {
   return q;
 }
 
+/* floor(x 2^-s + 1/2) for integer x, s >= 0 */
+static int64_t o_rhu_shift(int64_t x, int s) {
+  if (s <= 0) return x;
+  int64_t d = (int64_t)1 << s;
+  int64_t y = x + (d >> 1);
+  int64_t q = y / d;
+  if (y % d != 0 && y < 0) q -= 1;  /* floor */
+  return q;
+}
+
 static int64_t o_leaky_requant(int64_t a, int t) {
-  int64_t h = a >= 0 ? o_rne_shift(a, t) : o_rne_shift(a, t + 4);
+  int64_t h = a >= 0 ? o_rhu_shift(a, t) : o_rhu_shift(a, t + 4);
   return h > O_QH ? O_QH : (h < -O_QH ? -O_QH : h);
 }
 
@@ -552,17 +563,15 @@ static int64_t o_qw(float w, int e) { return (int64_t)rintf(ldexpf(w, e)); }
 
 static int64_t o_qb(float b, int E) {
   double v = rint(ldexp((double)b, E));
-  const double lim = 1099511627776.0; /* 2^40 */
+  const double lim = 1073741824.0; /* 2^30 */
   return (int64_t)(v > lim ? lim : (v < -lim ? -lim : v));
 }
 
-/* Smallest t in [-24, 40] with M 2^-t <= 16 (2^15 - 1), M = max 16|leaky(A)|. */
+/* Smallest t in [0, 40] with M 2^-t <= 16 (2^15 - 1), M = max 16|leaky(A)|. */
 static int o_shift_for(int64_t M) {
-  if (M <= 0) return 0;
   const int64_t lim = 16 * (int64_t)O_QH;
-  for (int t = -24; t < 40; t++) {
-    if (t >= 0 ? (M <= (lim << t)) : ((M << (-t)) <= lim)) return t;
-  }
+  for (int t = 0; t < 40; t++)
+    if (M <= (lim << t)) return t;
   return 40;
 }
 
@@ -1101,14 +1110,18 @@ int orc_decompress(const uint8_t* in, uint64_t in_size, void* xo, uint64_t cap_e
     for (int i = 0; i < nw; i++) qn[i] = (int64_t)get64(in + off_w + 8ull * i);
     int bad = qn[0] != k || qn[1] != h1 || qn[2] != h2 || qn[3] != s_in;
     for (int i = 4; i < 7; i++) bad |= qn[i] < -30 || qn[i] > 30;
-    for (int i = 7; i < 9; i++) bad |= qn[i] < -24 || qn[i] > 40;
+    for (int i = 7; i < 9; i++) bad |= qn[i] < 0 || qn[i] > 26;
+    {
+      int64_t F = qn[4] + qn[5] + qn[6] - qn[7] - qn[8];
+      bad |= F < -20 || F > 62;
+    }
     int li = O_QHDR;
     int lay[3][2] = {{h1, k}, {h2 ? h2 : 1, h1}, {h2 ? 1 : 0, h2}};
     for (int l = 0; l < 3 && !bad; l++) {
       for (int r = 0; r < lay[l][0]; r++) {
         for (int c2 = 0; c2 < lay[l][1]; c2++, li++) bad |= qn[li] < -255 || qn[li] > 255;
       }
-      for (int r = 0; r < lay[l][0]; r++, li++) bad |= qn[li] < -1099511627776LL || qn[li] > 1099511627776LL;
+      for (int r = 0; r < lay[l][0]; r++, li++) bad |= qn[li] < -1073741824LL || qn[li] > 1073741824LL;
     }
     if (bad || li != nw) { free(qn); return ORC_ERR_CORRUPT; }
   }

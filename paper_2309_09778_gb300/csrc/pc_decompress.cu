@@ -302,7 +302,9 @@ template <int BV, int PV, int TSZ, int MODE, int K, int H1, int H2>
 constexpr size_t recon_smem_bytes() {
   constexpr int G = BrickShape<BV>::G;
   size_t q = 0;
-  if constexpr (MODE == 2) q = ((size_t)QShape<K, H1, H2>::NFRAG * 4 + (size_t)QShape<K, H1, H2>::NBIAS * 8 + 15) & ~(size_t)15;
+  if constexpr (MODE == 2)
+    q = ((size_t)QShape<K, H1, H2>::NFRAG * 4 + (size_t)QShape<K, H1, H2>::NBIAS * 8 + (size_t)G * BV * 4 + 15) &
+        ~(size_t)15;
   return sizeof(Tabs) + q + (size_t)((G * PV + 3) & ~3) * 4 + (size_t)G * BV * TSZ * 2 + (size_t)G * BV * 2 * 2 +
          (size_t)BV * 2 + 16;
 }
@@ -324,9 +326,11 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
   constexpr int QK = MODE == 2 ? K : 7, QH1 = MODE == 2 ? H1 : 16, QH2 = MODE == 2 ? H2 : 16;
   using QS = QShape<QK, QH1, QH2>;
   // whole 16-byte units, so that the arrays after it keep their 16-byte alignment
-  constexpr size_t QBYTES = MODE == 2 ? (((size_t)QS::NFRAG * 4 + (size_t)QS::NBIAS * 8 + 15) & ~(size_t)15) : 0;
+  constexpr size_t QBYTES =
+      MODE == 2 ? (((size_t)QS::NFRAG * 4 + (size_t)QS::NBIAS * 8 + (size_t)G * BV * 4 + 15) & ~(size_t)15) : 0;
   uint32_t* s_frag = reinterpret_cast<uint32_t*>(smem + sizeof(Tabs));   // fixed-point form only
   long long* s_qbias = reinterpret_cast<long long*>(s_frag + (MODE == 2 ? QS::NFRAG : 0));
+  int* s_wpred = reinterpret_cast<int*>(s_qbias + (MODE == 2 ? QS::NBIAS : 0));  // one wave's predictions
   __shared__ QSc s_qsc;
   int* s_vp = reinterpret_cast<int*>(smem + sizeof(Tabs) + QBYTES);  // G*PV padded centred codes
   T* s_x = reinterpret_cast<T*>(s_vp + VPR);                        // G*BV
@@ -511,46 +515,47 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
           int pq[2];
           qnet_tile<QK, QH1, QH2>(s_frag, s_qbias, qsc, lv, pq[0], pq[1]);
           if ((lane & 3) == 0) {
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-              const int f = fs[r];
-              if (f >= tot) continue;
-              const int gb = f / S;
-              const int j = s_list[w0 + f - gb * S];
-              const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
-              const int e2g = s_e2[gb];
-              const bool fullg = e0 == B0 && e1 == B1 && e2g == B2;
-              if (!(e2g > 0 && (fullg || (lz < e0 && ly < e1 && lx < e2g)))) continue;
-              const int pj = PD::at(lz, ly, lx);
-              const unsigned int code = s_cd[gb * BV + j];
-              int q;
-              if (code == 0) {
-                const unsigned long long ob = s_obase[gb];
-                unsigned int rr = 1u + s_rk[gb * BV + j];
-                if (rr >= (unsigned int)s_no[gb] || ob + rr >= di.n_out) { bad = true; rr = 0; }
-                const T xv = s_ov[gb * BV + rr];
-                bool okk;
-                q = Num<T>::transform(xv, c, tb, okk);
-                s_x[gb * BV + j] = xv;
-              } else {
-                long long prd;
-                if (s_usen[gb]) {
-                  prd = pq[r];
-                } else {
-                  const int* vpg = s_vp + gb * PD::PV;
-                  int acc = 0;
-#pragma unroll
-                  for (int si = 0; si < 7; ++si) acc += lz_w(7, si) * vpg[pj + PD::off(s7_dz(si), s7_dy(si), s7_dx(si))];
-                  prd = acc;
-                }
-                const long long qq = (long long)s_da[gb] + prd + ((long long)code - R);
-                if (qq > 2147483647LL || qq < -2147483647LL) { bad = true; q = 0; }
-                else q = (int)qq;
-                s_x[gb * BV + j] = Num<T>::recon(q, c, tb);
-              }
-              s_vp[gb * PD::PV + pj] = clampv((long long)q - s_da[gb]);
-            }
+            if (fs[0] < tot) s_wpred[fs[0]] = pq[0];
+            if (fs[1] < tot) s_wpred[fs[1]] = pq[1];
           }
+        }
+        __syncthreads();
+        // finish the wave's points, one per thread
+        for (int f = tid; f < tot; f += 256) {
+          const int gb = f / S;
+          const int j = s_list[w0 + f - gb * S];
+          const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+          const int e2g = s_e2[gb];
+          const bool fullg = e0 == B0 && e1 == B1 && e2g == B2;
+          if (!(e2g > 0 && (fullg || (lz < e0 && ly < e1 && lx < e2g)))) continue;
+          const int pj = PD::at(lz, ly, lx);
+          const unsigned int code = s_cd[gb * BV + j];
+          int q;
+          if (code == 0) {
+            const unsigned long long ob = s_obase[gb];
+            unsigned int rr = 1u + s_rk[gb * BV + j];
+            if (rr >= (unsigned int)s_no[gb] || ob + rr >= di.n_out) { bad = true; rr = 0; }
+            const T xv = s_ov[gb * BV + rr];
+            bool okk;
+            q = Num<T>::transform(xv, c, tb, okk);
+            s_x[gb * BV + j] = xv;
+          } else {
+            long long prd;
+            if (s_usen[gb]) {
+              prd = s_wpred[f];
+            } else {
+              const int* vpg = s_vp + gb * PD::PV;
+              int acc = 0;
+#pragma unroll
+              for (int si = 0; si < 7; ++si) acc += lz_w(7, si) * vpg[pj + PD::off(s7_dz(si), s7_dy(si), s7_dx(si))];
+              prd = acc;
+            }
+            const long long qq = (long long)s_da[gb] + prd + ((long long)code - R);
+            if (qq > 2147483647LL || qq < -2147483647LL) { bad = true; q = 0; }
+            else q = (int)qq;
+            s_x[gb * BV + j] = Num<T>::recon(q, c, tb);
+          }
+          s_vp[gb * PD::PV + pj] = clampv((long long)q - s_da[gb]);
         }
         __syncthreads();
       }

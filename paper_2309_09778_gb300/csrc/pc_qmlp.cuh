@@ -4,10 +4,12 @@
 // is an integer |Wq| <= 255 times 2^-e_l (an exact bf16 value); the stencil
 // inputs are the centred codes clamped to +-(2^16 - 1); hidden activations
 // are integers clamped to +-(2^15 - 1):
-//   A = sum Wq x + Bq;  hidden: Hq = clamp(rne(leaky(A) 2^-t)), leaky(A) = A
-//   for A >= 0 else A / 16;  output: pred = clamp(rne(A 2^-F), +-2^30).
-// On the tensor cores every input and activation is split into signed 8-bit
-// limbs, x = 256 hi + lo, and each layer is one bf16 GEMM against a
+//   A = sum Wq x + Bq;  hidden: Hq = clamp(rhu(leaky(A) 2^-t)), leaky(A) = A
+//   for A >= 0 else A / 16, t >= 0;  output: pred = clamp(rne(A 2^-F), +-2^30)
+// (rhu: round half up; rne: round half to even).  Sums stay below 2^28 and
+// biases within 2^30, so the hidden layers run in 32-bit integers.
+// On the tensor cores every input and activation is split into 8-bit limbs,
+// x = 256 hi + lo with 0 <= lo < 256, and each layer is one bf16 GEMM against a
 // block-diagonal weight matrix [[Wq^T, 0], [0, Wq^T]], so the hi and lo sums
 // come out in separate columns.  Each product is bf16 x bf16, exact in FP32,
 // and each column's sum is an integer of magnitude below 2^21, so the FP32
@@ -37,16 +39,16 @@ __host__ __device__ constexpr int qnet_len(int k, int h1, int h2) {
   return kQHdr + h1 * k + h1 + (h2 ? h2 * h1 + h2 + h2 + 1 : h1 + 1);
 }
 
-// The network's stated ranges: shapes match, |W| <= 255, |B| <= 2^40,
-// e in [-30, 30], t in [-24, 40], F = sum e - sum t in [-20, 62] (so every
-// shift of a 41-bit sum stays inside 64 bits).  Checked on the host before
+// The network's stated ranges: shapes match, |W| <= 255, |B| <= 2^30,
+// e in [-30, 30], t in [0, 26] (t + 4 <= 30 keeps the hidden shifts inside
+// 32 bits), F = sum e - sum t in [-20, 62].  Checked on the host before
 // compression and on the device before decompression.
 __host__ __device__ inline bool qnet_valid(const long long* q, int k, int h1, int h2, int s_in) {
   if (q[0] != k || q[1] != h1 || q[2] != h2 || q[3] != s_in) return false;
   for (int i = 4; i < 7; ++i)
     if (q[i] < -30 || q[i] > 30) return false;
   for (int i = 7; i < 9; ++i)
-    if (q[i] < -24 || q[i] > 40) return false;
+    if (q[i] < 0 || q[i] > 26) return false;
   const long long F = q[4] + q[5] + q[6] - q[7] - q[8];
   if (F < -20 || F > 62) return false;
   int li = kQHdr;
@@ -56,7 +58,7 @@ __host__ __device__ inline bool qnet_valid(const long long* q, int k, int h1, in
     for (int r = 0; r < rows[l] * cols[l]; ++r, ++li)
       if (q[li] < -255 || q[li] > 255) return false;
     for (int r = 0; r < rows[l]; ++r, ++li)
-      if (q[li] < -(1ll << 40) || q[li] > (1ll << 40)) return false;
+      if (q[li] < -(1ll << 30) || q[li] > (1ll << 30)) return false;
   }
   return li == qnet_len(k, h1, h2);
 }
@@ -71,23 +73,31 @@ __device__ __forceinline__ long long rne_shift(long long x, int s) {
   return q + ((r > h || (r == h && (q & 1))) ? 1 : 0);
 }
 
-__device__ __forceinline__ int leaky_requant(long long a, int t) {
-  const long long h = a >= 0 ? rne_shift(a, t) : rne_shift(a, t + 4);
-  return (int)(h > kQAct ? kQAct : (h < -kQAct ? -kQAct : h));
+// Hidden-layer requantization of an exact 32-bit sum (|a| < 2^30 + 2^28):
+// rhu(leaky(a) 2^-t) = floor((a + h) 2^-s) with s = t (a >= 0) or t + 4,
+// h = 2^(s-1) (0 for s = 0); clamp to +-(2^15 - 1).  hp/hn: the two halves.
+__device__ __forceinline__ int leaky_requant32(int a, int t, int hp, int hn) {
+  const bool neg = a < 0;
+  const int h = (a + (neg ? hn : hp)) >> (neg ? t + 4 : t);
+  return h > kQAct ? kQAct : (h < -kQAct ? -kQAct : h);
 }
 
-// Signed limbs with the sign of x: x = 256 hi + lo.
+// 8-bit limbs: x = 256 hi + lo, 0 <= lo < 256 (hi in [-256, 255] for |x| <= 65535).
 __device__ __forceinline__ void split_limbs(int x, int& hi, int& lo) {
-  const int a = x < 0 ? -x : x;
-  hi = x < 0 ? -(a >> 8) : (a >> 8);
-  lo = x < 0 ? -(a & 255) : (a & 255);
+  hi = x >> 8;
+  lo = x & 255;
 }
 
-// two small integers (|v| <= 256) as packed bf16 (exact): low half = first
+// Exact float of a small integer (|n| < 2^22) without a conversion
+// instruction: adding 1.5 * 2^23 puts n in the low mantissa bits.
+__device__ __forceinline__ float small_float(int n) { return __fsub_rn(__int_as_float(n + 0x4B400000), kMagic); }
+// Integer of an exactly integral float (|v| < 2^22).
+__device__ __forceinline__ int small_int(float v) { return __float_as_int(__fadd_rn(v, kMagic)) - 0x4B400000; }
+
+// two small integers (|v| <= 256) as packed bf16 (exact: at most 8
+// significant bits, so the float's low 16 bits are zero): low half = first
 __device__ __forceinline__ uint32_t bf16x2_int(int a, int b) {
-  const uint32_t ua = __float_as_uint(small_int_to_float(a)) >> 16;
-  const uint32_t ub = __float_as_uint(small_int_to_float(b)) >> 16;
-  return ua | (ub << 16);
+  return __byte_perm(__float_as_uint(small_float(a)), __float_as_uint(small_float(b)), 0x7632);
 }
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
@@ -220,14 +230,15 @@ __device__ __forceinline__ void qnet_tile(const uint32_t* __restrict__ s_frag, c
   }
   // combine limbs, bias, leaky ReLU, requantize: this thread's units are
   // n = 8 nb + 2 c + {0, 1} (nb < H1/8) for rows g (regs 0, 1) and g + 8 (2, 3)
+  const int hp1 = (1 << sc.t1) >> 1, hn1 = (1 << (sc.t1 + 4)) >> 1;
   int h1v[S::NB1 / 2][4];
 #pragma unroll
   for (int nb = 0; nb < S::NB1 / 2; ++nb)
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int n = nb * 8 + 2 * c + (e & 1);
-      const long long sum = 256ll * (long long)(int)d1[nb][e] + (long long)(int)d1[nb + S::NB1 / 2][e];
-      h1v[nb][e] = leaky_requant(sum + s_bias[n], sc.t1);
+      const int sum = 256 * small_int(d1[nb][e]) + small_int(d1[nb + S::NB1 / 2][e]);
+      h1v[nb][e] = leaky_requant32(sum + (int)s_bias[n], sc.t1, hp1, hn1);
     }
   // layer 2: A columns [hi(H1 units) | lo(H1 units)], straight from h1v
   float d2[S::NB2][4];
@@ -258,14 +269,15 @@ __device__ __forceinline__ void qnet_tile(const uint32_t* __restrict__ s_frag, c
       mma_bf16(d2[nb], a, b.x, b.y);
     }
   }
+  const int hp2 = (1 << sc.t2) >> 1, hn2 = (1 << (sc.t2 + 4)) >> 1;
   int h2v[S::NB2 / 2][4];
 #pragma unroll
   for (int nb = 0; nb < S::NB2 / 2; ++nb)
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int n = nb * 8 + 2 * c + (e & 1);
-      const long long sum = 256ll * (long long)(int)d2[nb][e] + (long long)(int)d2[nb + S::NB2 / 2][e];
-      h2v[nb][e] = leaky_requant(sum + s_bias[H1 + n], sc.t2);
+      const int sum = 256 * small_int(d2[nb][e]) + small_int(d2[nb + S::NB2 / 2][e]);
+      h2v[nb][e] = leaky_requant32(sum + (int)s_bias[H1 + n], sc.t2, hp2, hn2);
     }
   // output: column 0 = hi sum, column 1 = lo sum
   float d3[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -292,8 +304,8 @@ __device__ __forceinline__ void qnet_tile(const uint32_t* __restrict__ s_frag, c
   }
   // lanes with c == 0 hold columns 0 (hi) and 1 (lo) of rows g and g + 8
   const long long bo = s_bias[H1 + H2];
-  long long o0 = 256ll * (long long)(int)d3[0] + (long long)(int)d3[1] + bo;
-  long long o1 = 256ll * (long long)(int)d3[2] + (long long)(int)d3[3] + bo;
+  long long o0 = 256ll * small_int(d3[0]) + small_int(d3[1]) + bo;
+  long long o1 = 256ll * small_int(d3[2]) + small_int(d3[3]) + bo;
   o0 = rne_shift(o0, sc.F);
   o1 = rne_shift(o1, sc.F);
   const long long lim = 1073741824ll;

@@ -445,9 +445,9 @@ int launch_train(const T* x, const Geo& g, const State* st, const Tabs* tabs, co
 // Fixed-point (BF16) form of a trained perceptron.  Weights of layer l become
 // integers |Wq| <= 255 times 2^-e_l, with e_l the largest exponent such that
 // max|W_l| 2^e_l <= 255 (kept in [-30, 30]); biases become integers in the
-// units of their layer's sums (clamped to +-2^40); each hidden layer's shift
-// t is the smallest t in [-24, 40] with max 16 |leaky(A)| 2^-t <= 16 (2^15 -
-// 1) over the used training and validation samples (0 when every A is 0).
+// units of their layer's sums (clamped to +-2^30); each hidden layer's shift
+// t is the smallest t in [0, 40] with max 16 |leaky(A)| 2^-t <= 16 (2^15 - 1)
+// over the used training and validation samples.
 // ---------------------------------------------------------------------------
 __device__ int q_wexp(float m) {
   if (m == 0.0f) return 0;
@@ -459,7 +459,7 @@ __device__ int q_wexp(float m) {
 __device__ long long q_w(float w, int e) { return (long long)rintf(ldexpf(w, e)); }
 __device__ long long q_b(float b, int E) {
   const double v = rint(ldexp((double)b, E));
-  const double lim = 1099511627776.0;
+  const double lim = 1073741824.0;  // 2^30
   return (long long)(v > lim ? lim : (v < -lim ? -lim : v));
 }
 
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(256) k_qscan(const int* __restrict__ tin, cons
         const unsigned long long l16 = (unsigned long long)(a >= 0 ? 16 * a : -a);
         m = l16 > m ? l16 : m;
       } else {
-        h1q[j] = leaky_requant(a, t1);
+        h1q[j] = leaky_requant32((int)a, t1, (1 << t1) >> 1, (1 << (t1 + 4)) >> 1);
       }
     }
     if (L == 2) {
@@ -553,14 +553,10 @@ __global__ void k_qshift(const float* __restrict__ w, long long* q, const unsign
   const int k = (int)q[0], h1 = (int)q[1], h2 = (int)q[2], s_in = (int)q[3];
   const int e1 = (int)q[4], e2 = (int)q[5], e3 = (int)q[6];
   const unsigned long long M = qmax[L - 1];
-  int t = 0;
-  if (M) {
-    const unsigned long long lim = 16ull * (unsigned long long)kQAct;
-    t = 40;
-    for (int c = -24; c < 40; ++c) {
-      if (c >= 0 ? (M <= (lim << c)) : ((M << (-c)) <= lim)) { t = c; break; }
-    }
-  }
+  const unsigned long long lim = 16ull * (unsigned long long)kQAct;
+  int t = 40;
+  for (int c = 0; c < 40; ++c)
+    if (M <= (lim << c)) { t = c; break; }
   const float* b2 = w + h1 * k + h1 + h2 * h1;
   const float* b3 = b2 + h2 + h2;
   long long* QB2 = q + kQHdr + h1 * k + h1 + h2 * h1;

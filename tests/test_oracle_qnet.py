@@ -3,7 +3,7 @@
 The form: weights are integers |W| <= 255 times 2^-e per layer (exact bf16
 values), stencil inputs integers clamped to +-(2^16 - 1), hidden activations
 integers clamped to +-(2^15 - 1) after a leaky ReLU (slope 2^-4) and a
-round-half-even shift by t, prediction = rne(A_out 2^-F) with
+round-half-up shift by t >= 0, prediction = rne(A_out 2^-F) with
 F = sum e - sum t.  These tests hold the oracle to
   - the exactness claim behind the tensor-core evaluation: splitting inputs
     and activations into signed 8-bit limbs keeps every FP32 partial sum of
@@ -22,10 +22,9 @@ from paper_2309_09778_gb300 import gen
 
 
 def limbs(v, base=256):
-    """Signed limbs with the sign of v: v = base * hi + lo, |hi|, |lo| < base."""
+    """8-bit limbs: v = base * hi + lo with 0 <= lo < base (floor division)."""
     v = np.asarray(v, np.int64)
-    a = np.abs(v)
-    return np.sign(v) * (a // base), np.sign(v) * (a % base)
+    return v // base, v % base
 
 
 def f32_sum(products, rng):
@@ -47,11 +46,17 @@ def test_limb_products_accumulate_exactly_in_fp32(K, lim):
         x = rng.integers(-lim, lim + 1, K)
         x[rng.random(K) < 0.2] = lim * rng.choice([-1, 1])
         hi, lo = limbs(x)
-        assert np.all(np.abs(hi) <= 255) and np.all(np.abs(lo) <= 255)
+        assert np.all(np.abs(hi) <= 256) and np.all((lo >= 0) & (lo <= 255))
         s_hi = f32_sum(w * hi, rng)
         s_lo = f32_sum(w * lo, rng)
         assert abs(float(s_hi)) < 2 ** 24 and abs(float(s_lo)) < 2 ** 24
         assert 256 * int(s_hi) + int(s_lo) == int(np.dot(w, x))
+
+
+def rhu_shift(x: int, s: int) -> int:
+    """floor(x 2^-s + 1/2)"""
+    f = Fraction(x, 2 ** s) + Fraction(1, 2)
+    return f.numerator // f.denominator
 
 
 def rne_shift(x: int, s: int) -> int:
@@ -64,11 +69,12 @@ def rne_shift(x: int, s: int) -> int:
 
 
 def test_quantized_net_equals_rational_value_when_lossless(O):
-    """One hidden layer whose weights and biases are exactly representable and
-    inputs small enough that the chosen shift t1 <= -4 (requantization only
-    shifts left): no step loses information, so the fixed-point prediction is
-    the round-half-even of the FP32 network's exact value.  This pins the
-    units of e, t, s_in, the biases and F."""
+    """One hidden layer whose weights and biases are exactly representable,
+    pre-activations multiples of 16 (so the leaky slope 1/16 is exact) and
+    inputs small enough that the chosen shift t1 = 0: no step loses
+    information, so the fixed-point prediction is the round-half-even of the
+    FP32 network's exact value.  This pins the units of e, t, s_in, the
+    biases and F."""
     rng = np.random.default_rng(3)
     k, h1, h2 = 7, 16, 0
     nw = O.mlp_nweights(k, h1, h2)
@@ -77,7 +83,7 @@ def test_quantized_net_equals_rational_value_when_lossless(O):
         s_in = int(rng.integers(0, 4))
         W1 = rng.integers(-8, 9, (h1, k)).astype(np.float64) / 8       # max |W1| = 1 -> e1 = 7
         W1[0, 0] = 1.0
-        b1 = rng.integers(-20, 21, h1).astype(np.float64) / 2 ** (7 + s_in)
+        b1 = 16 * rng.integers(-20, 21, h1).astype(np.float64) / 2 ** (7 + s_in)
         Wo = rng.integers(-8, 9, h1).astype(np.float64) / 4             # max |Wo| = 2 -> e2 = 6
         Wo[0] = 2.0
         bo = float(rng.integers(-20, 21)) / 4
@@ -86,7 +92,7 @@ def test_quantized_net_equals_rational_value_when_lossless(O):
         tin = rng.integers(-2, 3, (100, k)).astype(np.int32)
         q = O.qnet_build(w, k, h1, h2, s_in, tin, np.ones(100, np.uint8))
         assert (int(q[4]), int(q[5])) == (7, 6)
-        if int(q[7]) > -4:
+        if int(q[7]) != 0:
             continue
         for v in tin[:30]:
             u = [Fraction(int(a), 2 ** s_in) for a in v]
@@ -123,18 +129,18 @@ def test_rne_shift_matches_fractions(O):
         assert O.mlp_pred_q(q, v) == want, (x, F)
 
 
-def test_leaky_requant_uses_slope_and_ties_to_even(O):
-    """Negative pre-activations are divided by 16 before the shift; ties go to even."""
+def test_leaky_requant_uses_slope_and_rounds_half_up(O):
+    """Negative pre-activations are divided by 16 before the shift; halves round up."""
     k, h1, h2 = 7, 2, 0
     n = O.qnet_len(k, h1, h2)
-    for x in (-1, -8, -24, -40, -1000, 8, 24, 37):
-        for t in (-2, 0, 1, 3):
+    for x in (-1, -8, -24, -40, -1000, 8, 24, 37, -7, -9):
+        for t in (0, 1, 3):
             q = np.zeros(n, np.int64)
             q[:9] = [k, h1, h2, 0, 0, t, 0, t, 0]   # e1 = 0, e2 = t, t1 = t: F = 0
             q[9] = 1                                 # unit 0 = input 0
             q[9 + h1 * k + h1] = 1                   # output = unit 0
             v = np.zeros(k, np.int32); v[0] = x
-            h = rne_shift(x, t) if x >= 0 else rne_shift(x, t + 4)
+            h = rhu_shift(x, t) if x >= 0 else rhu_shift(x, t + 4)
             h = max(min(h, 32767), -32767)
             assert O.mlp_pred_q(q, v) == h, (x, t)
 
@@ -148,7 +154,7 @@ def test_input_and_activation_clamps(O):
     v = np.zeros(k, np.int32)
     v[0] = 10 ** 6                  # input clamp 65535, then activation clamp 32767
     assert O.mlp_pred_q(q, v) == 32767
-    v[0] = -10 ** 6                 # -65535 / 16 -> -4095.9375 -> -4096
+    v[0] = -10 ** 6                 # -65535 / 16 = -4095.9375, half up -> -4096
     assert O.mlp_pred_q(q, v) == -4096
 
 
