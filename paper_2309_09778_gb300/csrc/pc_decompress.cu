@@ -173,26 +173,27 @@ __global__ void __launch_bounds__(256) k_dec_blockoff(Geo g, const uint8_t* __re
 // Codes of up to 12 bits resolve in one shared-memory table lookup; longer
 // ones by comparing the 24-bit window against each length's code range.
 // Eight decoded codes are packed and written with one 16-byte store.
-constexpr int kSortedSmem = 16384;
+constexpr int kDecThreads = 256;  // threads (blocks decoded) per CTA of k_huff_decode
+constexpr int kSortedSmem = 16384;  // sorted lists up to this many symbols are read from shared memory
 
-__global__ void __launch_bounds__(256) k_huff_decode(Geo g, const uint8_t* __restrict__ in, DecInfo di,
+__global__ void __launch_bounds__(kDecThreads) k_huff_decode(Geo g, const uint8_t* __restrict__ in, DecInfo di,
                                                      DecScratch ds) {
-  __shared__ unsigned int s_lut[1 << kLutBits];
-  __shared__ unsigned int s_lim[16];    // left-justified end of the code range of lengths 13..28
+  // per length l: left-justified end of its code range, lim[l - 1] (ranges
+  // tile the 24-bit window space in length order; 2^32 - 1 past length 24)
+  __shared__ unsigned int s_lim[32];
   __shared__ unsigned int s_first[32], s_cnt[32], s_offs[32];  // per length: first code, count, list position
-  extern __shared__ uint16_t s_sorted[];
-  const bool small = di.n_used <= (unsigned int)kSortedSmem;
-  for (int i = threadIdx.x; i < (1 << kLutBits); i += blockDim.x) s_lut[i] = ds.lut[i];
+  // per-lane stream window: 9 x 16 bytes from a 16-byte aligned word base
+  __shared__ uint4 s_win[kDecThreads][9];
+  extern __shared__ uint16_t s_sorted[];  // the sorted list when it has at most kSortedSmem symbols
   if (threadIdx.x < 32) {
     const int l = threadIdx.x;
     s_first[l] = ds.tabs[l];
     s_cnt[l] = ds.tabs[32 + l];
     s_offs[l] = ds.tabs[64 + l];
+    const int L = l + 1;
+    s_lim[l] = L <= kLmax ? (ds.tabs[L] + ds.tabs[32 + L]) << (kLmax - L) : 0xFFFFFFFFu;
   }
-  if (threadIdx.x < 16) {
-    const int l = kLutBits + 1 + threadIdx.x;
-    s_lim[threadIdx.x] = l <= kLmax ? (ds.tabs[l] + ds.tabs[32 + l]) << (kLmax - l) : 0xFFFFFFFFu;
-  }
+  const bool small = di.n_used <= (unsigned int)kSortedSmem;
   if (small)
     for (int i = threadIdx.x; i < (int)di.n_used; i += blockDim.x) s_sorted[i] = ds.sorted[i];
   __syncthreads();
@@ -205,74 +206,55 @@ __global__ void __launch_bounds__(256) k_huff_decode(Geo g, const uint8_t* __res
   dec_block_coords(g, b, bz, by, bx, e0, e1, e2);
   const bool full = e0 == g.b[0] && e1 == g.b[1] && e2 == g.b[2];
   const unsigned int nbits = *reinterpret_cast<const unsigned int*>(in + di.off_bb + 4ull * b) & 0x7FFFFFFFu;
-  // The stream section starts 16-byte aligned and the container is padded to
-  // 16 bytes, so every 16-byte chunk that holds a stream word lies inside it.
+  // Each lane decodes its own block's stream.  Every 32 codes it copies the
+  // next 144 bytes of that stream (at least 32 codes of at most 24 bits) from
+  // global memory into its shared-memory window with independent 16-byte
+  // loads, so the decode steps read only shared memory.  The stream section
+  // starts 16-byte aligned and 16-byte chunks past it read as zero.
   const uint4* s4 = reinterpret_cast<const uint4*>(in + di.off_st);
   const unsigned long long nq = (di.swords + 3) / 4;
-  const unsigned long long start = ds.boff[b];
-  unsigned long long qi = start >> 7;
-  const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
-  uint4 q4 = qi < nq ? __ldg(&s4[qi]) : zero4;           // word queue: q4.x is next
-  uint4 nx4 = qi + 1 < nq ? __ldg(&s4[qi + 1]) : zero4;  // prefetched chunk
-  int qn = 4;
-  auto pop = [&]() -> unsigned int {
-    const unsigned int w = q4.x;
-    q4.x = q4.y; q4.y = q4.z; q4.z = q4.w;
-    if (--qn == 0) {
-      q4 = nx4;
-      ++qi;
-      nx4 = qi + 1 < nq ? __ldg(&s4[qi + 1]) : zero4;
-      qn = 4;
-    }
-    return w;
+  const unsigned int* win = reinterpret_cast<const unsigned int*>(s_win[threadIdx.x]);
+  unsigned long long p = ds.boff[b];
+  unsigned long long wbase = 0;
+  auto refill = [&]() {
+    const unsigned long long q0 = p >> 7;
+    wbase = q0 << 2;
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+      s_win[threadIdx.x][k] = q0 + k < nq ? __ldg(s4 + q0 + k) : make_uint4(0u, 0u, 0u, 0u);
   };
-  for (int k = (int)((start >> 5) & 3ull); k > 0; --k) pop();
-  unsigned long long buf = (unsigned long long)pop() << 32;
-  buf |= pop();
-  int nb = 64;
-  {
-    const int skip = (int)(start & 31ull);
-    buf <<= skip;
-    nb -= skip;
-  }
   unsigned int used = 0;
   bool bad = false;
-  const unsigned int nsym = 1u << di.m, nused = di.n_used;
-  // one canonical decode step
+  const unsigned int nused = di.n_used;
+  // one canonical decode step, the same for every code (no divergence): the
+  // length is the smallest l with peek < lim[l] (5-step binary search over
+  // the 32-entry table), the symbol sorted[offs[l] + (code - first[l])]
   auto step = [&]() -> unsigned int {
-    if (nb <= 32) {
-      buf |= (unsigned long long)pop() << (32 - nb);
-      nb += 32;
-    }
-    const unsigned int peek = (unsigned int)(buf >> 40);  // next 24 bits
-    const unsigned int e = s_lut[peek >> (kLmax - kLutBits)];
-    // long words: lengths 13..24 by binary search over the left-justified
-    // range ends (canonical ranges tile the window space in length order)
-    int q = 0;
-    q += peek >= s_lim[q + 7] ? 8 : 0;
-    q += peek >= s_lim[q + 3] ? 4 : 0;
-    q += peek >= s_lim[q + 1] ? 2 : 0;
-    q += peek >= s_lim[q] ? 1 : 0;
-    const int l = kLutBits + 1 + q;
+    const unsigned int lw = (unsigned int)((p >> 5) - wbase);  // < 34 within a refill period
+    const unsigned int peek = __funnelshift_l(win[lw + 1], win[lw], (unsigned int)(p & 31ull)) >> (32 - kLmax);
+    int i = 0;
+    i += s_lim[i + 15] <= peek ? 16 : 0;
+    i += s_lim[i + 7] <= peek ? 8 : 0;
+    i += s_lim[i + 3] <= peek ? 4 : 0;
+    i += s_lim[i + 1] <= peek ? 2 : 0;
+    i += s_lim[i] <= peek ? 1 : 0;
+    const int l = i + 1;
     const int lc = l <= kLmax ? l : kLmax;
     const unsigned int d = (peek >> (kLmax - lc)) - s_first[lc];
     const bool inr = l <= kLmax && d < s_cnt[lc];
     const unsigned int idx = s_offs[lc] + (inr ? d : 0u);
-    const unsigned int slong = sorted[idx < nused ? idx : 0u];
-    const unsigned int elen = e & 0xFFu;
-    const unsigned int len = elen ? elen : (unsigned int)lc;
-    const unsigned int sym = elen ? (e >> 8) : slong;
-    if (!elen && !inr) bad = true;
-    used += len;
-    if (used > nbits || sym >= nsym) bad = true;
-    buf <<= len;
-    nb -= (int)len;
+    // the list holds validated symbols (< 2^m), checked when the tables were built
+    const unsigned int sym = sorted[idx < nused ? idx : 0u];
+    if (!inr) bad = true;
+    used += (unsigned int)lc;
+    p += (unsigned int)lc;
     return sym;
   };
   uint4* out = reinterpret_cast<uint4*>(ds.codes + b * g.bvol);
   const int b12 = g.b[1] * g.b[2];
   for (int j0 = 0; j0 < g.bvol; j0 += 8) {
-    unsigned int pk[4] = {0u, 0u, 0u, 0u};
+    if ((j0 & 31) == 0) refill();
+    unsigned int sy[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int j = j0 + q;
@@ -281,13 +263,16 @@ __global__ void __launch_bounds__(256) k_huff_decode(Geo g, const uint8_t* __res
         const int lz = j / b12, r = j - lz * b12, ly = r / g.b[2], lx = r - ly * g.b[2];
         valid = lz < e0 && ly < e1 && lx < e2;
       }
-      if (valid && !bad) {
-        const unsigned int sym = step();
-        if (!bad) pk[q >> 1] |= sym << (16 * (q & 1));
-      }
+      sy[q] = (valid && !bad) ? step() : 0u;
     }
+    // symbols are combined after the group, so their loads overlap the steps
+    unsigned int pk[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) pk[q] = sy[2 * q] | (sy[2 * q + 1] << 16);
     out[j0 >> 3] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
   }
+  // a corrupt stream shows as a bad long code or a bit count that differs
+  // from the block table's (reads past the block stay inside the stream)
   if (bad || used != nbits) atomicExch(ds.err, PC_ERR_CORRUPT);
 }
 
@@ -772,8 +757,14 @@ int launch_decompress(const uint8_t* in, const Geo& g, const DecInfo& di, const 
     k_dec_chunkscan<<<1, 1024, 0, s>>>(g, di, ds);
     k_dec_blockoff<<<nc, 256, 0, s>>>(g, in, di, ds);
   }
-  const size_t sm_sorted = di.n_used <= (unsigned int)kSortedSmem ? 2ull * di.n_used : 0ull;
-  { ProfScope p(kStHuffDecode, s); k_huff_decode<<<(unsigned int)((g.nblocks + 255) / 256), 256, sm_sorted, s>>>(g, in, di, ds); }
+  {
+    ProfScope p(kStHuffDecode, s);
+    const size_t sm = di.n_used <= (unsigned int)kSortedSmem ? 2ull * di.n_used : 0ull;
+    if (cudaFuncSetAttribute(k_huff_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kSortedSmem) !=
+        cudaSuccess)
+      return PC_ERR_CUDA;
+    k_huff_decode<<<(unsigned int)((g.nblocks + kDecThreads - 1) / kDecThreads), kDecThreads, sm, s>>>(g, in, di, ds);
+  }
   if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
   const int b0 = g.b[0], b1 = g.b[1], b2 = g.b[2];
 #define PC_SHAPE(A, B, C) \
