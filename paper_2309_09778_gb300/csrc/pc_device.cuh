@@ -46,6 +46,11 @@ struct State {
   unsigned int cb_first[32], cb_offs[32];
 };
 
+// Entries of the FP32 weight blob: W1[h1][k], b1[h1], W2[h2][h1], b2[h2], W3[hl], b3.
+__host__ __device__ constexpr int mlp_nweights_c(int k, int h1, int h2) {
+  return h1 * k + h1 + (h2 > 0 ? h2 * h1 + h2 : 0) + (h2 > 0 ? h2 : h1) + 1;
+}
+
 struct Mlp {
   int k, h1, h2, s_in;
   float w[kMaxW];
@@ -337,10 +342,9 @@ __device__ __forceinline__ float2 f2_leaky(float2 v) {
   return make_float2(fmaxf(v.x, m.x), fmaxf(v.y, m.y));
 }
 
-template <int K, int H1, int H2>
-__device__ __forceinline__ void mlp_fwd2(const Mlp& m, const int* va, const int* vb, float sig, float unsig, float& pa,
-                                         float& pb) {
-  auto W = [&](int idx) { return make_float2(m.w[idx], m.w[idx]); };
+template <int K, int H1, int H2, typename WF>
+__device__ __forceinline__ void mlp_fwd2_core(WF W, const int* va, const int* vb, float sig, float unsig, float& pa,
+                                              float& pb) {
   float2 u[K];
 #pragma unroll
   for (int i = 0; i < K; ++i)
@@ -376,6 +380,13 @@ __device__ __forceinline__ void mlp_fwd2(const Mlp& m, const int* va, const int*
   o = __fmul2_rn(o, make_float2(unsig, unsig));
   pa = o.x;
   pb = o.y;
+}
+
+// Weights from the kernel parameters (constant bank).
+template <int K, int H1, int H2>
+__device__ __forceinline__ void mlp_fwd2(const Mlp& m, const int* va, const int* vb, float sig, float unsig, float& pa,
+                                         float& pb) {
+  mlp_fwd2_core<K, H1, H2>([&](int idx) { return make_float2(m.w[idx], m.w[idx]); }, va, vb, sig, unsig, pa, pb);
 }
 
 // Runtime-shaped forward for widths without a compiled instance.
