@@ -144,6 +144,10 @@ def run_reference(args, rank: int):
 # scan stage k_dec_chunksum, k_dec_chunkscan and k_dec_blockoff).
 KERNELS_PER_STAGE = {"codebook": 2, "dec_scan": 3}
 
+# DRAM bytes (read + write) of one launch, from the ncu capture in profiles/k_recon_c2_fp32.md
+# (FP32 form of this workload); valid while that kernel is unchanged.
+TRAFFIC_PER_LAUNCH = {("recon", "fp32"): 55112448 + 44073984}
+
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop (FMA) per cycle.
 SMS, FP32_LANES = 152, 128
 
@@ -392,7 +396,7 @@ def main():
             "bits_per_value_lorenzo_only": 8.0 * lz_size / n,
             "vs_fp32_plain": {"bits_per_value": 32.0, "ratio": 32.0 / bpv, "device_copy_gbs": copy_gbs},
             "roofline": dict(roofline(dom, dom_ms, n, size, nn_pts, fpp, clk.get("sm_max_mhz") or 2070.0, peak,
-                                      peak_kind), traffic=None),
+                                      peak_kind), traffic=TRAFFIC_PER_LAUNCH.get((dom, args.form))),
             "perceptron_blocks": {"fraction": float(nnflag.mean()), "points": nn_pts},
             "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
             "cpu_baseline": cpu,

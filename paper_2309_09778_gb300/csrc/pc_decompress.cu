@@ -742,13 +742,26 @@ static int launch_r_shape(const uint8_t* in, const Geo& g, const DecInfo& di, co
 // The fixed-point network read from the container must lie in its stated
 // ranges (exact tensor-core sums, shifts inside 64 bits).
 __global__ void k_qcheck(DecInfo di, int* err) {
-  if (threadIdx.x == 0 && !qnet_valid(di.qnet, di.stencil, di.h1, di.h2, di.s_in)) atomicExch(err, PC_ERR_CORRUPT);
+  const int n = qnet_len(di.stencil, di.h1, di.h2);
+  bool bad = false;
+  if (threadIdx.x == 0) {
+    // header: shapes, exponents, shifts (qnet_valid stops at the first entry check that fails)
+    const long long* q = di.qnet;
+    bad = q[0] != di.stencil || q[1] != di.h1 || q[2] != di.h2 || q[3] != di.s_in;
+    for (int i = 4; i < 7; ++i) bad |= q[i] < -30 || q[i] > 30;
+    for (int i = 7; i < 9; ++i) bad |= q[i] < 0 || q[i] > 26;
+    const long long F = q[4] + q[5] + q[6] - q[7] - q[8];
+    bad |= F < -20 || F > 62;
+  }
+  for (int i = kQHdr + threadIdx.x; i < n; i += blockDim.x)
+    bad |= !qnet_entry_ok(di.qnet, i, di.stencil, di.h1, di.h2);
+  if (bad) atomicExch(err, PC_ERR_CORRUPT);
 }
 
 template <typename T>
 int launch_decompress(const uint8_t* in, const Geo& g, const DecInfo& di, const DecScratch& ds, const Mlp& mlp,
                       T* out, int nsm, cudaStream_t s) {
-  if (di.qmode) k_qcheck<<<1, 32, 0, s>>>(di, ds.err);
+  if (di.qmode) k_qcheck<<<1, 256, 0, s>>>(di, ds.err);
   { ProfScope p(kStDecTables, s); k_dec_tables<<<1, 1024, 0, s>>>(in, di, ds); }
   const unsigned int nc = (unsigned int)g.nchunks;
   {

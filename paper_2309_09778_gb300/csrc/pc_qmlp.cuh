@@ -63,6 +63,22 @@ __host__ __device__ inline bool qnet_valid(const long long* q, int k, int h1, in
   return li == qnet_len(k, h1, h2);
 }
 
+// Entry i of a network with the given shape is a weight (|W| <= 255) or a
+// bias (|B| <= 2^30); the header entries (i < kQHdr) are checked by qnet_valid.
+__host__ __device__ inline bool qnet_entry_ok(const long long* q, int i, int k, int h1, int h2) {
+  const int rows[3] = {h1, h2 ? h2 : 1, h2 ? 1 : 0};
+  const int cols[3] = {k, h1, h2};
+  int base = kQHdr;
+  for (int l = 0; l < 3; ++l) {
+    const int nw = rows[l] * cols[l];
+    if (i < base + nw) return q[i] >= -255 && q[i] <= 255;
+    base += nw;
+    if (i < base + rows[l]) return q[i] >= -(1ll << 30) && q[i] <= (1ll << 30);
+    base += rows[l];
+  }
+  return true;
+}
+
 // rne(x 2^-s) for integer x: round to nearest, ties to even.
 __device__ __forceinline__ long long rne_shift(long long x, int s) {
   if (s <= 0) return x * (1ll << (-s));
