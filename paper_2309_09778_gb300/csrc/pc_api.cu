@@ -125,7 +125,7 @@ CompLayout comp_layout(const Geo& g, int m) {
 }
 
 struct DecLayout {
-  size_t err, ftab, lens, sorted, lut, tabs, key, cbits, cnout, cboff, cooff, boff, ooff, codes, total;
+  size_t err, ftab, sorted, tabs, key, cbits, cnout, cboff, cooff, boff, ooff, codes, total;
 };
 
 DecLayout dec_layout(const Geo& g, int m) {
@@ -134,9 +134,7 @@ DecLayout dec_layout(const Geo& g, int m) {
   size_t o = 0;
   L.err = o; o = up(o + 16);
   L.ftab = o; o = up(o + sizeof(Tabs));
-  L.lens = o; o = up(o + nsym);
   L.sorted = o; o = up(o + 2 * nsym);
-  L.lut = o; o = up(o + 4 * 4096);
   L.tabs = o; o = up(o + 4 * 96);
   L.key = o; o = up(o + 8 * nsym);
   L.cbits = o; o = up(o + 8 * (size_t)g.nchunks);
@@ -230,7 +228,8 @@ int parse_header(const uint8_t* h, size_t n, Hdr& H, Geo& g) {
     return PC_ERR_CORRUPT;
   }
   const unsigned long long npts = (unsigned long long)H.dims[0] * H.dims[1] * H.dims[2];
-  if (H.n_out > npts || H.swords > (npts * kLmax + 31) / 32 + 1) return PC_ERR_CORRUPT;
+  // every block stores its anchor as its first balance point
+  if (H.n_out > npts || H.n_out < H.nblocks || H.swords > (npts * kLmax + 31) / 32 + 1) return PC_ERR_CORRUPT;
   const unsigned long long ts = H.dtype == PC_F64 ? 8 : 4;
   const unsigned long long ocb = al16(kHdr + (H.pred == 2 ? 8ull : 4ull) * H.nw);
   const unsigned long long obb = al16(ocb + 4ull * H.n_used);
@@ -645,9 +644,7 @@ int pc_decompress(const void* d_in, size_t in_size, void* d_field, size_t field_
   DecScratch ds;
   ds.err = reinterpret_cast<int*>(ws + L.err);
   ds.ftab = reinterpret_cast<Tabs*>(ws + L.ftab);
-  ds.lens = ws + L.lens;
   ds.sorted = reinterpret_cast<uint16_t*>(ws + L.sorted);
-  ds.lut = reinterpret_cast<unsigned int*>(ws + L.lut);
   ds.tabs = reinterpret_cast<unsigned int*>(ws + L.tabs);
   ds.key = reinterpret_cast<unsigned long long*>(ws + L.key);
   ds.chunk_bits = reinterpret_cast<unsigned long long*>(ws + L.cbits);

@@ -590,7 +590,8 @@ static int launch_c(const void* x, const Geo& g, const State* st, const Tabs* ta
   constexpr int BV = B0 * B1 * B2;
   constexpr bool WIDE = MODE != 0 && (K == 13 || K == 0);
   auto kern = k_compress<T, B0, B1, B2, MODE, K, H1, H2>;
-  const size_t sm = compress_smem_bytes<BV, MODE, Pad<B0, B1, B2, WIDE>::PV, K, H1, H2>();
+  constexpr size_t sm = compress_smem_bytes<BV, MODE, Pad<B0, B1, B2, WIDE>::PV, K, H1, H2>();
+  static_assert(sm <= 232448, "shared memory per CTA");
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
     return PC_ERR_CUDA;
   int per_sm = 0;

@@ -3,8 +3,8 @@
 // k_dec_tables rebuilds the canonical decoder from the stored (symbol, length)
 // list and validates it; k_dec_chunksum / k_dec_chunkscan / k_dec_blockoff
 // turn the block table into per-block bit and balance-point offsets;
-// k_huff_decode decodes one block per thread (12-bit first-level table,
-// canonical search for longer words), checking every read against the block's
+// k_huff_decode decodes one block per thread (a branch-free canonical search
+// over the per-length range ends), checking every read against the block's
 // stated bit count; k_recon rebuilds each block along wavefronts of its causal
 // stencil with the same predictor and inverse map as the compressor, then
 // writes the brick with coalesced stores.  A damaged stream sets the error
@@ -14,8 +14,6 @@
 #include "pc_profile.cuh"
 
 namespace pc {
-
-constexpr int kLutBits = 12;
 
 // The stored list is the code order (lengths never decrease along it), so the
 // decoder tables follow from one pass: the symbol at list position p has code
@@ -31,8 +29,6 @@ __global__ void __launch_bounds__(1024) k_dec_tables(const uint8_t* __restrict__
   if (tid == 0) s_bad = 0;
   if (tid < 128) build_tabs_entry(ds.ftab, tid);
   for (int i = tid; i < 2048; i += nt) s_seen[i] = 0u;
-  for (int i = tid; i < nsym; i += nt) ds.lens[i] = 0;
-  for (int i = tid; i < (1 << kLutBits); i += nt) ds.lut[i] = 0;
   __syncthreads();
   const unsigned int* ent = reinterpret_cast<const unsigned int*>(in + di.off_cb);
   for (int p = tid; p < n; p += nt) {
@@ -45,7 +41,6 @@ __global__ void __launch_bounds__(1024) k_dec_tables(const uint8_t* __restrict__
       bad |= (atomicOr(&s_seen[sym >> 5], bit) & bit) != 0u;
     }
     if (bad) { s_bad = 1; continue; }
-    ds.lens[sym] = (uint8_t)len;
     ds.sorted[p] = (uint16_t)sym;
     atomicAdd(&s_cnt[len], 1u);
   }
@@ -64,16 +59,6 @@ __global__ void __launch_bounds__(1024) k_dec_tables(const uint8_t* __restrict__
       if (s_cnt[l] && (unsigned long long)code + s_cnt[l] > (1ull << l)) bad = true;
     }
     if (bad) atomicExch(ds.err, PC_ERR_CORRUPT);
-  }
-  __syncthreads();
-  for (int p = tid; p < n; p += nt) {
-    const unsigned int e = ent[p];
-    const unsigned int l = e >> 16, sym = e & 0xFFFFu;
-    if (l <= (unsigned int)kLutBits) {
-      const unsigned int code = ds.tabs[l] + ((unsigned int)p - ds.tabs[64 + l]);
-      const unsigned int lo = code << (kLutBits - l), hi = (code + 1) << (kLutBits - l);
-      for (unsigned int t = lo; t < hi && t < (1u << kLutBits); ++t) ds.lut[t] = (sym << 8) | l;
-    }
   }
 }
 
@@ -290,8 +275,8 @@ constexpr size_t recon_smem_bytes() {
   if constexpr (MODE == 2)
     q = ((size_t)QShape<K, H1, H2>::NFRAG * 4 + (size_t)QShape<K, H1, H2>::NBIAS * 8 + (size_t)G * BV * 4 + 15) &
         ~(size_t)15;
-  return sizeof(Tabs) + q + (size_t)((G * PV + 3) & ~3) * 4 + (size_t)G * BV * TSZ * 2 + (size_t)G * BV * 2 * 2 +
-         (size_t)BV * 2 + 16;
+  return sizeof(Tabs) + q + (size_t)((G * PV + 3) & ~3) * 4 + (size_t)G * BV * TSZ + (size_t)BV * 4 +
+         (size_t)G * BV * 2 + 16;
 }
 
 template <typename T, int B0, int B1, int B2, int MODE, int K, int H1, int H2>
@@ -319,17 +304,15 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
   __shared__ QSc s_qsc;
   int* s_vp = reinterpret_cast<int*>(smem + sizeof(Tabs) + QBYTES);  // G*PV padded centred codes
   T* s_x = reinterpret_cast<T*>(s_vp + VPR);                        // G*BV
-  T* s_ov = s_x + G * BV;                                           // G*BV balance points of each block
-  uint16_t* s_cd = reinterpret_cast<uint16_t*>(s_ov + G * BV);      // G*BV
-  uint16_t* s_rk = s_cd + G * BV;                                   // G*BV balance-point ranks
-  uint16_t* s_list = s_rk + G * BV;                                 // BV wave order
+  // BV points in wave order, each j | (padded index of j) << 16
+  unsigned int* s_list = reinterpret_cast<unsigned int*>(s_x + G * BV);
+  uint16_t* s_cd = reinterpret_cast<uint16_t*>(s_list + BV);        // G*BV
   __shared__ int s_ws[SZ + 2];
   __shared__ int s_fill[SZ + 2];
   __shared__ unsigned int s_wt[G][NWT];
   __shared__ int s_da[G];
   __shared__ int s_bad;
-  __shared__ int s_usen[G], s_no[G], s_e2[G];
-  __shared__ unsigned long long s_obase[G];
+  __shared__ int s_usen[G], s_e2[G];
 
   State c;
   c.Kp = di.Kp; c.Kn = di.Kn; c.Zq = di.Zq; c.S = di.S;
@@ -362,7 +345,7 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
   for (int j = tid; j < BV; j += 256) {
     const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
     const int sv = s13 ? 4 * lz + 2 * ly + lx : lz + ly + lx;
-    s_list[s_ws[sv] + atomicAdd(&s_fill[sv], 1)] = (uint16_t)j;
+    s_list[s_ws[sv] + atomicAdd(&s_fill[sv], 1)] = (unsigned int)j | ((unsigned int)PD::at(lz, ly, lx) << 16);
   }
   const int nwave = s13 ? SZ : (B0 - 1) + (B1 - 1) + (B2 - 1) + 1;
   __syncthreads();
@@ -378,7 +361,6 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
   int* vp = s_vp + team * PD::PV;
   T* xs = s_x + team * BV;
   uint16_t* cd = s_cd + team * BV;
-  uint16_t* rk = s_rk + team * BV;
   bool bad = false;
   for (long long brick = blockIdx.x; brick < nbricks; brick += gridDim.x) {
     const long long bxg = brick % nbx;
@@ -394,8 +376,7 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
     const int e2 = bvalid ? (int)min((long long)B2, g.n[2] - bx * B2) : 0;
     const bool bfull = e0 == B0 && e1 == B1 && e2 == B2;
     const long long b = (bz * g.nb[1] + by) * g.nb[2] + bx;
-    // codes, padded border for truncated blocks, and balance-point ranks
-    unsigned int run = 0;
+    // codes and the padded border for truncated blocks
     if (bvalid) {
       const uint4* src = reinterpret_cast<const uint4*>(ds.codes + b * BV);
       for (int i = t; i < BV / 8; i += TS) reinterpret_cast<uint4*>(cd)[i] = src[i];
@@ -406,49 +387,23 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
         }
       }
     }
+    const unsigned int no = bvalid ? *reinterpret_cast<const uint16_t*>(in + di.off_bn + 2ull * b) : 1u;
+    const bool usen = bvalid && ((*reinterpret_cast<const unsigned int*>(in + di.off_bb + 4ull * b)) >> 31);
+    const unsigned long long obase = bvalid ? ds.ooff[b] : 0ull;
     if (TS == 32) __syncwarp(); else __syncthreads();
+    // balance points (code 0) per warp segment of the block
     constexpr int SEG = BV / NWT;  // contiguous codes per warp of the team
+    unsigned int run = 0;
     if (bvalid) {
       for (int j0 = wt * SEG; j0 < (wt + 1) * SEG; j0 += 32) {
         const int j = j0 + lane;
         const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
         const bool f = j != 0 && (bfull || (lz < e0 && ly < e1 && lx < e2)) && cd[j] == 0;
-        const unsigned int bal = __ballot_sync(0xFFFFFFFFu, f);
-        rk[j] = (uint16_t)(run + __popc(bal & ((1u << lane) - 1u)));
-        run += __popc(bal);
+        run += __popc(__ballot_sync(0xFFFFFFFFu, f));
       }
       if (NWT > 1 && lane == 0) s_wt[team][wt] = run;
     }
-    __syncthreads();
-    unsigned int nzero = run;
-    if (NWT > 1 && bvalid) {
-      unsigned int base = 0, tot = 0;
-      for (int q = 0; q < NWT; ++q) {
-        if (q < wt) base += s_wt[team][q];
-        tot += s_wt[team][q];
-      }
-      if (base)
-        for (int j0 = wt * SEG; j0 < (wt + 1) * SEG; j0 += 32) rk[j0 + lane] += (uint16_t)base;
-      nzero = tot;
-    }
-    const unsigned int no = bvalid ? *reinterpret_cast<const uint16_t*>(in + di.off_bn + 2ull * b) : 1u;
-    const bool usen = bvalid && ((*reinterpret_cast<const unsigned int*>(in + di.off_bb + 4ull * b)) >> 31);
-    const unsigned long long obase = bvalid ? ds.ooff[b] : 0ull;
-    if (bvalid && (nzero + 1u != no || (usen && !MODE))) bad = true;
-    if (t == 0) {
-      s_usen[team] = usen;
-      s_no[team] = (int)no;
-      s_e2[team] = e2;
-      s_obase[team] = obase;
-    }
-    // the block's balance points (stored contiguously) into shared memory
-    T* ovs = s_ov + team * BV;
-    if (bvalid) {
-      const unsigned long long nv = min((unsigned long long)min(no, (unsigned int)BV),
-                                        obase < di.n_out ? di.n_out - obase : 0ull);
-      for (int r = t; r < (int)nv; r += TS) ovs[r] = ov[obase + r];
-    }
-    // anchor
+    // anchor: the block's first balance point (the container holds n_out >= nblocks of them)
     if (bvalid && t == 0) {
       const T xa = ov[obase < di.n_out ? obase : 0];
       bool okk;
@@ -456,11 +411,51 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
       vp[PD::at(0, 0, 0)] = 0;
       xs[0] = xa;
     }
+    if (t == 0) {
+      s_usen[team] = usen;
+      s_e2[team] = e2;
+    }
+    __syncthreads();
+    unsigned int rank = 0, nzero = run;
+    if (NWT > 1 && bvalid) {
+      unsigned int tot = 0;
+      for (int q = 0; q < NWT; ++q) {
+        if (q < wt) rank += s_wt[team][q];
+        tot += s_wt[team][q];
+      }
+      nzero = tot;
+    }
+    if (bvalid && (nzero + 1u != no || (usen && !MODE))) bad = true;
+    // Every other balance point: its value and centred code go in before the
+    // waves.  Only points of later waves read them.
+    if (bvalid) {
+      const int dab = s_da[team];
+      for (int j0 = wt * SEG; j0 < (wt + 1) * SEG; j0 += 32) {
+        const int j = j0 + lane;
+        const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+        const bool f = j != 0 && (bfull || (lz < e0 && ly < e1 && lx < e2)) && cd[j] == 0;
+        const unsigned int bal = __ballot_sync(0xFFFFFFFFu, f);
+        if (f) {
+          const unsigned int r = 1u + rank + __popc(bal & ((1u << lane) - 1u));
+          unsigned long long oi = obase + r;
+          if (r >= no || oi >= di.n_out) { bad = true; oi = 0; }
+          const T xv = ov[oi];
+          bool okk;
+          const int q = Num<T>::transform(xv, c, tb, okk);
+          xs[j] = xv;
+          vp[PD::at(lz, ly, lx)] = clampv((long long)q - dab);
+        }
+        rank += __popc(bal);
+      }
+    }
     __syncthreads();
     const int da = s_da[team];
+    // Waves of all G blocks at once: wave position f of the CTA is point
+    // f / G of the wave's list in block f % G.
+    const bool brick_full = e0 == B0 && e1 == B1 && W == G * B2;
     if constexpr (MODE == 2) {
-      // Each wave of all G blocks at once, in tiles of 16 points on the tensor
-      // cores; the lanes holding a tile's predictions finish its points.
+      // Each wave in tiles of 16 points on the tensor cores; the lanes holding
+      // a tile's predictions finish its points.
       const int wid = tid >> 5;
       const QSc qsc = s_qsc;
       int qoff[QS::KC1][4], qhi[QS::KC1][4];  // stencil offset; limb 1 hi, 0 lo, 2 padding
@@ -483,16 +478,13 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
           for (int r = 0; r < 2; ++r) {
             const int f = tile * 16 + (lane >> 2) + 8 * r;
             fs[r] = f;
-            const int gb = f < tot ? f / S : 0;
-            const int j = f < tot ? s_list[w0 + f - gb * S] : 0;
-            const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
-            const int pj = PD::at(lz, ly, lx);
-            const int* vpg = s_vp + gb * PD::PV;
+            const int fi = f < tot ? f : 0;
+            const int pj = (fi % G) * PD::PV + (int)(s_list[w0 + fi / G] >> 16);
 #pragma unroll
             for (int kc = 0; kc < QS::KC1; ++kc)
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
-                int v = qhi[kc][e] == 2 ? 0 : vpg[pj + qoff[kc][e]];
+                int v = qhi[kc][e] == 2 ? 0 : s_vp[pj + qoff[kc][e]];
                 v = v > kQIn ? kQIn : (v < -kQIn ? -kQIn : v);
                 lv[r][kc][e] = qlimb(v, qhi[kc][e]);
               }
@@ -507,113 +499,84 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
         __syncthreads();
         // finish the wave's points, one per thread
         for (int f = tid; f < tot; f += 256) {
-          const int gb = f / S;
-          const int j = s_list[w0 + f - gb * S];
-          const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
-          const int e2g = s_e2[gb];
-          const bool fullg = e0 == B0 && e1 == B1 && e2g == B2;
-          if (!(e2g > 0 && (fullg || (lz < e0 && ly < e1 && lx < e2g)))) continue;
-          const int pj = PD::at(lz, ly, lx);
-          const unsigned int code = s_cd[gb * BV + j];
-          int q;
-          if (code == 0) {
-            const unsigned long long ob = s_obase[gb];
-            unsigned int rr = 1u + s_rk[gb * BV + j];
-            if (rr >= (unsigned int)s_no[gb] || ob + rr >= di.n_out) { bad = true; rr = 0; }
-            const T xv = s_ov[gb * BV + rr];
-            bool okk;
-            q = Num<T>::transform(xv, c, tb, okk);
-            s_x[gb * BV + j] = xv;
-          } else {
-            long long prd;
-            if (s_usen[gb]) {
-              prd = s_wpred[f];
-            } else {
-              const int* vpg = s_vp + gb * PD::PV;
-              int acc = 0;
-#pragma unroll
-              for (int si = 0; si < 7; ++si) acc += lz_w(7, si) * vpg[pj + PD::off(s7_dz(si), s7_dy(si), s7_dx(si))];
-              prd = acc;
-            }
-            const long long qq = (long long)s_da[gb] + prd + ((long long)code - R);
-            if (qq > 2147483647LL || qq < -2147483647LL) { bad = true; q = 0; }
-            else q = (int)qq;
-            s_x[gb * BV + j] = Num<T>::recon(q, c, tb);
+          const int gb = f % G;
+          const unsigned int e = s_list[w0 + f / G];
+          const int j = (int)(e & 0xFFFFu), pj = gb * PD::PV + (int)(e >> 16);
+          if (!brick_full) {
+            const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+            if (!(lz < e0 && ly < e1 && lx < s_e2[gb])) continue;
           }
-          s_vp[gb * PD::PV + pj] = clampv((long long)q - s_da[gb]);
+          const unsigned int code = s_cd[gb * BV + j];
+          if (code == 0) continue;  // balance point, already in place
+          long long prd;
+          if (s_usen[gb]) {
+            prd = s_wpred[f];
+          } else {
+            int acc = 0;
+#pragma unroll
+            for (int si = 0; si < 7; ++si) acc += lz_w(7, si) * s_vp[pj + PD::off(s7_dz(si), s7_dy(si), s7_dx(si))];
+            prd = acc;
+          }
+          const int dag = s_da[gb];
+          const long long qq = (long long)dag + prd + ((long long)code - R);
+          int q;
+          if (qq > 2147483647LL || qq < -2147483647LL) { bad = true; q = 0; }
+          else q = (int)qq;
+          s_x[gb * BV + j] = Num<T>::recon(q, c, tb);
+          s_vp[pj] = clampv((long long)q - dag);
         }
         __syncthreads();
       }
     } else if constexpr (MODE != 0 && K > 0) {
-      // Each wave of all G blocks at once, flattened over the CTA, two points
-      // per thread through the packed perceptron forward.
+      // Two wave positions per thread through the packed perceptron forward.
+      // Every neighbour load is unconditional (all indices are inside the
+      // padded blocks), so a point's loads do not wait on its code.
       for (int sw = 1; sw < nwave; ++sw) {
         const int w0 = s_ws[sw], S = s_ws[sw + 1] - w0;
         const int tot = G * S, half = (tot + 1) >> 1;
         for (int pr2 = tid; pr2 < half; pr2 += 256) {
           int inp[2][K];
-          int jj[2], gbs[2], pjs[2];
+          int pjs[2], xis[2], dav[2], lzp[2];
           unsigned int cds[2];
           bool act[2], need[2];
-          long long lzp[2];
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
             const int f = pr2 + u * half;
-            act[u] = false;
-            need[u] = false;
-            lzp[u] = 0;
-            cds[u] = 0;
-            const int gb = f < tot ? f / S : 0;
-            const int j = f < tot ? s_list[w0 + f - gb * S] : 0;
-            const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
-            const int e2g = s_e2[gb];
-            const bool fullg = e0 == B0 && e1 == B1 && e2g == B2;
-            const bool valid = f < tot && e2g > 0 && (fullg || (lz < e0 && ly < e1 && lx < e2g));
-            const int pj = PD::at(lz, ly, lx);
-            const int* vpg = s_vp + gb * PD::PV;
-            jj[u] = j;
-            gbs[u] = gb;
-            pjs[u] = pj;
-            if (valid) {
-              act[u] = true;
-              const unsigned int code = s_cd[gb * BV + j];
-              cds[u] = code;
-              if (code == 0) {
-                const unsigned long long ob = s_obase[gb];
-                unsigned int r = 1u + s_rk[gb * BV + j];
-                if (r >= (unsigned int)s_no[gb] || ob + r >= di.n_out) { bad = true; r = 0; }
-                const T xv = s_ov[gb * BV + r];
-                bool okk;
-                const int q = Num<T>::transform(xv, c, tb, okk);
-                s_x[gb * BV + j] = xv;
-                s_vp[gb * PD::PV + pj] = clampv((long long)q - s_da[gb]);
-                act[u] = false;
-              } else if (s_usen[gb]) {
-                need[u] = true;
-              } else {
-                int acc = 0;
-#pragma unroll
-                for (int si = 0; si < 7; ++si) acc += lz_w(7, si) * vpg[pj + PD::off(s7_dz(si), s7_dy(si), s7_dx(si))];
-                lzp[u] = acc;
-              }
+            const int fi = f < tot ? f : 0;
+            const int gb = fi % G;
+            const unsigned int e = s_list[w0 + fi / G];
+            const int j = (int)(e & 0xFFFFu), pj = gb * PD::PV + (int)(e >> 16);
+            bool valid = f < tot;
+            if (!brick_full) {
+              const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+              valid = valid && lz < e0 && ly < e1 && lx < s_e2[gb];
             }
+            const unsigned int code = s_cd[gb * BV + j];
+            act[u] = valid && code != 0u;   // balance points are already in place
+            need[u] = act[u] && s_usen[gb] != 0;
+            cds[u] = code;
+            pjs[u] = pj;
+            xis[u] = gb * BV + j;
+            dav[u] = s_da[gb];
 #pragma unroll
-            for (int si = 0; si < K; ++si)
-              inp[u][si] = need[u] ? vpg[pj + PD::off(st_dz(K, si), st_dy(K, si), st_dx(K, si))] : 0;
+            for (int si = 0; si < K; ++si) inp[u][si] = s_vp[pj + PD::off(st_dz(K, si), st_dy(K, si), st_dx(K, si))];
+            int acc = 0;
+#pragma unroll
+            for (int si = 0; si < 7; ++si) acc += lz_w(7, si) * s_vp[pj + PD::off(s7_dz(si), s7_dy(si), s7_dx(si))];
+            lzp[u] = acc;
           }
           float pv[2] = {0.0f, 0.0f};
           if (need[0] || need[1]) mlp_fwd2<K, H1, H2>(mlp, inp[0], inp[1], sig, unsig, pv[0], pv[1]);
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
             if (!act[u]) continue;
-            const long long prd = need[u] ? (long long)round_pred(pv[u]) : lzp[u];
-            const int gb = gbs[u];
-            const long long qq = (long long)s_da[gb] + prd + ((long long)cds[u] - R);
+            const long long prd = need[u] ? (long long)round_pred(pv[u]) : (long long)lzp[u];
+            const long long qq = (long long)dav[u] + prd + ((long long)cds[u] - R);
             int q;
             if (qq > 2147483647LL || qq < -2147483647LL) { bad = true; q = 0; }
             else q = (int)qq;
-            s_x[gb * BV + jj[u]] = Num<T>::recon(q, c, tb);
-            s_vp[gb * PD::PV + pjs[u]] = clampv((long long)q - s_da[gb]);
+            s_x[xis[u]] = Num<T>::recon(q, c, tb);
+            s_vp[pjs[u]] = clampv((long long)q - dav[u]);
           }
         }
         __syncthreads();
@@ -622,48 +585,40 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
     for (int sw = 1; sw < nwave; ++sw) {
       if (bvalid) {
         for (int idx = s_ws[sw] + t; idx < s_ws[sw + 1]; idx += TS) {
-          const int j = s_list[idx];
+          const unsigned int e = s_list[idx];
+          const int j = (int)(e & 0xFFFFu), pj = (int)(e >> 16);
           const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
           if (!bfull && !(lz < e0 && ly < e1 && lx < e2)) continue;
-          const int pj = PD::at(lz, ly, lx);
           const unsigned int code = cd[j];
-          int q;
-          if (code == 0) {
-            unsigned int r = 1u + rk[j];
-            if (r >= no || obase + r >= di.n_out) { bad = true; r = 0; }
-            const T xv = ovs[r];
-            bool okk;
-            q = Num<T>::transform(xv, c, tb, okk);
-            xs[j] = xv;
-          } else {
-            long long pr = 0;
-            bool done = false;
-            if constexpr (MODE != 0) {
-              if (usen) {
-                constexpr int KK = K > 0 ? K : 13;
-                int inp[KK];
-                const int kk = K > 0 ? K : mlp.k;
+          if (code == 0) continue;  // balance point, already in place
+          long long pr = 0;
+          bool done = false;
+          if constexpr (MODE != 0) {
+            if (usen) {
+              constexpr int KK = K > 0 ? K : 13;
+              int inp[KK];
+              const int kk = K > 0 ? K : mlp.k;
 #pragma unroll
-                for (int si = 0; si < KK; ++si)
-                  inp[si] = si < kk ? vp[pj + PD::off(st_dz(kk, si), st_dy(kk, si), st_dx(kk, si))] : 0;
-                float p;
-                if constexpr (K > 0) p = mlp_fwd<K, H1, H2>(mlp, inp, sig, unsig);
-                else p = mlp_fwd_rt(mlp, inp, sig, unsig);
-                pr = round_pred(p);
-                done = true;
-              }
+              for (int si = 0; si < KK; ++si)
+                inp[si] = si < kk ? vp[pj + PD::off(st_dz(kk, si), st_dy(kk, si), st_dx(kk, si))] : 0;
+              float p;
+              if constexpr (K > 0) p = mlp_fwd<K, H1, H2>(mlp, inp, sig, unsig);
+              else p = mlp_fwd_rt(mlp, inp, sig, unsig);
+              pr = round_pred(p);
+              done = true;
             }
-            if (!done) {
-              int acc = 0;
-#pragma unroll
-              for (int si = 0; si < 7; ++si) acc += lz_w(7, si) * vp[pj + PD::off(s7_dz(si), s7_dy(si), s7_dx(si))];
-              pr = acc;
-            }
-            const long long qq = (long long)da + pr + ((long long)code - R);
-            if (qq > 2147483647LL || qq < -2147483647LL) { bad = true; q = 0; }
-            else q = (int)qq;
-            xs[j] = Num<T>::recon(q, c, tb);
           }
+          if (!done) {
+            int acc = 0;
+#pragma unroll
+            for (int si = 0; si < 7; ++si) acc += lz_w(7, si) * vp[pj + PD::off(s7_dz(si), s7_dy(si), s7_dx(si))];
+            pr = acc;
+          }
+          const long long qq = (long long)da + pr + ((long long)code - R);
+          int q;
+          if (qq > 2147483647LL || qq < -2147483647LL) { bad = true; q = 0; }
+          else q = (int)qq;
+          xs[j] = Num<T>::recon(q, c, tb);
           vp[pj] = clampv((long long)q - da);
         }
       }
@@ -706,7 +661,8 @@ static int launch_r(const uint8_t* in, const Geo& g, const DecInfo& di, const De
   constexpr int BV = B0 * B1 * B2;
   constexpr bool WIDE = MODE != 0 && (K == 13 || K == 0);
   auto kern = k_recon<T, B0, B1, B2, MODE, K, H1, H2>;
-  const size_t sm = recon_smem_bytes<BV, Pad<B0, B1, B2, WIDE>::PV, (int)sizeof(T), MODE, K, H1, H2>();
+  constexpr size_t sm = recon_smem_bytes<BV, Pad<B0, B1, B2, WIDE>::PV, (int)sizeof(T), MODE, K, H1, H2>();
+  static_assert(sm <= 232448, "shared memory per CTA");
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
     return PC_ERR_CUDA;
   int per_sm = 0;

@@ -24,18 +24,22 @@ struct BrickShape {
   static constexpr int PPT = (BV + TS - 1) / TS;
 };
 
+// Block with a zero border: stencil neighbours outside the block read 0
+// without bounds checks.  WIDE adds the +1 border in y and x that the
+// 13-point stencil reaches.  The pitches keep one spare row and column beyond
+// the border: with pitches B + 1 (B + 2 when WIDE) the points of one
+// reconstruction wavefront (the plane z + y + x = s or 4z + 2y + x = s) fall
+// on a few shared-memory banks (8-way conflicts for 8^3 blocks); the extra
+// pitch spreads them over all 32.
 template <int B0, int B1, int B2, bool WIDE>
 struct Pad {
-  static constexpr int P1 = B1 + (WIDE ? 2 : 1);
-  static constexpr int P2 = B2 + (WIDE ? 2 : 1);
+  static constexpr int P1 = B1 + (WIDE ? 3 : 2);
+  static constexpr int P2 = B2 + (WIDE ? 3 : 2);
   static constexpr int PV = (B0 + 1) * P1 * P2;
   static __device__ __forceinline__ int at(int lz, int ly, int lx) { return ((lz + 1) * P1 + (ly + 1)) * P2 + (lx + 1); }
   static constexpr int off(int dz, int dy, int dx) { return (dz * P1 + dy) * P2 + dx; }
 };
 
-// Block with a zero border: stencil neighbours outside the block read 0
-// without bounds checks.  WIDE adds the +1 border in y and x that the
-// 13-point stencil reaches.
 template <int TS>
 __device__ __forceinline__ int team_sum(int v, int* slot) {
   if constexpr (TS == 32) {
@@ -131,9 +135,7 @@ struct DecInfo {
   unsigned long long step_bits, inv_bits, ebdn_bits;
 };
 struct DecScratch {
-  uint8_t* lens;               // [2^m]
   uint16_t* sorted;            // [2^m] symbols in canonical (length, symbol) order
-  unsigned int* lut;           // [4096] 12-bit first-level decode table
   unsigned int* tabs;          // [3 * 32]: first code, count, offset per length
   unsigned long long* key;     // [np2] sort scratch
   unsigned long long* chunk_bits;
