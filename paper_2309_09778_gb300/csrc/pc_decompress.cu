@@ -268,15 +268,43 @@ __global__ void __launch_bounds__(kDecThreads) k_huff_decode(Geo g, const uint8_
 // bricks (as in compression) in zero-bordered padded arrays, and the brick is
 // written back with coalesced (16-byte where rows allow) stores.
 // ---------------------------------------------------------------------------
-template <int BV, int PV, int TSZ, int MODE, int K, int H1, int H2>
+// Blocks rebuilt together by one CTA.  The perceptron paths flatten every
+// wave over all of them, so single-precision bricks of up to 512-point blocks
+// take two groups of G (16 blocks, two CTAs per SM still fit): narrow waves
+// are latency-bound, and more blocks per wave spread that latency over more
+// points.
+template <int BV, int TSZ, int MODE, int K>
+constexpr int recon_blocks() {
+  return BrickShape<BV>::G * ((MODE != 0 && K > 0 && BV <= 512 && TSZ == 4) ? 2 : 1);
+}
+
+// Largest wavefront of a block under either schedule (z + y + x, 4z + 2y + x).
+template <int B0, int B1, int B2>
+constexpr int max_wave() {
+  int best = 0;
+  for (int s13 = 0; s13 < 2; ++s13)
+    for (int sv = 0; sv <= 4 * (B0 - 1) + 2 * (B1 - 1) + (B2 - 1); ++sv) {
+      int n = 0;
+      for (int z = 0; z < B0; ++z)
+        for (int y = 0; y < B1; ++y) {
+          const int x = sv - (s13 ? 4 * z + 2 * y : z + y);
+          n += x >= 0 && x < B2;
+        }
+      best = n > best ? n : best;
+    }
+  return best;
+}
+
+template <int B0, int B1, int B2, int PV, int TSZ, int MODE, int K, int H1, int H2>
 constexpr size_t recon_smem_bytes() {
-  constexpr int G = BrickShape<BV>::G;
+  constexpr int BV = B0 * B1 * B2;
+  constexpr int GR = recon_blocks<BV, TSZ, MODE, K>();
   size_t q = 0;
   if constexpr (MODE == 2)
-    q = ((size_t)QShape<K, H1, H2>::NFRAG * 4 + (size_t)QShape<K, H1, H2>::NBIAS * 8 + (size_t)G * BV * 4 + 15) &
-        ~(size_t)15;
-  return sizeof(Tabs) + q + (size_t)((G * PV + 3) & ~3) * 4 + (size_t)G * BV * TSZ + (size_t)BV * 4 +
-         (size_t)G * BV * 2 + 16;
+    q = ((size_t)QShape<K, H1, H2>::NFRAG * 4 + (size_t)QShape<K, H1, H2>::NBIAS * 8 +
+         (size_t)GR * max_wave<B0, B1, B2>() * 4 + 15) & ~(size_t)15;
+  return sizeof(Tabs) + q + (size_t)((GR * PV + 3) & ~3) * 4 + (size_t)GR * BV * TSZ + (size_t)BV * 4 +
+         (size_t)GR * BV * 2 + 16;
 }
 
 template <typename T, int B0, int B1, int B2, int MODE, int K, int H1, int H2>
@@ -285,34 +313,37 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
   constexpr int BV = B0 * B1 * B2;
   using BS = BrickShape<BV>;
   constexpr int G = BS::G, TS = BS::TS, NWT = TS / 32;
+  constexpr int GR = recon_blocks<BV, (int)sizeof(T), MODE, K>(), NSUB = GR / G;  // blocks per brick, team groups
   constexpr bool WIDE = MODE != 0 && (K == 13 || K == 0);
   using PD = Pad<B0, B1, B2, WIDE>;
-  constexpr int VPR = (G * PD::PV + 3) & ~3;
+  constexpr int VPR = (GR * PD::PV + 3) & ~3;
   constexpr int SZ = (B0 - 1) * 4 + (B1 - 1) * 2 + (B2 - 1) + 1;  // waves of the wider schedule
   constexpr int VW = 16 / (int)sizeof(T);
-  constexpr bool VEC_OK = (B2 * G) % VW == 0;
+  constexpr bool VEC_OK = (B2 * GR) % VW == 0;
   extern __shared__ __align__(16) unsigned char smem[];
   Tabs& tb = *reinterpret_cast<Tabs*>(smem);
   constexpr int QK = MODE == 2 ? K : 7, QH1 = MODE == 2 ? H1 : 16, QH2 = MODE == 2 ? H2 : 16;
   using QS = QShape<QK, QH1, QH2>;
   // whole 16-byte units, so that the arrays after it keep their 16-byte alignment
   constexpr size_t QBYTES =
-      MODE == 2 ? (((size_t)QS::NFRAG * 4 + (size_t)QS::NBIAS * 8 + (size_t)G * BV * 4 + 15) & ~(size_t)15) : 0;
+      MODE == 2 ? (((size_t)QS::NFRAG * 4 + (size_t)QS::NBIAS * 8 + (size_t)GR * max_wave<B0, B1, B2>() * 4 + 15) &
+                   ~(size_t)15)
+                : 0;
   uint32_t* s_frag = reinterpret_cast<uint32_t*>(smem + sizeof(Tabs));   // fixed-point form only
   long long* s_qbias = reinterpret_cast<long long*>(s_frag + (MODE == 2 ? QS::NFRAG : 0));
   int* s_wpred = reinterpret_cast<int*>(s_qbias + (MODE == 2 ? QS::NBIAS : 0));  // one wave's predictions
   __shared__ QSc s_qsc;
-  int* s_vp = reinterpret_cast<int*>(smem + sizeof(Tabs) + QBYTES);  // G*PV padded centred codes
-  T* s_x = reinterpret_cast<T*>(s_vp + VPR);                        // G*BV
+  int* s_vp = reinterpret_cast<int*>(smem + sizeof(Tabs) + QBYTES);  // GR*PV padded centred codes
+  T* s_x = reinterpret_cast<T*>(s_vp + VPR);                        // GR*BV
   // BV points in wave order, each j | (padded index of j) << 16
-  unsigned int* s_list = reinterpret_cast<unsigned int*>(s_x + G * BV);
-  uint16_t* s_cd = reinterpret_cast<uint16_t*>(s_list + BV);        // G*BV
+  unsigned int* s_list = reinterpret_cast<unsigned int*>(s_x + GR * BV);
+  uint16_t* s_cd = reinterpret_cast<uint16_t*>(s_list + BV);        // GR*BV
   __shared__ int s_ws[SZ + 2];
   __shared__ int s_fill[SZ + 2];
   __shared__ unsigned int s_wt[G][NWT];
-  __shared__ int s_da[G];
+  __shared__ int s_da[GR];
   __shared__ int s_bad;
-  __shared__ int s_usen[G], s_e2[G];
+  __shared__ int s_usen[GR], s_e2[GR];
 
   State c;
   c.Kp = di.Kp; c.Kn = di.Kn; c.Zq = di.Zq; c.S = di.S;
@@ -355,104 +386,114 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
   const float unsig = MODE ? __uint_as_float((unsigned int)(127 + mlp.s_in) << 23) : 1.0f;
   const T* ov = reinterpret_cast<const T*>(in + di.off_ov);
   const bool vec_rows = VEC_OK && (g.n[2] % VW == 0) && ((reinterpret_cast<uintptr_t>(xo) & 15u) == 0);
-  const long long nbx = (g.nb[2] + G - 1) / G;
+  const long long nbx = (g.nb[2] + GR - 1) / GR;
   const long long nbricks = g.nb[0] * g.nb[1] * nbx;
   const int team = tid / TS, t = tid % TS, wt = t >> 5;
-  int* vp = s_vp + team * PD::PV;
-  T* xs = s_x + team * BV;
-  uint16_t* cd = s_cd + team * BV;
   bool bad = false;
   for (long long brick = blockIdx.x; brick < nbricks; brick += gridDim.x) {
     const long long bxg = brick % nbx;
     const long long byz = brick / nbx;
     const long long by = byz % g.nb[1];
     const long long bz = byz / g.nb[1];
-    const long long z0 = bz * B0, y0 = by * B1, x0 = bxg * G * B2;
+    const long long z0 = bz * B0, y0 = by * B1, x0 = bxg * GR * B2;
     const int e0 = (int)min((long long)B0, g.n[0] - z0);
     const int e1 = (int)min((long long)B1, g.n[1] - y0);
-    const int W = (int)min((long long)(G * B2), g.n[2] - x0);
-    const long long bx = bxg * G + team;
-    const bool bvalid = bx < g.nb[2];
-    const int e2 = bvalid ? (int)min((long long)B2, g.n[2] - bx * B2) : 0;
-    const bool bfull = e0 == B0 && e1 == B1 && e2 == B2;
-    const long long b = (bz * g.nb[1] + by) * g.nb[2] + bx;
-    // codes and the padded border for truncated blocks
-    if (bvalid) {
-      const uint4* src = reinterpret_cast<const uint4*>(ds.codes + b * BV);
-      for (int i = t; i < BV / 8; i += TS) reinterpret_cast<uint4*>(cd)[i] = src[i];
-      if (!bfull) {
-        for (int j = t; j < BV; j += TS) {
+    const int W = (int)min((long long)(GR * B2), g.n[2] - x0);
+    // Each team sets up block team, team + G, ...; the per-team wave path
+    // (one group) keeps its block's state below.
+    bool bvalid = false, bfull = false, usen = false;
+    int e2 = 0;
+    int* vp = s_vp;
+    T* xs = s_x;
+    uint16_t* cd = s_cd;
+    for (int sub = 0; sub < NSUB; ++sub) {
+      const int blk = sub * G + team;
+      const long long bx = bxg * GR + blk;
+      bvalid = bx < g.nb[2];
+      e2 = bvalid ? (int)min((long long)B2, g.n[2] - bx * B2) : 0;
+      bfull = e0 == B0 && e1 == B1 && e2 == B2;
+      const long long b = (bz * g.nb[1] + by) * g.nb[2] + bx;
+      vp = s_vp + blk * PD::PV;
+      xs = s_x + blk * BV;
+      cd = s_cd + blk * BV;
+      // codes and the padded border for truncated blocks
+      if (bvalid) {
+        const uint4* src = reinterpret_cast<const uint4*>(ds.codes + b * BV);
+        for (int i = t; i < BV / 8; i += TS) reinterpret_cast<uint4*>(cd)[i] = src[i];
+        if (!bfull) {
+          for (int j = t; j < BV; j += TS) {
+            const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+            if (!(lz < e0 && ly < e1 && lx < e2)) vp[PD::at(lz, ly, lx)] = 0;
+          }
+        }
+      }
+      const unsigned int no = bvalid ? *reinterpret_cast<const uint16_t*>(in + di.off_bn + 2ull * b) : 1u;
+      usen = bvalid && ((*reinterpret_cast<const unsigned int*>(in + di.off_bb + 4ull * b)) >> 31);
+      const unsigned long long obase = bvalid ? ds.ooff[b] : 0ull;
+      if (TS == 32) __syncwarp(); else __syncthreads();
+      // balance points (code 0) per warp segment of the block
+      constexpr int SEG = BV / NWT;  // contiguous codes per warp of the team
+      unsigned int run = 0;
+      if (bvalid) {
+        for (int j0 = wt * SEG; j0 < (wt + 1) * SEG; j0 += 32) {
+          const int j = j0 + lane;
           const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
-          if (!(lz < e0 && ly < e1 && lx < e2)) vp[PD::at(lz, ly, lx)] = 0;
+          const bool f = j != 0 && (bfull || (lz < e0 && ly < e1 && lx < e2)) && cd[j] == 0;
+          run += __popc(__ballot_sync(0xFFFFFFFFu, f));
+        }
+        if (NWT > 1 && lane == 0) s_wt[team][wt] = run;
+      }
+      // anchor: the block's first balance point (the container holds n_out >= nblocks of them)
+      if (bvalid && t == 0) {
+        const T xa = ov[obase < di.n_out ? obase : 0];
+        bool okk;
+        s_da[blk] = Num<T>::transform(xa, c, tb, okk);
+        vp[PD::at(0, 0, 0)] = 0;
+        xs[0] = xa;
+      }
+      if (t == 0) {
+        s_usen[blk] = usen;
+        s_e2[blk] = e2;
+      }
+      __syncthreads();
+      unsigned int rank = 0, nzero = run;
+      if (NWT > 1 && bvalid) {
+        unsigned int tot = 0;
+        for (int q = 0; q < NWT; ++q) {
+          if (q < wt) rank += s_wt[team][q];
+          tot += s_wt[team][q];
+        }
+        nzero = tot;
+      }
+      if (bvalid && (nzero + 1u != no || (usen && !MODE))) bad = true;
+      // Every other balance point: its value and centred code go in before the
+      // waves.  Only points of later waves read them.
+      if (bvalid) {
+        const int dab = s_da[blk];
+        for (int j0 = wt * SEG; j0 < (wt + 1) * SEG; j0 += 32) {
+          const int j = j0 + lane;
+          const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+          const bool f = j != 0 && (bfull || (lz < e0 && ly < e1 && lx < e2)) && cd[j] == 0;
+          const unsigned int bal = __ballot_sync(0xFFFFFFFFu, f);
+          if (f) {
+            const unsigned int r = 1u + rank + __popc(bal & ((1u << lane) - 1u));
+            unsigned long long oi = obase + r;
+            if (r >= no || oi >= di.n_out) { bad = true; oi = 0; }
+            const T xv = ov[oi];
+            bool okk;
+            const int q = Num<T>::transform(xv, c, tb, okk);
+            xs[j] = xv;
+            vp[PD::at(lz, ly, lx)] = clampv((long long)q - dab);
+          }
+          rank += __popc(bal);
         }
       }
+      __syncthreads();
     }
-    const unsigned int no = bvalid ? *reinterpret_cast<const uint16_t*>(in + di.off_bn + 2ull * b) : 1u;
-    const bool usen = bvalid && ((*reinterpret_cast<const unsigned int*>(in + di.off_bb + 4ull * b)) >> 31);
-    const unsigned long long obase = bvalid ? ds.ooff[b] : 0ull;
-    if (TS == 32) __syncwarp(); else __syncthreads();
-    // balance points (code 0) per warp segment of the block
-    constexpr int SEG = BV / NWT;  // contiguous codes per warp of the team
-    unsigned int run = 0;
-    if (bvalid) {
-      for (int j0 = wt * SEG; j0 < (wt + 1) * SEG; j0 += 32) {
-        const int j = j0 + lane;
-        const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
-        const bool f = j != 0 && (bfull || (lz < e0 && ly < e1 && lx < e2)) && cd[j] == 0;
-        run += __popc(__ballot_sync(0xFFFFFFFFu, f));
-      }
-      if (NWT > 1 && lane == 0) s_wt[team][wt] = run;
-    }
-    // anchor: the block's first balance point (the container holds n_out >= nblocks of them)
-    if (bvalid && t == 0) {
-      const T xa = ov[obase < di.n_out ? obase : 0];
-      bool okk;
-      s_da[team] = Num<T>::transform(xa, c, tb, okk);
-      vp[PD::at(0, 0, 0)] = 0;
-      xs[0] = xa;
-    }
-    if (t == 0) {
-      s_usen[team] = usen;
-      s_e2[team] = e2;
-    }
-    __syncthreads();
-    unsigned int rank = 0, nzero = run;
-    if (NWT > 1 && bvalid) {
-      unsigned int tot = 0;
-      for (int q = 0; q < NWT; ++q) {
-        if (q < wt) rank += s_wt[team][q];
-        tot += s_wt[team][q];
-      }
-      nzero = tot;
-    }
-    if (bvalid && (nzero + 1u != no || (usen && !MODE))) bad = true;
-    // Every other balance point: its value and centred code go in before the
-    // waves.  Only points of later waves read them.
-    if (bvalid) {
-      const int dab = s_da[team];
-      for (int j0 = wt * SEG; j0 < (wt + 1) * SEG; j0 += 32) {
-        const int j = j0 + lane;
-        const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
-        const bool f = j != 0 && (bfull || (lz < e0 && ly < e1 && lx < e2)) && cd[j] == 0;
-        const unsigned int bal = __ballot_sync(0xFFFFFFFFu, f);
-        if (f) {
-          const unsigned int r = 1u + rank + __popc(bal & ((1u << lane) - 1u));
-          unsigned long long oi = obase + r;
-          if (r >= no || oi >= di.n_out) { bad = true; oi = 0; }
-          const T xv = ov[oi];
-          bool okk;
-          const int q = Num<T>::transform(xv, c, tb, okk);
-          xs[j] = xv;
-          vp[PD::at(lz, ly, lx)] = clampv((long long)q - dab);
-        }
-        rank += __popc(bal);
-      }
-    }
-    __syncthreads();
-    const int da = s_da[team];
-    // Waves of all G blocks at once: wave position f of the CTA is point
-    // f / G of the wave's list in block f % G.
-    const bool brick_full = e0 == B0 && e1 == B1 && W == G * B2;
+    const int da = s_da[team];  // the per-team path has one group: blk == team
+    // Waves of all GR blocks at once: wave position f of the CTA is point
+    // f / GR of the wave's list in block f % GR.
+    const bool brick_full = e0 == B0 && e1 == B1 && W == GR * B2;
     if constexpr (MODE == 2) {
       // Each wave in tiles of 16 points on the tensor cores; the lanes holding
       // a tile's predictions finish its points.
@@ -470,7 +511,7 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
         }
       for (int sw = 1; sw < nwave; ++sw) {
         const int w0 = s_ws[sw], S = s_ws[sw + 1] - w0;
-        const int tot = G * S;
+        const int tot = GR * S;
         for (int tile = wid; tile * 16 < tot; tile += 8) {
           int lv[2][QS::KC1][4];
           int fs[2];
@@ -479,7 +520,7 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
             const int f = tile * 16 + (lane >> 2) + 8 * r;
             fs[r] = f;
             const int fi = f < tot ? f : 0;
-            const int pj = (fi % G) * PD::PV + (int)(s_list[w0 + fi / G] >> 16);
+            const int pj = (fi % GR) * PD::PV + (int)(s_list[w0 + fi / GR] >> 16);
 #pragma unroll
             for (int kc = 0; kc < QS::KC1; ++kc)
 #pragma unroll
@@ -499,8 +540,8 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
         __syncthreads();
         // finish the wave's points, one per thread
         for (int f = tid; f < tot; f += 256) {
-          const int gb = f % G;
-          const unsigned int e = s_list[w0 + f / G];
+          const int gb = f % GR;
+          const unsigned int e = s_list[w0 + f / GR];
           const int j = (int)(e & 0xFFFFu), pj = gb * PD::PV + (int)(e >> 16);
           if (!brick_full) {
             const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
@@ -533,7 +574,7 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
       // padded blocks), so a point's loads do not wait on its code.
       for (int sw = 1; sw < nwave; ++sw) {
         const int w0 = s_ws[sw], S = s_ws[sw + 1] - w0;
-        const int tot = G * S, half = (tot + 1) >> 1;
+        const int tot = GR * S, half = (tot + 1) >> 1;
         for (int pr2 = tid; pr2 < half; pr2 += 256) {
           int inp[2][K];
           int pjs[2], xis[2], dav[2], lzp[2];
@@ -543,8 +584,8 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
           for (int u = 0; u < 2; ++u) {
             const int f = pr2 + u * half;
             const int fi = f < tot ? f : 0;
-            const int gb = fi % G;
-            const unsigned int e = s_list[w0 + fi / G];
+            const int gb = fi % GR;
+            const unsigned int e = s_list[w0 + fi / GR];
             const int j = (int)(e & 0xFFFFu), pj = gb * PD::PV + (int)(e >> 16);
             bool valid = f < tot;
             if (!brick_full) {
@@ -626,8 +667,8 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
     }
     __syncthreads();
     // coalesced brick store
-    if (e0 == B0 && e1 == B1 && W == G * B2 && vec_rows) {
-      constexpr int RW = G * B2 / VW;
+    if (e0 == B0 && e1 == B1 && W == GR * B2 && vec_rows) {
+      constexpr int RW = GR * B2 / VW;
       for (int e = tid; e < B0 * B1 * RW; e += 256) {
         const int r = e / RW, cv = e % RW;
         const int z = r / B1, y = r % B1;
@@ -661,15 +702,15 @@ static int launch_r(const uint8_t* in, const Geo& g, const DecInfo& di, const De
   constexpr int BV = B0 * B1 * B2;
   constexpr bool WIDE = MODE != 0 && (K == 13 || K == 0);
   auto kern = k_recon<T, B0, B1, B2, MODE, K, H1, H2>;
-  constexpr size_t sm = recon_smem_bytes<BV, Pad<B0, B1, B2, WIDE>::PV, (int)sizeof(T), MODE, K, H1, H2>();
+  constexpr size_t sm = recon_smem_bytes<B0, B1, B2, Pad<B0, B1, B2, WIDE>::PV, (int)sizeof(T), MODE, K, H1, H2>();
   static_assert(sm <= 232448, "shared memory per CTA");
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
     return PC_ERR_CUDA;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm);
   if (per_sm < 1) per_sm = 1;
-  constexpr int G = BrickShape<BV>::G;
-  const long long nbricks = g.nb[0] * g.nb[1] * ((g.nb[2] + G - 1) / G);
+  constexpr int GR = recon_blocks<BV, (int)sizeof(T), MODE, K>();
+  const long long nbricks = g.nb[0] * g.nb[1] * ((g.nb[2] + GR - 1) / GR);
   long long grid = (long long)nsm * per_sm;
   if (grid > nbricks) grid = nbricks;
   if (grid < 1) grid = 1;
