@@ -268,14 +268,14 @@ __global__ void __launch_bounds__(kDecThreads) k_huff_decode(Geo g, const uint8_
 // bricks (as in compression) in zero-bordered padded arrays, and the brick is
 // written back with coalesced (16-byte where rows allow) stores.
 // ---------------------------------------------------------------------------
-// Blocks rebuilt together by one CTA.  The perceptron paths flatten every
-// wave over all of them, so single-precision bricks of up to 512-point blocks
-// take two groups of G (16 blocks, two CTAs per SM still fit): narrow waves
-// are latency-bound, and more blocks per wave spread that latency over more
-// points.
+// Blocks rebuilt together by one CTA.  The FP32 perceptron path flattens
+// every wave over all of them, so its single-precision bricks of up to
+// 512-point blocks take two groups of G (16 blocks, two CTAs per SM still
+// fit): narrow waves are latency-bound, and more blocks per wave spread that
+// latency over more points.
 template <int BV, int TSZ, int MODE, int K>
 constexpr int recon_blocks() {
-  return BrickShape<BV>::G * ((MODE != 0 && K > 0 && BV <= 512 && TSZ == 4) ? 2 : 1);
+  return BrickShape<BV>::G * ((MODE == 1 && K > 0 && BV <= 512 && TSZ == 4) ? 2 : 1);
 }
 
 // Largest wavefront of a block under either schedule (z + y + x, 4z + 2y + x).
@@ -608,17 +608,25 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
           }
           float pv[2] = {0.0f, 0.0f};
           if (need[0] || need[1]) mlp_fwd2<K, H1, H2>(mlp, inp[0], inp[1], sig, unsig, pv[0], pv[1]);
+          // both positions finish without branches, so their chains overlap
+          int qv[2];
+          T xr[2];
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
-            if (!act[u]) continue;
             const long long prd = need[u] ? (long long)round_pred(pv[u]) : (long long)lzp[u];
             const long long qq = (long long)dav[u] + prd + ((long long)cds[u] - R);
-            int q;
-            if (qq > 2147483647LL || qq < -2147483647LL) { bad = true; q = 0; }
-            else q = (int)qq;
-            s_x[xis[u]] = Num<T>::recon(q, c, tb);
-            s_vp[pjs[u]] = clampv((long long)q - dav[u]);
+            const bool ovf = qq > 2147483647LL || qq < -2147483647LL;
+            bad |= act[u] && ovf;
+            qv[u] = ovf ? 0 : (int)qq;
           }
+#pragma unroll
+          for (int u = 0; u < 2; ++u) xr[u] = Num<T>::recon(qv[u], c, tb);
+#pragma unroll
+          for (int u = 0; u < 2; ++u)
+            if (act[u]) {
+              s_x[xis[u]] = xr[u];
+              s_vp[pjs[u]] = clampv((long long)qv[u] - dav[u]);
+            }
         }
         __syncthreads();
       }
