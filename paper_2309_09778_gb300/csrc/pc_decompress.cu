@@ -155,85 +155,100 @@ __global__ void __launch_bounds__(256) k_dec_blockoff(Geo g, const uint8_t* __re
 }
 
 // One thread per block: canonical Huffman decode into block-strided codes.
-// Codes of up to 12 bits resolve in one shared-memory table lookup; longer
-// ones by comparing the 24-bit window against each length's code range.
-// Eight decoded codes are packed and written with one 16-byte store.
-constexpr int kDecThreads = 256;  // threads (blocks decoded) per CTA of k_huff_decode
-constexpr int kSortedSmem = 16384;  // sorted lists up to this many symbols are read from shared memory
+// The output is each code's position in the canonical list (symbols sorted by
+// (length, symbol)); the reconstruction maps positions to symbols when it
+// stages a block.  Eight positions are packed and written with one 16-byte
+// store.
+constexpr int kDecThreads = 128;  // threads (blocks decoded) per CTA of k_huff_decode
+constexpr int kShortBits = 12;    // codes up to this long take their length from a table
 
 __global__ void __launch_bounds__(kDecThreads) k_huff_decode(Geo g, const uint8_t* __restrict__ in, DecInfo di,
                                                      DecScratch ds) {
-  // per length l: left-justified end of its code range, lim[l - 1] (ranges
-  // tile the 24-bit window space in length order; 2^32 - 1 past length 24)
+  // per length l: left-justified end of its code range (the ranges tile the
+  // 24-bit window space in length order) and list position minus first code
   __shared__ unsigned int s_lim[32];
-  __shared__ unsigned int s_first[32], s_cnt[32], s_offs[32];  // per length: first code, count, list position
+  __shared__ unsigned int s_base[32];
+  // length of the code a 12-bit window prefix starts, 0 for longer codes
+  __shared__ uint8_t s_len[1 << kShortBits];
   // per-lane stream window: 9 x 16 bytes from a 16-byte aligned word base
-  __shared__ uint4 s_win[kDecThreads][9];
-  extern __shared__ uint16_t s_sorted[];  // the sorted list when it has at most kSortedSmem symbols
+  __shared__ uint4 s_win[9][kDecThreads];
   if (threadIdx.x < 32) {
     const int l = threadIdx.x;
-    s_first[l] = ds.tabs[l];
-    s_cnt[l] = ds.tabs[32 + l];
-    s_offs[l] = ds.tabs[64 + l];
     const int L = l + 1;
     s_lim[l] = L <= kLmax ? (ds.tabs[L] + ds.tabs[32 + L]) << (kLmax - L) : 0xFFFFFFFFu;
+    s_base[l] = ds.tabs[64 + l] - ds.tabs[l];
   }
-  const bool small = di.n_used <= (unsigned int)kSortedSmem;
-  if (small)
-    for (int i = threadIdx.x; i < (int)di.n_used; i += blockDim.x) s_sorted[i] = ds.sorted[i];
+  __syncthreads();
+  for (int i = threadIdx.x; i < (1 << kShortBits); i += blockDim.x) {
+    // the shortest length whose range end is past every window with this prefix
+    const unsigned int top = ((unsigned int)(i + 1) << (kLmax - kShortBits)) - 1u;
+    int l = 1;
+    while (l <= kShortBits && s_lim[l - 1] <= top) ++l;
+    s_len[i] = (uint8_t)(l <= kShortBits ? l : 0);
+  }
   __syncthreads();
   if (*ds.err) return;
-  const uint16_t* sorted = small ? s_sorted : ds.sorted;
   const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= g.nblocks) return;
+  // range ends of the long lengths, in registers
+  unsigned int lim[kLmax - kShortBits];
+#pragma unroll
+  for (int k = 0; k < kLmax - kShortBits; ++k) lim[k] = s_lim[kShortBits + k];
+  const unsigned int lim_short = s_lim[kShortBits - 1];  // windows below it start a short code
   long long bz, by, bx;
   int e0, e1, e2;
   dec_block_coords(g, b, bz, by, bx, e0, e1, e2);
   const bool full = e0 == g.b[0] && e1 == g.b[1] && e2 == g.b[2];
   const unsigned int nbits = *reinterpret_cast<const unsigned int*>(in + di.off_bb + 4ull * b) & 0x7FFFFFFFu;
-  // Each lane decodes its own block's stream.  Every 32 codes it copies the
-  // next 144 bytes of that stream (at least 32 codes of at most 24 bits) from
-  // global memory into its shared-memory window with independent 16-byte
-  // loads, so the decode steps read only shared memory.  The stream section
-  // starts 16-byte aligned and 16-byte chunks past it read as zero.
+  // Every 32 codes each lane copies the next 144 bytes of its stream (at
+  // least 32 codes of at most 24 bits) into its shared-memory window with
+  // independent 16-byte loads.  The stream section starts 16-byte aligned and
+  // chunks past it read as zero.  Between refills the bits stream through a
+  // 64-bit register buffer whose next word is loaded one code ahead.
   const uint4* s4 = reinterpret_cast<const uint4*>(in + di.off_st);
   const unsigned long long nq = (di.swords + 3) / 4;
-  const unsigned int* win = reinterpret_cast<const unsigned int*>(s_win[threadIdx.x]);
-  unsigned long long p = ds.boff[b];
-  unsigned long long wbase = 0;
+  const unsigned int* win = reinterpret_cast<const unsigned int*>(&s_win[0][0]);
+  auto wword = [&](unsigned int w) { return win[((w >> 2) * kDecThreads + threadIdx.x) * 4 + (w & 3u)]; };
+  unsigned long long p = ds.boff[b];  // bit position of the next code
+  unsigned long long buf = 0;
+  int nb = 0;                         // valid bits in buf, > 32 before each step
+  unsigned int wi = 0, wnext = 0;     // next window word and its value
   auto refill = [&]() {
     const unsigned long long q0 = p >> 7;
-    wbase = q0 << 2;
 #pragma unroll
-    for (int k = 0; k < 9; ++k)
-      s_win[threadIdx.x][k] = q0 + k < nq ? __ldg(s4 + q0 + k) : make_uint4(0u, 0u, 0u, 0u);
+    for (int k = 0; k < 9; ++k) s_win[k][threadIdx.x] = q0 + k < nq ? __ldg(s4 + q0 + k) : make_uint4(0u, 0u, 0u, 0u);
+    const unsigned int w0 = (unsigned int)(p >> 5) - (unsigned int)(q0 << 2);  // < 4
+    const unsigned int sh = (unsigned int)(p & 31ull);
+    buf = (((unsigned long long)wword(w0) << 32) | wword(w0 + 1)) << sh;
+    nb = 64 - (int)sh;
+    wi = w0 + 2;
+    wnext = wword(wi);
   };
   unsigned int used = 0;
   bool bad = false;
   const unsigned int nused = di.n_used;
-  // one canonical decode step, the same for every code (no divergence): the
-  // length is the smallest l with peek < lim[l] (5-step binary search over
-  // the 32-entry table), the symbol sorted[offs[l] + (code - first[l])]
+  // one decode step, the same for every code: short lengths from the table,
+  // long ones by comparing the window with the long range ends
   auto step = [&]() -> unsigned int {
-    const unsigned int lw = (unsigned int)((p >> 5) - wbase);  // < 34 within a refill period
-    const unsigned int peek = __funnelshift_l(win[lw + 1], win[lw], (unsigned int)(p & 31ull)) >> (32 - kLmax);
-    int i = 0;
-    i += s_lim[i + 15] <= peek ? 16 : 0;
-    i += s_lim[i + 7] <= peek ? 8 : 0;
-    i += s_lim[i + 3] <= peek ? 4 : 0;
-    i += s_lim[i + 1] <= peek ? 2 : 0;
-    i += s_lim[i] <= peek ? 1 : 0;
-    const int l = i + 1;
+    const unsigned int peek = (unsigned int)(buf >> (64 - kLmax));
+    int ll = kShortBits + 1;
+#pragma unroll
+    for (int k = 0; k < kLmax - kShortBits; ++k) ll += lim[k] <= peek ? 1 : 0;
+    const int ls = s_len[peek >> (kLmax - kShortBits)];
+    const int l = peek < lim_short ? ls : ll;
+    bad |= l > kLmax;  // past the last code range: not a code
     const int lc = l <= kLmax ? l : kLmax;
-    const unsigned int d = (peek >> (kLmax - lc)) - s_first[lc];
-    const bool inr = l <= kLmax && d < s_cnt[lc];
-    const unsigned int idx = s_offs[lc] + (inr ? d : 0u);
-    // the list holds validated symbols (< 2^m), checked when the tables were built
-    const unsigned int sym = sorted[idx < nused ? idx : 0u];
-    if (!inr) bad = true;
-    used += (unsigned int)lc;
+    const unsigned int idx = s_base[lc] + (peek >> (kLmax - lc));
+    buf <<= lc;
+    nb -= lc;
+    const bool r = nb <= 32;
+    buf |= r ? (unsigned long long)wnext << (32 - nb) : 0ull;
+    nb += r ? 32 : 0;
+    wi += r ? 1u : 0u;
+    wnext = wword(wi < 36u ? wi : 35u);
     p += (unsigned int)lc;
-    return sym;
+    used += (unsigned int)lc;
+    return idx < nused ? idx : 0u;
   };
   uint4* out = reinterpret_cast<uint4*>(ds.codes + b * g.bvol);
   const int b12 = g.b[1] * g.b[2];
@@ -250,14 +265,13 @@ __global__ void __launch_bounds__(kDecThreads) k_huff_decode(Geo g, const uint8_
       }
       sy[q] = (valid && !bad) ? step() : 0u;
     }
-    // symbols are combined after the group, so their loads overlap the steps
     unsigned int pk[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) pk[q] = sy[2 * q] | (sy[2 * q + 1] << 16);
     out[j0 >> 3] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
   }
-  // a corrupt stream shows as a bad long code or a bit count that differs
-  // from the block table's (reads past the block stay inside the stream)
+  // a corrupt stream shows as a window past every code range or a bit count
+  // that differs from the block table's
   if (bad || used != nbits) atomicExch(ds.err, PC_ERR_CORRUPT);
 }
 
@@ -416,10 +430,18 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
       vp = s_vp + blk * PD::PV;
       xs = s_x + blk * BV;
       cd = s_cd + blk * BV;
-      // codes and the padded border for truncated blocks
+      // codes (the decoder leaves list positions; the canonical list maps
+      // them to symbols) and the padded border for truncated blocks
       if (bvalid) {
         const uint4* src = reinterpret_cast<const uint4*>(ds.codes + b * BV);
-        for (int i = t; i < BV / 8; i += TS) reinterpret_cast<uint4*>(cd)[i] = src[i];
+        const uint16_t* __restrict__ sorted = ds.sorted;
+        auto sym2 = [&](unsigned int u) {
+          return (unsigned int)sorted[u & 0xFFFFu] | ((unsigned int)sorted[u >> 16] << 16);
+        };
+        for (int i = t; i < BV / 8; i += TS) {
+          const uint4 v = src[i];
+          reinterpret_cast<uint4*>(cd)[i] = make_uint4(sym2(v.x), sym2(v.y), sym2(v.z), sym2(v.w));
+        }
         if (!bfull) {
           for (int j = t; j < BV; j += TS) {
             const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
@@ -777,11 +799,7 @@ int launch_decompress(const uint8_t* in, const Geo& g, const DecInfo& di, const 
   }
   {
     ProfScope p(kStHuffDecode, s);
-    const size_t sm = di.n_used <= (unsigned int)kSortedSmem ? 2ull * di.n_used : 0ull;
-    if (cudaFuncSetAttribute(k_huff_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kSortedSmem) !=
-        cudaSuccess)
-      return PC_ERR_CUDA;
-    k_huff_decode<<<(unsigned int)((g.nblocks + kDecThreads - 1) / kDecThreads), kDecThreads, sm, s>>>(g, in, di, ds);
+    k_huff_decode<<<(unsigned int)((g.nblocks + kDecThreads - 1) / kDecThreads), kDecThreads, 0, s>>>(g, in, di, ds);
   }
   if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
   const int b0 = g.b[0], b1 = g.b[1], b2 = g.b[2];
