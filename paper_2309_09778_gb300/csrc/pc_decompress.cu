@@ -170,8 +170,9 @@ __global__ void __launch_bounds__(kDecThreads) k_huff_decode(Geo g, const uint8_
   __shared__ unsigned int s_base[32];
   // length of the code a 12-bit window prefix starts, 0 for longer codes
   __shared__ uint8_t s_len[1 << kShortBits];
-  // per-lane stream window: 9 x 16 bytes from a 16-byte aligned word base
-  __shared__ uint4 s_win[9][kDecThreads];
+  // per-lane stream window: 36 words from a 16-byte aligned word base, word-major
+  // (the lanes of a warp read distinct banks whatever words they need)
+  __shared__ unsigned int s_win[36][kDecThreads];
   if (threadIdx.x < 32) {
     const int l = threadIdx.x;
     const int L = l + 1;
@@ -204,33 +205,42 @@ __global__ void __launch_bounds__(kDecThreads) k_huff_decode(Geo g, const uint8_
   // least 32 codes of at most 24 bits) into its shared-memory window with
   // independent 16-byte loads.  The stream section starts 16-byte aligned and
   // chunks past it read as zero.  Between refills the bits stream through a
-  // 64-bit register buffer whose next word is loaded one code ahead.
+  // 64-bit register buffer (hi:lo, next bit at bit 31 of hi) whose next word
+  // is read one code ahead.
   const uint4* s4 = reinterpret_cast<const uint4*>(in + di.off_st);
   const unsigned long long nq = (di.swords + 3) / 4;
-  const unsigned int* win = reinterpret_cast<const unsigned int*>(&s_win[0][0]);
-  auto wword = [&](unsigned int w) { return win[((w >> 2) * kDecThreads + threadIdx.x) * 4 + (w & 3u)]; };
-  unsigned long long p = ds.boff[b];  // bit position of the next code
-  unsigned long long buf = 0;
-  int nb = 0;                         // valid bits in buf, > 32 before each step
-  unsigned int wi = 0, wnext = 0;     // next window word and its value
+  const unsigned int tid = threadIdx.x;
+  const unsigned long long p0 = ds.boff[b];
+  unsigned int hi = 0, lo = 0;
+  int nb = 0;                      // valid bits in hi:lo, > 32 before each step
+  unsigned int wi = 0, wnext = 0;  // next window word and its value
+  unsigned int used = 0;           // bits consumed so far
   auto refill = [&]() {
+    const unsigned long long p = p0 + used;
     const unsigned long long q0 = p >> 7;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) s_win[k][threadIdx.x] = q0 + k < nq ? __ldg(s4 + q0 + k) : make_uint4(0u, 0u, 0u, 0u);
-    const unsigned int w0 = (unsigned int)(p >> 5) - (unsigned int)(q0 << 2);  // < 4
+    for (int k = 0; k < 9; ++k) {
+      const uint4 v = q0 + k < nq ? __ldg(s4 + q0 + k) : make_uint4(0u, 0u, 0u, 0u);
+      s_win[4 * k][tid] = v.x;
+      s_win[4 * k + 1][tid] = v.y;
+      s_win[4 * k + 2][tid] = v.z;
+      s_win[4 * k + 3][tid] = v.w;
+    }
+    const unsigned int w0 = (unsigned int)(p >> 5) & 3u;
     const unsigned int sh = (unsigned int)(p & 31ull);
-    buf = (((unsigned long long)wword(w0) << 32) | wword(w0 + 1)) << sh;
+    const unsigned int a0 = s_win[w0][tid], a1 = s_win[w0 + 1][tid], a2 = s_win[w0 + 2][tid];
+    hi = __funnelshift_l(a1, a0, sh);
+    lo = __funnelshift_l(a2, a1, sh);
     nb = 64 - (int)sh;
     wi = w0 + 2;
-    wnext = wword(wi);
+    wnext = a2;
   };
-  unsigned int used = 0;
   bool bad = false;
   const unsigned int nused = di.n_used;
   // one decode step, the same for every code: short lengths from the table,
   // long ones by comparing the window with the long range ends
   auto step = [&]() -> unsigned int {
-    const unsigned int peek = (unsigned int)(buf >> (64 - kLmax));
+    const unsigned int peek = hi >> (32 - kLmax);
     int ll = kShortBits + 1;
 #pragma unroll
     for (int k = 0; k < kLmax - kShortBits; ++k) ll += lim[k] <= peek ? 1 : 0;
@@ -239,29 +249,37 @@ __global__ void __launch_bounds__(kDecThreads) k_huff_decode(Geo g, const uint8_
     bad |= l > kLmax;  // past the last code range: not a code
     const int lc = l <= kLmax ? l : kLmax;
     const unsigned int idx = s_base[lc] + (peek >> (kLmax - lc));
-    buf <<= lc;
+    hi = __funnelshift_l(lo, hi, (unsigned int)lc);
+    lo <<= lc;
     nb -= lc;
+    // below 33 valid bits, all of them are in hi: the next word goes right after
     const bool r = nb <= 32;
-    buf |= r ? (unsigned long long)wnext << (32 - nb) : 0ull;
+    const unsigned int s2 = (unsigned int)(32 - nb);
+    hi |= r ? __funnelshift_l(wnext, 0u, s2) : 0u;
+    lo |= r ? wnext << s2 : 0u;
     nb += r ? 32 : 0;
     wi += r ? 1u : 0u;
-    wnext = wword(wi < 36u ? wi : 35u);
-    p += (unsigned int)lc;
+    wnext = s_win[wi < 35u ? wi : 35u][tid];
     used += (unsigned int)lc;
     return idx < nused ? idx : 0u;
   };
   uint4* out = reinterpret_cast<uint4*>(ds.codes + b * g.bvol);
-  const int b12 = g.b[1] * g.b[2];
+  const int B1 = g.b[1], B2 = g.b[2];
+  int lz0 = 0, ly0 = 0, lx0 = 0;  // block coordinates of slot j0
   for (int j0 = 0; j0 < g.bvol; j0 += 8) {
     if ((j0 & 31) == 0) refill();
     unsigned int sy[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const int j = j0 + q;
-      bool valid = j != 0;
-      if (!full && valid) {
-        const int lz = j / b12, r = j - lz * b12, ly = r / g.b[2], lx = r - ly * g.b[2];
-        valid = lz < e0 && ly < e1 && lx < e2;
+      bool valid = j0 + q != 0;
+      if (!full) {
+        // slot j0 + q, one row wrap at most (rows hold at least 4 slots)
+        int lx = lx0 + q, ly = ly0, lz = lz0;
+        if (lx >= B2) {
+          lx -= B2;
+          if (++ly == B1) { ly = 0; ++lz; }
+        }
+        valid = valid && lz < e0 && ly < e1 && lx < e2;
       }
       sy[q] = (valid && !bad) ? step() : 0u;
     }
@@ -269,6 +287,11 @@ __global__ void __launch_bounds__(kDecThreads) k_huff_decode(Geo g, const uint8_
 #pragma unroll
     for (int q = 0; q < 4; ++q) pk[q] = sy[2 * q] | (sy[2 * q + 1] << 16);
     out[j0 >> 3] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    lx0 += 8;
+    while (lx0 >= B2) {
+      lx0 -= B2;
+      if (++ly0 == B1) { ly0 = 0; ++lz0; }
+    }
   }
   // a corrupt stream shows as a window past every code range or a bit count
   // that differs from the block table's
