@@ -521,7 +521,8 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const unsigned long lon
     }
   }
   for (int i = tid; i < 128; i += nt) s_bits[i] = 0;
-  // merge rounds on the two queues: in shared memory when both fit
+  // merge rounds on the two queues: in shared memory when both fit, else the
+  // internal-node queue alone (the leaves are read-only and stay in the workspace)
   unsigned int* parent = reinterpret_cast<unsigned int*>(hs.parent);
   const unsigned int* qa = ks;
   unsigned int* qb = reinterpret_cast<unsigned int*>(hs.w);
@@ -530,6 +531,8 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const unsigned long lon
     for (int i = tid; i < n; i += nt) sA[i] = ks[i];
     qa = sA;
     qb = sA + kCbQueueN;
+  } else if ((size_t)n * 4 <= kCbSmem) {
+    qb = reinterpret_cast<unsigned int*>(arena);
   }
   __shared__ TwoQ s_q;
   const int rounds = huff_two_queue(qa, qb, n, parent, hs.rstart, &s_q, &s_u[2]);
@@ -575,6 +578,7 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const unsigned long lon
   const int maxlen = s_u[0];
   // canonical order: most frequent first (the sorted leaf list reversed);
   // the code tables indexed by symbol are filled by k_cb_assign
+#pragma unroll 4
   for (int i = tid; i < n; i += nt) {
     const unsigned int leaf = (unsigned int)(n - 1 - i);
     // length = largest l with leaf < s_lend[l] (s_lend decreases with l)
