@@ -332,16 +332,31 @@ constexpr int max_wave() {
   return best;
 }
 
+// Shared-memory layout of k_recon (16-byte aligned regions).  The per-block
+// strides are padded so that the same point of the GR blocks falls on
+// different banks: wave positions run block-fastest across the lanes.
+template <int B0, int B1, int B2, int PV, int TSZ, int MODE, int K, int H1, int H2>
+struct ReconLayout {
+  static constexpr int BV = B0 * B1 * B2;
+  static constexpr int GR = recon_blocks<BV, TSZ, MODE, K>();
+  static constexpr int PVS = PV | 1;  // padded-block stride of the centred codes (odd)
+  static constexpr int XS = BV + 1;   // block stride of the values
+  static constexpr int CS = BV + 8;   // block stride of the codes (16-byte rows for vector copies)
+  static constexpr size_t a16(size_t v) { return (v + 15) & ~(size_t)15; }
+  static constexpr size_t QB =
+      MODE == 2 ? a16((size_t)QShape<K, H1, H2>::NFRAG * 4 + (size_t)QShape<K, H1, H2>::NBIAS * 8 +
+                      (size_t)GR * max_wave<B0, B1, B2>() * 4)
+                : 0;
+  static constexpr size_t VP = sizeof(Tabs) + QB;
+  static constexpr size_t X = VP + a16((size_t)GR * PVS * 4);
+  static constexpr size_t L = X + a16((size_t)GR * XS * TSZ);
+  static constexpr size_t C = L + a16((size_t)BV * 4);
+  static constexpr size_t TOTAL = C + a16((size_t)GR * CS * 2);
+};
+
 template <int B0, int B1, int B2, int PV, int TSZ, int MODE, int K, int H1, int H2>
 constexpr size_t recon_smem_bytes() {
-  constexpr int BV = B0 * B1 * B2;
-  constexpr int GR = recon_blocks<BV, TSZ, MODE, K>();
-  size_t q = 0;
-  if constexpr (MODE == 2)
-    q = ((size_t)QShape<K, H1, H2>::NFRAG * 4 + (size_t)QShape<K, H1, H2>::NBIAS * 8 +
-         (size_t)GR * max_wave<B0, B1, B2>() * 4 + 15) & ~(size_t)15;
-  return sizeof(Tabs) + q + (size_t)((GR * PV + 3) & ~3) * 4 + (size_t)GR * BV * TSZ + (size_t)BV * 4 +
-         (size_t)GR * BV * 2 + 16;
+  return ReconLayout<B0, B1, B2, PV, TSZ, MODE, K, H1, H2>::TOTAL;
 }
 
 template <typename T, int B0, int B1, int B2, int MODE, int K, int H1, int H2>
@@ -353,7 +368,9 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
   constexpr int GR = recon_blocks<BV, (int)sizeof(T), MODE, K>(), NSUB = GR / G;  // blocks per brick, team groups
   constexpr bool WIDE = MODE != 0 && (K == 13 || K == 0);
   using PD = Pad<B0, B1, B2, WIDE>;
-  constexpr int VPR = (GR * PD::PV + 3) & ~3;
+  using RL = ReconLayout<B0, B1, B2, PD::PV, (int)sizeof(T), MODE, K, H1, H2>;
+  constexpr int PVS = RL::PVS, XS = RL::XS, CS = RL::CS;
+  static_assert(sizeof(Tabs) % 16 == 0, "regions after the tables stay 16-byte aligned");
   constexpr int SZ = (B0 - 1) * 4 + (B1 - 1) * 2 + (B2 - 1) + 1;  // waves of the wider schedule
   constexpr int VW = 16 / (int)sizeof(T);
   constexpr bool VEC_OK = (B2 * GR) % VW == 0;
@@ -361,20 +378,15 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
   Tabs& tb = *reinterpret_cast<Tabs*>(smem);
   constexpr int QK = MODE == 2 ? K : 7, QH1 = MODE == 2 ? H1 : 16, QH2 = MODE == 2 ? H2 : 16;
   using QS = QShape<QK, QH1, QH2>;
-  // whole 16-byte units, so that the arrays after it keep their 16-byte alignment
-  constexpr size_t QBYTES =
-      MODE == 2 ? (((size_t)QS::NFRAG * 4 + (size_t)QS::NBIAS * 8 + (size_t)GR * max_wave<B0, B1, B2>() * 4 + 15) &
-                   ~(size_t)15)
-                : 0;
   uint32_t* s_frag = reinterpret_cast<uint32_t*>(smem + sizeof(Tabs));   // fixed-point form only
   long long* s_qbias = reinterpret_cast<long long*>(s_frag + (MODE == 2 ? QS::NFRAG : 0));
   int* s_wpred = reinterpret_cast<int*>(s_qbias + (MODE == 2 ? QS::NBIAS : 0));  // one wave's predictions
   __shared__ QSc s_qsc;
-  int* s_vp = reinterpret_cast<int*>(smem + sizeof(Tabs) + QBYTES);  // GR*PV padded centred codes
-  T* s_x = reinterpret_cast<T*>(s_vp + VPR);                        // GR*BV
+  int* s_vp = reinterpret_cast<int*>(smem + RL::VP);             // GR padded blocks of centred codes
+  T* s_x = reinterpret_cast<T*>(smem + RL::X);                    // GR blocks of values
   // BV points in wave order, each j | (padded index of j) << 16
-  unsigned int* s_list = reinterpret_cast<unsigned int*>(s_x + GR * BV);
-  uint16_t* s_cd = reinterpret_cast<uint16_t*>(s_list + BV);        // GR*BV
+  unsigned int* s_list = reinterpret_cast<unsigned int*>(smem + RL::L);
+  uint16_t* s_cd = reinterpret_cast<uint16_t*>(smem + RL::C);     // GR blocks of codes
   __shared__ int s_ws[SZ + 2];
   __shared__ int s_fill[SZ + 2];
   __shared__ unsigned int s_wt[G][NWT];
@@ -397,7 +409,7 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
   const bool s13 = di.stencil == 13;
   for (int i = tid; i < (int)(sizeof(Tabs) / 4); i += 256)
     reinterpret_cast<float*>(&tb)[i] = reinterpret_cast<const float*>(ds.ftab)[i];
-  for (int i = tid; i < VPR; i += 256) s_vp[i] = 0;
+  for (int i = tid; i < GR * PVS; i += 256) s_vp[i] = 0;
   for (int i = tid; i < SZ + 2; i += 256) { s_ws[i] = 0; s_fill[i] = 0; }
   if (tid == 0) s_bad = 0;
   if constexpr (MODE == 2) qnet_stage<QK, QH1, QH2>(di.qnet, s_frag, s_qbias, &s_qsc);
@@ -450,9 +462,9 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
       e2 = bvalid ? (int)min((long long)B2, g.n[2] - bx * B2) : 0;
       bfull = e0 == B0 && e1 == B1 && e2 == B2;
       const long long b = (bz * g.nb[1] + by) * g.nb[2] + bx;
-      vp = s_vp + blk * PD::PV;
-      xs = s_x + blk * BV;
-      cd = s_cd + blk * BV;
+      vp = s_vp + blk * PVS;
+      xs = s_x + blk * XS;
+      cd = s_cd + blk * CS;
       // codes (the decoder leaves list positions; the canonical list maps
       // them to symbols) and the padded border for truncated blocks
       if (bvalid) {
@@ -565,7 +577,7 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
             const int f = tile * 16 + (lane >> 2) + 8 * r;
             fs[r] = f;
             const int fi = f < tot ? f : 0;
-            const int pj = (fi % GR) * PD::PV + (int)(s_list[w0 + fi / GR] >> 16);
+            const int pj = (fi % GR) * PVS + (int)(s_list[w0 + fi / GR] >> 16);
 #pragma unroll
             for (int kc = 0; kc < QS::KC1; ++kc)
 #pragma unroll
@@ -587,12 +599,12 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
         for (int f = tid; f < tot; f += 256) {
           const int gb = f % GR;
           const unsigned int e = s_list[w0 + f / GR];
-          const int j = (int)(e & 0xFFFFu), pj = gb * PD::PV + (int)(e >> 16);
+          const int j = (int)(e & 0xFFFFu), pj = gb * PVS + (int)(e >> 16);
           if (!brick_full) {
             const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
             if (!(lz < e0 && ly < e1 && lx < s_e2[gb])) continue;
           }
-          const unsigned int code = s_cd[gb * BV + j];
+          const unsigned int code = s_cd[gb * CS + j];
           if (code == 0) continue;  // balance point, already in place
           long long prd;
           if (s_usen[gb]) {
@@ -608,7 +620,7 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
           int q;
           if (qq > 2147483647LL || qq < -2147483647LL) { bad = true; q = 0; }
           else q = (int)qq;
-          s_x[gb * BV + j] = Num<T>::recon(q, c, tb);
+          s_x[gb * XS + j] = Num<T>::recon(q, c, tb);
           s_vp[pj] = clampv((long long)q - dag);
         }
         __syncthreads();
@@ -631,18 +643,18 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
             const int fi = f < tot ? f : 0;
             const int gb = fi % GR;
             const unsigned int e = s_list[w0 + fi / GR];
-            const int j = (int)(e & 0xFFFFu), pj = gb * PD::PV + (int)(e >> 16);
+            const int j = (int)(e & 0xFFFFu), pj = gb * PVS + (int)(e >> 16);
             bool valid = f < tot;
             if (!brick_full) {
               const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
               valid = valid && lz < e0 && ly < e1 && lx < s_e2[gb];
             }
-            const unsigned int code = s_cd[gb * BV + j];
+            const unsigned int code = s_cd[gb * CS + j];
             act[u] = valid && code != 0u;   // balance points are already in place
             need[u] = act[u] && s_usen[gb] != 0;
             cds[u] = code;
             pjs[u] = pj;
-            xis[u] = gb * BV + j;
+            xis[u] = gb * XS + j;
             dav[u] = s_da[gb];
 #pragma unroll
             for (int si = 0; si < K; ++si) inp[u][si] = s_vp[pj + PD::off(st_dz(K, si), st_dy(K, si), st_dx(K, si))];
@@ -729,7 +741,7 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
 #pragma unroll
         for (int q = 0; q < VW; ++q) {
           const int col = cv * VW + q;
-          v[q] = s_x[(col / B2) * BV + (z * B1 + y) * B2 + (col % B2)];
+          v[q] = s_x[(col / B2) * XS + (z * B1 + y) * B2 + (col % B2)];
         }
         uint4 u;
         memcpy(&u, v, 16);
@@ -739,7 +751,7 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
       for (int e = tid; e < e0 * e1 * W; e += 256) {
         const int r = e / W, col = e - r * W;
         const int z = r / e1, y = r - z * e1;
-        xo[((z0 + z) * g.n[1] + (y0 + y)) * g.n[2] + x0 + col] = s_x[(col / B2) * BV + (z * B1 + y) * B2 + (col % B2)];
+        xo[((z0 + z) * g.n[1] + (y0 + y)) * g.n[2] + x0 + col] = s_x[(col / B2) * XS + (z * B1 + y) * B2 + (col % B2)];
       }
     }
     __syncthreads();
