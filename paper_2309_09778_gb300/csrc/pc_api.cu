@@ -610,8 +610,10 @@ int pc_decompress(const void* d_in, size_t in_size, void* d_field, size_t field_
   if (!d_in || !d_field || !d_ws) return PC_ERR_ARG;
   if (in_size < (size_t)kHdr) return PC_ERR_CORRUPT;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  uint8_t hbuf[kHdr];
-  if (cudaMemcpyAsync(hbuf, d_in, kHdr, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PC_ERR_CUDA;
+  // the header and the largest FP32 weight section in one read-back
+  static thread_local uint8_t hbuf[kHdr + 4 * kMaxW];
+  const size_t pre = in_size < sizeof(hbuf) ? in_size : sizeof(hbuf);
+  if (cudaMemcpyAsync(hbuf, d_in, pre, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PC_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
   Hdr H;
   Geo g;
@@ -632,10 +634,9 @@ int pc_decompress(const void* d_in, size_t in_size, void* d_field, size_t field_
     mlp.s_in = H.s_in;
   }
   if (H.pred == 1) {
-    if (cudaMemcpyAsync(mlp.w, static_cast<const uint8_t*>(d_in) + kHdr, 4ull * H.nw, cudaMemcpyDeviceToHost, s) !=
-        cudaSuccess)
-      return PC_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
+    // nw <= kMaxW (checked with the header) and the container holds the section
+    if (kHdr + 4ull * H.nw > pre) return PC_ERR_CORRUPT;
+    memcpy(mlp.w, hbuf + kHdr, 4ull * H.nw);
   }
   if (dims_out)
     for (int i = 0; i < 3; ++i) dims_out[i] = H.dims[i];
