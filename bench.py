@@ -146,7 +146,7 @@ KERNELS_PER_STAGE = {"codebook": 2, "dec_scan": 3}
 
 # DRAM bytes (read + write) of one launch, from the ncu capture in profiles/k_recon_c2_fp32.md
 # (FP32 form of this workload); valid while that kernel is unchanged.
-TRAFFIC_PER_LAUNCH = {("recon", "fp32"): 55112448 + 44073984}
+TRAFFIC_PER_LAUNCH = {("recon", "fp32"): 55235584 + 43935488}
 
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop (FMA) per cycle.
 SMS, FP32_LANES = 152, 128
