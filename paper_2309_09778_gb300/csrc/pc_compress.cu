@@ -43,52 +43,64 @@ template <> struct Bits<double> {
 template <typename T>
 __global__ void __launch_bounds__(256) k_stats(const T* __restrict__ x, unsigned long long n, State* st) {
   using B = Bits<T>;
-  unsigned long long mn = ~0ull, mx = 0ull;
-  unsigned int bad = 0, have = 0;
+  using U = typename B::U;
+  // in the value's own width: the largest magnitude (non-finite ones sort
+  // above every finite one) and the smallest normal magnitude (the all-ones
+  // start means none)
+  U mn = ~U(0), mx = 0;
   auto acc = [&](T v) {
-    const auto a = B::mag(v);
-    bad |= (a >= B::kInf);
-    if (a >= B::kMinNormal && a < B::kInf) {
-      have = 1;
-      mn = min(mn, (unsigned long long)a);
-    }
-    mx = max(mx, (unsigned long long)a);
+    const U a = B::mag(v);
+    mx = max(mx, a);
+    mn = min(mn, (a >= B::kMinNormal && a < B::kInf) ? a : ~U(0));
   };
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   const unsigned long long tid0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-  // 16-byte vector loads over the aligned body, scalar loads for the tail
+  // 16-byte vector loads over the aligned body, four in flight per thread;
+  // scalar loads for the tail
   constexpr int V = 16 / sizeof(T);
+  constexpr int NL = 4;
   const bool aligned = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
   const unsigned long long nv = aligned ? n / V : 0;
   const uint4* xv = reinterpret_cast<const uint4*>(x);
-#pragma unroll 4
-  for (unsigned long long i = tid0; i < nv; i += stride) {
+  unsigned long long i = tid0;
+  for (; i + (NL - 1) * stride < nv; i += NL * stride) {
+    uint4 u[NL];
+#pragma unroll
+    for (int k = 0; k < NL; ++k) u[k] = __ldg(&xv[i + k * stride]);
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+      T t[V];
+      memcpy(t, &u[k], 16);
+#pragma unroll
+      for (int q = 0; q < V; ++q) acc(t[q]);
+    }
+  }
+  for (; i < nv; i += stride) {
     const uint4 u = __ldg(&xv[i]);
     T t[V];
     memcpy(t, &u, 16);
 #pragma unroll
     for (int q = 0; q < V; ++q) acc(t[q]);
   }
-  for (unsigned long long i = nv * V + tid0; i < n; i += stride) acc(__ldg(&x[i]));
+  for (unsigned long long j = nv * V + tid0; j < n; j += stride) acc(__ldg(&x[j]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    mn = min(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
-    mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
-    bad |= __shfl_xor_sync(0xFFFFFFFFu, bad, o);
-    have |= __shfl_xor_sync(0xFFFFFFFFu, have, o);
+    mn = min(mn, (U)__shfl_xor_sync(0xFFFFFFFFu, mn, o));
+    mx = max(mx, (U)__shfl_xor_sync(0xFFFFFFFFu, mx, o));
   }
-  __shared__ unsigned long long s_mn[8], s_mx[8];
-  __shared__ unsigned int s_bad[8], s_have[8];
-  int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) { s_mn[w] = mn; s_mx[w] = mx; s_bad[w] = bad; s_have[w] = have; }
+  __shared__ U s_mn[8], s_mx[8];
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { s_mn[w] = mn; s_mx[w] = mx; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
-      mn = min(mn, s_mn[i]); mx = max(mx, s_mx[i]); bad |= s_bad[i]; have |= s_have[i];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+      mn = min(mn, s_mn[k]);
+      mx = max(mx, s_mx[k]);
     }
-    if (have) atomicMin(&st->amin_bits, mn);
-    atomicMax(&st->amax_bits, mx);
-    if (bad) atomicOr(&st->nonfinite, 1u);
+    const bool have = mn != ~U(0);
+    if (have) atomicMin(&st->amin_bits, (unsigned long long)mn);
+    atomicMax(&st->amax_bits, (unsigned long long)mx);
+    if (mx >= B::kInf) atomicOr(&st->nonfinite, 1u);
     if (have) atomicOr(&st->have_normal, 1u);
   }
 }

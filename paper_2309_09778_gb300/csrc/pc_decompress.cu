@@ -3,12 +3,13 @@
 // k_dec_tables rebuilds the canonical decoder from the stored (symbol, length)
 // list and validates it; k_dec_chunksum / k_dec_chunkscan / k_dec_blockoff
 // turn the block table into per-block bit and balance-point offsets;
-// k_huff_decode decodes one block per thread (a branch-free canonical search
-// over the per-length range ends), checking every read against the block's
-// stated bit count; k_recon rebuilds each block along wavefronts of its causal
-// stencil with the same predictor and inverse map as the compressor, then
-// writes the brick with coalesced stores.  A damaged stream sets the error
-// word and never leads to an out-of-bounds access.
+// k_huff_decode decodes one block per thread (the same step for
+// every code: a 12-bit length table, register compares for longer codes),
+// checking every read against the block's stated bit count; k_recon rebuilds
+// each block along wavefronts of its causal stencil with the same predictor
+// and inverse map as the compressor, then writes the brick with coalesced
+// stores.  A damaged stream sets the error word and never leads to an
+// out-of-bounds access.
 #include "pc_kernels.cuh"
 #include "pc_qmlp.cuh"
 #include "pc_profile.cuh"
@@ -17,46 +18,67 @@ namespace pc {
 
 // The stored list is the code order (lengths never decrease along it), so the
 // decoder tables follow from one pass: the symbol at list position p has code
-// first[len] + (p - offset[len]).
+// first[len] + (p - offset[len]).  Each length's count is the distance from its
+// first position to the next length's; a position whose length differs from
+// its predecessor's marks a first position (one writer per length).
 __global__ void __launch_bounds__(1024) k_dec_tables(const uint8_t* __restrict__ in, DecInfo di, DecScratch ds) {
-  __shared__ unsigned int s_cnt[32];
+  __shared__ unsigned int s_start[32];
   __shared__ unsigned int s_seen[2048];  // one bit per symbol (m <= 16)
   __shared__ int s_bad;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nsym = 1 << di.m;
   const int n = (int)di.n_used;
-  if (tid < 32) s_cnt[tid] = 0;
+  if (tid < 32) s_start[tid] = 0xFFFFFFFFu;
   if (tid == 0) s_bad = 0;
   if (tid < 128) build_tabs_entry(ds.ftab, tid);
   for (int i = tid; i < 2048; i += nt) s_seen[i] = 0u;
   __syncthreads();
   const unsigned int* ent = reinterpret_cast<const unsigned int*>(in + di.off_cb);
-  for (int p = tid; p < n; p += nt) {
-    const unsigned int e = ent[p];
-    const unsigned int sym = e & 0xFFFFu, len = e >> 16;
-    bool bad = sym >= (unsigned int)nsym || len < 1 || len > (unsigned int)kLmax;
-    if (p > 0) bad |= len < (ent[p - 1] >> 16);
-    if (!bad) {
-      const unsigned int bit = 1u << (sym & 31u);
-      bad |= (atomicOr(&s_seen[sym >> 5], bit) & bit) != 0u;
+  // four entries per thread and step, their loads issued together
+  constexpr int U = 4;
+  for (int p0 = tid; p0 < n; p0 += U * nt) {
+    unsigned int e[U], pe[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int p = p0 + k * nt;
+      e[k] = p < n ? ent[p] : 0u;
+      pe[k] = p > 0 && p < n ? ent[p - 1] : 0u;
     }
-    if (bad) { s_bad = 1; continue; }
-    ds.sorted[p] = (uint16_t)sym;
-    atomicAdd(&s_cnt[len], 1u);
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int p = p0 + k * nt;
+      if (p >= n) break;
+      const unsigned int sym = e[k] & 0xFFFFu, len = e[k] >> 16, prev = pe[k] >> 16;
+      bool bad = sym >= (unsigned int)nsym || len < 1 || len > (unsigned int)kLmax || len < prev;
+      if (!bad) {
+        const unsigned int bit = 1u << (sym & 31u);
+        bad |= (atomicOr(&s_seen[sym >> 5], bit) & bit) != 0u;
+      }
+      if (bad) { s_bad = 1; continue; }
+      ds.sorted[p] = (uint16_t)sym;
+      if (len != prev) s_start[len] = (unsigned int)p;
+    }
   }
   __syncthreads();
   if (s_bad) { if (tid == 0) atomicExch(ds.err, PC_ERR_CORRUPT); return; }
   if (tid == 0) {
+    unsigned int cnt[kLmax + 1];
+    unsigned int next = (unsigned int)n;
+    for (int l = kLmax; l >= 1; --l) {
+      const unsigned int st = s_start[l];
+      cnt[l] = st != 0xFFFFFFFFu ? next - st : 0u;
+      if (st != 0xFFFFFFFFu) next = st;
+    }
     unsigned int code = 0, off = 0;
     bool bad = false;
     for (int l = 1; l <= kLmax; ++l) {
-      const unsigned int prevc = l > 1 ? s_cnt[l - 1] : 0u;
+      const unsigned int prevc = l > 1 ? cnt[l - 1] : 0u;
       code = (code + prevc) << 1;
       off += prevc;
-      ds.tabs[l] = code;            // first code of length l
-      ds.tabs[32 + l] = s_cnt[l];   // count
-      ds.tabs[64 + l] = off;        // list position of the first code of length l
-      if (s_cnt[l] && (unsigned long long)code + s_cnt[l] > (1ull << l)) bad = true;
+      ds.tabs[l] = code;        // first code of length l
+      ds.tabs[32 + l] = cnt[l];  // count
+      ds.tabs[64 + l] = off;     // list position of the first code of length l
+      if (cnt[l] && (unsigned long long)code + cnt[l] > (1ull << l)) bad = true;
     }
     if (bad) atomicExch(ds.err, PC_ERR_CORRUPT);
   }
