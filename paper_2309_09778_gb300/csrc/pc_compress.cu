@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(256) k_stats(const T* __restrict__ x, unsigned
 template <typename T>
 __global__ void k_consts(State* st, double eb, Tabs* tabs) {
   // four independent logarithms on four threads, combined by thread 0
+  // (launched with 128 threads, one per log/reciprocal table entry)
   __shared__ double s_l[4];
   __shared__ double s_ab[2];
   __shared__ int s_stop;
@@ -151,10 +152,7 @@ __global__ void k_consts(State* st, double eb, Tabs* tabs) {
   }
   __syncthreads();
   if (s_stop) return;
-  build_tabs_entry(tabs, t);
-  build_tabs_entry(tabs, t + 32);
-  build_tabs_entry(tabs, t + 64);
-  build_tabs_entry(tabs, t + 96);
+  build_tabs_entry(tabs, t);  // one table entry per thread (128 threads: four warps share the FP64 work)
   if (t < 4) {
     const double amin = s_ab[0], amax = s_ab[1];
     const double arg = t == 0 ? __dadd_rn(1.0, eb) : (t == 1 ? __dadd_rn(amax, e0) : (t == 2 ? amin : __dsub_rn(amin, e0)));
@@ -587,7 +585,7 @@ int launch_stats_consts(const void* x, unsigned long long n, State* st, Tabs* ta
                         int nsym, double eb, int nsm, cudaStream_t s) {
   { ProfScope p(kStInit, s); k_init<<<64, 256, 0, s>>>(st, hist, nsym); }
   { ProfScope p(kStStats, s); k_stats<T><<<nsm * 8, 256, 0, s>>>(static_cast<const T*>(x), n, st); }
-  { ProfScope p(kStConsts, s); k_consts<T><<<1, 32, 0, s>>>(st, eb, tabs); }
+  { ProfScope p(kStConsts, s); k_consts<T><<<1, 128, 0, s>>>(st, eb, tabs); }
   return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
 template int launch_stats_consts<float>(const void*, unsigned long long, State*, Tabs*, unsigned long long*, int,

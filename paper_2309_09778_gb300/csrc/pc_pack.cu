@@ -157,59 +157,64 @@ __global__ void __launch_bounds__(1024) k_chunkscan(Geo g, const unsigned long l
     for (int k = 0; k < 8; ++k) cr = (cr >> 1) ^ (0xEDB88320u & (0u - (cr & 1u)));
     s_crc[tid] = cr;
   }
-  if (tid < 64) st_u32(out + 4 * tid, 0u);
+  // assembled in shared memory, checksummed there, then copied out
+  __shared__ __align__(16) uint8_t s_hdr[256];
+  if (tid < 64) st_u32(s_hdr + 4 * tid, 0u);
   __syncthreads();
   if (tid == 0) {
+    uint8_t* const hd = s_hdr;
     const State& c = *st;
     const bool nn = hi.pred != 0;
-    st_u32(out + 0, 0x504D4350u);  // "PCMP"
-    st_u32(out + 4, 1u);
-    st_u32(out + 8, (unsigned int)hi.dtype);
-    st_u32(out + 12, (unsigned int)hi.pred);
-    st_u64(out + 16, (unsigned long long)g.n[0]);
-    st_u64(out + 24, (unsigned long long)g.n[1]);
-    st_u64(out + 32, (unsigned long long)g.n[2]);
-    st_u32(out + 40, (unsigned int)g.b[0]);
-    st_u32(out + 44, (unsigned int)g.b[1]);
-    st_u32(out + 48, (unsigned int)g.b[2]);
-    st_u32(out + 52, nn ? (unsigned int)hi.stencil : 0u);
-    st_u32(out + 56, nn ? (unsigned int)hi.h1 : 0u);
-    st_u32(out + 60, nn ? (unsigned int)hi.h2 : 0u);
-    st_u32(out + 64, (unsigned int)hi.m);
-    st_u32(out + 68, nn ? (unsigned int)hi.s_in : 0u);
-    st_u64(out + 72, (unsigned long long)__double_as_longlong(hi.eb));
-    st_u64(out + 80, (unsigned long long)__double_as_longlong(c.amin));
-    st_u64(out + 88, (unsigned long long)__double_as_longlong(c.amax));
-    st_u32(out + 96, (unsigned int)c.trivial);
-    st_u32(out + 100, (unsigned int)c.Kp);
-    st_u32(out + 104, (unsigned int)c.Kn);
-    st_u32(out + 108, (unsigned int)c.Zq);
-    st_u32(out + 112, (unsigned int)c.S);
-    st_u32(out + 116, c.n_used);
+    st_u32(hd + 0, 0x504D4350u);  // "PCMP"
+    st_u32(hd + 4, 1u);
+    st_u32(hd + 8, (unsigned int)hi.dtype);
+    st_u32(hd + 12, (unsigned int)hi.pred);
+    st_u64(hd + 16, (unsigned long long)g.n[0]);
+    st_u64(hd + 24, (unsigned long long)g.n[1]);
+    st_u64(hd + 32, (unsigned long long)g.n[2]);
+    st_u32(hd + 40, (unsigned int)g.b[0]);
+    st_u32(hd + 44, (unsigned int)g.b[1]);
+    st_u32(hd + 48, (unsigned int)g.b[2]);
+    st_u32(hd + 52, nn ? (unsigned int)hi.stencil : 0u);
+    st_u32(hd + 56, nn ? (unsigned int)hi.h1 : 0u);
+    st_u32(hd + 60, nn ? (unsigned int)hi.h2 : 0u);
+    st_u32(hd + 64, (unsigned int)hi.m);
+    st_u32(hd + 68, nn ? (unsigned int)hi.s_in : 0u);
+    st_u64(hd + 72, (unsigned long long)__double_as_longlong(hi.eb));
+    st_u64(hd + 80, (unsigned long long)__double_as_longlong(c.amin));
+    st_u64(hd + 88, (unsigned long long)__double_as_longlong(c.amax));
+    st_u32(hd + 96, (unsigned int)c.trivial);
+    st_u32(hd + 100, (unsigned int)c.Kp);
+    st_u32(hd + 104, (unsigned int)c.Kn);
+    st_u32(hd + 108, (unsigned int)c.Zq);
+    st_u32(hd + 112, (unsigned int)c.S);
+    st_u32(hd + 116, c.n_used);
     if (sizeof(T) == 4) {
-      st_u64(out + 120, __float_as_uint(c.step32));
-      st_u64(out + 128, __float_as_uint(c.inv32));
-      st_u64(out + 136, __float_as_uint(c.ebdn32));
+      st_u64(hd + 120, __float_as_uint(c.step32));
+      st_u64(hd + 128, __float_as_uint(c.inv32));
+      st_u64(hd + 136, __float_as_uint(c.ebdn32));
     } else {
-      st_u64(out + 120, (unsigned long long)__double_as_longlong(c.stepd));
-      st_u64(out + 128, (unsigned long long)__double_as_longlong(c.invd));
-      st_u64(out + 136, (unsigned long long)__double_as_longlong(c.ebdnd));
+      st_u64(hd + 120, (unsigned long long)__double_as_longlong(c.stepd));
+      st_u64(hd + 128, (unsigned long long)__double_as_longlong(c.invd));
+      st_u64(hd + 136, (unsigned long long)__double_as_longlong(c.ebdnd));
     }
-    st_u64(out + 144, (unsigned long long)g.nblocks);
-    st_u64(out + 152, to);
-    st_u64(out + 160, swords);
-    st_u64(out + 168, (unsigned long long)kHdr);
-    st_u64(out + 176, hi.off_cb);
-    st_u64(out + 184, off_bb);
-    st_u64(out + 192, off_bn);
-    st_u64(out + 200, off_ov);
-    st_u64(out + 208, off_st);
-    st_u64(out + 216, total);
-    st_u32(out + 224, (unsigned int)hi.nw);
+    st_u64(hd + 144, (unsigned long long)g.nblocks);
+    st_u64(hd + 152, to);
+    st_u64(hd + 160, swords);
+    st_u64(hd + 168, (unsigned long long)kHdr);
+    st_u64(hd + 176, hi.off_cb);
+    st_u64(hd + 184, off_bb);
+    st_u64(hd + 192, off_bn);
+    st_u64(hd + 200, off_ov);
+    st_u64(hd + 208, off_st);
+    st_u64(hd + 216, total);
+    st_u32(hd + 224, (unsigned int)hi.nw);
     unsigned int crc = 0xFFFFFFFFu;
-    for (int i = 0; i < 252; ++i) crc = s_crc[(crc ^ out[i]) & 0xFFu] ^ (crc >> 8);
-    st_u32(out + 252, crc ^ 0xFFFFFFFFu);
+    for (int i = 0; i < 252; ++i) crc = s_crc[(crc ^ hd[i]) & 0xFFu] ^ (crc >> 8);
+    st_u32(hd + 252, crc ^ 0xFFFFFFFFu);
   }
+  __syncthreads();
+  if (tid < 64) st_u32(out + 4 * tid, reinterpret_cast<const unsigned int*>(s_hdr)[tid]);
 }
 
 template <typename T>
