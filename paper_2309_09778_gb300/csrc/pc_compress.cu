@@ -292,7 +292,10 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restr
     constexpr int RW = G * B2 / VW;               // 16-byte vectors per brick row
     constexpr int NV = B0 * B1 * RW;
     const bool fullb = e0 == B0 && e1 == B1 && W == G * B2;
-    const bool vecb = fullb && vec_rows;
+    // whole-vector rows only when a thread's vectors fit its EPT registers
+    // (small bricks of 512 points have 2 elements per thread, fewer than one vector)
+    constexpr bool VEC_FITS = ((NV + 255) / 256) * VW <= EPT;
+    const bool vecb = VEC_FITS && fullb && vec_rows;
     const long long n12 = g.n[1] * g.n[2];
     const T* base = x + z0 * n12 + y0 * g.n[2] + x0;
     T vals[EPT];

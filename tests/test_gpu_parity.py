@@ -83,6 +83,9 @@ CASES = [
     ((1, 50, 61), (1, 16, 32), 1e-3, np.float32),
     ((1, 70, 130), (1, 64, 64), 1e-2, np.float32),
     ((3, 40, 33), (1, 8, 8), 1e-4, np.float32),
+    # rows a multiple of 16 bytes: whole bricks take the vector-load path
+    ((2, 40, 128), (1, 8, 8), 1e-3, np.float32),
+    ((8, 16, 64), (4, 4, 4), 1e-3, np.float32),
     ((17, 18, 19), (8, 8, 8), 1e-5, np.float64),
     ((33, 9, 70), (4, 4, 4), 1e-3, np.float64),
 ]
@@ -107,6 +110,12 @@ def test_lorenzo_container_and_decode_match_oracle(pc, O, shape, block, eb, dt):
     ((9, 30, 17), (4, 4, 4), 1e-2, 7, (2, 0)),
     ((13, 11, 40), (16, 16, 16), 1e-2, 13, (8, 4)),
     ((1, 50, 61), (1, 16, 32), 1e-3, 13, (32, 32)),
+    # several 16-block reconstruction bricks along x, truncated last brick
+    ((9, 30, 70), (4, 4, 4), 1e-2, 7, (16, 16)),
+    ((1, 40, 300), (1, 8, 8), 1e-3, 7, (16, 16)),
+    ((2, 40, 600), (1, 16, 32), 1e-3, 7, (16, 16)),
+    ((16, 20, 300), (8, 8, 8), 1e-3, 7, (16, 16)),
+    ((17, 24, 280), (8, 8, 8), 1e-3, 13, (32, 32)),
 ])
 def test_perceptron_container_and_decode_match_oracle(pc, O, shape, block, eb, k, h):
     x = gen.positive_lognormal(shape, 3.0, 5, 1.5)
