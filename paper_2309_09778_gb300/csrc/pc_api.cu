@@ -125,7 +125,7 @@ CompLayout comp_layout(const Geo& g, int m) {
 }
 
 struct DecLayout {
-  size_t err, ftab, sorted, tabs, key, cbits, cnout, cboff, cooff, boff, ooff, codes, total;
+  size_t err, ftab, sorted, tabs, cbits, cnout, cboff, cooff, boff, ooff, codes, total;
 };
 
 DecLayout dec_layout(const Geo& g, int m) {
@@ -136,7 +136,6 @@ DecLayout dec_layout(const Geo& g, int m) {
   L.ftab = o; o = up(o + sizeof(Tabs));
   L.sorted = o; o = up(o + 2 * nsym);
   L.tabs = o; o = up(o + 4 * 96);
-  L.key = o; o = up(o + 8 * nsym);
   L.cbits = o; o = up(o + 8 * (size_t)g.nchunks);
   L.cnout = o; o = up(o + 8 * (size_t)g.nchunks);
   L.cboff = o; o = up(o + 8 * (size_t)g.nchunks);
@@ -647,7 +646,6 @@ int pc_decompress(const void* d_in, size_t in_size, void* d_field, size_t field_
   ds.ftab = reinterpret_cast<Tabs*>(ws + L.ftab);
   ds.sorted = reinterpret_cast<uint16_t*>(ws + L.sorted);
   ds.tabs = reinterpret_cast<unsigned int*>(ws + L.tabs);
-  ds.key = reinterpret_cast<unsigned long long*>(ws + L.key);
   ds.chunk_bits = reinterpret_cast<unsigned long long*>(ws + L.cbits);
   ds.chunk_nout = reinterpret_cast<unsigned long long*>(ws + L.cnout);
   ds.chunk_boff = reinterpret_cast<unsigned long long*>(ws + L.cboff);

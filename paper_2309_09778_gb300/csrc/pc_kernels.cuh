@@ -137,7 +137,6 @@ struct DecInfo {
 struct DecScratch {
   uint16_t* sorted;            // [2^m] symbols in canonical (length, symbol) order
   unsigned int* tabs;          // [3 * 32]: first code, count, offset per length
-  unsigned long long* key;     // [np2] sort scratch
   unsigned long long* chunk_bits;
   unsigned long long* chunk_nout;
   unsigned long long* chunk_boff;
