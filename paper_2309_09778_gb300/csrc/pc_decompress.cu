@@ -177,9 +177,9 @@ __global__ void __launch_bounds__(256) k_dec_blockoff(Geo g, const uint8_t* __re
 }
 
 // One thread per block: canonical Huffman decode into block-strided codes.
-// The output is each code's position in the canonical list (symbols sorted by
-// (length, symbol)); the reconstruction maps positions to symbols when it
-// stages a block.  Eight positions are packed and written with one 16-byte
+// The output is each code's position in the stored codebook list (the code
+// order: lengths never decrease along it); the reconstruction maps positions
+// to symbols when it stages a block.  Eight positions are packed and written with one 16-byte
 // store.
 constexpr int kDecThreads = 128;  // threads (blocks decoded) per CTA of k_huff_decode
 constexpr int kShortBits = 12;    // codes up to this long take their length from a table
@@ -487,7 +487,7 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
       vp = s_vp + blk * PVS;
       xs = s_x + blk * XS;
       cd = s_cd + blk * CS;
-      // codes (the decoder leaves list positions; the canonical list maps
+      // codes (the decoder leaves positions in the codebook list, which maps
       // them to symbols) and the padded border for truncated blocks
       if (bvalid) {
         const uint4* src = reinterpret_cast<const uint4*>(ds.codes + b * BV);

@@ -135,7 +135,7 @@ struct DecInfo {
   unsigned long long step_bits, inv_bits, ebdn_bits;
 };
 struct DecScratch {
-  uint16_t* sorted;            // [2^m] symbols in canonical (length, symbol) order
+  uint16_t* sorted;            // [2^m] symbols in code order (the stored codebook list)
   unsigned int* tabs;          // [3 * 32]: first code, count, offset per length
   unsigned long long* chunk_bits;
   unsigned long long* chunk_nout;
