@@ -157,17 +157,19 @@ int pc_decompress(const void* d_in, size_t in_size, void* d_field, size_t field_
 
 /*
  * Decompression that allocates nothing, for callers that cannot obtain device
- * memory at the point of the call (inside a stream capture, under a fixed
- * memory budget, or as a plugin given only an input and an output buffer).
+ * memory at the point of the call: hosts whose device-memory budget is fixed
+ * up front, or plugins given only an input and an output buffer by a
+ * framework that owns every allocation.
  * The paper has no counterpart: this is a deployment convenience.
  * Same arguments and results as pc_decompress, without the workspace: the
  * scratch space is a fixed 32 MiB array compiled into the library, held on
  * every GPU that loads it until the process exits (enough for fields up to
  * about 16 million points with 8x8x8 blocks).  Returns PC_ERR_CAPACITY,
  * before launching anything, when the container needs more scratch than
- * that.  The first call on each device looks up the array's device address
- * (make it before any stream capture).  All calls share the array: calls
- * that overlap on the GPU race and must be serialized by the caller.
+ * that.  Like pc_decompress, the call reads the header back to the host and
+ * synchronizes the stream.  The first call on each device looks up the
+ * array's device address.  All calls share the array: calls that overlap on
+ * the GPU race and must be serialized by the caller.
  */
 int pc_decompress_noalloc(const void* d_in, size_t in_size, void* d_field, size_t field_cap,
                           size_t dims_out[3], int* dtype_out, void* stream);

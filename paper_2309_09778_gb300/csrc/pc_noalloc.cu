@@ -1,25 +1,24 @@
 // Decompression for callers that cannot allocate device memory.
 //
 // Some callers of this library have no way to obtain device memory when
-// they need to decompress: code that runs while the process's CUDA allocator
-// must not be touched (for example inside a region where cudaMalloc would
-// synchronize the device or break a stream capture), hosts whose memory
-// budget is fixed up front, or plugins handed only an input and an output
-// buffer by a framework that owns all allocations.  pc_decompress_noalloc
-// serves them: it runs the same kernels as pc_decompress, with the scratch
-// space taken from a fixed array compiled into this library.
+// they need to decompress: hosts whose device-memory budget is fixed up
+// front (every byte is handed out before the first call), or plugins given
+// only an input and an output buffer by a framework that owns every
+// allocation.  pc_decompress_noalloc serves them: it runs the same kernels as
+// pc_decompress, with the scratch space taken from a fixed array compiled
+// into this library.  Like pc_decompress it reads the container header back
+// to the host and synchronizes the stream.
 //
 // The array is a file-scope __device__ array of kNoAllocScratchBytes.  Every
 // GPU that loads this library's code for it holds the array until the
 // process exits.  Host code cannot use the array's name as a device address,
 // so the first call on each device looks the address up with
 // cudaGetSymbolAddress (with that device current) and caches it; later calls
-// reuse it.  Because that first call performs this set-up, make it before
-// any stream capture begins.
+// reuse it.
 //
 // Every call shares the one array and it keeps the contents of the last
 // call; the decompression kernels overwrite every scratch word they read and
-// this entry point clears the error word before launching.  Calls whose work
+// pc_decompress clears the error word before launching.  Calls whose work
 // overlaps on the GPU (different streams, or different host threads) race on
 // the array and must be serialized by the caller.
 #include <mutex>
@@ -55,18 +54,10 @@ extern "C" int pc_decompress_noalloc(const void* d_in, size_t in_size, void* d_f
                                      size_t dims_out[3], int* dtype_out, void* stream) {
   if (!d_in || !d_field) return PC_ERR_ARG;
   if (in_size < (size_t)pc::kHdr) return PC_ERR_CORRUPT;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  unsigned char hdr[pc::kHdr];
-  if (cudaMemcpyAsync(hdr, d_in, pc::kHdr, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PC_ERR_CUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
-  size_t dims[3];
-  int dt = 0;
-  size_t need = 0;
-  int st = pc_header_info(hdr, sizeof(hdr), dims, &dt, &need);
-  if (st) return st;
-  if (need > kNoAllocScratchBytes) return PC_ERR_CAPACITY;  // field needs more than the built-in scratch
   void* scratch = nullptr;
-  st = scratch_of_current_device(&scratch);
+  const int st = scratch_of_current_device(&scratch);
   if (st) return st;
+  // pc_decompress refuses, before any launch, a container that needs more
+  // scratch than the array holds (PC_ERR_CAPACITY)
   return pc_decompress(d_in, in_size, d_field, field_cap, dims_out, dtype_out, scratch, kNoAllocScratchBytes, stream);
 }

@@ -41,6 +41,62 @@ def grf(shape, beta: float, seed: int) -> np.ndarray:
     return g
 
 
+def grf_device(shape, beta: float, seed: int, device):
+    """grf() with the Fourier shaping done by torch on `device` (float64).
+
+    The white noise is numpy's Philox draw, as in grf(); the FFTs run on the
+    device so that the 512^3 workloads are made in seconds.  Returns a float64
+    torch tensor on `device`, mean 0 and sd 1.
+    """
+    import torch
+    shape = tuple(int(s) for s in shape)
+    rng = np.random.Generator(np.random.Philox(seed))
+    white = torch.from_numpy(rng.standard_normal(shape)).to(device)
+    spec = torch.fft.rfftn(white)
+    del white
+    k2 = torch.zeros((), dtype=torch.float64, device=device)
+    for ax, n in enumerate(shape):
+        f = torch.fft.rfftfreq(n, dtype=torch.float64, device=device) if ax == len(shape) - 1 else \
+            torch.fft.fftfreq(n, dtype=torch.float64, device=device)
+        k2 = k2 + (f ** 2).reshape([-1 if a == ax else 1 for a in range(len(shape))])
+    amp = torch.where(k2 > 0, k2.clamp_min(1e-300) ** (-beta / 4.0), torch.zeros_like(k2))
+    spec *= amp
+    del amp, k2
+    g = torch.fft.irfftn(spec, s=shape, dim=tuple(range(len(shape))))
+    del spec
+    g -= g.mean()
+    sd = g.std(correction=0)
+    if sd > 0:
+        g /= sd
+    return g
+
+
+def density_velocity_pair(shape, device, seed_density: int = 0, seed_velocity: int = 3):
+    """The 512^3-style pair: positive density exp(1.5 G), G with spectrum k^-2, and a
+    signed velocity-like G with spectrum k^-4; float32 torch tensors on `device`."""
+    import torch
+    rho = torch.exp(1.5 * grf_device(shape, 2.0, seed_density, device)).to(torch.float32)
+    vel = grf_device(shape, 4.0, seed_velocity, device).to(torch.float32)
+    return rho, vel
+
+
+def wide_range_device(shape, beta: float, seed: int, device, decades: float = 8.0, zero_frac: float = 0.01):
+    """wide_range() on the device: |x| = 10^(decades G1 / max|G1|), sign of G2, exact zeros where
+    G3 lies below its quantile; a float64 torch tensor on `device`."""
+    import torch
+    g1 = grf_device(shape, beta, seed, device)
+    m = g1.abs().max()
+    x = torch.pow(10.0, decades * g1 / (m if m > 0 else 1.0))
+    del g1
+    x *= torch.where(grf_device(shape, beta, seed + 1, device) >= 0, 1.0, -1.0)
+    if zero_frac > 0:
+        g3 = grf_device(shape, beta, seed + 2, device)
+        k = max(1, int(round(zero_frac * g3.numel())))
+        thr = torch.kthvalue(g3.reshape(-1).cpu(), k).values.item()
+        x = torch.where(g3 < thr, torch.zeros_like(x), x)
+    return x
+
+
 def signed_lognormal(shape, beta: float, seed: int, log_scale: float = 2.0,
                      zero_frac: float = 0.05, dtype=np.float32) -> np.ndarray:
     """|x| = exp(log_scale * G1), sign from G2, exact zeros where G3 < its quantile."""

@@ -1,9 +1,9 @@
 """Decompression without a caller workspace (pc_decompress_noalloc).
 
-Callers that cannot allocate device memory when they decompress (inside a
-stream capture, under a fixed memory budget, or as a plugin that only gets
-an input and an output buffer) use pc_decompress_noalloc, which takes its
-scratch space from a fixed array built into the library.  This test calls it
+Callers that cannot allocate device memory when they decompress (under a
+device-memory budget fixed up front, or as a plugin that only gets an input
+and an output buffer) use pc_decompress_noalloc, which takes its scratch
+space from a fixed array built into the library.  This test calls it
 through the C ABI and checks that it returns exactly what pc_decompress (with
 a caller workspace) returns, on two calls in a row, and that a container
 needing more scratch than the built-in array is refused before any work.
