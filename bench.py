@@ -1,19 +1,35 @@
 #!/usr/bin/env python
-"""Throughput benchmark of the GB300 compressor on one 100x500x500 float32 field.
+"""Throughput benchmark of the GB300 compressor.
 
-One step = pc_compress + pc_decompress of the field (the whole hot path:
-statistics, constants, transform, prediction, quantization, histogram,
-codebook, packing, and the inverse path).  The field is a seeded synthetic
-log-normal signed Gaussian random field (power spectrum k^-11/3, 2% exact
-zeros) standing in for the paper's SEG-Y volumes, eb_rel = 1e-3, 8x8x8 blocks.
+Headline workload (default): two 512^3 float32 fields, a positive log-normal
+density exp(1.5 G), G with power spectrum k^-2, and a signed velocity-like
+Gaussian random field with spectrum k^-4; eb_rel = 1e-4; 8x8x8 blocks; a
+perceptron over the 13-point causal stencil with hidden widths 32/32, trained
+on the device from 2^20 sampled stencils per field, evaluated in its
+fixed-point (bf16 tensor-core) form, with the Lorenzo predictor as per-block
+fallback.  Both fields together (1.07 GB) are larger than L2.
 
-Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
-bounded sample of the same field instead.
+One step = pc_compress of both fields + pc_decompress of both containers (the
+whole hot path: statistics, constants, transform, prediction, selection,
+quantization, histogram, codebook, packing, and the inverse path).
+
+Secondary workloads (reported inside the same JSON line unless
+--no-secondary): 100x500x500 float32 at eb_rel 1e-3 with the FP32 and the
+fixed-point 7-point 16/16 perceptron; 256x384x384 float64 at eb_rel 1e-5
+(fixed-point 16/16 perceptron, float64 transform); 64^3 float32 at eb_rel 1e-2
+with the FP32 perceptron trained by the oracle.
+
+All fields are seeded synthetic Gaussian random fields standing in for the
+paper's SEG-Y seismic volumes.  Prints one JSON line (rank 0).
+`--impl reference` times the CPU oracle (the reference arm: no reference code
+exists beyond the paper) on bounded samples of the same workload.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -28,29 +44,61 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "compress/decompress GB/s and bits/value at eb_rel, % of HBM roofline, vs FP32 plain"
-SHAPE = (100, 500, 500)
-EB = 1e-3
 BLOCK = (8, 8, 8)
-SAMPLE = (40, 200, 200)  # reference-arm sample per step: a corner sub-volume of the same field
-THR32 = int(0.1 * 2 ** 32)  # 10% of points drawn for training (Section IV.C)
+
+# name -> workload description
+WORKLOADS = {
+    "density_velocity_512": dict(desc="two 512^3 float32 fields: positive log-normal density exp(1.5 G), G ~ k^-2, "
+                                      "and a signed velocity-like GRF ~ k^-4", eb=1e-4, k=13, h1=32, h2=32,
+                                 samples=1 << 20, form="bf16", dtype="f32", train="device"),
+    "grf100x500x500_f32": dict(desc="100x500x500 float32 signed log-normal GRF, k^-11/3, 2% zeros", eb=1e-3, k=7,
+                               h1=16, h2=16, samples=None, form="fp32", dtype="f32", train="device"),
+    "grf256x384x384_f64": dict(desc="256x384x384 float64 GRF k^-3, magnitudes 1e-8..1e8, mixed sign, 1% zeros",
+                               eb=1e-5, k=7, h1=16, h2=16, samples=None, form="bf16", dtype="f64", train="device"),
+    "grf64_f32": dict(desc="64^3 float32 signed log-normal GRF, k^-3, 5% zeros", eb=1e-2, k=7, h1=16, h2=16,
+                      samples=None, form="fp32", dtype="f32", train="oracle"),
+}
+HEADLINE = "density_velocity_512"
+THR10 = int(0.1 * 2 ** 32)  # 10% of points drawn for training (Section IV.C)
 
 
-def field():
+def make_fields(name: str, device):
+    """The workload's fields as device tensors (seeded)."""
+    import torch
     from paper_2309_09778_gb300 import gen
-    return gen.signed_lognormal(SHAPE, 11.0 / 3.0, 0, 2.0, 0.02)
+    if name == "density_velocity_512":
+        return list(gen.density_velocity_pair((512, 512, 512), device))
+    if name == "grf100x500x500_f32":
+        return [torch.from_numpy(gen.signed_lognormal((100, 500, 500), 11.0 / 3.0, 0, 2.0, 0.02)).to(device)]
+    if name == "grf256x384x384_f64":
+        return [gen.wide_range_device((256, 384, 384), 3.0, 0, device, 8.0, 0.01)]
+    if name == "grf64_f32":
+        return [torch.from_numpy(gen.signed_lognormal((64, 64, 64), 3.0, 0, 2.0, 0.05)).to(device)]
+    raise KeyError(name)
 
 
-def peaks():
+def thr_for(shape, samples):
+    """Sampling threshold (of 2^32) for an expected count of `samples` non-anchor points, else 10%."""
+    if not samples:
+        return THR10
+    n = int(np.prod(shape))
+    nb = int(np.prod([-(-s // b) for s, b in zip(shape, BLOCK)]))
+    return min(int(round(samples / (n - nb) * 2 ** 32)), 2 ** 32 - 1)
+
+
+def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                "source": "measured"}
     except Exception:
-        return 6800.0, "fallback"
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms (read only)."""
 
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -99,105 +147,515 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def oracle_predictor(sub: np.ndarray):
-    """The oracle's own training phase on the sample (10% sampling, the 16-model grid)."""
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the cpu_baseline leg and the reference arm).  Workers are
+# spawned, never forked, so that no child inherits a CUDA context.
+# ---------------------------------------------------------------------------
+def oracle_worker(args):
+    sub, eb, k, h1, h2, s_in, w, q = args
     from oracle import oracle as O
-    best, W, s_in, costs = O.train(sub, EB, block=BLOCK, k=7, h1=16, h2=16, seed=0, thr32=THR32)
-    return (W[best], s_in, "mlp_fp32_s7_16x16") if best >= 0 else (None, 0, "lorenzo")
+    O.build()
+    t0 = time.perf_counter()
+    st, blob = O.compress(sub, eb, block=BLOCK, weights=w, stencil=k, h1=h1, h2=h2, s_in=s_in, qnet=q)
+    st2, y = O.decompress(blob)
+    dt = time.perf_counter() - t0
+    if st != 0 or st2 != 0:
+        raise RuntimeError(f"oracle status {st}/{st2}")
+    return sub.nbytes, dt, len(blob)
 
 
-def cpu_oracle_rate(x: np.ndarray, steps: int, predictor=None, shape=SAMPLE):
-    """Time the oracle's compress + decompress on a corner sub-volume of the given shape."""
-    from oracle import oracle as O
-    sub = np.ascontiguousarray(x[: shape[0], : shape[1], : shape[2]])
-    if predictor is None:
-        predictor = oracle_predictor(sub)
-    w, s_in = predictor[0], predictor[1]
-    t = []
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        st, blob = O.compress(sub, EB, block=BLOCK, weights=w, s_in=s_in)
-        st2, y = O.decompress(blob)
-        t.append(time.perf_counter() - t0)
-        assert st == 0 and st2 == 0
-    return sub.nbytes, t, predictor[2]
+def slabs(fields_host, pts_per_slab, count):
+    """`count` distinct corner-aligned sub-volumes of about pts_per_slab points, drawn round-robin from the fields."""
+    out = []
+    for i in range(count):
+        x = fields_host[i % len(fields_host)]
+        Z, Y, X = x.shape
+        sy, sx = min(Y, 128), min(X, 128)
+        dz = max(8, min(Z, (pts_per_slab // (sy * sx)) // 8 * 8))
+        j = i // len(fields_host)
+        z0 = (j * dz) % max(1, Z - dz + 1)
+        out.append(np.ascontiguousarray(x[z0: z0 + dz, :sy, :sx]))
+    return out
 
 
-def run_reference(args, rank: int):
-    if rank != 0:
-        return
-    x = field()
-    nbytes, t, pname = cpu_oracle_rate(x, max(1, args.steps))
-    v = nbytes * len(t) / sum(t) / 1e9
-    sample = f"sub-volume {SAMPLE[0]}x{SAMPLE[1]}x{SAMPLE[2]} of the workload field, compress+decompress per step"
-    line = {"metric": METRIC, "value": v, "unit": "GB/s", "impl": "reference", "n_gpus": args.gpus,
-            "steps": len(t), "warmup": 0, "ms_per_step": 1e3 * sum(t) / len(t), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "grf100x500x500_f32", "eb_rel": EB, "block": list(BLOCK),
-                       "predictor": pname, "training": "oracle training phase on the sample, untimed"},
-            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+def oracle_rate(fields_host, spec, pred, cores: int, pts_per_slab: int, rounds: int = 1):
+    """Oracle compress + decompress on `cores` slabs at once (one process per core), `rounds` times.
+    Returns (GB/s of input, per-round seconds, description)."""
+    eb, k, h1, h2 = spec["eb"], spec["k"], spec["h1"], spec["h2"]
+    s_in, w, q = pred
+    subs = slabs(fields_host, pts_per_slab, cores * rounds)
+    work = [(s, eb, k, h1, h2, s_in, w, q) for s in subs]
+    ctx = mp.get_context("spawn")
+    t_round = []
+    nbytes = 0
+    with ctx.Pool(cores) as pool:
+        # warm the workers (library load, page-in) on tiny sub-volumes
+        tiny = [(np.ascontiguousarray(subs[0][:8, :16, :16]),) + w[1:] for w in work[:cores]]
+        pool.map(oracle_worker, tiny)
+        for r in range(rounds):
+            t0 = time.perf_counter()
+            res = pool.map(oracle_worker, work[r * cores:(r + 1) * cores])
+            t_round.append(time.perf_counter() - t0)
+            nbytes += sum(b for b, _, _ in res)
+    shp = subs[0].shape
+    desc = (f"{cores} process(es) x 1 sub-volume {shp[0]}x{shp[1]}x{shp[2]} of the workload fields per round, "
+            f"{rounds} round(s), compress + decompress with the device-chosen predictor")
+    return nbytes / sum(t_round) / 1e9, t_round, desc
 
 
-# Kernels behind each profiled stage (the codebook stage launches k_codebook and k_cb_assign; the decoder's
-# scan stage k_dec_chunksum, k_dec_chunkscan and k_dec_blockoff).
+# ---------------------------------------------------------------------------
+# Device side.
+# ---------------------------------------------------------------------------
+def sha_of(*paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+# DRAM bytes (read + write) per launch of a kernel, from an ncu capture of the
+# kernel on the named workload and form; each entry carries the hash of the
+# sources it was captured from and is dropped (traffic null) once they change.
+TRAFFIC = {
+    # (workload, stage, form): (bytes per launch, sha of the sources, profile summary)
+}
+STAGE_SOURCES = {
+    "compress": ("paper_2309_09778_gb300/csrc/pc_compress.cu", "paper_2309_09778_gb300/csrc/pc_qmlp.cuh",
+                 "paper_2309_09778_gb300/csrc/pc_device.cuh"),
+    "recon": ("paper_2309_09778_gb300/csrc/pc_decompress.cu", "paper_2309_09778_gb300/csrc/pc_qmlp.cuh",
+              "paper_2309_09778_gb300/csrc/pc_device.cuh"),
+}
+# kernels behind each profiled stage (the codebook stage launches k_codebook and k_cb_assign; the decoder's
+# scan stage k_dec_chunksum, k_dec_chunkscan and k_dec_blockoff)
 KERNELS_PER_STAGE = {"codebook": 2, "dec_scan": 3}
 
-# DRAM bytes (read + write) of one launch, from the ncu capture in profiles/k_recon_c2_fp32.md
-# (FP32 form of this workload); valid while that kernel is unchanged.
-TRAFFIC_PER_LAUNCH = {("recon", "fp32"): 55235584 + 43935488}
 
-# FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop (FMA) per cycle.
-SMS, FP32_LANES = 152, 128
-
-
-def perceptron_flops_per_point(k: int, h1: int, h2: int) -> int:
-    """2 flop per weight multiply-accumulate of one forward pass (biases initialise the sums)."""
-    return 2 * (k * h1 + (h1 * h2 + h2 if h2 else h1))
+def traffic_for(workload, stage, form):
+    e = TRAFFIC.get((workload, stage, form))
+    if not e or stage not in STAGE_SOURCES:
+        return None
+    return e[0] if sha_of(*STAGE_SOURCES[stage]) == e[1] else None
 
 
-def block_census(blob: bytes, shape, block):
-    """Per block: perceptron flag, points that are neither anchor nor balance point (from the container)."""
+def net_flops(k, h1, h2, form):
+    """Algorithmic flops of one forward pass: 2 per multiply-add; the fixed-point form multiplies
+    every weight by two 8-bit limbs of its input."""
+    macs = k * h1 + (h1 * h2 + h2 if h2 else h1)
+    return 2 * macs * (2 if form == "bf16" else 1)
+
+
+def block_census(blob: bytes, shape):
+    """Per block: perceptron flag and the points that are neither anchor nor balance point."""
     import struct
     _, off_bb, off_bn, _, _ = struct.unpack_from("<5Q", blob, 176)
-    nb = [-(-s // b) for s, b in zip(shape, block)]
+    nb = [-(-s // b) for s, b in zip(shape, BLOCK)]
     nblocks = nb[0] * nb[1] * nb[2]
     flags = np.frombuffer(blob, "<u4", nblocks, off_bb) >> 31
     nout = np.frombuffer(blob, "<u2", nblocks, off_bn).astype(np.int64)
-    ext = [np.minimum(b, s - np.arange(n) * b) for s, b, n in zip(shape, block, nb)]
+    ext = [np.minimum(b, s - np.arange(n) * b) for s, b, n in zip(shape, BLOCK, nb)]
     pts = (ext[0][:, None, None] * ext[1][None, :, None] * ext[2][None, None, :]).reshape(-1)
     return flags.astype(bool), pts - nout
 
 
-def roofline(stage: str, ms: float, n: int, comp_bytes: int, nn_pts: int, fpp: int, sm_mhz: float, hbm: float,
-             hbm_kind: str):
-    """Algorithmic work of one launch of `stage` against its bounding roof."""
-    alu_peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
-    if stage in ("recon", "compress") and fpp:
-        pts = nn_pts if stage == "recon" else n
-        flops = fpp * pts
+def train_predictors(torch, pc, fields, spec, dev):
+    """Training phase per field (Section IV.C): on the device (or by the oracle), then the fixed-point
+    form of the chosen network.  Returns one dict per field."""
+    out = []
+    k, h1, h2, eb = spec["k"], spec["h1"], spec["h2"], spec["eb"]
+    lrs, lams = pc.default_grid()
+    for d in fields:
+        shape = tuple(d.shape)
+        dt = pc.PC_F32 if d.dtype == torch.float32 else pc.PC_F64
+        thr32 = thr_for(shape, spec["samples"])
+        tp = pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_FP32, stencil=k, hidden=(h1, h2))
+        ws = torch.empty(pc.pc_train_workspace_size(shape, dt, tp, thr32, lrs.size), dtype=torch.uint8, device=dev)
+        info = {"thr32": thr32, "samples_expected": thr32 / 2 ** 32 * (d.numel() - d.numel() // 512)}
+        if spec["train"] == "oracle":
+            from oracle import oracle as O
+            x = d.cpu().numpy()
+            t0 = time.perf_counter()
+            chosen, W, s_in, costs = O.train(x, eb, block=BLOCK, k=k, h1=h1, h2=h2, seed=0, thr32=thr32)
+            info["train_s"] = time.perf_counter() - t0
+            info["trained_by"] = "oracle"
+        else:
+            pc.pc_train(d, tp, 0, thr32, lrs, lams, ws)  # warm-up (module load, first launches)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            W, s_in, chosen, costs = pc.pc_train(d, tp, 0, thr32, lrs, lams, ws)
+            torch.cuda.synchronize()
+            info["train_s"] = time.perf_counter() - t0
+            info["trained_by"] = "device"
+        info.update(chosen=int(chosen), s_in=int(s_in), val_costs=[int(c) for c in costs])
+        w = W[chosen] if chosen >= 0 else None
+        info["w"] = w
+        info["q"] = None
+        info["quant_s"] = None
+        if w is not None:
+            p32 = pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_FP32, stencil=k, hidden=(h1, h2), s_in=s_in,
+                                 weights=w)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info["q"] = pc.pc_quantize(d, p32, 0, thr32, ws)
+            torch.cuda.synchronize()
+            info["quant_s"] = time.perf_counter() - t0
+        del ws
+        out.append(info)
+    return out
+
+
+def params_for(pc, spec, info, form):
+    eb, k, h1, h2 = spec["eb"], spec["k"], spec["h1"], spec["h2"]
+    if info["w"] is None:
+        return pc.make_params(eb, BLOCK), "lorenzo"
+    if form == "bf16":
+        return pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_BF16, stencil=k, hidden=(h1, h2), s_in=info["s_in"],
+                              qnet=info["q"]), f"mlp_bf16_fixed_point_s{k}_{h1}x{h2}"
+    if form == "lorenzo":
+        return pc.make_params(eb, BLOCK), "lorenzo"
+    return pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_FP32, stencil=k, hidden=(h1, h2), s_in=info["s_in"],
+                          weights=info["w"]), f"mlp_fp32_s{k}_{h1}x{h2}"
+
+
+class Runner:
+    """Buffers for compressing every field and decompressing every container of one workload."""
+
+    def __init__(self, torch, pc, fields, params, dev):
+        self.torch, self.pc, self.fields, self.params = torch, pc, fields, params
+        self.dt = [pc.PC_F32 if d.dtype == torch.float32 else pc.PC_F64 for d in fields]
+        self.out = [torch.empty(pc.pc_compress_bound(tuple(d.shape), t, p), dtype=torch.uint8, device=dev)
+                    for d, t, p in zip(fields, self.dt, params)]
+        self.wsc = [torch.empty(pc.pc_compress_workspace_size(tuple(d.shape), t, p), dtype=torch.uint8, device=dev)
+                    for d, t, p in zip(fields, self.dt, params)]
+        self.y = [torch.empty_like(d) for d in fields]
+        self.size = [self.compress(i) for i in range(len(fields))]
+        self.wsd = []
+        for o in self.out:
+            _, _, wsb = pc.pc_header_info(o[:256].cpu().numpy().tobytes())
+            self.wsd.append(torch.empty(max(wsb, 1), dtype=torch.uint8, device=dev))
+
+    def compress(self, i, stream=None):
+        return self.pc.pc_compress(self.fields[i], self.params[i], self.out[i], self.wsc[i], stream)
+
+    def decompress(self, i, stream=None):
+        self.pc.pc_decompress(self.out[i], self.size[i], self.y[i], self.wsd[i], stream)
+
+    def step(self, stream, ev):
+        torch = self.torch
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        for i in range(len(self.fields)):
+            self.size[i] = self.compress(i, stream)
+        e[1].record(stream)
+        for i in range(len(self.fields)):
+            self.decompress(i, stream)
+        e[2].record(stream)
+        ev.append(e)
+
+    def bound_held(self, eb):
+        ok = True
+        for d, y in zip(self.fields, self.y):
+            ok &= bool(((y.double() - d.double()).abs() <= eb * d.double().abs()).all().item())
+        return ok
+
+    def free(self):
+        self.out = self.wsc = self.y = self.wsd = None
+
+
+def measure(torch, pc, fields, spec, params, steps, warmup, stream, flush, dist=None):
+    """Warm-up, bound check, then `steps` timed steps (CUDA events on the launching stream, L2 flushed
+    between steps).  Returns (result dict, runner)."""
+    r = Runner(torch, pc, fields, params, fields[0].device)
+    for _ in range(warmup):
+        flush.zero_()
+        r.step(stream, [])
+    torch.cuda.synchronize()
+    ok = r.bound_held(spec["eb"])
+    pc.pc_profile_enable(True)
+    pc.pc_profile_read()
+    ev = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        flush.zero_()
+        r.step(stream, ev)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - t0
+    prof = pc.pc_profile_read()
+    pc.pc_profile_enable(False)
+    tc = sum(a.elapsed_time(b) for a, b, _ in ev) / len(ev)
+    td = sum(b.elapsed_time(c) for _, b, c in ev) / len(ev)
+    if dist:
+        tt = torch.tensor([tc, td], device=fields[0].device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tc, td = tt.tolist()
+    nbytes = sum(d.numel() * d.element_size() for d in fields)
+    npts = sum(d.numel() for d in fields)
+    out_bytes = sum(r.size)
+    stages = {k: (v[0] / steps, v[1] / steps) for k, v in prof.items() if v[1] > 0}
+    res = {"compress_ms": tc, "decompress_ms": td, "ms_per_step": tc + td, "input_bytes": nbytes, "points": npts,
+           "compressed_bytes": out_bytes, "bits_per_value": 8.0 * out_bytes / npts, "bound_held": ok,
+           "compress_gbs": nbytes / (tc * 1e6), "decompress_gbs": nbytes / (td * 1e6),
+           "stages_ms_per_step": {k: v[0] for k, v in stages.items()},
+           "launches_per_step": sum(v[1] * KERNELS_PER_STAGE.get(k, 1) for k, v in stages.items()),
+           "stage_launches_per_step": {k: v[1] for k, v in stages.items()}, "wall_s_timed": wall}
+    return res, r
+
+
+def hbm_fractions(res, peak):
+    """Whole-step HBM roofline: compress must read the field twice (the global extrema come before any
+    transform) and write the container; decompress reads the container and writes the field."""
+    n, out, tc, td = res["input_bytes"], res["compressed_bytes"], res["compress_ms"], res["decompress_ms"]
+    c = (2 * n + out) / (tc * 1e6)
+    c1 = (n + out) / (tc * 1e6)
+    d = (out + n) / (td * 1e6)
+    return {"peak_gbs": peak["hbm_gbs"], "peak_source": peak["source"],
+            "compress": {"algorithmic_bytes": 2 * n + out, "achieved_gbs": c, "frac": c / peak["hbm_gbs"],
+                         "single_read_frac": c1 / peak["hbm_gbs"]},
+            "decompress": {"algorithmic_bytes": out + n, "achieved_gbs": d, "frac": d / peak["hbm_gbs"]}}
+
+
+def stage_roofline(workload, stage, ms, res, spec, form, nn_pts, nsm, sm_mhz, peak):
+    """The dominant stage against its bounding roof, from its algorithmic work per launch."""
+    n_pts = res["points"]
+    ts = res["input_bytes"] // n_pts
+    nf = len(spec.get("_fields", [])) or 1
+    if stage in ("compress", "recon") and form in ("fp32", "bf16"):
+        pts = nn_pts if stage == "recon" else n_pts
+        flops = net_flops(spec["k"], spec["h1"], spec["h2"], form) * pts / nf
         a = flops / (ms * 1e-3) / 1e12
-        return {"kernel": stage, "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": a / alu_peak, "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 flop x "
-                f"{sm_mhz:.0f} MHz", "algorithmic_flops_per_launch": flops, "avg_launch_ms": ms}
-    alg = {"stats": 4 * n, "compress": 4 * n + 2 * n, "pack": 2 * n + comp_bytes, "huff_decode": comp_bytes + 2 * n,
-           "recon": 2 * n + 4 * n}.get(stage, 0)
+        if form == "fp32":
+            pk = nsm * 128 * 2 * sm_mhz * 1e6 / 1e12
+            src = f"derived: {nsm} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz"
+            bound = "alu"
+        else:
+            pk = peak["bf16_tflops_sustained"]
+            src = f"{peak['source']} bf16 dense, sustained"
+            bound = "tensor"
+        return {"kernel": stage, "bound": bound, "achieved": a, "peak": pk, "unit": "TFLOP/s", "frac": a / pk,
+                "traffic": traffic_for(workload, stage, form), "peak_source": src,
+                "algorithmic_flops_per_launch": flops, "avg_launch_ms": ms}
+    alg = {"stats": ts * n_pts, "compress": ts * n_pts + 2 * n_pts, "pack": 2 * n_pts + res["compressed_bytes"],
+           "huff_decode": res["compressed_bytes"] + 2 * n_pts, "recon": 2 * n_pts + ts * n_pts}.get(stage, 0) / nf
     a = alg / (ms * 1e6) if alg else None
-    return {"kernel": stage, "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
-            "frac": (a / hbm) if a else None, "peak_source": hbm_kind, "algorithmic_bytes_per_launch": alg,
-            "avg_launch_ms": ms}
+    return {"kernel": stage, "bound": "hbm", "achieved": a, "peak": peak["hbm_gbs"], "unit": "GB/s",
+            "frac": (a / peak["hbm_gbs"]) if a else None, "traffic": traffic_for(workload, stage, form),
+            "peak_source": peak["source"], "algorithmic_bytes_per_launch": alg, "avg_launch_ms": ms}
+
+
+def e2e_rate(torch, pc, r, steps):
+    """The user's call with HOST buffers: pc_compress_host + pc_decompress_host of every field, pinned host
+    memory, host<->device copies inside the timed region."""
+    hosts = [d.cpu().pin_memory() for d in r.fields]
+    outs = [torch.empty(o.numel(), dtype=torch.uint8).pin_memory() for o in r.out]
+    ys = [torch.empty_like(h).pin_memory() for h in hosts]
+    stage = [torch.empty_like(d) for d in r.fields]
+    hf = [h.numpy() for h in hosts]
+    ho = [o.numpy() for o in outs]
+    hy = [y.numpy() for y in ys]
+    t = []
+    sizes = [0] * len(hf)
+    for it in range(2 + steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(len(hf)):
+            sizes[i] = pc.pc_compress_host(hf[i], r.params[i], ho[i], stage[i], r.out[i], r.wsc[i])
+            pc.pc_decompress_host(ho[i], sizes[i], hy[i], r.out[i], stage[i], r.wsd[i])
+        if it >= 2:
+            t.append(time.perf_counter() - t0)
+    same = all(np.array_equal(hy[i].view(np.uint8), r.y[i].cpu().numpy().view(np.uint8)) for i in range(len(hf)))
+    nbytes = sum(h.nbytes for h in hf)
+    return {"value": nbytes / statistics.median(t) / 1e9, "unit": "GB/s",
+            "h2d_bytes_per_step": nbytes + sum(sizes), "d2h_bytes_per_step": sum(sizes) + nbytes,
+            "matches_device_path": bool(same)}, hosts
+
+
+def e2e_with_training(torch, pc, hosts, spec, form, dev):
+    """The whole user path from host memory, the learned part included: host->device copy, device training,
+    the fixed-point form (bf16), compression, container to host, then host-buffer decompression."""
+    k, h1, h2, eb = spec["k"], spec["h1"], spec["h2"], spec["eb"]
+    lrs, lams = pc.default_grid()
+    bufs = []
+    for h in hosts:
+        shape = tuple(h.shape)
+        dt = pc.PC_F32 if h.dtype == torch.float32 else pc.PC_F64
+        thr32 = thr_for(shape, spec["samples"])
+        tp = pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_FP32, stencil=k, hidden=(h1, h2))
+        pmax = pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_FP32, stencil=k, hidden=(h1, h2), s_in=0,
+                              weights=np.zeros(pc.pc_mlp_nweights(k, h1, h2), np.float32))
+        bufs.append(dict(
+            d=torch.empty(shape, dtype=h.dtype, device=dev), thr32=thr32, tp=tp,
+            wst=torch.empty(pc.pc_train_workspace_size(shape, dt, tp, thr32, lrs.size), dtype=torch.uint8, device=dev),
+            out=torch.empty(pc.pc_compress_bound(shape, dt, pmax) + 65536, dtype=torch.uint8, device=dev),
+            wsc=torch.empty(pc.pc_compress_workspace_size(shape, dt, pmax), dtype=torch.uint8, device=dev),
+            ho=torch.empty(pc.pc_compress_bound(shape, dt, pmax) + 65536, dtype=torch.uint8).pin_memory(),
+            hy=torch.empty_like(h).pin_memory()))
+    t = []
+    for it in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for h, b in zip(hosts, bufs):
+            b["d"].copy_(h, non_blocking=True)
+            W, s_in, chosen, _ = pc.pc_train(b["d"], b["tp"], 0, b["thr32"], lrs, lams, b["wst"])
+            if chosen < 0:
+                p = pc.make_params(eb, BLOCK)
+            else:
+                p = pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_FP32, stencil=k, hidden=(h1, h2), s_in=s_in,
+                                   weights=W[chosen])
+                if form == "bf16":
+                    q = pc.pc_quantize(b["d"], p, 0, b["thr32"], b["wst"])
+                    p = pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_BF16, stencil=k, hidden=(h1, h2), s_in=s_in,
+                                       qnet=q)
+            sz = pc.pc_compress(b["d"], p, b["out"], b["wsc"])
+            b["ho"][:sz].copy_(b["out"][:sz])
+            _, _, wsb = pc.pc_header_info(b["ho"][:256].numpy().tobytes())
+            wsd = b.get("wsd")
+            if wsd is None or wsd.numel() < wsb:
+                wsd = b["wsd"] = torch.empty(wsb, dtype=torch.uint8, device=dev)
+            pc.pc_decompress_host(b["ho"].numpy(), sz, b["hy"].numpy(), b["out"], b["d"], wsd)
+        if it >= 1:
+            t.append(time.perf_counter() - t0)
+    nbytes = sum(h.numel() * h.element_size() for h in hosts)
+    return {"value": nbytes / min(t) / 1e9, "unit": "GB/s", "seconds": min(t),
+            "includes": "H2D, device training of 16 models, fixed-point form, compress, D2H, host-buffer decompress"}
+
+
+def cpu_baseline(fields_host, spec, info, form, cores_all, pts_per_slab):
+    """The oracle as it stands on the host cores: all of them, and one."""
+    w = info["w"] if form == "fp32" else None
+    q = info["q"] if form == "bf16" else None
+    pred = (info["s_in"] if (w is not None or q is not None) else 0, w, q)
+    v_all, t_all, desc_all = oracle_rate(fields_host, spec, pred, cores_all, pts_per_slab, rounds=1)
+    v_one, t_one, desc_one = oracle_rate(fields_host, spec, pred, 1, pts_per_slab, rounds=1)
+    return {"value": v_all, "unit": "GB/s", "cores": cores_all, "kind": "oracle", "sample": desc_all,
+            "seconds": sum(t_all), "one_core": {"value": v_one, "cores": 1, "sample": desc_one,
+                                                 "seconds": sum(t_one)}}
+
+
+def run_workload(torch, pc, name, args, dev, stream, flush, peak, nsm, dist=None, headline=False, clk=None):
+    spec = dict(WORKLOADS[name])
+    fields = make_fields(name, dev)
+    spec["_fields"] = fields
+    infos = train_predictors(torch, pc, fields, spec, dev)
+    form = args.form if (headline and args.form) else spec["form"]
+    if infos[0]["w"] is None or (form == "bf16" and infos[0]["q"] is None):
+        form = "fp32" if infos[0]["w"] is not None else "lorenzo"
+    params, pnames = zip(*[params_for(pc, spec, inf, form) for inf in infos])
+    steps = args.steps if headline else max(3, min(args.steps, 10))
+    if clk:
+        clk.start()
+        time.sleep(0.5)
+    res, r = measure(torch, pc, fields, spec, list(params), steps, args.warmup, stream, flush, dist)
+    clocks = clk.stop() if clk else None
+    res["predictor"] = sorted(set(pnames))
+    res["form"] = form
+    res["hbm_roofline"] = hbm_fractions(res, peak)
+    # perceptron-predicted points (the recon stage's perceptron work)
+    nn_pts = 0
+    nn_blocks = []
+    for i, d in enumerate(fields):
+        blob = r.out[i][: r.size[i]].cpu().numpy().tobytes()
+        flags, free_pts = block_census(blob, tuple(d.shape))
+        nn_pts += int(free_pts[flags].sum())
+        nn_blocks.append(float(flags.mean()))
+    res["perceptron_blocks_fraction"] = nn_blocks
+    res["perceptron_points"] = nn_pts
+    st = res["stages_ms_per_step"]
+    dom = max(st, key=lambda k: st[k])
+    nlaunch = res["stage_launches_per_step"][dom]
+    sm_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    res["roofline"] = stage_roofline(name, dom, st[dom] / nlaunch, res, spec, form, nn_pts / len(fields), nsm,
+                                     sm_mhz, peak)
+    res["training"] = [{k: v for k, v in inf.items() if k not in ("w", "q")} for inf in infos]
+    res["training_seconds_total"] = sum(inf["train_s"] for inf in infos) + sum(inf["quant_s"] or 0 for inf in infos)
+    out = {"res": res, "runner": r, "infos": infos, "spec": spec, "form": form, "clocks": clocks}
+    return out
+
+
+def form_compare(torch, pc, w, args, stream, flush):
+    """The same workload with the other predictor forms (bits/value and throughput), for the
+    FP32-vs-fixed-point comparison and the Lorenzo-only fallback."""
+    spec, infos, fields = w["spec"], w["infos"], w["spec"]["_fields"]
+    forms = {}
+    for form in ("fp32", "bf16", "lorenzo"):
+        if form != "lorenzo" and (infos[0]["w"] is None or (form == "bf16" and infos[0]["q"] is None)):
+            continue
+        params = [params_for(pc, spec, inf, form)[0] for inf in infos]
+        res, r = measure(torch, pc, fields, spec, params, max(3, min(args.steps, 8)), 2, stream, flush)
+        r.free()
+        forms[form] = {k: res[k] for k in ("compress_gbs", "decompress_gbs", "bits_per_value", "bound_held",
+                                           "compress_ms", "decompress_ms", "stages_ms_per_step")}
+    if "fp32" in forms and "bf16" in forms:
+        forms["bf16_bits_vs_fp32"] = forms["bf16"]["bits_per_value"] / forms["fp32"]["bits_per_value"] - 1.0
+    if "lorenzo" in forms:
+        for f in ("fp32", "bf16"):
+            if f in forms:
+                forms[f"{f}_bits_vs_lorenzo"] = forms[f]["bits_per_value"] / forms["lorenzo"]["bits_per_value"] - 1.0
+    return forms
+
+
+def summary(w):
+    res = w["res"]
+    keep = ("compress_gbs", "decompress_gbs", "bits_per_value", "bound_held", "compress_ms", "decompress_ms",
+            "predictor", "form", "hbm_roofline", "roofline", "perceptron_blocks_fraction", "training_seconds_total")
+    return {k: res[k] for k in keep}
+
+
+def run_reference(args, rank: int):
+    """The reference arm: the oracle, as it stands, on the host cores, on bounded samples of the headline
+    workload (the same recipe at a sub-volume size), with the oracle's own training phase (untimed)."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2309_09778_gb300 import gen
+    O.build()
+    spec = dict(WORKLOADS[HEADLINE])
+    shp = (32, 128, 128)
+    fields = [np.exp(1.5 * gen.grf(shp, 2.0, 0)).astype(np.float32), gen.grf(shp, 4.0, 3).astype(np.float32)]
+    best, W, s_in, _ = O.train(fields[0], spec["eb"], block=BLOCK, k=spec["k"], h1=spec["h1"], h2=spec["h2"], seed=0)
+    w = W[best] if best >= 0 else None
+    q = O.quantize(fields[0], spec["eb"], w, s_in, block=BLOCK, k=spec["k"], h1=spec["h1"], h2=spec["h2"]) \
+        if w is not None else None
+    cores = os.cpu_count() or 1
+    pred = (s_in if w is not None else 0, None, q)
+    for _ in range(args.warmup):
+        oracle_rate(fields, spec, pred, cores, shp[0] * shp[1] * shp[2], rounds=1)
+    ts = []
+    nbytes = 0
+    desc = ""
+    for _ in range(max(1, args.steps)):
+        v, t, desc = oracle_rate(fields, spec, pred, cores, shp[0] * shp[1] * shp[2], rounds=1)
+        ts.append(sum(t))
+        nbytes += v * sum(t) * 1e9
+    v = nbytes / sum(ts) / 1e9
+    line = {"metric": METRIC, "value": v, "unit": "GB/s", "impl": "reference", "n_gpus": args.gpus,
+            "steps": len(ts), "warmup": args.warmup, "ms_per_step": 1e3 * sum(ts) / len(ts),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": HEADLINE, "eb_rel": spec["eb"], "block": list(BLOCK),
+                       "predictor": f"mlp_bf16_fixed_point_s{spec['k']}_{spec['h1']}x{spec['h2']} (oracle-trained "
+                                    f"on a {shp[0]}x{shp[1]}x{shp[2]} density sample)" if q is not None else "lorenzo",
+                       "sample": f"{shp[0]}x{shp[1]}x{shp[2]} fields of the same recipe (density and velocity)"},
+            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=HEADLINE, choices=sorted(WORKLOADS))
+    ap.add_argument("--form", default=None, choices=["bf16", "fp32", "lorenzo"],
+                    help="predictor form of the timed step (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", default="fp32", choices=["bf16", "fp32"],
-                    help="perceptron form of the timed step (the other form is timed beside it)")
+    ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -217,193 +675,78 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    x = field()
-    n = x.size
-    nbytes = x.nbytes
-    d = torch.from_numpy(x).to(dev)
-    # training phase (Section IV.C / V): on the device, before compression, timed separately
-    tparams = pc.make_params(EB, BLOCK, pred=pc.PC_PRED_MLP_FP32, stencil=7, hidden=(16, 16))
-    lrs, lams = pc.default_grid()
-    tws = torch.empty(pc.pc_train_workspace_size(SHAPE, pc.PC_F32, tparams, THR32, lrs.size), dtype=torch.uint8,
-                      device=dev)
-    pc.pc_train(d, tparams, 0, THR32, lrs, lams, tws)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    W, s_in, chosen, tcosts = pc.pc_train(d, tparams, 0, THR32, lrs, lams, tws)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
-    w = W[chosen] if chosen >= 0 else None
-    # fixed-point (BF16 tensor-core) form of the chosen perceptron, from the same samples
-    q = None
-    quant_s = None
-    p32 = pc.make_params(EB, BLOCK, pred=pc.PC_PRED_MLP_FP32, stencil=7, hidden=(16, 16), s_in=s_in, weights=w)
-    if w is not None:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        q = pc.pc_quantize(d, p32, 0, THR32, tws)
-        torch.cuda.synchronize()
-        quant_s = time.perf_counter() - t0
-    del tws
-    pbf = pc.make_params(EB, BLOCK, pred=pc.PC_PRED_MLP_BF16, stencil=7, hidden=(16, 16), s_in=s_in, qnet=q)
-    if w is None:
-        pname, params = "lorenzo", pc.make_params(EB, BLOCK)
-    elif args.form == "bf16":
-        pname, params = "mlp_bf16_tensorcore_s7_16x16", pbf
-    else:
-        pname, params = "mlp_fp32_s7_16x16", p32
-    lz_size = pc.compress(d, pc.make_params(EB, BLOCK)).numel()
-    cap = pc.pc_compress_bound(SHAPE, pc.PC_F32, params)
-    out = torch.empty(cap, dtype=torch.uint8, device=dev)
-    wsc = torch.empty(pc.pc_compress_workspace_size(SHAPE, pc.PC_F32, params), dtype=torch.uint8, device=dev)
-    y = torch.empty_like(d)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    peak = measured_peaks()
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     stream = torch.cuda.current_stream(dev)
-    size = pc.pc_compress(d, params, out, wsc)
-    _, _, wsb = pc.pc_header_info(out[:256].cpu().numpy().tobytes())
-    wsd = torch.empty(wsb, dtype=torch.uint8, device=dev)
-
-    def step(timing):
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    clk = ClockSampler(local)
+    head = run_workload(torch, pc, args.workload, args, dev, stream, flush, peak, nsm, dist, headline=True, clk=clk)
+    res, spec, r = head["res"], head["spec"], head["runner"]
+    forms = {} if args.no_forms else None
+    e2e, hosts = e2e_rate(torch, pc, r, max(3, min(args.steps, 10)))
+    e2e_t = e2e_with_training(torch, pc, hosts, spec, head["form"], dev)
+    r.free()
+    if not args.no_forms:
+        forms = form_compare(torch, pc, head, args, stream, flush)
+    # plain FP32: a device copy of the fields at HBM speed
+    copy_gbs = []
+    for d in spec["_fields"]:
+        dst = torch.empty_like(d)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         flush.zero_()
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        e0.record(stream)
-        sz = pc.pc_compress(d, params, out, wsc, stream)
-        e1.record(stream)
-        pc.pc_decompress(out, sz, y, wsd, stream)
-        e2.record(stream)
-        timing.append((e0, e1, e2))
-        return sz
-
-    for _ in range(args.warmup):
-        step([])
-    torch.cuda.synchronize()
-    ok = bool(((y.double() - d.double()).abs() <= EB * d.double().abs()).all().item())
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.5)  # let the sampler start before the timed region
-    pc.pc_profile_enable(True)
-    pc.pc_profile_read()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ev = []
-    for _ in range(args.steps):
-        size = step(ev)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    wall = time.perf_counter() - t0
-    prof = pc.pc_profile_read()
-    pc.pc_profile_enable(False)
-    clk = clocks.stop()
-    tc = sum(a.elapsed_time(b) for a, b, _ in ev) / len(ev)
-    td = sum(b.elapsed_time(c) for _, b, c in ev) / len(ev)
-    t_step = tc + td
-    if dist:
-        tt = torch.tensor([t_step, tc, td], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step, tc, td = tt.tolist()
-
-    # end to end through the host-buffer entry points (pinned host memory)
-    h_field = torch.from_numpy(x).pin_memory()
-    h_out = torch.empty(cap, dtype=torch.uint8).pin_memory()
-    h_y = torch.empty(SHAPE, dtype=torch.float32).pin_memory()
-    dstage = torch.empty_like(d)
-    hf, ho, hy = h_field.numpy(), h_out.numpy(), h_y.numpy()
-    for _ in range(2):
-        sz = pc.pc_compress_host(hf, params, ho, dstage, out, wsc)
-        pc.pc_decompress_host(ho, sz, hy, out, dstage, wsd)
-    te = []
-    for _ in range(max(3, args.steps // 2)):
-        flush.zero_()
+        c0.record(stream)
+        for _ in range(5):
+            dst.copy_(d)
+        c1.record(stream)
         torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        sz = pc.pc_compress_host(hf, params, ho, dstage, out, wsc)
-        pc.pc_decompress_host(ho, sz, hy, out, dstage, wsd)
-        te.append(time.perf_counter() - t1)
-    e2e_ok = np.array_equal(hy.view(np.uint32), y.cpu().numpy().view(np.uint32))
-
-    # the other perceptron form on the same field, for the FP32 vs BF16 comparison
-    forms = {}
-    if w is not None:
-        for fname, fp in (("bf16", pbf), ("fp32", p32)):
-            ws2 = torch.empty(pc.pc_compress_workspace_size(SHAPE, pc.PC_F32, fp), dtype=torch.uint8, device=dev)
-            o2 = torch.empty(pc.pc_compress_bound(SHAPE, pc.PC_F32, fp), dtype=torch.uint8, device=dev)
-            tcs, tds = [], []
-            for it in range(3 + min(args.steps, 40)):
-                flush.zero_()
-                a, b, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-                a.record(stream)
-                sz2 = pc.pc_compress(d, fp, o2, ws2, stream)
-                b.record(stream)
-                pc.pc_decompress(o2, sz2, y, wsd, stream)
-                c2.record(stream)
-                torch.cuda.synchronize()
-                if it >= 3:
-                    tcs.append(a.elapsed_time(b))
-                    tds.append(b.elapsed_time(c2))
-            okf = bool(((y.double() - d.double()).abs() <= EB * d.double().abs()).all().item())
-            forms[fname] = {"compress_gbs": nbytes / (statistics.median(tcs) * 1e6),
-                            "decompress_gbs": nbytes / (statistics.median(tds) * 1e6),
-                            "bits_per_value": 8.0 * sz2 / n, "bound_held": okf}
-            del ws2, o2
-        forms["bf16_size_vs_fp32"] = forms["bf16"]["bits_per_value"] / forms["fp32"]["bits_per_value"] - 1.0
-
-    # plain FP32: a device copy of the field at HBM speed
-    dst = torch.empty_like(d)
-    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    flush.zero_()
-    c0.record(stream)
-    for _ in range(5):
-        dst.copy_(d)
-    c1.record(stream)
-    torch.cuda.synchronize()
-    copy_gbs = 2 * nbytes * 5 / (c0.elapsed_time(c1) * 1e6)
-
-    peak, peak_kind = peaks()
-    stages = {k: v for k, v in prof.items() if v[1] > 0}
-    dom = max(stages, key=lambda k: stages[k][0])
-    dom_ms = stages[dom][0] / stages[dom][1]
-    blob = out[:size].cpu().numpy().tobytes()
-    nnflag, free_pts = block_census(blob, SHAPE, BLOCK)
-    nn_pts = int(free_pts[nnflag].sum())
-    fpp = perceptron_flops_per_point(7, 16, 16) if (w is not None and args.form == "fp32") else 0
-    bpv = 8.0 * size / n
-    launches = sum(v[1] * KERNELS_PER_STAGE.get(k, 1) for k, v in stages.items())
-
+        copy_gbs.append(2 * d.numel() * d.element_size() * 5 / (c0.elapsed_time(c1) * 1e6))
+        del dst
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        fh = [h.numpy() for h in hosts]
+        cpu = cpu_baseline(fh, spec, head["infos"][0], head["form"], os.cpu_count() or 1,
+                           (32 * 128 * 128) if spec["k"] == 13 else (64 * 128 * 128))
+    del hosts
+    spec.pop("_fields")
+    torch.cuda.empty_cache()
+    secondary = {}
+    if world == 1 and not args.no_secondary:
+        for name in WORKLOADS:
+            if name == args.workload:
+                continue
+            w = run_workload(torch, pc, name, args, dev, stream, flush, peak, nsm)
+            w["runner"].free()
+            secondary[name] = summary(w)
+            if name == "grf100x500x500_f32" and not args.no_forms:
+                secondary[name]["forms"] = form_compare(torch, pc, w, args, stream, flush)
+            w["spec"].pop("_fields")
+            del w
+            torch.cuda.empty_cache()
+    clocks = head["clocks"]
     if rank == 0:
-        cpu = None
-        if not args.no_cpu_baseline:
-            # the whole workload field, once; the oracle first trains its own predictor on it (untimed)
-            nb, t, opn = cpu_oracle_rate(x, 1, shape=SHAPE)
-            cpu = {"value": nb / t[0] / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                   "sample": f"the whole {SHAPE[0]}x{SHAPE[1]}x{SHAPE[2]} field once, compress+decompress with "
-                             f"the oracle's own trained {opn} predictor (training untimed), {t[0]:.1f} s"}
         line = {
-            "metric": METRIC, "value": world * nbytes / (t_step * 1e6), "unit": "GB/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "grf100x500x500_f32: 100x500x500 float32 signed log-normal GRF, k^-11/3, "
-                                   "2% zeros", "eb_rel": EB, "block": list(BLOCK), "predictor": pname,
-                       "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
-            "compress_gbs": nbytes / (tc * 1e6), "decompress_gbs": nbytes / (td * 1e6),
-            "bits_per_value": bpv, "bound_held": ok,
-            "perceptron_forms": forms,
-            "training": {"seconds": train_s, "quantize_seconds": quant_s, "models": int(lrs.size),
-                         "chosen": int(chosen), "s_in": int(s_in),
-                         "samples_rate": THR32 / 2 ** 32, "val_cost_chosen": int(tcosts[chosen]) if chosen >= 0 else None,
-                         "val_cost_lorenzo": int(tcosts[-1])},
-            "bits_per_value_lorenzo_only": 8.0 * lz_size / n,
-            "vs_fp32_plain": {"bits_per_value": 32.0, "ratio": 32.0 / bpv, "device_copy_gbs": copy_gbs},
-            "roofline": dict(roofline(dom, dom_ms, n, size, nn_pts, fpp, clk.get("sm_max_mhz") or 2070.0, peak,
-                                      peak_kind), traffic=TRAFFIC_PER_LAUNCH.get((dom, args.form))),
-            "perceptron_blocks": {"fraction": float(nnflag.mean()), "points": nn_pts},
-            "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
-            "cpu_baseline": cpu,
-            "e2e": {"value": nbytes / statistics.median(te) / 1e9, "unit": "GB/s",
-                    "h2d_bytes_per_step": nbytes + size, "d2h_bytes_per_step": size + nbytes,
-                    "matches_device_path": e2e_ok},
-            "clocks": clk, "gpu_launches": launches, "wall_s_timed": wall,
+            "metric": METRIC, "value": world * res["input_bytes"] / (res["ms_per_step"] * 1e6), "unit": "GB/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if spec["dtype"] == "f64" else "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "fields": spec["desc"], "eb_rel": spec["eb"], "block": list(BLOCK),
+                       "predictor": res["predictor"], "form": res["form"],
+                       "training": f"device, {spec['samples'] or '10% of'} sampled stencils per field, 16 models",
+                       "l2": "inputs larger than L2 where they are; 256 MB flush between steps",
+                       "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "value_is": "input bytes / (compress + decompress time) per step"},
+            "compress_gbs": res["compress_gbs"], "decompress_gbs": res["decompress_gbs"],
+            "bits_per_value": res["bits_per_value"], "bound_held": res["bound_held"],
+            "hbm_roofline": res["hbm_roofline"], "roofline": res["roofline"],
+            "perceptron_blocks_fraction": res["perceptron_blocks_fraction"],
+            "perceptron_forms": forms, "stages_ms_per_step": res["stages_ms_per_step"],
+            "training": res["training"], "training_seconds_total": res["training_seconds_total"],
+            "vs_fp32_plain": {"bits_per_value": 32.0 * (2 if spec["dtype"] == "f64" else 1),
+                              "ratio": 32.0 * (2 if spec["dtype"] == "f64" else 1) / res["bits_per_value"],
+                              "device_copy_gbs": copy_gbs},
+            "cpu_baseline": cpu, "e2e": e2e, "e2e_with_training": e2e_t, "secondary": secondary,
+            "clocks": clocks, "gpu_launches": int(round(res["launches_per_step"] * args.steps)),
+            "wall_s_timed": res["wall_s_timed"], "sm_count": nsm,
         }
         print(json.dumps(line), flush=True)
     if dist:
