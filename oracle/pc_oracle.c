@@ -428,6 +428,54 @@ int32_t orc_mlp_pred32(const float* w, int k, int h1, int h2, int s_in, const in
   return o_round_pred(orc_mlp_fwd32(w, k, h1, h2, s_in, v));
 }
 
+/* FP64 form of the same network (Section IV.B), for reporting only: the
+ * FP32 weights taken exactly into double, u_i = v_i 2^-s, each unit
+ * acc = bias, then acc = fma(w, u_i, acc) in input order, leaky ReLU slope
+ * 2^-4, linear output, prediction rint(o 2^s) clamped to +-2^30.  Prediction
+ * error and compression ratio are reported against this predictor; the
+ * device never encodes with it. */
+double orc_mlp_fwd64(const float* w, int k, int h1, int h2, int s_in, const int32_t* v) {
+  double sig = ldexp(1.0, -s_in);
+  double u[32];
+  for (int i = 0; i < k; i++) u[i] = (double)v[i] * sig;
+  const float* W1 = w;
+  const float* b1 = W1 + h1 * k;
+  double a1[O_MAXH];
+  for (int j = 0; j < h1; j++) {
+    double acc = (double)b1[j];
+    for (int i = 0; i < k; i++) acc = fma((double)W1[j * k + i], u[i], acc);
+    a1[j] = acc >= 0.0 ? acc : acc * (double)O_ALPHA;
+  }
+  const float* p = b1 + h1;
+  double* hl = a1;
+  int nl = h1;
+  double a2[O_MAXH];
+  if (h2 > 0) {
+    const float* W2 = p;
+    const float* b2 = W2 + h2 * h1;
+    for (int j = 0; j < h2; j++) {
+      double acc = (double)b2[j];
+      for (int i = 0; i < h1; i++) acc = fma((double)W2[j * h1 + i], a1[i], acc);
+      a2[j] = acc >= 0.0 ? acc : acc * (double)O_ALPHA;
+    }
+    p = b2 + h2;
+    hl = a2;
+    nl = h2;
+  }
+  const float* W3 = p;
+  double o = (double)W3[nl];
+  for (int j = 0; j < nl; j++) o = fma((double)W3[j], hl[j], o);
+  return o * ldexp(1.0, s_in);
+}
+
+int32_t orc_mlp_pred64(const float* w, int k, int h1, int h2, int s_in, const int32_t* v) {
+  double p = orc_mlp_fwd64(w, k, h1, h2, s_in, v);
+  if (p != p) return 0;
+  if (p > 1073741824.0) p = 1073741824.0;
+  if (p < -1073741824.0) p = -1073741824.0;
+  return (int32_t)rint(p);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Fixed-point (BF16) form of the perceptron (Section IV.B network, the      */
 /* precision form evaluated on bf16 tensor-core operands).                    */
@@ -792,7 +840,8 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
   if (dtype != ORC_F32 && dtype != ORC_F64) return ORC_ERR_DTYPE;
   if (p->m < 2 || p->m > 16) return ORC_ERR_ARG;
   int use_q = p->pred == ORC_PRED_MLP_BF16 && p->qnet != NULL;
-  int use_nn = (p->pred == ORC_PRED_MLP && p->weights != NULL) || use_q;
+  int use_64 = p->pred == ORC_PRED_MLP64 && p->weights != NULL;
+  int use_nn = ((p->pred == ORC_PRED_MLP || use_64) && p->weights != NULL) || use_q;
   int k = p->stencil;
   if (use_q && (p->qnet[0] != k || p->qnet[1] != p->h1 || p->qnet[2] != p->h2 || p->qnet[3] != p->s_in))
     return ORC_ERR_ARG;
@@ -881,7 +930,8 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
                               ? vc[(qz * e1 + qy) * e2 + qx] : 0;
                 }
                 int64_t pr = use_q ? (int64_t)orc_mlp_pred_q(p->qnet, in)
-                                   : (int64_t)orc_mlp_pred32(p->weights, k, p->h1, p->h2, p->s_in, in);
+                             : use_64 ? (int64_t)orc_mlp_pred64(p->weights, k, p->h1, p->h2, p->s_in, in)
+                                      : (int64_t)orc_mlp_pred32(p->weights, k, p->h1, p->h2, p->s_in, in);
                 int64_t kn = vt[j] - pr;
                 int64_t an = kn < 0 ? -kn : kn;
                 costn += o_bitlen((uint64_t)(an < R ? an : R));
@@ -944,7 +994,7 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
   memcpy(out, "PCMP", 4);
   put32(out + 4, 1);
   put32(out + 8, (uint32_t)dtype);
-  put32(out + 12, (uint32_t)(use_q ? ORC_PRED_MLP_BF16 : (use_nn ? ORC_PRED_MLP : ORC_PRED_LORENZO)));
+  put32(out + 12, (uint32_t)(use_q ? ORC_PRED_MLP_BF16 : (use_64 ? ORC_PRED_MLP64 : (use_nn ? ORC_PRED_MLP : ORC_PRED_LORENZO))));
   put64(out + 16, dims[0]); put64(out + 24, dims[1]); put64(out + 32, dims[2]);
   put32(out + 40, (uint32_t)p->block[0]); put32(out + 44, (uint32_t)p->block[1]); put32(out + 48, (uint32_t)p->block[2]);
   put32(out + 52, (uint32_t)(use_nn ? k : 0));
@@ -1081,9 +1131,9 @@ int orc_decompress(const uint8_t* in, uint64_t in_size, void* xo, uint64_t cap_e
   if (o_geom_make(dims, block, &g)) return ORC_ERR_CORRUPT;
   if (m < 2 || m > 16 || g.nblocks != nblocks || total > in_size) return ORC_ERR_CORRUPT;
   int wsz = pred == ORC_PRED_MLP_BF16 ? 8 : 4;
-  if (pred == ORC_PRED_MLP || pred == ORC_PRED_MLP_BF16) {
+  if (pred == ORC_PRED_MLP || pred == ORC_PRED_MLP64 || pred == ORC_PRED_MLP_BF16) {
     if ((k != 7 && k != 13) || h1 < 1 || h1 > O_MAXH || h2 < 0 || h2 > O_MAXH || s_in < 0 || s_in > 30 ||
-        nw != (pred == ORC_PRED_MLP ? orc_mlp_nweights(k, h1, h2) : orc_qnet_len(k, h1, h2)))
+        nw != (pred != ORC_PRED_MLP_BF16 ? orc_mlp_nweights(k, h1, h2) : orc_qnet_len(k, h1, h2)))
       return ORC_ERR_CORRUPT;
   } else if (pred != ORC_PRED_LORENZO || nw != 0) {
     return ORC_ERR_CORRUPT;
@@ -1099,7 +1149,7 @@ int orc_decompress(const uint8_t* in, uint64_t in_size, void* xo, uint64_t cap_e
 
   float* wts = NULL;
   int64_t* qn = NULL;
-  if (nw && pred == ORC_PRED_MLP) {
+  if (nw && (pred == ORC_PRED_MLP || pred == ORC_PRED_MLP64)) {
     wts = (float*)malloc(sizeof(float) * (size_t)nw);
     for (int i = 0; i < nw; i++) wts[i] = f_from_bits(get32(in + off_w + 4ull * i));
   }
@@ -1221,7 +1271,9 @@ int orc_decompress(const uint8_t* in, uint64_t in_size, void* xo, uint64_t cap_e
                 inn[i] = (qz >= 0 && qy >= 0 && qx >= 0 && qz < e0 && qy < e1 && qx < e2)
                              ? vc[(qz * e1 + qy) * e2 + qx] : 0;
               }
-              pr = qn ? orc_mlp_pred_q(qn, inn) : orc_mlp_pred32(wts, k, h1, h2, s_in, inn);
+              pr = qn ? orc_mlp_pred_q(qn, inn)
+                      : (pred == ORC_PRED_MLP64 ? orc_mlp_pred64(wts, k, h1, h2, s_in, inn)
+                                                : orc_mlp_pred32(wts, k, h1, h2, s_in, inn));
             } else {
               pr = o_lorenzo(in7);
             }

@@ -29,6 +29,7 @@
 #define ORC_PRED_LORENZO 0
 #define ORC_PRED_MLP 1
 #define ORC_PRED_MLP_BF16 2  /* fixed-point perceptron on bf16 tensor-core operands */
+#define ORC_PRED_MLP64 3     /* the FP32 weights evaluated in FP64 (reporting only) */
 
 typedef struct {
   int dtype;

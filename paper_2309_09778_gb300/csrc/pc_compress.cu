@@ -2,6 +2,7 @@
 // transform / predict / select / quantize / histogram pass (a4-a9).
 #include "pc_kernels.cuh"
 #include "pc_qmlp.cuh"
+#include "pc_tcnet.cuh"
 #include "pc_profile.cuh"
 
 namespace pc {
@@ -202,24 +203,23 @@ __global__ void k_consts(State* st, double eb, Tabs* tabs) {
 // ---------------------------------------------------------------------------
 constexpr int kHistWin = 2048;
 
-// Extra shared memory of the fixed-point form: B fragments, biases, and one
-// prediction per point of the brick.
-template <int BV, int MODE, int K, int H1, int H2>
-constexpr size_t qnet_smem_bytes() {
-  if constexpr (MODE == 2) {
-    using S = QShape<K, H1, H2>;
-    return (size_t)S::NFRAG * 4 + (size_t)S::NBIAS * 8 + (size_t)BrickShape<BV>::G * BV * 4;
-  } else {
-    return 0;
-  }
-}
-
+// Shared memory of k_compress (16-byte aligned regions): tables, codes with
+// bound flags, padded centred inputs, Lorenzo codes (in the fixed-point form
+// this region first holds the tensor-core A tiles of the two warpgroups),
+// perceptron codes, histogram window, and the staged fixed-point network.
 template <int BV, int MODE, int PV, int K, int H1, int H2>
-constexpr size_t compress_smem_bytes() {
-  constexpr int G = BrickShape<BV>::G;
-  return sizeof(Tabs) + (size_t)G * BV * 4 + (size_t)((G * PV + 3) & ~3) * 4 + (size_t)G * BV * 2 * (MODE ? 2 : 1) +
-         (size_t)kHistWin * 4 + qnet_smem_bytes<BV, MODE, K, H1, H2>();
-}
+struct CompLayout {
+  static constexpr int G = BrickShape<BV>::G;
+  static constexpr size_t a16(size_t v) { return (v + 15) & ~(size_t)15; }
+  static constexpr size_t DQ = sizeof(Tabs);
+  static constexpr size_t VP = DQ + a16((size_t)G * BV * 4);
+  static constexpr size_t CZ = VP + a16((size_t)((G * PV + 3) & ~3) * 4);
+  static constexpr size_t ATILES = MODE == 2 ? (size_t)2 * 2 * 128 * H1 * 2 : 0;  // 2 warpgroups x 2 limbs
+  static constexpr size_t CN = CZ + a16((size_t)G * BV * 2 > ATILES ? (size_t)G * BV * 2 : ATILES);
+  static constexpr size_t HI = CN + (MODE ? a16((size_t)G * BV * 2) : 0);
+  static constexpr size_t ST = HI + (size_t)kHistWin * 4;
+  static constexpr size_t TOTAL = ST + (MODE == 2 ? a16(sizeof(TcStage<H1 == 32 ? 32 : 16>)) : 0);
+};
 
 template <typename T, int B0, int B1, int B2, int MODE, int K, int H1, int H2>
 __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restrict__ x, Geo g, const State* __restrict__ st,
@@ -235,25 +235,24 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restr
   using PD = Pad<B0, B1, B2, WIDE>;
   constexpr int VW = (16 / (int)sizeof(T));
   constexpr bool VEC_OK = (B2 * G) % VW == 0;
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
+  constexpr int QK = MODE == 2 ? K : 7, QH = MODE == 2 ? H1 : 16;
+  using CL = CompLayout<BV, MODE, PD::PV, K, H1, H2>;
   Tabs& tb = *reinterpret_cast<Tabs*>(smem);
-  int* s_dq = reinterpret_cast<int*>(smem + sizeof(Tabs));             // G*BV: 2 q + ok
-  int* s_vp = s_dq + G * BV;                                           // G*PV padded inputs
-  uint16_t* s_cz = reinterpret_cast<uint16_t*>(s_vp + ((G * PD::PV + 3) & ~3));  // G*BV
-  uint16_t* s_cn = s_cz + G * BV;                                      // G*BV (perceptron only)
-  unsigned int* s_hist = reinterpret_cast<unsigned int*>(s_cn + (MODE ? G * BV : 0));
-  // fixed-point form: B fragments, biases, per-point predictions
-  constexpr int QK = MODE == 2 ? K : 7, QH1 = MODE == 2 ? H1 : 16, QH2 = MODE == 2 ? H2 : 16;
-  using QS = QShape<QK, QH1, QH2>;
-  uint32_t* s_frag = reinterpret_cast<uint32_t*>(s_hist + kHistWin);
-  long long* s_qbias = reinterpret_cast<long long*>(s_frag + (MODE == 2 ? QS::NFRAG : 0));
-  int* s_pred = reinterpret_cast<int*>(s_qbias + (MODE == 2 ? QS::NBIAS : 0));
-  __shared__ QSc s_qsc;
+  int* s_dq = reinterpret_cast<int*>(smem + CL::DQ);                   // G*BV: 2 q + ok
+  int* s_vp = reinterpret_cast<int*>(smem + CL::VP);                   // G*PV padded inputs
+  uint16_t* s_cz = reinterpret_cast<uint16_t*>(smem + CL::CZ);         // G*BV (after the A tiles)
+  uint16_t* s_cn = reinterpret_cast<uint16_t*>(smem + CL::CN);         // G*BV (perceptron only)
+  unsigned int* s_hist = reinterpret_cast<unsigned int*>(smem + CL::HI);
+  // fixed-point form: staged network, tensor-core A tiles (over the Lorenzo codes)
+  TcStage<QH>& tcs = *reinterpret_cast<TcStage<QH>*>(smem + CL::ST);
+  uint8_t* s_atile = smem + CL::CZ;
   __shared__ int s_cost[G][2];
   __shared__ int s_nz[G];
   __shared__ int s_da[G];
 
   if (st->err) return;
+  int* errw = const_cast<int*>(&st->err);
   State c;
   c.Kp = st->Kp; c.Kn = st->Kn; c.Zq = st->Zq; c.S = st->S;
   c.step32 = st->step32; c.inv32 = st->inv32; c.ebdn32 = st->ebdn32;
@@ -268,8 +267,29 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restr
   const float sig = MODE ? __uint_as_float((unsigned int)(127 - mlp.s_in) << 23) : 1.0f;
   const float unsig = MODE ? __uint_as_float((unsigned int)(127 + mlp.s_in) << 23) : 1.0f;
   const bool vec_rows = VEC_OK && (g.n[2] % VW == 0) && ((reinterpret_cast<uintptr_t>(x) & 15u) == 0);
-  if constexpr (MODE == 2) qnet_stage<QK, QH1, QH2>(qnet, s_frag, s_qbias, &s_qsc);
+  // fixed-point form: the network in shared memory, TMEM for the two
+  // warpgroups' accumulators (2 limbs x QH columns each)
+  constexpr uint32_t kTmemCols = QH == 32 ? 128 : 64;
+  uint32_t tmem_base = 0, tc_phase = 0;
+  bool tc_ok = true;
+  if constexpr (MODE == 2) {
+    tcnet_stage<QK, QH>(qnet, tcs);
+    if (tid < 32) {
+      tc::tmem_alloc(&tcs.tmem, kTmemCols);
+      tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+      tc::mbar_init(&tcs.mbar[0], 1);
+      tc::mbar_init(&tcs.mbar[1], 1);
+      tc::mbar_init_fence();
+    }
+    tc::fence_before_sync();
+  }
   __syncthreads();
+  if constexpr (MODE == 2) {
+    tc::fence_after_sync();
+    tmem_base = tcs.tmem;
+  }
 
   const long long nbx = (g.nb[2] + G - 1) / G;
   const long long nbricks = g.nb[0] * g.nb[1] * nbx;
@@ -368,45 +388,40 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restr
     }
     __syncthreads();
     if constexpr (MODE == 2) {
-      // a6, fixed-point form: tiles of 16 points on the tensor cores
-      const int wid = tid >> 5, lane = tid & 31;
-      const QSc qsc = s_qsc;
-      // this thread's layer-1 columns: stencil offset (or none) and limb
-      int qoff[QS::KC1][4], qhi[QS::KC1][4];  // stencil offset; limb 1 hi, 0 lo, 2 padding
+      // a6-a8, fixed-point form: tiles of 128 points on the tensor cores, one
+      // per warpgroup at a time; each point's perceptron code and cost
+      const int wg = tid >> 7, r = tid & 127;
+      uint8_t* abuf = s_atile + (size_t)wg * 2 * 128 * QH * 2;
+      const uint32_t tm = tmem_base + (uint32_t)(wg * 2 * QH);
+      for (int tile = wg; tile < G * BV / 128; tile += 2) {
+        const int f = tile * 128 + r;
+        const int gb = f / BV, j = f - gb * BV;
+        const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+        const int pj = gb * PD::PV + PD::at(lz, ly, lx);
+        int xin[QK];
 #pragma unroll
-      for (int kc = 0; kc < QS::KC1; ++kc)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          int in, hi;
-          qcol<QK>(kc, e, in, hi);
-          qoff[kc][e] = in < 0 ? 0 : PD::off(st_dz(QK, in), st_dy(QK, in), st_dx(QK, in));
-          qhi[kc][e] = in < 0 ? 2 : hi;  // 2: padding column
+        for (int q = 0; q < QK; ++q) xin[q] = s_vp[pj + PD::off(st_dz(QK, q), st_dy(QK, q), st_dx(QK, q))];
+        int prd;
+        tc_ok &= tcnet_tile<QK, QH>(tcs, abuf, tm, wg, r, tc_phase, xin, tcs.mul512, prd);
+        const long long bxp = bxg * G + gb;
+        const int e2p = bxp < g.nb[2] ? (int)min((long long)B2, g.n[2] - bxp * B2) : 0;
+        const bool valid = j != 0 && lz < e0 && ly < e1 && lx < e2p;
+        uint16_t coden = 0;
+        int costn = 0;
+        if (valid) {
+          const int pd = s_dq[f];
+          const int v = (pd >> 1) - s_da[gb];
+          const int vk = v > (1 << 30) ? (1 << 30) : (v < -(1 << 30) ? -(1 << 30) : v);
+          const long long kn = (long long)vk - (long long)prd;
+          const long long an = kn < 0 ? -kn : kn;
+          costn = bitlen_u((unsigned int)(an < R ? an : R));
+          coden = (an <= R - 1 && (pd & 1)) ? (uint16_t)(kn + R) : 0;
         }
-      for (int tile = wid; tile < G * BV / 16; tile += 8) {
-        const int f0 = tile * 16;
-        const int gb = f0 / BV;
-        const int* vpg = s_vp + gb * PD::PV;
-        int lv[2][QS::KC1][4];
+        s_cn[f] = coden;
+        // the 32 points of a warp lie in one block
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          const int j = f0 - gb * BV + (lane >> 2) + 8 * r;
-          const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
-          const int pj = PD::at(lz, ly, lx);
-#pragma unroll
-          for (int kc = 0; kc < QS::KC1; ++kc)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              int v = qhi[kc][e] == 2 ? 0 : vpg[pj + qoff[kc][e]];
-              v = v > kQIn ? kQIn : (v < -kQIn ? -kQIn : v);
-              lv[r][kc][e] = qlimb(v, qhi[kc][e]);
-            }
-        }
-        int p0, p1;
-        qnet_tile<QK, QH1, QH2>(s_frag, s_qbias, qsc, lv, p0, p1);
-        if ((lane & 3) == 0) {
-          s_pred[f0 + (lane >> 2)] = p0;
-          s_pred[f0 + (lane >> 2) + 8] = p1;
-        }
+        for (int o = 16; o > 0; o >>= 1) costn += __shfl_xor_sync(0xFFFFFFFFu, costn, o);
+        if ((tid & 31) == 0 && costn) atomicAdd(&s_cost[gb][1], costn);
       }
       __syncthreads();
     }
@@ -496,11 +511,9 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restr
           const int az = kz < 0 ? -kz : kz;
           cz += bitlen_u((unsigned int)(az < R ? az : R));
           codez = (az <= R - 1 && okp) ? (uint16_t)(kz + R) : 0;
-          if constexpr (MODE != 0) {
+          if constexpr (MODE == 1) {
             long long prd;
-            if constexpr (MODE == 2) {
-              prd = s_pred[team * BV + j];
-            } else {
+            {
               constexpr int KK = K > 0 ? K : 13;
               int in[KK];
               const int kk = K > 0 ? K : mlp.k;
@@ -516,7 +529,7 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restr
             const long long an = kn < 0 ? -kn : kn;
             cn += bitlen_u((unsigned int)(an < R ? an : R));
             coden = (an <= R - 1 && okp) ? (uint16_t)(kn + R) : 0;
-          } else {
+          } else if constexpr (MODE == 0) {
             nz += codez == 0;
             const int hi = (int)codez - hbase;
             if (hi >= 0 && hi < kHistWin) atomicAdd(&s_hist[hi], 1u);
@@ -524,12 +537,12 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restr
           }
         }
         s_cz[team * BV + j] = codez;
-        if constexpr (MODE != 0) s_cn[team * BV + j] = coden;
+        if constexpr (MODE == 1) s_cn[team * BV + j] = coden;
       }
     }
-    // team sums
+    // team sums (the fixed-point form summed its perceptron costs per warp)
     int tcz = team_sum<TS>(cz, &s_cost[team][0]);
-    int tcn = MODE ? team_sum<TS>(cn, &s_cost[team][1]) : 0;
+    int tcn = MODE == 1 ? team_sum<TS>(cn, &s_cost[team][1]) : 0;
     int tnz = MODE ? 0 : team_sum<TS>(nz, &s_nz[team]);
     __syncthreads();
     if constexpr (TS != 32) {
@@ -537,6 +550,7 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restr
       tcn = s_cost[team][1];
       tnz = s_nz[team];
     }
+    if constexpr (MODE == 2) tcn = s_cost[team][1];
     // a7 select, a8 emit, a9 histogram of the chosen codes
     if (bvalid) {
       const bool usen = MODE != 0 && tcn < tcz;
@@ -578,6 +592,12 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restr
     const unsigned int h = s_hist[i];
     if (h && hbase + i < (1 << m)) atomicAdd(&hist[hbase + i], (unsigned long long)h);
   }
+  if constexpr (MODE == 2) {
+    if (!tc_ok) atomicExch(errw, PC_ERR_TIMEOUT);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid < 32) tc::tmem_dealloc(tmem_base, kTmemCols);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -603,12 +623,23 @@ static int launch_c(const void* x, const Geo& g, const State* st, const Tabs* ta
   constexpr int BV = B0 * B1 * B2;
   constexpr bool WIDE = MODE != 0 && (K == 13 || K == 0);
   auto kern = k_compress<T, B0, B1, B2, MODE, K, H1, H2>;
-  constexpr size_t sm = compress_smem_bytes<BV, MODE, Pad<B0, B1, B2, WIDE>::PV, K, H1, H2>();
+  constexpr size_t sm = CompLayout<BV, MODE, Pad<B0, B1, B2, WIDE>::PV, K, H1, H2>::TOTAL;
   static_assert(sm <= 232448, "shared memory per CTA");
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
     return PC_ERR_CUDA;
+  // the whole unified L1 as shared memory, so that two CTAs fit on an SM
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+      cudaSuccess)
+    return PC_ERR_CUDA;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm);
+  if constexpr (MODE == 2) {
+    // The occupancy query reports one CTA per SM for the tensor-core form;
+    // registers (launch bounds) and shared memory allow two, and two CTAs
+    // hold 2 x 128 (or 2 x 64) of the 512 TMEM columns.
+    const int by_smem = (int)((228u << 10) / (sm + 2048));
+    per_sm = by_smem >= 2 ? 2 : 1;
+  }
   if (per_sm < 1) per_sm = 1;
   constexpr int G = BrickShape<BV>::G;
   long long nbricks = g.nb[0] * g.nb[1] * ((g.nb[2] + G - 1) / G);
