@@ -164,6 +164,55 @@ def oracle_worker(args):
     return sub.nbytes, dt, len(blob)
 
 
+def report_worker(args):
+    """One field sample: the oracle's prediction report, or its container size with one predictor form."""
+    kind, sub, eb, k, h1, h2, s_in, w, q = args
+    from oracle import oracle as O
+    O.build()
+    if kind == "report":
+        return kind, O.pred_report(sub, eb, w, s_in, block=BLOCK, k=k, h1=h1, h2=h2, qnet=q)
+    st, blob = O.compress(sub, eb, block=BLOCK, weights=w, stencil=k, h1=h1, h2=h2, s_in=s_in,
+                          qnet=q if kind == "bf16" else None, fp64=kind == "fp64")
+    if st != 0:
+        raise RuntimeError(f"oracle status {st}")
+    return kind, 8.0 * len(blob) / sub.size
+
+
+def fp64_report(fields_host, spec, infos, cores, pts):
+    """Prediction error and compression ratio of the FP32 and fixed-point forms against the same trained
+    weights evaluated in FP64 (the reporting predictor), by the oracle on one sub-volume per field."""
+    eb, k, h1, h2 = spec["eb"], spec["k"], spec["h1"], spec["h2"]
+    tasks, idx = [], []
+    for fi, (x, inf) in enumerate(zip(fields_host, infos)):
+        if inf["w"] is None:
+            continue
+        sub = slabs([x], pts, 1)[0]
+        for kind in ("report", "fp64", "fp32", "bf16"):
+            if kind == "bf16" and inf["q"] is None:
+                continue
+            tasks.append((kind, sub, eb, k, h1, h2, inf["s_in"], inf["w"], inf["q"]))
+            idx.append(fi)
+    if not tasks:
+        return None
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(min(cores, len(tasks))) as pool:
+        res = pool.map(report_worker, tasks)
+    out = {}
+    for fi, (kind, v) in zip(idx, res):
+        d = out.setdefault(fi, {"bits_per_value": {}})
+        if kind == "report":
+            d.update(v)
+        else:
+            d["bits_per_value"][kind] = v
+    for d in out.values():
+        b = d["bits_per_value"]
+        d["size_vs_fp64"] = {f: b[f] / b["fp64"] - 1.0 for f in ("fp32", "bf16") if f in b and "fp64" in b}
+    shp = slabs([fields_host[0]], pts, 1)[0].shape
+    return {"sample": f"one {shp[0]}x{shp[1]}x{shp[2]} corner sub-volume per field, the device-trained weights",
+            "seconds": time.perf_counter() - t0, "fields": [out[i] for i in sorted(out)]}
+
+
 def slabs(fields_host, pts_per_slab, count):
     """`count` distinct corner-aligned sub-volumes of about pts_per_slab points, drawn round-robin from the fields."""
     out = []
@@ -702,10 +751,12 @@ def main():
         copy_gbs.append(2 * d.numel() * d.element_size() * 5 / (c0.elapsed_time(c1) * 1e6))
         del dst
     cpu = None
+    report = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         fh = [h.numpy() for h in hosts]
-        cpu = cpu_baseline(fh, spec, head["infos"][0], head["form"], os.cpu_count() or 1,
-                           (32 * 128 * 128) if spec["k"] == 13 else (64 * 128 * 128))
+        pts = (32 * 128 * 128) if spec["k"] == 13 else (64 * 128 * 128)
+        cpu = cpu_baseline(fh, spec, head["infos"][0], head["form"], os.cpu_count() or 1, pts)
+        report = fp64_report(fh, spec, head["infos"], os.cpu_count() or 1, pts)
     del hosts
     spec.pop("_fields")
     torch.cuda.empty_cache()
@@ -744,7 +795,8 @@ def main():
             "vs_fp32_plain": {"bits_per_value": 32.0 * (2 if spec["dtype"] == "f64" else 1),
                               "ratio": 32.0 * (2 if spec["dtype"] == "f64" else 1) / res["bits_per_value"],
                               "device_copy_gbs": copy_gbs},
-            "cpu_baseline": cpu, "e2e": e2e, "e2e_with_training": e2e_t, "secondary": secondary,
+            "cpu_baseline": cpu, "e2e": e2e, "e2e_with_training": e2e_t, "fp64_predictor_report": report,
+            "secondary": secondary,
             "clocks": clocks, "gpu_launches": int(round(res["launches_per_step"] * args.steps)),
             "wall_s_timed": res["wall_s_timed"], "sm_count": nsm,
         }

@@ -21,7 +21,7 @@ _lock = threading.Lock()
 _lib = None
 
 F32, F64 = 0, 1
-PRED_LORENZO, PRED_MLP, PRED_MLP_BF16 = 0, 1, 2
+PRED_LORENZO, PRED_MLP, PRED_MLP_BF16, PRED_MLP64 = 0, 1, 2, 3
 ERR = {0: "ok", -1: "arg", -2: "dtype", -3: "nonfinite", -4: "capacity", -5: "corrupt", -8: "eb_range"}
 LMAX = 24
 BATCH = 256
@@ -89,6 +89,13 @@ def lib():
             L.orc_mlp_fwd32.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]
             L.orc_mlp_pred32.restype = C.c_int32
             L.orc_mlp_pred32.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]
+            L.orc_mlp_fwd64.restype = C.c_double
+            L.orc_mlp_fwd64.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]
+            L.orc_mlp_pred64.restype = C.c_int32
+            L.orc_mlp_pred64.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]
+            L.orc_pred_report.restype = C.c_int
+            L.orc_pred_report.argtypes = [C.c_void_p, u64p, C.c_int, C.c_double, C.POINTER(C.c_int), C.c_int,
+                                          C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
             L.orc_huffman_lengths.restype = C.c_int
             L.orc_huffman_lengths.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
             L.orc_canonical_codes.restype = C.c_int
@@ -233,6 +240,39 @@ def mlp_pred32(w: np.ndarray, k, h1, h2, s_in, v) -> int:
     return lib().orc_mlp_pred32(_p(w), k, h1, h2, s_in, _p(v))
 
 
+def mlp_fwd64(w: np.ndarray, k, h1, h2, s_in, v) -> float:
+    """The FP32 weights evaluated in FP64 (the reporting predictor)."""
+    w = np.ascontiguousarray(w, np.float32)
+    v = np.ascontiguousarray(v, np.int32)
+    return lib().orc_mlp_fwd64(_p(w), k, h1, h2, s_in, _p(v))
+
+
+def mlp_pred64(w: np.ndarray, k, h1, h2, s_in, v) -> int:
+    w = np.ascontiguousarray(w, np.float32)
+    v = np.ascontiguousarray(v, np.int32)
+    return lib().orc_mlp_pred64(_p(w), k, h1, h2, s_in, _p(v))
+
+
+def pred_report(x: np.ndarray, eb: float, w, s_in: int, block=(8, 8, 8), k=7, h1=16, h2=16, qnet=None, m=16):
+    """Prediction error of Lorenzo and of the FP64, FP32 and fixed-point forms of one network over every
+    non-anchor point of a field (the oracle's orc_pred_report).  Returns a dict."""
+    x = np.ascontiguousarray(x)
+    w = np.ascontiguousarray(w, np.float32)
+    q = None if qnet is None else np.ascontiguousarray(qnet, np.int64)
+    out = np.zeros(13, np.float64)
+    b = (C.c_int * 3)(*block)
+    st = lib().orc_pred_report(_p(x), _dims(x), _dtype_code(x), eb, b, k, h1, h2, s_in, _p(w),
+                               None if q is None else _p(q), m, _p(out))
+    assert st == 0, st
+    n = max(out[0], 1.0)
+    names = ["lorenzo", "fp64", "fp32", "fixed_point"]
+    return {"points": int(out[0]),
+            "rms_residual": {nm: float(np.sqrt(out[1 + i] / n)) for i, nm in enumerate(names)},
+            "rms_vs_fp64": {"fp32": float(np.sqrt(out[5] / n)), "fixed_point": float(np.sqrt(out[6] / n))},
+            "frac_differs_from_fp64": {"fp32": out[7] / n, "fixed_point": out[8] / n},
+            "bits_proxy_per_point": {nm: out[9 + i] / n for i, nm in enumerate(names)}}
+
+
 # ------------------------------------------------ fixed-point (BF16) perceptron
 def qnet_len(k: int, h1: int, h2: int) -> int:
     return lib().orc_qnet_len(k, h1, h2)
@@ -318,9 +358,10 @@ def compress_bound(shape3, dtype: int, block, m: int = 16, nweights: int = 0) ->
 
 
 def compress(x: np.ndarray, eb: float, block=(8, 8, 8), weights=None, stencil=7, h1=16, h2=16,
-             m: int = 16, s_in: int = 0, dump: bool = False, qnet=None):
+             m: int = 16, s_in: int = 0, dump: bool = False, qnet=None, fp64: bool = False):
     """Compress with the oracle.  Returns (status, bytes[, dump dict]).  `qnet` selects the
-    fixed-point (BF16) perceptron form instead of the FP32 weights."""
+    fixed-point (BF16) perceptron form instead of the FP32 weights; fp64=True evaluates the
+    FP32 weights in FP64 (the reporting predictor, which only the oracle encodes with)."""
     x = np.ascontiguousarray(x)
     dims = _dims(x)
     dt = _dtype_code(x)
@@ -333,6 +374,8 @@ def compress(x: np.ndarray, eb: float, block=(8, 8, 8), weights=None, stencil=7,
         assert q.size == qnet_len(stencil, h1, h2)
         nw = 2 * q.size
     pred = PRED_MLP_BF16 if q is not None else (PRED_MLP if w is not None else PRED_LORENZO)
+    if fp64 and w is not None and q is None:
+        pred = PRED_MLP64
     p = _params(eb, block, pred, stencil, h1, h2, m, s_in, w, q)
     cap = compress_bound(tuple(dims), dt, block, m, nw)
     out = np.zeros(cap, np.uint8)

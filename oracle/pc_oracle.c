@@ -1661,3 +1661,96 @@ int orc_quantize(const void* x, const uint64_t dims[3], int dtype, double eb, co
   free(tin); free(ttg); free(tus); free(vin); free(vtg); free(vus);
   return st;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Report (not part of the method): prediction error of the FP32 and the      */
+/* fixed-point perceptron against the same weights evaluated in FP64, and of  */
+/* Lorenzo, over every non-anchor point of every block of a field, with the   */
+/* inputs of the data-selection rule (Section IV.D, exact pre-quantized       */
+/* codes).  out[0] = points; out[1..4] = sum of squared residuals (target     */
+/* minus prediction) of Lorenzo, FP64, FP32, fixed point; out[5], out[6] =    */
+/* sum of squared differences FP32 - FP64 and fixed point - FP64; out[7],     */
+/* out[8] = points where FP32, fixed point differ from FP64; out[9..12] =     */
+/* sum of bitlen(min(|residual|, R)) of the four predictors.  qnet may be     */
+/* NULL (fixed-point entries stay 0).                                         */
+/* ------------------------------------------------------------------------- */
+int orc_pred_report(const void* x, const uint64_t dims[3], int dtype, double eb, const int block[3], int k, int h1,
+                    int h2, int s_in, const float* w, const int64_t* qnet, int m, double out[13]) {
+  for (int i = 0; i < 13; i++) out[i] = 0.0;
+  if (dtype != ORC_F32 && dtype != ORC_F64) return ORC_ERR_DTYPE;
+  if ((k != 7 && k != 13) || !w || m < 2 || m > 16) return ORC_ERR_ARG;
+  o_geom g;
+  if (o_geom_make(dims, block, &g)) return ORC_ERR_ARG;
+  uint64_t n = dims[0] * dims[1] * dims[2];
+  double amin, amax;
+  int trivial;
+  int st = orc_stats(x, n, dtype, &amin, &amax, &trivial);
+  if (st) return st;
+  orc_consts c;
+  st = orc_make_consts(dtype, amin, amax, trivial, eb, &c);
+  if (st) return st;
+  int64_t R = (int64_t)1 << (m - 1);
+  int32_t* dq = (int32_t*)malloc(sizeof(int32_t) * n);
+  for (uint64_t i = 0; i < n; i++) {
+    int ok;
+    if (dtype == ORC_F32) orc_transform32(((const float*)x)[i], &c, &dq[i], &ok);
+    else orc_transform64(((const double*)x)[i], &c, &dq[i], &ok);
+  }
+  int32_t* vc = (int32_t*)malloc(sizeof(int32_t) * g.bvol);
+  int64_t* vt = (int64_t*)malloc(sizeof(int64_t) * g.bvol);
+  for (uint64_t bz = 0; bz < g.nb[0]; bz++)
+    for (uint64_t by = 0; by < g.nb[1]; by++)
+      for (uint64_t bx = 0; bx < g.nb[2]; bx++) {
+        uint64_t o0 = bz * block[0], o1 = by * block[1], o2 = bx * block[2];
+        int e0 = (int)((dims[0] - o0) < (uint64_t)block[0] ? dims[0] - o0 : (uint64_t)block[0]);
+        int e1 = (int)((dims[1] - o1) < (uint64_t)block[1] ? dims[1] - o1 : (uint64_t)block[1]);
+        int e2 = (int)((dims[2] - o2) < (uint64_t)block[2] ? dims[2] - o2 : (uint64_t)block[2]);
+        int32_t da = dq[(o0 * dims[1] + o1) * dims[2] + o2];
+        for (int lz = 0; lz < e0; lz++)
+          for (int ly = 0; ly < e1; ly++)
+            for (int lx = 0; lx < e2; lx++) {
+              int j = (lz * e1 + ly) * e2 + lx;
+              int64_t v = (int64_t)dq[((o0 + lz) * dims[1] + (o1 + ly)) * dims[2] + (o2 + lx)] - (int64_t)da;
+              vt[j] = v;
+              vc[j] = (int32_t)(v > O_VCLAMP ? O_VCLAMP : (v < -O_VCLAMP ? -O_VCLAMP : v));
+            }
+        for (int lz = 0; lz < e0; lz++)
+          for (int ly = 0; ly < e1; ly++)
+            for (int lx = 0; lx < e2; lx++) {
+              int j = (lz * e1 + ly) * e2 + lx;
+              if (j == 0) continue;
+              int32_t in7[7], in[13];
+              for (int i = 0; i < 7; i++) {
+                int qz = lz + O_S7[i][0], qy = ly + O_S7[i][1], qx = lx + O_S7[i][2];
+                in7[i] = (qz >= 0 && qy >= 0 && qx >= 0) ? vc[(qz * e1 + qy) * e2 + qx] : 0;
+              }
+              for (int i = 0; i < k; i++) {
+                int dz, dy, dx;
+                o_stencil(k, i, &dz, &dy, &dx);
+                int qz = lz + dz, qy = ly + dy, qx = lx + dx;
+                in[i] = (qz >= 0 && qy >= 0 && qx >= 0 && qz < e0 && qy < e1 && qx < e2) ? vc[(qz * e1 + qy) * e2 + qx]
+                                                                                          : 0;
+              }
+              int64_t pr[4];
+              pr[0] = o_lorenzo(in7);
+              pr[1] = orc_mlp_pred64(w, k, h1, h2, s_in, in);
+              pr[2] = orc_mlp_pred32(w, k, h1, h2, s_in, in);
+              pr[3] = qnet ? orc_mlp_pred_q(qnet, in) : pr[1];
+              out[0] += 1.0;
+              for (int f = 0; f < 4; f++) {
+                double d = (double)(vt[j] - pr[f]);
+                out[1 + f] += d * d;
+                int64_t a = vt[j] - pr[f];
+                a = a < 0 ? -a : a;
+                out[9 + f] += (double)o_bitlen((uint64_t)(a < R ? a : R));
+              }
+              double d32 = (double)(pr[2] - pr[1]), dqv = (double)(pr[3] - pr[1]);
+              out[5] += d32 * d32;
+              out[6] += dqv * dqv;
+              out[7] += pr[2] != pr[1];
+              out[8] += pr[3] != pr[1];
+            }
+      }
+  free(vt); free(vc); free(dq);
+  return ORC_OK;
+}
