@@ -70,7 +70,24 @@ typedef struct {
                              used by PC_PRED_MLP_FP32 */
   const long long* h_qnet;/* host pointer to the fixed-point network (pc_qnet_len int64, from
                              pc_quantize); used by PC_PRED_MLP_BF16 */
+  unsigned long long seed;/* sampling and initialisation seed of the training phase */
+  long long train_samples;/* expected number of sampled stencils of the training phase;
+                             0 draws 10% of the non-anchor points (Section IV.C) */
+  int ndims;              /* 1, 2 or 3 (0: not stated); the leading 3 - ndims dims must be 1 */
+  int reserved_;          /* 0 */
 } pc_params;
+/*
+ * Learned predictor trained inside pc_compress (Section IV.C, V): with
+ * pred = PC_PRED_MLP_FP32 and h_weights = NULL, or PC_PRED_MLP_BF16 and
+ * h_qnet = NULL, pc_compress first runs the training phase of pc_train on the
+ * device (seed, train_samples, the library's 16-model learning-rate x L2 grid)
+ * and, for the fixed-point form, pc_quantize; the chosen network (or Lorenzo,
+ * when no model beats it) then compresses the field.  The chosen weights come
+ * back to the host once, mid-call.  The workspace must then also hold the
+ * training buffers (pc_compress_workspace_size accounts for them).
+ * Supported shapes: (7, 16, 16) and (13, 32, 32); the FP32 form also
+ * (7, 8, 8), (7, 2, 0) and (13, 16, 16).
+ */
 
 /* Number of floats in the weight blob for stencil k and hidden widths h1, h2. */
 int pc_mlp_nweights(int k, int h1, int h2);

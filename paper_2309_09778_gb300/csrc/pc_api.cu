@@ -63,27 +63,42 @@ bool make_geo(const size_t dims[3], const int block[3], Geo& g) {
 
 bool qshape_ok(int k, int h1, int h2) { return (k == 7 && h1 == 16 && h2 == 16) || (k == 13 && h1 == 32 && h2 == 32); }
 
+bool train_shape_ok(int k, int h1, int h2);
+
+// The predictor is trained inside pc_compress (no weights given).
+bool wants_training(const pc_params* p) {
+  return (p->pred == PC_PRED_MLP_FP32 && !p->h_weights) || (p->pred == PC_PRED_MLP_BF16 && !p->h_qnet);
+}
+
 int check_params(const size_t dims[3], int dtype, const pc_params* p, Geo& g, int& mode, int& nw) {
   if (!dims || !p) return PC_ERR_ARG;
   if (dtype != PC_F32 && dtype != PC_F64) return PC_ERR_DTYPE;
   if (!(p->eb_rel > 0.0 && p->eb_rel < 1.0)) return PC_ERR_ARG;
   if (p->m < 2 || p->m > 16) return PC_ERR_ARG;
+  if (p->ndims < 0 || p->ndims > 3 || p->train_samples < 0) return PC_ERR_ARG;
+  for (int i = 0; i < 3 - p->ndims && p->ndims > 0; ++i)
+    if (dims[i] != 1) return PC_ERR_ARG;
   if (!make_geo(dims, p->block, g)) return PC_ERR_ARG;
   if (!shape_supported(p->block)) return PC_ERR_ARG;
   mode = p->pred == PC_PRED_MLP_FP32 ? 1 : (p->pred == PC_PRED_MLP_BF16 ? 2 : 0);
   if (p->pred != PC_PRED_LORENZO && p->pred != PC_PRED_MLP_FP32 && p->pred != PC_PRED_MLP_BF16) return PC_ERR_ARG;
   nw = 0;
   if (mode == 2) {
-    if (!qshape_ok(p->stencil, p->hidden[0], p->hidden[1]) || p->s_in < 0 || p->s_in > 30 || !p->h_qnet)
-      return PC_ERR_ARG;
+    if (!qshape_ok(p->stencil, p->hidden[0], p->hidden[1])) return PC_ERR_ARG;
+    if (!p->h_qnet) return PC_OK;  // trained inside pc_compress
+    if (p->s_in < 0 || p->s_in > 30) return PC_ERR_ARG;
     if (!qnet_valid(p->h_qnet, p->stencil, p->hidden[0], p->hidden[1], p->s_in)) return PC_ERR_ARG;
     nw = qnet_len(p->stencil, p->hidden[0], p->hidden[1]);
   } else if (mode) {
     if (p->stencil != 7 && p->stencil != 13) return PC_ERR_ARG;
     if (p->hidden[0] < 2 || p->hidden[0] > kMaxH || p->hidden[1] < 0 || p->hidden[1] > kMaxH) return PC_ERR_ARG;
-    if (p->s_in < 0 || p->s_in > 30 || !p->h_weights) return PC_ERR_ARG;
     nw = nweights(p->stencil, p->hidden[0], p->hidden[1]);
     if (nw > kMaxW) return PC_ERR_ARG;
+    if (!p->h_weights) {  // trained inside pc_compress
+      if (!train_shape_ok(p->stencil, p->hidden[0], p->hidden[1])) return PC_ERR_ARG;
+      return PC_OK;
+    }
+    if (p->s_in < 0 || p->s_in > 30) return PC_ERR_ARG;
   }
   return PC_OK;
 }
@@ -297,6 +312,22 @@ int train_check(const size_t dims[3], int dtype, const pc_params* p, int nmodels
   return PC_OK;
 }
 
+// Sampling threshold (of 2^32) of the training phase run inside pc_compress:
+// p->train_samples expected non-anchor samples, or 10% of them.
+unsigned int train_thr32(const size_t dims[3], const Geo& g, const pc_params* p) {
+  const double n = (double)dims[0] * (double)dims[1] * (double)dims[2] - (double)g.nblocks;
+  if (p->train_samples <= 0 || n <= 0.0) return (unsigned int)(0.1 * 4294967296.0);
+  const double t = (double)p->train_samples / n * 4294967296.0;
+  return t >= 4294967295.0 ? 4294967295u : (unsigned int)(t < 1.0 ? 1.0 : t);
+}
+
+// The library's (learning rate, L2 weight) grid of the training phase run
+// inside pc_compress (Section IV.C trains several settings and keeps the best;
+// the paper gives no values).
+constexpr int kTrainModels = 16;
+const float kGridLr[4] = {3e-3f, 1e-2f, 3e-2f, 1e-1f};
+const float kGridLam[4] = {0.0f, 1e-5f, 1e-4f, 1e-3f};
+
 }  // namespace
 
 extern "C" {
@@ -459,6 +490,8 @@ size_t pc_compress_bound(const size_t dims[3], int dtype, const pc_params* p) {
   Geo g;
   int mode, nw;
   if (check_params(dims, dtype, p, g, mode, nw) != PC_OK) return 0;
+  if (wants_training(p))  // the network chosen inside the call (or none)
+    nw = mode == 2 ? qnet_len(p->stencil, p->hidden[0], p->hidden[1]) : nweights(p->stencil, p->hidden[0], p->hidden[1]);
   const unsigned long long n = (unsigned long long)dims[0] * dims[1] * dims[2];
   const unsigned long long ts = dtype == PC_F64 ? 8 : 4;
   unsigned long long b = kHdr;
@@ -478,6 +511,11 @@ int pc_compress_workspace_size(const size_t dims[3], int dtype, const pc_params*
   if (st) return st;
   if (!ws) return PC_ERR_ARG;
   *ws = comp_layout(g, p->m).total;
+  if (wants_training(p)) {
+    const size_t tw = train_layout(g, p->m, p->stencil, nweights(p->stencil, p->hidden[0], p->hidden[1]),
+                                   train_thr32(dims, g, p), kTrainModels).total;
+    if (tw > *ws) *ws = tw;
+  }
   return PC_OK;
 }
 
@@ -501,6 +539,43 @@ int pc_compress(const void* d_field, const size_t dims[3], int dtype, const pc_p
   int st = check_params(dims, dtype, p, g, mode, nw);
   if (st) return st;
   if (!d_field || !d_out || !out_size || !d_ws) return PC_ERR_ARG;
+  if (wants_training(p)) {
+    // the learned part on the device (Section IV.C), then compression with its choice
+    size_t need = 0;
+    st = pc_compress_workspace_size(dims, dtype, p, &need);
+    if (st) return st;
+    if (ws_bytes < need) return PC_ERR_CAPACITY;
+    pc_params tp = *p;
+    tp.pred = PC_PRED_MLP_FP32;
+    tp.h_weights = nullptr;
+    tp.h_qnet = nullptr;
+    const int nwt = nweights(p->stencil, p->hidden[0], p->hidden[1]);
+    static thread_local float W[kTrainModels * kMaxW];
+    static thread_local long long Q[kQHdr + 2 * kMaxH * 13 + kMaxH * kMaxH + 4 * kMaxH + 1];
+    float lrs[kTrainModels], lams[kTrainModels];
+    for (int i = 0; i < kTrainModels; ++i) {
+      lrs[i] = kGridLr[i / 4];
+      lams[i] = kGridLam[i % 4];
+    }
+    const unsigned int thr32 = train_thr32(dims, g, p);
+    int s_in = 0, chosen = -1;
+    st = pc_train(d_field, dims, dtype, &tp, p->seed, thr32, kTrainModels, lrs, lams, W, &s_in, &chosen, nullptr,
+                  d_ws, ws_bytes, stream);
+    if (st) return st;
+    pc_params cp = *p;
+    if (chosen < 0) {
+      cp.pred = PC_PRED_LORENZO;
+    } else {
+      cp.s_in = s_in;
+      cp.h_weights = W + (size_t)chosen * nwt;
+      if (mode == 2) {
+        st = pc_quantize(d_field, dims, dtype, &cp, p->seed, thr32, Q, d_ws, ws_bytes, stream);
+        if (st) return st;
+        cp.h_qnet = Q;
+      }
+    }
+    return pc_compress(d_field, dims, dtype, &cp, d_out, out_cap, out_size, d_ws, ws_bytes, stream);
+  }
   CompLayout L = comp_layout(g, p->m);
   if (ws_bytes < L.total) return PC_ERR_CAPACITY;
   HdrInfo hi;

@@ -50,7 +50,8 @@ class PcError(RuntimeError):
 class pc_params(C.Structure):
     _fields_ = [("eb_rel", C.c_double), ("block", C.c_int * 3), ("pred", C.c_int), ("stencil", C.c_int),
                 ("hidden", C.c_int * 2), ("m", C.c_int), ("s_in", C.c_int), ("h_weights", C.c_void_p),
-                ("h_qnet", C.c_void_p)]
+                ("h_qnet", C.c_void_p), ("seed", C.c_ulonglong), ("train_samples", C.c_longlong),
+                ("ndims", C.c_int), ("reserved_", C.c_int)]
 
 
 def lib():
@@ -141,9 +142,15 @@ def _stream_ptr(stream):
 
 
 def make_params(eb_rel: float, block=(8, 8, 8), pred: int = PC_PRED_LORENZO, stencil: int = 7,
-                hidden=(16, 16), m: int = 16, s_in: int = 0, weights=None, qnet=None):
-    """Fill a pc_params struct; the weights and network arrays are kept alive on the struct."""
+                hidden=(16, 16), m: int = 16, s_in: int = 0, weights=None, qnet=None, seed: int = 0,
+                train_samples: int = 0, ndims: int = 0):
+    """Fill a pc_params struct; the weights and network arrays are kept alive on the struct.
+    With a perceptron form and no weights (or network), pc_compress trains one on the device."""
     p = pc_params()
+    p.seed = int(seed)
+    p.train_samples = int(train_samples)
+    p.ndims = int(ndims)
+    p.reserved_ = 0
     p.eb_rel = float(eb_rel)
     p.block[:] = [int(b) for b in block]
     p.pred = int(pred)

@@ -65,3 +65,33 @@ def test_trained_model_beats_lorenzo(pc, O):
     assert nn.numel() < 0.97 * lz.numel()
     y = pc.decompress(nn).cpu().numpy()
     assert np.all(np.abs(y.astype(np.float64) - x) <= 1e-2 * np.abs(x.astype(np.float64)))
+
+
+@pytest.mark.parametrize("pred,k,h,samples", [("fp32", 7, (16, 16), 0), ("bf16", 7, (16, 16), 0),
+                                              ("bf16", 13, (32, 32), 20000)])
+def test_compress_trains_when_no_weights_are_given(pc, O, pred, k, h, samples):
+    """pc_compress with a perceptron form and no weights runs the training phase
+    (and, for the fixed-point form, the quantization) on the device itself; the
+    container equals the oracle's, trained with the same seed, rate and grid."""
+    x = gen.positive_lognormal((24, 40, 48), 3.0, 7, 1.5)
+    eb, seed = 1e-2, 11
+    form = pc.PC_PRED_MLP_FP32 if pred == "fp32" else pc.PC_PRED_MLP_BF16
+    p = pc.make_params(eb, (8, 8, 8), pred=form, stencil=k, hidden=h, seed=seed, train_samples=samples, ndims=3)
+    blob = pc.compress(torch.from_numpy(x).cuda(), p).cpu().numpy().tobytes()
+    n = x.size - (x.shape[0] // 8) * (x.shape[1] // 8) * (x.shape[2] // 8)
+    thr = int(0.1 * 2 ** 32) if samples == 0 else int(samples / n * 2 ** 32)
+    best, W, s_in, _ = O.train(x, eb, k=k, h1=h[0], h2=h[1], seed=seed, thr32=thr)
+    if best < 0:
+        st, want = O.compress(x, eb)
+    elif pred == "fp32":
+        st, want = O.compress(x, eb, weights=W[best], stencil=k, h1=h[0], h2=h[1], s_in=s_in)
+    else:
+        q = O.quantize(x, eb, W[best], s_in, k=k, h1=h[0], h2=h[1], seed=seed, thr32=thr)
+        st, want = O.compress(x, eb, qnet=q, stencil=k, h1=h[0], h2=h[1], s_in=s_in)
+    assert st == 0 and blob == want
+
+
+def test_params_ndims_checked(pc):
+    p = pc.make_params(1e-2, (1, 16, 32), ndims=2)
+    assert pc.pc_compress_bound((1, 40, 50), pc.PC_F32, p) > 0
+    assert pc.pc_compress_bound((3, 40, 50), pc.PC_F32, p) == 0
