@@ -55,7 +55,7 @@ extern "C" {
 /* predictor forms */
 #define PC_PRED_LORENZO 0      /* Lorenzo only (Section IV.A) */
 #define PC_PRED_MLP_FP32 1     /* perceptron in FP32 on CUDA cores, Lorenzo per-block fallback */
-#define PC_PRED_MLP_BF16 2     /* fixed-point perceptron on bf16 tensor cores (pc_quantize), Lorenzo fallback */
+#define PC_PRED_MLP_BF16 2     /* fixed-point perceptron on the tensor cores (pc_quantize), Lorenzo fallback */
 
 typedef struct {
   double eb_rel;          /* pointwise relative bound b_r, 0 < eb_rel < 1 (Eq. 1) */
@@ -93,15 +93,20 @@ typedef struct {
 int pc_mlp_nweights(int k, int h1, int h2);
 
 /*
- * Fixed-point (BF16) form of the perceptron of Section IV.B, evaluated on
- * bf16 tensor cores with FP32 accumulation and bit-reproducible by
- * construction.  The network is an int64 array of pc_qnet_len(k, h1, h2)
+ * Fixed-point form of the perceptron of Section IV.B (the low-precision
+ * tensor-core form), bit-reproducible by construction.  Its weights are 8-bit
+ * integers, exact in bf16 and f16; the device evaluates it on the tensor cores
+ * with 16-bit operands holding 9-bit integer limbs of the inputs and
+ * activations and exact FP32 accumulation (tcgen05 with TMEM accumulators in
+ * compression, warp-level MMAs along the decoder's wavefronts).
+ * The network is an int64 array of pc_qnet_len(k, h1, h2)
  * entries: k, h1, h2, s_in, e1, e2, e3, t1, t2, then W1[h1][k], B1[h1],
  * W2[h2][h1], B2[h2], W3[h2], B3.
  *  - Weights of layer l are integers |W| <= 255 standing for W 2^-e_l.
  *  - Stencil inputs are the centred codes clamped to +-(2^16 - 1).
  *  - Each hidden layer computes A = sum W x + B (exact integer), then
- *    leaky(A) = A >= 0 ? A : A / 16, then H = clamp(rne(leaky(A) 2^-t), +-(2^15 - 1)).
+ *    leaky(A) = A >= 0 ? A : A / 16, then H = clamp(rhu(leaky(A) 2^-t), +-(2^15 - 1)),
+ *    rhu rounding halves up.
  *  - The output is pred = clamp(rne(A 2^-F), +-2^30), F = e1 + e2 + e3 - t1 - t2;
  *    rne rounds to nearest, ties to even.
  * Supported shapes: (k, h1, h2) = (7, 16, 16) and (13, 32, 32).

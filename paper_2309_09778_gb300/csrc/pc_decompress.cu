@@ -12,6 +12,7 @@
 // out-of-bounds access.
 #include "pc_kernels.cuh"
 #include "pc_qmlp.cuh"
+#include "pc_tcnet.cuh"
 #include "pc_profile.cuh"
 
 namespace pc {
@@ -365,10 +366,11 @@ struct ReconLayout {
   static constexpr int XS = BV + 1;   // block stride of the values
   static constexpr int CS = BV + 8;   // block stride of the codes (16-byte rows for vector copies)
   static constexpr size_t a16(size_t v) { return (v + 15) & ~(size_t)15; }
-  static constexpr size_t QB =
-      MODE == 2 ? a16((size_t)QShape<K, H1, H2>::NFRAG * 4 + (size_t)QShape<K, H1, H2>::NBIAS * 8 +
-                      (size_t)GR * max_wave<B0, B1, B2>() * 4)
-                : 0;
+  // fixed-point form: staged constants, B fragments, one wave's predictions
+  static constexpr int QH = H1 == 32 ? 32 : 16;
+  static constexpr size_t QB = MODE == 2 ? a16(sizeof(TcStage<QH>)) + a16(sizeof(WStage<QH>)) +
+                                               a16((size_t)GR * max_wave<B0, B1, B2>() * 4)
+                                         : 0;
   static constexpr size_t VP = sizeof(Tabs) + QB;
   static constexpr size_t X = VP + a16((size_t)GR * PVS * 4);
   static constexpr size_t L = X + a16((size_t)GR * XS * TSZ);
@@ -398,12 +400,12 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
   constexpr bool VEC_OK = (B2 * GR) % VW == 0;
   extern __shared__ __align__(16) unsigned char smem[];
   Tabs& tb = *reinterpret_cast<Tabs*>(smem);
-  constexpr int QK = MODE == 2 ? K : 7, QH1 = MODE == 2 ? H1 : 16, QH2 = MODE == 2 ? H2 : 16;
-  using QS = QShape<QK, QH1, QH2>;
-  uint32_t* s_frag = reinterpret_cast<uint32_t*>(smem + sizeof(Tabs));   // fixed-point form only
-  long long* s_qbias = reinterpret_cast<long long*>(s_frag + (MODE == 2 ? QS::NFRAG : 0));
-  int* s_wpred = reinterpret_cast<int*>(s_qbias + (MODE == 2 ? QS::NBIAS : 0));  // one wave's predictions
-  __shared__ QSc s_qsc;
+  constexpr int QK = MODE == 2 ? K : 7, QH = RL::QH;
+  // fixed-point form only: constants, fragments, one wave's predictions
+  TcStage<QH>& qst = *reinterpret_cast<TcStage<QH>*>(smem + sizeof(Tabs));
+  WStage<QH>& qwf = *reinterpret_cast<WStage<QH>*>(smem + sizeof(Tabs) + RL::a16(sizeof(TcStage<QH>)));
+  int* s_wpred = reinterpret_cast<int*>(smem + sizeof(Tabs) + RL::a16(sizeof(TcStage<QH>)) +
+                                        RL::a16(sizeof(WStage<QH>)));
   int* s_vp = reinterpret_cast<int*>(smem + RL::VP);             // GR padded blocks of centred codes
   T* s_x = reinterpret_cast<T*>(smem + RL::X);                    // GR blocks of values
   // BV points in wave order, each j | (padded index of j) << 16
@@ -434,7 +436,10 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
   for (int i = tid; i < GR * PVS; i += 256) s_vp[i] = 0;
   for (int i = tid; i < SZ + 2; i += 256) { s_ws[i] = 0; s_fill[i] = 0; }
   if (tid == 0) s_bad = 0;
-  if constexpr (MODE == 2) qnet_stage<QK, QH1, QH2>(di.qnet, s_frag, s_qbias, &s_qsc);
+  if constexpr (MODE == 2) {
+    tcnet_stage<QK, QH>(di.qnet, qst);
+    wnet_stage<QK, QH>(di.qnet, qwf);
+  }
   __syncthreads();
   for (int j = tid; j < BV; j += 256) {
     const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
@@ -574,25 +579,21 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
     // f / GR of the wave's list in block f % GR.
     const bool brick_full = e0 == B0 && e1 == B1 && W == GR * B2;
     if constexpr (MODE == 2) {
-      // Each wave in tiles of 16 points on the tensor cores; the lanes holding
-      // a tile's predictions finish its points.
-      const int wid = tid >> 5;
-      const QSc qsc = s_qsc;
-      int qoff[QS::KC1][4], qhi[QS::KC1][4];  // stencil offset; limb 1 hi, 0 lo, 2 padding
+      // Each wave in tiles of 16 points through warp-level MMAs (a wave of a
+      // few blocks is too narrow for 128-point tiles); the lanes of a quad
+      // hold its two points' predictions.
+      const int wid = tid >> 5, qc = lane & 3;
+      int qoff[4];  // stencil offsets of this thread's input columns 2c, 2c + 1, 2c + 8, 2c + 9
 #pragma unroll
-      for (int kc = 0; kc < QS::KC1; ++kc)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          int in, hi;
-          qcol<QK>(kc, e, in, hi);
-          qoff[kc][e] = in < 0 ? 0 : PD::off(st_dz(QK, in), st_dy(QK, in), st_dx(QK, in));
-          qhi[kc][e] = in < 0 ? 2 : hi;  // 2: padding column
-        }
+      for (int i = 0; i < 4; ++i) {
+        const int col = 2 * qc + (i & 1) + 8 * (i >> 1);
+        qoff[i] = col < QK ? PD::off(st_dz(QK, col), st_dy(QK, col), st_dx(QK, col)) : 0;
+      }
       for (int sw = 1; sw < nwave; ++sw) {
         const int w0 = s_ws[sw], S = s_ws[sw + 1] - w0;
         const int tot = GR * S;
         for (int tile = wid; tile * 16 < tot; tile += 8) {
-          int lv[2][QS::KC1][4];
+          int xv[2][4];
           int fs[2];
 #pragma unroll
           for (int r = 0; r < 2; ++r) {
@@ -601,17 +602,11 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
             const int fi = f < tot ? f : 0;
             const int pj = (fi % GR) * PVS + (int)(s_list[w0 + fi / GR] >> 16);
 #pragma unroll
-            for (int kc = 0; kc < QS::KC1; ++kc)
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                int v = qhi[kc][e] == 2 ? 0 : s_vp[pj + qoff[kc][e]];
-                v = v > kQIn ? kQIn : (v < -kQIn ? -kQIn : v);
-                lv[r][kc][e] = qlimb(v, qhi[kc][e]);
-              }
+            for (int i = 0; i < 4; ++i) xv[r][i] = s_vp[pj + qoff[i]];
           }
           int pq[2];
-          qnet_tile<QK, QH1, QH2>(s_frag, s_qbias, qsc, lv, pq[0], pq[1]);
-          if ((lane & 3) == 0) {
+          wnet_tile<QK, QH>(qwf, qst, xv, pq[0], pq[1]);
+          if (qc == 0) {
             if (fs[0] < tot) s_wpred[fs[0]] = pq[0];
             if (fs[1] < tot) s_wpred[fs[1]] = pq[1];
           }

@@ -255,3 +255,156 @@ __device__ __forceinline__ bool tcnet_tile(TcStage<H>& S, uint8_t* abuf, uint32_
 }
 
 }  // namespace pc
+
+namespace pc {
+
+// ---------------------------------------------------------------------------
+// The same exact evaluation with warp-level MMAs (mma.sync m16n8k16, f16 in,
+// f32 accumulate): a warp evaluates 16 points, each layer as two MMA sets
+// (hi limbs, lo limbs) against one weight matrix.  With lane = 4 g + c the
+// thread holds rows g and g + 8, columns 2c, 2c + 1 (+ 8) of A and of each
+// 16 x 8 accumulator block; an accumulator block pair is the next layer's A
+// fragment.  Used where waves are too narrow for 128-point tiles.
+// ---------------------------------------------------------------------------
+template <int H>
+struct WStage {
+  static constexpr int NB = H / 8;          // n-blocks of a layer
+  static constexpr int F1 = NB * 64;        // layer-1 B fragments (one k-chunk of 16 inputs)
+  static constexpr int F2 = (H / 16) * NB * 64;
+  uint32_t frag[F1 + F2];
+};
+
+// B fragment words of one 16 x 8 block: b0 = (k 2c, 2c + 1; n g), b1 = (k 2c + 8, 2c + 9; n g)
+template <int K, int H>
+__device__ void wnet_stage(const long long* __restrict__ q, WStage<H>& W) {
+  using S = WStage<H>;
+  const long long* W1 = q + kQHdr;
+  const long long* W2 = W1 + H * K + H;
+  for (int f = threadIdx.x; f < S::F1 + S::F2; f += blockDim.x) {
+    const bool l2 = f >= S::F1;
+    const int r = l2 ? f - S::F1 : f;
+    const int reg = r & 1, lane = (r >> 1) & 31, blk = r >> 6;
+    const int g = lane >> 2, c = lane & 3;
+    const int kc = l2 ? blk / S::NB : 0, nb = l2 ? blk % S::NB : blk;
+    const int n = nb * 8 + g;
+    const int k0 = kc * 16 + 2 * c + (reg ? 8 : 0);
+    long long w0, w1;
+    if (!l2) {
+      w0 = k0 < K ? W1[n * K + k0] : 0;
+      w1 = k0 + 1 < K ? W1[n * K + k0 + 1] : 0;
+    } else {
+      w0 = W2[n * H + k0];
+      w1 = W2[n * H + k0 + 1];
+    }
+    W.frag[f] = (uint32_t)f16_of_small(w0) | ((uint32_t)f16_of_small(w1) << 16);
+  }
+}
+
+__device__ __forceinline__ void mma_f16_sync(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// One hidden-layer element: accumulator limbs to the clamped activation.
+__device__ __forceinline__ int w_requant(float dh, float dl, float c, int cp, int cn, int t, int t4, int mul512) {
+  const uint32_t hb = __float_as_uint(__fadd_rn(dh, c));
+  const uint32_t lb = __float_as_uint(__fadd_rn(dl, c));
+  const uint32_t base = hb * (uint32_t)mul512 + lb;
+  const int p = (int)(base + (uint32_t)cp) >> t;
+  const int n = (int)(base + (uint32_t)cn) >> t4;
+  return max(-kQAct, min(kQAct, max(p, n)));
+}
+
+// Pack two activations (columns 2c, 2c + 1) as the next layer's hi and lo A words.
+__device__ __forceinline__ void w_pack(int h0, int h1, uint32_t& hi, uint32_t& lo) {
+  const uint32_t tw = __byte_perm((uint32_t)h0, (uint32_t)h1, 0x5410);
+  lo = (tw & 0x01FF01FFu) | 0x64006400u;
+  hi = ((tw >> 9) & 0x007F007Fu) ^ 0x64406440u;
+}
+
+// 16 points of a warp.  x[r][i]: this thread's inputs of row g (r = 0) and
+// g + 8 (r = 1) at columns 2c, 2c + 1, 2c + 8, 2c + 9 (i = 0..3; columns >= K
+// are ignored).  Returns the predictions of rows g and g + 8 in every lane of
+// the quad.
+template <int K, int H>
+__device__ __forceinline__ void wnet_tile(const WStage<H>& W, const TcStage<H>& S, const int (&x)[2][4], int& pred0,
+                                          int& pred1) {
+  constexpr int NB = H / 8;
+  const int lane = threadIdx.x & 31, c = lane & 3;
+  const int mul512 = S.mul512;
+  // layer 1: one k-chunk of 16 inputs
+  uint32_t ah[4], al[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = q & 1, half = q >> 1;  // a[0]: row g cols 2c.., a[1]: row g+8, a[2]/a[3]: cols 2c+8..
+    const int c0 = 2 * c + 8 * half;
+    uint32_t h0 = 0x6400u, l0 = 0x6400u, h1 = 0x6400u, l1 = 0x6400u;
+    if (c0 < K) tc_in_limbs(max(-kQIn, min(kQIn, x[r][2 * half])), h0, l0);
+    if (c0 + 1 < K) tc_in_limbs(max(-kQIn, min(kQIn, x[r][2 * half + 1])), h1, l1);
+    ah[q] = h0 | (h1 << 16);
+    al[q] = l0 | (l1 << 16);
+  }
+  float dh[NB][4], dl[NB][4];
+#pragma unroll
+  for (int nb = 0; nb < NB; ++nb) {
+    dh[nb][0] = dh[nb][1] = dh[nb][2] = dh[nb][3] = 0.0f;
+    dl[nb][0] = dl[nb][1] = dl[nb][2] = dl[nb][3] = 0.0f;
+    const uint2 b = reinterpret_cast<const uint2*>(W.frag)[nb * 32 + lane];
+    mma_f16_sync(dh[nb], ah, b.x, b.y);
+    mma_f16_sync(dl[nb], al, b.x, b.y);
+  }
+  int h[NB][4];
+#pragma unroll
+  for (int nb = 0; nb < NB; ++nb)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int u = nb * 8 + 2 * c + (e & 1);
+      h[nb][e] = w_requant(dh[nb][e], dl[nb][e], S.c1[u], S.cp1[u], S.cn1[u], S.t1, S.t1 + 4, mul512);
+    }
+  // layer 2: k-chunk kc covers the units of n-blocks 2 kc and 2 kc + 1
+#pragma unroll
+  for (int nb = 0; nb < NB; ++nb) {
+    dh[nb][0] = dh[nb][1] = dh[nb][2] = dh[nb][3] = 0.0f;
+    dl[nb][0] = dl[nb][1] = dl[nb][2] = dl[nb][3] = 0.0f;
+  }
+#pragma unroll
+  for (int kc = 0; kc < H / 16; ++kc) {
+    w_pack(h[2 * kc][0], h[2 * kc][1], ah[0], al[0]);
+    w_pack(h[2 * kc][2], h[2 * kc][3], ah[1], al[1]);
+    w_pack(h[2 * kc + 1][0], h[2 * kc + 1][1], ah[2], al[2]);
+    w_pack(h[2 * kc + 1][2], h[2 * kc + 1][3], ah[3], al[3]);
+#pragma unroll
+    for (int nb = 0; nb < NB; ++nb) {
+      const uint2 b = reinterpret_cast<const uint2*>(W.frag + WStage<H>::F1)[(kc * NB + nb) * 32 + lane];
+      mma_f16_sync(dh[nb], ah, b.x, b.y);
+      mma_f16_sync(dl[nb], al, b.x, b.y);
+    }
+  }
+  // layer 2 activations and the output unit on the CUDA cores: this thread's
+  // units of rows g (e = 0, 1) and g + 8 (e = 2, 3), summed over the quad
+  int acc0 = 0, acc1 = 0;
+#pragma unroll
+  for (int nb = 0; nb < NB; ++nb)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int u = nb * 8 + 2 * c + (e & 1);
+      const int a = w_requant(dh[nb][e], dl[nb][e], S.c2[u], S.cp2[u], S.cn2[u], S.t2, S.t2 + 4, mul512);
+      if (e < 2) acc0 += S.w3[u] * a;
+      else acc1 += S.w3[u] * a;
+    }
+#pragma unroll
+  for (int o = 1; o <= 2; o <<= 1) {
+    acc0 += __shfl_xor_sync(0xFFFFFFFFu, acc0, o);
+    acc1 += __shfl_xor_sync(0xFFFFFFFFu, acc1, o);
+  }
+  const long long lim = 1073741824ll;
+  long long o0 = rne_shift((long long)acc0 + S.b3, S.F);
+  long long o1 = rne_shift((long long)acc1 + S.b3, S.F);
+  pred0 = (int)(o0 > lim ? lim : (o0 < -lim ? -lim : o0));
+  pred1 = (int)(o1 > lim ? lim : (o1 < -lim ? -lim : o1));
+}
+
+}  // namespace pc
