@@ -647,6 +647,99 @@ def form_compare(torch, pc, w, args, stream, flush):
     return forms
 
 
+def run_batch64(torch, pc, args, dev, stream, flush, peak):
+    """The many-field batch: 32 2-D float32 fields 1800 x 3600 and 32 3-D float32 fields with dims drawn
+    uniformly from [64, 384]^3, spectral slopes drawn from [2, 5], eb_rel cycling 1e-2, 1e-3, 1e-4;
+    block shape per field from the autotuner, a fixed-point 7-point 16/16 perceptron trained on the
+    device per field (2^18 sampled stencils), everything through pc_compress_batch / pc_decompress_batch."""
+    from paper_2309_09778_gb300 import gen
+    from paper_2309_09778_gb300.autotune import BlockTuner
+    rng = np.random.default_rng(7)
+    t0 = time.perf_counter()
+    fields, ebs = [], []
+    for f in range(64):
+        shape = (1, 1800, 3600) if f < 32 else tuple(int(v) for v in rng.integers(64, 385, 3))
+        beta = float(rng.uniform(2.0, 5.0))
+        fields.append(gen.signed_lognormal_device(shape, beta, 100 + 10 * f, dev, 2.0, 0.05))
+        ebs.append((1e-2, 1e-3, 1e-4)[f % 3])
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    tuner = BlockTuner(os.environ.get("PC_AUTOTUNE_CACHE"))
+    t0 = time.perf_counter()
+    blocks = [tuner.choose(x, eb, "lorenzo", lambda b, eb=eb: pc.make_params(eb, b)) for x, eb in zip(fields, ebs)]
+    tune_s = time.perf_counter() - t0
+    lrs, lams = pc.default_grid()
+    params = []
+    t0 = time.perf_counter()
+    nn = 0
+    for x, eb, b in zip(fields, ebs, blocks):
+        thr = thr_for(tuple(x.shape), 1 << 18)
+        tp = pc.make_params(eb, b, pred=pc.PC_PRED_MLP_FP32, stencil=7, hidden=(16, 16))
+        ws = torch.empty(pc.pc_train_workspace_size(tuple(x.shape), pc.PC_F32, tp, thr, lrs.size), dtype=torch.uint8,
+                         device=dev)
+        W, s_in, chosen, _ = pc.pc_train(x, tp, 0, thr, lrs, lams, ws)
+        if chosen < 0:
+            params.append(pc.make_params(eb, b))
+            continue
+        p32 = pc.make_params(eb, b, pred=pc.PC_PRED_MLP_FP32, stencil=7, hidden=(16, 16), s_in=s_in,
+                             weights=W[chosen])
+        q = pc.pc_quantize(x, p32, 0, thr, ws)
+        params.append(pc.make_params(eb, b, pred=pc.PC_PRED_MLP_BF16, stencil=7, hidden=(16, 16), s_in=s_in, qnet=q))
+        nn += 1
+        del ws
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    wsb, outb = pc.pc_compress_batch_workspace_size(fields, params)
+    out = torch.empty(outb, dtype=torch.uint8, device=dev)
+    wsc = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    offs, sizes = pc.pc_compress_batch(fields, params, out, wsc, stream)
+    host = out.cpu().numpy()
+    hdrs = [host[offs[i]: offs[i] + 256].tobytes() for i in range(len(fields))]
+    del host
+    wsd = torch.empty(pc.pc_decompress_batch_workspace_size(hdrs), dtype=torch.uint8, device=dev)
+    ys = [torch.empty_like(x) for x in fields]
+    steps = max(3, min(args.steps, 6))
+    for _ in range(2):
+        offs, sizes = pc.pc_compress_batch(fields, params, out, wsc, stream)
+        pc.pc_decompress_batch(out, offs, sizes, ys, wsd, stream)
+    torch.cuda.synchronize()
+    ok = all(bool(((y.double() - x.double()).abs() <= eb * x.double().abs()).all().item())
+             for x, y, eb in zip(fields, ys, ebs))
+    pc.pc_profile_enable(True)
+    pc.pc_profile_read()
+    tc, td = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        offs, sizes = pc.pc_compress_batch(fields, params, out, wsc, stream)
+        e[1].record(stream)
+        pc.pc_decompress_batch(out, offs, sizes, ys, wsd, stream)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        tc.append(e[0].elapsed_time(e[1]))
+        td.append(e[1].elapsed_time(e[2]))
+    prof = pc.pc_profile_read()
+    pc.pc_profile_enable(False)
+    nbytes = sum(x.numel() * 4 for x in fields)
+    npts = sum(x.numel() for x in fields)
+    tcm, tdm = statistics.median(tc), statistics.median(td)
+    comp = sum(sizes)
+    stages = {k: v[0] / steps for k, v in prof.items() if v[1] > 0}
+    choice = {}
+    for b in blocks:
+        choice["x".join(str(v) for v in b)] = choice.get("x".join(str(v) for v in b), 0) + 1
+    return {"fields": len(fields), "points": npts, "input_bytes": nbytes,
+            "compress_gbs": nbytes / (tcm * 1e6), "decompress_gbs": nbytes / (tdm * 1e6),
+            "compress_ms": tcm, "decompress_ms": tdm, "bits_per_value": 8.0 * comp / npts, "bound_held": ok,
+            "perceptron_fields": nn, "block_shapes_chosen": choice, "autotune_trials": tuner.trials,
+            "hbm_frac_compress": (2 * nbytes + comp) / (tcm * 1e6) / peak["hbm_gbs"],
+            "hbm_frac_decompress": (nbytes + comp) / (tdm * 1e6) / peak["hbm_gbs"],
+            "compress_launches": {k: prof[k][1] / steps for k in ("compress",) if k in prof},
+            "stages_ms_per_step": stages,
+            "setup_seconds": {"generate": gen_s, "autotune": tune_s, "train_and_quantize": train_s}}
+
+
 def summary(w):
     res = w["res"]
     keep = ("compress_gbs", "decompress_gbs", "bits_per_value", "bound_held", "compress_ms", "decompress_ms",
@@ -773,6 +866,8 @@ def main():
             w["spec"].pop("_fields")
             del w
             torch.cuda.empty_cache()
+        secondary["batch64_uneven"] = run_batch64(torch, pc, args, dev, stream, flush, peak)
+        torch.cuda.empty_cache()
     clocks = head["clocks"]
     if rank == 0:
         line = {

@@ -178,6 +178,43 @@ int pc_decompress(const void* d_in, size_t in_size, void* d_field, size_t field_
                   size_t dims_out[3], int* dtype_out, void* d_ws, size_t ws_bytes, void* stream);
 
 /*
+ * Batched compression of nfields fields of uneven shapes and dtypes (the
+ * batching of many fields: each field is compressed exactly as pc_compress
+ * would, into its own container).  Fields that share dtype, block shape and
+ * predictor form (and, for PC_PRED_MLP_FP32, the same h_weights pointer) go
+ * through the hot kernel (a4-a9) in one persistent launch over their
+ * (field, brick) work list, up to 32 fields per launch; statistics, codebook
+ * and packing stay per field.  Every field needs explicit weights (no
+ * training inside the batch).  The stream is synchronized once, at the end.
+ *   dims      [in]  host, 3 * nfields sizes (field i: dims[3i .. 3i+2]).
+ *   dtypes, params [in] host, nfields each.
+ *   d_out     [out] container i starts at d_out + offsets[i] (offsets are
+ *                   the 256-byte aligned prefix sums of pc_compress_bound).
+ *   offsets   [out] host, nfields + 1;  sizes [out] host, container bytes.
+ *   d_ws      [scratch] pc_compress_batch_workspace_size bytes.
+ * Errors: as pc_compress (the first failing field's status); PC_ERR_ARG when a
+ * field asks for training.
+ */
+int pc_compress_batch_workspace_size(int nfields, const size_t* dims, const int* dtypes, const pc_params* params,
+                                     size_t* ws_bytes, size_t* out_bytes);
+int pc_compress_batch(int nfields, const void* const* d_fields, const size_t* dims, const int* dtypes,
+                      const pc_params* params, void* d_out, size_t out_cap, size_t* offsets, size_t* sizes,
+                      void* d_ws, size_t ws_bytes, void* stream);
+
+/*
+ * Batched decompression of nfields containers held in one device buffer
+ * (container i at d_in + offsets[i], sizes[i] bytes) into d_fields[i]
+ * (field_caps[i] bytes each).  Reads every header back in one
+ * synchronization, then runs each field's decoder without further host
+ * round trips; synchronizes once more at the end.  The workspace size comes
+ * from the 256-byte headers (host copies) through
+ * pc_decompress_batch_workspace_size.
+ */
+int pc_decompress_batch_workspace_size(int nfields, const void* const* h_headers, size_t* ws_bytes);
+int pc_decompress_batch(int nfields, const void* d_in, const size_t* offsets, const size_t* sizes,
+                        void* const* d_fields, const size_t* field_caps, void* d_ws, size_t ws_bytes, void* stream);
+
+/*
  * Decompression that allocates nothing, for callers that cannot obtain device
  * memory at the point of the call: hosts whose device-memory budget is fixed
  * up front, or plugins given only an input and an output buffer by a

@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "pc_kernels.cuh"
 #include "pc_qmlp.cuh"
@@ -328,6 +329,225 @@ constexpr int kTrainModels = 16;
 const float kGridLr[4] = {3e-3f, 1e-2f, 3e-2f, 1e-1f};
 const float kGridLam[4] = {0.0f, 1e-5f, 1e-4f, 1e-3f};
 
+// Everything one field's compression needs: layout of its workspace,
+// header values, device pointers.
+struct FieldPlan {
+  const void* x;
+  size_t dims[3];
+  int dtype, mode, nw, m;
+  double eb;
+  Geo g;
+  CompLayout L;
+  HdrInfo hi;
+  uint8_t* ws;
+  uint8_t* out;
+  State* stp;
+  Tabs* tabs;
+  unsigned long long* hist;
+  uint16_t* codes;
+  uint8_t* nnflag;
+  uint32_t* nout;
+  uint8_t* lens;
+  uint32_t* cw;
+  HuffScratch hs;
+  const long long* h_qnet;  // host network to copy into the container (fixed-point form)
+  const long long* qnet;    // its device copy in the container's weights section
+};
+
+// Lay out one field's compression (checked parameters, explicit weights).
+int plan_field(FieldPlan& F, const void* d_field, const size_t dims[3], int dtype, const pc_params* p, const Geo& g,
+               int mode, int nw, void* d_out, size_t out_cap, void* d_ws, size_t ws_bytes, Mlp& mlp) {
+  F.x = d_field;
+  for (int i = 0; i < 3; ++i) F.dims[i] = dims[i];
+  F.dtype = dtype;
+  F.mode = mode;
+  F.nw = nw;
+  F.m = p->m;
+  F.eb = p->eb_rel;
+  F.g = g;
+  F.L = comp_layout(g, p->m);
+  if (ws_bytes < F.L.total) return PC_ERR_CAPACITY;
+  HdrInfo& hi = F.hi;
+  hi.dtype = dtype;
+  hi.pred = mode;
+  hi.stencil = p->stencil;
+  hi.h1 = p->hidden[0];
+  hi.h2 = p->hidden[1];
+  hi.m = p->m;
+  hi.s_in = p->s_in;
+  hi.nw = nw;
+  hi.wsz = mode == 2 ? 8 : 4;
+  hi.eb = p->eb_rel;
+  hi.off_cb = al16(kHdr + (unsigned long long)hi.wsz * nw);
+  hi.cap = out_cap;
+  if (out_cap < hi.off_cb + 16) return PC_ERR_CAPACITY;
+  memset(&mlp, 0, sizeof(Mlp));
+  if (mode) {
+    mlp.k = p->stencil;
+    mlp.h1 = p->hidden[0];
+    mlp.h2 = p->hidden[1];
+    mlp.s_in = p->s_in;
+    if (mode == 1) memcpy(mlp.w, p->h_weights, sizeof(float) * (size_t)nw);
+  }
+  const CompLayout& L = F.L;
+  uint8_t* ws = static_cast<uint8_t*>(d_ws);
+  F.ws = ws;
+  F.out = static_cast<uint8_t*>(d_out);
+  F.stp = reinterpret_cast<State*>(ws + L.st);
+  F.tabs = reinterpret_cast<Tabs*>(ws + L.tabs);
+  F.hist = reinterpret_cast<unsigned long long*>(ws + L.hist);
+  F.codes = reinterpret_cast<uint16_t*>(ws + L.codes);
+  F.nnflag = reinterpret_cast<uint8_t*>(ws + L.nnflag);
+  F.nout = reinterpret_cast<uint32_t*>(ws + L.nout);
+  F.lens = reinterpret_cast<uint8_t*>(ws + L.lens);
+  F.cw = reinterpret_cast<uint32_t*>(ws + L.cw);
+  F.hs.key = reinterpret_cast<unsigned long long*>(ws + L.key);
+  F.hs.w = reinterpret_cast<unsigned long long*>(ws + L.w);
+  F.hs.parent = reinterpret_cast<int*>(ws + L.parent);
+  F.hs.depth = reinterpret_cast<int*>(ws + L.depth);
+  F.hs.la = reinterpret_cast<int*>(ws + L.la);
+  F.hs.lb = reinterpret_cast<int*>(ws + L.lb);
+  F.hs.rstart = reinterpret_cast<int*>(ws + L.rstart);
+  F.hs.symord = reinterpret_cast<unsigned int*>(ws + L.symord);
+  // the fixed-point network goes straight into the container's weights
+  // section, where the kernels read it
+  F.h_qnet = mode == 2 ? p->h_qnet : nullptr;
+  F.qnet = mode == 2 ? reinterpret_cast<const long long*>(F.out + kHdr) : nullptr;
+  return PC_OK;
+}
+
+// a1, a2 (and the network into the container)
+int launch_head(const FieldPlan& F, cudaStream_t s, int nsm) {
+  if (F.mode == 2 &&
+      cudaMemcpyAsync(F.out + kHdr, F.h_qnet, 8ull * F.nw, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return PC_ERR_CUDA;
+  const unsigned long long n = (unsigned long long)F.dims[0] * F.dims[1] * F.dims[2];
+  const int nsym = 1 << F.m;
+  return F.dtype == PC_F32 ? launch_stats_consts<float>(F.x, n, F.stp, F.tabs, F.hist, nsym, F.eb, nsm, s)
+                           : launch_stats_consts<double>(F.x, n, F.stp, F.tabs, F.hist, nsym, F.eb, nsm, s);
+}
+
+CJob job_of(const FieldPlan& F) {
+  CJob job{};
+  job.x = F.x;
+  job.g = F.g;
+  job.st = F.stp;
+  job.tabs = F.tabs;
+  job.codes = F.codes;
+  job.nnflag = F.nnflag;
+  job.nout = F.nout;
+  job.hist = F.hist;
+  job.qnet = F.qnet;
+  job.m = F.m;
+  return job;
+}
+
+// a10-a12
+int launch_tail(FieldPlan& F, const Mlp& mlp, cudaStream_t s) {
+  int r = launch_codebook(F.hist, F.m, F.lens, F.cw, F.stp, F.hs, F.out, F.g, F.hi, s);
+  if (r) return r;
+  const CompLayout& L = F.L;
+  auto* bbits = reinterpret_cast<uint32_t*>(F.ws + L.bbits);
+  auto* cb = reinterpret_cast<unsigned long long*>(F.ws + L.cbits);
+  auto* cn = reinterpret_cast<unsigned long long*>(F.ws + L.cnout);
+  auto* cbo = reinterpret_cast<unsigned long long*>(F.ws + L.cboff);
+  auto* coo = reinterpret_cast<unsigned long long*>(F.ws + L.cooff);
+  if (F.dtype == PC_F32)
+    return launch_pack<float>(static_cast<const float*>(F.x), F.g, F.codes, F.nnflag, F.nout, F.lens, F.cw, bbits, cb,
+                              cn, cbo, coo, F.stp, F.out, F.hi, mlp, s);
+  return launch_pack<double>(static_cast<const double*>(F.x), F.g, F.codes, F.nnflag, F.nout, F.lens, F.cw, bbits, cb,
+                             cn, cbo, coo, F.stp, F.out, F.hi, mlp, s);
+}
+
+// Everything one container's decompression needs.
+struct DecPlan {
+  Hdr H;
+  Geo g;
+  DecLayout L;
+  DecScratch ds;
+  DecInfo di;
+  const uint8_t* in;
+  void* out;
+};
+
+// Parse and check a container (hbuf: its first `pre` host bytes) and lay out
+// the decompression; fills the FP32 weights into mlp.
+int plan_dec(DecPlan& P, const uint8_t* hbuf, size_t pre, const void* d_in, size_t in_size, void* d_field,
+             size_t field_cap, void* d_ws, size_t ws_bytes, Mlp& mlp) {
+  Hdr& H = P.H;
+  int st = parse_header(hbuf, pre, H, P.g);
+  if (st) return st;
+  if (H.total > in_size) return PC_ERR_CORRUPT;
+  const size_t ts = H.dtype == PC_F64 ? 8 : 4;
+  const size_t n = H.dims[0] * H.dims[1] * H.dims[2];
+  if (field_cap < n * ts) return PC_ERR_CAPACITY;
+  P.L = dec_layout(P.g, H.m);
+  const DecLayout& L = P.L;
+  if (ws_bytes < L.total) return PC_ERR_CAPACITY;
+  memset(&mlp, 0, sizeof(Mlp));
+  if (H.pred == 1 || H.pred == 2) {
+    mlp.k = H.stencil;
+    mlp.h1 = H.h1;
+    mlp.h2 = H.h2;
+    mlp.s_in = H.s_in;
+  }
+  if (H.pred == 1) {
+    // nw <= kMaxW (checked with the header) and the container holds the section
+    if (kHdr + 4ull * H.nw > pre) return PC_ERR_CORRUPT;
+    memcpy(mlp.w, hbuf + kHdr, 4ull * H.nw);
+  }
+  uint8_t* ws = static_cast<uint8_t*>(d_ws);
+  DecScratch& ds = P.ds;
+  ds.err = reinterpret_cast<int*>(ws + L.err);
+  ds.ftab = reinterpret_cast<Tabs*>(ws + L.ftab);
+  ds.sorted = reinterpret_cast<uint16_t*>(ws + L.sorted);
+  ds.tabs = reinterpret_cast<unsigned int*>(ws + L.tabs);
+  ds.chunk_bits = reinterpret_cast<unsigned long long*>(ws + L.cbits);
+  ds.chunk_nout = reinterpret_cast<unsigned long long*>(ws + L.cnout);
+  ds.chunk_boff = reinterpret_cast<unsigned long long*>(ws + L.cboff);
+  ds.chunk_ooff = reinterpret_cast<unsigned long long*>(ws + L.cooff);
+  ds.boff = reinterpret_cast<unsigned long long*>(ws + L.boff);
+  ds.ooff = reinterpret_cast<unsigned long long*>(ws + L.ooff);
+  ds.codes = reinterpret_cast<uint16_t*>(ws + L.codes);
+  DecInfo& di = P.di;
+  di.dtype = H.dtype;
+  di.m = H.m;
+  di.stencil = H.pred != 0 ? H.stencil : 7;
+  di.h1 = H.h1;
+  di.h2 = H.h2;
+  di.s_in = H.s_in;
+  di.usenn_any = H.pred != 0;
+  di.qmode = H.pred == 2;
+  // the fixed-point network is read in place from the container
+  di.qnet = H.pred == 2 ? reinterpret_cast<const long long*>(static_cast<const uint8_t*>(d_in) + kHdr) : nullptr;
+  di.n_used = H.n_used;
+  di.n_out = H.n_out;
+  di.swords = H.swords;
+  di.off_cb = H.off_cb;
+  di.off_bb = H.off_bb;
+  di.off_bn = H.off_bn;
+  di.off_ov = H.off_ov;
+  di.off_st = H.off_st;
+  di.in_size = in_size;
+  di.Kp = H.Kp;
+  di.Kn = H.Kn;
+  di.Zq = H.Zq;
+  di.S = H.S;
+  di.step_bits = H.step_bits;
+  di.inv_bits = H.inv_bits;
+  di.ebdn_bits = H.ebdn_bits;
+  P.in = static_cast<const uint8_t*>(d_in);
+  P.out = d_field;
+  return PC_OK;
+}
+
+int launch_dec(const DecPlan& P, const Mlp& mlp, int nsm, cudaStream_t s) {
+  if (cudaMemsetAsync(P.ds.err, 0, sizeof(int), s) != cudaSuccess) return PC_ERR_CUDA;
+  return P.H.dtype == PC_F32
+             ? launch_decompress<float>(P.in, P.g, P.di, P.ds, mlp, static_cast<float*>(P.out), nsm, s)
+             : launch_decompress<double>(P.in, P.g, P.di, P.ds, mlp, static_cast<double*>(P.out), nsm, s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -576,94 +796,185 @@ int pc_compress(const void* d_field, const size_t dims[3], int dtype, const pc_p
     }
     return pc_compress(d_field, dims, dtype, &cp, d_out, out_cap, out_size, d_ws, ws_bytes, stream);
   }
-  CompLayout L = comp_layout(g, p->m);
-  if (ws_bytes < L.total) return PC_ERR_CAPACITY;
-  HdrInfo hi;
-  hi.dtype = dtype;
-  hi.pred = mode;
-  hi.stencil = p->stencil;
-  hi.h1 = p->hidden[0];
-  hi.h2 = p->hidden[1];
-  hi.m = p->m;
-  hi.s_in = p->s_in;
-  hi.nw = nw;
-  hi.wsz = mode == 2 ? 8 : 4;
-  hi.eb = p->eb_rel;
-  hi.off_cb = al16(kHdr + (unsigned long long)hi.wsz * nw);
-  hi.cap = out_cap;
-  if (out_cap < hi.off_cb + 16) return PC_ERR_CAPACITY;
   static thread_local Mlp mlp;
-  memset(&mlp, 0, sizeof(Mlp));
-  if (mode) {
-    mlp.k = p->stencil;
-    mlp.h1 = p->hidden[0];
-    mlp.h2 = p->hidden[1];
-    mlp.s_in = p->s_in;
-    if (mode == 1) memcpy(mlp.w, p->h_weights, sizeof(float) * (size_t)nw);
-  }
+  FieldPlan F;
+  st = plan_field(F, d_field, dims, dtype, p, g, mode, nw, d_out, out_cap, d_ws, ws_bytes, mlp);
+  if (st) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // the fixed-point network goes straight into the container's weights
-  // section, where the kernels read it
-  const long long* qnet = nullptr;
-  if (mode == 2) {
-    if (cudaMemcpyAsync(static_cast<uint8_t*>(d_out) + kHdr, p->h_qnet, 8ull * nw, cudaMemcpyHostToDevice, s) !=
-        cudaSuccess)
-      return PC_ERR_CUDA;
-    qnet = reinterpret_cast<const long long*>(static_cast<uint8_t*>(d_out) + kHdr);
-  }
   const int nsm = sm_count();
   if (nsm <= 0) return PC_ERR_CUDA;
-  uint8_t* ws = static_cast<uint8_t*>(d_ws);
-  uint8_t* out = static_cast<uint8_t*>(d_out);
-  State* stp = reinterpret_cast<State*>(ws + L.st);
-  Tabs* tabs = reinterpret_cast<Tabs*>(ws + L.tabs);
-  auto* hist = reinterpret_cast<unsigned long long*>(ws + L.hist);
-  auto* codes = reinterpret_cast<uint16_t*>(ws + L.codes);
-  auto* nnflag = reinterpret_cast<uint8_t*>(ws + L.nnflag);
-  auto* nout = reinterpret_cast<uint32_t*>(ws + L.nout);
-  auto* lens = reinterpret_cast<uint8_t*>(ws + L.lens);
-  auto* cw = reinterpret_cast<uint32_t*>(ws + L.cw);
-  HuffScratch hs;
-  hs.key = reinterpret_cast<unsigned long long*>(ws + L.key);
-  hs.w = reinterpret_cast<unsigned long long*>(ws + L.w);
-  hs.parent = reinterpret_cast<int*>(ws + L.parent);
-  hs.depth = reinterpret_cast<int*>(ws + L.depth);
-  hs.la = reinterpret_cast<int*>(ws + L.la);
-  hs.lb = reinterpret_cast<int*>(ws + L.lb);
-  hs.rstart = reinterpret_cast<int*>(ws + L.rstart);
-  hs.symord = reinterpret_cast<unsigned int*>(ws + L.symord);
-  const unsigned long long n = (unsigned long long)dims[0] * dims[1] * dims[2];
-  const int nsym = 1 << p->m;
-  int r;
-  if (dtype == PC_F32) {
-    r = launch_stats_consts<float>(d_field, n, stp, tabs, hist, nsym, p->eb_rel, nsm, s);
-    if (!r) r = launch_compress<float>(d_field, g, stp, tabs, codes, nnflag, nout, hist, p->m, mode, mlp, qnet, nsm, s);
-  } else {
-    r = launch_stats_consts<double>(d_field, n, stp, tabs, hist, nsym, p->eb_rel, nsm, s);
-    if (!r) r = launch_compress<double>(d_field, g, stp, tabs, codes, nnflag, nout, hist, p->m, mode, mlp, qnet, nsm,
-                                        s);
-  }
-  if (!r) r = launch_codebook(hist, p->m, lens, cw, stp, hs, out, g, hi, s);
+  int r = launch_head(F, s, nsm);
   if (!r) {
-    auto* bbits = reinterpret_cast<uint32_t*>(ws + L.bbits);
-    auto* cb = reinterpret_cast<unsigned long long*>(ws + L.cbits);
-    auto* cn = reinterpret_cast<unsigned long long*>(ws + L.cnout);
-    auto* cbo = reinterpret_cast<unsigned long long*>(ws + L.cboff);
-    auto* coo = reinterpret_cast<unsigned long long*>(ws + L.cooff);
-    if (dtype == PC_F32)
-      r = launch_pack<float>(static_cast<const float*>(d_field), g, codes, nnflag, nout, lens, cw, bbits, cb, cn, cbo,
-                             coo, stp, out, hi, mlp, s);
-    else
-      r = launch_pack<double>(static_cast<const double*>(d_field), g, codes, nnflag, nout, lens, cw, bbits, cb, cn,
-                              cbo, coo, stp, out, hi, mlp, s);
+    const CJob job = job_of(F);
+    r = dtype == PC_F32 ? launch_compress<float>(&job, 1, mode, mlp, nsm, s)
+                        : launch_compress<double>(&job, 1, mode, mlp, nsm, s);
   }
+  if (!r) r = launch_tail(F, mlp, s);
   if (r) return r;
   State hst;
-  if (cudaMemcpyAsync(&hst, stp, sizeof(State), cudaMemcpyDeviceToHost, s) != cudaSuccess) return PC_ERR_CUDA;
+  if (cudaMemcpyAsync(&hst, F.stp, sizeof(State), cudaMemcpyDeviceToHost, s) != cudaSuccess) return PC_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
   prof_collect();
   if (hst.err) return hst.err;
   *out_size = (size_t)hst.out_size;
+  return PC_OK;
+}
+
+int pc_compress_batch_workspace_size(int nfields, const size_t* dims, const int* dtypes, const pc_params* params,
+                                     size_t* ws_bytes, size_t* out_bytes) {
+  if (nfields < 1 || !dims || !dtypes || !params || !ws_bytes || !out_bytes) return PC_ERR_ARG;
+  size_t ws = 0, ob = 0;
+  for (int i = 0; i < nfields; ++i) {
+    Geo g;
+    int mode, nw;
+    int st = check_params(dims + 3 * i, dtypes[i], params + i, g, mode, nw);
+    if (st) return st;
+    if (wants_training(params + i)) return PC_ERR_ARG;
+    ws += up(comp_layout(g, params[i].m).total);
+    ob += up(pc_compress_bound(dims + 3 * i, dtypes[i], params + i));
+  }
+  *ws_bytes = ws;
+  *out_bytes = ob;
+  return PC_OK;
+}
+
+int pc_compress_batch(int nfields, const void* const* d_fields, const size_t* dims, const int* dtypes,
+                      const pc_params* params, void* d_out, size_t out_cap, size_t* offsets, size_t* sizes,
+                      void* d_ws, size_t ws_bytes, void* stream) {
+  if (nfields < 1 || !d_fields || !dims || !dtypes || !params || !d_out || !offsets || !sizes || !d_ws)
+    return PC_ERR_ARG;
+  size_t need_ws = 0, need_out = 0;
+  int st = pc_compress_batch_workspace_size(nfields, dims, dtypes, params, &need_ws, &need_out);
+  if (st) return st;
+  if (ws_bytes < need_ws || out_cap < need_out) return PC_ERR_CAPACITY;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int nsm = sm_count();
+  if (nsm <= 0) return PC_ERR_CUDA;
+  std::vector<FieldPlan> F((size_t)nfields);
+  std::vector<Mlp> mlps((size_t)nfields);
+  uint8_t* ws = static_cast<uint8_t*>(d_ws);
+  uint8_t* out = static_cast<uint8_t*>(d_out);
+  size_t wo = 0, oo = 0;
+  for (int i = 0; i < nfields; ++i) {
+    Geo g;
+    int mode, nw;
+    check_params(dims + 3 * i, dtypes[i], params + i, g, mode, nw);
+    const size_t wsz = up(comp_layout(g, params[i].m).total);
+    const size_t osz = up(pc_compress_bound(dims + 3 * i, dtypes[i], params + i));
+    offsets[i] = oo;
+    st = plan_field(F[i], d_fields[i], dims + 3 * i, dtypes[i], params + i, g, mode, nw, out + oo, osz, ws + wo, wsz,
+                    mlps[i]);
+    if (st) return st;
+    wo += wsz;
+    oo += osz;
+  }
+  offsets[nfields] = oo;
+  // a1, a2 per field
+  for (int i = 0; i < nfields; ++i)
+    if ((st = launch_head(F[i], s, nsm))) return st;
+  // a4-a9: one persistent launch per group of fields that share dtype, block
+  // shape and predictor form (and, for the FP32 form, the weights)
+  std::vector<int> done((size_t)nfields, 0);
+  std::vector<CJob> jl;
+  auto same_launch = [&](int i, int j) {
+    const pc_params& pi = params[i];
+    const pc_params& pj = params[j];
+    return dtypes[j] == dtypes[i] && F[j].mode == F[i].mode && pj.block[0] == pi.block[0] &&
+           pj.block[1] == pi.block[1] && pj.block[2] == pi.block[2] &&
+           (F[i].mode == 0 ||
+            (pj.stencil == pi.stencil && pj.hidden[0] == pi.hidden[0] && pj.hidden[1] == pi.hidden[1])) &&
+           (F[i].mode != 1 || (pj.h_weights == pi.h_weights && pj.s_in == pi.s_in));
+  };
+  for (;;) {
+    int i = 0;
+    while (i < nfields && done[i]) ++i;
+    if (i == nfields) break;
+    jl.clear();
+    for (int j = i; j < nfields && (int)jl.size() < kMaxJobs; ++j)
+      if (!done[j] && same_launch(i, j)) {
+        jl.push_back(job_of(F[j]));
+        done[j] = 1;
+      }
+    st = dtypes[i] == PC_F32 ? launch_compress<float>(jl.data(), (int)jl.size(), F[i].mode, mlps[i], nsm, s)
+                             : launch_compress<double>(jl.data(), (int)jl.size(), F[i].mode, mlps[i], nsm, s);
+    if (st) return st;
+  }
+  // a10-a12 per field
+  for (int i = 0; i < nfields; ++i)
+    if ((st = launch_tail(F[i], mlps[i], s))) return st;
+  std::vector<State> hs((size_t)nfields);
+  for (int i = 0; i < nfields; ++i)
+    if (cudaMemcpyAsync(&hs[i], F[i].stp, sizeof(State), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return PC_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
+  prof_collect();
+  int err = PC_OK;
+  for (int i = 0; i < nfields; ++i) {
+    if (hs[i].err && !err) err = hs[i].err;
+    sizes[i] = (size_t)hs[i].out_size;
+  }
+  return err;
+}
+
+int pc_decompress_batch_workspace_size(int nfields, const void* const* h_headers, size_t* ws_bytes) {
+  if (nfields < 1 || !h_headers || !ws_bytes) return PC_ERR_ARG;
+  size_t ws = 0;
+  for (int i = 0; i < nfields; ++i) {
+    size_t w = 0;
+    int st = pc_header_info(h_headers[i], kHdr, nullptr, nullptr, &w);
+    if (st) return st;
+    ws += up(w);
+  }
+  *ws_bytes = ws;
+  return PC_OK;
+}
+
+int pc_decompress_batch(int nfields, const void* d_in, const size_t* offsets, const size_t* sizes,
+                        void* const* d_fields, const size_t* field_caps, void* d_ws, size_t ws_bytes, void* stream) {
+  if (nfields < 1 || !d_in || !offsets || !sizes || !d_fields || !field_caps || !d_ws) return PC_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint8_t* in = static_cast<const uint8_t*>(d_in);
+  // every header (and FP32 weight section) in one read-back
+  const size_t hb = kHdr + 4 * kMaxW;
+  std::vector<uint8_t> hbuf((size_t)nfields * hb);
+  std::vector<size_t> pre((size_t)nfields);
+  for (int i = 0; i < nfields; ++i) {
+    if (sizes[i] < (size_t)kHdr) return PC_ERR_CORRUPT;
+    pre[i] = sizes[i] < hb ? sizes[i] : hb;
+    if (cudaMemcpyAsync(hbuf.data() + (size_t)i * hb, in + offsets[i], pre[i], cudaMemcpyDeviceToHost, s) !=
+        cudaSuccess)
+      return PC_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
+  const int nsm = sm_count();
+  if (nsm <= 0) return PC_ERR_CUDA;
+  std::vector<DecPlan> P((size_t)nfields);
+  std::vector<Mlp> mlps((size_t)nfields);
+  uint8_t* ws = static_cast<uint8_t*>(d_ws);
+  size_t wo = 0;
+  for (int i = 0; i < nfields; ++i) {
+    size_t w = 0;
+    int st = pc_header_info(hbuf.data() + (size_t)i * hb, kHdr, nullptr, nullptr, &w);
+    if (st) return st;
+    w = up(w);
+    if (wo + w > ws_bytes) return PC_ERR_CAPACITY;
+    st = plan_dec(P[i], hbuf.data() + (size_t)i * hb, pre[i], in + offsets[i], sizes[i], d_fields[i], field_caps[i],
+                  ws + wo, w, mlps[i]);
+    if (st) return st;
+    wo += w;
+  }
+  for (int i = 0; i < nfields; ++i) {
+    int st = launch_dec(P[i], mlps[i], nsm, s);
+    if (st) return st;
+  }
+  std::vector<int> errs((size_t)nfields, 0);
+  for (int i = 0; i < nfields; ++i)
+    if (cudaMemcpyAsync(&errs[i], P[i].ds.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return PC_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
+  prof_collect();
+  for (int i = 0; i < nfields; ++i)
+    if (errs[i]) return errs[i];
   return PC_OK;
 }
 
@@ -689,81 +1000,19 @@ int pc_decompress(const void* d_in, size_t in_size, void* d_field, size_t field_
   const size_t pre = in_size < sizeof(hbuf) ? in_size : sizeof(hbuf);
   if (cudaMemcpyAsync(hbuf, d_in, pre, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PC_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
-  Hdr H;
-  Geo g;
-  int st = parse_header(hbuf, kHdr, H, g);
-  if (st) return st;
-  if (H.total > in_size) return PC_ERR_CORRUPT;
-  const size_t ts = H.dtype == PC_F64 ? 8 : 4;
-  const size_t n = H.dims[0] * H.dims[1] * H.dims[2];
-  if (field_cap < n * ts) return PC_ERR_CAPACITY;
-  DecLayout L = dec_layout(g, H.m);
-  if (ws_bytes < L.total) return PC_ERR_CAPACITY;
   static thread_local Mlp mlp;
-  memset(&mlp, 0, sizeof(Mlp));
-  if (H.pred == 1 || H.pred == 2) {
-    mlp.k = H.stencil;
-    mlp.h1 = H.h1;
-    mlp.h2 = H.h2;
-    mlp.s_in = H.s_in;
-  }
-  if (H.pred == 1) {
-    // nw <= kMaxW (checked with the header) and the container holds the section
-    if (kHdr + 4ull * H.nw > pre) return PC_ERR_CORRUPT;
-    memcpy(mlp.w, hbuf + kHdr, 4ull * H.nw);
-  }
+  DecPlan P;
+  int st = plan_dec(P, hbuf, pre, d_in, in_size, d_field, field_cap, d_ws, ws_bytes, mlp);
+  if (st) return st;
   if (dims_out)
-    for (int i = 0; i < 3; ++i) dims_out[i] = H.dims[i];
-  if (dtype_out) *dtype_out = H.dtype;
-  uint8_t* ws = static_cast<uint8_t*>(d_ws);
-  DecScratch ds;
-  ds.err = reinterpret_cast<int*>(ws + L.err);
-  ds.ftab = reinterpret_cast<Tabs*>(ws + L.ftab);
-  ds.sorted = reinterpret_cast<uint16_t*>(ws + L.sorted);
-  ds.tabs = reinterpret_cast<unsigned int*>(ws + L.tabs);
-  ds.chunk_bits = reinterpret_cast<unsigned long long*>(ws + L.cbits);
-  ds.chunk_nout = reinterpret_cast<unsigned long long*>(ws + L.cnout);
-  ds.chunk_boff = reinterpret_cast<unsigned long long*>(ws + L.cboff);
-  ds.chunk_ooff = reinterpret_cast<unsigned long long*>(ws + L.cooff);
-  ds.boff = reinterpret_cast<unsigned long long*>(ws + L.boff);
-  ds.ooff = reinterpret_cast<unsigned long long*>(ws + L.ooff);
-  ds.codes = reinterpret_cast<uint16_t*>(ws + L.codes);
-  DecInfo di;
-  di.dtype = H.dtype;
-  di.m = H.m;
-  di.stencil = H.pred != 0 ? H.stencil : 7;
-  di.h1 = H.h1;
-  di.h2 = H.h2;
-  di.s_in = H.s_in;
-  di.usenn_any = H.pred != 0;
-  di.qmode = H.pred == 2;
-  // the fixed-point network is read in place from the container
-  di.qnet = H.pred == 2 ? reinterpret_cast<const long long*>(static_cast<const uint8_t*>(d_in) + kHdr) : nullptr;
-  di.n_used = H.n_used;
-  di.n_out = H.n_out;
-  di.swords = H.swords;
-  di.off_cb = H.off_cb;
-  di.off_bb = H.off_bb;
-  di.off_bn = H.off_bn;
-  di.off_ov = H.off_ov;
-  di.off_st = H.off_st;
-  di.in_size = in_size;
-  di.Kp = H.Kp;
-  di.Kn = H.Kn;
-  di.Zq = H.Zq;
-  di.S = H.S;
-  di.step_bits = H.step_bits;
-  di.inv_bits = H.inv_bits;
-  di.ebdn_bits = H.ebdn_bits;
-  if (cudaMemsetAsync(ds.err, 0, sizeof(int), s) != cudaSuccess) return PC_ERR_CUDA;
+    for (int i = 0; i < 3; ++i) dims_out[i] = P.H.dims[i];
+  if (dtype_out) *dtype_out = P.H.dtype;
   const int nsm = sm_count();
   if (nsm <= 0) return PC_ERR_CUDA;
-  const uint8_t* in = static_cast<const uint8_t*>(d_in);
-  int r = H.dtype == PC_F32 ? launch_decompress<float>(in, g, di, ds, mlp, static_cast<float*>(d_field), nsm, s)
-                            : launch_decompress<double>(in, g, di, ds, mlp, static_cast<double*>(d_field), nsm, s);
+  int r = launch_dec(P, mlp, nsm, s);
   if (r) return r;
   int err = 0;
-  if (cudaMemcpyAsync(&err, ds.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return PC_ERR_CUDA;
+  if (cudaMemcpyAsync(&err, P.ds.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return PC_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
   prof_collect();
   return err ? err : PC_OK;

@@ -222,12 +222,8 @@ struct CompLayout {
 };
 
 template <typename T, int B0, int B1, int B2, int MODE, int K, int H1, int H2>
-__global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restrict__ x, Geo g, const State* __restrict__ st,
-                                                   const Tabs* __restrict__ tabs, uint16_t* __restrict__ codes,
-                                                   uint8_t* __restrict__ nnflag, uint32_t* __restrict__ nout,
-                                                   unsigned long long* __restrict__ hist, int m,
-                                                   const __grid_constant__ Mlp mlp,
-                                                   const long long* __restrict__ qnet) {
+__global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const __grid_constant__ CJobs jobs,
+                                                                const __grid_constant__ Mlp mlp) {
   constexpr int BV = B0 * B1 * B2;
   using BS = BrickShape<BV>;
   constexpr int G = BS::G, TS = BS::TS, PPT = BS::PPT;
@@ -251,29 +247,17 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restr
   __shared__ int s_nz[G];
   __shared__ int s_da[G];
 
-  if (st->err) return;
-  int* errw = const_cast<int*>(&st->err);
-  State c;
-  c.Kp = st->Kp; c.Kn = st->Kn; c.Zq = st->Zq; c.S = st->S;
-  c.step32 = st->step32; c.inv32 = st->inv32; c.ebdn32 = st->ebdn32;
-  c.stepd = st->stepd; c.invd = st->invd; c.ebdnd = st->ebdnd;
   const int tid = threadIdx.x;
-  for (int i = tid; i < (int)(sizeof(Tabs) / 4); i += 256)
-    reinterpret_cast<float*>(&tb)[i] = reinterpret_cast<const float*>(tabs)[i];
   for (int i = tid; i < G * PD::PV; i += 256) s_vp[i] = 0;
   for (int i = tid; i < kHistWin; i += 256) s_hist[i] = 0u;
-  const int R = 1 << (m - 1);
-  const int hbase = R - kHistWin / 2 > 0 ? R - kHistWin / 2 : 0;
   const float sig = MODE ? __uint_as_float((unsigned int)(127 - mlp.s_in) << 23) : 1.0f;
   const float unsig = MODE ? __uint_as_float((unsigned int)(127 + mlp.s_in) << 23) : 1.0f;
-  const bool vec_rows = VEC_OK && (g.n[2] % VW == 0) && ((reinterpret_cast<uintptr_t>(x) & 15u) == 0);
-  // fixed-point form: the network in shared memory, TMEM for the two
-  // warpgroups' accumulators (2 limbs x QH columns each)
+  // fixed-point form: TMEM for the two warpgroups' accumulators (2 limbs x QH
+  // columns each); the network is staged per field
   constexpr uint32_t kTmemCols = QH == 32 ? 128 : 64;
   uint32_t tmem_base = 0, tc_phase = 0;
   bool tc_ok = true;
   if constexpr (MODE == 2) {
-    tcnet_stage<QK, QH>(qnet, tcs);
     if (tid < 32) {
       tc::tmem_alloc(&tcs.tmem, kTmemCols);
       tc::tmem_relinquish();
@@ -290,13 +274,68 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restr
     tc::fence_after_sync();
     tmem_base = tcs.tmem;
   }
-
-  const long long nbx = (g.nb[2] + G - 1) / G;
-  const long long nbricks = g.nb[0] * g.nb[1] * nbx;
+  __shared__ int s_skip;
+  // the current field (in shared memory, reloaded uniformly over the CTA when
+  // the brick sequence enters the next field; kept out of registers)
+  __shared__ CJob s_job;
+  int jcur = -1;
+  const Geo& g = s_job.g;
+  uint16_t* const& codes = s_job.codes;
+  uint8_t* const& nnflag = s_job.nnflag;
+  uint32_t* const& nout = s_job.nout;
+  unsigned long long* const& hist = s_job.hist;
+  int* errw = nullptr;
+  State c;
+  int R = 2;
+  bool jskip = true;
+  // per-field scalars of the brick loop, also in shared memory
+  __shared__ long long s_nbx, s_jb0;
+  __shared__ int s_m, s_hbase, s_vec;
+  const long long& nbx = s_nbx;
+  const int& m = s_m;
+  const int& hbase = s_hbase;
+  auto flush_hist = [&]() {
+    __syncthreads();
+    for (int i = tid; i < kHistWin; i += 256) {
+      const unsigned int h = s_hist[i];
+      if (h && hbase + i < (1 << m)) atomicAdd(&hist[hbase + i], (unsigned long long)h);
+      s_hist[i] = 0u;
+    }
+  };
   const int team = tid / TS, t = tid % TS;
   int* dq = s_dq + team * BV;
   int* vp = s_vp + team * PD::PV;
-  for (long long brick = blockIdx.x; brick < nbricks; brick += gridDim.x) {
+  for (long long gbk = blockIdx.x; gbk < jobs.total; gbk += gridDim.x) {
+    int jn = jcur < 0 ? 0 : jcur;
+    while (jn + 1 < jobs.n && gbk >= jobs.j[jn + 1].brick0) ++jn;
+    if (jn != jcur) {
+      if (jcur >= 0 && !jskip) flush_hist();
+      const CJob& J = jobs.j[jn];
+      jcur = jn;
+      __syncthreads();  // the previous field's last brick is done with the tables and s_job
+      if (tid == 0) s_job = J;
+      errw = const_cast<int*>(&J.st->err);
+      R = 1 << (J.m - 1);
+      if (tid == 0) {
+        s_m = J.m;
+        s_hbase = R - kHistWin / 2 > 0 ? R - kHistWin / 2 : 0;
+        s_nbx = (J.g.nb[2] + G - 1) / G;
+        s_jb0 = J.brick0;
+        s_vec = VEC_OK && (J.g.n[2] % VW == 0) && ((reinterpret_cast<uintptr_t>(J.x) & 15u) == 0);
+        s_skip = J.st->err != 0;
+      }
+      c.Kp = J.st->Kp; c.Kn = J.st->Kn; c.Zq = J.st->Zq; c.S = J.st->S;
+      c.step32 = J.st->step32; c.inv32 = J.st->inv32; c.ebdn32 = J.st->ebdn32;
+      c.stepd = J.st->stepd; c.invd = J.st->invd; c.ebdnd = J.st->ebdnd;
+      for (int i = tid; i < (int)(sizeof(Tabs) / 4); i += 256)
+        reinterpret_cast<float*>(&tb)[i] = reinterpret_cast<const float*>(J.tabs)[i];
+      if constexpr (MODE == 2) tcnet_stage<QK, QH>(J.qnet, tcs);
+      __syncthreads();
+      jskip = s_skip != 0;
+    }
+    if (jskip) continue;
+    const long long brick = gbk - s_jb0;
+    const bool vec_rows = s_vec != 0;
     const long long bxg = brick % nbx;
     const long long byz = brick / nbx;
     const long long by = byz % g.nb[1];
@@ -317,7 +356,7 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restr
     constexpr bool VEC_FITS = ((NV + 255) / 256) * VW <= EPT;
     const bool vecb = VEC_FITS && fullb && vec_rows;
     const long long n12 = g.n[1] * g.n[2];
-    const T* base = x + z0 * n12 + y0 * g.n[2] + x0;
+    const T* base = static_cast<const T*>(s_job.x) + z0 * n12 + y0 * g.n[2] + x0;
     T vals[EPT];
     if (vecb) {
 #pragma unroll
@@ -424,6 +463,10 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restr
         if ((tid & 31) == 0 && costn) atomicAdd(&s_cost[gb][1], costn);
       }
       __syncthreads();
+      if (!tc_ok) {
+        atomicExch(errw, PC_ERR_TIMEOUT);
+        tc_ok = true;
+      }
     }
     const long long bx = bxg * G + team;
     const bool bvalid = bx < g.nb[2];
@@ -588,12 +631,8 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const T* __restr
     }
     __syncthreads();
   }
-  for (int i = tid; i < kHistWin; i += 256) {
-    const unsigned int h = s_hist[i];
-    if (h && hbase + i < (1 << m)) atomicAdd(&hist[hbase + i], (unsigned long long)h);
-  }
+  if (jcur >= 0 && !jskip) flush_hist();
   if constexpr (MODE == 2) {
-    if (!tc_ok) atomicExch(errw, PC_ERR_TIMEOUT);
     tc::fence_before_sync();
     __syncthreads();
     if (tid < 32) tc::tmem_dealloc(tmem_base, kTmemCols);
@@ -617,9 +656,7 @@ template int launch_stats_consts<double>(const void*, unsigned long long, State*
                                          double, int, cudaStream_t);
 
 template <typename T, int B0, int B1, int B2, int MODE, int K, int H1, int H2>
-static int launch_c(const void* x, const Geo& g, const State* st, const Tabs* tabs, uint16_t* codes, uint8_t* nnflag,
-                    uint32_t* nout, unsigned long long* hist, int m, const Mlp& mlp, const long long* qnet, int nsm,
-                    cudaStream_t s) {
+static int launch_c(const CJobs& jobs, const Mlp& mlp, int nsm, cudaStream_t s) {
   constexpr int BV = B0 * B1 * B2;
   constexpr bool WIDE = MODE != 0 && (K == 13 || K == 0);
   auto kern = k_compress<T, B0, B1, B2, MODE, K, H1, H2>;
@@ -627,13 +664,13 @@ static int launch_c(const void* x, const Geo& g, const State* st, const Tabs* ta
   static_assert(sm <= 232448, "shared memory per CTA");
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
     return PC_ERR_CUDA;
-  // the whole unified L1 as shared memory, so that two CTAs fit on an SM
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
-      cudaSuccess)
-    return PC_ERR_CUDA;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm);
   if constexpr (MODE == 2) {
+    // the whole unified L1 as shared memory, so that two CTAs fit on an SM
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+      return PC_ERR_CUDA;
     // The occupancy query reports one CTA per SM for the tensor-core form;
     // registers (launch bounds) and shared memory allow two, and two CTAs
     // hold 2 x 128 (or 2 x 64) of the 512 TMEM columns.
@@ -641,46 +678,46 @@ static int launch_c(const void* x, const Geo& g, const State* st, const Tabs* ta
     per_sm = by_smem >= 2 ? 2 : 1;
   }
   if (per_sm < 1) per_sm = 1;
-  constexpr int G = BrickShape<BV>::G;
-  long long nbricks = g.nb[0] * g.nb[1] * ((g.nb[2] + G - 1) / G);
   long long grid = (long long)nsm * per_sm;
-  if (grid > nbricks) grid = nbricks;
+  if (grid > jobs.total) grid = jobs.total;
   if (grid < 1) grid = 1;
   {
     ProfScope p(kStCompress, s);
-    kern<<<(unsigned int)grid, 256, sm, s>>>(static_cast<const T*>(x), g, st, tabs, codes, nnflag, nout, hist, m, mlp,
-                                             qnet);
+    kern<<<(unsigned int)grid, 256, sm, s>>>(jobs, mlp);
   }
   return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
 
 template <typename T, int B0, int B1, int B2>
-static int launch_c_shape(const void* x, const Geo& g, const State* st, const Tabs* tabs, uint16_t* codes,
-                          uint8_t* nnflag, uint32_t* nout, unsigned long long* hist, int m, int mode, const Mlp& mlp,
-                          const long long* qnet, int nsm, cudaStream_t s) {
-  if (mode == 0)
-    return launch_c<T, B0, B1, B2, 0, 0, 0, 0>(x, g, st, tabs, codes, nnflag, nout, hist, m, mlp, qnet, nsm, s);
+static int launch_c_shape(const CJobs& jobs, int mode, const Mlp& mlp, int nsm, cudaStream_t s) {
+  if (mode == 0) return launch_c<T, B0, B1, B2, 0, 0, 0, 0>(jobs, mlp, nsm, s);
   if (mode == 2) {
-    if (mlp.k == 7 && mlp.h1 == 16 && mlp.h2 == 16)
-      return launch_c<T, B0, B1, B2, 2, 7, 16, 16>(x, g, st, tabs, codes, nnflag, nout, hist, m, mlp, qnet, nsm, s);
-    if (mlp.k == 13 && mlp.h1 == 32 && mlp.h2 == 32)
-      return launch_c<T, B0, B1, B2, 2, 13, 32, 32>(x, g, st, tabs, codes, nnflag, nout, hist, m, mlp, qnet, nsm, s);
+    if (mlp.k == 7 && mlp.h1 == 16 && mlp.h2 == 16) return launch_c<T, B0, B1, B2, 2, 7, 16, 16>(jobs, mlp, nsm, s);
+    if (mlp.k == 13 && mlp.h1 == 32 && mlp.h2 == 32) return launch_c<T, B0, B1, B2, 2, 13, 32, 32>(jobs, mlp, nsm, s);
     return PC_ERR_ARG;
   }
-  if (mlp.k == 7 && mlp.h1 == 16 && mlp.h2 == 16)
-    return launch_c<T, B0, B1, B2, 1, 7, 16, 16>(x, g, st, tabs, codes, nnflag, nout, hist, m, mlp, qnet, nsm, s);
-  if (mlp.k == 13 && mlp.h1 == 32 && mlp.h2 == 32)
-    return launch_c<T, B0, B1, B2, 1, 13, 32, 32>(x, g, st, tabs, codes, nnflag, nout, hist, m, mlp, qnet, nsm, s);
-  return launch_c<T, B0, B1, B2, 1, 0, 0, 0>(x, g, st, tabs, codes, nnflag, nout, hist, m, mlp, qnet, nsm, s);
+  if (mlp.k == 7 && mlp.h1 == 16 && mlp.h2 == 16) return launch_c<T, B0, B1, B2, 1, 7, 16, 16>(jobs, mlp, nsm, s);
+  if (mlp.k == 13 && mlp.h1 == 32 && mlp.h2 == 32) return launch_c<T, B0, B1, B2, 1, 13, 32, 32>(jobs, mlp, nsm, s);
+  return launch_c<T, B0, B1, B2, 1, 0, 0, 0>(jobs, mlp, nsm, s);
 }
 
 template <typename T>
-int launch_compress(const void* x, const Geo& g, const State* st, const Tabs* tabs, uint16_t* codes, uint8_t* nnflag,
-                    uint32_t* nout, unsigned long long* hist, int m, int mode, const Mlp& mlp,
-                    const long long* qnet, int nsm, cudaStream_t s) {
+int launch_compress(const CJob* jl, int n, int mode, const Mlp& mlp, int nsm, cudaStream_t s) {
+  if (n < 1 || n > kMaxJobs) return PC_ERR_ARG;
+  static thread_local CJobs jobs;
+  jobs.n = n;
+  jobs.total = 0;
+  const Geo& g = jl[0].g;
+  for (int i = 0; i < n; ++i) {
+    if (jl[i].g.b[0] != g.b[0] || jl[i].g.b[1] != g.b[1] || jl[i].g.b[2] != g.b[2]) return PC_ERR_ARG;
+    jobs.j[i] = jl[i];
+    jobs.j[i].brick0 = jobs.total;
+    const int G = jl[i].g.bvol <= 512 ? 8 : (jl[i].g.bvol <= 1024 ? 4 : (jl[i].g.bvol <= 2048 ? 2 : 1));
+    jobs.total += jl[i].g.nb[0] * jl[i].g.nb[1] * ((jl[i].g.nb[2] + G - 1) / G);
+  }
   const int b0 = g.b[0], b1 = g.b[1], b2 = g.b[2];
 #define PC_SHAPE(A, B, C) \
-  if (b0 == A && b1 == B && b2 == C) return launch_c_shape<T, A, B, C>(x, g, st, tabs, codes, nnflag, nout, hist, m, mode, mlp, qnet, nsm, s);
+  if (b0 == A && b1 == B && b2 == C) return launch_c_shape<T, A, B, C>(jobs, mode, mlp, nsm, s);
   PC_SHAPE(8, 8, 8)
   PC_SHAPE(4, 4, 4)
   PC_SHAPE(16, 16, 16)
@@ -690,11 +727,7 @@ int launch_compress(const void* x, const Geo& g, const State* st, const Tabs* ta
 #undef PC_SHAPE
   return PC_ERR_ARG;
 }
-template int launch_compress<float>(const void*, const Geo&, const State*, const Tabs*, uint16_t*, uint8_t*,
-                                    uint32_t*, unsigned long long*, int, int, const Mlp&, const long long*, int,
-                                    cudaStream_t);
-template int launch_compress<double>(const void*, const Geo&, const State*, const Tabs*, uint16_t*, uint8_t*,
-                                     uint32_t*, unsigned long long*, int, int, const Mlp&, const long long*, int,
-                                     cudaStream_t);
+template int launch_compress<float>(const CJob*, int, int, const Mlp&, int, cudaStream_t);
+template int launch_compress<double>(const CJob*, int, int, const Mlp&, int, cudaStream_t);
 
 }  // namespace pc

@@ -112,10 +112,35 @@ __host__ __device__ inline unsigned long long al16(unsigned long long x) { retur
 template <typename T>
 int launch_stats_consts(const void* x, unsigned long long n, State* st, Tabs* tabs, unsigned long long* hist,
                         int nsym, double eb, int nsm, cudaStream_t s);
+// One field of a fused compression launch: its input, geometry, per-call
+// state (constants, tables, histogram) and outputs.  brick0 is the field's
+// first brick in the launch's brick numbering (fields in order).
+struct CJob {
+  const void* x;
+  Geo g;
+  const State* st;
+  const Tabs* tabs;
+  uint16_t* codes;
+  uint8_t* nnflag;
+  uint32_t* nout;
+  unsigned long long* hist;
+  const long long* qnet;  // fixed-point network (container weights section) or null
+  long long brick0;
+  int m;
+  int pad_;
+};
+constexpr int kMaxJobs = 32;  // fields per fused launch (the table travels as a kernel parameter)
+struct CJobs {
+  int n;
+  int pad_;
+  long long total;  // bricks of all fields
+  CJob j[kMaxJobs];
+};
+
+// Compression of n fields that share dtype, block shape and predictor form
+// (and, for the FP32 perceptron, the weights mlp) in one persistent launch.
 template <typename T>
-int launch_compress(const void* x, const Geo& g, const State* st, const Tabs* tabs, uint16_t* codes, uint8_t* nnflag,
-                    uint32_t* nout, unsigned long long* hist, int m, int mode, const Mlp& mlp,
-                    const long long* qnet, int nsm, cudaStream_t s);
+int launch_compress(const CJob* jobs, int n, int mode, const Mlp& mlp, int nsm, cudaStream_t s);
 int launch_codebook(const unsigned long long* hist, int m, uint8_t* lens, uint32_t* cw, State* st,
                     const HuffScratch& hs, uint8_t* out, const Geo& g, const HdrInfo& hi, cudaStream_t s);
 template <typename T>

@@ -71,6 +71,47 @@ def grf_device(shape, beta: float, seed: int, device):
     return g
 
 
+def grf_torch_noise(shape, beta: float, seed: int, device):
+    """Gaussian random field with spectrum |k|^-beta from torch's own seeded
+    device generator (white noise drawn on the device; float64, mean 0, sd 1).
+    Used for the many-field batch, where drawing the noise on the host would
+    dominate; deterministic for a given seed, device type and torch version."""
+    import torch
+    shape = tuple(int(s) for s in shape)
+    gen_ = torch.Generator(device=device)
+    gen_.manual_seed(int(seed))
+    white = torch.randn(shape, generator=gen_, dtype=torch.float64, device=device)
+    spec = torch.fft.rfftn(white)
+    del white
+    k2 = torch.zeros((), dtype=torch.float64, device=device)
+    for ax, n in enumerate(shape):
+        f = torch.fft.rfftfreq(n, dtype=torch.float64, device=device) if ax == len(shape) - 1 else \
+            torch.fft.fftfreq(n, dtype=torch.float64, device=device)
+        k2 = k2 + (f ** 2).reshape([-1 if a == ax else 1 for a in range(len(shape))])
+    spec *= torch.where(k2 > 0, k2.clamp_min(1e-300) ** (-beta / 4.0), torch.zeros_like(k2))
+    g = torch.fft.irfftn(spec, s=shape, dim=tuple(range(len(shape))))
+    del spec
+    g -= g.mean()
+    sd = g.std(correction=0)
+    if sd > 0:
+        g /= sd
+    return g
+
+
+def signed_lognormal_device(shape, beta: float, seed: int, device, log_scale: float = 2.0,
+                            zero_frac: float = 0.05):
+    """signed_lognormal() drawn entirely on the device (grf_torch_noise), float32 tensor."""
+    import torch
+    x = torch.exp(log_scale * grf_torch_noise(shape, beta, seed, device))
+    x *= torch.where(grf_torch_noise(shape, beta, seed + 1, device) >= 0, 1.0, -1.0)
+    if zero_frac > 0:
+        g3 = grf_torch_noise(shape, beta, seed + 2, device).float()
+        k = max(1, int(round(zero_frac * g3.numel())))
+        thr = torch.kthvalue(g3.reshape(-1), k).values.item()
+        x = torch.where(g3 < thr, torch.zeros_like(x), x)
+    return x.to(torch.float32)
+
+
 def density_velocity_pair(shape, device, seed_density: int = 0, seed_velocity: int = 3):
     """The 512^3-style pair: positive density exp(1.5 G), G with spectrum k^-2, and a
     signed velocity-like G with spectrum k^-4; float32 torch tensors on `device`."""

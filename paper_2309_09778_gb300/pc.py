@@ -25,7 +25,8 @@ STATUS = {0: "PC_OK", -1: "PC_ERR_ARG", -2: "PC_ERR_DTYPE", -3: "PC_ERR_NONFINIT
 SYMBOLS = ["pc_mlp_nweights", "pc_compress_bound", "pc_compress_workspace_size", "pc_compress",
            "pc_header_info", "pc_decompress", "pc_decompress_noalloc", "pc_compress_host", "pc_decompress_host",
            "pc_train_workspace_size", "pc_train", "pc_compress_workspace_layout", "pc_profile_enable",
-           "pc_profile_read", "pc_profile_stage_name", "pc_strerror"]
+           "pc_profile_read", "pc_profile_stage_name", "pc_strerror", "pc_compress_batch_workspace_size",
+           "pc_compress_batch", "pc_decompress_batch_workspace_size", "pc_decompress_batch"]
 
 
 # (lr, lambda) grid trained side by side in the training phase (Section IV.C
@@ -97,6 +98,15 @@ def lib():
                 L.pc_qnet_len.argtypes = [C.c_int, C.c_int, C.c_int]
                 L.pc_quantize.restype = C.c_int
                 L.pc_quantize.argtypes = [vp, szp, C.c_int, P, C.c_ulonglong, C.c_uint, vp, vp, sz, vp]
+            L.pc_compress_batch_workspace_size.restype = C.c_int
+            L.pc_compress_batch_workspace_size.argtypes = [C.c_int, szp, C.POINTER(C.c_int), P, szp, szp]
+            L.pc_compress_batch.restype = C.c_int
+            L.pc_compress_batch.argtypes = [C.c_int, C.POINTER(C.c_void_p), szp, C.POINTER(C.c_int), P, vp, sz, szp,
+                                            szp, vp, sz, vp]
+            L.pc_decompress_batch_workspace_size.restype = C.c_int
+            L.pc_decompress_batch_workspace_size.argtypes = [C.c_int, C.POINTER(C.c_void_p), szp]
+            L.pc_decompress_batch.restype = C.c_int
+            L.pc_decompress_batch.argtypes = [C.c_int, vp, szp, szp, C.POINTER(C.c_void_p), szp, vp, sz, vp]
             L.pc_profile_enable.restype = C.c_int
             L.pc_profile_enable.argtypes = [C.c_int]
             L.pc_profile_read.restype = C.c_int
@@ -297,6 +307,56 @@ def pc_quantize(field, params: pc_params, seed: int, thr32: int, ws, stream=None
                            ws.numel(), _stream_ptr(stream))
     _check(st, "pc_quantize")
     return q
+
+
+def _batch_args(fields, params):
+    n = len(fields)
+    dims = (C.c_size_t * (3 * n))(*[d for f in fields for d in _dims3(f.shape)])
+    dts = (C.c_int * n)(*[_dtype_of(f) for f in fields])
+    ps = (pc_params * n)(*params)
+    return n, dims, dts, ps
+
+
+def pc_compress_batch_workspace_size(fields, params):
+    """(workspace bytes, output bytes) of a batched compression of these fields."""
+    n, dims, dts, ps = _batch_args(fields, params)
+    ws, ob = C.c_size_t(), C.c_size_t()
+    _check(lib().pc_compress_batch_workspace_size(n, dims, dts, ps, C.byref(ws), C.byref(ob)),
+           "pc_compress_batch_workspace_size")
+    return ws.value, ob.value
+
+
+def pc_compress_batch(fields, params, out, ws, stream=None):
+    """Compress device tensors `fields` (each with its pc_params) into the uint8 device buffer `out`.
+    Returns (offsets [n + 1], sizes [n])."""
+    n, dims, dts, ps = _batch_args(fields, params)
+    ptrs = (C.c_void_p * n)(*[f.data_ptr() for f in fields])
+    offs = (C.c_size_t * (n + 1))()
+    sizes = (C.c_size_t * n)()
+    st = lib().pc_compress_batch(n, ptrs, dims, dts, ps, C.c_void_p(out.data_ptr()), out.numel(), offs, sizes,
+                                 C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream))
+    _check(st, "pc_compress_batch")
+    return list(offs), list(sizes)
+
+
+def pc_decompress_batch_workspace_size(headers):
+    """headers: list of 256-byte host copies of the containers' headers."""
+    bufs = [np.frombuffer(bytes(h[:256]), np.uint8).copy() for h in headers]
+    ptrs = (C.c_void_p * len(bufs))(*[b.ctypes.data for b in bufs])
+    ws = C.c_size_t()
+    _check(lib().pc_decompress_batch_workspace_size(len(bufs), ptrs, C.byref(ws)), "pc_decompress_batch_workspace_size")
+    return ws.value
+
+
+def pc_decompress_batch(blob, offsets, sizes, outs, ws, stream=None):
+    n = len(outs)
+    offs = (C.c_size_t * n)(*offsets[:n])
+    szs = (C.c_size_t * n)(*sizes)
+    ptrs = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+    caps = (C.c_size_t * n)(*[o.numel() * o.element_size() for o in outs])
+    st = lib().pc_decompress_batch(n, C.c_void_p(blob.data_ptr()), offs, szs, ptrs, caps, C.c_void_p(ws.data_ptr()),
+                                   ws.numel(), _stream_ptr(stream))
+    _check(st, "pc_decompress_batch")
 
 
 def pc_profile_enable(on: bool) -> None:
