@@ -93,6 +93,9 @@ def lib():
             L.orc_mlp_fwd64.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]
             L.orc_mlp_pred64.restype = C.c_int32
             L.orc_mlp_pred64.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]
+            L.orc_block_codes.restype = C.c_int
+            L.orc_block_codes.argtypes = [C.c_void_p, u64p, C.c_int, C.POINTER(Consts), C.POINTER(Params), C.c_uint64,
+                                          C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
             L.orc_pred_report.restype = C.c_int
             L.orc_pred_report.argtypes = [C.c_void_p, u64p, C.c_int, C.c_double, C.POINTER(C.c_int), C.c_int,
                                           C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
@@ -396,6 +399,23 @@ def compress(x: np.ndarray, eb: float, block=(8, 8, 8), weights=None, stencil=7,
     if dump:
         return st, blob, d
     return st, blob
+
+
+def block_codes(x: np.ndarray, consts, bi: int, eb: float, block=(8, 8, 8), weights=None, stencil=7, h1=16, h2=16,
+                m: int = 16, s_in: int = 0, qnet=None):
+    """Codes (as stored) and perceptron flag of block bi, from the field's constants `consts`
+    (consts_for of the whole field); only the block's points are transformed."""
+    x = np.ascontiguousarray(x)
+    w = None if weights is None else np.ascontiguousarray(weights, np.float32)
+    q = None if qnet is None else np.ascontiguousarray(qnet, np.int64)
+    pred = PRED_MLP_BF16 if q is not None else (PRED_MLP if w is not None else PRED_LORENZO)
+    p = _params(eb, block, pred, stencil, h1, h2, m, s_in, w, q)
+    codes = np.zeros(block[0] * block[1] * block[2], np.uint16)
+    usen, npts = C.c_int(), C.c_int()
+    st = lib().orc_block_codes(_p(x), _dims(x), _dtype_code(x), C.byref(consts), C.byref(p), int(bi), _p(codes),
+                               C.byref(usen), C.byref(npts))
+    assert st == 0, st
+    return codes[: npts.value], bool(usen.value)
 
 
 def read_header(blob: bytes):

@@ -832,6 +832,58 @@ uint64_t orc_compress_bound(const uint64_t dims[3], int dtype, const int block[3
   return b;
 }
 
+/* a5-a8 of one block (Section IV.A, IV.B, IV.D; Alg. 1): dqb[j], okb[j] are
+ * the codes and bound flags of the block's points in local raster order
+ * (e0 x e1 x e2, truncated at the field's edge).  Centres the codes on the
+ * anchor (j = 0), predicts every other point by Lorenzo and, if use_nn, by
+ * the perceptron from its causal in-block neighbours, quantizes both into
+ * cz / cn (code k + R, or 0 for a balance point), and returns 1 when the
+ * perceptron's residual bits are strictly fewer (the block then uses cn). */
+static int o_block(const int32_t* dqb, const uint8_t* okb, int e0, int e1, int e2, const orc_params* p, int use_nn,
+                   int use_q, int use_64, int k, int64_t R, int32_t* vc, int64_t* vt, uint16_t* cz, uint16_t* cn) {
+  int32_t da = dqb[0];
+  for (int j = 0; j < e0 * e1 * e2; j++) {
+    int64_t v = (int64_t)dqb[j] - (int64_t)da;
+    vt[j] = v;
+    vc[j] = (int32_t)(v > O_VCLAMP ? O_VCLAMP : (v < -O_VCLAMP ? -O_VCLAMP : v));
+  }
+  int64_t costz = 0, costn = 0;
+  for (int lz = 0; lz < e0; lz++)
+    for (int ly = 0; ly < e1; ly++)
+      for (int lx = 0; lx < e2; lx++) {
+        int j = (lz * e1 + ly) * e2 + lx;
+        if (j == 0) continue;
+        int32_t in7[7];
+        for (int i = 0; i < 7; i++) {
+          int qz = lz + O_S7[i][0], qy = ly + O_S7[i][1], qx = lx + O_S7[i][2];
+          in7[i] = (qz >= 0 && qy >= 0 && qx >= 0) ? vc[(qz * e1 + qy) * e2 + qx] : 0;
+        }
+        int64_t kz = vt[j] - o_lorenzo(in7);
+        int64_t az = kz < 0 ? -kz : kz;
+        costz += o_bitlen((uint64_t)(az < R ? az : R));
+        cz[j] = (uint16_t)((az <= R - 1 && okb[j]) ? kz + R : 0);
+        if (use_nn) {
+          int32_t in[13];
+          for (int i = 0; i < k; i++) {
+            int dz, dy, dx;
+            o_stencil(k, i, &dz, &dy, &dx);
+            int qz = lz + dz, qy = ly + dy, qx = lx + dx;
+            in[i] = (qz >= 0 && qy >= 0 && qx >= 0 && qz < e0 && qy < e1 && qx < e2) ? vc[(qz * e1 + qy) * e2 + qx]
+                                                                                      : 0;
+          }
+          int64_t pr = use_q ? (int64_t)orc_mlp_pred_q(p->qnet, in)
+                       : use_64 ? (int64_t)orc_mlp_pred64(p->weights, k, p->h1, p->h2, p->s_in, in)
+                                : (int64_t)orc_mlp_pred32(p->weights, k, p->h1, p->h2, p->s_in, in);
+          int64_t kn = vt[j] - pr;
+          int64_t an = kn < 0 ? -kn : kn;
+          costn += o_bitlen((uint64_t)(an < R ? an : R));
+          cn[j] = (uint16_t)((an <= R - 1 && okb[j]) ? kn + R : 0);
+        }
+      }
+  /* a7: perceptron only where it is strictly cheaper than Lorenzo */
+  return use_nn && costn < costz;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Algorithm 1: compression.                                                  */
 /* ------------------------------------------------------------------------- */
@@ -883,6 +935,8 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
   int64_t* vt = (int64_t*)malloc(sizeof(int64_t) * g.bvol);
   uint16_t* cz = (uint16_t*)malloc(sizeof(uint16_t) * g.bvol);
   uint16_t* cn = (uint16_t*)malloc(sizeof(uint16_t) * g.bvol);
+  int32_t* dqb = (int32_t*)malloc(sizeof(int32_t) * g.bvol);
+  uint8_t* okb = (uint8_t*)malloc(g.bvol);
   uint64_t n_out = 0;
   uint64_t bi = 0;
   for (uint64_t bz = 0; bz < g.nb[0]; bz++)
@@ -893,53 +947,15 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
         int e1 = (int)((dims[1] - o1) < (uint64_t)p->block[1] ? dims[1] - o1 : (uint64_t)p->block[1]);
         int e2 = (int)((dims[2] - o2) < (uint64_t)p->block[2] ? dims[2] - o2 : (uint64_t)p->block[2]);
         int np = e0 * e1 * e2;
-        uint64_t ia = (o0 * dims[1] + o1) * dims[2] + o2;
-        int32_t da = dq[ia];
         for (int lz = 0; lz < e0; lz++)
           for (int ly = 0; ly < e1; ly++)
             for (int lx = 0; lx < e2; lx++) {
               int j = (lz * e1 + ly) * e2 + lx;
               uint64_t ig = ((o0 + lz) * dims[1] + (o1 + ly)) * dims[2] + (o2 + lx);
-              int64_t v = (int64_t)dq[ig] - (int64_t)da;
-              vt[j] = v;
-              vc[j] = (int32_t)(v > O_VCLAMP ? O_VCLAMP : (v < -O_VCLAMP ? -O_VCLAMP : v));
+              dqb[j] = dq[ig];
+              okb[j] = okv[ig];
             }
-        int64_t costz = 0, costn = 0;
-        for (int lz = 0; lz < e0; lz++)
-          for (int ly = 0; ly < e1; ly++)
-            for (int lx = 0; lx < e2; lx++) {
-              int j = (lz * e1 + ly) * e2 + lx;
-              if (j == 0) continue;
-              uint64_t ig = ((o0 + lz) * dims[1] + (o1 + ly)) * dims[2] + (o2 + lx);
-              int32_t in7[7];
-              for (int i = 0; i < 7; i++) {
-                int qz = lz + O_S7[i][0], qy = ly + O_S7[i][1], qx = lx + O_S7[i][2];
-                in7[i] = (qz >= 0 && qy >= 0 && qx >= 0) ? vc[(qz * e1 + qy) * e2 + qx] : 0;
-              }
-              int64_t kz = vt[j] - o_lorenzo(in7);
-              int64_t az = kz < 0 ? -kz : kz;
-              costz += o_bitlen((uint64_t)(az < R ? az : R));
-              cz[j] = (uint16_t)((az <= R - 1 && okv[ig]) ? kz + R : 0);
-              if (use_nn) {
-                int32_t in[13];
-                for (int i = 0; i < k; i++) {
-                  int dz, dy, dx;
-                  o_stencil(k, i, &dz, &dy, &dx);
-                  int qz = lz + dz, qy = ly + dy, qx = lx + dx;
-                  in[i] = (qz >= 0 && qy >= 0 && qx >= 0 && qz < e0 && qy < e1 && qx < e2)
-                              ? vc[(qz * e1 + qy) * e2 + qx] : 0;
-                }
-                int64_t pr = use_q ? (int64_t)orc_mlp_pred_q(p->qnet, in)
-                             : use_64 ? (int64_t)orc_mlp_pred64(p->weights, k, p->h1, p->h2, p->s_in, in)
-                                      : (int64_t)orc_mlp_pred32(p->weights, k, p->h1, p->h2, p->s_in, in);
-                int64_t kn = vt[j] - pr;
-                int64_t an = kn < 0 ? -kn : kn;
-                costn += o_bitlen((uint64_t)(an < R ? an : R));
-                cn[j] = (uint16_t)((an <= R - 1 && okv[ig]) ? kn + R : 0);
-              }
-            }
-        /* a7: perceptron only where it is strictly cheaper than Lorenzo */
-        int usen = use_nn && costn < costz;
+        int usen = o_block(dqb, okb, e0, e1, e2, p, use_nn, use_q, use_64, k, R, vc, vt, cz, cn);
         nnf[bi] = (uint8_t)usen;
         const uint16_t* cs = usen ? cn : cz;
         int no = 1;  /* the anchor */
@@ -1077,7 +1093,7 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
     if (dump->lens) memcpy(dump->lens, lens, (size_t)nsym);
   }
 done:
-  free(order); free(bbits); free(cw); free(lens); free(cz); free(cn); free(vt); free(vc);
+  free(order); free(bbits); free(cw); free(lens); free(cz); free(dqb); free(okb); free(cn); free(vt); free(vc);
   free(hist); free(nout); free(nnf); free(codes); free(okv); free(dq);
   return ret;
 }
@@ -1752,5 +1768,57 @@ int orc_pred_report(const void* x, const uint64_t dims[3], int dtype, double eb,
             }
       }
   free(vt); free(vc); free(dq);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* The codes of block bi of a field exactly as orc_compress stores them, with */
+/* the field's constants c (orc_stats + orc_make_consts of the whole field);  */
+/* only the block's points are transformed.  A test aid that checks sampled   */
+/* blocks of fields too large to compress here in full.  codes[j] for local   */
+/* raster j < *npts (codes[0] = 0, the anchor); *usen = perceptron chosen.    */
+/* ------------------------------------------------------------------------- */
+int orc_block_codes(const void* x, const uint64_t dims[3], int dtype, const orc_consts* c, const orc_params* p,
+                    uint64_t bi, uint16_t* codes, int* usen, int* npts) {
+  if (dtype != ORC_F32 && dtype != ORC_F64) return ORC_ERR_DTYPE;
+  if (p->m < 2 || p->m > 16) return ORC_ERR_ARG;
+  o_geom g;
+  if (o_geom_make(dims, p->block, &g)) return ORC_ERR_ARG;
+  if (bi >= g.nblocks) return ORC_ERR_ARG;
+  int use_q = p->pred == ORC_PRED_MLP_BF16 && p->qnet != NULL;
+  int use_64 = p->pred == ORC_PRED_MLP64 && p->weights != NULL;
+  int use_nn = ((p->pred == ORC_PRED_MLP || use_64) && p->weights != NULL) || use_q;
+  int k = p->stencil;
+  if (use_nn && (k != 7 && k != 13)) return ORC_ERR_ARG;
+  int64_t R = (int64_t)1 << (p->m - 1);
+  uint64_t bz = bi / (g.nb[1] * g.nb[2]), by = (bi / g.nb[2]) % g.nb[1], bx = bi % g.nb[2];
+  uint64_t o0 = bz * p->block[0], o1 = by * p->block[1], o2 = bx * p->block[2];
+  int e0 = (int)((dims[0] - o0) < (uint64_t)p->block[0] ? dims[0] - o0 : (uint64_t)p->block[0]);
+  int e1 = (int)((dims[1] - o1) < (uint64_t)p->block[1] ? dims[1] - o1 : (uint64_t)p->block[1]);
+  int e2 = (int)((dims[2] - o2) < (uint64_t)p->block[2] ? dims[2] - o2 : (uint64_t)p->block[2]);
+  int np = e0 * e1 * e2;
+  int32_t* dqb = (int32_t*)malloc(sizeof(int32_t) * (size_t)np);
+  uint8_t* okb = (uint8_t*)malloc((size_t)np);
+  int32_t* vc = (int32_t*)malloc(sizeof(int32_t) * (size_t)np);
+  int64_t* vt = (int64_t*)malloc(sizeof(int64_t) * (size_t)np);
+  uint16_t* cz = (uint16_t*)calloc((size_t)np, sizeof(uint16_t));
+  uint16_t* cn = (uint16_t*)calloc((size_t)np, sizeof(uint16_t));
+  for (int lz = 0; lz < e0; lz++)
+    for (int ly = 0; ly < e1; ly++)
+      for (int lx = 0; lx < e2; lx++) {
+        int j = (lz * e1 + ly) * e2 + lx;
+        uint64_t ig = ((o0 + lz) * dims[1] + (o1 + ly)) * dims[2] + (o2 + lx);
+        int ok;
+        if (dtype == ORC_F32) orc_transform32(((const float*)x)[ig], c, &dqb[j], &ok);
+        else orc_transform64(((const double*)x)[ig], c, &dqb[j], &ok);
+        okb[j] = (uint8_t)ok;
+      }
+  int un = o_block(dqb, okb, e0, e1, e2, p, use_nn, use_q, use_64, k, R, vc, vt, cz, cn);
+  const uint16_t* cs = un ? cn : cz;
+  codes[0] = 0;
+  for (int j = 1; j < np; j++) codes[j] = cs[j];
+  *usen = un;
+  *npts = np;
+  free(dqb); free(okb); free(vc); free(vt); free(cz); free(cn);
   return ORC_OK;
 }

@@ -140,3 +140,25 @@ def test_corrupt_streams_are_rejected(O):
         st, y = O.decompress(bytes(bad))
         assert st in (0, -5)   # never a crash; payload damage may decode to other values
     assert O.decompress(blob[: len(blob) - 16])[0] == -5
+
+
+@pytest.mark.parametrize("form", ["lorenzo", "fp32", "fixed"])
+def test_block_codes_equal_full_compression(O, form):
+    """The per-block export (used to check sampled blocks of full-size fields)
+    gives every block's stored codes and perceptron flag exactly as the full
+    compressor does, truncated edge blocks included."""
+    x = gen.signed_lognormal((19, 21, 26), 3.0, 8, 2.0, 0.05)
+    eb = 1e-2
+    kw = {}
+    if form != "lorenzo":
+        best, W, s_in, _ = O.train(x, eb, k=7, h1=16, h2=16, seed=2)
+        w = W[best if best >= 0 else 0]
+        kw = dict(weights=w, s_in=s_in) if form == "fp32" else dict(qnet=O.quantize(x, eb, w, s_in, seed=2), s_in=s_in)
+    st, blob, d = O.compress(x, eb, dump=True, **kw)
+    assert st == 0
+    c = O.consts_for(x, eb)
+    nb = 3 * 3 * 4
+    for bi in range(nb):
+        codes, usen = O.block_codes(x, c, bi, eb, **kw)
+        assert usen == bool(d["nnflag"][bi])
+        assert np.array_equal(codes[1:], d["codes"][bi * 512 + 1: bi * 512 + codes.size])
