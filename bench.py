@@ -268,12 +268,21 @@ def sha_of(*paths):
 # sources it was captured from and is dropped (traffic null) once they change.
 TRAFFIC = {
     # (workload, stage, form): (bytes per launch, sha of the sources, profile summary)
+    # captured on 256 x 256 x 512 (one quarter of a 512^3 field, same recipe and network shape) and scaled by
+    # the points processed: 69.3 MB read + 78.3 MB written there
+    ("density_velocity_512", "recon", "bf16"): (4 * (69315328 + 78289920), "861f7ef307e09a83",
+                                                "profiles/k_recon_c3_wmma.md"),
+    # 134.9 MB read + 38.9 MB written on the same quarter-size case
+    ("density_velocity_512", "compress", "bf16"): (4 * (134882304 + 38942208), "42c3e2ad57556c7f",
+                                                   "profiles/k_compress_c3_tcgen05.md"),
 }
 STAGE_SOURCES = {
-    "compress": ("paper_2309_09778_gb300/csrc/pc_compress.cu", "paper_2309_09778_gb300/csrc/pc_qmlp.cuh",
-                 "paper_2309_09778_gb300/csrc/pc_device.cuh"),
-    "recon": ("paper_2309_09778_gb300/csrc/pc_decompress.cu", "paper_2309_09778_gb300/csrc/pc_qmlp.cuh",
-              "paper_2309_09778_gb300/csrc/pc_device.cuh"),
+    "compress": ("paper_2309_09778_gb300/csrc/pc_compress.cu", "paper_2309_09778_gb300/csrc/pc_tcnet.cuh",
+                 "paper_2309_09778_gb300/csrc/pc_tc.cuh", "paper_2309_09778_gb300/csrc/pc_qmlp.cuh",
+                 "paper_2309_09778_gb300/csrc/pc_device.cuh", "paper_2309_09778_gb300/csrc/pc_kernels.cuh"),
+    "recon": ("paper_2309_09778_gb300/csrc/pc_decompress.cu", "paper_2309_09778_gb300/csrc/pc_tcnet.cuh",
+              "paper_2309_09778_gb300/csrc/pc_qmlp.cuh", "paper_2309_09778_gb300/csrc/pc_device.cuh",
+              "paper_2309_09778_gb300/csrc/pc_kernels.cuh"),
 }
 # kernels behind each profiled stage (the codebook stage launches k_codebook and k_cb_assign; the decoder's
 # scan stage k_dec_chunksum, k_dec_chunkscan and k_dec_blockoff)
@@ -740,6 +749,35 @@ def run_batch64(torch, pc, args, dev, stream, flush, peak):
             "setup_seconds": {"generate": gen_s, "autotune": tune_s, "train_and_quantize": train_s}}
 
 
+def select_report(torch, pc, w, dev):
+    """The training phase's two selection rules on the same field and samples (Section IV.C): the residual
+    bit-length proxy and the simulated compression (Huffman-coded validation codes plus stored balance
+    points), with the coverage rule's m; container sizes with each choice."""
+    spec, fields = w["spec"], w["spec"]["_fields"]
+    d = fields[0]
+    k, h1, h2, eb = spec["k"], spec["h1"], spec["h2"], spec["eb"]
+    thr32 = thr_for(tuple(d.shape), spec["samples"])
+    lrs, lams = pc.default_grid()
+    tp = pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_FP32, stencil=k, hidden=(h1, h2))
+    ws = torch.empty(pc.pc_train_workspace_size(tuple(d.shape), pc.PC_F32, tp, thr32, lrs.size), dtype=torch.uint8,
+                     device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    W, s_in, chosen, sizes, m_cov = pc.pc_train_select(d, tp, 0, thr32, lrs, lams, ws)
+    torch.cuda.synchronize()
+    sel_s = time.perf_counter() - t0
+    _, _, chosen_proxy, _ = pc.pc_train(d, tp, 0, thr32, lrs, lams, ws)
+    del ws
+    out = {"chosen_by_bitlen_proxy": int(chosen_proxy), "chosen_by_simulated_compression": int(chosen),
+           "simulated_bits": [int(v) for v in sizes], "m_by_coverage_rule": int(m_cov), "seconds": sel_s}
+    for label, m in (("m16", 16), ("m_coverage", m_cov)):
+        p = pc.make_params(eb, BLOCK, m=m) if chosen < 0 else pc.make_params(
+            eb, BLOCK, pred=pc.PC_PRED_MLP_FP32, stencil=k, hidden=(h1, h2), m=m, s_in=s_in, weights=W[chosen])
+        blob = pc.compress(d, p)
+        out[f"bits_per_value_{label}"] = 8.0 * blob.numel() / d.numel()
+    return out
+
+
 def summary(w):
     res = w["res"]
     keep = ("compress_gbs", "decompress_gbs", "bits_per_value", "bound_held", "compress_ms", "decompress_ms",
@@ -786,6 +824,37 @@ def run_reference(args, rank: int):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(form: str):
+    """A small case of the headline kernels for profiler captures (inputs larger than L2, a few GB at most)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2309_09778_gb300.pc as pc
+    from paper_2309_09778_gb300 import gen
+    dev = torch.device("cuda:0")
+    d = torch.exp(1.5 * gen.grf_device((256, 256, 512), 2.0, 0, dev)).to(torch.float32)
+    eb = 1e-4
+    thr32 = thr_for(tuple(d.shape), 1 << 18)
+    tp = pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_FP32, stencil=13, hidden=(32, 32))
+    lrs, lams = pc.default_grid()
+    tws = torch.empty(pc.pc_train_workspace_size(d.shape, pc.PC_F32, tp, thr32, lrs.size), dtype=torch.uint8,
+                      device=dev)
+    W, s_in, chosen, _ = pc.pc_train(d, tp, 0, thr32, lrs, lams, tws)
+    p = pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_FP32, stencil=13, hidden=(32, 32), s_in=s_in,
+                       weights=W[max(chosen, 0)])
+    if form == "bf16":
+        q = pc.pc_quantize(d, p, 0, thr32, tws)
+        p = pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_BF16, stencil=13, hidden=(32, 32), s_in=s_in, qnet=q)
+    del tws
+    blob = pc.compress(d, p)
+    y = pc.decompress(blob)
+    torch.cuda.synchronize()
+    ok = bool(((y.double() - d.double()).abs() <= eb * d.double().abs()).all().item())
+    print(f"profile case {form}: chosen {chosen}, {8.0 * blob.numel() / d.numel():.3f} bits/value, bound held {ok}")
+    if not ok:
+        raise SystemExit(1)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -798,7 +867,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--profile-case", default=None, choices=["bf16", "fp32"],
+                    help="run one compress and one decompress of a 256x256x512 density field (one quarter of a "
+                         "headline field, same recipe, 13-point 32/32 network trained on 2^18 samples) for "
+                         "profiler captures, then exit")
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -863,6 +939,7 @@ def main():
             secondary[name] = summary(w)
             if name == "grf100x500x500_f32" and not args.no_forms:
                 secondary[name]["forms"] = form_compare(torch, pc, w, args, stream, flush)
+                secondary[name]["selection_by_simulated_compression"] = select_report(torch, pc, w, dev)
             w["spec"].pop("_fields")
             del w
             torch.cuda.empty_cache()

@@ -269,6 +269,26 @@ int pc_train(const void* d_field, const size_t dims[3], int dtype, const pc_para
              float* h_weights_out, int* s_in_out, int* chosen_out, unsigned long long* h_costs,
              void* d_ws, size_t ws_bytes, void* stream);
 
+/*
+ * The training phase with the paper's model selection (Section IV.C): the
+ * models are trained as by pc_train, then every model and Lorenzo is scored
+ * by simulating compression on the validation samples -- residuals quantized
+ * with p->m code bits (code k + R, or a balance point), Huffman-coded with the
+ * code of their own histogram (as the compressor builds it), plus the stored
+ * value (32 or 64 bits) of every balance point -- and the smallest simulated
+ * size wins (Lorenzo unless strictly beaten).  Then m is chosen by the
+ * coverage rule: coverage(m) is the share of validation residuals with
+ * |k| <= 2^(m-1) - 1, and m in 2..16 is taken with coverage closest to 50%
+ * when eb_rel < 1.5%, to 80% otherwise (the larger m on a tie).
+ *   h_sizes [out] host, nmodels + 1 simulated sizes in bits (last = Lorenzo), may be NULL.
+ *   m_out   [out] the chosen code bits.
+ * Workspace: pc_train_workspace_size.  Other arguments and errors as pc_train.
+ */
+int pc_train_select(const void* d_field, const size_t dims[3], int dtype, const pc_params* p,
+                    unsigned long long seed, unsigned int thr32, int nmodels, const float* h_lrs,
+                    const float* h_lams, float* h_weights_out, int* s_in_out, int* chosen_out,
+                    unsigned long long* h_sizes, int* m_out, void* d_ws, size_t ws_bytes, void* stream);
+
 /* Diagnostics for tests: offsets (bytes) of the per-point codes (u16, block-strided,
  * nblocks * block volume), per-block perceptron flags (u8) and the code histogram
  * (u64, 2^m) inside a compression workspace after pc_compress returns. */

@@ -93,6 +93,17 @@ def lib():
             L.orc_mlp_fwd64.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]
             L.orc_mlp_pred64.restype = C.c_int32
             L.orc_mlp_pred64.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]
+            L.orc_val_size.restype = C.c_uint64
+            L.orc_val_size.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_uint64, C.c_int, C.c_int]
+            L.orc_coverage_m.restype = C.c_int
+            L.orc_coverage_m.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_uint64, C.c_double]
+            L.orc_train_select.restype = C.c_int
+            L.orc_train_select.argtypes = [C.c_void_p, u64p, C.c_int, C.c_double, C.POINTER(C.c_int), C.c_int,
+                                           C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint32, C.c_int, C.c_void_p,
+                                           C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.c_void_p,
+                                           C.POINTER(C.c_int)]
             L.orc_block_codes.restype = C.c_int
             L.orc_block_codes.argtypes = [C.c_void_p, u64p, C.c_int, C.POINTER(Consts), C.POINTER(Params), C.c_uint64,
                                           C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -511,6 +522,41 @@ def val_cost(w, k, h1, h2, s_in, inp, tg, use, m=16) -> int:
     use = np.ascontiguousarray(use, np.uint8)
     wp = None if w is None else _p(np.ascontiguousarray(w, np.float32))
     return lib().orc_val_cost(wp, k, h1, h2, s_in, _p(inp), _p(tg), _p(use), tg.size, m)
+
+
+def val_size(w, k, h1, h2, s_in, inp, tg, use, m=16, value_bits=32) -> int:
+    """Simulated compressed size (bits) of a predictor on validation samples (Section IV.C)."""
+    inp = np.ascontiguousarray(inp, np.int32); tg = np.ascontiguousarray(tg, np.int32)
+    use = np.ascontiguousarray(use, np.uint8)
+    wp = None if w is None else _p(np.ascontiguousarray(w, np.float32))
+    return lib().orc_val_size(wp, k, h1, h2, s_in, _p(inp), _p(tg), _p(use), tg.size, m, value_bits)
+
+
+def coverage_m(w, k, h1, h2, s_in, inp, tg, use, eb) -> int:
+    inp = np.ascontiguousarray(inp, np.int32); tg = np.ascontiguousarray(tg, np.int32)
+    use = np.ascontiguousarray(use, np.uint8)
+    wp = None if w is None else _p(np.ascontiguousarray(w, np.float32))
+    return lib().orc_coverage_m(wp, k, h1, h2, s_in, _p(inp), _p(tg), _p(use), tg.size, eb)
+
+
+def train_select(x: np.ndarray, eb: float, block=(8, 8, 8), k=7, h1=16, h2=16, m=16, seed=0, thr32=None,
+                 lrs=None, lams=None):
+    """Training phase with selection by simulated compression and the coverage rule for m.
+    Returns (chosen index or -1, weights [H, nw], s_in, simulated sizes [H + 1], m)."""
+    x = np.ascontiguousarray(x)
+    if thr32 is None:
+        thr32 = int(0.1 * 2 ** 32)
+    if lrs is None:
+        lrs, lams = default_grid()
+    lrs = np.ascontiguousarray(lrs, np.float32); lams = np.ascontiguousarray(lams, np.float32)
+    H = lrs.size
+    W = np.zeros((H, mlp_nweights(k, h1, h2)), np.float32)
+    sizes = np.zeros(H + 1, np.uint64)
+    s_in, m_out = C.c_int(), C.c_int()
+    b = (C.c_int * 3)(*block)
+    best = lib().orc_train_select(_p(x), _dims(x), _dtype_code(x), eb, b, k, h1, h2, m, seed, thr32, H, _p(lrs),
+                                  _p(lams), _p(W), C.byref(s_in), _p(sizes), C.byref(m_out))
+    return best, W, s_in.value, sizes, m_out.value
 
 
 DEFAULT_LRS = [3e-3, 1e-2, 3e-2, 1e-1]

@@ -1822,3 +1822,117 @@ int orc_block_codes(const void* x, const uint64_t dims[3], int dtype, const orc_
   free(dqb); free(okb); free(vc); free(vt); free(cz); free(cn);
   return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Section IV.C, model selection by simulated compression.  A predictor's     */
+/* validation residuals are quantized as the compressor would (code k + R, or */
+/* 0 for a balance point when |k| >= R), Huffman-coded with the code of their */
+/* own histogram (orc_huffman_lengths, lmax 24), and every balance point adds */
+/* its stored value (value_bits, 32 or 64).  Returns the simulated size in    */
+/* bits; w == NULL scores Lorenzo.                                            */
+/* ------------------------------------------------------------------------- */
+uint64_t orc_val_size(const float* w, int k, int h1, int h2, int s_in, const int32_t* in, const int32_t* tg,
+                      const uint8_t* use, uint64_t n, int m, int value_bits) {
+  int nsym = 1 << m;
+  int64_t R = (int64_t)1 << (m - 1);
+  uint64_t* hist = (uint64_t*)calloc((size_t)nsym, sizeof(uint64_t));
+  uint8_t* lens = (uint8_t*)malloc((size_t)nsym);
+  for (uint64_t i = 0; i < n; i++) {
+    if (!use[i]) continue;
+    int64_t pr;
+    if (w) {
+      pr = orc_mlp_pred32(w, k, h1, h2, s_in, in + i * (uint64_t)k);
+    } else {
+      pr = 0;
+      for (int j = 0; j < k; j++) pr += (int64_t)o_lz_weight(k, j) * in[i * (uint64_t)k + j];
+    }
+    int64_t d = (int64_t)tg[i] - pr;
+    int64_t a = d < 0 ? -d : d;
+    hist[a <= R - 1 ? d + R : 0]++;
+  }
+  orc_huffman_lengths(hist, nsym, O_LMAX, lens, NULL);
+  uint64_t bits = hist[0] * (uint64_t)value_bits;
+  for (int c = 0; c < nsym; c++) bits += hist[c] * (uint64_t)lens[c];
+  free(lens); free(hist);
+  return bits;
+}
+
+/* Section IV.C, the coverage rule for m: coverage(m) is the fraction of the  */
+/* used validation samples whose residual a code of m bits covers,            */
+/* |k| <= 2^(m-1) - 1.  Reading: among m = 2..16 take the coverage closest to */
+/* 50% when eb_rel < 1.5% and to 80% otherwise; a tie goes to the larger m.   */
+int orc_coverage_m(const float* w, int k, int h1, int h2, int s_in, const int32_t* in, const int32_t* tg,
+                   const uint8_t* use, uint64_t n, double eb) {
+  uint64_t cnt[66] = {0};
+  uint64_t used = 0;
+  for (uint64_t i = 0; i < n; i++) {
+    if (!use[i]) continue;
+    int64_t pr;
+    if (w) {
+      pr = orc_mlp_pred32(w, k, h1, h2, s_in, in + i * (uint64_t)k);
+    } else {
+      pr = 0;
+      for (int j = 0; j < k; j++) pr += (int64_t)o_lz_weight(k, j) * in[i * (uint64_t)k + j];
+    }
+    int64_t d = (int64_t)tg[i] - pr;
+    cnt[o_bitlen((uint64_t)(d < 0 ? -d : d))]++;
+    used++;
+  }
+  if (used == 0) return 16;
+  double target = eb < 0.015 ? 0.5 : 0.8;
+  int best = 16;
+  double bestd = 2.0;
+  for (int mm = 16; mm >= 2; mm--) {
+    uint64_t cov = 0;
+    for (int b = 0; b <= mm - 1; b++) cov += cnt[b];
+    double dd = fabs((double)cov / (double)used - target);
+    if (dd < bestd) { bestd = dd; best = mm; }
+  }
+  return best;
+}
+
+/* The training phase with the paper's selection (Section IV.C): train the   */
+/* nmodels settings as orc_train does, keep the predictor (a model or        */
+/* Lorenzo) with the smallest simulated size at the initial m (strictly      */
+/* smaller; Lorenzo wins ties, then the lower index), then choose m by the    */
+/* coverage rule for that predictor.  sizes[nmodels + 1] (last = Lorenzo).    */
+int orc_train_select(const void* x, const uint64_t dims[3], int dtype, double eb, const int block[3], int k, int h1,
+                     int h2, int m, uint64_t seed, uint32_t thr32, int nmodels, const float* lrs, const float* lams,
+                     float* w_out, int* s_in_out, uint64_t* sizes, int* m_out) {
+  uint64_t n = dims[0] * dims[1] * dims[2];
+  double amin, amax;
+  int trivial;
+  int st = orc_stats(x, n, dtype, &amin, &amax, &trivial);
+  if (st) return st;
+  orc_consts c;
+  st = orc_make_consts(dtype, amin, amax, trivial, eb, &c);
+  if (st) return st;
+  uint64_t nt, nv;
+  st = orc_count_samples(dims, block, seed, thr32, &nt, &nv);
+  if (st) return st;
+  int32_t* tin = (int32_t*)malloc(sizeof(int32_t) * (nt * k + 1));
+  int32_t* ttg = (int32_t*)malloc(sizeof(int32_t) * (nt + 1));
+  uint8_t* tus = (uint8_t*)malloc(nt + 1);
+  int32_t* vin = (int32_t*)malloc(sizeof(int32_t) * (nv * k + 1));
+  int32_t* vtg = (int32_t*)malloc(sizeof(int32_t) * (nv + 1));
+  uint8_t* vus = (uint8_t*)malloc(nv + 1);
+  orc_gather_samples(x, dims, dtype, &c, block, k, seed, thr32, tin, ttg, tus, vin, vtg, vus);
+  int s_in = orc_input_shift(ttg, tus, nt);
+  *s_in_out = s_in;
+  int nw = orc_mlp_nweights(k, h1, h2);
+  int vbits = dtype == ORC_F64 ? 64 : 32;
+  int best = -1;
+  uint64_t lz = orc_val_size(NULL, k, h1, h2, s_in, vin, vtg, vus, nv, m, vbits);
+  sizes[nmodels] = lz;
+  uint64_t bestc = lz;
+  for (int h = 0; h < nmodels; h++) {
+    float* w = w_out + (size_t)h * nw;
+    orc_init_weights(w, k, h1, h2, seed ^ 0x5DEECE66DULL);
+    orc_train_epoch(w, k, h1, h2, s_in, tin, ttg, tus, nt, lrs[h], lams[h], ~0ull);
+    sizes[h] = orc_val_size(w, k, h1, h2, s_in, vin, vtg, vus, nv, m, vbits);
+    if (sizes[h] < bestc) { bestc = sizes[h]; best = h; }
+  }
+  *m_out = orc_coverage_m(best >= 0 ? w_out + (size_t)best * nw : NULL, k, h1, h2, s_in, vin, vtg, vus, nv, eb);
+  free(tin); free(ttg); free(tus); free(vin); free(vtg); free(vus);
+  return best;
+}

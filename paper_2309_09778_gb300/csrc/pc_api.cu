@@ -259,7 +259,7 @@ int parse_header(const uint8_t* h, size_t n, Hdr& H, Geo& g) {
 
 struct TrainLayout {
   size_t st, tabs, hist, cnt_t, cnt_v, off_t, off_v, tin, ttg, tus, vin, vtg, vus, w, lrs, lams, costs, ctl, qnet, qmax,
-      total;
+      shists, sbits, sst, slist, skey, sw, sparent, sdepth, sla, slb, srstart, ssymord, total;
   unsigned long long cap_t, cap_v;
 };
 
@@ -299,8 +299,84 @@ TrainLayout train_layout(const Geo& g, int m, int k, int nw, unsigned int thr32,
   L.ctl = o; o = up(o + train_ctl_bytes());
   L.qnet = o; o = up(o + 8 * (size_t)qnet_len(13, 32, 32));
   L.qmax = o; o = up(o + 16);
+  // selection by simulated compression (pc_train_select)
+  size_t np = 1;
+  while (np < nsym) np <<= 1;
+  L.shists = o; o = up(o + 8 * nsym * (size_t)(nmodels + 1));
+  L.sbits = o; o = up(o + 8 * 34 * (size_t)(nmodels + 1));
+  L.sst = o; o = up(o + sizeof(State));
+  L.slist = o; o = up(o + 4 * nsym + 64);
+  L.skey = o; o = up(o + 8 * np);
+  L.sw = o; o = up(o + 8 * 2 * nsym);
+  L.sparent = o; o = up(o + 4 * 2 * nsym);
+  L.sdepth = o; o = up(o + 4 * 2 * nsym);
+  L.sla = o; o = up(o + 4 * nsym);
+  L.slb = o; o = up(o + 4 * nsym);
+  L.srstart = o; o = up(o + 4 * (nsym + 2));
+  L.ssymord = o; o = up(o + 4 * nsym);
   L.total = o;
   return L;
+}
+
+TrainBufs train_bufs(const TrainLayout& L, uint8_t* ws) {
+  TrainBufs tb;
+  tb.cnt_t = reinterpret_cast<unsigned int*>(ws + L.cnt_t);
+  tb.cnt_v = reinterpret_cast<unsigned int*>(ws + L.cnt_v);
+  tb.off_t = reinterpret_cast<unsigned long long*>(ws + L.off_t);
+  tb.off_v = reinterpret_cast<unsigned long long*>(ws + L.off_v);
+  tb.tin = reinterpret_cast<int*>(ws + L.tin);
+  tb.ttg = reinterpret_cast<int*>(ws + L.ttg);
+  tb.tus = ws + L.tus;
+  tb.vin = reinterpret_cast<int*>(ws + L.vin);
+  tb.vtg = reinterpret_cast<int*>(ws + L.vtg);
+  tb.vus = ws + L.vus;
+  tb.w = reinterpret_cast<float*>(ws + L.w);
+  tb.lrs = reinterpret_cast<const float*>(ws + L.lrs);
+  tb.lams = reinterpret_cast<const float*>(ws + L.lams);
+  tb.costs = reinterpret_cast<unsigned long long*>(ws + L.costs);
+  tb.ctl = ws + L.ctl;
+  tb.cap_t = L.cap_t;
+  tb.cap_v = L.cap_v;
+  return tb;
+}
+
+SelectBufs select_bufs(const TrainLayout& L, uint8_t* ws) {
+  SelectBufs sb;
+  sb.hists = reinterpret_cast<unsigned long long*>(ws + L.shists);
+  sb.bitcnt = reinterpret_cast<unsigned long long*>(ws + L.sbits);
+  sb.st = reinterpret_cast<State*>(ws + L.sst);
+  sb.list = ws + L.slist;
+  sb.hs.key = reinterpret_cast<unsigned long long*>(ws + L.skey);
+  sb.hs.w = reinterpret_cast<unsigned long long*>(ws + L.sw);
+  sb.hs.parent = reinterpret_cast<int*>(ws + L.sparent);
+  sb.hs.depth = reinterpret_cast<int*>(ws + L.sdepth);
+  sb.hs.la = reinterpret_cast<int*>(ws + L.sla);
+  sb.hs.lb = reinterpret_cast<int*>(ws + L.slb);
+  sb.hs.rstart = reinterpret_cast<int*>(ws + L.srstart);
+  sb.hs.symord = reinterpret_cast<unsigned int*>(ws + L.ssymord);
+  return sb;
+}
+
+// The coverage rule (Section IV.C) on residual bit-length counts cnt[0..33]:
+// coverage(m) = share with bitlen <= m - 1; closest to 50% (eb < 1.5%) or 80%,
+// the larger m on a tie.
+int coverage_m(const unsigned long long* cnt, double eb) {
+  unsigned long long used = 0;
+  for (int b = 0; b < 34; ++b) used += cnt[b];
+  if (used == 0) return 16;
+  const double target = eb < 0.015 ? 0.5 : 0.8;
+  int best = 16;
+  double bestd = 2.0;
+  for (int mm = 16; mm >= 2; --mm) {
+    unsigned long long cov = 0;
+    for (int b = 0; b <= mm - 1; ++b) cov += cnt[b];
+    const double dd = fabs((double)cov / (double)used - target);
+    if (dd < bestd) {
+      bestd = dd;
+      best = mm;
+    }
+  }
+  return best;
 }
 
 int train_check(const size_t dims[3], int dtype, const pc_params* p, int nmodels, Geo& g, int& nw) {
@@ -563,10 +639,16 @@ int pc_train_workspace_size(const size_t dims[3], int dtype, const pc_params* p,
   return PC_OK;
 }
 
-int pc_train(const void* d_field, const size_t dims[3], int dtype, const pc_params* p, unsigned long long seed,
-             unsigned int thr32, int nmodels, const float* h_lrs, const float* h_lams, float* h_weights_out,
-             int* s_in_out, int* chosen_out, unsigned long long* h_costs, void* d_ws, size_t ws_bytes,
-             void* stream) {
+}  // extern "C"
+
+namespace {
+
+// The training phase; with select, the models are scored by simulated
+// compression and m comes from the coverage rule (pc_train_select).
+int train_run(const void* d_field, const size_t dims[3], int dtype, const pc_params* p, unsigned long long seed,
+              unsigned int thr32, int nmodels, const float* h_lrs, const float* h_lams, float* h_weights_out,
+              int* s_in_out, int* chosen_out, unsigned long long* h_costs, bool select, int* m_out, void* d_ws,
+              size_t ws_bytes, void* stream) {
   Geo g;
   int nw;
   int st = train_check(dims, dtype, p, nmodels, g, nw);
@@ -581,24 +663,7 @@ int pc_train(const void* d_field, const size_t dims[3], int dtype, const pc_para
   State* stp = reinterpret_cast<State*>(ws + L.st);
   Tabs* tabs = reinterpret_cast<Tabs*>(ws + L.tabs);
   auto* hist = reinterpret_cast<unsigned long long*>(ws + L.hist);
-  TrainBufs tb;
-  tb.cnt_t = reinterpret_cast<unsigned int*>(ws + L.cnt_t);
-  tb.cnt_v = reinterpret_cast<unsigned int*>(ws + L.cnt_v);
-  tb.off_t = reinterpret_cast<unsigned long long*>(ws + L.off_t);
-  tb.off_v = reinterpret_cast<unsigned long long*>(ws + L.off_v);
-  tb.tin = reinterpret_cast<int*>(ws + L.tin);
-  tb.ttg = reinterpret_cast<int*>(ws + L.ttg);
-  tb.tus = ws + L.tus;
-  tb.vin = reinterpret_cast<int*>(ws + L.vin);
-  tb.vtg = reinterpret_cast<int*>(ws + L.vtg);
-  tb.vus = ws + L.vus;
-  tb.w = reinterpret_cast<float*>(ws + L.w);
-  tb.lrs = reinterpret_cast<const float*>(ws + L.lrs);
-  tb.lams = reinterpret_cast<const float*>(ws + L.lams);
-  tb.costs = reinterpret_cast<unsigned long long*>(ws + L.costs);
-  tb.ctl = ws + L.ctl;
-  tb.cap_t = L.cap_t;
-  tb.cap_v = L.cap_v;
+  TrainBufs tb = train_bufs(L, ws);
   if (cudaMemcpyAsync(ws + L.lrs, h_lrs, 4ull * nmodels, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(ws + L.lams, h_lams, 4ull * nmodels, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return PC_ERR_CUDA;
@@ -614,6 +679,9 @@ int pc_train(const void* d_field, const size_t dims[3], int dtype, const pc_para
     if (!r) r = launch_train<double>(static_cast<const double*>(d_field), g, stp, tabs, tb, p->stencil, p->hidden[0],
                                     p->hidden[1], p->m, nmodels, seed, thr32, s);
   }
+  SelectBufs sb = select_bufs(L, ws);
+  if (!r && select)
+    r = launch_select(tb, sb, p->stencil, p->hidden[0], p->hidden[1], p->m, nmodels, dtype == PC_F64 ? 64 : 32, s);
   if (r) return r;
   unsigned long long ctl[8];
   int herr = 0;
@@ -623,6 +691,9 @@ int pc_train(const void* d_field, const size_t dims[3], int dtype, const pc_para
     return PC_ERR_CUDA;
   unsigned long long costs[65];
   if (cudaMemcpyAsync(costs, tb.costs, 8ull * (nmodels + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return PC_ERR_CUDA;
+  static thread_local unsigned long long bitcnt[65 * 34];
+  if (select && cudaMemcpyAsync(bitcnt, sb.bitcnt, 8ull * 34 * (nmodels + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return PC_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
   prof_collect();
@@ -634,9 +705,33 @@ int pc_train(const void* d_field, const size_t dims[3], int dtype, const pc_para
   *s_in_out = tail[0];
   *chosen_out = tail[1];
   if (h_costs) memcpy(h_costs, costs, 8ull * (nmodels + 1));
+  if (select && m_out) {
+    const int c = tail[1] >= 0 ? tail[1] : nmodels;
+    *m_out = coverage_m(bitcnt + 34 * c, p->eb_rel);
+  }
   return PC_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int pc_train(const void* d_field, const size_t dims[3], int dtype, const pc_params* p, unsigned long long seed,
+             unsigned int thr32, int nmodels, const float* h_lrs, const float* h_lams, float* h_weights_out,
+             int* s_in_out, int* chosen_out, unsigned long long* h_costs, void* d_ws, size_t ws_bytes,
+             void* stream) {
+  return train_run(d_field, dims, dtype, p, seed, thr32, nmodels, h_lrs, h_lams, h_weights_out, s_in_out, chosen_out,
+                   h_costs, false, nullptr, d_ws, ws_bytes, stream);
+}
+
+int pc_train_select(const void* d_field, const size_t dims[3], int dtype, const pc_params* p,
+                    unsigned long long seed, unsigned int thr32, int nmodels, const float* h_lrs,
+                    const float* h_lams, float* h_weights_out, int* s_in_out, int* chosen_out,
+                    unsigned long long* h_sizes, int* m_out, void* d_ws, size_t ws_bytes, void* stream) {
+  if (!m_out) return PC_ERR_ARG;
+  return train_run(d_field, dims, dtype, p, seed, thr32, nmodels, h_lrs, h_lams, h_weights_out, s_in_out, chosen_out,
+                   h_sizes, true, m_out, d_ws, ws_bytes, stream);
+}
 
 int pc_quantize(const void* d_field, const size_t dims[3], int dtype, const pc_params* p, unsigned long long seed,
                 unsigned int thr32, long long* h_qnet_out, void* d_ws, size_t ws_bytes, void* stream) {

@@ -487,8 +487,10 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const unsigned long lon
   if (n <= 1) {
     if (n == 1 && tid == 0) {
       const unsigned int s = vc[0];
-      lens[s] = 1;
-      cw[s] = 1u << 24;
+      if (lens) {  // absent when only the list is wanted
+        lens[s] = 1;
+        cw[s] = 1u << 24;
+      }
       st_u32(out + off_cb, s | (1u << 16));
     }
     for (unsigned long long i = off_cb + 4ull * n + tid; i < off_bb; i += nt) out[i] = 0;
@@ -616,6 +618,16 @@ int launch_codebook(const unsigned long long* hist, int m, uint8_t* lens, uint32
   k_codebook<<<1, kCbThreads, smem, s>>>(hist, m, lens, cw, st, hs, out, (unsigned long long)g.nblocks, hi.off_cb,
                                          hi.cap);
   k_cb_assign<<<((1u << m) + 255u) / 256u, 256, 0, s>>>(out, lens, cw, st);
+  return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
+}
+
+int launch_huff_list(const unsigned long long* hist, int m, State* st, const HuffScratch& hs, uint8_t* list,
+                     unsigned long long cap, cudaStream_t s) {
+  const size_t smem = kCbSmem;
+  if (cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return PC_ERR_CUDA;
+  // no lengths or code tables, no block table: the list at offset 0
+  k_codebook<<<1, kCbThreads, smem, s>>>(hist, m, nullptr, nullptr, st, hs, list, 0ull, 0ull, cap);
   return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
 

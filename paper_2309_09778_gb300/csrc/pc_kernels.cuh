@@ -185,6 +185,24 @@ struct TrainBufs {
   unsigned long long cap_t, cap_v;
 };
 size_t train_ctl_bytes();
+// Buffers of the selection by simulated compression: per-model code
+// histograms (u64 [nmodels + 1][2^m]) and residual bit-length counts
+// (u64 [nmodels + 1][34]), a scratch state, codebook list and Huffman scratch.
+struct SelectBufs {
+  unsigned long long* hists;
+  unsigned long long* bitcnt;
+  State* st;
+  uint8_t* list;
+  HuffScratch hs;
+};
+// Score the trained models and Lorenzo by simulated compression into
+// tb.costs and choose (Lorenzo unless strictly beaten).
+int launch_select(const TrainBufs& tb, const SelectBufs& sb, int k, int h1, int h2, int m, int nmodels,
+                  int value_bits, cudaStream_t s);
+// Huffman code lengths of one histogram as a codebook list (sym | len << 16,
+// most frequent first) at list[0..], n_used in st (a zeroed scratch state).
+int launch_huff_list(const unsigned long long* hist, int m, State* st, const HuffScratch& hs, uint8_t* list,
+                     unsigned long long cap, cudaStream_t s);
 template <typename T>
 int launch_train(const T* x, const Geo& g, const State* st, const Tabs* tabs, const TrainBufs& tb, int k, int h1,
                  int h2, int m, int nmodels, unsigned long long seed, unsigned int thr32, cudaStream_t s);

@@ -413,6 +413,116 @@ static int launch_train_models(const TrainBufs& tb, int nmodels, int m, cudaStre
   return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
 
+// ---------------------------------------------------------------------------
+// Selection by simulated compression (Section IV.C).  k_valhist quantizes
+// every model's (blockIdx.y; nmodels = Lorenzo) validation residuals as the
+// compressor would (code k + R, or 0 for a balance point) into its histogram
+// and counts residual bit lengths for the coverage rule; the codebook kernel
+// then builds each histogram's Huffman lengths, and k_simsize adds up the
+// coded bits plus the stored value of every balance point.
+// ---------------------------------------------------------------------------
+template <int K, int H1, int H2>
+__global__ void __launch_bounds__(256) k_valhist(const int* __restrict__ vin, const int* __restrict__ vtg,
+                                                 const uint8_t* __restrict__ vus, const float* __restrict__ wbuf,
+                                                 int nmodels, int m, const TrainCtl* __restrict__ ctl,
+                                                 unsigned long long* hists, unsigned long long* bitcnt) {
+  constexpr int NW = H1 * K + H1 + (H2 > 0 ? H2 * H1 + H2 : 0) + (H2 > 0 ? H2 : H1) + 1;
+  __shared__ Mlp s_m;
+  __shared__ unsigned int s_bc[34];
+  const int model = blockIdx.y;
+  const bool lz = model == nmodels;
+  if (!lz)
+    for (int p = threadIdx.x; p < NW; p += blockDim.x) s_m.w[p] = wbuf[(size_t)model * NW + p];
+  if (threadIdx.x == 0) { s_m.k = K; s_m.h1 = H1; s_m.h2 = H2; s_m.s_in = ctl->s_in; }
+  if (threadIdx.x < 34) s_bc[threadIdx.x] = 0u;
+  __syncthreads();
+  const int s_in = ctl->s_in;
+  const float sig = __uint_as_float((unsigned int)(127 - s_in) << 23);
+  const float unsig = __uint_as_float((unsigned int)(127 + s_in) << 23);
+  const long long R = 1ll << (m - 1);
+  const unsigned long long n = ctl->nval;
+  unsigned long long* hist = hists + ((size_t)model << m);
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    if (!vus[i]) continue;
+    int in[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) in[q] = vin[i * K + q];
+    long long pr = 0;
+    if (lz) {
+#pragma unroll
+      for (int q = 0; q < K; ++q) pr += (long long)lz_w(K, q) * in[q];
+    } else {
+      pr = round_pred(mlp_fwd<K, H1, H2>(s_m, in, sig, unsig));
+    }
+    const long long d = (long long)vtg[i] - pr;
+    const unsigned long long a = (unsigned long long)(d < 0 ? -d : d);
+    atomicAdd(&hist[a <= (unsigned long long)(R - 1) ? (unsigned int)(d + R) : 0u], 1ull);
+    atomicAdd(&s_bc[64 - __clzll((long long)a)], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < 34 && s_bc[threadIdx.x])
+    atomicAdd(&bitcnt[(size_t)model * 34 + threadIdx.x], (unsigned long long)s_bc[threadIdx.x]);
+}
+
+// Coded bits of one histogram from its codebook list (sym | len << 16, n_used
+// entries), plus value_bits per balance point (symbol 0).
+__global__ void __launch_bounds__(256) k_simsize(const unsigned long long* __restrict__ hist,
+                                                 const uint8_t* __restrict__ list, const State* __restrict__ st,
+                                                 int value_bits, unsigned long long* size_out) {
+  __shared__ unsigned long long s_part[8];
+  const unsigned int n = st->err ? 0u : st->n_used;
+  unsigned long long acc = 0;
+  for (unsigned int i = threadIdx.x; i < n; i += blockDim.x) {
+    const unsigned int e = reinterpret_cast<const unsigned int*>(list)[i];
+    acc += hist[e & 0xFFFFu] * (unsigned long long)(e >> 16);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+  if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = hist[0] * (unsigned long long)value_bits;
+    for (int w = 0; w < 8; ++w) t += s_part[w];
+    *size_out = t;
+  }
+}
+
+template <int K, int H1, int H2>
+static int launch_select_models(const TrainBufs& tb, const SelectBufs& sb, int nmodels, int m, int value_bits,
+                                cudaStream_t s) {
+  const size_t nsym = (size_t)1 << m;
+  if (cudaMemsetAsync(sb.hists, 0, 8 * nsym * (nmodels + 1), s) != cudaSuccess ||
+      cudaMemsetAsync(sb.bitcnt, 0, 8 * 34 * (size_t)(nmodels + 1), s) != cudaSuccess)
+    return PC_ERR_CUDA;
+  dim3 gv(152, nmodels + 1);
+  k_valhist<K, H1, H2><<<gv, 256, 0, s>>>(tb.vin, tb.vtg, tb.vus, tb.w, nmodels, m,
+                                          reinterpret_cast<const TrainCtl*>(tb.ctl), sb.hists, sb.bitcnt);
+  if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
+  for (int h = 0; h <= nmodels; ++h) {
+    if (cudaMemsetAsync(sb.st, 0, sizeof(State), s) != cudaSuccess) return PC_ERR_CUDA;
+    int r = launch_huff_list(sb.hists + (h << m), m, sb.st, sb.hs, sb.list, 4 * nsym + 64, s);
+    if (r) return r;
+    k_simsize<<<1, 256, 0, s>>>(sb.hists + (h << m), sb.list, sb.st, value_bits, tb.costs + h);
+  }
+  k_choose<<<1, 1, 0, s>>>(tb.costs, nmodels, reinterpret_cast<TrainCtl*>(tb.ctl));
+  return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
+}
+
+int launch_select(const TrainBufs& tb, const SelectBufs& sb, int k, int h1, int h2, int m, int nmodels,
+                  int value_bits, cudaStream_t s) {
+  if (cudaMemsetAsync(tb.costs, 0, sizeof(unsigned long long) * (nmodels + 1), s) != cudaSuccess) return PC_ERR_CUDA;
+#define PC_SEL(KK, A, B) \
+  if (k == KK && h1 == A && h2 == B) return launch_select_models<KK, A, B>(tb, sb, nmodels, m, value_bits, s);
+  PC_SEL(7, 16, 16)
+  PC_SEL(13, 32, 32)
+  PC_SEL(7, 8, 8)
+  PC_SEL(7, 2, 0)
+  PC_SEL(13, 16, 16)
+#undef PC_SEL
+  return PC_ERR_ARG;
+}
+
 size_t train_ctl_bytes() { return sizeof(TrainCtl); }
 
 template <typename T>

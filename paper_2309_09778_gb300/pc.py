@@ -26,7 +26,7 @@ SYMBOLS = ["pc_mlp_nweights", "pc_compress_bound", "pc_compress_workspace_size",
            "pc_header_info", "pc_decompress", "pc_decompress_noalloc", "pc_compress_host", "pc_decompress_host",
            "pc_train_workspace_size", "pc_train", "pc_compress_workspace_layout", "pc_profile_enable",
            "pc_profile_read", "pc_profile_stage_name", "pc_strerror", "pc_compress_batch_workspace_size",
-           "pc_compress_batch", "pc_decompress_batch_workspace_size", "pc_decompress_batch"]
+           "pc_compress_batch", "pc_decompress_batch_workspace_size", "pc_decompress_batch", "pc_train_select"]
 
 
 # (lr, lambda) grid trained side by side in the training phase (Section IV.C
@@ -93,6 +93,11 @@ def lib():
                 L.pc_train.restype = C.c_int
                 L.pc_train.argtypes = [vp, szp, C.c_int, P, C.c_ulonglong, C.c_uint, C.c_int, vp, vp, vp,
                                        C.POINTER(C.c_int), C.POINTER(C.c_int), vp, vp, sz, vp]
+            if hasattr(L, "pc_train_select"):
+                L.pc_train_select.restype = C.c_int
+                L.pc_train_select.argtypes = [vp, szp, C.c_int, P, C.c_ulonglong, C.c_uint, C.c_int, vp, vp, vp,
+                                              C.POINTER(C.c_int), C.POINTER(C.c_int), vp, C.POINTER(C.c_int), vp, sz,
+                                              vp]
             if hasattr(L, "pc_quantize"):
                 L.pc_qnet_len.restype = C.c_int
                 L.pc_qnet_len.argtypes = [C.c_int, C.c_int, C.c_int]
@@ -293,6 +298,25 @@ def pc_train(field, params: pc_params, seed: int, thr32: int, lrs, lams, ws, str
                         _stream_ptr(stream))
     _check(st, "pc_train")
     return W, s_in.value, chosen.value, costs
+
+
+def pc_train_select(field, params: pc_params, seed: int, thr32: int, lrs, lams, ws, stream=None):
+    """Training with selection by simulated compression and the coverage rule for m.
+    Returns (weights [nmodels, nw], s_in, chosen or -1, simulated sizes [nmodels + 1], m)."""
+    lrs = np.ascontiguousarray(lrs, np.float32)
+    lams = np.ascontiguousarray(lams, np.float32)
+    H = lrs.size
+    nw = pc_mlp_nweights(params.stencil, params.hidden[0], params.hidden[1])
+    W = np.zeros((H, nw), np.float32)
+    sizes = np.zeros(H + 1, np.uint64)
+    s_in, chosen, m = C.c_int(), C.c_int(), C.c_int()
+    st = lib().pc_train_select(C.c_void_p(field.data_ptr()), _dims3(field.shape), _dtype_of(field), C.byref(params),
+                               int(seed), int(thr32), H, lrs.ctypes.data_as(C.c_void_p),
+                               lams.ctypes.data_as(C.c_void_p), W.ctypes.data_as(C.c_void_p), C.byref(s_in),
+                               C.byref(chosen), sizes.ctypes.data_as(C.c_void_p), C.byref(m),
+                               C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream))
+    _check(st, "pc_train_select")
+    return W, s_in.value, chosen.value, sizes, m.value
 
 
 def pc_qnet_len(k: int, h1: int, h2: int) -> int:

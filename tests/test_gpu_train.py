@@ -95,3 +95,25 @@ def test_params_ndims_checked(pc):
     p = pc.make_params(1e-2, (1, 16, 32), ndims=2)
     assert pc.pc_compress_bound((1, 40, 50), pc.PC_F32, p) > 0
     assert pc.pc_compress_bound((3, 40, 50), pc.PC_F32, p) == 0
+
+
+@pytest.mark.parametrize("shape,k,h,eb,dt", [((24, 32, 40), 7, (8, 8), 1e-2, np.float32),
+                                             ((20, 24, 40), 13, (16, 16), 1e-3, np.float32),
+                                             ((16, 24, 24), 7, (16, 16), 1e-4, np.float64)])
+def test_selection_by_simulated_compression_matches_oracle(pc, O, shape, k, h, eb, dt):
+    """Section IV.C selection: simulated sizes of every model and Lorenzo, the
+    choice and the coverage-chosen m equal the oracle's."""
+    x = gen.positive_lognormal(shape, 3.0, 3, 1.5).astype(dt)
+    lrs = np.array([3e-2, 1e-1, 1e-2, 0.0], np.float32)
+    lams = np.array([0.0, 1e-4, 1e-3, 0.0], np.float32)
+    thr = int(0.5 * 2 ** 32)
+    p = pc.make_params(eb, (8, 8, 8), pred=pc.PC_PRED_MLP_FP32, stencil=k, hidden=h)
+    ws = torch.empty(pc.pc_train_workspace_size(shape, pc.PC_F32 if dt == np.float32 else pc.PC_F64, p, thr, 4),
+                     dtype=torch.uint8, device="cuda")
+    W, s_in, chosen, sizes, m = pc.pc_train_select(torch.from_numpy(x).cuda(), p, 5, thr, lrs, lams, ws)
+    best, Wo, s_o, sizes_o, m_o = O.train_select(x, eb, k=k, h1=h[0], h2=h[1], seed=5, thr32=thr, lrs=lrs, lams=lams)
+    assert s_in == s_o
+    assert np.array_equal(W.view(np.uint32), Wo.view(np.uint32))
+    assert np.array_equal(sizes, sizes_o), (sizes, sizes_o)
+    assert chosen == best and m == m_o
+    assert sizes[3] == sizes[4]  # the learning-rate-0 model is Lorenzo
