@@ -246,6 +246,7 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const __grid_con
   __shared__ int s_cost[G][2];
   __shared__ int s_nz[G];
   __shared__ int s_da[G];
+  __shared__ int s_e2b[G];  // extent along x of each block of the brick (0: beyond the field)
 
   const int tid = threadIdx.x;
   for (int i = tid; i < G * PD::PV; i += 256) s_vp[i] = 0;
@@ -290,10 +291,10 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const __grid_con
   bool jskip = true;
   // per-field scalars of the brick loop, also in shared memory
   __shared__ long long s_nbx, s_jb0;
-  __shared__ int s_m, s_hbase, s_vec;
+  __shared__ int s_m, s_vec;
   const long long& nbx = s_nbx;
   const int& m = s_m;
-  const int& hbase = s_hbase;
+  int hbase = 0;
   auto flush_hist = [&]() {
     __syncthreads();
     for (int i = tid; i < kHistWin; i += 256) {
@@ -316,9 +317,9 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const __grid_con
       if (tid == 0) s_job = J;
       errw = const_cast<int*>(&J.st->err);
       R = 1 << (J.m - 1);
+      hbase = R - kHistWin / 2 > 0 ? R - kHistWin / 2 : 0;
       if (tid == 0) {
         s_m = J.m;
-        s_hbase = R - kHistWin / 2 > 0 ? R - kHistWin / 2 : 0;
         s_nbx = (J.g.nb[2] + G - 1) / G;
         s_jb0 = J.brick0;
         s_vec = VEC_OK && (J.g.n[2] % VW == 0) && ((reinterpret_cast<uintptr_t>(J.x) & 15u) == 0);
@@ -388,11 +389,13 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const __grid_con
     }
     if (tid < G) {
       int qa = 0;
-      if (bxg * G + tid < g.nb[2]) {
+      const long long bxt = bxg * G + tid;
+      if (bxt < g.nb[2]) {
         bool okk;
         qa = Num<T>::transform(__ldg(&base[tid * B2]), c, tb, okk);
       }
       s_da[tid] = qa;
+      s_e2b[tid] = bxt < g.nb[2] ? (int)min((long long)B2, g.n[2] - bxt * B2) : 0;
       s_cost[tid][0] = 0; s_cost[tid][1] = 0; s_nz[tid] = 0;
     }
     __syncthreads();
@@ -442,9 +445,7 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const __grid_con
         for (int q = 0; q < QK; ++q) xin[q] = s_vp[pj + PD::off(st_dz(QK, q), st_dy(QK, q), st_dx(QK, q))];
         int prd;
         tc_ok &= tcnet_tile<QK, QH>(tcs, abuf, tm, wg, r, tc_phase, xin, tcs.mul512, prd);
-        const long long bxp = bxg * G + gb;
-        const int e2p = bxp < g.nb[2] ? (int)min((long long)B2, g.n[2] - bxp * B2) : 0;
-        const bool valid = j != 0 && lz < e0 && ly < e1 && lx < e2p;
+        const bool valid = j != 0 && lz < e0 && ly < e1 && lx < s_e2b[gb];
         uint16_t coden = 0;
         int costn = 0;
         if (valid) {
