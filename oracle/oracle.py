@@ -51,7 +51,7 @@ class Consts(C.Structure):
 class Params(C.Structure):
     _fields_ = [("eb", C.c_double), ("block", C.c_int * 3), ("pred", C.c_int), ("stencil", C.c_int),
                 ("h1", C.c_int), ("h2", C.c_int), ("m", C.c_int), ("s_in", C.c_int),
-                ("weights", C.c_void_p), ("qnet", C.c_void_p)]
+                ("weights", C.c_void_p), ("qnet", C.c_void_p), ("codebook", C.c_void_p), ("codebook_n", C.c_int)]
 
 
 class Dump(C.Structure):
@@ -96,6 +96,15 @@ def lib():
             L.orc_val_size.restype = C.c_uint64
             L.orc_val_size.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_uint64, C.c_int, C.c_int]
+            L.orc_val_hist.restype = None
+            L.orc_val_hist.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_uint64, C.c_int, C.c_void_p]
+            L.orc_sample_codebook.restype = C.c_int
+            L.orc_sample_codebook.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
+            L.orc_sample_codebook_for.restype = C.c_int
+            L.orc_sample_codebook_for.argtypes = [C.c_void_p, u64p, C.c_int, C.c_double, C.POINTER(C.c_int),
+                                                  C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                                  C.c_uint64, C.c_uint32, C.c_void_p]
             L.orc_coverage_m.restype = C.c_int
             L.orc_coverage_m.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_uint64, C.c_double]
@@ -353,8 +362,10 @@ def canonical_codes(lens: np.ndarray, order=None) -> np.ndarray:
     return out
 
 
-def _params(eb, block, pred, stencil, h1, h2, m, s_in, w, q=None):
+def _params(eb, block, pred, stencil, h1, h2, m, s_in, w, q=None, cb=None):
     p = Params()
+    p.codebook = None if cb is None else cb.ctypes.data
+    p.codebook_n = 0 if cb is None else cb.size
     p.eb = eb
     p.block[:] = list(block)
     p.pred = pred
@@ -372,10 +383,12 @@ def compress_bound(shape3, dtype: int, block, m: int = 16, nweights: int = 0) ->
 
 
 def compress(x: np.ndarray, eb: float, block=(8, 8, 8), weights=None, stencil=7, h1=16, h2=16,
-             m: int = 16, s_in: int = 0, dump: bool = False, qnet=None, fp64: bool = False):
+             m: int = 16, s_in: int = 0, dump: bool = False, qnet=None, fp64: bool = False, codebook=None):
     """Compress with the oracle.  Returns (status, bytes[, dump dict]).  `qnet` selects the
     fixed-point (BF16) perceptron form instead of the FP32 weights; fp64=True evaluates the
-    FP32 weights in FP64 (the reporting predictor, which only the oracle encodes with)."""
+    FP32 weights in FP64 (the reporting predictor, which only the oracle encodes with).
+    `codebook` (uint32 list, sym | len << 16) compresses with that sample codebook: codes
+    outside it become balance points and the stream precedes the balance values."""
     x = np.ascontiguousarray(x)
     dims = _dims(x)
     dt = _dtype_code(x)
@@ -390,7 +403,8 @@ def compress(x: np.ndarray, eb: float, block=(8, 8, 8), weights=None, stencil=7,
     pred = PRED_MLP_BF16 if q is not None else (PRED_MLP if w is not None else PRED_LORENZO)
     if fp64 and w is not None and q is None:
         pred = PRED_MLP64
-    p = _params(eb, block, pred, stencil, h1, h2, m, s_in, w, q)
+    cb = None if codebook is None else np.ascontiguousarray(codebook, np.uint32)
+    p = _params(eb, block, pred, stencil, h1, h2, m, s_in, w, q, cb)
     cap = compress_bound(tuple(dims), dt, block, m, nw)
     out = np.zeros(cap, np.uint8)
     size = C.c_uint64()
@@ -530,6 +544,42 @@ def val_size(w, k, h1, h2, s_in, inp, tg, use, m=16, value_bits=32) -> int:
     use = np.ascontiguousarray(use, np.uint8)
     wp = None if w is None else _p(np.ascontiguousarray(w, np.float32))
     return lib().orc_val_size(wp, k, h1, h2, s_in, _p(inp), _p(tg), _p(use), tg.size, m, value_bits)
+
+
+def val_hist(w, k, h1, h2, s_in, inp, tg, use, m=16) -> np.ndarray:
+    """Validation histogram of one predictor (w None: Lorenzo) at m code bits."""
+    inp = np.ascontiguousarray(inp, np.int32); tg = np.ascontiguousarray(tg, np.int32)
+    use = np.ascontiguousarray(use, np.uint8)
+    wp = None if w is None else _p(np.ascontiguousarray(w, np.float32))
+    h = np.zeros(1 << m, np.uint64)
+    lib().orc_val_hist(wp, k, h1, h2, s_in, _p(inp), _p(tg), _p(use), tg.size, m, _p(h))
+    return h
+
+
+def sample_codebook(hist, m=16) -> np.ndarray:
+    """The training phase's Huffman code from a validation histogram: uint32 list
+    (sym | len << 16) in container order."""
+    h = np.ascontiguousarray(hist, np.uint64)
+    assert h.size == 1 << m
+    out = np.zeros(1 << m, np.uint32)
+    n = lib().orc_sample_codebook(_p(h), m, _p(out))
+    return out[:n].copy()
+
+
+def sample_codebook_for(x: np.ndarray, eb: float, block=(8, 8, 8), k=7, h1=16, h2=16, s_in=0, weights=None, m=16,
+                        seed=0, thr32=None) -> np.ndarray:
+    """Sample codebook of field x for the FP32 weights (None: Lorenzo), validation samples drawn
+    as the training phase draws them."""
+    x = np.ascontiguousarray(x)
+    if thr32 is None:
+        thr32 = int(0.1 * 2 ** 32)
+    w = None if weights is None else np.ascontiguousarray(weights, np.float32)
+    out = np.zeros(1 << m, np.uint32)
+    b = (C.c_int * 3)(*block)
+    n = lib().orc_sample_codebook_for(_p(x), _dims(x), _dtype_code(x), eb, b, k, h1, h2, s_in,
+                                      None if w is None else _p(w), m, seed, thr32, _p(out))
+    assert n > 0, n
+    return out[:n].copy()
 
 
 def coverage_m(w, k, h1, h2, s_in, inp, tg, use, eb) -> int:

@@ -884,8 +884,43 @@ static int o_block(const int32_t* dqb, const uint8_t* okb, int e0, int e1, int e
   return use_nn && costn < costz;
 }
 
+/* A given codebook (sym | len << 16 per entry, in the order the container
+ * stores it): symbols below 2^m and distinct, lengths 1..24 and never
+ * decreasing along the list (the canonical construction needs that order),
+ * Kraft sum at most one, and symbol 0 present, because balance points are
+ * coded as symbol 0.  Fills lens (zero for symbols not in the list) and the
+ * symbol order.  A single entry gets length 1, as the Huffman construction
+ * gives a single used symbol. */
+static int o_codebook_check(const uint32_t* cb, int n, int m, uint8_t* lens, uint32_t* order) {
+  int nsym = 1 << m;
+  if (n < 1 || n > nsym) return ORC_ERR_ARG;
+  memset(lens, 0, (size_t)nsym);
+  double kraft = 0.0;
+  int prev = 1, have0 = 0;
+  for (int t = 0; t < n; t++) {
+    uint32_t sym = cb[t] & 0xFFFFu, l = cb[t] >> 16;
+    if (sym >= (uint32_t)nsym || l < 1 || l > O_LMAX || (int)l < prev || lens[sym]) return ORC_ERR_ARG;
+    if (n == 1 && l != 1) return ORC_ERR_ARG;
+    lens[sym] = (uint8_t)l;
+    order[t] = sym;
+    prev = (int)l;
+    kraft += ldexp(1.0, -(int)l);
+    have0 |= sym == 0;
+  }
+  if (kraft > 1.0 || !have0) return ORC_ERR_ARG;
+  return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Algorithm 1: compression.                                                  */
+/* With p->codebook (Section IV.C: the Huffman code built in the training     */
+/* phase from the validation set's averaged per-block code frequencies and    */
+/* kept for the compression phase), the code words come from that list        */
+/* instead of the field's own histogram, and a code the list does not hold    */
+/* becomes a balance point (code 0, value stored) like any code outside the   */
+/* quantization range.  The container then carries the list as its codebook   */
+/* and places the bitstream before the balance-point values (header flag      */
+/* ORC_FLAG_STREAM_FIRST), the order in which a single pass can write them.   */
 /* ------------------------------------------------------------------------- */
 int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_params* p,
                  uint8_t* out, uint64_t cap, uint64_t* out_size, orc_dump* dump) {
@@ -926,6 +961,16 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
     okv[i] = (uint8_t)ok;
   }
 
+  /* a given codebook: its lengths and symbol order */
+  int fixed_cb = p->codebook != NULL;
+  uint8_t* lens = (uint8_t*)malloc((size_t)nsym);
+  uint32_t* cw = (uint32_t*)calloc((size_t)nsym, sizeof(uint32_t));
+  uint32_t* order = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)nsym);
+  if (fixed_cb && o_codebook_check(p->codebook, p->codebook_n, p->m, lens, order)) {
+    free(lens); free(cw); free(order); free(dq); free(okv);
+    return ORC_ERR_ARG;
+  }
+
   /* a5-a9: per block predict, select, quantize, histogram */
   uint16_t* codes = (uint16_t*)calloc(g.nblocks * g.bvol, sizeof(uint16_t));
   uint8_t* nnf = (uint8_t*)calloc(g.nblocks, 1);
@@ -960,19 +1005,18 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
         const uint16_t* cs = usen ? cn : cz;
         int no = 1;  /* the anchor */
         for (int j = 1; j < np; j++) {
-          codes[bi * g.bvol + j] = cs[j];
-          hist[cs[j]]++;
-          if (cs[j] == 0) no++;
+          /* a code outside a given codebook is stored as a balance point */
+          uint16_t cd = (fixed_cb && lens[cs[j]] == 0) ? 0 : cs[j];
+          codes[bi * g.bvol + j] = cd;
+          hist[cd]++;
+          if (cd == 0) no++;
         }
         nout[bi] = (uint16_t)no;
         n_out += (uint64_t)no;
       }
 
-  /* a10: code lengths and canonical codes */
-  uint8_t* lens = (uint8_t*)malloc((size_t)nsym);
-  uint32_t* cw = (uint32_t*)calloc((size_t)nsym, sizeof(uint32_t));
-  uint32_t* order = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)nsym);
-  int n_used = orc_huffman_lengths(hist, nsym, O_LMAX, lens, order);
+  /* a10: code lengths and canonical codes (of the field's histogram, or the given list) */
+  int n_used = fixed_cb ? p->codebook_n : orc_huffman_lengths(hist, nsym, O_LMAX, lens, order);
   orc_canonical_codes(order, n_used, lens, cw);
 
   /* a11: per-block bit counts and total */
@@ -999,9 +1043,16 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
   uint64_t off_cb = al16(off_w + (use_q ? 8ull : 4ull) * (uint64_t)nw);
   uint64_t off_bb = al16(off_cb + 4ull * (uint64_t)n_used);
   uint64_t off_bn = al16(off_bb + 4ull * g.nblocks);
-  uint64_t off_ov = al16(off_bn + 2ull * g.nblocks);
-  uint64_t off_st = al16(off_ov + ts * n_out);
-  uint64_t total = al16(off_st + 4ull * swords);
+  uint64_t off_ov, off_st, total;
+  if (fixed_cb) {
+    off_st = al16(off_bn + 2ull * g.nblocks);
+    off_ov = al16(off_st + 4ull * swords);
+    total = al16(off_ov + ts * n_out);
+  } else {
+    off_ov = al16(off_bn + 2ull * g.nblocks);
+    off_st = al16(off_ov + ts * n_out);
+    total = al16(off_st + 4ull * swords);
+  }
   int ret = ORC_OK;
   if (total > cap) { ret = ORC_ERR_CAPACITY; goto done; }
   memset(out, 0, total);
@@ -1037,6 +1088,7 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
   put64(out + 192, off_bn); put64(out + 200, off_ov); put64(out + 208, off_st);
   put64(out + 216, total);
   put32(out + 224, (uint32_t)nw);
+  put32(out + 228, fixed_cb ? ORC_FLAG_STREAM_FIRST : 0u);
   put32(out + 252, orc_crc32(out, 252));
 
   /* sections */
@@ -1831,12 +1883,13 @@ int orc_block_codes(const void* x, const uint64_t dims[3], int dtype, const orc_
 /* its stored value (value_bits, 32 or 64).  Returns the simulated size in    */
 /* bits; w == NULL scores Lorenzo.                                            */
 /* ------------------------------------------------------------------------- */
-uint64_t orc_val_size(const float* w, int k, int h1, int h2, int s_in, const int32_t* in, const int32_t* tg,
-                      const uint8_t* use, uint64_t n, int m, int value_bits) {
+/* The validation histogram of one predictor: every used sample's residual  */
+/* quantized as the compressor would (code k + R, or 0 when |k| >= R).       */
+void orc_val_hist(const float* w, int k, int h1, int h2, int s_in, const int32_t* in, const int32_t* tg,
+                  const uint8_t* use, uint64_t n, int m, uint64_t* hist) {
   int nsym = 1 << m;
   int64_t R = (int64_t)1 << (m - 1);
-  uint64_t* hist = (uint64_t*)calloc((size_t)nsym, sizeof(uint64_t));
-  uint8_t* lens = (uint8_t*)malloc((size_t)nsym);
+  memset(hist, 0, sizeof(uint64_t) * (size_t)nsym);
   for (uint64_t i = 0; i < n; i++) {
     if (!use[i]) continue;
     int64_t pr;
@@ -1850,11 +1903,75 @@ uint64_t orc_val_size(const float* w, int k, int h1, int h2, int s_in, const int
     int64_t a = d < 0 ? -d : d;
     hist[a <= R - 1 ? d + R : 0]++;
   }
+}
+
+uint64_t orc_val_size(const float* w, int k, int h1, int h2, int s_in, const int32_t* in, const int32_t* tg,
+                      const uint8_t* use, uint64_t n, int m, int value_bits) {
+  int nsym = 1 << m;
+  uint64_t* hist = (uint64_t*)calloc((size_t)nsym, sizeof(uint64_t));
+  uint8_t* lens = (uint8_t*)malloc((size_t)nsym);
+  orc_val_hist(w, k, h1, h2, s_in, in, tg, use, n, m, hist);
   orc_huffman_lengths(hist, nsym, O_LMAX, lens, NULL);
   uint64_t bits = hist[0] * (uint64_t)value_bits;
   for (int c = 0; c < nsym; c++) bits += hist[c] * (uint64_t)lens[c];
   free(lens); free(hist);
   return bits;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Section IV.C, the Huffman code of the training phase: from the validation  */
+/* set's code frequencies averaged per block, a Huffman tree whose code the   */
+/* compression phase then uses directly.  Readings: averaging divides every   */
+/* count by the same number of blocks, which leaves the Huffman construction  */
+/* unchanged, so the totals are used; symbol 0 (the balance-point marker)     */
+/* counts at least once, so that balance points stay codable whether or not  */
+/* the sample held one.  Writes the list (sym | len << 16, most frequent      */
+/* first) and returns its length.                                             */
+/* ------------------------------------------------------------------------- */
+int orc_sample_codebook(const uint64_t* hist, int m, uint32_t* list) {
+  int nsym = 1 << m;
+  uint64_t* h = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)nsym);
+  uint8_t* lens = (uint8_t*)malloc((size_t)nsym);
+  uint32_t* order = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)nsym);
+  memcpy(h, hist, sizeof(uint64_t) * (size_t)nsym);
+  if (h[0] == 0) h[0] = 1;
+  int n = orc_huffman_lengths(h, nsym, O_LMAX, lens, order);
+  for (int t = 0; t < n; t++) list[t] = order[t] | ((uint32_t)lens[order[t]] << 16);
+  free(order); free(lens); free(h);
+  return n;
+}
+
+/* The sample codebook of a field for one predictor (FP32 weights w, or       */
+/* Lorenzo when w is NULL): the validation samples are drawn as the training  */
+/* phase draws them (seed, thr32), their residuals histogrammed at m code     */
+/* bits, and the list built by orc_sample_codebook.  Returns its length, or a */
+/* negative status.                                                           */
+int orc_sample_codebook_for(const void* x, const uint64_t dims[3], int dtype, double eb, const int block[3], int k,
+                            int h1, int h2, int s_in, const float* w, int m, uint64_t seed, uint32_t thr32,
+                            uint32_t* list) {
+  uint64_t n = dims[0] * dims[1] * dims[2];
+  double amin, amax;
+  int trivial;
+  int st = orc_stats(x, n, dtype, &amin, &amax, &trivial);
+  if (st) return st;
+  orc_consts c;
+  st = orc_make_consts(dtype, amin, amax, trivial, eb, &c);
+  if (st) return st;
+  uint64_t nt, nv;
+  st = orc_count_samples(dims, block, seed, thr32, &nt, &nv);
+  if (st) return st;
+  int32_t* tin = (int32_t*)malloc(sizeof(int32_t) * (nt * k + 1));
+  int32_t* ttg = (int32_t*)malloc(sizeof(int32_t) * (nt + 1));
+  uint8_t* tus = (uint8_t*)malloc(nt + 1);
+  int32_t* vin = (int32_t*)malloc(sizeof(int32_t) * (nv * k + 1));
+  int32_t* vtg = (int32_t*)malloc(sizeof(int32_t) * (nv + 1));
+  uint8_t* vus = (uint8_t*)malloc(nv + 1);
+  uint64_t* hist = (uint64_t*)malloc(sizeof(uint64_t) << m);
+  orc_gather_samples(x, dims, dtype, &c, block, k, seed, thr32, tin, ttg, tus, vin, vtg, vus);
+  orc_val_hist(w, k, h1, h2, s_in, vin, vtg, vus, nv, m, hist);
+  int nl = orc_sample_codebook(hist, m, list);
+  free(hist); free(tin); free(ttg); free(tus); free(vin); free(vtg); free(vus);
+  return nl;
 }
 
 /* Section IV.C, the coverage rule for m: coverage(m) is the fraction of the  */

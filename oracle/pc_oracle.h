@@ -51,7 +51,14 @@ typedef struct {
   int s_in;              /* input scale: u = v * 2^-s_in */
   const float* weights;  /* MLP weight blob, NULL for Lorenzo only */
   const int64_t* qnet;   /* fixed-point network (ORC_PRED_MLP_BF16), see orc_qnet_len */
+  const uint32_t* codebook; /* sample codebook (sym | len << 16, container order) or NULL: see
+                               orc_compress; NULL builds the code of the field's own histogram */
+  int codebook_n;        /* entries of codebook */
 } orc_params;
+
+/* container flag (header offset 228): the bitstream section precedes the
+ * balance-point values (the layout of a compression with a sample codebook) */
+#define ORC_FLAG_STREAM_FIRST 1u
 
 typedef struct {
   int32_t* dq;           /* [N] integer log codes, field order */
