@@ -362,17 +362,16 @@ def train_predictors(torch, pc, fields, spec, dev):
     return out
 
 
-def params_for(pc, spec, info, form):
+def params_for(pc, spec, info, form, codebook=None):
     eb, k, h1, h2 = spec["eb"], spec["k"], spec["h1"], spec["h2"]
-    if info["w"] is None:
-        return pc.make_params(eb, BLOCK), "lorenzo"
+    cb = dict(codebook=codebook)
+    if info["w"] is None or form == "lorenzo":
+        return pc.make_params(eb, BLOCK, **cb), "lorenzo"
     if form == "bf16":
         return pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_BF16, stencil=k, hidden=(h1, h2), s_in=info["s_in"],
-                              qnet=info["q"]), f"mlp_bf16_fixed_point_s{k}_{h1}x{h2}"
-    if form == "lorenzo":
-        return pc.make_params(eb, BLOCK), "lorenzo"
+                              qnet=info["q"], **cb), f"mlp_bf16_fixed_point_s{k}_{h1}x{h2}"
     return pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_FP32, stencil=k, hidden=(h1, h2), s_in=info["s_in"],
-                          weights=info["w"]), f"mlp_fp32_s{k}_{h1}x{h2}"
+                          weights=info["w"], **cb), f"mlp_fp32_s{k}_{h1}x{h2}"
 
 
 class Runner:
@@ -656,6 +655,56 @@ def form_compare(torch, pc, w, args, stream, flush):
     return forms
 
 
+def single_pass(torch, pc, w, args, stream, flush, peak, two_pass):
+    """Single-pass compression with the training phase's sample codebook (Section IV.C): the Huffman
+    code of the validation samples' residuals (the chosen FP32 network's, or Lorenzo's), then one pass
+    over each field.  Throughput, bits/value and the bits lost against the field's own code."""
+    spec, infos, fields = w["spec"], w["infos"], w["spec"]["_fields"]
+    k, h1, h2, eb = spec["k"], spec["h1"], spec["h2"], spec["eb"]
+    out = {}
+    for form in (w["form"], "lorenzo"):
+        cbs, lits, t_cb = [], [], 0.0
+        for d, inf in zip(fields, infos):
+            use_w = form != "lorenzo" and inf["w"] is not None
+            dt = pc.PC_F32 if d.dtype == torch.float32 else pc.PC_F64
+            pp = pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_FP32 if use_w else pc.PC_PRED_LORENZO, stencil=k,
+                                hidden=(h1, h2), s_in=inf["s_in"] if use_w else 0,
+                                weights=inf["w"] if use_w else None)
+            ws = torch.empty(pc.pc_train_workspace_size(tuple(d.shape), dt, pp, inf["thr32"], 1),
+                             dtype=torch.uint8, device=d.device)
+            lits.append(pc.pc_sample_codebook(d, pp, 0, inf["thr32"], ws))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            cbs.append(pc.pc_sample_codebook(d, pp, 0, inf["thr32"], ws, span_fill=True))
+            torch.cuda.synchronize()
+            t_cb += time.perf_counter() - t0
+            del ws
+        params = [params_for(pc, spec, inf, form, cb)[0] for inf, cb in zip(infos, cbs)]
+        res, r = measure(torch, pc, fields, spec, params, max(3, min(args.steps, 10)), 2, stream, flush)
+        r.free()
+        e = {k2: res[k2] for k2 in ("compress_gbs", "decompress_gbs", "bits_per_value", "bound_held", "compress_ms",
+                                    "decompress_ms", "stages_ms_per_step")}
+        e["hbm_roofline"] = hbm_fractions(res, peak)
+        e["sample_codebook_s"] = t_cb
+        e["codebook"] = "span-filled sample code (every code inside the sampled span has a code word)"
+        e["codebook_entries"] = [int(c.size) for c in cbs]
+        # the literal reading: codes the sample never saw become balance points
+        lit_bytes = 0
+        for d, inf, cb in zip(fields, infos, lits):
+            p = params_for(pc, spec, inf, form, cb)[0]
+            lit_bytes += pc.compress(d, p).numel()
+        e["literal_sample_code"] = {"bits_per_value": 8.0 * lit_bytes / res["points"],
+                                    "codebook_entries": [int(c.size) for c in lits]}
+        ref = two_pass.get(form)
+        if ref:
+            e["bits_vs_two_pass"] = res["bits_per_value"] / ref["bits_per_value"] - 1.0
+            e["literal_sample_code"]["bits_vs_two_pass"] = (e["literal_sample_code"]["bits_per_value"] /
+                                                            ref["bits_per_value"] - 1.0)
+            e["compress_speedup_vs_two_pass"] = ref["compress_ms"] / res["compress_ms"]
+        out[form] = e
+    return out
+
+
 def run_batch64(torch, pc, args, dev, stream, flush, peak):
     """The many-field batch: 32 2-D float32 fields 1800 x 3600 and 32 3-D float32 fields with dims drawn
     uniformly from [64, 384]^3, spectral slopes drawn from [2, 5], eb_rel cycling 1e-2, 1e-3, 1e-4;
@@ -904,8 +953,11 @@ def main():
     e2e, hosts = e2e_rate(torch, pc, r, max(3, min(args.steps, 10)))
     e2e_t = e2e_with_training(torch, pc, hosts, spec, head["form"], dev)
     r.free()
+    sp = None
     if not args.no_forms:
         forms = form_compare(torch, pc, head, args, stream, flush)
+        two = {f: forms[f] for f in ("fp32", "bf16", "lorenzo") if f in forms}
+        sp = single_pass(torch, pc, head, args, stream, flush, peak, two)
     # plain FP32: a device copy of the fields at HBM speed
     copy_gbs = []
     for d in spec["_fields"]:
@@ -962,7 +1014,8 @@ def main():
             "bits_per_value": res["bits_per_value"], "bound_held": res["bound_held"],
             "hbm_roofline": res["hbm_roofline"], "roofline": res["roofline"],
             "perceptron_blocks_fraction": res["perceptron_blocks_fraction"],
-            "perceptron_forms": forms, "stages_ms_per_step": res["stages_ms_per_step"],
+            "perceptron_forms": forms, "single_pass_sample_codebook": sp,
+            "stages_ms_per_step": res["stages_ms_per_step"],
             "training": res["training"], "training_seconds_total": res["training_seconds_total"],
             "vs_fp32_plain": {"bits_per_value": 32.0 * (2 if spec["dtype"] == "f64" else 1),
                               "ratio": 32.0 * (2 if spec["dtype"] == "f64" else 1) / res["bits_per_value"],

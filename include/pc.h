@@ -74,7 +74,14 @@ typedef struct {
   long long train_samples;/* expected number of sampled stencils of the training phase;
                              0 draws 10% of the non-anchor points (Section IV.C) */
   int ndims;              /* 1, 2 or 3 (0: not stated); the leading 3 - ndims dims must be 1 */
-  int reserved_;          /* 0 */
+  int codebook_n;         /* entries of h_codebook */
+  const unsigned int* h_codebook;
+                          /* host pointer to a sample codebook (pc_sample_codebook) or NULL.
+                             With it, pc_compress runs in one pass over the field: the code
+                             words come from this list instead of the field's own histogram,
+                             a code the list lacks becomes a balance point, and the container
+                             places the bitstream before the balance values (Section IV.C
+                             keeps the training phase's Huffman code for compression) */
 } pc_params;
 /*
  * Learned predictor trained inside pc_compress (Section IV.C, V): with
@@ -288,6 +295,31 @@ int pc_train_select(const void* d_field, const size_t dims[3], int dtype, const 
                     unsigned long long seed, unsigned int thr32, int nmodels, const float* h_lrs,
                     const float* h_lams, float* h_weights_out, int* s_in_out, int* chosen_out,
                     unsigned long long* h_sizes, int* m_out, void* d_ws, size_t ws_bytes, void* stream);
+
+/*
+ * Sample codebook (Section IV.C): the training phase draws its validation
+ * samples (seed, thr32, as pc_train), quantizes their residuals under the
+ * predictor of p -- the FP32 weights p->h_weights (stencil, hidden, s_in), or
+ * Lorenzo when p->pred is PC_PRED_LORENZO -- at p->m code bits, and builds the
+ * Huffman code of their histogram.  The paper averages the frequencies per
+ * block; dividing every count by the block count leaves the Huffman code
+ * unchanged, so the totals are used.  Symbol 0 (the balance-point marker)
+ * counts at least once so that balance points stay codable.  A code the
+ * sample never saw has no code word and compresses as a balance point;
+ * span_fill = 1 gives every code between the smallest and the largest sampled
+ * code a code word (counted once), so that only codes beyond the sampled span
+ * do (not in the paper: a small validation sample of a wide residual
+ * distribution misses many codes inside its span).
+ *   h_codebook_out [out] host, up to 2^m entries: sym | length << 16, in the
+ *                  order the container stores them (most frequent first).
+ *   n_out          [out] number of entries.
+ * Pass the list as pc_params.h_codebook / codebook_n to compress in one pass.
+ * Workspace: pc_train_workspace_size(dims, dtype, p, thr32, 1).
+ * Errors: PC_ERR_ARG (unsupported shape, missing weights), PC_ERR_CAPACITY, PC_ERR_CUDA.
+ */
+int pc_sample_codebook(const void* d_field, const size_t dims[3], int dtype, const pc_params* p,
+                       unsigned long long seed, unsigned int thr32, int span_fill, unsigned int* h_codebook_out,
+                       int* n_out, void* d_ws, size_t ws_bytes, void* stream);
 
 /* Diagnostics for tests: offsets (bytes) of the per-point codes (u16, block-strided,
  * nblocks * block volume), per-block perceptron flags (u8) and the code histogram

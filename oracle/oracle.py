@@ -100,11 +100,11 @@ def lib():
             L.orc_val_hist.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_uint64, C.c_int, C.c_void_p]
             L.orc_sample_codebook.restype = C.c_int
-            L.orc_sample_codebook.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
+            L.orc_sample_codebook.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p]
             L.orc_sample_codebook_for.restype = C.c_int
             L.orc_sample_codebook_for.argtypes = [C.c_void_p, u64p, C.c_int, C.c_double, C.POINTER(C.c_int),
                                                   C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
-                                                  C.c_uint64, C.c_uint32, C.c_void_p]
+                                                  C.c_uint64, C.c_uint32, C.c_int, C.c_void_p]
             L.orc_coverage_m.restype = C.c_int
             L.orc_coverage_m.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_uint64, C.c_double]
@@ -556,18 +556,19 @@ def val_hist(w, k, h1, h2, s_in, inp, tg, use, m=16) -> np.ndarray:
     return h
 
 
-def sample_codebook(hist, m=16) -> np.ndarray:
+def sample_codebook(hist, m=16, span_fill=False) -> np.ndarray:
     """The training phase's Huffman code from a validation histogram: uint32 list
-    (sym | len << 16) in container order."""
+    (sym | len << 16) in container order.  span_fill: every code inside the sampled span
+    gets a code word."""
     h = np.ascontiguousarray(hist, np.uint64)
     assert h.size == 1 << m
     out = np.zeros(1 << m, np.uint32)
-    n = lib().orc_sample_codebook(_p(h), m, _p(out))
+    n = lib().orc_sample_codebook(_p(h), m, int(bool(span_fill)), _p(out))
     return out[:n].copy()
 
 
 def sample_codebook_for(x: np.ndarray, eb: float, block=(8, 8, 8), k=7, h1=16, h2=16, s_in=0, weights=None, m=16,
-                        seed=0, thr32=None) -> np.ndarray:
+                        seed=0, thr32=None, span_fill=False) -> np.ndarray:
     """Sample codebook of field x for the FP32 weights (None: Lorenzo), validation samples drawn
     as the training phase draws them."""
     x = np.ascontiguousarray(x)
@@ -577,7 +578,7 @@ def sample_codebook_for(x: np.ndarray, eb: float, block=(8, 8, 8), k=7, h1=16, h
     out = np.zeros(1 << m, np.uint32)
     b = (C.c_int * 3)(*block)
     n = lib().orc_sample_codebook_for(_p(x), _dims(x), _dtype_code(x), eb, b, k, h1, h2, s_in,
-                                      None if w is None else _p(w), m, seed, thr32, _p(out))
+                                      None if w is None else _p(w), m, seed, thr32, int(bool(span_fill)), _p(out))
     assert n > 0, n
     return out[:n].copy()
 

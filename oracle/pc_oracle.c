@@ -1925,15 +1925,27 @@ uint64_t orc_val_size(const float* w, int k, int h1, int h2, int s_in, const int
 /* count by the same number of blocks, which leaves the Huffman construction  */
 /* unchanged, so the totals are used; symbol 0 (the balance-point marker)     */
 /* counts at least once, so that balance points stay codable whether or not  */
-/* the sample held one.  Writes the list (sym | len << 16, most frequent      */
-/* first) and returns its length.                                             */
+/* the sample held one.  The paper leaves codes the sample never saw without  */
+/* a code word (they become balance points).  With span_fill, every code     */
+/* between the smallest and the largest code the sample saw counts at least   */
+/* once too, so that only codes beyond the sampled span become balance points */
+/* (a variant of this build: a validation sample of a wide residual           */
+/* distribution misses many codes inside its span).  Writes the list          */
+/* (sym | len << 16, most frequent first) and returns its length.             */
 /* ------------------------------------------------------------------------- */
-int orc_sample_codebook(const uint64_t* hist, int m, uint32_t* list) {
+int orc_sample_codebook(const uint64_t* hist, int m, int span_fill, uint32_t* list) {
   int nsym = 1 << m;
   uint64_t* h = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)nsym);
   uint8_t* lens = (uint8_t*)malloc((size_t)nsym);
   uint32_t* order = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)nsym);
   memcpy(h, hist, sizeof(uint64_t) * (size_t)nsym);
+  if (span_fill) {
+    int lo = nsym, hi = 0;
+    for (int c = 1; c < nsym; c++)
+      if (h[c] > 0) { if (c < lo) lo = c; hi = c; }
+    for (int c = lo; c <= hi; c++)
+      if (h[c] == 0) h[c] = 1;
+  }
   if (h[0] == 0) h[0] = 1;
   int n = orc_huffman_lengths(h, nsym, O_LMAX, lens, order);
   for (int t = 0; t < n; t++) list[t] = order[t] | ((uint32_t)lens[order[t]] << 16);
@@ -1948,7 +1960,7 @@ int orc_sample_codebook(const uint64_t* hist, int m, uint32_t* list) {
 /* negative status.                                                           */
 int orc_sample_codebook_for(const void* x, const uint64_t dims[3], int dtype, double eb, const int block[3], int k,
                             int h1, int h2, int s_in, const float* w, int m, uint64_t seed, uint32_t thr32,
-                            uint32_t* list) {
+                            int span_fill, uint32_t* list) {
   uint64_t n = dims[0] * dims[1] * dims[2];
   double amin, amax;
   int trivial;
@@ -1969,7 +1981,7 @@ int orc_sample_codebook_for(const void* x, const uint64_t dims[3], int dtype, do
   uint64_t* hist = (uint64_t*)malloc(sizeof(uint64_t) << m);
   orc_gather_samples(x, dims, dtype, &c, block, k, seed, thr32, tin, ttg, tus, vin, vtg, vus);
   orc_val_hist(w, k, h1, h2, s_in, vin, vtg, vus, nv, m, hist);
-  int nl = orc_sample_codebook(hist, m, list);
+  int nl = orc_sample_codebook(hist, m, span_fill, list);
   free(hist); free(tin); free(ttg); free(tus); free(vin); free(vtg); free(vus);
   return nl;
 }

@@ -67,6 +67,31 @@ bool qshape_ok(int k, int h1, int h2) { return (k == 7 && h1 == 16 && h2 == 16) 
 bool train_shape_ok(int k, int h1, int h2);
 
 // The predictor is trained inside pc_compress (no weights given).
+// A given codebook list (sym | length << 16, in container order): at most
+// 2^m entries, symbols below 2^m and distinct, lengths 1..24 never decreasing
+// (the canonical construction runs along the list), Kraft sum at most one,
+// symbol 0 present (balance points are coded as symbol 0), and a single
+// entry of length 1.
+bool codebook_ok(const unsigned int* cb, int n, int m) {
+  const int nsym = 1 << m;
+  if (n < 1 || n > nsym) return false;
+  static thread_local uint8_t seen[1 << 16];
+  memset(seen, 0, (size_t)nsym);
+  unsigned long long kraft = 0;  // in units of 2^-24
+  int prev = 1;
+  bool have0 = false;
+  for (int i = 0; i < n; ++i) {
+    const unsigned int sym = cb[i] & 0xFFFFu, l = cb[i] >> 16;
+    if (sym >= (unsigned int)nsym || l < 1 || l > (unsigned int)kLmax || (int)l < prev || seen[sym]) return false;
+    if (n == 1 && l != 1) return false;
+    seen[sym] = 1;
+    prev = (int)l;
+    kraft += 1ull << (kLmax - l);
+    have0 |= sym == 0;
+  }
+  return have0 && kraft <= (1ull << kLmax);
+}
+
 bool wants_training(const pc_params* p) {
   return (p->pred == PC_PRED_MLP_FP32 && !p->h_weights) || (p->pred == PC_PRED_MLP_BF16 && !p->h_qnet);
 }
@@ -81,6 +106,7 @@ int check_params(const size_t dims[3], int dtype, const pc_params* p, Geo& g, in
     if (dims[i] != 1) return PC_ERR_ARG;
   if (!make_geo(dims, p->block, g)) return PC_ERR_ARG;
   if (!shape_supported(p->block)) return PC_ERR_ARG;
+  if (p->h_codebook && !codebook_ok(p->h_codebook, p->codebook_n, p->m)) return PC_ERR_ARG;
   mode = p->pred == PC_PRED_MLP_FP32 ? 1 : (p->pred == PC_PRED_MLP_BF16 ? 2 : 0);
   if (p->pred != PC_PRED_LORENZO && p->pred != PC_PRED_MLP_FP32 && p->pred != PC_PRED_MLP_BF16) return PC_ERR_ARG;
   nw = 0;
@@ -106,10 +132,13 @@ int check_params(const size_t dims[3], int dtype, const pc_params* p, Geo& g, in
 
 struct CompLayout {
   size_t st, tabs, hist, lens, cw, key, w, parent, depth, la, lb, rstart, symord, codes, nnflag, nout, bbits, cbits, cnout,
-      cboff, cooff, total;
+      cboff, cooff, rec, side, next, ov, total;
 };
 
-CompLayout comp_layout(const Geo& g, int m) {
+// sp: single pass (a given codebook): no code spill; look-back records, brick
+// edge words, the brick counter and room for every point as a balance value
+// (ts bytes each) instead.
+CompLayout comp_layout(const Geo& g, int m, bool sp = false, size_t ts = 4) {
   const size_t nsym = (size_t)1 << m;
   size_t np = 1;
   while (np < nsym) np <<= 1;
@@ -128,7 +157,7 @@ CompLayout comp_layout(const Geo& g, int m) {
   L.lb = o; o = up(o + 4 * nsym);
   L.rstart = o; o = up(o + 4 * (nsym + 2));
   L.symord = o; o = up(o + 4 * nsym);
-  L.codes = o; o = up(o + 2 * (size_t)g.nblocks * g.bvol);
+  L.codes = o; o = up(o + (sp ? 0 : 2 * (size_t)g.nblocks * g.bvol));
   L.nnflag = o; o = up(o + (size_t)g.nblocks);
   L.nout = o; o = up(o + 4 * (size_t)g.nblocks);
   L.bbits = o; o = up(o + 4 * (size_t)g.nblocks);
@@ -136,6 +165,11 @@ CompLayout comp_layout(const Geo& g, int m) {
   L.cnout = o; o = up(o + 8 * (size_t)g.nchunks);
   L.cboff = o; o = up(o + 8 * (size_t)g.nchunks);
   L.cooff = o; o = up(o + 8 * (size_t)g.nchunks);
+  const size_t nbk = sp ? (size_t)bricks_of(g) : 0;
+  L.rec = o; o = up(o + 16 * nbk);
+  L.side = o; o = up(o + 8 * nbk);
+  L.next = o; o = up(o + (sp ? 16 : 0));
+  L.ov = o; o = up(o + (sp ? ts * (size_t)g.n[0] * g.n[1] * g.n[2] : 0));
   L.total = o;
   return L;
 }
@@ -225,6 +259,8 @@ int parse_header(const uint8_t* h, size_t n, Hdr& H, Geo& g) {
   H.off_st = rd64(h + 208);
   H.total = rd64(h + 216);
   H.nw = (int)rd32(h + 224);
+  const unsigned int flags = rd32(h + 228);
+  if (flags & ~kFlagStreamFirst) return PC_ERR_CORRUPT;
   if (H.dtype != PC_F32 && H.dtype != PC_F64) return PC_ERR_CORRUPT;
   if (H.m < 2 || H.m > 16) return PC_ERR_CORRUPT;
   for (int i = 0; i < 3; ++i)
@@ -249,9 +285,12 @@ int parse_header(const uint8_t* h, size_t n, Hdr& H, Geo& g) {
   const unsigned long long ocb = al16(kHdr + (H.pred == 2 ? 8ull : 4ull) * H.nw);
   const unsigned long long obb = al16(ocb + 4ull * H.n_used);
   const unsigned long long obn = al16(obb + 4ull * H.nblocks);
-  const unsigned long long oov = al16(obn + 2ull * H.nblocks);
-  const unsigned long long ost = al16(oov + ts * H.n_out);
-  const unsigned long long tot = al16(ost + 4ull * H.swords);
+  // balance values then stream, or (single pass) stream then balance values
+  const bool sfirst = (flags & kFlagStreamFirst) != 0;
+  const unsigned long long oov =
+      sfirst ? al16(al16(obn + 2ull * H.nblocks) + 4ull * H.swords) : al16(obn + 2ull * H.nblocks);
+  const unsigned long long ost = sfirst ? al16(obn + 2ull * H.nblocks) : al16(oov + ts * H.n_out);
+  const unsigned long long tot = sfirst ? al16(oov + ts * H.n_out) : al16(ost + 4ull * H.swords);
   if (H.off_cb != ocb || H.off_bb != obb || H.off_bn != obn || H.off_ov != oov || H.off_st != ost || H.total != tot)
     return PC_ERR_CORRUPT;
   return PC_OK;
@@ -428,6 +467,15 @@ struct FieldPlan {
   HuffScratch hs;
   const long long* h_qnet;  // host network to copy into the container (fixed-point form)
   const long long* qnet;    // its device copy in the container's weights section
+  // single pass (a given codebook)
+  bool sp;
+  const unsigned int* h_cb;
+  int cb_n;
+  unsigned long long off_bb, off_bn, off_st;
+  unsigned long long* rec;
+  uint32_t* side;
+  unsigned long long* next;
+  void* ov;
 };
 
 // Lay out one field's compression (checked parameters, explicit weights).
@@ -441,7 +489,7 @@ int plan_field(FieldPlan& F, const void* d_field, const size_t dims[3], int dtyp
   F.m = p->m;
   F.eb = p->eb_rel;
   F.g = g;
-  F.L = comp_layout(g, p->m);
+  F.L = comp_layout(g, p->m, p->h_codebook != nullptr, dtype == PC_F64 ? 8 : 4);
   if (ws_bytes < F.L.total) return PC_ERR_CAPACITY;
   HdrInfo& hi = F.hi;
   hi.dtype = dtype;
@@ -453,6 +501,7 @@ int plan_field(FieldPlan& F, const void* d_field, const size_t dims[3], int dtyp
   hi.s_in = p->s_in;
   hi.nw = nw;
   hi.wsz = mode == 2 ? 8 : 4;
+  hi.flags = p->h_codebook ? kFlagStreamFirst : 0u;
   hi.eb = p->eb_rel;
   hi.off_cb = al16(kHdr + (unsigned long long)hi.wsz * nw);
   hi.cap = out_cap;
@@ -489,6 +538,17 @@ int plan_field(FieldPlan& F, const void* d_field, const size_t dims[3], int dtyp
   // section, where the kernels read it
   F.h_qnet = mode == 2 ? p->h_qnet : nullptr;
   F.qnet = mode == 2 ? reinterpret_cast<const long long*>(F.out + kHdr) : nullptr;
+  F.sp = p->h_codebook != nullptr;
+  F.h_cb = p->h_codebook;
+  F.cb_n = p->codebook_n;
+  F.off_bb = al16(hi.off_cb + 4ull * (unsigned long long)(F.sp ? p->codebook_n : 0));
+  F.off_bn = al16(F.off_bb + 4ull * (unsigned long long)g.nblocks);
+  F.off_st = al16(F.off_bn + 2ull * (unsigned long long)g.nblocks);
+  F.rec = reinterpret_cast<unsigned long long*>(ws + L.rec);
+  F.side = reinterpret_cast<uint32_t*>(ws + L.side);
+  F.next = reinterpret_cast<unsigned long long*>(ws + L.next);
+  F.ov = ws + L.ov;
+  if (F.sp && out_cap < F.off_st) return PC_ERR_CAPACITY;
   return PC_OK;
 }
 
@@ -499,8 +559,16 @@ int launch_head(const FieldPlan& F, cudaStream_t s, int nsm) {
     return PC_ERR_CUDA;
   const unsigned long long n = (unsigned long long)F.dims[0] * F.dims[1] * F.dims[2];
   const int nsym = 1 << F.m;
-  return F.dtype == PC_F32 ? launch_stats_consts<float>(F.x, n, F.stp, F.tabs, F.hist, nsym, F.eb, nsm, s)
-                           : launch_stats_consts<double>(F.x, n, F.stp, F.tabs, F.hist, nsym, F.eb, nsm, s);
+  int r = F.dtype == PC_F32 ? launch_stats_consts<float>(F.x, n, F.stp, F.tabs, F.hist, nsym, F.eb, nsm, s)
+                            : launch_stats_consts<double>(F.x, n, F.stp, F.tabs, F.hist, nsym, F.eb, nsm, s);
+  if (r || !F.sp) return r;
+  // single pass: the codebook into the container and its code table, cleared
+  // look-back records and brick counter
+  const size_t nbk = (size_t)bricks_of(F.g);
+  if (cudaMemcpyAsync(F.out + F.hi.off_cb, F.h_cb, 4ull * F.cb_n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemsetAsync(F.rec, 0, 16 * nbk, s) != cudaSuccess || cudaMemsetAsync(F.next, 0, 16, s) != cudaSuccess)
+    return PC_ERR_CUDA;
+  return launch_cb_table(F.out, F.hi.off_cb, F.cb_n, F.m, F.cw, F.stp, F.g, F.hi.cap, s);
 }
 
 CJob job_of(const FieldPlan& F) {
@@ -515,11 +583,35 @@ CJob job_of(const FieldPlan& F) {
   job.hist = F.hist;
   job.qnet = F.qnet;
   job.m = F.m;
+  if (F.sp) {
+    job.out = F.out;
+    job.cwl = F.cw;
+    job.rec = F.rec;
+    job.side = F.side;
+    job.ov = F.ov;
+    job.off_bb = F.off_bb;
+    job.off_bn = F.off_bn;
+    job.off_st = F.off_st;
+    job.cap_words = F.hi.cap > F.off_st ? (F.hi.cap - F.off_st) / 4 : 0;
+    job.nbk = bricks_of(F.g);
+  }
   return job;
 }
 
-// a10-a12
-int launch_tail(FieldPlan& F, const Mlp& mlp, cudaStream_t s) {
+// a10-a12 (single pass: only the finish)
+int launch_tail(FieldPlan& F, const Mlp& mlp, cudaStream_t s, int nsm) {
+  if (F.sp) {
+    SpFinish f;
+    f.rec = F.rec;
+    f.side = F.side;
+    f.ov = F.ov;
+    f.nbk = bricks_of(F.g);
+    f.off_bb = F.off_bb;
+    f.off_bn = F.off_bn;
+    f.off_st = F.off_st;
+    return F.dtype == PC_F32 ? launch_sp_finish<float>(F.g, F.stp, F.out, F.hi, mlp, f, nsm, s)
+                             : launch_sp_finish<double>(F.g, F.stp, F.out, F.hi, mlp, f, nsm, s);
+  }
   int r = launch_codebook(F.hist, F.m, F.lens, F.cw, F.stp, F.hs, F.out, F.g, F.hi, s);
   if (r) return r;
   const CompLayout& L = F.L;
@@ -733,6 +825,68 @@ int pc_train_select(const void* d_field, const size_t dims[3], int dtype, const 
                    h_sizes, true, m_out, d_ws, ws_bytes, stream);
 }
 
+int pc_sample_codebook(const void* d_field, const size_t dims[3], int dtype, const pc_params* p,
+                       unsigned long long seed, unsigned int thr32, int span_fill, unsigned int* h_codebook_out,
+                       int* n_out, void* d_ws, size_t ws_bytes, void* stream) {
+  if (!p || !d_field || !h_codebook_out || !n_out || !d_ws) return PC_ERR_ARG;
+  const bool lorenzo = p->pred == PC_PRED_LORENZO;
+  if (!lorenzo && (p->pred != PC_PRED_MLP_FP32 && p->pred != PC_PRED_MLP_BF16)) return PC_ERR_ARG;
+  if (!lorenzo && (!p->h_weights || p->s_in < 0 || p->s_in > 30)) return PC_ERR_ARG;
+  // the sampling and the histogram run on the training phase's buffers
+  pc_params tp = *p;
+  if (lorenzo) {
+    tp.stencil = 7;
+    tp.hidden[0] = 16;
+    tp.hidden[1] = 16;
+  }
+  Geo g;
+  int nw;
+  int st = train_check(dims, dtype, &tp, 1, g, nw);
+  if (st) return st;
+  TrainLayout L = train_layout(g, tp.m, tp.stencil, nw, thr32, 1);
+  if (ws_bytes < L.total) return PC_ERR_CAPACITY;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int nsm = sm_count();
+  if (nsm <= 0) return PC_ERR_CUDA;
+  uint8_t* ws = static_cast<uint8_t*>(d_ws);
+  State* stp = reinterpret_cast<State*>(ws + L.st);
+  Tabs* tabs = reinterpret_cast<Tabs*>(ws + L.tabs);
+  auto* hist = reinterpret_cast<unsigned long long*>(ws + L.hist);
+  TrainBufs tb = train_bufs(L, ws);
+  SelectBufs sb = select_bufs(L, ws);
+  if ((lorenzo ? cudaMemsetAsync(tb.w, 0, 4ull * nw, s)
+               : cudaMemcpyAsync(tb.w, p->h_weights, 4ull * nw, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return PC_ERR_CUDA;
+  const unsigned long long n = (unsigned long long)dims[0] * dims[1] * dims[2];
+  const int nsym = 1 << tp.m;
+  int r;
+  if (dtype == PC_F32) {
+    r = launch_stats_consts<float>(d_field, n, stp, tabs, hist, nsym, tp.eb_rel, nsm, s);
+    if (!r) r = launch_sample_hist<float>(static_cast<const float*>(d_field), g, stp, tabs, tb, sb, tp.stencil,
+                                         tp.hidden[0], tp.hidden[1], tp.s_in, tp.m, lorenzo, span_fill, seed, thr32, s);
+  } else {
+    r = launch_stats_consts<double>(d_field, n, stp, tabs, hist, nsym, tp.eb_rel, nsm, s);
+    if (!r) r = launch_sample_hist<double>(static_cast<const double*>(d_field), g, stp, tabs, tb, sb, tp.stencil,
+                                          tp.hidden[0], tp.hidden[1], tp.s_in, tp.m, lorenzo, span_fill, seed, thr32, s);
+  }
+  if (r) return r;
+  unsigned long long ctl[8];
+  int herr = 0;
+  State hs;
+  if (cudaMemcpyAsync(ctl, tb.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&herr, &stp->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&hs, sb.st, sizeof(State), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(h_codebook_out, sb.list, 4ull * nsym, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return PC_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
+  prof_collect();
+  if (herr) return herr;
+  if (hs.err) return hs.err;
+  if (ctl[0] > L.cap_t || ctl[1] > L.cap_v) return PC_ERR_CAPACITY;
+  *n_out = (int)hs.n_used;
+  return PC_OK;
+}
+
 int pc_quantize(const void* d_field, const size_t dims[3], int dtype, const pc_params* p, unsigned long long seed,
                 unsigned int thr32, long long* h_qnet_out, void* d_ws, size_t ws_bytes, void* stream) {
   Geo g;
@@ -825,7 +979,7 @@ int pc_compress_workspace_size(const size_t dims[3], int dtype, const pc_params*
   int st = check_params(dims, dtype, p, g, mode, nw);
   if (st) return st;
   if (!ws) return PC_ERR_ARG;
-  *ws = comp_layout(g, p->m).total;
+  *ws = comp_layout(g, p->m, p->h_codebook != nullptr, dtype == PC_F64 ? 8 : 4).total;
   if (wants_training(p)) {
     const size_t tw = train_layout(g, p->m, p->stencil, nweights(p->stencil, p->hidden[0], p->hidden[1]),
                                    train_thr32(dims, g, p), kTrainModels).total;
@@ -840,7 +994,7 @@ int pc_compress_workspace_layout(const size_t dims[3], int dtype, const pc_param
   int mode, nw;
   int st = check_params(dims, dtype, p, g, mode, nw);
   if (st) return st;
-  CompLayout L = comp_layout(g, p->m);
+  CompLayout L = comp_layout(g, p->m, p->h_codebook != nullptr, dtype == PC_F64 ? 8 : 4);
   if (off_codes) *off_codes = L.codes;
   if (off_nnflag) *off_nnflag = L.nnflag;
   if (off_hist) *off_hist = L.hist;
@@ -901,10 +1055,11 @@ int pc_compress(const void* d_field, const size_t dims[3], int dtype, const pc_p
   int r = launch_head(F, s, nsm);
   if (!r) {
     const CJob job = job_of(F);
-    r = dtype == PC_F32 ? launch_compress<float>(&job, 1, mode, mlp, nsm, s)
-                        : launch_compress<double>(&job, 1, mode, mlp, nsm, s);
+    unsigned long long* next = F.sp ? F.next : nullptr;
+    r = dtype == PC_F32 ? launch_compress<float>(&job, 1, mode, mlp, nsm, s, next)
+                        : launch_compress<double>(&job, 1, mode, mlp, nsm, s, next);
   }
-  if (!r) r = launch_tail(F, mlp, s);
+  if (!r) r = launch_tail(F, mlp, s, nsm);
   if (r) return r;
   State hst;
   if (cudaMemcpyAsync(&hst, F.stp, sizeof(State), cudaMemcpyDeviceToHost, s) != cudaSuccess) return PC_ERR_CUDA;
@@ -925,7 +1080,7 @@ int pc_compress_batch_workspace_size(int nfields, const size_t* dims, const int*
     int st = check_params(dims + 3 * i, dtypes[i], params + i, g, mode, nw);
     if (st) return st;
     if (wants_training(params + i)) return PC_ERR_ARG;
-    ws += up(comp_layout(g, params[i].m).total);
+    ws += up(comp_layout(g, params[i].m, params[i].h_codebook != nullptr, dtypes[i] == PC_F64 ? 8 : 4).total);
     ob += up(pc_compress_bound(dims + 3 * i, dtypes[i], params + i));
   }
   *ws_bytes = ws;
@@ -954,7 +1109,7 @@ int pc_compress_batch(int nfields, const void* const* d_fields, const size_t* di
     Geo g;
     int mode, nw;
     check_params(dims + 3 * i, dtypes[i], params + i, g, mode, nw);
-    const size_t wsz = up(comp_layout(g, params[i].m).total);
+    const size_t wsz = up(comp_layout(g, params[i].m, params[i].h_codebook != nullptr, dtypes[i] == PC_F64 ? 8 : 4).total);
     const size_t osz = up(pc_compress_bound(dims + 3 * i, dtypes[i], params + i));
     offsets[i] = oo;
     st = plan_field(F[i], d_fields[i], dims + 3 * i, dtypes[i], params + i, g, mode, nw, out + oo, osz, ws + wo, wsz,
@@ -978,7 +1133,7 @@ int pc_compress_batch(int nfields, const void* const* d_fields, const size_t* di
            pj.block[1] == pi.block[1] && pj.block[2] == pi.block[2] &&
            (F[i].mode == 0 ||
             (pj.stencil == pi.stencil && pj.hidden[0] == pi.hidden[0] && pj.hidden[1] == pi.hidden[1])) &&
-           (F[i].mode != 1 || (pj.h_weights == pi.h_weights && pj.s_in == pi.s_in));
+           (F[i].mode != 1 || (pj.h_weights == pi.h_weights && pj.s_in == pi.s_in)) && F[j].sp == F[i].sp;
   };
   for (;;) {
     int i = 0;
@@ -990,13 +1145,14 @@ int pc_compress_batch(int nfields, const void* const* d_fields, const size_t* di
         jl.push_back(job_of(F[j]));
         done[j] = 1;
       }
-    st = dtypes[i] == PC_F32 ? launch_compress<float>(jl.data(), (int)jl.size(), F[i].mode, mlps[i], nsm, s)
-                             : launch_compress<double>(jl.data(), (int)jl.size(), F[i].mode, mlps[i], nsm, s);
+    unsigned long long* next = F[i].sp ? F[i].next : nullptr;
+    st = dtypes[i] == PC_F32 ? launch_compress<float>(jl.data(), (int)jl.size(), F[i].mode, mlps[i], nsm, s, next)
+                             : launch_compress<double>(jl.data(), (int)jl.size(), F[i].mode, mlps[i], nsm, s, next);
     if (st) return st;
   }
   // a10-a12 per field
   for (int i = 0; i < nfields; ++i)
-    if ((st = launch_tail(F[i], mlps[i], s))) return st;
+    if ((st = launch_tail(F[i], mlps[i], s, nsm))) return st;
   std::vector<State> hs((size_t)nfields);
   for (int i = 0; i < nfields; ++i)
     if (cudaMemcpyAsync(&hs[i], F[i].stp, sizeof(State), cudaMemcpyDeviceToHost, s) != cudaSuccess)

@@ -621,6 +621,54 @@ int launch_codebook(const unsigned long long* hist, int m, uint8_t* lens, uint32
   return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
 
+// Code table of a given codebook list (the sample codebook of the training
+// phase, already copied into the container's codebook section, checked on the
+// host: lengths 1..24 never decreasing, distinct symbols, Kraft sum <= 1).
+// One CTA: clear the table, count the entries per length, then each entry i
+// of length l gets the canonical code first[l] + (i - offs[l]).
+__global__ void __launch_bounds__(1024) k_cb_table(const uint8_t* __restrict__ out, unsigned long long off_cb, int n,
+                                                   int m, uint32_t* cwl, State* st, unsigned long long nblocks,
+                                                   unsigned long long cap) {
+  __shared__ unsigned int s_cnt[32], s_first[32], s_offs[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid < 32) s_cnt[tid] = 0u;
+  for (int i = tid; i < (1 << m); i += nt) cwl[i] = 0u;
+  __syncthreads();
+  const unsigned int* list = reinterpret_cast<const unsigned int*>(out + off_cb);
+  for (int i = tid; i < n; i += nt) atomicAdd(&s_cnt[(list[i] >> 16) & 31u], 1u);
+  __syncthreads();
+  if (tid == 0) {
+    unsigned int code = 0, off = 0;
+    for (int l = 1; l <= kLmax; ++l) {
+      const unsigned int prevc = l > 1 ? s_cnt[l - 1] : 0u;
+      code = (code + prevc) << 1;
+      off += prevc;
+      s_first[l] = code;
+      s_offs[l] = off;
+    }
+    const unsigned long long off_bb = al16(off_cb + 4ull * (unsigned long long)n);
+    const unsigned long long off_bn = al16(off_bb + 4ull * nblocks);
+    st->n_used = (unsigned int)n;
+    st->off_cb = off_cb;
+    st->off_bb = off_bb;
+    st->off_bn = off_bn;
+    if (off_bn + 2ull * nblocks > cap) st->err = PC_ERR_CAPACITY;
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += nt) {
+    const unsigned int e = list[i];
+    const unsigned int sym = e & 0xFFFFu, l = e >> 16;
+    cwl[sym] = (s_first[l] + ((unsigned int)i - s_offs[l])) | (l << 24);
+  }
+}
+
+int launch_cb_table(const uint8_t* out, unsigned long long off_cb, int n, int m, uint32_t* cwl, State* st,
+                    const Geo& g, unsigned long long cap, cudaStream_t s) {
+  ProfScope p(kStCodebook, s);
+  k_cb_table<<<1, 1024, 0, s>>>(out, off_cb, n, m, cwl, st, (unsigned long long)g.nblocks, cap);
+  return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
+}
+
 int launch_huff_list(const unsigned long long* hist, int m, State* st, const HuffScratch& hs, uint8_t* list,
                      unsigned long long cap, cudaStream_t s) {
   const size_t smem = kCbSmem;

@@ -203,6 +203,95 @@ __global__ void k_consts(State* st, double eb, Tabs* tabs) {
 // ---------------------------------------------------------------------------
 constexpr int kHistWin = 2048;
 
+// Exclusive scan of two counters over the TS threads of a team (TS = 32 or a
+// multiple of 32 that divides 256); ta, tb receive the team totals.  For
+// TS > 32 it synchronizes the CTA (all teams call it together).
+template <int TS>
+__device__ __forceinline__ void team_exscan2(unsigned int a, unsigned int b, unsigned int& pa, unsigned int& pb,
+                                             unsigned int& ta, unsigned int& tb, unsigned int* s_scr) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned int xa = a, xb = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned int ya = __shfl_up_sync(0xFFFFFFFFu, xa, o);
+    const unsigned int yb = __shfl_up_sync(0xFFFFFFFFu, xb, o);
+    if (lane >= o) { xa += ya; xb += yb; }
+  }
+  if constexpr (TS == 32) {
+    pa = xa - a;
+    pb = xb - b;
+    ta = __shfl_sync(0xFFFFFFFFu, xa, 31);
+    tb = __shfl_sync(0xFFFFFFFFu, xb, 31);
+  } else {
+    constexpr int NW = TS / 32;
+    if (lane == 31) { s_scr[w] = xa; s_scr[8 + w] = xb; }
+    __syncthreads();
+    const int w0 = (w / NW) * NW;
+    unsigned int oa = 0, ob = 0, sa = 0, sb = 0;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+      const unsigned int va = s_scr[w0 + i], vb = s_scr[8 + w0 + i];
+      if (w0 + i < w) { oa += va; ob += vb; }
+      sa += va;
+      sb += vb;
+    }
+    pa = oa + xa - a;
+    pb = ob + xb - b;
+    ta = sa;
+    tb = sb;
+    __syncthreads();
+  }
+}
+
+// Decoupled look-back over the bricks of a field (one warp): publish this
+// brick's aggregate, add up the aggregates of the bricks before it back to
+// the nearest published inclusive prefix, publish this brick's inclusive
+// prefix and return its exclusive one.  Records are flag << 62 | value with
+// flag 1 = aggregate, 2 = inclusive prefix (0: not yet written).  Bricks are
+// handed out in order to running CTAs and a brick publishes its aggregate
+// before it waits, so every wait ends; it is still bounded, and a wait that
+// runs out sets PC_ERR_TIMEOUT and takes the sum so far.
+constexpr unsigned int kLookbackPolls = 1u << 21;
+__device__ __forceinline__ unsigned long long lookback(unsigned long long* rec, long long k, unsigned long long agg,
+                                                       int lane, int* errw) {
+  constexpr unsigned long long kA = 1ull << 62, kP = 2ull << 62, kV = (1ull << 62) - 1;
+  volatile unsigned long long* vr = rec;
+  if (k == 0) {
+    if (lane == 0) vr[0] = kP | agg;
+    return 0ull;
+  }
+  if (lane == 0) vr[k] = kA | agg;
+  unsigned long long excl = 0;
+  long long base = k - 1;
+  unsigned int polls = 0;
+  while (true) {
+    const long long idx = base - lane;
+    const unsigned long long r = idx >= 0 ? vr[idx] : kP;  // before the first brick: prefix 0
+    const unsigned int flag = (unsigned int)(r >> 62);
+    const unsigned int pm = __ballot_sync(0xFFFFFFFFu, flag == 2u);
+    const unsigned int zm = __ballot_sync(0xFFFFFFFFu, flag == 0u);
+    const int lp = pm ? __ffs(pm) - 1 : 31;
+    const unsigned int need = lp == 31 ? 0xFFFFFFFFu : ((2u << lp) - 1u);
+    if (zm & need) {
+      // a wait that ran out here or in another brick ends this one too
+      if (++polls > kLookbackPolls || *reinterpret_cast<volatile int*>(errw) != 0) {
+        if (lane == 0) atomicCAS(errw, 0, PC_ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(64);
+      continue;
+    }
+    unsigned long long v = lane <= lp ? (r & kV) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    excl += v;
+    if (pm) break;
+    base -= 32;
+  }
+  if (lane == 0) vr[k] = kP | (excl + agg);
+  return excl;
+}
+
 // Shared memory of k_compress (16-byte aligned regions): tables, codes with
 // bound flags, padded centred inputs, Lorenzo codes (in the fixed-point form
 // this region first holds the tensor-core A tiles of the two warpgroups),
@@ -306,7 +395,21 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const __grid_con
   const int team = tid / TS, t = tid % TS;
   int* dq = s_dq + team * BV;
   int* vp = s_vp + team * PD::PV;
-  for (long long gbk = blockIdx.x; gbk < jobs.total; gbk += gridDim.x) {
+  // single pass: bricks in order from the launch's counter; per-block bit and
+  // balance counts, look-back results and team-scan scratch
+  const bool sp = jobs.next != nullptr;
+  __shared__ long long s_gbk;
+  __shared__ unsigned int s_bbits[G], s_bout[G], s_scr[16];
+  __shared__ unsigned long long s_pre[2];
+  auto next_brick = [&](long long cur) -> long long {
+    if (!sp) return cur + gridDim.x;
+    __syncthreads();  // every thread has read the previous index
+    if (tid == 0) s_gbk = (long long)atomicAdd(jobs.next, 1ull);
+    __syncthreads();
+    return s_gbk;
+  };
+  const long long gbk_first = sp ? next_brick(-1) : (long long)blockIdx.x;
+  for (long long gbk = gbk_first; gbk < jobs.total; gbk = next_brick(gbk)) {
     int jn = jcur < 0 ? 0 : jcur;
     while (jn + 1 < jobs.n && gbk >= jobs.j[jn + 1].brick0) ++jn;
     if (jn != jcur) {
@@ -574,10 +677,12 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const __grid_con
             cn += bitlen_u((unsigned int)(an < R ? an : R));
             coden = (an <= R - 1 && okp) ? (uint16_t)(kn + R) : 0;
           } else if constexpr (MODE == 0) {
-            nz += codez == 0;
-            const int hi = (int)codez - hbase;
-            if (hi >= 0 && hi < kHistWin) atomicAdd(&s_hist[hi], 1u);
-            else atomicAdd(&hist[codez], 1ull);
+            if (!sp) {
+              nz += codez == 0;
+              const int hi = (int)codez - hbase;
+              if (hi >= 0 && hi < kHistWin) atomicAdd(&s_hist[hi], 1u);
+              else atomicAdd(&hist[codez], 1ull);
+            }
           }
         }
         s_cz[team * BV + j] = codez;
@@ -595,6 +700,121 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const __grid_con
       tnz = s_nz[team];
     }
     if constexpr (MODE == 2) tcn = s_cost[team][1];
+    if (sp) {
+      // a7 select and a8-a12 in one pass: codes outside the codebook become
+      // balance points; each block's bits and balance points are counted,
+      // the brick's stream and balance offsets come from a look-back over
+      // the bricks before it, and the brick's code words are packed on chip
+      // and written with its block-table entries and balance values.
+      const bool usen = MODE != 0 && tcn < tcz;
+      uint16_t* srcw = (usen ? s_cn : s_cz) + team * BV;
+      constexpr int CPT = BV / TS;
+      const uint32_t* cwl = s_job.cwl;
+      const unsigned int cw0 = __ldg(cwl);  // symbol 0: always in the codebook
+      unsigned int nbits = 0, nzero = 0;
+      if (bvalid) {
+#pragma unroll 4
+        for (int i = 0; i < CPT; ++i) {
+          const int j = t * CPT + i;
+          const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+          const bool valid = (bfull || (lz < e0 && ly < e1 && lx < e2)) && j != 0;
+          if (valid) {
+            unsigned int cd = srcw[j];
+            unsigned int e = __ldg(cwl + cd);
+            if ((e >> 24) == 0u) {
+              cd = 0u;
+              e = cw0;
+              srcw[j] = 0;
+            }
+            nbits += e >> 24;
+            nzero += cd == 0u;
+          }
+        }
+      }
+      unsigned int pb, po, tbits, tzero;
+      team_exscan2<TS>(nbits, nzero, pb, po, tbits, tzero, s_scr);
+      if (t == 0) {
+        s_bbits[team] = bvalid ? tbits : 0u;
+        s_bout[team] = bvalid ? 1u + tzero : 0u;
+      }
+      __syncthreads();
+      if (bvalid && t == 0) {
+        st_u32(s_job.out + s_job.off_bb + 4ull * b, tbits | (usen ? 0x80000000u : 0u));
+        *reinterpret_cast<uint16_t*>(s_job.out + s_job.off_bn + 2ull * b) = (uint16_t)(1u + tzero);
+      }
+      if (tid < 64) {
+        // warp 0: stream bits, warp 1: balance points
+        const int w = tid >> 5, lane = tid & 31;
+        unsigned long long agg = 0;
+#pragma unroll
+        for (int q = 0; q < G; ++q) agg += w ? s_bout[q] : s_bbits[q];
+        const unsigned long long ex = lookback(s_job.rec + (w ? s_job.nbk : 0), brick, agg, lane, errw);
+        if (lane == 0) s_pre[w] = ex;
+      }
+      __syncthreads();
+      const unsigned long long S = s_pre[0], O = s_pre[1];
+      unsigned int bo = 0, oo = 0, btot = 0;
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        if (q < team) { bo += s_bbits[q]; oo += s_bout[q]; }
+        btot += s_bbits[q];
+      }
+      const unsigned int sh = (unsigned int)(S & 31ull);
+      const int nwords = (int)((sh + btot + 31u) >> 5);
+      unsigned int* buf = reinterpret_cast<unsigned int*>(s_dq);  // the brick's words (codes are done)
+      for (int i = tid; i < nwords; i += 256) buf[i] = 0u;
+      __syncthreads();
+      if (bvalid) {
+        T* ov = static_cast<T*>(s_job.ov);
+        const T* org = base + team * B2;  // the block's first point
+        unsigned long long o = O + oo;
+        if (t == 0) ov[o] = org[0];       // the anchor, first of the block's balance values
+        o += 1ull + po;
+        unsigned int p = sh + bo + pb;
+#pragma unroll 4
+        for (int i = 0; i < CPT; ++i) {
+          const int j = t * CPT + i;
+          const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+          const bool valid = (bfull || (lz < e0 && ly < e1 && lx < e2)) && j != 0;
+          if (valid) {
+            const unsigned int cd = srcw[j];
+            const unsigned int e = __ldg(cwl + cd);
+            const unsigned int L = e >> 24, wv = e & 0xFFFFFFu;
+            const unsigned int wi = p >> 5, bb2 = p & 31u;
+            if (bb2 + L <= 32u) {
+              atomicOr(&buf[wi], wv << (32u - bb2 - L));
+            } else {
+              atomicOr(&buf[wi], wv >> (bb2 + L - 32u));
+              atomicOr(&buf[wi + 1], wv << (64u - bb2 - L));
+            }
+            p += L;
+            if (cd == 0u) ov[o++] = org[lz * n12 + ly * g.n[2] + lx];
+          }
+        }
+      }
+      __syncthreads();
+      if (btot) {
+        // whole words go straight out; a word shared with a neighbouring
+        // brick is kept aside and assembled once every brick is done
+        uint32_t* stream = reinterpret_cast<uint32_t*>(s_job.out + s_job.off_st);
+        const unsigned long long W0 = S >> 5;
+        const bool head_part = sh != 0u, tail_part = ((sh + btot) & 31u) != 0u;
+        if (W0 + (unsigned long long)nwords > s_job.cap_words) {
+          if (tid == 0) atomicExch(errw, PC_ERR_CAPACITY);
+        } else {
+          for (int i = tid; i < nwords; i += 256) {
+            const bool part = (i == 0 && head_part) || (i == nwords - 1 && tail_part);
+            if (!part) stream[W0 + i] = buf[i];
+          }
+        }
+        if (tid == 0) {
+          s_job.side[2 * brick] = buf[0];
+          s_job.side[2 * brick + 1] = buf[nwords - 1];
+        }
+      }
+      __syncthreads();
+      continue;
+    }
     // a7 select, a8 emit, a9 histogram of the chosen codes
     if (bvalid) {
       const bool usen = MODE != 0 && tcn < tcz;
@@ -703,18 +923,19 @@ static int launch_c_shape(const CJobs& jobs, int mode, const Mlp& mlp, int nsm, 
 }
 
 template <typename T>
-int launch_compress(const CJob* jl, int n, int mode, const Mlp& mlp, int nsm, cudaStream_t s) {
+int launch_compress(const CJob* jl, int n, int mode, const Mlp& mlp, int nsm, cudaStream_t s,
+                    unsigned long long* next) {
   if (n < 1 || n > kMaxJobs) return PC_ERR_ARG;
   static thread_local CJobs jobs;
   jobs.n = n;
   jobs.total = 0;
+  jobs.next = next;
   const Geo& g = jl[0].g;
   for (int i = 0; i < n; ++i) {
     if (jl[i].g.b[0] != g.b[0] || jl[i].g.b[1] != g.b[1] || jl[i].g.b[2] != g.b[2]) return PC_ERR_ARG;
     jobs.j[i] = jl[i];
     jobs.j[i].brick0 = jobs.total;
-    const int G = jl[i].g.bvol <= 512 ? 8 : (jl[i].g.bvol <= 1024 ? 4 : (jl[i].g.bvol <= 2048 ? 2 : 1));
-    jobs.total += jl[i].g.nb[0] * jl[i].g.nb[1] * ((jl[i].g.nb[2] + G - 1) / G);
+    jobs.total += bricks_of(jl[i].g);
   }
   const int b0 = g.b[0], b1 = g.b[1], b2 = g.b[2];
 #define PC_SHAPE(A, B, C) \
@@ -728,7 +949,7 @@ int launch_compress(const CJob* jl, int n, int mode, const Mlp& mlp, int nsm, cu
 #undef PC_SHAPE
   return PC_ERR_ARG;
 }
-template int launch_compress<float>(const CJob*, int, int, const Mlp&, int, cudaStream_t);
-template int launch_compress<double>(const CJob*, int, int, const Mlp&, int, cudaStream_t);
+template int launch_compress<float>(const CJob*, int, int, const Mlp&, int, cudaStream_t, unsigned long long*);
+template int launch_compress<double>(const CJob*, int, int, const Mlp&, int, cudaStream_t, unsigned long long*);
 
 }  // namespace pc

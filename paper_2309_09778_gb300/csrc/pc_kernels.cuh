@@ -56,6 +56,7 @@ __device__ __forceinline__ int team_sum(int v, int* slot) {
 struct HdrInfo {
   int dtype, pred, stencil, h1, h2, m, s_in, nw;
   int wsz;                    // bytes per weights-section entry: 4 (f32 weights) or 8 (int64 fixed-point network)
+  unsigned int flags;         // header flags (kFlagStreamFirst)
   double eb;
   unsigned long long off_cb;  // = al16(256 + wsz nw)
   unsigned long long cap;     // output capacity in bytes
@@ -112,6 +113,16 @@ __host__ __device__ inline unsigned long long al16(unsigned long long x) { retur
 template <typename T>
 int launch_stats_consts(const void* x, unsigned long long n, State* st, Tabs* tabs, unsigned long long* hist,
                         int nsym, double eb, int nsm, cudaStream_t s);
+// Container flag (header offset 228): the bitstream precedes the balance
+// values, the layout that single-pass compression writes.
+constexpr unsigned int kFlagStreamFirst = 1u;
+
+// Bricks of a field: G blocks along x per brick (BrickShape), rows of bricks.
+inline long long bricks_of(const Geo& g) {
+  const int G = g.bvol <= 512 ? 8 : (g.bvol <= 1024 ? 4 : (g.bvol <= 2048 ? 2 : 1));
+  return g.nb[0] * g.nb[1] * ((g.nb[2] + G - 1) / G);
+}
+
 // One field of a fused compression launch: its input, geometry, per-call
 // state (constants, tables, histogram) and outputs.  brick0 is the field's
 // first brick in the launch's brick numbering (fields in order).
@@ -128,19 +139,53 @@ struct CJob {
   long long brick0;
   int m;
   int pad_;
+  // single pass (a given codebook): the container, the code table, the
+  // look-back records, each brick's first and last stream word, and the
+  // balance values in container order (workspace)
+  uint8_t* out;
+  const uint32_t* cwl;       // [2^m] (length << 24) | code word; 0 for symbols outside the codebook
+  unsigned long long* rec;   // [2 nbk]: bit counts, then balance-point counts (flag << 62 | value)
+  uint32_t* side;            // [2 nbk]
+  void* ov;                  // [points] balance values
+  unsigned long long off_bb, off_bn, off_st;
+  unsigned long long cap_words;  // stream words that fit the output
+  long long nbk;             // bricks of the field
 };
 constexpr int kMaxJobs = 32;  // fields per fused launch (the table travels as a kernel parameter)
 struct CJobs {
   int n;
   int pad_;
   long long total;  // bricks of all fields
+  // single pass: bricks are taken in order from this counter (zeroed before
+  // the launch), so that every brick a look-back waits for belongs to a
+  // running CTA; null: static assignment, no look-back
+  unsigned long long* next;
   CJob j[kMaxJobs];
 };
 
 // Compression of n fields that share dtype, block shape and predictor form
-// (and, for the FP32 perceptron, the weights mlp) in one persistent launch.
+// (and, for the FP32 perceptron, the weights mlp) in one persistent launch;
+// with `next`, single-pass packing against each job's codebook.
 template <typename T>
-int launch_compress(const CJob* jobs, int n, int mode, const Mlp& mlp, int nsm, cudaStream_t s);
+int launch_compress(const CJob* jobs, int n, int mode, const Mlp& mlp, int nsm, cudaStream_t s,
+                    unsigned long long* next = nullptr);
+// Code table of a given codebook list (already in the container at off_cb):
+// cwl[sym] = (length << 24) | canonical code word, 0 for absent symbols; sets
+// the codebook and block-table offsets in the state.
+int launch_cb_table(const uint8_t* out, unsigned long long off_cb, int n, int m, uint32_t* cwl, State* st,
+                    const Geo& g, unsigned long long cap, cudaStream_t s);
+// Finish of a single-pass compression: stream words shared by bricks, the
+// balance values moved after the stream, section pads, weights and header.
+struct SpFinish {
+  const unsigned long long* rec;
+  const uint32_t* side;
+  const void* ov;
+  long long nbk;
+  unsigned long long off_bb, off_bn, off_st;
+};
+template <typename T>
+int launch_sp_finish(const Geo& g, State* st, uint8_t* out, const HdrInfo& hi, const Mlp& mlp, const SpFinish& f,
+                     int nsm, cudaStream_t s);
 int launch_codebook(const unsigned long long* hist, int m, uint8_t* lens, uint32_t* cw, State* st,
                     const HuffScratch& hs, uint8_t* out, const Geo& g, const HdrInfo& hi, cudaStream_t s);
 template <typename T>
@@ -203,6 +248,14 @@ int launch_select(const TrainBufs& tb, const SelectBufs& sb, int k, int h1, int 
 // most frequent first) at list[0..], n_used in st (a zeroed scratch state).
 int launch_huff_list(const unsigned long long* hist, int m, State* st, const HuffScratch& hs, uint8_t* list,
                      unsigned long long cap, cudaStream_t s);
+// The sample codebook of the training phase (validation samples of seed and
+// thr32, residuals of the FP32 weights in tb.w[0] or of Lorenzo, at m code
+// bits; span_fill: every code inside the sampled span coded) as a codebook
+// list in sb.list, its length in sb.st->n_used.
+template <typename T>
+int launch_sample_hist(const T* x, const Geo& g, const State* st, const Tabs* tabs, const TrainBufs& tb,
+                       const SelectBufs& sb, int k, int h1, int h2, int s_in, int m, bool lorenzo, int span_fill,
+                       unsigned long long seed, unsigned int thr32, cudaStream_t s);
 template <typename T>
 int launch_train(const T* x, const Geo& g, const State* st, const Tabs* tabs, const TrainBufs& tb, int k, int h1,
                  int h2, int m, int nmodels, unsigned long long seed, unsigned int thr32, cudaStream_t s);

@@ -88,6 +88,77 @@ __global__ void __launch_bounds__(256) k_blockbits(Geo g, const uint16_t* __rest
 }
 
 
+// The 256-byte header, assembled in shared memory (s_hdr) by the whole CTA
+// and checksummed there (CRC-32, reflected 0xEDB88320, table in s_crc);
+// the caller copies it out.  Contains __syncthreads.
+template <typename T>
+__device__ void write_header(uint8_t* s_hdr, unsigned int* s_crc, const State& c, const Geo& g, const HdrInfo& hi,
+                             unsigned long long to, unsigned long long swords, unsigned long long off_bb,
+                             unsigned long long off_bn, unsigned long long off_ov, unsigned long long off_st,
+                             unsigned long long total) {
+  const int tid = threadIdx.x;
+  if (tid < 256) {
+    unsigned int cr = (unsigned int)tid;
+    for (int k = 0; k < 8; ++k) cr = (cr >> 1) ^ (0xEDB88320u & (0u - (cr & 1u)));
+    s_crc[tid] = cr;
+  }
+  if (tid < 64) st_u32(s_hdr + 4 * tid, 0u);
+  __syncthreads();
+  if (tid == 0) {
+    uint8_t* const hd = s_hdr;
+    const bool nn = hi.pred != 0;
+    st_u32(hd + 0, 0x504D4350u);  // "PCMP"
+    st_u32(hd + 4, 1u);
+    st_u32(hd + 8, (unsigned int)hi.dtype);
+    st_u32(hd + 12, (unsigned int)hi.pred);
+    st_u64(hd + 16, (unsigned long long)g.n[0]);
+    st_u64(hd + 24, (unsigned long long)g.n[1]);
+    st_u64(hd + 32, (unsigned long long)g.n[2]);
+    st_u32(hd + 40, (unsigned int)g.b[0]);
+    st_u32(hd + 44, (unsigned int)g.b[1]);
+    st_u32(hd + 48, (unsigned int)g.b[2]);
+    st_u32(hd + 52, nn ? (unsigned int)hi.stencil : 0u);
+    st_u32(hd + 56, nn ? (unsigned int)hi.h1 : 0u);
+    st_u32(hd + 60, nn ? (unsigned int)hi.h2 : 0u);
+    st_u32(hd + 64, (unsigned int)hi.m);
+    st_u32(hd + 68, nn ? (unsigned int)hi.s_in : 0u);
+    st_u64(hd + 72, (unsigned long long)__double_as_longlong(hi.eb));
+    st_u64(hd + 80, (unsigned long long)__double_as_longlong(c.amin));
+    st_u64(hd + 88, (unsigned long long)__double_as_longlong(c.amax));
+    st_u32(hd + 96, (unsigned int)c.trivial);
+    st_u32(hd + 100, (unsigned int)c.Kp);
+    st_u32(hd + 104, (unsigned int)c.Kn);
+    st_u32(hd + 108, (unsigned int)c.Zq);
+    st_u32(hd + 112, (unsigned int)c.S);
+    st_u32(hd + 116, c.n_used);
+    if (sizeof(T) == 4) {
+      st_u64(hd + 120, __float_as_uint(c.step32));
+      st_u64(hd + 128, __float_as_uint(c.inv32));
+      st_u64(hd + 136, __float_as_uint(c.ebdn32));
+    } else {
+      st_u64(hd + 120, (unsigned long long)__double_as_longlong(c.stepd));
+      st_u64(hd + 128, (unsigned long long)__double_as_longlong(c.invd));
+      st_u64(hd + 136, (unsigned long long)__double_as_longlong(c.ebdnd));
+    }
+    st_u64(hd + 144, (unsigned long long)g.nblocks);
+    st_u64(hd + 152, to);
+    st_u64(hd + 160, swords);
+    st_u64(hd + 168, (unsigned long long)kHdr);
+    st_u64(hd + 176, hi.off_cb);
+    st_u64(hd + 184, off_bb);
+    st_u64(hd + 192, off_bn);
+    st_u64(hd + 200, off_ov);
+    st_u64(hd + 208, off_st);
+    st_u64(hd + 216, total);
+    st_u32(hd + 224, (unsigned int)hi.nw);
+    st_u32(hd + 228, hi.flags);
+    unsigned int crc = 0xFFFFFFFFu;
+    for (int i = 0; i < 252; ++i) crc = s_crc[(crc ^ hd[i]) & 0xFFu] ^ (crc >> 8);
+    st_u32(hd + 252, crc ^ 0xFFFFFFFFu);
+  }
+  __syncthreads();
+}
+
 template <typename T>
 __global__ void __launch_bounds__(1024) k_chunkscan(Geo g, const unsigned long long* __restrict__ chunk_bits,
                                                     const unsigned long long* __restrict__ chunk_nout,
@@ -152,70 +223,95 @@ __global__ void __launch_bounds__(1024) k_chunkscan(Geo g, const unsigned long l
     for (int i = tid; i < hi.nw; i += nt) st_u32(out + kHdr + 4ull * i, __float_as_uint(mlp.w[i]));
   for (unsigned long long i = kHdr + (unsigned long long)hi.wsz * hi.nw + tid; i < hi.off_cb; i += nt) out[i] = 0;
   // header
-  if (tid < 256) {
-    unsigned int cr = (unsigned int)tid;
-    for (int k = 0; k < 8; ++k) cr = (cr >> 1) ^ (0xEDB88320u & (0u - (cr & 1u)));
-    s_crc[tid] = cr;
-  }
-  // assembled in shared memory, checksummed there, then copied out
   __shared__ __align__(16) uint8_t s_hdr[256];
-  if (tid < 64) st_u32(s_hdr + 4 * tid, 0u);
-  __syncthreads();
-  if (tid == 0) {
-    uint8_t* const hd = s_hdr;
-    const State& c = *st;
-    const bool nn = hi.pred != 0;
-    st_u32(hd + 0, 0x504D4350u);  // "PCMP"
-    st_u32(hd + 4, 1u);
-    st_u32(hd + 8, (unsigned int)hi.dtype);
-    st_u32(hd + 12, (unsigned int)hi.pred);
-    st_u64(hd + 16, (unsigned long long)g.n[0]);
-    st_u64(hd + 24, (unsigned long long)g.n[1]);
-    st_u64(hd + 32, (unsigned long long)g.n[2]);
-    st_u32(hd + 40, (unsigned int)g.b[0]);
-    st_u32(hd + 44, (unsigned int)g.b[1]);
-    st_u32(hd + 48, (unsigned int)g.b[2]);
-    st_u32(hd + 52, nn ? (unsigned int)hi.stencil : 0u);
-    st_u32(hd + 56, nn ? (unsigned int)hi.h1 : 0u);
-    st_u32(hd + 60, nn ? (unsigned int)hi.h2 : 0u);
-    st_u32(hd + 64, (unsigned int)hi.m);
-    st_u32(hd + 68, nn ? (unsigned int)hi.s_in : 0u);
-    st_u64(hd + 72, (unsigned long long)__double_as_longlong(hi.eb));
-    st_u64(hd + 80, (unsigned long long)__double_as_longlong(c.amin));
-    st_u64(hd + 88, (unsigned long long)__double_as_longlong(c.amax));
-    st_u32(hd + 96, (unsigned int)c.trivial);
-    st_u32(hd + 100, (unsigned int)c.Kp);
-    st_u32(hd + 104, (unsigned int)c.Kn);
-    st_u32(hd + 108, (unsigned int)c.Zq);
-    st_u32(hd + 112, (unsigned int)c.S);
-    st_u32(hd + 116, c.n_used);
-    if (sizeof(T) == 4) {
-      st_u64(hd + 120, __float_as_uint(c.step32));
-      st_u64(hd + 128, __float_as_uint(c.inv32));
-      st_u64(hd + 136, __float_as_uint(c.ebdn32));
-    } else {
-      st_u64(hd + 120, (unsigned long long)__double_as_longlong(c.stepd));
-      st_u64(hd + 128, (unsigned long long)__double_as_longlong(c.invd));
-      st_u64(hd + 136, (unsigned long long)__double_as_longlong(c.ebdnd));
-    }
-    st_u64(hd + 144, (unsigned long long)g.nblocks);
-    st_u64(hd + 152, to);
-    st_u64(hd + 160, swords);
-    st_u64(hd + 168, (unsigned long long)kHdr);
-    st_u64(hd + 176, hi.off_cb);
-    st_u64(hd + 184, off_bb);
-    st_u64(hd + 192, off_bn);
-    st_u64(hd + 200, off_ov);
-    st_u64(hd + 208, off_st);
-    st_u64(hd + 216, total);
-    st_u32(hd + 224, (unsigned int)hi.nw);
-    unsigned int crc = 0xFFFFFFFFu;
-    for (int i = 0; i < 252; ++i) crc = s_crc[(crc ^ hd[i]) & 0xFFu] ^ (crc >> 8);
-    st_u32(hd + 252, crc ^ 0xFFFFFFFFu);
-  }
-  __syncthreads();
+  write_header<T>(s_hdr, s_crc, *st, g, hi, to, swords, off_bb, off_bn, off_ov, off_st, total);
   if (tid < 64) st_u32(out + 4 * tid, reinterpret_cast<const unsigned int*>(s_hdr)[tid]);
 }
+
+// ---------------------------------------------------------------------------
+// Finish of a single-pass compression (the sample codebook of the training
+// phase, Section IV.C).  The last brick's inclusive prefixes give the stream
+// bits and balance points; the stream ends the fixed sections and the balance
+// values follow it.  Each stream word that several bricks share is assembled
+// by the brick holding its first bit, from the edge words the bricks kept
+// aside; the balance values move from the workspace to their section; CTA 0
+// writes the pads, the weights and the header.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_sp_finish(Geo g, State* st, uint8_t* out, HdrInfo hi,
+                                                   const __grid_constant__ Mlp mlp, SpFinish f) {
+  __shared__ unsigned int s_crc[256];
+  __shared__ __align__(16) uint8_t s_hdr[256];
+  if (st->err) return;
+  constexpr unsigned long long kV = (1ull << 62) - 1;
+  const unsigned long long* rb = f.rec;
+  const unsigned long long* ro = f.rec + f.nbk;
+  const unsigned long long tb = rb[f.nbk - 1] & kV, to = ro[f.nbk - 1] & kV;
+  const unsigned long long ts = sizeof(T);
+  const unsigned long long swords = (tb + 31) / 32;
+  const unsigned long long off_st = f.off_st;
+  const unsigned long long off_ov = al16(off_st + 4ull * swords);
+  const unsigned long long total = al16(off_ov + ts * to);
+  const int tid = threadIdx.x;
+  if (total > hi.cap) {
+    if (blockIdx.x == 0 && tid == 0) st->err = PC_ERR_CAPACITY;
+    return;
+  }
+  const unsigned long long gt = (unsigned long long)blockIdx.x * blockDim.x + tid;
+  const unsigned long long gs = (unsigned long long)gridDim.x * blockDim.x;
+  uint32_t* stream = reinterpret_cast<uint32_t*>(out + off_st);
+  for (unsigned long long k = gt; k < (unsigned long long)f.nbk; k += gs) {
+    const unsigned long long sk = k ? (rb[k - 1] & kV) : 0ull;
+    const unsigned long long ek = rb[k] & kV;
+    if (ek == sk || (ek & 31ull) == 0ull) continue;  // no bits, or the last word is whole
+    const unsigned long long lw = (ek - 1) >> 5;
+    if (sk > 32ull * lw) continue;  // the word's first bit is an earlier brick's
+    unsigned int v = (sk >> 5) == lw ? f.side[2 * k] : f.side[2 * k + 1];
+    for (unsigned long long j = k + 1; j < (unsigned long long)f.nbk; ++j) {
+      const unsigned long long sj = rb[j - 1] & kV;
+      if (sj >= 32ull * (lw + 1)) break;
+      if ((rb[j] & kV) > sj) v |= f.side[2 * j];
+    }
+    stream[lw] = v;
+  }
+  const T* ovs = static_cast<const T*>(f.ov);
+  T* ovd = reinterpret_cast<T*>(out + off_ov);
+  for (unsigned long long i = gt; i < to; i += gs) ovd[i] = ovs[i];
+  if (blockIdx.x != 0) return;
+  const int nt = blockDim.x;
+  if (tid == 0) {
+    st->n_out = to;
+    st->total_bits = tb;
+    st->swords = swords;
+    st->off_ov = off_ov;
+    st->off_st = off_st;
+    st->total = total;
+    st->out_size = total;
+  }
+  const unsigned long long off_bb = f.off_bb, off_bn = f.off_bn;
+  for (unsigned long long i = hi.off_cb + 4ull * st->n_used + tid; i < off_bb; i += nt) out[i] = 0;
+  for (unsigned long long i = off_bb + 4ull * g.nblocks + tid; i < off_bn; i += nt) out[i] = 0;
+  for (unsigned long long i = off_bn + 2ull * g.nblocks + tid; i < off_st; i += nt) out[i] = 0;
+  for (unsigned long long i = off_st + 4ull * swords + tid; i < off_ov; i += nt) out[i] = 0;
+  for (unsigned long long i = off_ov + ts * to + tid; i < total; i += nt) out[i] = 0;
+  if (hi.pred == 1)
+    for (int i = tid; i < hi.nw; i += nt) st_u32(out + kHdr + 4ull * i, __float_as_uint(mlp.w[i]));
+  for (unsigned long long i = kHdr + (unsigned long long)hi.wsz * hi.nw + tid; i < hi.off_cb; i += nt) out[i] = 0;
+  write_header<T>(s_hdr, s_crc, *st, g, hi, to, swords, off_bb, off_bn, off_ov, off_st, total);
+  if (tid < 64) st_u32(out + 4 * tid, reinterpret_cast<const unsigned int*>(s_hdr)[tid]);
+}
+
+template <typename T>
+int launch_sp_finish(const Geo& g, State* st, uint8_t* out, const HdrInfo& hi, const Mlp& mlp, const SpFinish& f,
+                     int nsm, cudaStream_t s) {
+  ProfScope p(kStPack, s);
+  k_sp_finish<T><<<(unsigned int)nsm, 256, 0, s>>>(g, st, out, hi, mlp, f);
+  return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
+}
+template int launch_sp_finish<float>(const Geo&, State*, uint8_t*, const HdrInfo&, const Mlp&, const SpFinish&, int,
+                                     cudaStream_t);
+template int launch_sp_finish<double>(const Geo&, State*, uint8_t*, const HdrInfo&, const Mlp&, const SpFinish&, int,
+                                      cudaStream_t);
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_pack(Geo g, const T* __restrict__ x, const uint16_t* __restrict__ codes,

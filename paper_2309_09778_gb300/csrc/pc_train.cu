@@ -523,6 +523,88 @@ int launch_select(const TrainBufs& tb, const SelectBufs& sb, int k, int h1, int 
   return PC_ERR_ARG;
 }
 
+// ---------------------------------------------------------------------------
+// Sample codebook (Section IV.C): the validation samples of the training
+// phase (seed, thr32), their residuals under the given FP32 weights (model 0)
+// or Lorenzo quantized into a histogram at m code bits, symbol 0 counted at
+// least once, and its Huffman code as a codebook list in sb.list (n_used in
+// sb.st).
+// ---------------------------------------------------------------------------
+__global__ void k_set_sin(TrainCtl* ctl, int s_in) { ctl->s_in = s_in; }
+// Symbol 0 counts at least once; with span_fill every code between the
+// smallest and the largest sampled code (symbols >= 1) counts at least once.
+__global__ void __launch_bounds__(1024) k_sample_fill(unsigned long long* hist, int nsym, int span_fill) {
+  __shared__ int s_lo, s_hi;
+  if (threadIdx.x == 0) {
+    s_lo = nsym;
+    s_hi = 0;
+  }
+  __syncthreads();
+  if (span_fill) {
+    int lo = nsym, hi = 0;
+    for (int c = 1 + threadIdx.x; c < nsym; c += blockDim.x)
+      if (hist[c]) {
+        lo = min(lo, c);
+        hi = max(hi, c);
+      }
+    atomicMin(&s_lo, lo);
+    atomicMax(&s_hi, hi);
+    __syncthreads();
+    for (int c = s_lo + threadIdx.x; c <= s_hi; c += blockDim.x)
+      if (hist[c] == 0ull) hist[c] = 1ull;
+  }
+  if (threadIdx.x == 0 && hist[0] == 0ull) hist[0] = 1ull;
+}
+
+template <int K, int H1, int H2>
+static int launch_sample_hist_k(const TrainBufs& tb, const SelectBufs& sb, int m, bool lorenzo, int span_fill,
+                                cudaStream_t s) {
+  const size_t nsym = (size_t)1 << m;
+  if (cudaMemsetAsync(sb.hists, 0, 8 * nsym * 2, s) != cudaSuccess ||
+      cudaMemsetAsync(sb.bitcnt, 0, 8 * 34 * 2, s) != cudaSuccess)
+    return PC_ERR_CUDA;
+  dim3 gv(152, 2);
+  k_valhist<K, H1, H2><<<gv, 256, 0, s>>>(tb.vin, tb.vtg, tb.vus, tb.w, 1, m,
+                                          reinterpret_cast<const TrainCtl*>(tb.ctl), sb.hists, sb.bitcnt);
+  unsigned long long* h = sb.hists + (lorenzo ? nsym : 0);
+  k_sample_fill<<<1, 1024, 0, s>>>(h, (int)nsym, span_fill);
+  if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
+  if (cudaMemsetAsync(sb.st, 0, sizeof(State), s) != cudaSuccess) return PC_ERR_CUDA;
+  return launch_huff_list(h, m, sb.st, sb.hs, sb.list, 4 * nsym + 64, s);
+}
+
+template <typename T>
+int launch_sample_hist(const T* x, const Geo& g, const State* st, const Tabs* tabs, const TrainBufs& tb,
+                       const SelectBufs& sb, int k, int h1, int h2, int s_in, int m, bool lorenzo, int span_fill,
+                       unsigned long long seed, unsigned int thr32, cudaStream_t s) {
+  TrainCtl* ctl = reinterpret_cast<TrainCtl*>(tb.ctl);
+  if (cudaMemsetAsync(ctl, 0, sizeof(TrainCtl), s) != cudaSuccess) return PC_ERR_CUDA;
+  const unsigned int nb8 = (unsigned int)((g.nblocks + 7) / 8);
+  k_samp_count<<<nb8, 256, 0, s>>>(g, seed, thr32, tb.cnt_t, tb.cnt_v);
+  k_samp_scan<<<1, 1024, 0, s>>>(g.nblocks, tb.cnt_t, tb.cnt_v, tb.off_t, tb.off_v, ctl);
+  const size_t gsm = sizeof(Tabs) + 4ull * g.bvol * 4;
+  if (cudaFuncSetAttribute(k_samp_gather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm) != cudaSuccess)
+    return PC_ERR_CUDA;
+  k_samp_gather<T><<<(unsigned int)((g.nblocks + 3) / 4), 128, gsm, s>>>(
+      x, g, st, tabs, seed, thr32, k, tb.off_t, tb.off_v, tb.tin, tb.ttg, tb.tus, tb.vin, tb.vtg, tb.vus, ctl,
+      tb.cap_t, tb.cap_v);
+  k_set_sin<<<1, 1, 0, s>>>(ctl, s_in);
+  if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
+  if (lorenzo) return launch_sample_hist_k<7, 16, 16>(tb, sb, m, true, span_fill, s);
+  if (k == 7 && h1 == 16 && h2 == 16) return launch_sample_hist_k<7, 16, 16>(tb, sb, m, false, span_fill, s);
+  if (k == 13 && h1 == 32 && h2 == 32) return launch_sample_hist_k<13, 32, 32>(tb, sb, m, false, span_fill, s);
+  if (k == 7 && h1 == 8 && h2 == 8) return launch_sample_hist_k<7, 8, 8>(tb, sb, m, false, span_fill, s);
+  if (k == 7 && h1 == 2 && h2 == 0) return launch_sample_hist_k<7, 2, 0>(tb, sb, m, false, span_fill, s);
+  if (k == 13 && h1 == 16 && h2 == 16) return launch_sample_hist_k<13, 16, 16>(tb, sb, m, false, span_fill, s);
+  return PC_ERR_ARG;
+}
+template int launch_sample_hist<float>(const float*, const Geo&, const State*, const Tabs*, const TrainBufs&,
+                                       const SelectBufs&, int, int, int, int, int, bool, int, unsigned long long,
+                                       unsigned int, cudaStream_t);
+template int launch_sample_hist<double>(const double*, const Geo&, const State*, const Tabs*, const TrainBufs&,
+                                        const SelectBufs&, int, int, int, int, int, bool, int, unsigned long long,
+                                        unsigned int, cudaStream_t);
+
 size_t train_ctl_bytes() { return sizeof(TrainCtl); }
 
 template <typename T>

@@ -52,7 +52,7 @@ class pc_params(C.Structure):
     _fields_ = [("eb_rel", C.c_double), ("block", C.c_int * 3), ("pred", C.c_int), ("stencil", C.c_int),
                 ("hidden", C.c_int * 2), ("m", C.c_int), ("s_in", C.c_int), ("h_weights", C.c_void_p),
                 ("h_qnet", C.c_void_p), ("seed", C.c_ulonglong), ("train_samples", C.c_longlong),
-                ("ndims", C.c_int), ("reserved_", C.c_int)]
+                ("ndims", C.c_int), ("codebook_n", C.c_int), ("h_codebook", C.c_void_p)]
 
 
 def lib():
@@ -94,6 +94,9 @@ def lib():
                 L.pc_train.argtypes = [vp, szp, C.c_int, P, C.c_ulonglong, C.c_uint, C.c_int, vp, vp, vp,
                                        C.POINTER(C.c_int), C.POINTER(C.c_int), vp, vp, sz, vp]
             if hasattr(L, "pc_train_select"):
+                L.pc_sample_codebook.restype = C.c_int
+                L.pc_sample_codebook.argtypes = [vp, szp, C.c_int, P, C.c_ulonglong, C.c_uint, C.c_int, vp,
+                                                 C.POINTER(C.c_int), vp, sz, vp]
                 L.pc_train_select.restype = C.c_int
                 L.pc_train_select.argtypes = [vp, szp, C.c_int, P, C.c_ulonglong, C.c_uint, C.c_int, vp, vp, vp,
                                               C.POINTER(C.c_int), C.POINTER(C.c_int), vp, C.POINTER(C.c_int), vp, sz,
@@ -158,14 +161,22 @@ def _stream_ptr(stream):
 
 def make_params(eb_rel: float, block=(8, 8, 8), pred: int = PC_PRED_LORENZO, stencil: int = 7,
                 hidden=(16, 16), m: int = 16, s_in: int = 0, weights=None, qnet=None, seed: int = 0,
-                train_samples: int = 0, ndims: int = 0):
-    """Fill a pc_params struct; the weights and network arrays are kept alive on the struct.
-    With a perceptron form and no weights (or network), pc_compress trains one on the device."""
+                train_samples: int = 0, ndims: int = 0, codebook=None):
+    """Fill a pc_params struct; the weights, network and codebook arrays are kept alive on the
+    struct.  With a perceptron form and no weights (or network), pc_compress trains one on the
+    device; with a codebook (uint32 list from pc_sample_codebook) it compresses in one pass."""
     p = pc_params()
     p.seed = int(seed)
     p.train_samples = int(train_samples)
     p.ndims = int(ndims)
-    p.reserved_ = 0
+    if codebook is not None:
+        cb = np.ascontiguousarray(np.asarray(codebook, dtype=np.uint32))
+        p._cb = cb
+        p.h_codebook = cb.ctypes.data
+        p.codebook_n = int(cb.size)
+    else:
+        p.h_codebook = None
+        p.codebook_n = 0
     p.eb_rel = float(eb_rel)
     p.block[:] = [int(b) for b in block]
     p.pred = int(pred)
@@ -317,6 +328,21 @@ def pc_train_select(field, params: pc_params, seed: int, thr32: int, lrs, lams, 
                                C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream))
     _check(st, "pc_train_select")
     return W, s_in.value, chosen.value, sizes, m.value
+
+
+def pc_sample_codebook(field, params: pc_params, seed: int, thr32: int, ws, stream=None,
+                       span_fill: bool = False) -> np.ndarray:
+    """Sample codebook of the training phase for params' predictor (FP32 weights, or Lorenzo):
+    uint32 list (sym | length << 16) in container order.  span_fill: every code inside the
+    sampled span gets a code word."""
+    out = np.zeros(1 << params.m, np.uint32)
+    n = C.c_int()
+    st = lib().pc_sample_codebook(C.c_void_p(field.data_ptr()), _dims3(field.shape), _dtype_of(field),
+                                  C.byref(params), int(seed), int(thr32), int(bool(span_fill)),
+                                  out.ctypes.data_as(C.c_void_p),
+                                  C.byref(n), C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream))
+    _check(st, "pc_sample_codebook")
+    return out[: n.value].copy()
 
 
 def pc_qnet_len(k: int, h1: int, h2: int) -> int:

@@ -60,6 +60,15 @@ def test_list_by_hand(O):
     # a histogram with nothing but balance points: one symbol of length 1
     z = np.zeros(16, np.uint64)
     assert O.sample_codebook(z, m=4).tolist() == [0 | 1 << 16]
+    # span fill: {5: 3, 7: 1} and symbol 0 forced, 6 (inside the sampled span 5..7) counts once:
+    # leaves (1, 0), (1, 6), (1, 7), (3, 5); merge 0 and 6 (2), then 7 (1) with that node (3),
+    # then 5 (3, leaf first) with it: lengths 5 -> 1, 7 -> 2, 0 -> 3, 6 -> 3; order 5, 7, 6, 0
+    h = np.zeros(8, np.uint64)
+    h[5], h[7] = 3, 1
+    assert O.sample_codebook(h, m=3, span_fill=True).tolist() == [5 | 1 << 16, 7 | 2 << 16, 6 | 3 << 16,
+                                                                   0 | 3 << 16]
+    # codes beyond the span (1..4) stay without a code word; only symbol 0 when nothing else was seen
+    assert O.sample_codebook(z, m=4, span_fill=True).tolist() == [0 | 1 << 16]
 
 
 def test_average_per_block_is_the_same_code(O):
@@ -198,3 +207,27 @@ def test_malformed_lists_are_refused(O, bad):
     elif bad == "single_long":
         cb = np.array([0 | 2 << 16], np.uint32)
     assert O.compress(x, 1e-2, codebook=cb)[0] == -1
+
+
+def test_span_fill_leaves_only_codes_beyond_the_span(O):
+    # with span fill, a point becomes a balance point only when its code lies outside the
+    # sampled span (or outside the quantization range / bound check, as without a codebook)
+    x = gen.positive_lognormal((32, 64, 64), 2.0, 0, 1.5)
+    eb, thr = 1e-4, int(0.05 * 2 ** 32)
+    _, (vin, vtg, vus) = O.gather_samples(x, eb, (8, 8, 8), 7, 0, thr)
+    h = O.val_hist(None, 7, 2, 0, 0, vin, vtg, vus, m=16)
+    nz = np.flatnonzero(h[1:]) + 1
+    lo, hi = int(nz.min()), int(nz.max())
+    cb = O.sample_codebook_for(x, eb, seed=0, thr32=thr, span_fill=True)
+    syms = set((cb & 0xFFFF).tolist())
+    assert syms == set(range(lo, hi + 1)) | {0}
+    st, two, d2 = O.compress(x, eb, dump=True)
+    st, one, d1 = O.compress(x, eb, codebook=cb, dump=True)
+    c2, c1 = d2["codes"], d1["codes"]
+    moved = (c1 == 0) & (c2 != 0)
+    assert moved.any()
+    assert np.all((c2[moved] < lo) | (c2[moved] > hi))
+    assert np.array_equal(c1[~moved], c2[~moved])
+    # and it codes far closer to the field's own code than the literal reading
+    st, lit = O.compress(x, eb, codebook=O.sample_codebook_for(x, eb, seed=0, thr32=thr))
+    assert len(one) < len(lit)
