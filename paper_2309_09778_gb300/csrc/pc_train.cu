@@ -8,12 +8,15 @@
 //                  in block order;
 //   k_in_shift     input scale s (sum of min(t^2, 2^40) over used samples);
 //   k_init_w       Lorenzo-equal initial weights (Section IV.B);
-//   k_train        one CTA per (lr, lambda) model: one epoch of minibatch SGD,
-//                  every gradient a pairwise tree sum over the 256 rows
-//                  (xor butterfly in each warp, then warp pairs);
+//   k_train        a cluster of 8 CTAs per (lr, lambda) model: one epoch of
+//                  minibatch SGD, every gradient a pairwise tree sum over the
+//                  256 rows (32 rows per CTA, then the 8 CTA sums through
+//                  distributed shared memory);
 //   k_val          residual bit cost of every model and of Lorenzo on the
 //                  validation samples;
 //   k_choose       the cheapest model (Lorenzo unless strictly beaten).
+#include <cooperative_groups.h>
+
 #include "pc_kernels.cuh"
 #include "pc_profile.cuh"
 #include "pc_qmlp.cuh"
@@ -224,126 +227,193 @@ __global__ void k_init_w(float* w, int nmodels, int k, int h1, int h2, unsigned 
   for (int m = 0; m < nmodels; ++m) w[(size_t)m * nw + p] = v;
 }
 
-// Pairwise tree over the block's 256 rows: xor butterfly inside each warp
-// (lane 0 ends with ((r0+r1)+(r2+r3))+...), then the eight warp sums pairwise.
-__device__ __forceinline__ float warp_tree(float v) {
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) v = __fadd_rn(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
-  return v;
-}
+// One epoch of minibatch SGD per (lr, lambda) model (Section IV.C), each model
+// on a cluster of 8 CTAs: CTA c of the cluster takes rows 32c .. 32c + 31 of
+// every 256-row minibatch.  Warp 0 runs its rows' forward and backward passes
+// and leaves every row's inputs, activations and deltas in shared memory; the
+// CTA then sums each parameter's 32 row terms over a pairwise tree in row
+// order ((r0 + r1) + (r2 + r3)) + ...; after a cluster barrier CTA c adds the
+// eight CTA sums of its slice of the parameters pairwise, ((q0 + q1) +
+// (q2 + q3)) + ((q4 + q5) + (q6 + q7)), updates them and writes the new
+// values into every CTA's copy of the weights (distributed shared memory);
+// a second cluster barrier ends the step.  The gradient is therefore the
+// same balanced pairwise tree over the minibatch's 256 rows, in row order.
+constexpr int kTrainCluster = 8;
+constexpr int kTrainRows = 32;  // rows per CTA
 
 template <int K, int H1, int H2>
-__global__ void __launch_bounds__(256) k_train(const int* __restrict__ tin, const int* __restrict__ ttg,
-                                               const uint8_t* __restrict__ tus, float* __restrict__ wbuf,
-                                               const float* __restrict__ lrs, const float* __restrict__ lams,
-                                               const TrainCtl* __restrict__ ctl) {
+__global__ void __cluster_dims__(kTrainCluster, 1, 1) __launch_bounds__(128)
+    k_train(const int* __restrict__ tin, const int* __restrict__ ttg, const uint8_t* __restrict__ tus,
+            float* __restrict__ wbuf, const float* __restrict__ lrs, const float* __restrict__ lams,
+            const TrainCtl* __restrict__ ctl) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
   constexpr int HL = H2 > 0 ? H2 : H1;
+  constexpr int H2E = H2 > 0 ? H2 : 1;
   constexpr int NW = H1 * K + H1 + (H2 > 0 ? H2 * H1 + H2 : 0) + HL + 1;
   constexpr int OB1 = H1 * K, OW2 = OB1 + H1, OB2 = OW2 + H2 * H1, OW3 = H2 > 0 ? OB2 + H2 : OW2;
-  extern __shared__ __align__(16) float sm[];
-  float* w = sm;            // NW
-  float* part = sm + NW;    // 8 * NW warp sums
-  const int model = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // per-row vector: u[K] | a1[H1] | a2[H2] | d1[H1] | d2[H2] | go | 1
+  constexpr int VA1 = K, VA2 = VA1 + H1, VD1 = VA2 + H2, VD2 = VD1 + H1, VGO = VD2 + H2, VONE = VGO + 1;
+  constexpr int VS = (VONE + 1) | 1;  // odd row stride
+  constexpr int SL = (NW + kTrainCluster - 1) / kTrainCluster;
+  __shared__ float w[NW];
+  __shared__ float part[NW];
+  __shared__ float V[kTrainRows * VS];
+  __shared__ unsigned short fa[NW], fb[NW];
+  const int rank = (int)cl.block_rank();
+  const int model = blockIdx.x / kTrainCluster;
+  const int tid = threadIdx.x;
   float* wm = wbuf + (size_t)model * NW;
-  for (int p = tid; p < NW; p += 256) w[p] = wm[p];
+  for (int p = tid; p < NW; p += blockDim.x) {
+    w[p] = wm[p];
+    // the two row-vector entries whose product is parameter p's row term
+    int a, b;
+    if (p < OB1) { a = VD1 + p / K; b = p % K; }
+    else if (p < OW2) { a = VD1 + (p - OB1); b = VONE; }
+    else if (H2 > 0 && p < OB2) { a = VD2 + (p - OW2) / H1; b = VA1 + (p - OW2) % H1; }
+    else if (H2 > 0 && p < OW3) { a = VD2 + (p - OB2); b = VONE; }
+    else if (p < OW3 + HL) { a = VGO; b = (H2 > 0 ? VA2 : VA1) + (p - OW3); }
+    else { a = VGO; b = VONE; }
+    fa[p] = (unsigned short)a;
+    fb[p] = (unsigned short)b;
+  }
   const float lr = lrs[model], lam2 = __fadd_rn(lams[model], lams[model]);
   const int s_in = ctl->s_in;
   const float sig = __uint_as_float((unsigned int)(127 - s_in) << 23);
   const unsigned long long n = ctl->ntrain;
+  float* const peer_part[kTrainCluster] = {
+      cl.map_shared_rank(part, 0), cl.map_shared_rank(part, 1), cl.map_shared_rank(part, 2),
+      cl.map_shared_rank(part, 3), cl.map_shared_rank(part, 4), cl.map_shared_rank(part, 5),
+      cl.map_shared_rank(part, 6), cl.map_shared_rank(part, 7)};
+  float* const peer_w[kTrainCluster] = {
+      cl.map_shared_rank(w, 0), cl.map_shared_rank(w, 1), cl.map_shared_rank(w, 2), cl.map_shared_rank(w, 3),
+      cl.map_shared_rank(w, 4), cl.map_shared_rank(w, 5), cl.map_shared_rank(w, 6), cl.map_shared_rank(w, 7)};
   __syncthreads();
   for (unsigned long long s0 = 0; s0 < n; s0 += 256) {
     const int B = (int)((n - s0) < 256ull ? (n - s0) : 256ull);
-    const bool row = tid < B;
-    float u[K], z1[H1], a1[H1], z2[H2 > 0 ? H2 : 1], a2[H2 > 0 ? H2 : 1], d1[H1], d2[H2 > 0 ? H2 : 1];
-    float go = 0.0f;
-    if (row) {
-      const unsigned long long r = s0 + tid;
+    // forward and backward of the CTA's 32 rows (lane = row), the hidden units
+    // split over the four warps; each unit's sums run in the same order as a
+    // single thread's would
+    {
+      const int lane = tid & 31, q = tid >> 5;
+      const int lrow = rank * kTrainRows + lane;
+      const bool valid = lrow < B;
+      const unsigned long long r = s0 + (valid ? lrow : 0);
+      float* v = V + lane * VS;
+      constexpr int NU1 = (H1 + 3) / 4, NU2 = (H2E + 3) / 4;
+      float u[K], z1[NU1], z2[NU2];
 #pragma unroll
-      for (int i = 0; i < K; ++i) u[i] = __fmul_rn(small_int_to_float(tin[r * K + i]), sig);
+      for (int i = 0; i < K; ++i) u[i] = valid ? __fmul_rn(small_int_to_float(tin[r * K + i]), sig) : 0.0f;
 #pragma unroll
-      for (int j = 0; j < H1; ++j) {
-        float acc = w[OB1 + j];
+      for (int jj = 0; jj < NU1; ++jj) {
+        const int j = q * NU1 + jj;
+        if (j < H1) {
+          float acc = w[OB1 + j];
 #pragma unroll
-        for (int i = 0; i < K; ++i) acc = __fmaf_rn(w[j * K + i], u[i], acc);
-        z1[j] = acc;
-        a1[j] = acc >= 0.0f ? acc : __fmul_rn(acc, kAlpha);
+          for (int i = 0; i < K; ++i) acc = __fmaf_rn(w[j * K + i], u[i], acc);
+          z1[jj] = acc;
+          v[VA1 + j] = valid ? (acc >= 0.0f ? acc : __fmul_rn(acc, kAlpha)) : 0.0f;
+        }
       }
+      if (q == 0) {
+#pragma unroll
+        for (int i = 0; i < K; ++i) v[i] = u[i];
+      }
+      __syncthreads();
       if constexpr (H2 > 0) {
 #pragma unroll
-        for (int j = 0; j < H2; ++j) {
-          float acc = w[OB2 + j];
-#pragma unroll
-          for (int i = 0; i < H1; ++i) acc = __fmaf_rn(w[OW2 + j * H1 + i], a1[i], acc);
-          z2[j] = acc;
-          a2[j] = acc >= 0.0f ? acc : __fmul_rn(acc, kAlpha);
+        for (int jj = 0; jj < NU2; ++jj) {
+          const int j = q * NU2 + jj;
+          if (j < H2) {
+            float acc = w[OB2 + j];
+#pragma unroll 8
+            for (int i = 0; i < H1; ++i) acc = __fmaf_rn(w[OW2 + j * H1 + i], v[VA1 + i], acc);
+            z2[jj] = acc;
+            v[VA2 + j] = valid ? (acc >= 0.0f ? acc : __fmul_rn(acc, kAlpha)) : 0.0f;
+          }
         }
+        __syncthreads();
       }
-      float o = w[OW3 + HL];
-#pragma unroll
-      for (int j = 0; j < HL; ++j) o = __fmaf_rn(w[OW3 + j], H2 > 0 ? a2[j] : a1[j], o);
-      const float tt = __fmul_rn(small_int_to_float(ttg[r]), sig);
-      const float ginv = __fdiv_rn(2.0f, (float)B);
-      go = tus[r] ? __fmul_rn(__fsub_rn(o, tt), ginv) : 0.0f;
+      if (q == 0) {
+        float o = w[OW3 + HL];
+#pragma unroll 8
+        for (int j = 0; j < HL; ++j) o = __fmaf_rn(w[OW3 + j], v[(H2 > 0 ? VA2 : VA1) + j], o);
+        float go = 0.0f;
+        if (valid) {
+          const float tt = __fmul_rn(small_int_to_float(ttg[r]), sig);
+          const float ginv = __fdiv_rn(2.0f, (float)B);
+          go = tus[r] ? __fmul_rn(__fsub_rn(o, tt), ginv) : 0.0f;
+        }
+        v[VGO] = go;
+        v[VONE] = valid ? 1.0f : 0.0f;
+      }
+      __syncthreads();
+      const float go = v[VGO];
       if constexpr (H2 > 0) {
 #pragma unroll
-        for (int j = 0; j < H2; ++j) {
-          const float q = __fmul_rn(go, w[OW3 + j]);
-          d2[j] = z2[j] >= 0.0f ? q : __fmul_rn(q, kAlpha);
+        for (int jj = 0; jj < NU2; ++jj) {
+          const int j = q * NU2 + jj;
+          if (j < H2) {
+            const float qq = __fmul_rn(go, w[OW3 + j]);
+            v[VD2 + j] = valid ? (z2[jj] >= 0.0f ? qq : __fmul_rn(qq, kAlpha)) : 0.0f;
+          }
         }
+        __syncthreads();
+      }
 #pragma unroll
-        for (int i = 0; i < H1; ++i) {
-          float sacc = 0.0f;
-#pragma unroll
-          for (int j = 0; j < H2; ++j) sacc = __fmaf_rn(w[OW2 + j * H1 + i], d2[j], sacc);
-          d1[i] = z1[i] >= 0.0f ? sacc : __fmul_rn(sacc, kAlpha);
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < H1; ++i) {
-          const float q = __fmul_rn(go, w[OW3 + i]);
-          d1[i] = z1[i] >= 0.0f ? q : __fmul_rn(q, kAlpha);
+      for (int jj = 0; jj < NU1; ++jj) {
+        const int i = q * NU1 + jj;
+        if (i < H1) {
+          float d;
+          if constexpr (H2 > 0) {
+            float sacc = 0.0f;
+#pragma unroll 8
+            for (int j = 0; j < H2; ++j) sacc = __fmaf_rn(w[OW2 + j * H1 + i], v[VD2 + j], sacc);
+            d = z1[jj] >= 0.0f ? sacc : __fmul_rn(sacc, kAlpha);
+          } else {
+            const float qq = __fmul_rn(go, w[OW3 + i]);
+            d = z1[jj] >= 0.0f ? qq : __fmul_rn(qq, kAlpha);
+          }
+          v[VD1 + i] = valid ? d : 0.0f;
         }
       }
     }
-    // per-parameter row terms, tree-summed; rows >= B contribute +0
-    auto put = [&](int p, float term) {
-      const float sum = warp_tree(row ? term : 0.0f);
-      if (lane == 0) part[wid * NW + p] = sum;
-    };
-#pragma unroll
-    for (int j = 0; j < H1; ++j) {
-#pragma unroll
-      for (int i = 0; i < K; ++i) put(j * K + i, __fmul_rn(d1[j], u[i]));
-      put(OB1 + j, d1[j]);
-    }
-    if constexpr (H2 > 0) {
-#pragma unroll
-      for (int j = 0; j < H2; ++j) {
-#pragma unroll
-        for (int i = 0; i < H1; ++i) put(OW2 + j * H1 + i, __fmul_rn(d2[j], a1[i]));
-        put(OB2 + j, d2[j]);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < HL; ++j) put(OW3 + j, __fmul_rn(go, H2 > 0 ? a2[j] : a1[j]));
-    put(OW3 + HL, go);
     __syncthreads();
-    for (int p = tid; p < NW; p += 256) {
-      const float* q = part + p;
-      const float g = __fadd_rn(__fadd_rn(__fadd_rn(q[0], q[NW]), __fadd_rn(q[2 * NW], q[3 * NW])),
-                                __fadd_rn(__fadd_rn(q[4 * NW], q[5 * NW]), __fadd_rn(q[6 * NW], q[7 * NW])));
+    // this CTA's 32-row sum of every parameter's terms, pairwise in row order
+    for (int p = tid; p < NW; p += blockDim.x) {
+      const int a = fa[p], b = fb[p];
+      float t[kTrainRows];
+#pragma unroll
+      for (int r = 0; r < kTrainRows; ++r) t[r] = __fmul_rn(V[r * VS + a], V[r * VS + b]);
+#pragma unroll
+      for (int st = 1; st < kTrainRows; st <<= 1)
+#pragma unroll
+        for (int r = 0; r < kTrainRows; r += 2 * st) t[r] = __fadd_rn(t[r], t[r + st]);
+      part[p] = t[0];
+    }
+    cl.sync();
+    // the cluster sum of this CTA's slice, the update, and the new weights to every CTA
+    for (int p = rank * SL + tid; p < NW && p < (rank + 1) * SL; p += blockDim.x) {
+      float q[kTrainCluster];
+#pragma unroll
+      for (int c = 0; c < kTrainCluster; ++c) q[c] = peer_part[c][p];
+      const float g = __fadd_rn(__fadd_rn(__fadd_rn(q[0], q[1]), __fadd_rn(q[2], q[3])),
+                                __fadd_rn(__fadd_rn(q[4], q[5]), __fadd_rn(q[6], q[7])));
       const bool bias = (p >= OB1 && p < OB1 + H1) || (H2 > 0 && p >= OB2 && p < OB2 + H2) || p == NW - 1;
+      float nv;
       if (bias) {
-        w[p] = __fsub_rn(w[p], __fmul_rn(lr, g));
+        nv = __fsub_rn(w[p], __fmul_rn(lr, g));
       } else {
         const float gt = __fadd_rn(g, __fmul_rn(lam2, w[p]));
-        w[p] = __fsub_rn(w[p], __fmul_rn(lr, gt));
+        nv = __fsub_rn(w[p], __fmul_rn(lr, gt));
       }
+#pragma unroll
+      for (int c = 0; c < kTrainCluster; ++c) peer_w[c][p] = nv;
     }
-    __syncthreads();
+    cl.sync();
   }
-  for (int p = tid; p < NW; p += 256) wm[p] = w[p];
+  if (rank == 0)
+    for (int p = tid; p < NW; p += blockDim.x) wm[p] = w[p];
 }
 
 // validation cost; blockIdx.y = model (nmodels = Lorenzo)
@@ -398,13 +468,10 @@ __global__ void k_choose(const unsigned long long* costs, int nmodels, TrainCtl*
 
 template <int K, int H1, int H2>
 static int launch_train_models(const TrainBufs& tb, int nmodels, int m, cudaStream_t s) {
-  constexpr int NW = H1 * K + H1 + (H2 > 0 ? H2 * H1 + H2 : 0) + (H2 > 0 ? H2 : H1) + 1;
-  const size_t sm = (size_t)NW * 9 * sizeof(float);
-  auto kt = k_train<K, H1, H2>;
-  if (cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return PC_ERR_CUDA;
   {
     ProfScope p(kStTrain, s);
-    kt<<<nmodels, 256, sm, s>>>(tb.tin, tb.ttg, tb.tus, tb.w, tb.lrs, tb.lams, reinterpret_cast<const TrainCtl*>(tb.ctl));
+    k_train<K, H1, H2><<<nmodels * kTrainCluster, 128, 0, s>>>(tb.tin, tb.ttg, tb.tus, tb.w, tb.lrs, tb.lams,
+                                                               reinterpret_cast<const TrainCtl*>(tb.ctl));
   }
   dim3 gv(152, nmodels + 1);
   k_val<K, H1, H2><<<gv, 256, 0, s>>>(tb.vin, tb.vtg, tb.vus, tb.w, nmodels, m,
