@@ -338,23 +338,6 @@ constexpr int recon_blocks() {
   return BrickShape<BV>::G * ((MODE == 1 && K > 0 && BV <= 512 && TSZ == 4) ? 2 : 1);
 }
 
-// Largest wavefront of a block under either schedule (z + y + x, 4z + 2y + x).
-template <int B0, int B1, int B2>
-constexpr int max_wave() {
-  int best = 0;
-  for (int s13 = 0; s13 < 2; ++s13)
-    for (int sv = 0; sv <= 4 * (B0 - 1) + 2 * (B1 - 1) + (B2 - 1); ++sv) {
-      int n = 0;
-      for (int z = 0; z < B0; ++z)
-        for (int y = 0; y < B1; ++y) {
-          const int x = sv - (s13 ? 4 * z + 2 * y : z + y);
-          n += x >= 0 && x < B2;
-        }
-      best = n > best ? n : best;
-    }
-  return best;
-}
-
 // Shared-memory layout of k_recon (16-byte aligned regions).  The per-block
 // strides are padded so that the same point of the GR blocks falls on
 // different banks: wave positions run block-fastest across the lanes.
@@ -366,11 +349,9 @@ struct ReconLayout {
   static constexpr int XS = BV + 1;   // block stride of the values
   static constexpr int CS = BV + 8;   // block stride of the codes (16-byte rows for vector copies)
   static constexpr size_t a16(size_t v) { return (v + 15) & ~(size_t)15; }
-  // fixed-point form: staged constants, B fragments, one wave's predictions
+  // fixed-point form: staged constants and B fragments
   static constexpr int QH = H1 == 32 ? 32 : 16;
-  static constexpr size_t QB = MODE == 2 ? a16(sizeof(TcStage<QH>)) + a16(sizeof(WStage<QH>)) +
-                                               a16((size_t)GR * max_wave<B0, B1, B2>() * 4)
-                                         : 0;
+  static constexpr size_t QB = MODE == 2 ? a16(sizeof(TcStage<QH>)) + a16(sizeof(WStage<QH>)) : 0;
   static constexpr size_t VP = sizeof(Tabs) + QB;
   static constexpr size_t X = VP + a16((size_t)GR * PVS * 4);
   static constexpr size_t L = X + a16((size_t)GR * XS * TSZ);
@@ -383,8 +364,16 @@ constexpr size_t recon_smem_bytes() {
   return ReconLayout<B0, B1, B2, PV, TSZ, MODE, K, H1, H2>::TOTAL;
 }
 
+// A coded point's value slot holds its code q until the waves are done.
+template <typename T>
+__device__ __forceinline__ void put_q(T* slot, int q) { *reinterpret_cast<int*>(slot) = q; }
+template <typename T>
+__device__ __forceinline__ int get_q(const T* slot) { return *reinterpret_cast<const int*>(slot); }
+
+// Three CTAs per SM for the fixed-point form (80 registers, 73 KB of shared
+// memory each): its waves are latency-bound, and more resident warps hide it.
 template <typename T, int B0, int B1, int B2, int MODE, int K, int H1, int H2>
-__global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_t* __restrict__ in, DecInfo di, DecScratch ds,
+__global__ void __launch_bounds__(256, MODE == 1 ? 2 : 3) k_recon(Geo g, const uint8_t* __restrict__ in, DecInfo di, DecScratch ds,
                                                T* __restrict__ xo, const __grid_constant__ Mlp mlp) {
   constexpr int BV = B0 * B1 * B2;
   using BS = BrickShape<BV>;
@@ -401,11 +390,9 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
   extern __shared__ __align__(16) unsigned char smem[];
   Tabs& tb = *reinterpret_cast<Tabs*>(smem);
   constexpr int QK = MODE == 2 ? K : 7, QH = RL::QH;
-  // fixed-point form only: constants, fragments, one wave's predictions
+  // fixed-point form only: constants and fragments
   TcStage<QH>& qst = *reinterpret_cast<TcStage<QH>*>(smem + sizeof(Tabs));
   WStage<QH>& qwf = *reinterpret_cast<WStage<QH>*>(smem + sizeof(Tabs) + RL::a16(sizeof(TcStage<QH>)));
-  int* s_wpred = reinterpret_cast<int*>(smem + sizeof(Tabs) + RL::a16(sizeof(TcStage<QH>)) +
-                                        RL::a16(sizeof(WStage<QH>)));
   int* s_vp = reinterpret_cast<int*>(smem + RL::VP);             // GR padded blocks of centred codes
   T* s_x = reinterpret_cast<T*>(smem + RL::X);                    // GR blocks of values
   // BV points in wave order, each j | (padded index of j) << 16
@@ -592,6 +579,9 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
       for (int sw = 1; sw < nwave; ++sw) {
         const int w0 = s_ws[sw], S = s_ws[sw + 1] - w0;
         const int tot = GR * S;
+        // A wave's points read only earlier waves, so each tile finishes its own
+        // points right after the network (lane c of a quad takes row g, lane
+        // c + 1 row g + 8); one barrier per wave.
         for (int tile = wid; tile * 16 < tot; tile += 8) {
           int xv[2][4];
           int fs[2];
@@ -606,39 +596,39 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
           }
           int pq[2];
           wnet_tile<QK, QH>(qwf, qst, xv, pq[0], pq[1]);
-          if (qc == 0) {
-            if (fs[0] < tot) s_wpred[fs[0]] = pq[0];
-            if (fs[1] < tot) s_wpred[fs[1]] = pq[1];
-          }
-        }
-        __syncthreads();
-        // finish the wave's points, one per thread
-        for (int f = tid; f < tot; f += 256) {
-          const int gb = f % GR;
-          const unsigned int e = s_list[w0 + f / GR];
-          const int j = (int)(e & 0xFFFFu), pj = gb * PVS + (int)(e >> 16);
-          if (!brick_full) {
-            const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
-            if (!(lz < e0 && ly < e1 && lx < s_e2[gb])) continue;
-          }
-          const unsigned int code = s_cd[gb * CS + j];
-          if (code == 0) continue;  // balance point, already in place
-          long long prd;
-          if (s_usen[gb]) {
-            prd = s_wpred[f];
-          } else {
-            int acc = 0;
+          if (qc < 2) {
+            const int f = fs[qc];
+            if (f < tot) {
+              const int gb = f % GR;
+              const unsigned int e = s_list[w0 + f / GR];
+              const int j = (int)(e & 0xFFFFu), pj = gb * PVS + (int)(e >> 16);
+              bool valid = true;
+              if (!brick_full) {
+                const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+                valid = lz < e0 && ly < e1 && lx < s_e2[gb];
+              }
+              const unsigned int code = s_cd[gb * CS + j];
+              if (valid && code != 0) {  // balance points are already in place
+                long long prd;
+                if (s_usen[gb]) {
+                  prd = qc ? pq[1] : pq[0];
+                } else {
+                  int acc = 0;
 #pragma unroll
-            for (int si = 0; si < 7; ++si) acc += lz_w(7, si) * s_vp[pj + PD::off(s7_dz(si), s7_dy(si), s7_dx(si))];
-            prd = acc;
+                  for (int si = 0; si < 7; ++si)
+                    acc += lz_w(7, si) * s_vp[pj + PD::off(s7_dz(si), s7_dy(si), s7_dx(si))];
+                  prd = acc;
+                }
+                const int dag = s_da[gb];
+                const long long qq = (long long)dag + prd + ((long long)code - R);
+                int q;
+                if (qq > 2147483647LL || qq < -2147483647LL) { bad = true; q = 0; }
+                else q = (int)qq;
+                put_q(&s_x[gb * XS + j], q);
+                s_vp[pj] = clampv((long long)q - dag);
+              }
+            }
           }
-          const int dag = s_da[gb];
-          const long long qq = (long long)dag + prd + ((long long)code - R);
-          int q;
-          if (qq > 2147483647LL || qq < -2147483647LL) { bad = true; q = 0; }
-          else q = (int)qq;
-          s_x[gb * XS + j] = Num<T>::recon(q, c, tb);
-          s_vp[pj] = clampv((long long)q - dag);
         }
         __syncthreads();
       }
@@ -684,7 +674,6 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
           if (need[0] || need[1]) mlp_fwd2<K, H1, H2>(mlp, inp[0], inp[1], sig, unsig, pv[0], pv[1]);
           // both positions finish without branches, so their chains overlap
           int qv[2];
-          T xr[2];
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
             const long long prd = need[u] ? (long long)round_pred(pv[u]) : (long long)lzp[u];
@@ -694,11 +683,9 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
             qv[u] = ovf ? 0 : (int)qq;
           }
 #pragma unroll
-          for (int u = 0; u < 2; ++u) xr[u] = Num<T>::recon(qv[u], c, tb);
-#pragma unroll
           for (int u = 0; u < 2; ++u)
             if (act[u]) {
-              s_x[xis[u]] = xr[u];
+              put_q(&s_x[xis[u]], qv[u]);
               s_vp[pjs[u]] = clampv((long long)qv[u] - dav[u]);
             }
         }
@@ -741,11 +728,23 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_recon(Geo g, const uint8_
           int q;
           if (qq > 2147483647LL || qq < -2147483647LL) { bad = true; q = 0; }
           else q = (int)qq;
-          xs[j] = Num<T>::recon(q, c, tb);
+          put_q(&xs[j], q);
           vp[pj] = clampv((long long)q - da);
         }
       }
       if (TS == 32) __syncwarp(); else __syncthreads();
+    }
+    __syncthreads();
+    // The waves kept each coded point's code q in its value slot; the values
+    // (the inverse map, Section III.B) need no wave order.
+    for (int i = tid; i < GR * BV; i += 256) {
+      const int gb = i / BV, j = i - gb * BV;
+      if (j == 0) continue;  // the anchor holds its stored value
+      const int lz = j / (B1 * B2), ly = (j / B2) % B1, lx = j % B2;
+      if (!(lz < e0 && ly < e1 && lx < s_e2[gb])) continue;
+      if (s_cd[gb * CS + j] == 0) continue;  // balance point: stored value
+      T* slot = &s_x[gb * XS + j];
+      *slot = Num<T>::recon(get_q(slot), c, tb);
     }
     __syncthreads();
     // coalesced brick store
@@ -787,6 +786,9 @@ static int launch_r(const uint8_t* in, const Geo& g, const DecInfo& di, const De
   constexpr size_t sm = recon_smem_bytes<B0, B1, B2, Pad<B0, B1, B2, WIDE>::PV, (int)sizeof(T), MODE, K, H1, H2>();
   static_assert(sm <= 232448, "shared memory per CTA");
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+    return PC_ERR_CUDA;
+  if (MODE == 2 && cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                        cudaSharedmemCarveoutMaxShared) != cudaSuccess)
     return PC_ERR_CUDA;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm);
