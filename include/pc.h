@@ -82,6 +82,13 @@ typedef struct {
                              a code the list lacks becomes a balance point, and the container
                              places the bitstream before the balance values (Section IV.C
                              keeps the training phase's Huffman code for compression) */
+  int literal;            /* 1: the paper-literal data selection of Section IV.D, an experimental mode
+                             (float32 fields, PC_PRED_LORENZO or PC_PRED_MLP_FP32 with weights): every
+                             point is predicted from the true values of its neighbours, the decoder
+                             predicts from its reconstructions and drifts, so the bound is NOT
+                             guaranteed; the container is flagged and decodes with the drift */
+  int eq_period;          /* literal mode: every eq_period-th point of a block (raster order) is stored
+                             as a deliberate equilibrium point; 0 = none */
 } pc_params;
 /*
  * Learned predictor trained inside pc_compress (Section IV.C, V): with

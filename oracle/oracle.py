@@ -51,7 +51,8 @@ class Consts(C.Structure):
 class Params(C.Structure):
     _fields_ = [("eb", C.c_double), ("block", C.c_int * 3), ("pred", C.c_int), ("stencil", C.c_int),
                 ("h1", C.c_int), ("h2", C.c_int), ("m", C.c_int), ("s_in", C.c_int),
-                ("weights", C.c_void_p), ("qnet", C.c_void_p), ("codebook", C.c_void_p), ("codebook_n", C.c_int)]
+                ("weights", C.c_void_p), ("qnet", C.c_void_p), ("codebook", C.c_void_p), ("codebook_n", C.c_int),
+                ("literal", C.c_int), ("eq_period", C.c_int)]
 
 
 class Dump(C.Structure):
@@ -383,12 +384,15 @@ def compress_bound(shape3, dtype: int, block, m: int = 16, nweights: int = 0) ->
 
 
 def compress(x: np.ndarray, eb: float, block=(8, 8, 8), weights=None, stencil=7, h1=16, h2=16,
-             m: int = 16, s_in: int = 0, dump: bool = False, qnet=None, fp64: bool = False, codebook=None):
+             m: int = 16, s_in: int = 0, dump: bool = False, qnet=None, fp64: bool = False, codebook=None,
+             literal: bool = False, eq_period: int = 0):
     """Compress with the oracle.  Returns (status, bytes[, dump dict]).  `qnet` selects the
     fixed-point (BF16) perceptron form instead of the FP32 weights; fp64=True evaluates the
     FP32 weights in FP64 (the reporting predictor, which only the oracle encodes with).
     `codebook` (uint32 list, sym | len << 16) compresses with that sample codebook: codes
-    outside it become balance points and the stream precedes the balance values."""
+    outside it become balance points and the stream precedes the balance values.
+    literal=True: the paper-literal data selection (predict from true values; float32 only),
+    with a deliberate equilibrium point every eq_period points of each block (0: none)."""
     x = np.ascontiguousarray(x)
     dims = _dims(x)
     dt = _dtype_code(x)
@@ -405,6 +409,8 @@ def compress(x: np.ndarray, eb: float, block=(8, 8, 8), weights=None, stencil=7,
         pred = PRED_MLP64
     cb = None if codebook is None else np.ascontiguousarray(codebook, np.uint32)
     p = _params(eb, block, pred, stencil, h1, h2, m, s_in, w, q, cb)
+    p.literal = int(bool(literal))
+    p.eq_period = int(eq_period)
     cap = compress_bound(tuple(dims), dt, block, m, nw)
     out = np.zeros(cap, np.uint8)
     size = C.c_uint64()

@@ -884,6 +884,159 @@ static int o_block(const int32_t* dqb, const uint8_t* okb, int e0, int e1, int e
   return use_nn && costn < costz;
 }
 
+/* ------------------------------------------------------------------------- */
+/* The paper-literal data selection (Section IV.D, float32 only): every      */
+/* point is predicted from the true values of its causal in-block            */
+/* neighbours, not from values the decoder can reproduce, so decompression,  */
+/* which can only predict from its own reconstructions, drifts; balance      */
+/* points (stored values, "equilibrium points") stop the drift.  Readings:   */
+/*  - a value's real code is (t, K): t = L32(|x|) * inv in steps and K the  */
+/*    factor offset of its sign class, for non-zero values that pass the     */
+/*    bound check of the bound-safe transform; any other value (zero,        */
+/*    subnormal, a failed check) has t = 0 and K = its integer code and is   */
+/*    always stored as a balance point;                                      */
+/*  - values enter the predictor centred on the block anchor:               */
+/*    c = (t - t_a) + (K - K_a), clamped to +-(2^24 - 1);                   */
+/*  - Lorenzo sums w_i c_i in stencil order; the FP32 perceptron takes       */
+/*    u_i = c_i 2^-s and returns o 2^s, as for integer inputs;              */
+/*  - residual k = rint(c - pred); the code is k + R when |k| <= R - 1,     */
+/*    else 0 (balance point); with eq_period > 0, every eq_period-th point  */
+/*    of the block in raster order is a deliberate balance point;           */
+/*  - every block uses the given predictor (no per-block Lorenzo choice);   */
+/*  - decoding walks each block serially in raster order: c' = pred(c'_nb)  */
+/*    + k, z = c' + t_a, q' = rint(z) + K_a, and the value is 0 in the zero  */
+/*    class, else the sign of the class times E32((z + K_a - K_cls) step).   */
+/* ------------------------------------------------------------------------- */
+static void o_realcode32(float x, const orc_consts* c, float* t, int64_t* K) {
+  int32_t q;
+  int ok;
+  orc_transform32(x, c, &q, &ok);
+  if (x != 0.0f && ok) {
+    *t = orc_L32(fabsf(x)) * c->inv32;
+    *K = x > 0.0f ? c->Kp : c->Kn;
+  } else {
+    *t = 0.0f;
+    *K = q;
+  }
+}
+
+static int o_lit_codable(float x, const orc_consts* c) {
+  int32_t q;
+  int ok;
+  orc_transform32(x, c, &q, &ok);
+  return x != 0.0f && ok;
+}
+
+static float o_cen(float t, int64_t K, float ta, int64_t Ka) { return (t - ta) + (float)(K - Ka); }
+
+static float o_clampf(float v) { return v > 16777215.0f ? 16777215.0f : (v < -16777215.0f ? -16777215.0f : v); }
+
+/* FP32 perceptron on real centred inputs: the arithmetic of orc_mlp_fwd32
+ * with u_i = v_i 2^-s. */
+static float o_mlp_fwd32f(const float* w, int k, int h1, int h2, int s_in, const float* v) {
+  float sig = ldexpf(1.0f, -s_in);
+  float u[32];
+  for (int i = 0; i < k; i++) u[i] = v[i] * sig;
+  const float* W1 = w;
+  const float* b1 = W1 + h1 * k;
+  float a1[O_MAXH];
+  for (int j = 0; j < h1; j++) {
+    float acc = b1[j];
+    for (int i = 0; i < k; i++) acc = fmaf(W1[j * k + i], u[i], acc);
+    a1[j] = acc >= 0.0f ? acc : acc * O_ALPHA;
+  }
+  const float* p = b1 + h1;
+  float* hl = a1;
+  int nl = h1;
+  float a2[O_MAXH];
+  if (h2 > 0) {
+    const float* W2 = p;
+    const float* b2 = W2 + h2 * h1;
+    for (int j = 0; j < h2; j++) {
+      float acc = b2[j];
+      for (int i = 0; i < h1; i++) acc = fmaf(W2[j * h1 + i], a1[i], acc);
+      a2[j] = acc >= 0.0f ? acc : acc * O_ALPHA;
+    }
+    p = b2 + h2;
+    hl = a2;
+    nl = h2;
+  }
+  const float* W3 = p;
+  float o = W3[nl];
+  for (int j = 0; j < nl; j++) o = fmaf(W3[j], hl[j], o);
+  return o * ldexpf(1.0f, s_in);
+}
+
+/* The prediction of point (lz, ly, lx) of an e0 x e1 x e2 block from the
+ * centred real values cv (raster order) of its causal in-block neighbours. */
+static float o_lit_pred(const float* cv, int lz, int ly, int lx, int e0, int e1, int e2, const float* w, int k, int h1,
+                        int h2, int s_in) {
+  if (w) {
+    float in[13];
+    for (int i = 0; i < k; i++) {
+      int dz, dy, dx;
+      o_stencil(k, i, &dz, &dy, &dx);
+      int qz = lz + dz, qy = ly + dy, qx = lx + dx;
+      in[i] = (qz >= 0 && qy >= 0 && qx >= 0 && qz < e0 && qy < e1 && qx < e2) ? cv[(qz * e1 + qy) * e2 + qx] : 0.0f;
+    }
+    return o_mlp_fwd32f(w, k, h1, h2, s_in, in);
+  }
+  float acc = 0.0f;
+  for (int i = 0; i < 7; i++) {
+    int qz = lz + O_S7[i][0], qy = ly + O_S7[i][1], qx = lx + O_S7[i][2];
+    float v = (qz >= 0 && qy >= 0 && qx >= 0) ? cv[(qz * e1 + qy) * e2 + qx] : 0.0f;
+    acc = acc + (float)O_LZ7[i] * v;
+  }
+  return acc;
+}
+
+static int64_t o_lit_round(float r) {
+  if (r != r) return 0;
+  if (r > 1073741824.0f) r = 1073741824.0f;
+  if (r < -1073741824.0f) r = -1073741824.0f;
+  return (int64_t)rintf(r);
+}
+
+/* Codes of one block under the literal selection: x in raster order. */
+static void o_block_literal(const float* xb, int e0, int e1, int e2, const orc_consts* c, const float* w, int k, int h1,
+                            int h2, int s_in, int64_t R, int eq_period, float* cv, uint16_t* cs) {
+  int np = e0 * e1 * e2;
+  float ta;
+  int64_t Ka;
+  o_realcode32(xb[0], c, &ta, &Ka);
+  for (int j = 0; j < np; j++) {
+    float t;
+    int64_t K;
+    o_realcode32(xb[j], c, &t, &K);
+    cv[j] = o_clampf(o_cen(t, K, ta, Ka));
+  }
+  for (int lz = 0; lz < e0; lz++)
+    for (int ly = 0; ly < e1; ly++)
+      for (int lx = 0; lx < e2; lx++) {
+        int j = (lz * e1 + ly) * e2 + lx;
+        if (j == 0) continue;
+        if (!o_lit_codable(xb[j], c) || (eq_period > 0 && j % eq_period == 0)) { cs[j] = 0; continue; }
+        float pr = o_lit_pred(cv, lz, ly, lx, e0, e1, e2, w, k, h1, h2, s_in);
+        int64_t kk = o_lit_round(cv[j] - pr);
+        int64_t a = kk < 0 ? -kk : kk;
+        cs[j] = (uint16_t)(a <= R - 1 ? kk + R : 0);
+      }
+}
+
+/* The literal decoder's value of a centred real code cc (anchor (ta, Ka)). */
+static float o_lit_value(float cc, float ta, int64_t Ka, const orc_consts* c) {
+  float z = cc + ta;
+  int64_t q = o_lit_round(z) + Ka;
+  if (q > 2147483647LL) q = 2147483647LL;
+  if (q < -2147483647LL) q = -2147483647LL;
+  int cl = o_class((int32_t)q, c);
+  if (cl == 0) return 0.0f;
+  int64_t Kc = cl == 1 ? c->Kp : c->Kn;
+  float nr = z + (float)(Ka - Kc);
+  float a = orc_E32(nr * c->step32);
+  return cl == 1 ? a : -a;
+}
+
 /* A given codebook (sym | len << 16 per entry, in the order the container
  * stores it): symbols below 2^m and distinct, lengths 1..24 and never
  * decreasing along the list (the canonical construction needs that order),
@@ -935,6 +1088,8 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
   if (use_nn && (k != 7 && k != 13)) return ORC_ERR_ARG;
   if (use_nn && (p->h1 < 1 || p->h1 > O_MAXH || p->h2 < 0 || p->h2 > O_MAXH)) return ORC_ERR_ARG;
   if (use_nn && (p->s_in < 0 || p->s_in > 30)) return ORC_ERR_ARG;
+  int lit = p->literal != 0;
+  if (lit && (dtype != ORC_F32 || use_q || use_64 || p->codebook || p->eq_period < 0)) return ORC_ERR_ARG;
   o_geom g;
   if (o_geom_make(dims, p->block, &g)) return ORC_ERR_ARG;
   uint64_t n = dims[0] * dims[1] * dims[2];
@@ -1000,9 +1155,24 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
               dqb[j] = dq[ig];
               okb[j] = okv[ig];
             }
-        int usen = o_block(dqb, okb, e0, e1, e2, p, use_nn, use_q, use_64, k, R, vc, vt, cz, cn);
+        int usen;
+        if (lit) {
+          float* xb = (float*)malloc(sizeof(float) * (size_t)np);
+          float* cvf = (float*)malloc(sizeof(float) * (size_t)np);
+          for (int lz = 0; lz < e0; lz++)
+            for (int ly = 0; ly < e1; ly++)
+              for (int lx = 0; lx < e2; lx++)
+                xb[(lz * e1 + ly) * e2 + lx] = ((const float*)x)[((o0 + lz) * dims[1] + (o1 + ly)) * dims[2] + (o2 + lx)];
+          o_block_literal(xb, e0, e1, e2, &c, use_nn ? p->weights : NULL, k, p->h1, p->h2, p->s_in, R, p->eq_period,
+                          cvf, cn);
+          free(cvf);
+          free(xb);
+          usen = use_nn;
+        } else {
+          usen = o_block(dqb, okb, e0, e1, e2, p, use_nn, use_q, use_64, k, R, vc, vt, cz, cn);
+        }
         nnf[bi] = (uint8_t)usen;
-        const uint16_t* cs = usen ? cn : cz;
+        const uint16_t* cs = (usen || lit) ? cn : cz;
         int no = 1;  /* the anchor */
         for (int j = 1; j < np; j++) {
           /* a code outside a given codebook is stored as a balance point */
@@ -1088,7 +1258,8 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
   put64(out + 192, off_bn); put64(out + 200, off_ov); put64(out + 208, off_st);
   put64(out + 216, total);
   put32(out + 224, (uint32_t)nw);
-  put32(out + 228, fixed_cb ? ORC_FLAG_STREAM_FIRST : 0u);
+  put32(out + 228, (fixed_cb ? ORC_FLAG_STREAM_FIRST : 0u) | (lit ? ORC_FLAG_LITERAL : 0u));
+  put32(out + 232, lit ? (uint32_t)p->eq_period : 0u);
   put32(out + 252, orc_crc32(out, 252));
 
   /* sections */
@@ -1270,6 +1441,13 @@ int orc_decompress(const uint8_t* in, uint64_t in_size, void* xo, uint64_t cap_e
   }
   int32_t* dq = (int32_t*)malloc(sizeof(int32_t) * g.bvol);
   int32_t* vc = (int32_t*)malloc(sizeof(int32_t) * g.bvol);
+  /* the paper-literal selection: real centred values, walked serially with drift */
+  uint32_t flags = get32(in + 228);
+  int lit = (flags & ORC_FLAG_LITERAL) != 0;
+  if (lit && (dtype != ORC_F32 || pred == ORC_PRED_MLP_BF16 || pred == ORC_PRED_MLP64)) ret = ORC_ERR_CORRUPT;
+  float* cvf = (float*)malloc(sizeof(float) * g.bvol);
+  float ta = 0.0f;
+  int64_t Ka = 0;
   uint64_t bp = 0, oi = 0;
   uint64_t sbits = swords * 32ull;
   for (uint64_t b = 0; b < nblocks && ret == ORC_OK; b++) {
@@ -1305,6 +1483,26 @@ int orc_decompress(const uint8_t* in, uint64_t in_size, void* xo, uint64_t cap_e
               if (cnt[l] && code - first[l] < cnt[l]) { sym = sorted[offs[l] + code - first[l]]; found = 1; break; }
             }
             if (!found) { ret = ORC_ERR_CORRUPT; break; }
+          }
+          if (lit) {
+            float xv;
+            if (j == 0 || sym == 0) {
+              if (oi >= oend) { ret = ORC_ERR_CORRUPT; break; }
+              memcpy(&xv, in + off_ov + ts * oi, 4);
+              oi++;
+              float t;
+              int64_t K;
+              o_realcode32(xv, &c, &t, &K);
+              if (j == 0) { ta = t; Ka = K; }
+              cvf[j] = o_clampf(o_cen(t, K, ta, Ka));
+            } else {
+              float pr = o_lit_pred(cvf, lz, ly, lx, e0, e1, e2, usen ? wts : NULL, k, h1, h2, s_in);
+              float cc = pr + (float)((int64_t)sym - R);
+              cvf[j] = o_clampf(cc);
+              xv = o_lit_value(cc, ta, Ka, &c);
+            }
+            ((float*)xo)[ig] = xv;
+            continue;
           }
           int32_t q;
           if (j == 0 || sym == 0) {
@@ -1357,7 +1555,7 @@ int orc_decompress(const uint8_t* in, uint64_t in_size, void* xo, uint64_t cap_e
         }
     if (ret == ORC_OK && (bp != bend || oi != oend)) ret = ORC_ERR_CORRUPT;
   }
-  free(vc); free(dq); free(sorted); free(lens); free(wts); free(qn);
+  free(cvf); free(vc); free(dq); free(sorted); free(lens); free(wts); free(qn);
   return ret;
 }
 

@@ -54,11 +54,18 @@ typedef struct {
   const uint32_t* codebook; /* sample codebook (sym | len << 16, container order) or NULL: see
                                orc_compress; NULL builds the code of the field's own histogram */
   int codebook_n;        /* entries of codebook */
+  int literal;           /* 1: the paper-literal data selection (Section IV.D), float32 only, FP32
+                            perceptron or Lorenzo: see orc_compress */
+  int eq_period;         /* literal mode: every eq_period-th point of a block (raster order) is a
+                            deliberate equilibrium point; 0 = none */
 } orc_params;
 
 /* container flag (header offset 228): the bitstream section precedes the
  * balance-point values (the layout of a compression with a sample codebook) */
 #define ORC_FLAG_STREAM_FIRST 1u
+/* container flag: codes of the paper-literal data selection (decoded serially, with drift);
+ * header offset 232 holds the equilibrium-point period */
+#define ORC_FLAG_LITERAL 4u
 
 typedef struct {
   int32_t* dq;           /* [N] integer log codes, field order */

@@ -107,6 +107,11 @@ int check_params(const size_t dims[3], int dtype, const pc_params* p, Geo& g, in
   if (!make_geo(dims, p->block, g)) return PC_ERR_ARG;
   if (!shape_supported(p->block)) return PC_ERR_ARG;
   if (p->h_codebook && !codebook_ok(p->h_codebook, p->codebook_n, p->m)) return PC_ERR_ARG;
+  // the paper-literal selection: float32, Lorenzo or the FP32 perceptron with weights, two passes
+  if (p->literal && (dtype != PC_F32 || p->eq_period < 0 || p->h_codebook ||
+                     (p->pred != PC_PRED_LORENZO && !(p->pred == PC_PRED_MLP_FP32 && p->h_weights))))
+    return PC_ERR_ARG;
+  if (!p->literal && p->eq_period != 0) return PC_ERR_ARG;
   mode = p->pred == PC_PRED_MLP_FP32 ? 1 : (p->pred == PC_PRED_MLP_BF16 ? 2 : 0);
   if (p->pred != PC_PRED_LORENZO && p->pred != PC_PRED_MLP_FP32 && p->pred != PC_PRED_MLP_BF16) return PC_ERR_ARG;
   nw = 0;
@@ -219,6 +224,7 @@ uint64_t rd64(const uint8_t* p) { uint64_t v; memcpy(&v, p, 8); return v; }
 // Parsed, validated header.
 struct Hdr {
   int dtype, pred, m, stencil, h1, h2, s_in, nw, block[3];
+  int literal;
   size_t dims[3];
   unsigned int n_used;
   unsigned long long nblocks, n_out, swords, off_cb, off_bb, off_bn, off_ov, off_st, total;
@@ -260,7 +266,10 @@ int parse_header(const uint8_t* h, size_t n, Hdr& H, Geo& g) {
   H.total = rd64(h + 216);
   H.nw = (int)rd32(h + 224);
   const unsigned int flags = rd32(h + 228);
-  if (flags & ~kFlagStreamFirst) return PC_ERR_CORRUPT;
+  if (flags & ~(kFlagStreamFirst | kFlagLiteral)) return PC_ERR_CORRUPT;
+  H.literal = (flags & kFlagLiteral) != 0;
+  if (H.literal && (H.dtype != PC_F32 || (H.pred != 0 && H.pred != 1) || (flags & kFlagStreamFirst)))
+    return PC_ERR_CORRUPT;
   if (H.dtype != PC_F32 && H.dtype != PC_F64) return PC_ERR_CORRUPT;
   if (H.m < 2 || H.m > 16) return PC_ERR_CORRUPT;
   for (int i = 0; i < 3; ++i)
@@ -467,6 +476,7 @@ struct FieldPlan {
   HuffScratch hs;
   const long long* h_qnet;  // host network to copy into the container (fixed-point form)
   const long long* qnet;    // its device copy in the container's weights section
+  int literal, eq_period;  // the paper-literal selection
   // single pass (a given codebook)
   bool sp;
   const unsigned int* h_cb;
@@ -501,7 +511,8 @@ int plan_field(FieldPlan& F, const void* d_field, const size_t dims[3], int dtyp
   hi.s_in = p->s_in;
   hi.nw = nw;
   hi.wsz = mode == 2 ? 8 : 4;
-  hi.flags = p->h_codebook ? kFlagStreamFirst : 0u;
+  hi.flags = (p->h_codebook ? kFlagStreamFirst : 0u) | (p->literal ? kFlagLiteral : 0u);
+  hi.eq_period = p->literal ? p->eq_period : 0;
   hi.eb = p->eb_rel;
   hi.off_cb = al16(kHdr + (unsigned long long)hi.wsz * nw);
   hi.cap = out_cap;
@@ -538,6 +549,8 @@ int plan_field(FieldPlan& F, const void* d_field, const size_t dims[3], int dtyp
   // section, where the kernels read it
   F.h_qnet = mode == 2 ? p->h_qnet : nullptr;
   F.qnet = mode == 2 ? reinterpret_cast<const long long*>(F.out + kHdr) : nullptr;
+  F.literal = p->literal;
+  F.eq_period = p->eq_period;
   F.sp = p->h_codebook != nullptr;
   F.h_cb = p->h_codebook;
   F.cb_n = p->codebook_n;
@@ -686,6 +699,7 @@ int plan_dec(DecPlan& P, const uint8_t* hbuf, size_t pre, const void* d_in, size
   di.s_in = H.s_in;
   di.usenn_any = H.pred != 0;
   di.qmode = H.pred == 2;
+  di.literal = H.literal;
   // the fixed-point network is read in place from the container
   di.qnet = H.pred == 2 ? reinterpret_cast<const long long*>(static_cast<const uint8_t*>(d_in) + kHdr) : nullptr;
   di.n_used = H.n_used;
@@ -1053,7 +1067,10 @@ int pc_compress(const void* d_field, const size_t dims[3], int dtype, const pc_p
   const int nsm = sm_count();
   if (nsm <= 0) return PC_ERR_CUDA;
   int r = launch_head(F, s, nsm);
-  if (!r) {
+  if (!r && F.literal) {
+    r = launch_lit_compress(static_cast<const float*>(F.x), F.g, F.stp, F.tabs, mlp, mode, F.eq_period, F.m, F.codes,
+                            F.nnflag, F.nout, F.hist, nsm, s);
+  } else if (!r) {
     const CJob job = job_of(F);
     unsigned long long* next = F.sp ? F.next : nullptr;
     r = dtype == PC_F32 ? launch_compress<float>(&job, 1, mode, mlp, nsm, s, next)
@@ -1079,7 +1096,7 @@ int pc_compress_batch_workspace_size(int nfields, const size_t* dims, const int*
     int mode, nw;
     int st = check_params(dims + 3 * i, dtypes[i], params + i, g, mode, nw);
     if (st) return st;
-    if (wants_training(params + i)) return PC_ERR_ARG;
+    if (wants_training(params + i) || params[i].literal) return PC_ERR_ARG;
     ws += up(comp_layout(g, params[i].m, params[i].h_codebook != nullptr, dtypes[i] == PC_F64 ? 8 : 4).total);
     ob += up(pc_compress_bound(dims + 3 * i, dtypes[i], params + i));
   }

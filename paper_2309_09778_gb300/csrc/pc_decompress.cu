@@ -856,6 +856,10 @@ int launch_decompress(const uint8_t* in, const Geo& g, const DecInfo& di, const 
     k_huff_decode<<<(unsigned int)((g.nblocks + kDecThreads - 1) / kDecThreads), kDecThreads, 0, s>>>(g, in, di, ds);
   }
   if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
+  if (di.literal) {
+    if constexpr (sizeof(T) == 4) return launch_lit_decode(in, g, di, ds, mlp, out, nsm, s);
+    return PC_ERR_ARG;
+  }
   const int b0 = g.b[0], b1 = g.b[1], b2 = g.b[2];
 #define PC_SHAPE(A, B, C) \
   if (b0 == A && b1 == B && b2 == C) return launch_r_shape<T, A, B, C>(in, g, di, ds, mlp, out, nsm, s);

@@ -56,7 +56,8 @@ __device__ __forceinline__ int team_sum(int v, int* slot) {
 struct HdrInfo {
   int dtype, pred, stencil, h1, h2, m, s_in, nw;
   int wsz;                    // bytes per weights-section entry: 4 (f32 weights) or 8 (int64 fixed-point network)
-  unsigned int flags;         // header flags (kFlagStreamFirst)
+  unsigned int flags;         // header flags (kFlagStreamFirst, kFlagLiteral)
+  int eq_period;              // literal selection: equilibrium-point period (header offset 232)
   double eb;
   unsigned long long off_cb;  // = al16(256 + wsz nw)
   unsigned long long cap;     // output capacity in bytes
@@ -116,6 +117,9 @@ int launch_stats_consts(const void* x, unsigned long long n, State* st, Tabs* ta
 // Container flag (header offset 228): the bitstream precedes the balance
 // values, the layout that single-pass compression writes.
 constexpr unsigned int kFlagStreamFirst = 1u;
+// Container flag: codes of the paper-literal data selection (Section IV.D;
+// decoded with drift); header offset 232 holds the equilibrium-point period.
+constexpr unsigned int kFlagLiteral = 4u;
 
 // Bricks of a field: G blocks along x per brick (BrickShape), rows of bricks.
 inline long long bricks_of(const Geo& g) {
@@ -197,6 +201,7 @@ int launch_pack(const T* x, const Geo& g, const uint16_t* codes, const uint8_t* 
 // Decompression.
 struct DecInfo {
   int dtype, m, stencil, h1, h2, s_in, usenn_any, qmode;
+  int literal;            // codes of the paper-literal data selection (float32 only)
   const long long* qnet;  // fixed-point network in the container (qmode), else null
   unsigned int n_used;
   unsigned long long n_out, swords;
@@ -268,5 +273,13 @@ int launch_quantize(const T* x, const Geo& g, const State* st, const Tabs* tabs,
 template <typename T>
 int launch_decompress(const uint8_t* in, const Geo& g, const DecInfo& di, const DecScratch& ds, const Mlp& mlp,
                       T* out, int nsm, cudaStream_t s);
+// The paper-literal data selection (Section IV.D, float32): codes, flags,
+// balance counts and histogram of a field (mode 0 Lorenzo, 1 FP32 perceptron);
+// and the drifting decoder that follows the Huffman decoder.
+int launch_lit_compress(const float* x, const Geo& g, const State* st, const Tabs* tabs, const Mlp& mlp, int mode,
+                        int eq_period, int m, uint16_t* codes, uint8_t* nnflag, uint32_t* nout,
+                        unsigned long long* hist, int nsm, cudaStream_t s);
+int launch_lit_decode(const uint8_t* in, const Geo& g, const DecInfo& di, const DecScratch& ds, const Mlp& mlp,
+                      float* out, int nsm, cudaStream_t s);
 
 }  // namespace pc

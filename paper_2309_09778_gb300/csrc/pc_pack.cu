@@ -152,6 +152,7 @@ __device__ void write_header(uint8_t* s_hdr, unsigned int* s_crc, const State& c
     st_u64(hd + 216, total);
     st_u32(hd + 224, (unsigned int)hi.nw);
     st_u32(hd + 228, hi.flags);
+    st_u32(hd + 232, (unsigned int)hi.eq_period);
     unsigned int crc = 0xFFFFFFFFu;
     for (int i = 0; i < 252; ++i) crc = s_crc[(crc ^ hd[i]) & 0xFFu] ^ (crc >> 8);
     st_u32(hd + 252, crc ^ 0xFFFFFFFFu);
