@@ -827,6 +827,68 @@ def select_report(torch, pc, w, dev):
     return out
 
 
+def literal_report(torch, pc, w, dev):
+    """The paper-literal data selection (Section IV.D, experimental): every point predicted from the true
+    values of its neighbours, the decoder drifting on its own reconstructions.  For Lorenzo and the chosen
+    FP32 network, with no, sparse and dense deliberate equilibrium points: bits/value, the drift (largest
+    relative error over eb, share of points beyond eb and beyond 1.5 eb) and device throughput, beside the
+    bound-safe reading; then the acceptance rule over the 16 trained models (a model counts when its
+    decoded field stays within 1.5 eb everywhere)."""
+    spec, fields, infos = w["spec"], w["spec"]["_fields"], w["infos"]
+    d = fields[0]
+    if d.dtype != torch.float32:
+        return None
+    k, h1, h2, eb = spec["k"], spec["h1"], spec["h2"], spec["eb"]
+    info = infos[0]
+    dd = d.double()
+    nz = dd != 0
+
+    def run(p):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        blob = pc.compress(d, p)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        y = pc.decompress(blob)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        e = ((y.double() - dd).abs() / dd.abs())[nz]
+        nb = d.numel() * 4
+        return {"bits_per_value": 8.0 * blob.numel() / d.numel(), "max_rel_err_over_eb": float(e.max()) / eb,
+                "frac_beyond_eb": float((e > eb).double().mean()), "frac_beyond_1p5eb": float((e > 1.5 * eb).double().mean()),
+                "compress_gbs": nb / (t1 - t0) / 1e9, "decompress_gbs": nb / (t2 - t1) / 1e9}
+
+    out = {"field": list(d.shape), "eb_rel": eb}
+    preds = [("lorenzo", None)]
+    if info["w"] is not None:
+        preds.append((f"mlp_fp32_s{k}_{h1}x{h2}", info["w"]))
+    for name, wt in preds:
+        kw = dict(pred=pc.PC_PRED_MLP_FP32, stencil=k, hidden=(h1, h2), s_in=info["s_in"], weights=wt) if wt is not None \
+            else {}
+        run(pc.make_params(eb, BLOCK, literal=True, **kw))  # warm-up
+        out[name] = {"bound_safe": run(pc.make_params(eb, BLOCK, **kw))}
+        for eq in (0, 64, 16):
+            out[name][f"literal_eq{eq}"] = run(pc.make_params(eb, BLOCK, literal=True, eq_period=eq, **kw))
+    # the 1.5x acceptance rule over the trained models
+    lrs, lams = pc.default_grid()
+    thr32 = thr_for(tuple(d.shape), spec["samples"])
+    tp = pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_FP32, stencil=k, hidden=(h1, h2))
+    ws = torch.empty(pc.pc_train_workspace_size(tuple(d.shape), pc.PC_F32, tp, thr32, lrs.size), dtype=torch.uint8,
+                     device=dev)
+    W, s_in, _, _ = pc.pc_train(d, tp, 0, thr32, lrs, lams, ws)
+    del ws
+    acc = []
+    for i in range(W.shape[0]):
+        r = run(pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_FP32, stencil=k, hidden=(h1, h2), s_in=s_in,
+                               weights=W[i], literal=True))
+        acc.append({"model": i, "bits_per_value": r["bits_per_value"], "max_rel_err_over_eb": r["max_rel_err_over_eb"],
+                    "accepted": r["max_rel_err_over_eb"] <= 1.5})
+    ok = [a for a in acc if a["accepted"]]
+    out["acceptance_1p5eb"] = {"models": acc, "accepted": len(ok),
+                               "chosen": min(ok, key=lambda a: a["bits_per_value"])["model"] if ok else None}
+    return out
+
+
 def summary(w):
     res = w["res"]
     keep = ("compress_gbs", "decompress_gbs", "bits_per_value", "bound_held", "compress_ms", "decompress_ms",
@@ -992,6 +1054,7 @@ def main():
             if name == "grf100x500x500_f32" and not args.no_forms:
                 secondary[name]["forms"] = form_compare(torch, pc, w, args, stream, flush)
                 secondary[name]["selection_by_simulated_compression"] = select_report(torch, pc, w, dev)
+                secondary[name]["literal_data_selection"] = literal_report(torch, pc, w, dev)
             w["spec"].pop("_fields")
             del w
             torch.cuda.empty_cache()
