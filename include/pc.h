@@ -89,6 +89,8 @@ typedef struct {
                              guaranteed; the container is flagged and decodes with the drift */
   int eq_period;          /* literal mode: every eq_period-th point of a block (raster order) is stored
                              as a deliberate equilibrium point; 0 = none */
+  int lossless;           /* 1: the fourth SZ stage of Section IV.A, a lossless LZ77-style pass over the
+                             bitstream bytes in independent 16 KiB chunks (not with h_codebook) */
 } pc_params;
 /*
  * Learned predictor trained inside pc_compress (Section IV.C, V): with

@@ -52,7 +52,7 @@ class Params(C.Structure):
     _fields_ = [("eb", C.c_double), ("block", C.c_int * 3), ("pred", C.c_int), ("stencil", C.c_int),
                 ("h1", C.c_int), ("h2", C.c_int), ("m", C.c_int), ("s_in", C.c_int),
                 ("weights", C.c_void_p), ("qnet", C.c_void_p), ("codebook", C.c_void_p), ("codebook_n", C.c_int),
-                ("literal", C.c_int), ("eq_period", C.c_int)]
+                ("literal", C.c_int), ("eq_period", C.c_int), ("lossless", C.c_int)]
 
 
 class Dump(C.Structure):
@@ -106,6 +106,12 @@ def lib():
             L.orc_sample_codebook_for.argtypes = [C.c_void_p, u64p, C.c_int, C.c_double, C.POINTER(C.c_int),
                                                   C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
                                                   C.c_uint64, C.c_uint32, C.c_int, C.c_void_p]
+            L.orc_lz_bound.restype = C.c_uint64
+            L.orc_lz_bound.argtypes = [C.c_uint64]
+            L.orc_lz_encode.restype = C.c_uint64
+            L.orc_lz_encode.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p]
+            L.orc_lz_decode.restype = C.c_int
+            L.orc_lz_decode.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint64]
             L.orc_coverage_m.restype = C.c_int
             L.orc_coverage_m.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_uint64, C.c_double]
@@ -385,14 +391,15 @@ def compress_bound(shape3, dtype: int, block, m: int = 16, nweights: int = 0) ->
 
 def compress(x: np.ndarray, eb: float, block=(8, 8, 8), weights=None, stencil=7, h1=16, h2=16,
              m: int = 16, s_in: int = 0, dump: bool = False, qnet=None, fp64: bool = False, codebook=None,
-             literal: bool = False, eq_period: int = 0):
+             literal: bool = False, eq_period: int = 0, lossless: bool = False):
     """Compress with the oracle.  Returns (status, bytes[, dump dict]).  `qnet` selects the
     fixed-point (BF16) perceptron form instead of the FP32 weights; fp64=True evaluates the
     FP32 weights in FP64 (the reporting predictor, which only the oracle encodes with).
     `codebook` (uint32 list, sym | len << 16) compresses with that sample codebook: codes
     outside it become balance points and the stream precedes the balance values.
     literal=True: the paper-literal data selection (predict from true values; float32 only),
-    with a deliberate equilibrium point every eq_period points of each block (0: none)."""
+    with a deliberate equilibrium point every eq_period points of each block (0: none).
+    lossless=True: the lossless stage over the bitstream bytes."""
     x = np.ascontiguousarray(x)
     dims = _dims(x)
     dt = _dtype_code(x)
@@ -411,6 +418,7 @@ def compress(x: np.ndarray, eb: float, block=(8, 8, 8), weights=None, stencil=7,
     p = _params(eb, block, pred, stencil, h1, h2, m, s_in, w, q, cb)
     p.literal = int(bool(literal))
     p.eq_period = int(eq_period)
+    p.lossless = int(bool(lossless))
     cap = compress_bound(tuple(dims), dt, block, m, nw)
     out = np.zeros(cap, np.uint8)
     size = C.c_uint64()
@@ -587,6 +595,23 @@ def sample_codebook_for(x: np.ndarray, eb: float, block=(8, 8, 8), k=7, h1=16, h
                                       None if w is None else _p(w), m, seed, thr32, int(bool(span_fill)), _p(out))
     assert n > 0, n
     return out[:n].copy()
+
+
+def lz_encode(data: bytes) -> bytes:
+    """The lossless stage's section for a byte string (length a multiple of 4)."""
+    src = np.frombuffer(bytes(data), np.uint8).copy()
+    cap = lib().orc_lz_bound(src.size)
+    out = np.zeros(cap, np.uint8)
+    n = lib().orc_lz_encode(_p(src) if src.size else None, src.size, _p(out))
+    return out[:n].tobytes()
+
+
+def lz_decode(section: bytes, raw_bytes: int):
+    """Inverse of lz_encode: (status, bytes)."""
+    sec = np.frombuffer(bytes(section), np.uint8).copy()
+    out = np.zeros(max(raw_bytes, 1), np.uint8)
+    st = lib().orc_lz_decode(_p(sec), sec.size, _p(out), raw_bytes)
+    return st, out[:raw_bytes].tobytes()
 
 
 def coverage_m(w, k, h1, h2, s_in, inp, tg, use, eb) -> int:

@@ -800,6 +800,150 @@ static uint32_t get32(const uint8_t* p) { uint32_t v = 0; for (int i = 0; i < 4;
 static uint64_t get64(const uint8_t* p) { uint64_t v = 0; for (int i = 0; i < 8; i++) v |= (uint64_t)p[i] << (8 * i); return v; }
 static uint64_t al16(uint64_t x) { return (x + 15u) & ~(uint64_t)15u; }
 
+/* ------------------------------------------------------------------------- */
+/* Section IV.A, the fourth SZ stage: a lossless pass over the bitstream      */
+/* bytes (the paper names it; Algorithm 1 does not use it).  This build's     */
+/* stage is an LZ77-style matcher over independent chunks of ORC_LZ_CHUNK    */
+/* bytes, so that every chunk codes and decodes on its own:                  */
+/*  - tokens: a control byte c < 128 is followed by c + 1 literal bytes; a   */
+/*    control byte c >= 128 is a match of (c - 128) + 4 bytes (4..131) at a  */
+/*    distance d (1..chunk) given by the next two bytes, little-endian;      */
+/*  - greedy parse: at position i (with 4 bytes left) the hash of the 4      */
+/*    bytes at i, h = (b0 | b1 << 8 | b2 << 16 | b3 << 24) * 2654435761 >>  */
+/*    20 (Knuth's multiplicative hashing), names the last position that      */
+/*    started a parse step with the same hash; if at least 4 bytes match     */
+/*    there, the longest match up to 131 bytes is taken, else one literal;  */
+/*    the table then names i; literals are emitted in runs of up to 128 just */
+/*    before the next match or the chunk's end;                              */
+/*  - a chunk whose tokens are not shorter than the chunk is stored as is.   */
+/* Section: u32 chunk count, u32 chunk bytes, u64 raw bytes, then per chunk  */
+/* u32 (coded bytes | stored << 31), 16-byte aligned, then the chunks'      */
+/* bytes back to back.                                                        */
+/* ------------------------------------------------------------------------- */
+#define O_LZ_HB 12
+static uint32_t o_lz_hash(const uint8_t* p) {
+  uint32_t v = (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+  return (v * 2654435761u) >> (32 - O_LZ_HB);
+}
+
+static size_t o_lz_lits(const uint8_t* src, size_t a, size_t b, uint8_t* dst, size_t o) {
+  while (a < b) {
+    size_t r = b - a < 128 ? b - a : 128;
+    dst[o++] = (uint8_t)(r - 1);
+    memcpy(dst + o, src + a, r);
+    o += r;
+    a += r;
+  }
+  return o;
+}
+
+/* tokens of one chunk (dst holds n + n / 128 + 1 bytes); returns their size */
+static size_t o_lz_chunk(const uint8_t* src, size_t n, uint8_t* dst) {
+  uint16_t tab[1 << O_LZ_HB];
+  memset(tab, 0, sizeof(tab));
+  size_t i = 0, lit0 = 0, o = 0;
+  while (i < n) {
+    size_t L = 0, d = 0;
+    if (i + 4 <= n) {
+      uint32_t h = o_lz_hash(src + i);
+      size_t cand = tab[h];
+      tab[h] = (uint16_t)(i + 1);
+      if (cand) {
+        size_t j = cand - 1;
+        while (i + L < n && L < 131 && src[j + L] == src[i + L]) L++;
+        if (L >= 4) d = i - j;
+        else L = 0;
+      }
+    }
+    if (L) {
+      o = o_lz_lits(src, lit0, i, dst, o);
+      dst[o++] = (uint8_t)(128 + (L - 4));
+      dst[o++] = (uint8_t)(d & 0xFF);
+      dst[o++] = (uint8_t)(d >> 8);
+      i += L;
+      lit0 = i;
+    } else {
+      i++;
+    }
+  }
+  return o_lz_lits(src, lit0, n, dst, o);
+}
+
+uint64_t orc_lz_bound(uint64_t raw) {
+  uint64_t nch = (raw + ORC_LZ_CHUNK - 1) / ORC_LZ_CHUNK;
+  return al16(16 + 4 * nch) + raw + 16;
+}
+
+uint64_t orc_lz_encode(const uint8_t* src, uint64_t raw, uint8_t* out) {
+  uint64_t nch = (raw + ORC_LZ_CHUNK - 1) / ORC_LZ_CHUNK;
+  put32(out, (uint32_t)nch);
+  put32(out + 4, ORC_LZ_CHUNK);
+  put64(out + 8, raw);
+  uint64_t o = al16(16 + 4 * nch);
+  memset(out + 16, 0, o - 16);
+  uint8_t* tmp = (uint8_t*)malloc(ORC_LZ_CHUNK + ORC_LZ_CHUNK / 128 + 8);
+  for (uint64_t c = 0; c < nch; c++) {
+    uint64_t a = c * ORC_LZ_CHUNK;
+    size_t n = (size_t)(raw - a < ORC_LZ_CHUNK ? raw - a : ORC_LZ_CHUNK);
+    size_t sz = o_lz_chunk(src + a, n, tmp);
+    if (sz >= n) {
+      memcpy(out + o, src + a, n);
+      put32(out + 16 + 4 * c, (uint32_t)n | 0x80000000u);
+      o += n;
+    } else {
+      memcpy(out + o, tmp, sz);
+      put32(out + 16 + 4 * c, (uint32_t)sz);
+      o += sz;
+    }
+  }
+  free(tmp);
+  return o;
+}
+
+/* Decode a section of sec_bytes into raw bytes; ORC_ERR_CORRUPT on any
+ * inconsistency (sizes, token bounds, distances). */
+int orc_lz_decode(const uint8_t* sec, uint64_t sec_bytes, uint8_t* dst, uint64_t raw) {
+  if (sec_bytes < 16) return ORC_ERR_CORRUPT;
+  uint64_t nch = get32(sec), chunk = get32(sec + 4), r = get64(sec + 8);
+  if (chunk != ORC_LZ_CHUNK || r != raw || nch != (raw + ORC_LZ_CHUNK - 1) / ORC_LZ_CHUNK) return ORC_ERR_CORRUPT;
+  uint64_t o = al16(16 + 4 * nch);
+  if (o > sec_bytes) return ORC_ERR_CORRUPT;
+  for (uint64_t c = 0; c < nch; c++) {
+    uint32_t e = get32(sec + 16 + 4 * c);
+    uint64_t sz = e & 0x7FFFFFFFu, a = c * ORC_LZ_CHUNK;
+    uint64_t n = raw - a < ORC_LZ_CHUNK ? raw - a : ORC_LZ_CHUNK;
+    if (o + sz > sec_bytes) return ORC_ERR_CORRUPT;
+    const uint8_t* t = sec + o;
+    uint8_t* d = dst + a;
+    if (e >> 31) {
+      if (sz != n) return ORC_ERR_CORRUPT;
+      memcpy(d, t, n);
+    } else {
+      uint64_t p = 0, q = 0;
+      while (p < sz) {
+        uint32_t cb = t[p++];
+        if (cb < 128) {
+          uint64_t L = cb + 1;
+          if (p + L > sz || q + L > n) return ORC_ERR_CORRUPT;
+          memcpy(d + q, t + p, L);
+          p += L;
+          q += L;
+        } else {
+          uint64_t L = cb - 128 + 4;
+          if (p + 2 > sz) return ORC_ERR_CORRUPT;
+          uint64_t dist = (uint64_t)t[p] | ((uint64_t)t[p + 1] << 8);
+          p += 2;
+          if (dist < 1 || dist > q || q + L > n) return ORC_ERR_CORRUPT;
+          for (uint64_t k = 0; k < L; k++, q++) d[q] = d[q - dist];
+        }
+      }
+      if (q != n) return ORC_ERR_CORRUPT;
+    }
+    o += sz;
+  }
+  return o == sec_bytes ? ORC_OK : ORC_ERR_CORRUPT;
+}
+
 typedef struct {
   uint64_t nb[3], nblocks, bvol;
 } o_geom;
@@ -829,6 +973,8 @@ uint64_t orc_compress_bound(const uint64_t dims[3], int dtype, const int block[3
   b = al16(b + 2ull * g.nblocks);
   b = al16(b + ts * n);
   b = al16(b + 4ull * ((n * O_LMAX + 31) / 32 + 1));
+  /* the lossless stage's chunk table (a stored chunk is never longer than itself) */
+  b += orc_lz_bound(4ull * ((n * O_LMAX + 31) / 32 + 1)) - 4ull * ((n * O_LMAX + 31) / 32 + 1);
   return b;
 }
 
@@ -1090,6 +1236,7 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
   if (use_nn && (p->s_in < 0 || p->s_in > 30)) return ORC_ERR_ARG;
   int lit = p->literal != 0;
   if (lit && (dtype != ORC_F32 || use_q || use_64 || p->codebook || p->eq_period < 0)) return ORC_ERR_ARG;
+  if (p->lossless && p->codebook) return ORC_ERR_ARG;  /* the stage follows a stream that ends the container */
   o_geom g;
   if (o_geom_make(dims, p->block, &g)) return ORC_ERR_ARG;
   uint64_t n = dims[0] * dims[1] * dims[2];
@@ -1305,6 +1452,22 @@ int orc_compress(const void* x, const uint64_t dims[3], int dtype, const orc_par
           }
     }
   }
+  if (p->lossless) {
+    /* the fourth SZ stage over the finished stream, which ends the container */
+    uint64_t raw = 4ull * swords;
+    uint8_t* tmp = (uint8_t*)malloc(orc_lz_bound(raw));
+    uint64_t lzb = orc_lz_encode(out + off_st, raw, tmp);
+    uint64_t tot2 = al16(off_st + lzb);
+    if (tot2 > cap) { free(tmp); ret = ORC_ERR_CAPACITY; goto done; }
+    memset(out + off_st, 0, tot2 - off_st);
+    memcpy(out + off_st, tmp, lzb);
+    free(tmp);
+    total = tot2;
+    put64(out + 216, total);
+    put32(out + 228, get32(out + 228) | ORC_FLAG_LOSSLESS);
+    put64(out + 240, lzb);
+    put32(out + 252, orc_crc32(out, 252));
+  }
   *out_size = total;
 
   if (dump) {
@@ -1377,8 +1540,12 @@ int orc_decompress(const uint8_t* in, uint64_t in_size, void* xo, uint64_t cap_e
   } else if (pred != ORC_PRED_LORENZO || nw != 0) {
     return ORC_ERR_CORRUPT;
   }
+  uint32_t hflags = get32(in + 228);
+  int lossless = (hflags & ORC_FLAG_LOSSLESS) != 0;
+  uint64_t lzb = get64(in + 240);
   if (off_w + (uint64_t)wsz * nw > total || off_cb + 4ull * n_used > total || off_bb + 4ull * nblocks > total ||
-      off_bn + 2ull * nblocks > total || off_ov + ts * n_out > total || off_st + 4ull * swords > total)
+      off_bn + 2ull * nblocks > total || off_ov + ts * n_out > total ||
+      (lossless ? off_st + lzb > total : off_st + 4ull * swords > total))
     return ORC_ERR_CORRUPT;
   uint64_t n = dims[0] * dims[1] * dims[2];
   if (n > cap_elems) return ORC_ERR_CAPACITY;
@@ -1448,6 +1615,14 @@ int orc_decompress(const uint8_t* in, uint64_t in_size, void* xo, uint64_t cap_e
   float* cvf = (float*)malloc(sizeof(float) * g.bvol);
   float ta = 0.0f;
   int64_t Ka = 0;
+  /* the stream words: in place, or decoded from the lossless stage's section */
+  const uint8_t* sbase = in + off_st;
+  uint8_t* rawbuf = NULL;
+  if (lossless && ret == ORC_OK) {
+    rawbuf = (uint8_t*)malloc(4ull * swords + 16);
+    if (orc_lz_decode(in + off_st, lzb, rawbuf, 4ull * swords)) ret = ORC_ERR_CORRUPT;
+    sbase = rawbuf;
+  }
   uint64_t bp = 0, oi = 0;
   uint64_t sbits = swords * 32ull;
   for (uint64_t b = 0; b < nblocks && ret == ORC_OK; b++) {
@@ -1476,7 +1651,7 @@ int orc_decompress(const uint8_t* in, uint64_t in_size, void* xo, uint64_t cap_e
             int found = 0;
             for (int l = 1; l <= O_LMAX; l++) {
               if (bp >= bend) break;
-              uint32_t word = get32(in + off_st + 4ull * (bp >> 5));
+              uint32_t word = get32(sbase + 4ull * (bp >> 5));
               uint32_t bit = (word >> (31u - (uint32_t)(bp & 31u))) & 1u;
               bp++;
               code = (code << 1) | bit;
@@ -1555,7 +1730,7 @@ int orc_decompress(const uint8_t* in, uint64_t in_size, void* xo, uint64_t cap_e
         }
     if (ret == ORC_OK && (bp != bend || oi != oend)) ret = ORC_ERR_CORRUPT;
   }
-  free(cvf); free(vc); free(dq); free(sorted); free(lens); free(wts); free(qn);
+  free(rawbuf); free(cvf); free(vc); free(dq); free(sorted); free(lens); free(wts); free(qn);
   return ret;
 }
 

@@ -58,6 +58,7 @@ typedef struct {
                             perceptron or Lorenzo: see orc_compress */
   int eq_period;         /* literal mode: every eq_period-th point of a block (raster order) is a
                             deliberate equilibrium point; 0 = none */
+  int lossless;          /* 1: the lossless back-end stage over the bitstream bytes (orc_lz_encode) */
 } orc_params;
 
 /* container flag (header offset 228): the bitstream section precedes the
@@ -66,6 +67,10 @@ typedef struct {
 /* container flag: codes of the paper-literal data selection (decoded serially, with drift);
  * header offset 232 holds the equilibrium-point period */
 #define ORC_FLAG_LITERAL 4u
+/* container flag: the bitstream section holds the lossless stage's chunks
+ * (header offset 240: the section's bytes) */
+#define ORC_FLAG_LOSSLESS 8u
+#define ORC_LZ_CHUNK 16384
 
 typedef struct {
   int32_t* dq;           /* [N] integer log codes, field order */

@@ -92,6 +92,9 @@ bool codebook_ok(const unsigned int* cb, int n, int m) {
   return have0 && kraft <= (1ull << kLmax);
 }
 
+// Bytes of the longest bitstream of n points (every code at the length limit).
+unsigned long long stream_bytes_max(unsigned long long n) { return 4ull * ((n * kLmax + 31) / 32 + 1); }
+
 bool wants_training(const pc_params* p) {
   return (p->pred == PC_PRED_MLP_FP32 && !p->h_weights) || (p->pred == PC_PRED_MLP_BF16 && !p->h_qnet);
 }
@@ -112,6 +115,7 @@ int check_params(const size_t dims[3], int dtype, const pc_params* p, Geo& g, in
                      (p->pred != PC_PRED_LORENZO && !(p->pred == PC_PRED_MLP_FP32 && p->h_weights))))
     return PC_ERR_ARG;
   if (!p->literal && p->eq_period != 0) return PC_ERR_ARG;
+  if (p->lossless && p->h_codebook) return PC_ERR_ARG;  // the stage follows a stream that ends the container
   mode = p->pred == PC_PRED_MLP_FP32 ? 1 : (p->pred == PC_PRED_MLP_BF16 ? 2 : 0);
   if (p->pred != PC_PRED_LORENZO && p->pred != PC_PRED_MLP_FP32 && p->pred != PC_PRED_MLP_BF16) return PC_ERR_ARG;
   nw = 0;
@@ -137,13 +141,14 @@ int check_params(const size_t dims[3], int dtype, const pc_params* p, Geo& g, in
 
 struct CompLayout {
   size_t st, tabs, hist, lens, cw, key, w, parent, depth, la, lb, rstart, symord, codes, nnflag, nout, bbits, cbits, cnout,
-      cboff, cooff, rec, side, next, ov, total;
+      cboff, cooff, rec, side, next, ov, lztab, lzslot, lzsize, lzoff, total;
+  unsigned long long lz_nch;
 };
 
 // sp: single pass (a given codebook): no code spill; look-back records, brick
 // edge words, the brick counter and room for every point as a balance value
 // (ts bytes each) instead.
-CompLayout comp_layout(const Geo& g, int m, bool sp = false, size_t ts = 4) {
+CompLayout comp_layout(const Geo& g, int m, bool sp = false, size_t ts = 4, bool lossless = false) {
   const size_t nsym = (size_t)1 << m;
   size_t np = 1;
   while (np < nsym) np <<= 1;
@@ -175,15 +180,22 @@ CompLayout comp_layout(const Geo& g, int m, bool sp = false, size_t ts = 4) {
   L.side = o; o = up(o + 8 * nbk);
   L.next = o; o = up(o + (sp ? 16 : 0));
   L.ov = o; o = up(o + (sp ? ts * (size_t)g.n[0] * g.n[1] * g.n[2] : 0));
+  // the lossless stage: per chunk of the longest stream a hash table, a token slot, a size, an offset
+  L.lz_nch = lossless ? lz_chunks_max(stream_bytes_max((unsigned long long)g.n[0] * g.n[1] * g.n[2])) : 0;
+  L.lztab = o; o = up(o + 2 * 4096 * (size_t)L.lz_nch);
+  L.lzslot = o; o = up(o + (size_t)kLzSlot * L.lz_nch);
+  L.lzsize = o; o = up(o + 4 * (size_t)L.lz_nch);
+  L.lzoff = o; o = up(o + 8 * (size_t)L.lz_nch);
   L.total = o;
   return L;
 }
 
 struct DecLayout {
-  size_t err, ftab, sorted, tabs, cbits, cnout, cboff, cooff, boff, ooff, codes, total;
+  size_t err, ftab, sorted, tabs, cbits, cnout, cboff, cooff, boff, ooff, codes, lzraw, lzoff, total;
 };
 
-DecLayout dec_layout(const Geo& g, int m) {
+// lz_raw: bytes of the bitstream to decode from the lossless stage (0: none)
+DecLayout dec_layout(const Geo& g, int m, unsigned long long lz_raw = 0) {
   const size_t nsym = (size_t)1 << m;
   DecLayout L;
   size_t o = 0;
@@ -198,6 +210,8 @@ DecLayout dec_layout(const Geo& g, int m) {
   L.boff = o; o = up(o + 8 * (size_t)g.nblocks);
   L.ooff = o; o = up(o + 8 * (size_t)g.nblocks);
   L.codes = o; o = up(o + 2 * (size_t)g.nblocks * g.bvol);
+  L.lzraw = o; o = up(o + (lz_raw ? al16(lz_raw) + 64 : 0));
+  L.lzoff = o; o = up(o + 8 * (size_t)lz_chunks_max(lz_raw));
   L.total = o;
   return L;
 }
@@ -224,7 +238,8 @@ uint64_t rd64(const uint8_t* p) { uint64_t v; memcpy(&v, p, 8); return v; }
 // Parsed, validated header.
 struct Hdr {
   int dtype, pred, m, stencil, h1, h2, s_in, nw, block[3];
-  int literal;
+  int literal, lossless;
+  unsigned long long lzb;
   size_t dims[3];
   unsigned int n_used;
   unsigned long long nblocks, n_out, swords, off_cb, off_bb, off_bn, off_ov, off_st, total;
@@ -266,7 +281,10 @@ int parse_header(const uint8_t* h, size_t n, Hdr& H, Geo& g) {
   H.total = rd64(h + 216);
   H.nw = (int)rd32(h + 224);
   const unsigned int flags = rd32(h + 228);
-  if (flags & ~(kFlagStreamFirst | kFlagLiteral)) return PC_ERR_CORRUPT;
+  if (flags & ~(kFlagStreamFirst | kFlagLiteral | kFlagLossless)) return PC_ERR_CORRUPT;
+  H.lossless = (flags & kFlagLossless) != 0;
+  H.lzb = rd64(h + 240);
+  if (H.lossless && (flags & kFlagStreamFirst)) return PC_ERR_CORRUPT;
   H.literal = (flags & kFlagLiteral) != 0;
   if (H.literal && (H.dtype != PC_F32 || (H.pred != 0 && H.pred != 1) || (flags & kFlagStreamFirst)))
     return PC_ERR_CORRUPT;
@@ -299,7 +317,10 @@ int parse_header(const uint8_t* h, size_t n, Hdr& H, Geo& g) {
   const unsigned long long oov =
       sfirst ? al16(al16(obn + 2ull * H.nblocks) + 4ull * H.swords) : al16(obn + 2ull * H.nblocks);
   const unsigned long long ost = sfirst ? al16(obn + 2ull * H.nblocks) : al16(oov + ts * H.n_out);
-  const unsigned long long tot = sfirst ? al16(oov + ts * H.n_out) : al16(ost + 4ull * H.swords);
+  const unsigned long long tot = sfirst ? al16(oov + ts * H.n_out)
+                                        : al16(ost + (H.lossless ? H.lzb : 4ull * H.swords));
+  // the lossless section holds at most the stream and its chunk table
+  if (H.lossless && H.lzb > al16(16 + 4 * lz_chunks_max(4ull * H.swords)) + 4ull * H.swords) return PC_ERR_CORRUPT;
   if (H.off_cb != ocb || H.off_bb != obb || H.off_bn != obn || H.off_ov != oov || H.off_st != ost || H.total != tot)
     return PC_ERR_CORRUPT;
   return PC_OK;
@@ -477,6 +498,7 @@ struct FieldPlan {
   const long long* h_qnet;  // host network to copy into the container (fixed-point form)
   const long long* qnet;    // its device copy in the container's weights section
   int literal, eq_period;  // the paper-literal selection
+  LzBufs lz;               // the lossless stage (nch_max 0: off)
   // single pass (a given codebook)
   bool sp;
   const unsigned int* h_cb;
@@ -499,7 +521,7 @@ int plan_field(FieldPlan& F, const void* d_field, const size_t dims[3], int dtyp
   F.m = p->m;
   F.eb = p->eb_rel;
   F.g = g;
-  F.L = comp_layout(g, p->m, p->h_codebook != nullptr, dtype == PC_F64 ? 8 : 4);
+  F.L = comp_layout(g, p->m, p->h_codebook != nullptr, dtype == PC_F64 ? 8 : 4, p->lossless != 0);
   if (ws_bytes < F.L.total) return PC_ERR_CAPACITY;
   HdrInfo& hi = F.hi;
   hi.dtype = dtype;
@@ -549,6 +571,11 @@ int plan_field(FieldPlan& F, const void* d_field, const size_t dims[3], int dtyp
   // section, where the kernels read it
   F.h_qnet = mode == 2 ? p->h_qnet : nullptr;
   F.qnet = mode == 2 ? reinterpret_cast<const long long*>(F.out + kHdr) : nullptr;
+  F.lz.nch_max = L.lz_nch;
+  F.lz.tabs = reinterpret_cast<uint16_t*>(ws + L.lztab);
+  F.lz.slots = ws + L.lzslot;
+  F.lz.sizes = reinterpret_cast<unsigned int*>(ws + L.lzsize);
+  F.lz.offs = reinterpret_cast<unsigned long long*>(ws + L.lzoff);
   F.literal = p->literal;
   F.eq_period = p->eq_period;
   F.sp = p->h_codebook != nullptr;
@@ -633,11 +660,13 @@ int launch_tail(FieldPlan& F, const Mlp& mlp, cudaStream_t s, int nsm) {
   auto* cn = reinterpret_cast<unsigned long long*>(F.ws + L.cnout);
   auto* cbo = reinterpret_cast<unsigned long long*>(F.ws + L.cboff);
   auto* coo = reinterpret_cast<unsigned long long*>(F.ws + L.cooff);
-  if (F.dtype == PC_F32)
-    return launch_pack<float>(static_cast<const float*>(F.x), F.g, F.codes, F.nnflag, F.nout, F.lens, F.cw, bbits, cb,
-                              cn, cbo, coo, F.stp, F.out, F.hi, mlp, s);
-  return launch_pack<double>(static_cast<const double*>(F.x), F.g, F.codes, F.nnflag, F.nout, F.lens, F.cw, bbits, cb,
-                             cn, cbo, coo, F.stp, F.out, F.hi, mlp, s);
+  r = F.dtype == PC_F32
+          ? launch_pack<float>(static_cast<const float*>(F.x), F.g, F.codes, F.nnflag, F.nout, F.lens, F.cw, bbits, cb,
+                               cn, cbo, coo, F.stp, F.out, F.hi, mlp, s)
+          : launch_pack<double>(static_cast<const double*>(F.x), F.g, F.codes, F.nnflag, F.nout, F.lens, F.cw, bbits,
+                                cb, cn, cbo, coo, F.stp, F.out, F.hi, mlp, s);
+  if (r || F.lz.nch_max == 0) return r;
+  return launch_lz_encode(F.out, F.hi.cap, F.stp, F.lz, s);
 }
 
 // Everything one container's decompression needs.
@@ -649,6 +678,8 @@ struct DecPlan {
   DecInfo di;
   const uint8_t* in;
   void* out;
+  uint8_t* lzraw;                // the lossless stage's raw stream and chunk offsets (workspace)
+  unsigned long long* lzoff;
 };
 
 // Parse and check a container (hbuf: its first `pre` host bytes) and lay out
@@ -662,7 +693,7 @@ int plan_dec(DecPlan& P, const uint8_t* hbuf, size_t pre, const void* d_in, size
   const size_t ts = H.dtype == PC_F64 ? 8 : 4;
   const size_t n = H.dims[0] * H.dims[1] * H.dims[2];
   if (field_cap < n * ts) return PC_ERR_CAPACITY;
-  P.L = dec_layout(P.g, H.m);
+  P.L = dec_layout(P.g, H.m, H.lossless ? 4ull * H.swords : 0ull);
   const DecLayout& L = P.L;
   if (ws_bytes < L.total) return PC_ERR_CAPACITY;
   memset(&mlp, 0, sizeof(Mlp));
@@ -710,6 +741,10 @@ int plan_dec(DecPlan& P, const uint8_t* hbuf, size_t pre, const void* d_in, size
   di.off_bn = H.off_bn;
   di.off_ov = H.off_ov;
   di.off_st = H.off_st;
+  // the bitstream: in place, or the lossless stage's output in the workspace
+  P.lzraw = ws + L.lzraw;
+  P.lzoff = reinterpret_cast<unsigned long long*>(ws + L.lzoff);
+  di.stream = H.lossless ? P.lzraw : static_cast<const uint8_t*>(d_in) + H.off_st;
   di.in_size = in_size;
   di.Kp = H.Kp;
   di.Kn = H.Kn;
@@ -725,6 +760,13 @@ int plan_dec(DecPlan& P, const uint8_t* hbuf, size_t pre, const void* d_in, size
 
 int launch_dec(const DecPlan& P, const Mlp& mlp, int nsm, cudaStream_t s) {
   if (cudaMemsetAsync(P.ds.err, 0, sizeof(int), s) != cudaSuccess) return PC_ERR_CUDA;
+  if (P.H.lossless) {
+    // the fourth SZ stage undone first: the raw words (and zero padding) for the Huffman decoder
+    const unsigned long long nraw = 4ull * P.H.swords;
+    if (cudaMemsetAsync(P.lzraw + nraw, 0, al16(nraw) + 64 - nraw, s) != cudaSuccess) return PC_ERR_CUDA;
+    const int r = launch_lz_decode(P.in + P.H.off_st, P.H.lzb, nraw, P.lzraw, P.lzoff, P.ds.err, s);
+    if (r) return r;
+  }
   return P.H.dtype == PC_F32
              ? launch_decompress<float>(P.in, P.g, P.di, P.ds, mlp, static_cast<float*>(P.out), nsm, s)
              : launch_decompress<double>(P.in, P.g, P.di, P.ds, mlp, static_cast<double*>(P.out), nsm, s);
@@ -983,7 +1025,9 @@ size_t pc_compress_bound(const size_t dims[3], int dtype, const pc_params* p) {
   b = al16(b + 4ull * g.nblocks);
   b = al16(b + 2ull * g.nblocks);
   b = al16(b + ts * n);
-  b = al16(b + 4ull * ((n * kLmax + 31) / 32 + 1));
+  b = al16(b + stream_bytes_max(n));
+  // the lossless stage's section header and chunk table (a chunk is never stored longer than itself)
+  if (p->lossless) b += al16(16 + 4 * lz_chunks_max(stream_bytes_max(n))) + 16;
   return (size_t)b;
 }
 
@@ -993,7 +1037,7 @@ int pc_compress_workspace_size(const size_t dims[3], int dtype, const pc_params*
   int st = check_params(dims, dtype, p, g, mode, nw);
   if (st) return st;
   if (!ws) return PC_ERR_ARG;
-  *ws = comp_layout(g, p->m, p->h_codebook != nullptr, dtype == PC_F64 ? 8 : 4).total;
+  *ws = comp_layout(g, p->m, p->h_codebook != nullptr, dtype == PC_F64 ? 8 : 4, p->lossless != 0).total;
   if (wants_training(p)) {
     const size_t tw = train_layout(g, p->m, p->stencil, nweights(p->stencil, p->hidden[0], p->hidden[1]),
                                    train_thr32(dims, g, p), kTrainModels).total;
@@ -1008,7 +1052,7 @@ int pc_compress_workspace_layout(const size_t dims[3], int dtype, const pc_param
   int mode, nw;
   int st = check_params(dims, dtype, p, g, mode, nw);
   if (st) return st;
-  CompLayout L = comp_layout(g, p->m, p->h_codebook != nullptr, dtype == PC_F64 ? 8 : 4);
+  CompLayout L = comp_layout(g, p->m, p->h_codebook != nullptr, dtype == PC_F64 ? 8 : 4, p->lossless != 0);
   if (off_codes) *off_codes = L.codes;
   if (off_nnflag) *off_nnflag = L.nnflag;
   if (off_hist) *off_hist = L.hist;
@@ -1097,7 +1141,7 @@ int pc_compress_batch_workspace_size(int nfields, const size_t* dims, const int*
     int st = check_params(dims + 3 * i, dtypes[i], params + i, g, mode, nw);
     if (st) return st;
     if (wants_training(params + i) || params[i].literal) return PC_ERR_ARG;
-    ws += up(comp_layout(g, params[i].m, params[i].h_codebook != nullptr, dtypes[i] == PC_F64 ? 8 : 4).total);
+    ws += up(comp_layout(g, params[i].m, params[i].h_codebook != nullptr, dtypes[i] == PC_F64 ? 8 : 4, params[i].lossless != 0).total);
     ob += up(pc_compress_bound(dims + 3 * i, dtypes[i], params + i));
   }
   *ws_bytes = ws;
@@ -1126,7 +1170,7 @@ int pc_compress_batch(int nfields, const void* const* d_fields, const size_t* di
     Geo g;
     int mode, nw;
     check_params(dims + 3 * i, dtypes[i], params + i, g, mode, nw);
-    const size_t wsz = up(comp_layout(g, params[i].m, params[i].h_codebook != nullptr, dtypes[i] == PC_F64 ? 8 : 4).total);
+    const size_t wsz = up(comp_layout(g, params[i].m, params[i].h_codebook != nullptr, dtypes[i] == PC_F64 ? 8 : 4, params[i].lossless != 0).total);
     const size_t osz = up(pc_compress_bound(dims + 3 * i, dtypes[i], params + i));
     offsets[i] = oo;
     st = plan_field(F[i], d_fields[i], dims + 3 * i, dtypes[i], params + i, g, mode, nw, out + oo, osz, ws + wo, wsz,
@@ -1254,7 +1298,7 @@ int pc_header_info(const void* h_hdr, size_t hdr_bytes, size_t dims_out[3], int*
   if (dims_out)
     for (int i = 0; i < 3; ++i) dims_out[i] = H.dims[i];
   if (dtype_out) *dtype_out = H.dtype;
-  if (ws_bytes) *ws_bytes = dec_layout(g, H.m).total;
+  if (ws_bytes) *ws_bytes = dec_layout(g, H.m, H.lossless ? 4ull * H.swords : 0ull).total;
   return PC_OK;
 }
 

@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kDecThreads) k_huff_decode(Geo g, const uint8_
   // chunks past it read as zero.  Between refills the bits stream through a
   // 64-bit register buffer (hi:lo, next bit at bit 31 of hi) whose next word
   // is read one code ahead.
-  const uint4* s4 = reinterpret_cast<const uint4*>(in + di.off_st);
+  const uint4* s4 = reinterpret_cast<const uint4*>(di.stream);
   const unsigned long long nq = (di.swords + 3) / 4;
   const unsigned int tid = threadIdx.x;
   const unsigned long long p0 = ds.boff[b];

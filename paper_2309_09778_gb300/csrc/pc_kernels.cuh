@@ -120,6 +120,28 @@ constexpr unsigned int kFlagStreamFirst = 1u;
 // Container flag: codes of the paper-literal data selection (Section IV.D;
 // decoded with drift); header offset 232 holds the equilibrium-point period.
 constexpr unsigned int kFlagLiteral = 4u;
+// Container flag: the bitstream section holds the lossless stage's chunks
+// (header offset 240: the section's bytes).
+constexpr unsigned int kFlagLossless = 8u;
+constexpr int kLzChunk = 16384;             // bytes per chunk of the lossless stage
+constexpr int kLzSlot = kLzChunk + 256;     // workspace bytes per chunk's tokens
+// Workspace of the lossless stage: per chunk a hash table, a token slot, its
+// size and its section offset; nch_max chunks (the longest stream).
+struct LzBufs {
+  uint16_t* tabs;
+  uint8_t* slots;
+  unsigned int* sizes;
+  unsigned long long* offs;
+  unsigned long long nch_max;
+};
+unsigned long long lz_chunks_max(unsigned long long raw_max);
+// The stage over the finished stream (its offset and length in the state):
+// the container's stream section replaced by the chunks, header rewritten.
+int launch_lz_encode(uint8_t* out, unsigned long long cap, State* st, const LzBufs& lb, cudaStream_t s);
+// The raw stream (nraw bytes) back from a section of lzb bytes (offs: one
+// u64 per chunk of scratch).
+int launch_lz_decode(const uint8_t* sec, unsigned long long lzb, unsigned long long nraw, uint8_t* raw,
+                     unsigned long long* offs, int* err, cudaStream_t s);
 
 // Bricks of a field: G blocks along x per brick (BrickShape), rows of bricks.
 inline long long bricks_of(const Geo& g) {
@@ -202,6 +224,7 @@ int launch_pack(const T* x, const Geo& g, const uint16_t* codes, const uint8_t* 
 struct DecInfo {
   int dtype, m, stencil, h1, h2, s_in, usenn_any, qmode;
   int literal;            // codes of the paper-literal data selection (float32 only)
+  const uint8_t* stream;  // the bitstream words: in the container, or decoded from the lossless stage
   const long long* qnet;  // fixed-point network in the container (qmode), else null
   unsigned int n_used;
   unsigned long long n_out, swords;

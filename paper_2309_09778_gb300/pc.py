@@ -53,7 +53,7 @@ class pc_params(C.Structure):
                 ("hidden", C.c_int * 2), ("m", C.c_int), ("s_in", C.c_int), ("h_weights", C.c_void_p),
                 ("h_qnet", C.c_void_p), ("seed", C.c_ulonglong), ("train_samples", C.c_longlong),
                 ("ndims", C.c_int), ("codebook_n", C.c_int), ("h_codebook", C.c_void_p), ("literal", C.c_int),
-                ("eq_period", C.c_int)]
+                ("eq_period", C.c_int), ("lossless", C.c_int)]
 
 
 def lib():
@@ -162,13 +162,15 @@ def _stream_ptr(stream):
 
 def make_params(eb_rel: float, block=(8, 8, 8), pred: int = PC_PRED_LORENZO, stencil: int = 7,
                 hidden=(16, 16), m: int = 16, s_in: int = 0, weights=None, qnet=None, seed: int = 0,
-                train_samples: int = 0, ndims: int = 0, codebook=None, literal: bool = False, eq_period: int = 0):
+                train_samples: int = 0, ndims: int = 0, codebook=None, literal: bool = False, eq_period: int = 0,
+                lossless: bool = False):
     """Fill a pc_params struct; the weights, network and codebook arrays are kept alive on the
     struct.  With a perceptron form and no weights (or network), pc_compress trains one on the
     device; with a codebook (uint32 list from pc_sample_codebook) it compresses in one pass."""
     p = pc_params()
     p.literal = int(bool(literal))
     p.eq_period = int(eq_period)
+    p.lossless = int(bool(lossless))
     p.seed = int(seed)
     p.train_samples = int(train_samples)
     p.ndims = int(ndims)
