@@ -705,6 +705,40 @@ def single_pass(torch, pc, w, args, stream, flush, peak, two_pass):
     return out
 
 
+def lossless_report(torch, pc, fields, params, label):
+    """The lossless back-end stage (Section IV.A's fourth SZ stage) on the given fields and predictors: bits per
+    value and device throughput of compression and decompression with and without it."""
+    out = {"fields": label}
+    for name, on in (("without", False), ("with", True)):
+        tot_bytes, tc, td = 0, 0.0, 0.0
+        for d, p0 in zip(fields, params):
+            p = pc.pc_params.from_buffer_copy(p0)
+            for attr in ("_w", "_q", "_cb"):
+                if hasattr(p0, attr):
+                    setattr(p, attr, getattr(p0, attr))
+            p.lossless = int(on)
+            blob = pc.compress(d, p)  # warm-up and buffers
+            y = pc.decompress(blob)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            blob = pc.compress(d, p)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            y = pc.decompress(blob)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            tot_bytes += blob.numel()
+            tc += t1 - t0
+            td += t2 - t1
+            del y
+        npts = sum(d.numel() for d in fields)
+        nb = sum(d.numel() * d.element_size() for d in fields)
+        out[name] = {"bits_per_value": 8.0 * tot_bytes / npts, "compress_gbs": nb / tc / 1e9,
+                     "decompress_gbs": nb / td / 1e9}
+    out["bits_vs_without"] = out["with"]["bits_per_value"] / out["without"]["bits_per_value"] - 1.0
+    return out
+
+
 def run_batch64(torch, pc, args, dev, stream, flush, peak):
     """The many-field batch: 32 2-D float32 fields 1800 x 3600 and 32 3-D float32 fields with dims drawn
     uniformly from [64, 384]^3, spectral slopes drawn from [2, 5], eb_rel cycling 1e-2, 1e-3, 1e-4;
@@ -1015,11 +1049,19 @@ def main():
     e2e, hosts = e2e_rate(torch, pc, r, max(3, min(args.steps, 10)))
     e2e_t = e2e_with_training(torch, pc, hosts, spec, head["form"], dev)
     r.free()
-    sp = None
+    sp = lossless = None
     if not args.no_forms:
         forms = form_compare(torch, pc, head, args, stream, flush)
         two = {f: forms[f] for f in ("fp32", "bf16", "lorenzo") if f in forms}
         sp = single_pass(torch, pc, head, args, stream, flush, peak, two)
+        hparams = [params_for(pc, spec, inf, head["form"])[0] for inf in head["infos"]]
+        lossless = [lossless_report(torch, pc, spec["_fields"], hparams, "the headline fields, headline form")]
+        from paper_2309_09778_gb300 import gen
+        muted = gen.signed_lognormal_device((100, 500, 500), 11 / 3, 7, dev, 2.0, 0.6)
+        lossless.append(lossless_report(torch, pc, [muted], [pc.make_params(1e-3, BLOCK)],
+                                        "100x500x500 float32 signed log-normal with 60% muted (zero) regions, "
+                                        "Lorenzo, eb 1e-3"))
+        del muted
     # plain FP32: a device copy of the fields at HBM speed
     copy_gbs = []
     for d in spec["_fields"]:
@@ -1077,7 +1119,7 @@ def main():
             "bits_per_value": res["bits_per_value"], "bound_held": res["bound_held"],
             "hbm_roofline": res["hbm_roofline"], "roofline": res["roofline"],
             "perceptron_blocks_fraction": res["perceptron_blocks_fraction"],
-            "perceptron_forms": forms, "single_pass_sample_codebook": sp,
+            "perceptron_forms": forms, "single_pass_sample_codebook": sp, "lossless_stage": lossless,
             "stages_ms_per_step": res["stages_ms_per_step"],
             "training": res["training"], "training_seconds_total": res["training_seconds_total"],
             "vs_fp32_plain": {"bits_per_value": 32.0 * (2 if spec["dtype"] == "f64" else 1),

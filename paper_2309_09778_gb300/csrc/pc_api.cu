@@ -141,7 +141,7 @@ int check_params(const size_t dims[3], int dtype, const pc_params* p, Geo& g, in
 
 struct CompLayout {
   size_t st, tabs, hist, lens, cw, key, w, parent, depth, la, lb, rstart, symord, codes, nnflag, nout, bbits, cbits, cnout,
-      cboff, cooff, rec, side, next, ov, lztab, lzslot, lzsize, lzoff, total;
+      cboff, cooff, rec, side, next, ov, lzslot, lzsize, lzoff, total;
   unsigned long long lz_nch;
 };
 
@@ -180,9 +180,8 @@ CompLayout comp_layout(const Geo& g, int m, bool sp = false, size_t ts = 4, bool
   L.side = o; o = up(o + 8 * nbk);
   L.next = o; o = up(o + (sp ? 16 : 0));
   L.ov = o; o = up(o + (sp ? ts * (size_t)g.n[0] * g.n[1] * g.n[2] : 0));
-  // the lossless stage: per chunk of the longest stream a hash table, a token slot, a size, an offset
+  // the lossless stage: per chunk of the longest stream a token slot, a size, an offset
   L.lz_nch = lossless ? lz_chunks_max(stream_bytes_max((unsigned long long)g.n[0] * g.n[1] * g.n[2])) : 0;
-  L.lztab = o; o = up(o + 2 * 4096 * (size_t)L.lz_nch);
   L.lzslot = o; o = up(o + (size_t)kLzSlot * L.lz_nch);
   L.lzsize = o; o = up(o + 4 * (size_t)L.lz_nch);
   L.lzoff = o; o = up(o + 8 * (size_t)L.lz_nch);
@@ -572,7 +571,6 @@ int plan_field(FieldPlan& F, const void* d_field, const size_t dims[3], int dtyp
   F.h_qnet = mode == 2 ? p->h_qnet : nullptr;
   F.qnet = mode == 2 ? reinterpret_cast<const long long*>(F.out + kHdr) : nullptr;
   F.lz.nch_max = L.lz_nch;
-  F.lz.tabs = reinterpret_cast<uint16_t*>(ws + L.lztab);
   F.lz.slots = ws + L.lzslot;
   F.lz.sizes = reinterpret_cast<unsigned int*>(ws + L.lzsize);
   F.lz.offs = reinterpret_cast<unsigned long long*>(ws + L.lzoff);

@@ -125,10 +125,9 @@ constexpr unsigned int kFlagLiteral = 4u;
 constexpr unsigned int kFlagLossless = 8u;
 constexpr int kLzChunk = 16384;             // bytes per chunk of the lossless stage
 constexpr int kLzSlot = kLzChunk + 256;     // workspace bytes per chunk's tokens
-// Workspace of the lossless stage: per chunk a hash table, a token slot, its
-// size and its section offset; nch_max chunks (the longest stream).
+// Workspace of the lossless stage: per chunk a token slot, its size and its
+// section offset; nch_max chunks (the longest stream).
 struct LzBufs {
-  uint16_t* tabs;
   uint8_t* slots;
   unsigned int* sizes;
   unsigned long long* offs;

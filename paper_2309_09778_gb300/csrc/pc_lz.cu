@@ -38,53 +38,69 @@ __device__ __forceinline__ unsigned int lz_lits(const uint8_t* src, unsigned int
   return o;
 }
 
-// One thread per chunk (grid over the most chunks a stream of this field can
-// have; the stream's length is on the device): tokens into the chunk's slot,
-// or the raw chunk when they are not shorter, and its size | stored << 31.
-__global__ void __launch_bounds__(64) k_lz_encode(const uint8_t* __restrict__ out, unsigned long long nch_max,
-                                                  uint16_t* tabs, uint8_t* slots, unsigned int* sizes,
-                                                  const State* __restrict__ st) {
-  const unsigned long long c = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per chunk (grid over the most chunks a stream of this field can
+// have; the stream's length is on the device).  The warp stages the chunk and
+// a fresh hash table in shared memory; lane 0 runs the greedy parse (serial by
+// nature) against them and writes the tokens to the chunk's slot; the warp
+// then writes the raw chunk instead when the tokens are not shorter.  Sizes:
+// coded bytes | stored << 31.
+constexpr int kLzWarps = 4;
+__global__ void __launch_bounds__(32 * kLzWarps) k_lz_encode(const uint8_t* __restrict__ out, unsigned long long nch_max,
+                                                             uint8_t* slots, unsigned int* sizes,
+                                                             const State* __restrict__ st) {
+  extern __shared__ __align__(16) unsigned char lzsm[];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* sdat = lzsm + (size_t)wid * (kLzChunk + 2 * (1 << kLzHashBits));
+  uint16_t* tab = reinterpret_cast<uint16_t*>(sdat + kLzChunk);
+  const unsigned long long c = (unsigned long long)blockIdx.x * kLzWarps + wid;
   if (c >= nch_max || st->err) return;
   const unsigned long long nraw = 4ull * st->swords;
   if (c * kLzChunk >= nraw) return;
   const uint8_t* src = out + st->off_st + c * kLzChunk;
   const unsigned int n = (unsigned int)(nraw - c * kLzChunk < (unsigned long long)kLzChunk ? nraw - c * kLzChunk
                                                                                             : kLzChunk);
-  uint16_t* tab = tabs + c * (1u << kLzHashBits);
-  for (int i = 0; i < (1 << kLzHashBits); ++i) tab[i] = 0;
+  // the chunk (16-byte loads: the stream starts 16-byte aligned, chunks are 16 KiB, n a multiple of 4)
+  for (unsigned int i = 4 * lane; i < n; i += 128) *reinterpret_cast<unsigned int*>(sdat + i) =
+      *reinterpret_cast<const unsigned int*>(src + i);
+  for (int i = lane; i < (1 << kLzHashBits) / 2; i += 32) reinterpret_cast<unsigned int*>(tab)[i] = 0u;
+  __syncwarp();
   uint8_t* dst = slots + c * kLzSlot;
-  unsigned int i = 0, lit0 = 0, o = 0;
-  while (i < n) {
-    unsigned int L = 0, d = 0;
-    if (i + 4 <= n) {
-      const unsigned int h = lz_hash(src + i);
-      const unsigned int cand = tab[h];
-      tab[h] = (uint16_t)(i + 1);
-      if (cand) {
-        const unsigned int j = cand - 1;
-        while (i + L < n && L < 131u && src[j + L] == src[i + L]) ++L;
-        if (L >= 4) d = i - j;
-        else L = 0;
+  unsigned int o = 0;
+  if (lane == 0) {
+    unsigned int i = 0, lit0 = 0;
+    while (i < n) {
+      unsigned int L = 0, d = 0;
+      if (i + 4 <= n) {
+        const unsigned int h = lz_hash(sdat + i);
+        const unsigned int cand = tab[h];
+        tab[h] = (uint16_t)(i + 1);
+        if (cand) {
+          const unsigned int j = cand - 1;
+          while (i + L < n && L < 131u && sdat[j + L] == sdat[i + L]) ++L;
+          if (L >= 4) d = i - j;
+          else L = 0;
+        }
       }
+      if (L) {
+        o = lz_lits(sdat, lit0, i, dst, o);
+        dst[o++] = (uint8_t)(128 + (L - 4));
+        dst[o++] = (uint8_t)(d & 0xFFu);
+        dst[o++] = (uint8_t)(d >> 8);
+        i += L;
+        lit0 = i;
+      } else {
+        ++i;
+      }
+      if (o >= n) break;  // no shorter than the chunk: it is stored
     }
-    if (L) {
-      o = lz_lits(src, lit0, i, dst, o);
-      dst[o++] = (uint8_t)(128 + (L - 4));
-      dst[o++] = (uint8_t)(d & 0xFFu);
-      dst[o++] = (uint8_t)(d >> 8);
-      i += L;
-      lit0 = i;
-    } else {
-      ++i;
-    }
-    if (o >= n) break;  // no shorter than the chunk: it is stored
+    if (o < n) o = lz_lits(sdat, lit0, n, dst, o);
   }
-  if (o < n) o = lz_lits(src, lit0, n, dst, o);
+  o = __shfl_sync(0xFFFFFFFFu, o, 0);
   if (o >= n) {
-    for (unsigned int k = 0; k < n; ++k) dst[k] = src[k];
-    sizes[c] = n | 0x80000000u;
-  } else {
+    for (unsigned int i = 4 * lane; i < n; i += 128)
+      *reinterpret_cast<unsigned int*>(dst + i) = *reinterpret_cast<const unsigned int*>(sdat + i);
+    if (lane == 0) sizes[c] = n | 0x80000000u;
+  } else if (lane == 0) {
     sizes[c] = o;
   }
 }
@@ -195,11 +211,15 @@ __global__ void __launch_bounds__(1024) k_lz_offsets(const uint8_t* __restrict__
   if (tid == 0 && head + tot != lzb) atomicExch(err, PC_ERR_CORRUPT);
 }
 
-__global__ void __launch_bounds__(64) k_lz_decode(const uint8_t* __restrict__ sec, unsigned long long nraw,
-                                                  const unsigned long long* __restrict__ offs, uint8_t* raw,
-                                                  int* err) {
+// One warp per chunk: lane 0 reads each control byte; the lanes copy literal
+// runs, and matches in steps no longer than the distance (every source byte
+// is written before it is read).
+__global__ void __launch_bounds__(32 * kLzWarps) k_lz_decode(const uint8_t* __restrict__ sec, unsigned long long nraw,
+                                                             const unsigned long long* __restrict__ offs, uint8_t* raw,
+                                                             int* err) {
   const unsigned long long nch = (nraw + kLzChunk - 1) / kLzChunk;
-  const unsigned long long c = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long c = (unsigned long long)blockIdx.x * kLzWarps + (threadIdx.x >> 5);
   if (c >= nch || *reinterpret_cast<volatile int*>(err)) return;
   const unsigned int e = reinterpret_cast<const unsigned int*>(sec + 16)[c];
   const unsigned long long sz = e & 0x7FFFFFFFu;
@@ -210,7 +230,7 @@ __global__ void __launch_bounds__(64) k_lz_decode(const uint8_t* __restrict__ se
   if (e >> 31) {
     if (sz != n) bad = true;
     else
-      for (unsigned long long i = 0; i < n; ++i) d[i] = t[i];
+      for (unsigned long long i = lane; i < n; i += 32) d[i] = t[i];
   } else {
     unsigned long long p = 0, q = 0;
     while (p < sz) {
@@ -218,7 +238,7 @@ __global__ void __launch_bounds__(64) k_lz_decode(const uint8_t* __restrict__ se
       if (cb < 128u) {
         const unsigned long long L = cb + 1;
         if (p + L > sz || q + L > n) { bad = true; break; }
-        for (unsigned long long k = 0; k < L; ++k) d[q + k] = t[p + k];
+        for (unsigned long long k = lane; k < L; k += 32) d[q + k] = t[p + k];
         p += L;
         q += L;
       } else {
@@ -227,12 +247,18 @@ __global__ void __launch_bounds__(64) k_lz_decode(const uint8_t* __restrict__ se
         const unsigned long long dist = (unsigned long long)t[p] | ((unsigned long long)t[p + 1] << 8);
         p += 2;
         if (dist < 1 || dist > q || q + L > n) { bad = true; break; }
-        for (unsigned long long k = 0; k < L; ++k, ++q) d[q] = d[q - dist];
+        const unsigned long long stp = dist < 32 ? dist : 32;
+        for (unsigned long long k0 = 0; k0 < L; k0 += stp) {
+          if (lane < stp && k0 + lane < L) d[q + k0 + lane] = d[q + k0 + lane - dist];
+          __syncwarp();
+        }
+        q += L;
       }
+      __syncwarp();
     }
     if (q != n) bad = true;
   }
-  if (bad) atomicExch(err, PC_ERR_CORRUPT);
+  if (bad && lane == 0) atomicExch(err, PC_ERR_CORRUPT);
 }
 
 unsigned long long lz_chunks_max(unsigned long long raw_max) { return (raw_max + kLzChunk - 1) / kLzChunk; }
@@ -241,7 +267,11 @@ int launch_lz_encode(uint8_t* out, unsigned long long cap, State* st, const LzBu
   ProfScope p(kStPack, s);
   const unsigned long long nch = lb.nch_max;
   if (nch == 0) return PC_OK;
-  k_lz_encode<<<(unsigned int)((nch + 63) / 64), 64, 0, s>>>(out, nch, lb.tabs, lb.slots, lb.sizes, st);
+  const size_t sm = (size_t)kLzWarps * (kLzChunk + 2 * (1 << kLzHashBits));
+  if (cudaFuncSetAttribute(k_lz_encode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+    return PC_ERR_CUDA;
+  k_lz_encode<<<(unsigned int)((nch + kLzWarps - 1) / kLzWarps), 32 * kLzWarps, sm, s>>>(out, nch, lb.slots, lb.sizes,
+                                                                                         st);
   k_lz_layout<<<1, 1024, 0, s>>>(lb.sizes, lb.offs, st, out, cap);
   k_lz_gather<<<(unsigned int)nch, 256, 0, s>>>(lb.slots, lb.sizes, lb.offs, st, out);
   return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
@@ -253,7 +283,7 @@ int launch_lz_decode(const uint8_t* sec, unsigned long long lzb, unsigned long l
   if (nch == 0) return PC_OK;
   ProfScope p(kStDecScan, s);
   k_lz_offsets<<<1, 1024, 0, s>>>(sec, lzb, nraw, offs, err);
-  k_lz_decode<<<(unsigned int)((nch + 63) / 64), 64, 0, s>>>(sec, nraw, offs, raw, err);
+  k_lz_decode<<<(unsigned int)((nch + kLzWarps - 1) / kLzWarps), 32 * kLzWarps, 0, s>>>(sec, nraw, offs, raw, err);
   return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
 
