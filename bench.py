@@ -269,11 +269,11 @@ def sha_of(*paths):
 TRAFFIC = {
     # (workload, stage, form): (bytes per launch, sha of the sources, profile summary)
     # captured on 256 x 256 x 512 (one quarter of a 512^3 field, same recipe and network shape) and scaled by
-    # the points processed: 69.3 MB read + 78.3 MB written there
-    ("density_velocity_512", "recon", "bf16"): (4 * (69315328 + 78289920), "861f7ef307e09a83",
+    # the points processed: 68.6 MB read + 78.6 MB written there
+    ("density_velocity_512", "recon", "bf16"): (4 * (68578560 + 78550016), "80c3a0197821d068",
                                                 "profiles/k_recon_c3_wmma.md"),
-    # 134.9 MB read + 38.9 MB written on the same quarter-size case
-    ("density_velocity_512", "compress", "bf16"): (4 * (134882304 + 38942208), "42c3e2ad57556c7f",
+    # 134.9 MB read + 39.2 MB written on the same quarter-size case
+    ("density_velocity_512", "compress", "bf16"): (4 * (134929152 + 39155968), "2408bf572c256e09",
                                                    "profiles/k_compress_c3_tcgen05.md"),
 }
 STAGE_SOURCES = {
