@@ -419,6 +419,18 @@ class Runner:
         self.out = self.wsc = self.y = self.wsd = None
 
 
+def rank_max(torch, dist, values, device):
+    """Replicas (one per GPU, the same step each): the job's times are the slowest rank's."""
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_rate(world, bytes_per_rank, ms_per_step):
+    """Whole-job throughput in GB/s: every rank's bytes over the slowest rank's step time."""
+    return world * bytes_per_rank / (ms_per_step * 1e6)
+
+
 def measure(torch, pc, fields, spec, params, steps, warmup, stream, flush, dist=None):
     """Warm-up, bound check, then `steps` timed steps (CUDA events on the launching stream, L2 flushed
     between steps).  Returns (result dict, runner)."""
@@ -447,9 +459,7 @@ def measure(torch, pc, fields, spec, params, steps, warmup, stream, flush, dist=
     tc = sum(a.elapsed_time(b) for a, b, _ in ev) / len(ev)
     td = sum(b.elapsed_time(c) for _, b, c in ev) / len(ev)
     if dist:
-        tt = torch.tensor([tc, td], device=fields[0].device)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tc, td = tt.tolist()
+        tc, td = rank_max(torch, dist, [tc, td], fields[0].device)
     nbytes = sum(d.numel() * d.element_size() for d in fields)
     npts = sum(d.numel() for d in fields)
     out_bytes = sum(r.size)
@@ -1105,7 +1115,7 @@ def main():
     clocks = head["clocks"]
     if rank == 0:
         line = {
-            "metric": METRIC, "value": world * res["input_bytes"] / (res["ms_per_step"] * 1e6), "unit": "GB/s",
+            "metric": METRIC, "value": job_rate(world, res["input_bytes"], res["ms_per_step"]), "unit": "GB/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if spec["dtype"] == "f64" else "f32", "data": "synthetic",
