@@ -252,9 +252,14 @@ int pc_decompress_noalloc(const void* d_in, size_t in_size, void* d_field, size_
 /*
  * End-to-end forms with HOST buffers: copy the input host -> device, run the
  * device call, copy the result device -> host, synchronize.  The caller passes
- * device staging buffers (nothing is allocated): d_field_stage holds the field
- * (field bytes), d_out_stage the container (d_out_cap bytes).  h_field and h_out
- * should be pinned for full copy speed.
+ * device staging buffers (no device memory is allocated): d_field_stage holds
+ * the field (field bytes), d_out_stage the container (d_out_cap bytes).
+ * h_field and h_out should be pinned for full copy speed.
+ * pc_decompress_host reads the header from the host copy (no read-back) and,
+ * for fields of at least 16 block planes, copies the field out in 8 slabs of
+ * whole block planes on a stream of its own while later slabs are being
+ * reconstructed; that stream and its events are created on first use, one set
+ * per host thread and device, and kept.
  */
 int pc_compress_host(const void* h_field, const size_t dims[3], int dtype, const pc_params* p,
                      void* h_out, size_t out_cap, size_t* out_size,

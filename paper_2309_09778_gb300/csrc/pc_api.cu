@@ -756,7 +756,7 @@ int plan_dec(DecPlan& P, const uint8_t* hbuf, size_t pre, const void* d_in, size
   return PC_OK;
 }
 
-int launch_dec(const DecPlan& P, const Mlp& mlp, int nsm, cudaStream_t s) {
+int launch_dec(const DecPlan& P, const Mlp& mlp, int nsm, cudaStream_t s, SlabSink* sink = nullptr) {
   if (cudaMemsetAsync(P.ds.err, 0, sizeof(int), s) != cudaSuccess) return PC_ERR_CUDA;
   if (P.H.lossless) {
     // the fourth SZ stage undone first: the raw words (and zero padding) for the Huffman decoder
@@ -766,8 +766,27 @@ int launch_dec(const DecPlan& P, const Mlp& mlp, int nsm, cudaStream_t s) {
     if (r) return r;
   }
   return P.H.dtype == PC_F32
-             ? launch_decompress<float>(P.in, P.g, P.di, P.ds, mlp, static_cast<float*>(P.out), nsm, s)
-             : launch_decompress<double>(P.in, P.g, P.di, P.ds, mlp, static_cast<double*>(P.out), nsm, s);
+             ? launch_decompress<float>(P.in, P.g, P.di, P.ds, mlp, static_cast<float*>(P.out), nsm, s, sink)
+             : launch_decompress<double>(P.in, P.g, P.di, P.ds, mlp, static_cast<double*>(P.out), nsm, s, sink);
+}
+
+// The copy stream and events of the host-buffer decoder, one set per host
+// thread and device, created on first use and kept for the thread's life.
+SlabSink* host_sink(void* h_field) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  static thread_local SlabSink sinks[64];
+  static thread_local bool ready[64];
+  SlabSink& k = sinks[dev];
+  if (!ready[dev]) {
+    if (cudaStreamCreateWithFlags(&k.cs, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    for (int i = 0; i <= kSlabs; ++i)
+      if (cudaEventCreateWithFlags(&k.ev[i], cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    ready[dev] = true;
+  }
+  k.host = h_field;
+  k.used = false;
+  return &k;
 }
 
 }  // namespace
@@ -1349,21 +1368,36 @@ int pc_compress_host(const void* h_field, const size_t dims[3], int dtype, const
 int pc_decompress_host(const void* h_in, size_t in_size, void* h_field, size_t field_cap, size_t dims_out[3],
                        int* dtype_out, void* d_in_stage, size_t d_in_cap, void* d_field_stage, void* d_ws,
                        size_t ws_bytes, void* stream) {
-  if (!h_in || !h_field || !d_in_stage || !d_field_stage) return PC_ERR_ARG;
+  if (!h_in || !h_field || !d_in_stage || !d_field_stage || !d_ws) return PC_ERR_ARG;
   if (in_size > d_in_cap) return PC_ERR_CAPACITY;
+  if (in_size < (size_t)kHdr) return PC_ERR_CORRUPT;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cudaMemcpyAsync(d_in_stage, h_in, in_size, cudaMemcpyHostToDevice, s) != cudaSuccess) return PC_ERR_CUDA;
-  size_t dims[3];
-  int dt = 0;
-  int st = pc_decompress(d_in_stage, in_size, d_field_stage, field_cap, dims, &dt, d_ws, ws_bytes, stream);
+  // the header (and the FP32 weights) straight from the host copy: no read-back
+  const size_t pre = in_size < (size_t)(kHdr + 4 * kMaxW) ? in_size : (size_t)(kHdr + 4 * kMaxW);
+  static thread_local Mlp mlp;
+  DecPlan P;
+  int st = plan_dec(P, static_cast<const uint8_t*>(h_in), pre, d_in_stage, in_size, d_field_stage, field_cap, d_ws,
+                    ws_bytes, mlp);
   if (st) return st;
-  const size_t bytes = dims[0] * dims[1] * dims[2] * (dt == PC_F64 ? 8 : 4);
-  if (bytes > field_cap) return PC_ERR_CAPACITY;
-  if (cudaMemcpyAsync(h_field, d_field_stage, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PC_ERR_CUDA;
+  const int nsm = sm_count();
+  if (nsm <= 0) return PC_ERR_CUDA;
+  if (cudaMemcpyAsync(d_in_stage, h_in, in_size, cudaMemcpyHostToDevice, s) != cudaSuccess) return PC_ERR_CUDA;
+  // the field goes to the host in slabs while later slabs are reconstructed
+  SlabSink* sink = host_sink(h_field);
+  if (!sink) return PC_ERR_CUDA;
+  int r = launch_dec(P, mlp, nsm, s, sink);
+  if (r) return r;
+  const size_t bytes = P.H.dims[0] * P.H.dims[1] * P.H.dims[2] * (P.H.dtype == PC_F64 ? 8 : 4);
+  if (!sink->used && cudaMemcpyAsync(h_field, d_field_stage, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return PC_ERR_CUDA;
+  int err = 0;
+  if (cudaMemcpyAsync(&err, P.ds.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return PC_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return PC_ERR_CUDA;
+  prof_collect();
+  if (err) return err;
   if (dims_out)
-    for (int i = 0; i < 3; ++i) dims_out[i] = dims[i];
-  if (dtype_out) *dtype_out = dt;
+    for (int i = 0; i < 3; ++i) dims_out[i] = P.H.dims[i];
+  if (dtype_out) *dtype_out = P.H.dtype;
   return PC_OK;
 }
 

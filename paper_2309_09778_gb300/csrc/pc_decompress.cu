@@ -374,7 +374,8 @@ __device__ __forceinline__ int get_q(const T* slot) { return *reinterpret_cast<c
 // memory each): its waves are latency-bound, and more resident warps hide it.
 template <typename T, int B0, int B1, int B2, int MODE, int K, int H1, int H2>
 __global__ void __launch_bounds__(256, MODE == 1 ? 2 : 3) k_recon(Geo g, const uint8_t* __restrict__ in, DecInfo di, DecScratch ds,
-                                               T* __restrict__ xo, const __grid_constant__ Mlp mlp) {
+                                               T* __restrict__ xo, const __grid_constant__ Mlp mlp,
+                                               long long brick_lo, long long brick_hi) {
   constexpr int BV = B0 * B1 * B2;
   using BS = BrickShape<BV>;
   constexpr int G = BS::G, TS = BS::TS, NWT = TS / 32;
@@ -453,7 +454,8 @@ __global__ void __launch_bounds__(256, MODE == 1 ? 2 : 3) k_recon(Geo g, const u
   const long long nbricks = g.nb[0] * g.nb[1] * nbx;
   const int team = tid / TS, t = tid % TS, wt = t >> 5;
   bool bad = false;
-  for (long long brick = blockIdx.x; brick < nbricks; brick += gridDim.x) {
+  (void)nbricks;
+  for (long long brick = brick_lo + blockIdx.x; brick < brick_hi; brick += gridDim.x) {
     const long long bxg = brick % nbx;
     const long long byz = brick / nbx;
     const long long by = byz % g.nb[1];
@@ -779,7 +781,7 @@ __global__ void __launch_bounds__(256, MODE == 1 ? 2 : 3) k_recon(Geo g, const u
 
 template <typename T, int B0, int B1, int B2, int MODE, int K, int H1, int H2>
 static int launch_r(const uint8_t* in, const Geo& g, const DecInfo& di, const DecScratch& ds, const Mlp& mlp, T* out,
-                    int nsm, cudaStream_t s) {
+                    int nsm, cudaStream_t s, SlabSink* sink) {
   constexpr int BV = B0 * B1 * B2;
   constexpr bool WIDE = MODE != 0 && (K == 13 || K == 0);
   auto kern = k_recon<T, B0, B1, B2, MODE, K, H1, H2>;
@@ -796,28 +798,52 @@ static int launch_r(const uint8_t* in, const Geo& g, const DecInfo& di, const De
   constexpr int GR = recon_blocks<BV, (int)sizeof(T), MODE, K>();
   const long long nbricks = g.nb[0] * g.nb[1] * ((g.nb[2] + GR - 1) / GR);
   long long grid = (long long)nsm * per_sm;
-  if (grid > nbricks) grid = nbricks;
-  if (grid < 1) grid = 1;
-  { ProfScope p(kStRecon, s); kern<<<(unsigned int)grid, 256, sm, s>>>(g, in, di, ds, out, mlp); }
+  // With a host sink, the field goes out in slabs of whole block planes (z), each copied to the host on the
+  // sink's stream while the next slab is reconstructed.
+  const long long per_z = g.nb[1] * ((g.nb[2] + GR - 1) / GR);  // bricks per block plane
+  const int nslab = (sink && B0 > 1 && g.nb[0] >= 2 * kSlabs) ? kSlabs : 1;
+  ProfScope p(kStRecon, s);
+  for (int k = 0; k < nslab; ++k) {
+    const long long z0 = g.nb[0] * k / nslab, z1 = g.nb[0] * (k + 1) / nslab;
+    const long long lo = nslab == 1 ? 0 : z0 * per_z, hi = nslab == 1 ? nbricks : z1 * per_z;
+    long long gk = grid < hi - lo ? grid : hi - lo;
+    if (gk < 1) gk = 1;
+    kern<<<(unsigned int)gk, 256, sm, s>>>(g, in, di, ds, out, mlp, lo, hi);
+    if (nslab > 1) {
+      const size_t row = (size_t)g.n[1] * g.n[2] * sizeof(T);
+      const size_t r0 = (size_t)(z0 * B0), r1 = (size_t)min((long long)g.n[0], z1 * B0);
+      if (cudaEventRecord(sink->ev[k], s) != cudaSuccess || cudaStreamWaitEvent(sink->cs, sink->ev[k], 0) != cudaSuccess ||
+          cudaMemcpyAsync(static_cast<uint8_t*>(sink->host) + r0 * row, reinterpret_cast<const uint8_t*>(out) + r0 * row,
+                          (r1 - r0) * row, cudaMemcpyDeviceToHost, sink->cs) != cudaSuccess)
+        return PC_ERR_CUDA;
+    }
+  }
+  if (nslab > 1) {
+    // the caller's stream waits for the last copy
+    if (cudaEventRecord(sink->ev[kSlabs], sink->cs) != cudaSuccess ||
+        cudaStreamWaitEvent(s, sink->ev[kSlabs], 0) != cudaSuccess)
+      return PC_ERR_CUDA;
+    sink->used = true;
+  }
   return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
 
 template <typename T, int B0, int B1, int B2>
 static int launch_r_shape(const uint8_t* in, const Geo& g, const DecInfo& di, const DecScratch& ds, const Mlp& mlp,
-                          T* out, int nsm, cudaStream_t s) {
-  if (!di.usenn_any) return launch_r<T, B0, B1, B2, 0, 0, 0, 0>(in, g, di, ds, mlp, out, nsm, s);
+                          T* out, int nsm, cudaStream_t s, SlabSink* sink) {
+  if (!di.usenn_any) return launch_r<T, B0, B1, B2, 0, 0, 0, 0>(in, g, di, ds, mlp, out, nsm, s, sink);
   if (di.qmode) {
     if (mlp.k == 7 && mlp.h1 == 16 && mlp.h2 == 16)
-      return launch_r<T, B0, B1, B2, 2, 7, 16, 16>(in, g, di, ds, mlp, out, nsm, s);
+      return launch_r<T, B0, B1, B2, 2, 7, 16, 16>(in, g, di, ds, mlp, out, nsm, s, sink);
     if (mlp.k == 13 && mlp.h1 == 32 && mlp.h2 == 32)
-      return launch_r<T, B0, B1, B2, 2, 13, 32, 32>(in, g, di, ds, mlp, out, nsm, s);
+      return launch_r<T, B0, B1, B2, 2, 13, 32, 32>(in, g, di, ds, mlp, out, nsm, s, sink);
     return PC_ERR_ARG;
   }
   if (mlp.k == 7 && mlp.h1 == 16 && mlp.h2 == 16)
-    return launch_r<T, B0, B1, B2, 1, 7, 16, 16>(in, g, di, ds, mlp, out, nsm, s);
+    return launch_r<T, B0, B1, B2, 1, 7, 16, 16>(in, g, di, ds, mlp, out, nsm, s, sink);
   if (mlp.k == 13 && mlp.h1 == 32 && mlp.h2 == 32)
-    return launch_r<T, B0, B1, B2, 1, 13, 32, 32>(in, g, di, ds, mlp, out, nsm, s);
-  return launch_r<T, B0, B1, B2, 1, 0, 0, 0>(in, g, di, ds, mlp, out, nsm, s);
+    return launch_r<T, B0, B1, B2, 1, 13, 32, 32>(in, g, di, ds, mlp, out, nsm, s, sink);
+  return launch_r<T, B0, B1, B2, 1, 0, 0, 0>(in, g, di, ds, mlp, out, nsm, s, sink);
 }
 
 // The fixed-point network read from the container must lie in its stated
@@ -841,7 +867,7 @@ __global__ void k_qcheck(DecInfo di, int* err) {
 
 template <typename T>
 int launch_decompress(const uint8_t* in, const Geo& g, const DecInfo& di, const DecScratch& ds, const Mlp& mlp,
-                      T* out, int nsm, cudaStream_t s) {
+                      T* out, int nsm, cudaStream_t s, SlabSink* sink) {
   if (di.qmode) k_qcheck<<<1, 256, 0, s>>>(di, ds.err);
   { ProfScope p(kStDecTables, s); k_dec_tables<<<1, 1024, 0, s>>>(in, di, ds); }
   const unsigned int nc = (unsigned int)g.nchunks;
@@ -862,7 +888,7 @@ int launch_decompress(const uint8_t* in, const Geo& g, const DecInfo& di, const 
   }
   const int b0 = g.b[0], b1 = g.b[1], b2 = g.b[2];
 #define PC_SHAPE(A, B, C) \
-  if (b0 == A && b1 == B && b2 == C) return launch_r_shape<T, A, B, C>(in, g, di, ds, mlp, out, nsm, s);
+  if (b0 == A && b1 == B && b2 == C) return launch_r_shape<T, A, B, C>(in, g, di, ds, mlp, out, nsm, s, sink);
   PC_SHAPE(8, 8, 8)
   PC_SHAPE(4, 4, 4)
   PC_SHAPE(16, 16, 16)
@@ -873,8 +899,8 @@ int launch_decompress(const uint8_t* in, const Geo& g, const DecInfo& di, const 
   return PC_ERR_ARG;
 }
 template int launch_decompress<float>(const uint8_t*, const Geo&, const DecInfo&, const DecScratch&, const Mlp&,
-                                      float*, int, cudaStream_t);
+                                      float*, int, cudaStream_t, SlabSink*);
 template int launch_decompress<double>(const uint8_t*, const Geo&, const DecInfo&, const DecScratch&, const Mlp&,
-                                       double*, int, cudaStream_t);
+                                       double*, int, cudaStream_t, SlabSink*);
 
 }  // namespace pc

@@ -292,9 +292,20 @@ int launch_quantize(const T* x, const Geo& g, const State* st, const Tabs* tabs,
                     int h2, int s_in, unsigned long long seed, unsigned int thr32, long long* q,
                     unsigned long long* qmax, cudaStream_t s);
 
+// Host destination of a decompression that copies the field out slab by slab
+// (whole block planes) on its own stream while later slabs are reconstructed;
+// `used` tells whether the reconstruction took that path (else the caller
+// copies the whole field).
+constexpr int kSlabs = 8;
+struct SlabSink {
+  void* host;
+  cudaStream_t cs;
+  cudaEvent_t ev[kSlabs + 1];
+  bool used;
+};
 template <typename T>
 int launch_decompress(const uint8_t* in, const Geo& g, const DecInfo& di, const DecScratch& ds, const Mlp& mlp,
-                      T* out, int nsm, cudaStream_t s);
+                      T* out, int nsm, cudaStream_t s, SlabSink* sink = nullptr);
 // The paper-literal data selection (Section IV.D, float32): codes, flags,
 // balance counts and histogram of a field (mode 0 Lorenzo, 1 FP32 perceptron);
 // and the drifting decoder that follows the Huffman decoder.
