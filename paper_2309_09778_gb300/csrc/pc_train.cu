@@ -229,9 +229,10 @@ __global__ void k_init_w(float* w, int nmodels, int k, int h1, int h2, unsigned 
 
 // One epoch of minibatch SGD per (lr, lambda) model (Section IV.C), each model
 // on a cluster of 8 CTAs: CTA c of the cluster takes rows 32c .. 32c + 31 of
-// every 256-row minibatch.  Warp 0 runs its rows' forward and backward passes
-// and leaves every row's inputs, activations and deltas in shared memory; the
-// CTA then sums each parameter's 32 row terms over a pairwise tree in row
+// every 256-row minibatch.  Its warps run the forward and backward passes of
+// those rows (lane = row, the hidden units split over the warps) and leave
+// every row's inputs, activations and deltas in shared memory; the CTA then
+// sums each parameter's 32 row terms over a pairwise tree in row
 // order ((r0 + r1) + (r2 + r3)) + ...; after a cluster barrier CTA c adds the
 // eight CTA sums of its slice of the parameters pairwise, ((q0 + q1) +
 // (q2 + q3)) + ((q4 + q5) + (q6 + q7)), updates them and writes the new
@@ -239,10 +240,11 @@ __global__ void k_init_w(float* w, int nmodels, int k, int h1, int h2, unsigned 
 // a second cluster barrier ends the step.  The gradient is therefore the
 // same balanced pairwise tree over the minibatch's 256 rows, in row order.
 constexpr int kTrainCluster = 8;
-constexpr int kTrainRows = 32;  // rows per CTA
+constexpr int kTrainRows = 32;   // rows per CTA
+constexpr int kTrainWarps = 8;   // warps per CTA: hidden units of the row phase, parameters of the sums
 
 template <int K, int H1, int H2>
-__global__ void __cluster_dims__(kTrainCluster, 1, 1) __launch_bounds__(128)
+__global__ void __cluster_dims__(kTrainCluster, 1, 1) __launch_bounds__(32 * kTrainWarps)
     k_train(const int* __restrict__ tin, const int* __restrict__ ttg, const uint8_t* __restrict__ tus,
             float* __restrict__ wbuf, const float* __restrict__ lrs, const float* __restrict__ lams,
             const TrainCtl* __restrict__ ctl) {
@@ -292,15 +294,15 @@ __global__ void __cluster_dims__(kTrainCluster, 1, 1) __launch_bounds__(128)
   for (unsigned long long s0 = 0; s0 < n; s0 += 256) {
     const int B = (int)((n - s0) < 256ull ? (n - s0) : 256ull);
     // forward and backward of the CTA's 32 rows (lane = row), the hidden units
-    // split over the four warps; each unit's sums run in the same order as a
-    // single thread's would
+    // split over the warps; each unit's sums run in the same order as a single
+    // thread's would
     {
       const int lane = tid & 31, q = tid >> 5;
       const int lrow = rank * kTrainRows + lane;
       const bool valid = lrow < B;
       const unsigned long long r = s0 + (valid ? lrow : 0);
       float* v = V + lane * VS;
-      constexpr int NU1 = (H1 + 3) / 4, NU2 = (H2E + 3) / 4;
+      constexpr int NU1 = (H1 + kTrainWarps - 1) / kTrainWarps, NU2 = (H2E + kTrainWarps - 1) / kTrainWarps;
       float u[K], z1[NU1], z2[NU2];
 #pragma unroll
       for (int i = 0; i < K; ++i) u[i] = valid ? __fmul_rn(small_int_to_float(tin[r * K + i]), sig) : 0.0f;
@@ -436,22 +438,38 @@ __global__ void __launch_bounds__(256) k_val(const int* __restrict__ vin, const 
   const long long R = 1ll << (m - 1);
   const unsigned long long n = ctl->nval;
   unsigned long long cost = 0;
-  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (unsigned long long)gridDim.x * blockDim.x) {
-    if (!vus[i]) continue;
-    int in[K];
-#pragma unroll
-    for (int q = 0; q < K; ++q) in[q] = vin[i * K + q];
-    long long pr = 0;
-    if (lz) {
-#pragma unroll
-      for (int q = 0; q < K; ++q) pr += (long long)lz_w(K, q) * in[q];
-    } else {
-      pr = round_pred(mlp_fwd<K, H1, H2>(s_m, in, sig, unsig));
-    }
+  auto bits = [&](unsigned long long i, long long pr) {
     const long long d = (long long)vtg[i] - pr;
     const unsigned long long a = (unsigned long long)(d < 0 ? -d : d);
-    cost += (unsigned long long)bitlen_u((unsigned int)(a < (unsigned long long)R ? a : (unsigned long long)R));
+    return (unsigned long long)bitlen_u((unsigned int)(a < (unsigned long long)R ? a : (unsigned long long)R));
+  };
+  // two samples per thread: the packed forward gives each the scalar forward's bits
+  for (unsigned long long i2 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; 2 * i2 < n;
+       i2 += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long i0 = 2 * i2, i1 = i0 + 1;
+    const bool u0 = vus[i0] != 0, u1 = i1 < n && vus[i1] != 0;
+    if (!u0 && !u1) continue;
+    int in0[K], in1[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      in0[q] = vin[i0 * K + q];
+      in1[q] = i1 < n ? vin[i1 * K + q] : 0;
+    }
+    long long p0 = 0, p1 = 0;
+    if (lz) {
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        p0 += (long long)lz_w(K, q) * in0[q];
+        p1 += (long long)lz_w(K, q) * in1[q];
+      }
+    } else {
+      float f0, f1;
+      mlp_fwd2<K, H1, H2>(s_m, in0, in1, sig, unsig, f0, f1);
+      p0 = round_pred(f0);
+      p1 = round_pred(f1);
+    }
+    if (u0) cost += bits(i0, p0);
+    if (u1) cost += bits(i1, p1);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) cost += __shfl_xor_sync(0xFFFFFFFFu, cost, o);
@@ -470,8 +488,8 @@ template <int K, int H1, int H2>
 static int launch_train_models(const TrainBufs& tb, int nmodels, int m, cudaStream_t s) {
   {
     ProfScope p(kStTrain, s);
-    k_train<K, H1, H2><<<nmodels * kTrainCluster, 128, 0, s>>>(tb.tin, tb.ttg, tb.tus, tb.w, tb.lrs, tb.lams,
-                                                               reinterpret_cast<const TrainCtl*>(tb.ctl));
+    k_train<K, H1, H2><<<nmodels * kTrainCluster, 32 * kTrainWarps, 0, s>>>(
+        tb.tin, tb.ttg, tb.tus, tb.w, tb.lrs, tb.lams, reinterpret_cast<const TrainCtl*>(tb.ctl));
   }
   dim3 gv(152, nmodels + 1);
   k_val<K, H1, H2><<<gv, 256, 0, s>>>(tb.vin, tb.vtg, tb.vus, tb.w, nmodels, m,
