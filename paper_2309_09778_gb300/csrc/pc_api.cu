@@ -756,9 +756,10 @@ int plan_dec(DecPlan& P, const uint8_t* hbuf, size_t pre, const void* d_in, size
   return PC_OK;
 }
 
-int launch_dec(const DecPlan& P, const Mlp& mlp, int nsm, cudaStream_t s, SlabSink* sink = nullptr) {
-  if (cudaMemsetAsync(P.ds.err, 0, sizeof(int), s) != cudaSuccess) return PC_ERR_CUDA;
-  if (P.H.lossless) {
+int launch_dec(const DecPlan& P, const Mlp& mlp, int nsm, cudaStream_t s, SlabSink* sink = nullptr,
+               int phase = kDecAll) {
+  if (phase != kDecRecon && cudaMemsetAsync(P.ds.err, 0, sizeof(int), s) != cudaSuccess) return PC_ERR_CUDA;
+  if (phase != kDecRecon && P.H.lossless) {
     // the fourth SZ stage undone first: the raw words (and zero padding) for the Huffman decoder
     const unsigned long long nraw = 4ull * P.H.swords;
     if (cudaMemsetAsync(P.lzraw + nraw, 0, al16(nraw) + 64 - nraw, s) != cudaSuccess) return PC_ERR_CUDA;
@@ -766,8 +767,9 @@ int launch_dec(const DecPlan& P, const Mlp& mlp, int nsm, cudaStream_t s, SlabSi
     if (r) return r;
   }
   return P.H.dtype == PC_F32
-             ? launch_decompress<float>(P.in, P.g, P.di, P.ds, mlp, static_cast<float*>(P.out), nsm, s, sink)
-             : launch_decompress<double>(P.in, P.g, P.di, P.ds, mlp, static_cast<double*>(P.out), nsm, s, sink);
+             ? launch_decompress<float>(P.in, P.g, P.di, P.ds, mlp, static_cast<float*>(P.out), nsm, s, sink, phase)
+             : launch_decompress<double>(P.in, P.g, P.di, P.ds, mlp, static_cast<double*>(P.out), nsm, s, sink,
+                                         phase);
 }
 
 // The copy stream and events of the host-buffer decoder, one set per host
@@ -1292,8 +1294,28 @@ int pc_decompress_batch(int nfields, const void* d_in, const size_t* offsets, co
     if (st) return st;
     wo += w;
   }
+  // tables and offsets per field, the Huffman decoders of up to 32 fields in one launch (small fields alone
+  // fill few SMs), then each field's reconstruction
   for (int i = 0; i < nfields; ++i) {
-    int st = launch_dec(P[i], mlps[i], nsm, s);
+    int st = launch_dec(P[i], mlps[i], nsm, s, nullptr, kDecPrep);
+    if (st) return st;
+  }
+  std::vector<DecJob> jl;
+  for (int i0 = 0; i0 < nfields; i0 += kMaxDecJobs) {
+    jl.clear();
+    for (int i = i0; i < nfields && i < i0 + kMaxDecJobs; ++i) {
+      DecJob j{};
+      j.g = P[i].g;
+      j.in = P[i].in;
+      j.di = P[i].di;
+      j.ds = P[i].ds;
+      jl.push_back(j);
+    }
+    int st = launch_huff_jobs(jl.data(), (int)jl.size(), s);
+    if (st) return st;
+  }
+  for (int i = 0; i < nfields; ++i) {
+    int st = launch_dec(P[i], mlps[i], nsm, s, nullptr, kDecRecon);
     if (st) return st;
   }
   std::vector<int> errs((size_t)nfields, 0);

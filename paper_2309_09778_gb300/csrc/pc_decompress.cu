@@ -185,8 +185,9 @@ __global__ void __launch_bounds__(256) k_dec_blockoff(Geo g, const uint8_t* __re
 constexpr int kDecThreads = 128;  // threads (blocks decoded) per CTA of k_huff_decode
 constexpr int kShortBits = 12;    // codes up to this long take their length from a table
 
-__global__ void __launch_bounds__(kDecThreads) k_huff_decode(Geo g, const uint8_t* __restrict__ in, DecInfo di,
-                                                     DecScratch ds) {
+// The decoder of CTA `cta` of one field (kDecThreads blocks, one per thread).
+__device__ __forceinline__ void huff_decode_cta(const Geo& g, const uint8_t* __restrict__ in, const DecInfo& di,
+                                                const DecScratch& ds, long long cta) {
   // per length l: left-justified end of its code range (the ranges tile the
   // 24-bit window space in length order) and list position minus first code
   __shared__ unsigned int s_lim[32];
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(kDecThreads) k_huff_decode(Geo g, const uint8_
   }
   __syncthreads();
   if (*ds.err) return;
-  const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long b = cta * blockDim.x + threadIdx.x;
   if (b >= g.nblocks) return;
   // range ends of the long lengths, in registers
   unsigned int lim[kLmax - kShortBits];
@@ -319,6 +320,36 @@ __global__ void __launch_bounds__(kDecThreads) k_huff_decode(Geo g, const uint8_
   // a corrupt stream shows as a window past every code range or a bit count
   // that differs from the block table's
   if (bad || used != nbits) atomicExch(ds.err, PC_ERR_CORRUPT);
+}
+
+__global__ void __launch_bounds__(kDecThreads) k_huff_decode(Geo g, const uint8_t* __restrict__ in, DecInfo di,
+                                                     DecScratch ds) {
+  huff_decode_cta(g, in, di, ds, blockIdx.x);
+}
+
+// Many fields in one launch: CTA c belongs to the last job whose first CTA is
+// at most c (the job table travels as a kernel parameter).
+__global__ void __launch_bounds__(kDecThreads) k_huff_decode_jobs(const __grid_constant__ DecJobs jobs) {
+  int jn = 0;
+  while (jn + 1 < jobs.n && (long long)blockIdx.x >= jobs.j[jn + 1].cta0) ++jn;
+  const DecJob& J = jobs.j[jn];
+  huff_decode_cta(J.g, J.in, J.di, J.ds, (long long)blockIdx.x - J.cta0);
+}
+
+int launch_huff_jobs(const DecJob* jl, int n, cudaStream_t s) {
+  if (n < 1 || n > kMaxDecJobs) return PC_ERR_ARG;
+  static thread_local DecJobs jobs;
+  jobs.n = n;
+  long long ctas = 0;
+  for (int i = 0; i < n; ++i) {
+    jobs.j[i] = jl[i];
+    jobs.j[i].cta0 = ctas;
+    ctas += (jl[i].g.nblocks + kDecThreads - 1) / kDecThreads;
+  }
+  if (ctas < 1) return PC_OK;
+  ProfScope p(kStHuffDecode, s);
+  k_huff_decode_jobs<<<(unsigned int)ctas, kDecThreads, 0, s>>>(jobs);
+  return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
 
 // ---------------------------------------------------------------------------
@@ -867,21 +898,25 @@ __global__ void k_qcheck(DecInfo di, int* err) {
 
 template <typename T>
 int launch_decompress(const uint8_t* in, const Geo& g, const DecInfo& di, const DecScratch& ds, const Mlp& mlp,
-                      T* out, int nsm, cudaStream_t s, SlabSink* sink) {
-  if (di.qmode) k_qcheck<<<1, 256, 0, s>>>(di, ds.err);
-  { ProfScope p(kStDecTables, s); k_dec_tables<<<1, 1024, 0, s>>>(in, di, ds); }
-  const unsigned int nc = (unsigned int)g.nchunks;
-  {
-    ProfScope p(kStDecScan, s);
-    k_dec_chunksum<<<nc, 256, 0, s>>>(g, in, di, ds);
-    k_dec_chunkscan<<<1, 1024, 0, s>>>(g, di, ds);
-    k_dec_blockoff<<<nc, 256, 0, s>>>(g, in, di, ds);
+                      T* out, int nsm, cudaStream_t s, SlabSink* sink, int phase) {
+  if (phase != kDecRecon) {
+    if (di.qmode) k_qcheck<<<1, 256, 0, s>>>(di, ds.err);
+    { ProfScope p(kStDecTables, s); k_dec_tables<<<1, 1024, 0, s>>>(in, di, ds); }
+    const unsigned int nc = (unsigned int)g.nchunks;
+    {
+      ProfScope p(kStDecScan, s);
+      k_dec_chunksum<<<nc, 256, 0, s>>>(g, in, di, ds);
+      k_dec_chunkscan<<<1, 1024, 0, s>>>(g, di, ds);
+      k_dec_blockoff<<<nc, 256, 0, s>>>(g, in, di, ds);
+    }
+    if (phase == kDecPrep) return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
+    {
+      ProfScope p(kStHuffDecode, s);
+      k_huff_decode<<<(unsigned int)((g.nblocks + kDecThreads - 1) / kDecThreads), kDecThreads, 0, s>>>(g, in, di,
+                                                                                                       ds);
+    }
+    if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
   }
-  {
-    ProfScope p(kStHuffDecode, s);
-    k_huff_decode<<<(unsigned int)((g.nblocks + kDecThreads - 1) / kDecThreads), kDecThreads, 0, s>>>(g, in, di, ds);
-  }
-  if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
   if (di.literal) {
     if constexpr (sizeof(T) == 4) return launch_lit_decode(in, g, di, ds, mlp, out, nsm, s);
     return PC_ERR_ARG;
@@ -899,8 +934,8 @@ int launch_decompress(const uint8_t* in, const Geo& g, const DecInfo& di, const 
   return PC_ERR_ARG;
 }
 template int launch_decompress<float>(const uint8_t*, const Geo&, const DecInfo&, const DecScratch&, const Mlp&,
-                                      float*, int, cudaStream_t, SlabSink*);
+                                      float*, int, cudaStream_t, SlabSink*, int);
 template int launch_decompress<double>(const uint8_t*, const Geo&, const DecInfo&, const DecScratch&, const Mlp&,
-                                       double*, int, cudaStream_t, SlabSink*);
+                                       double*, int, cudaStream_t, SlabSink*, int);
 
 }  // namespace pc

@@ -303,9 +303,28 @@ struct SlabSink {
   cudaEvent_t ev[kSlabs + 1];
   bool used;
 };
+// Phases of a decompression: everything, only what precedes the Huffman
+// decoder (checks, tables, offsets), or only what follows it (reconstruction).
+constexpr int kDecAll = 0, kDecPrep = 1, kDecRecon = 2;
 template <typename T>
 int launch_decompress(const uint8_t* in, const Geo& g, const DecInfo& di, const DecScratch& ds, const Mlp& mlp,
-                      T* out, int nsm, cudaStream_t s, SlabSink* sink = nullptr);
+                      T* out, int nsm, cudaStream_t s, SlabSink* sink = nullptr, int phase = kDecAll);
+// One field of a fused Huffman-decoder launch; cta0 is its first CTA.
+struct DecJob {
+  Geo g;
+  const uint8_t* in;
+  DecInfo di;
+  DecScratch ds;
+  long long cta0;
+};
+constexpr int kMaxDecJobs = 32;
+struct DecJobs {
+  int n;
+  int pad_;
+  DecJob j[kMaxDecJobs];
+};
+// The Huffman decoder of n fields (each prepared by a kDecPrep phase) in one launch.
+int launch_huff_jobs(const DecJob* jobs, int n, cudaStream_t s);
 // The paper-literal data selection (Section IV.D, float32): codes, flags,
 // balance counts and histogram of a field (mode 0 Lorenzo, 1 FP32 perceptron);
 // and the drifting decoder that follows the Huffman decoder.
