@@ -221,8 +221,11 @@ int pc_compress_batch(int nfields, const void* const* d_fields, const size_t* di
  * Batched decompression of nfields containers held in one device buffer
  * (container i at d_in + offsets[i], sizes[i] bytes) into d_fields[i]
  * (field_caps[i] bytes each).  Reads every header back in one
- * synchronization, then runs each field's decoder without further host
- * round trips; synchronizes once more at the end.  The workspace size comes
+ * synchronization, prepares every field's decoder tables, runs the Huffman
+ * decoders of up to 32 fields in one launch, then the reconstructions on four
+ * streams of the library's own (created on first use, one set per host thread
+ * and device, and kept) that the caller's stream waits for; synchronizes once
+ * more at the end.  The workspace size comes
  * from the 256-byte headers (host copies) through
  * pc_decompress_batch_workspace_size.
  */

@@ -772,6 +772,30 @@ int launch_dec(const DecPlan& P, const Mlp& mlp, int nsm, cudaStream_t s, SlabSi
                                          phase);
 }
 
+// Streams of the batched decoder's reconstructions (and their fork and join
+// events), one set per host thread and device, created on first use and kept.
+constexpr int kAuxStreams = 4;
+struct AuxStreams {
+  cudaStream_t s[kAuxStreams];
+  cudaEvent_t fork, join[kAuxStreams];
+};
+AuxStreams* aux_streams() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  static thread_local AuxStreams sets[64];
+  static thread_local bool ready[64];
+  AuxStreams& a = sets[dev];
+  if (!ready[dev]) {
+    for (int i = 0; i < kAuxStreams; ++i)
+      if (cudaStreamCreateWithFlags(&a.s[i], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&a.join[i], cudaEventDisableTiming) != cudaSuccess)
+        return nullptr;
+    if (cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    ready[dev] = true;
+  }
+  return &a;
+}
+
 // The copy stream and events of the host-buffer decoder, one set per host
 // thread and device, created on first use and kept for the thread's life.
 SlabSink* host_sink(void* h_field) {
@@ -1314,10 +1338,19 @@ int pc_decompress_batch(int nfields, const void* d_in, const size_t* offsets, co
     int st = launch_huff_jobs(jl.data(), (int)jl.size(), s);
     if (st) return st;
   }
+  // reconstructions on a few streams of their own, so that small fields run side by side
+  AuxStreams* aux = aux_streams();
+  if (!aux) return PC_ERR_CUDA;
+  if (cudaEventRecord(aux->fork, s) != cudaSuccess) return PC_ERR_CUDA;
+  for (int a = 0; a < kAuxStreams; ++a)
+    if (cudaStreamWaitEvent(aux->s[a], aux->fork, 0) != cudaSuccess) return PC_ERR_CUDA;
   for (int i = 0; i < nfields; ++i) {
-    int st = launch_dec(P[i], mlps[i], nsm, s, nullptr, kDecRecon);
+    int st = launch_dec(P[i], mlps[i], nsm, aux->s[i % kAuxStreams], nullptr, kDecRecon);
     if (st) return st;
   }
+  for (int a = 0; a < kAuxStreams; ++a)
+    if (cudaEventRecord(aux->join[a], aux->s[a]) != cudaSuccess || cudaStreamWaitEvent(s, aux->join[a], 0) != cudaSuccess)
+      return PC_ERR_CUDA;
   std::vector<int> errs((size_t)nfields, 0);
   for (int i = 0; i < nfields; ++i)
     if (cudaMemcpyAsync(&errs[i], P[i].ds.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
