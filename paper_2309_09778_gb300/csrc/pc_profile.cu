@@ -7,7 +7,7 @@
 
 namespace pc {
 namespace {
-constexpr int kPool = 256;
+constexpr int kPool = 4096;  // event pairs: enough for a 64-field batch (about 12 launches per field)
 std::mutex g_mu;
 bool g_on = false;
 bool g_made = false;
