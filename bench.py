@@ -486,11 +486,30 @@ def hbm_fractions(res, peak):
             "decompress": {"algorithmic_bytes": out + n, "achieved_gbs": d, "frac": d / peak["hbm_gbs"]}}
 
 
-def stage_roofline(workload, stage, ms, res, spec, form, nn_pts, nsm, sm_mhz, peak):
+# FP64 flops of the float64 transform per point (Eq. 6, 7 and the bound check), 2 per fused multiply-add:
+# log2 (m - 1, m + 1, the quotient, s^2, 10 fma, two products, the exponent's sum) = 27; the code's product
+# and its inverse's product = 2; exp2 (t - n, times ln 2, 13 fma, three power-of-two scalings) = 31; the error
+# and its bound = 2.  The inverse transform of a coded point is its product and exp2: 32.
+F64_FLOPS_TRANSFORM = 62
+F64_FLOPS_INVERSE = 32
+# the FP64 rate of the part (nominal; no measured figure exists for it)
+F64_PEAK_TFLOPS = 1.25
+
+
+def stage_roofline(workload, stage, ms, res, spec, form, nn_pts, nsm, sm_mhz, peak, coded_pts=0):
     """The dominant stage against its bounding roof, from its algorithmic work per launch."""
     n_pts = res["points"]
     ts = res["input_bytes"] // n_pts
     nf = len(spec.get("_fields", [])) or 1
+    if ts == 8 and stage in ("compress", "recon"):
+        # the float64 transform on the narrow FP64 pipe binds these stages; coded points are those that are
+        # neither a block's anchor nor a stored balance point
+        flops = (F64_FLOPS_TRANSFORM * n_pts if stage == "compress" else F64_FLOPS_INVERSE * coded_pts) / nf
+        a = flops / (ms * 1e-3) / 1e12
+        return {"kernel": stage, "bound": "alu", "achieved": a, "peak": F64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": a / F64_PEAK_TFLOPS, "traffic": traffic_for(workload, stage, form),
+                "peak_source": "nominal FP64 rate of the part (1.25 TFLOP/s dense); no measured FP64 peak",
+                "algorithmic_flops_per_launch": flops, "avg_launch_ms": ms}
     if stage in ("compress", "recon") and form in ("fp32", "bf16"):
         pts = nn_pts if stage == "recon" else n_pts
         flops = net_flops(spec["k"], spec["h1"], spec["h2"], form) * pts / nf
@@ -623,11 +642,13 @@ def run_workload(torch, pc, name, args, dev, stream, flush, peak, nsm, dist=None
     res["hbm_roofline"] = hbm_fractions(res, peak)
     # perceptron-predicted points (the recon stage's perceptron work)
     nn_pts = 0
+    coded_pts = 0
     nn_blocks = []
     for i, d in enumerate(fields):
         blob = r.out[i][: r.size[i]].cpu().numpy().tobytes()
         flags, free_pts = block_census(blob, tuple(d.shape))
         nn_pts += int(free_pts[flags].sum())
+        coded_pts += int(free_pts.sum())
         nn_blocks.append(float(flags.mean()))
     res["perceptron_blocks_fraction"] = nn_blocks
     res["perceptron_points"] = nn_pts
@@ -636,7 +657,7 @@ def run_workload(torch, pc, name, args, dev, stream, flush, peak, nsm, dist=None
     nlaunch = res["stage_launches_per_step"][dom]
     sm_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
     res["roofline"] = stage_roofline(name, dom, st[dom] / nlaunch, res, spec, form, nn_pts / len(fields), nsm,
-                                     sm_mhz, peak)
+                                     sm_mhz, peak, coded_pts)
     res["training"] = [{k: v for k, v in inf.items() if k not in ("w", "q")} for inf in infos]
     res["training_seconds_total"] = sum(inf["train_s"] for inf in infos) + sum(inf["quant_s"] or 0 for inf in infos)
     out = {"res": res, "runner": r, "infos": infos, "spec": spec, "form": form, "clocks": clocks}

@@ -796,6 +796,22 @@ AuxStreams* aux_streams() {
   return &a;
 }
 
+// Work recorded on s so far runs before anything later on the aux streams.
+int aux_fork(AuxStreams* a, cudaStream_t s) {
+  if (!a || cudaEventRecord(a->fork, s) != cudaSuccess) return PC_ERR_CUDA;
+  for (int i = 0; i < kAuxStreams; ++i)
+    if (cudaStreamWaitEvent(a->s[i], a->fork, 0) != cudaSuccess) return PC_ERR_CUDA;
+  return PC_OK;
+}
+
+// Everything recorded on the aux streams so far runs before anything later on s.
+int aux_join(AuxStreams* a, cudaStream_t s) {
+  for (int i = 0; i < kAuxStreams; ++i)
+    if (cudaEventRecord(a->join[i], a->s[i]) != cudaSuccess || cudaStreamWaitEvent(s, a->join[i], 0) != cudaSuccess)
+      return PC_ERR_CUDA;
+  return PC_OK;
+}
+
 // The copy stream and events of the host-buffer decoder, one set per host
 // thread and device, created on first use and kept for the thread's life.
 SlabSink* host_sink(void* h_field) {
@@ -1223,9 +1239,12 @@ int pc_compress_batch(int nfields, const void* const* d_fields, const size_t* di
     oo += osz;
   }
   offsets[nfields] = oo;
-  // a1, a2 per field
+  // a1, a2 per field, on a few streams of their own so that small fields run side by side
+  AuxStreams* aux = aux_streams();
+  if ((st = aux_fork(aux, s))) return st;
   for (int i = 0; i < nfields; ++i)
-    if ((st = launch_head(F[i], s, nsm))) return st;
+    if ((st = launch_head(F[i], aux->s[i % kAuxStreams], nsm))) return st;
+  if ((st = aux_join(aux, s))) return st;
   // a4-a9: one persistent launch per group of fields that share dtype, block
   // shape and predictor form (and, for the FP32 form, the weights)
   std::vector<int> done((size_t)nfields, 0);
@@ -1254,9 +1273,11 @@ int pc_compress_batch(int nfields, const void* const* d_fields, const size_t* di
                              : launch_compress<double>(jl.data(), (int)jl.size(), F[i].mode, mlps[i], nsm, s, next);
     if (st) return st;
   }
-  // a10-a12 per field
+  // a10-a12 per field, on the aux streams again
+  if ((st = aux_fork(aux, s))) return st;
   for (int i = 0; i < nfields; ++i)
-    if ((st = launch_tail(F[i], mlps[i], s, nsm))) return st;
+    if ((st = launch_tail(F[i], mlps[i], aux->s[i % kAuxStreams], nsm))) return st;
+  if ((st = aux_join(aux, s))) return st;
   std::vector<State> hs((size_t)nfields);
   for (int i = 0; i < nfields; ++i)
     if (cudaMemcpyAsync(&hs[i], F[i].stp, sizeof(State), cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -1340,17 +1361,12 @@ int pc_decompress_batch(int nfields, const void* d_in, const size_t* offsets, co
   }
   // reconstructions on a few streams of their own, so that small fields run side by side
   AuxStreams* aux = aux_streams();
-  if (!aux) return PC_ERR_CUDA;
-  if (cudaEventRecord(aux->fork, s) != cudaSuccess) return PC_ERR_CUDA;
-  for (int a = 0; a < kAuxStreams; ++a)
-    if (cudaStreamWaitEvent(aux->s[a], aux->fork, 0) != cudaSuccess) return PC_ERR_CUDA;
+  if (int st = aux_fork(aux, s)) return st;
   for (int i = 0; i < nfields; ++i) {
     int st = launch_dec(P[i], mlps[i], nsm, aux->s[i % kAuxStreams], nullptr, kDecRecon);
     if (st) return st;
   }
-  for (int a = 0; a < kAuxStreams; ++a)
-    if (cudaEventRecord(aux->join[a], aux->s[a]) != cudaSuccess || cudaStreamWaitEvent(s, aux->join[a], 0) != cudaSuccess)
-      return PC_ERR_CUDA;
+  if (int st = aux_join(aux, s)) return st;
   std::vector<int> errs((size_t)nfields, 0);
   for (int i = 0; i < nfields; ++i)
     if (cudaMemcpyAsync(&errs[i], P[i].ds.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)

@@ -139,26 +139,34 @@ __device__ __forceinline__ double pow2_scale_d(int k) {
   return __longlong_as_double((long long)((unsigned long long)(k + 1023) << 52));
 }
 
+// The tests below read the bit pattern (ordered like the value for a
+// non-negative double, sign bit set for a negative one) and halve m by its
+// exponent (exact): the same results as the floating-point forms, kept off
+// the narrow FP64 pipe.
 __device__ inline double dev_log2d(double y) {
-  const double sqrt2 = 0x1.6a09e667f3bcdp+0;
+  const unsigned long long sqrt2_bits = 0x3FF6A09E667F3BCDull;  // 0x1.6a09e667f3bcdp+0
   const double two_over_ln2 = 0x1.71547652b82fep+1;
   int extra = 0;
-  if (y < 0x1p-1022) {  // subnormal: rescale into the normal range
+  if (__double_as_longlong(y) < 0x0010000000000000ll) {  // y < 2^-1022, subnormal: rescale into the normal range
     y = __dmul_rn(y, 0x1p64);
     extra = -64;
   }
-  unsigned long long b = (unsigned long long)__double_as_longlong(y);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(y);
   int e = (int)((b >> 52) & 0x7FFull) - 1023;
-  double m = __longlong_as_double((long long)((b & 0xFFFFFFFFFFFFFull) | 0x3FF0000000000000ull));
-  if (m > sqrt2) {
-    m = __dmul_rn(m, 0.5);
+  unsigned long long mb = (b & 0xFFFFFFFFFFFFFull) | 0x3FF0000000000000ull;
+  if (mb > sqrt2_bits) {  // m > sqrt 2: m / 2
+    mb -= 1ull << 52;
     e += 1;
   }
+  const double m = __longlong_as_double((long long)mb);
+  // 1/(2j+1) for j = 0..10, each rounded once, folded at compile time
+  constexpr double inv_odd[11] = {1.0,        1.0 / 3.0,  1.0 / 5.0,  1.0 / 7.0,  1.0 / 9.0, 1.0 / 11.0,
+                                  1.0 / 13.0, 1.0 / 15.0, 1.0 / 17.0, 1.0 / 19.0, 1.0 / 21.0};
   double s = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
   double z = __dmul_rn(s, s);
-  double p = 1.0 / 21.0;
+  double p = inv_odd[10];
 #pragma unroll
-  for (int j = 9; j >= 0; --j) p = __fma_rn(p, z, 1.0 / (double)(2 * j + 1));
+  for (int j = 9; j >= 0; --j) p = __fma_rn(p, z, inv_odd[j]);
   double t = __dmul_rn(__dmul_rn(s, p), two_over_ln2);
   double r = __dadd_rn((double)e, t);
   return extra ? __dadd_rn(r, (double)extra) : r;
@@ -166,19 +174,31 @@ __device__ inline double dev_log2d(double y) {
 
 __device__ inline double dev_exp2d(double t) {
   const double ln2 = 0x1.62e42fefa39efp-1;
-  // 1/i! for i = 0..13, each the division 1/i! with i! exact in double
-  t = fmin(fmax(t, -2100.0), 2100.0);
+  // 1/i! for i = 0..13: i! is exact in double, so each entry is the division
+  // rounded once, folded at compile time (the FP64 pipe is narrow on this part)
+  constexpr double inv_fact[14] = {1.0,
+                                   1.0,
+                                   1.0 / 2.0,
+                                   1.0 / 6.0,
+                                   1.0 / 24.0,
+                                   1.0 / 120.0,
+                                   1.0 / 720.0,
+                                   1.0 / 5040.0,
+                                   1.0 / 40320.0,
+                                   1.0 / 362880.0,
+                                   1.0 / 3628800.0,
+                                   1.0 / 39916800.0,
+                                   1.0 / 479001600.0,
+                                   1.0 / 6227020800.0};
+  if (((unsigned long long)__double_as_longlong(t) & 0x7FFFFFFFFFFFFFFFull) > 0x40A0680000000000ull)  // |t| > 2100
+    t = __double_as_longlong(t) < 0 ? -2100.0 : 2100.0;
   double nf = rint(t);
   int k = (int)nf;
   double f = __dsub_rn(t, nf);
   double u = __dmul_rn(f, ln2);
-  double fact = 6227020800.0;  // 13!
-  double p = __ddiv_rn(1.0, fact);
+  double p = inv_fact[13];
 #pragma unroll
-  for (int i = 12; i >= 0; --i) {
-    fact = fact / (double)(i + 1);  // exact: i! is an integer below 2^53
-    p = __fma_rn(p, u, __ddiv_rn(1.0, fact));
-  }
+  for (int i = 12; i >= 0; --i) p = __fma_rn(p, u, inv_fact[i]);
   int k1 = k / 3;
   int k2 = (k - k1) / 2;
   int k3 = k - k1 - k2;
@@ -250,7 +270,7 @@ template <> struct Num<double> {
     unsigned long long b = (unsigned long long)__double_as_longlong(x);
     double a = fabs(x);
     if (b == 0ull) { ok = true; return c.Zq; }
-    if (a < 0x1p-1022) { ok = false; return c.Zq; }
+    if ((b & 0x7FFFFFFFFFFFFFFFull) < 0x0010000000000000ull) { ok = false; return c.Zq; }  // a < 2^-1022
     double l = dev_log2d(a);
     double nf = rint(__dmul_rn(l, c.invd));
     int n = (int)nf;
