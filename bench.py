@@ -1008,19 +1008,23 @@ def profile_case(form: str):
     import paper_2309_09778_gb300.pc as pc
     from paper_2309_09778_gb300 import gen
     dev = torch.device("cuda:0")
-    d = torch.exp(1.5 * gen.grf_device((256, 256, 512), 2.0, 0, dev)).to(torch.float32)
-    eb = 1e-4
-    thr32 = thr_for(tuple(d.shape), 1 << 18)
-    tp = pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_FP32, stencil=13, hidden=(32, 32))
+    if form == "f64":
+        # the float64 workload's recipe at half its size (151 MB)
+        d = gen.wide_range_device((128, 384, 384), 3.0, 0, dev, 8.0, 0.01)
+        eb, k, h, thr32, dt = 1e-5, 7, (16, 16), THR10, pc.PC_F64
+    else:
+        d = torch.exp(1.5 * gen.grf_device((256, 256, 512), 2.0, 0, dev)).to(torch.float32)
+        eb, k, h, thr32, dt = 1e-4, 13, (32, 32), thr_for((256, 256, 512), 1 << 18), pc.PC_F32
+    tp = pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_FP32, stencil=k, hidden=h)
     lrs, lams = pc.default_grid()
-    tws = torch.empty(pc.pc_train_workspace_size(d.shape, pc.PC_F32, tp, thr32, lrs.size), dtype=torch.uint8,
+    tws = torch.empty(pc.pc_train_workspace_size(d.shape, dt, tp, thr32, lrs.size), dtype=torch.uint8,
                       device=dev)
     W, s_in, chosen, _ = pc.pc_train(d, tp, 0, thr32, lrs, lams, tws)
-    p = pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_FP32, stencil=13, hidden=(32, 32), s_in=s_in,
+    p = pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_FP32, stencil=k, hidden=h, s_in=s_in,
                        weights=W[max(chosen, 0)])
-    if form == "bf16":
+    if form in ("bf16", "f64"):
         q = pc.pc_quantize(d, p, 0, thr32, tws)
-        p = pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_BF16, stencil=13, hidden=(32, 32), s_in=s_in, qnet=q)
+        p = pc.make_params(eb, BLOCK, pred=pc.PC_PRED_MLP_BF16, stencil=k, hidden=h, s_in=s_in, qnet=q)
     del tws
     blob = pc.compress(d, p)
     y = pc.decompress(blob)
@@ -1043,9 +1047,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--profile-case", default=None, choices=["bf16", "fp32"],
+    ap.add_argument("--profile-case", default=None, choices=["bf16", "fp32", "f64"],
                     help="run one compress and one decompress of a 256x256x512 density field (one quarter of a "
-                         "headline field, same recipe, 13-point 32/32 network trained on 2^18 samples) for "
+                         "headline field, same recipe, 13-point 32/32 network trained on 2^18 samples), or with "
+                         "f64 of a 128x384x384 float64 field (the float64 workload's recipe at half size), for "
                          "profiler captures, then exit")
     args = ap.parse_args()
     if args.profile_case:
