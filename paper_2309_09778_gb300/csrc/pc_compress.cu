@@ -334,12 +334,14 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const __grid_con
   uint8_t* s_atile = smem + CL::CZ;
   __shared__ int s_cost[G][2];
   __shared__ int s_nz[G];
+  __shared__ unsigned int s_hz;  // the histogram's symbol 0 (balance points), from the per-block counts
   __shared__ int s_da[G];
   __shared__ int s_e2b[G];  // extent along x of each block of the brick (0: beyond the field)
 
   const int tid = threadIdx.x;
   for (int i = tid; i < G * PD::PV; i += 256) s_vp[i] = 0;
   for (int i = tid; i < kHistWin; i += 256) s_hist[i] = 0u;
+  if (tid == 0) s_hz = 0u;
   const float sig = MODE ? __uint_as_float((unsigned int)(127 - mlp.s_in) << 23) : 1.0f;
   const float unsig = MODE ? __uint_as_float((unsigned int)(127 + mlp.s_in) << 23) : 1.0f;
   // fixed-point form: TMEM for the two warpgroups' accumulators (2 limbs x QH
@@ -390,6 +392,10 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const __grid_con
       const unsigned int h = s_hist[i];
       if (h && hbase + i < (1 << m)) atomicAdd(&hist[hbase + i], (unsigned long long)h);
       s_hist[i] = 0u;
+    }
+    if (tid == 0) {
+      if (s_hz) atomicAdd(&hist[0], (unsigned long long)s_hz);
+      s_hz = 0u;
     }
   };
   const int team = tid / TS, t = tid % TS;
@@ -462,6 +468,10 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const __grid_con
     const long long n12 = g.n[1] * g.n[2];
     const T* base = static_cast<const T*>(s_job.x) + z0 * n12 + y0 * g.n[2] + x0;
     T vals[EPT];
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+      for (int i = 0; i < EPT; ++i) vals[i] = T(0);  // elements a thread does not load stay defined
+    }
     if (vecb) {
 #pragma unroll
       for (int it = 0; it < (NV + 255) / 256; ++it) {
@@ -502,12 +512,30 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const __grid_con
       s_cost[tid][0] = 0; s_cost[tid][1] = 0; s_nz[tid] = 0;
     }
     __syncthreads();
-    auto emit = [&](T v, int row, int col) {
+    // float64: every element's transform first, NP points side by side so
+    // that their operations interleave on the narrow FP64 unit: codes and a
+    // mask of ok
+    int qv[sizeof(T) == 8 ? EPT : 1];
+    unsigned int okm = 0;
+    if constexpr (sizeof(T) == 8) {
+      constexpr int NP = EPT % 4 == 0 ? 4 : (EPT % 2 == 0 ? 2 : 1);
+#pragma unroll
+      for (int i = 0; i < EPT; i += NP)
+        transform_dn<NP>(reinterpret_cast<const double*>(vals) + i, c, qv + i, okm, i);
+    }
+    auto emit = [&](int vi, int row, int col) {
       const int gb = col / B2, lx = col % B2;
       const int lz = row / B1, ly = row % B1;
-      bool ok;
-      const int q = Num<T>::transform(v, c, tb, ok);
-      s_dq[gb * BV + row * B2 + lx] = 2 * q + (ok ? 1 : 0);
+      int q, dq;
+      if constexpr (sizeof(T) == 8) {
+        q = qv[vi];
+        dq = 2 * q + (int)((okm >> vi) & 1u);
+      } else {
+        bool ok;
+        q = Num<T>::transform(vals[vi], c, tb, ok);
+        dq = 2 * q + (ok ? 1 : 0);
+      }
+      s_dq[gb * BV + row * B2 + lx] = dq;
       s_vp[gb * PD::PV + PD::at(lz, ly, lx)] = clampd(q, s_da[gb]);
     };
     if (vecb) {
@@ -517,7 +545,7 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const __grid_con
         if (e < NV) {
           const int r = e / RW, cv = e % RW;
 #pragma unroll
-          for (int q = 0; q < VW; ++q) emit(vals[it * VW + q], r, cv * VW + q);
+          for (int q = 0; q < VW; ++q) emit(it * VW + q, r, cv * VW + q);
         }
       }
     } else {
@@ -527,7 +555,7 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const __grid_con
         const int e = tid + 256 * i;
         if (e < tot) {
           const int r = e / W, col = e - r * W;
-          emit(vals[i], (r / e1) * B1 + (r % e1), col);
+          emit(i, (r / e1) * B1 + (r % e1), col);
         }
       }
     }
@@ -679,9 +707,13 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const __grid_con
           } else if constexpr (MODE == 0) {
             if (!sp) {
               nz += codez == 0;
+              // balance points (code 0, most points of a field the predictors miss) are
+              // counted per block, not one atomic each on a single bin
               const int hi = (int)codez - hbase;
-              if (hi >= 0 && hi < kHistWin) atomicAdd(&s_hist[hi], 1u);
-              else atomicAdd(&hist[codez], 1ull);
+              if (codez != 0) {
+                if (hi >= 0 && hi < kHistWin) atomicAdd(&s_hist[hi], 1u);
+                else atomicAdd(&hist[codez], 1ull);
+              }
             }
           }
         }
@@ -831,8 +863,10 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const __grid_con
               const uint16_t cd = src[j];
               nzz += cd == 0;
               const int hi = (int)cd - hbase;
-              if (hi >= 0 && hi < kHistWin) atomicAdd(&s_hist[hi], 1u);
-              else atomicAdd(&hist[cd], 1ull);
+              if (cd != 0) {  // code 0: counted per block
+                if (hi >= 0 && hi < kHistWin) atomicAdd(&s_hist[hi], 1u);
+                else atomicAdd(&hist[cd], 1ull);
+              }
             }
           }
         }
@@ -849,6 +883,7 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const __grid_con
     if (bvalid && t == 0) {
       nnflag[b] = (MODE != 0 && tcn < tcz) ? 1 : 0;
       nout[b] = 1u + (unsigned int)tnz;
+      if (tnz) atomicAdd(&s_hz, (unsigned int)tnz);
     }
     __syncthreads();
   }

@@ -157,7 +157,9 @@ __global__ void __launch_bounds__(256) k_lit_compress(Geo g, const float* __rest
   __shared__ unsigned int s_hist[kLitHistWin];
   for (int i = threadIdx.x; i < (int)(sizeof(Tabs) / 4); i += blockDim.x)
     reinterpret_cast<float*>(&tb)[i] = reinterpret_cast<const float*>(tabs)[i];
+  __shared__ unsigned int s_hz;  // symbol 0: counted on chip, one atomic per CTA
   for (int i = threadIdx.x; i < kLitHistWin; i += blockDim.x) s_hist[i] = 0u;
+  if (threadIdx.x == 0) s_hz = 0u;
   __syncthreads();
   const bool skip = st->err != 0;
   State c;
@@ -206,14 +208,20 @@ __global__ void __launch_bounds__(256) k_lit_compress(Geo g, const float* __rest
       code = ak <= R - 1 ? (unsigned int)(kk + R) : 0u;
     }
     codes[idx] = (uint16_t)code;
-    if (code == 0) atomicAdd(&nout[b], 1u);
     const int hi = (int)code - hbase;
-    if (hi >= 0 && hi < kLitHistWin) atomicAdd(&s_hist[hi], 1u);
-    else atomicAdd(&hist[code], 1ull);
+    if (code == 0) {
+      atomicAdd(&nout[b], 1u);
+      atomicAdd(&s_hz, 1u);
+    } else if (hi >= 0 && hi < kLitHistWin) {
+      atomicAdd(&s_hist[hi], 1u);
+    } else {
+      atomicAdd(&hist[code], 1ull);
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < kLitHistWin; i += blockDim.x)
     if (s_hist[i] && hbase + i < (1 << m)) atomicAdd(&hist[hbase + i], (unsigned long long)s_hist[i]);
+  if (threadIdx.x == 0 && s_hz) atomicAdd(&hist[0], (unsigned long long)s_hz);
 }
 
 // Decoding, one warp per block: the block's wavefronts (z + y + x for the
