@@ -512,16 +512,17 @@ __global__ void __launch_bounds__(256, MODE ? 2 : 3) k_compress(const __grid_con
       s_cost[tid][0] = 0; s_cost[tid][1] = 0; s_nz[tid] = 0;
     }
     __syncthreads();
-    // float64: every element's transform first, NP points side by side so
-    // that their operations interleave on the narrow FP64 unit: codes and a
-    // mask of ok
+    // float64: every element's transform first (branch-free, independent
+    // chains on the narrow FP64 unit): codes and a mask of ok
     int qv[sizeof(T) == 8 ? EPT : 1];
     unsigned int okm = 0;
     if constexpr (sizeof(T) == 8) {
-      constexpr int NP = EPT % 4 == 0 ? 4 : (EPT % 2 == 0 ? 2 : 1);
 #pragma unroll
-      for (int i = 0; i < EPT; i += NP)
-        transform_dn<NP>(reinterpret_cast<const double*>(vals) + i, c, qv + i, okm, i);
+      for (int i = 0; i < EPT; ++i) {
+        bool ok;
+        qv[i] = Num<T>::transform(vals[i], c, tb, ok);
+        okm |= (ok ? 1u : 0u) << i;
+      }
     }
     auto emit = [&](int vi, int row, int col) {
       const int gb = col / B2, lx = col % B2;

@@ -317,9 +317,8 @@ template <> struct Num<double> {
     double a = dev_exp2d(__dmul_rn((double)n, c.stepd));
     return cl == 1 ? a : -a;
   }
-  // Without branches (every case computes the whole chain, on a stand-in
-  // for zero and subnormal magnitudes, and selects), so that the transforms
-  // of a thread's points overlap on the narrow FP64 pipe.
+  // Without branches: every case computes the whole chain (on a stand-in
+  // for zero and subnormal magnitudes) and selects its result.
   static __device__ __forceinline__ int transform(double x, const State& c, const Tabs&, bool& ok) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const unsigned long long ab = b & 0x7FFFFFFFFFFFFFFFull;
@@ -339,112 +338,6 @@ template <> struct Num<double> {
     return small ? c.Zq : q;
   }
 };
-
-// Num<double>::transform of NP points side by side: each stage for all of
-// them before the next, so that the FP64 operations of different points
-// interleave (one point's chain alone leaves the narrow FP64 unit mostly
-// idle).  The same operations, and so the same results, point by point:
-// codes to q[0 .. NP-1], ok to bits bit0 .. bit0 + NP - 1 of okm.
-template <int NP>
-__device__ __forceinline__ void transform_dn(const double* x, const State& c, int* q, unsigned int& okm, int bit0) {
-  constexpr unsigned long long kMant = 0xFFFFFFFFFFFFFull;
-  constexpr unsigned long long kSqrt2Mant = 0x6A09E667F3BCDull;  // significand of 0x1.6a09e667f3bcdp+0
-  const double two_over_ln2 = 0x1.71547652b82fep+1;
-  const double ln2 = 0x1.62e42fefa39efp-1;
-  constexpr double inv_odd[11] = {1.0,        1.0 / 3.0,  1.0 / 5.0,  1.0 / 7.0,  1.0 / 9.0, 1.0 / 11.0,
-                                  1.0 / 13.0, 1.0 / 15.0, 1.0 / 17.0, 1.0 / 19.0, 1.0 / 21.0};
-  constexpr double inv_fact[14] = {1.0,          1.0,           1.0 / 2.0,      1.0 / 6.0,       1.0 / 24.0,
-                                   1.0 / 120.0,  1.0 / 720.0,   1.0 / 5040.0,   1.0 / 40320.0,   1.0 / 362880.0,
-                                   1.0 / 3628800.0, 1.0 / 39916800.0, 1.0 / 479001600.0, 1.0 / 6227020800.0};
-  double a[NP], num[NP], d[NP], y[NP], s[NP], t[NP];
-  int e[NP], n[NP];
-  bool zero[NP], small[NP], pos[NP];
-  // magnitudes (a stand-in 1.0 for zero and subnormal ones) and log2's reduction
-#pragma unroll
-  for (int j = 0; j < NP; ++j) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x[j]);
-    const unsigned long long ab = b & 0x7FFFFFFFFFFFFFFFull;
-    zero[j] = b == 0ull;
-    small[j] = ab < 0x0010000000000000ull;
-    const unsigned long long ub = small[j] ? 0x3FF0000000000000ull : ab;
-    a[j] = __longlong_as_double((long long)ub);
-    const bool half = (ub & kMant) > kSqrt2Mant;
-    e[j] = (int)((ub >> 52) & 0x7FFull) - 1023 + (half ? 1 : 0);
-    const double m = __longlong_as_double((long long)((ub & kMant) | (half ? 0x3FE0000000000000ull
-                                                                            : 0x3FF0000000000000ull)));
-    num[j] = __dsub_rn(m, 1.0);
-    d[j] = __dadd_rn(m, 1.0);
-    pos[j] = x[j] > 0.0;
-  }
-  // s = RN(num / d), div_markstein's steps
-#pragma unroll
-  for (int j = 0; j < NP; ++j) {
-    float yf;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(__double2float_rn(d[j])));
-    y[j] = (double)yf;
-  }
-#pragma unroll
-  for (int it = 0; it < 3; ++it)
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      const double r = __fma_rn(-d[j], y[j], 1.0);
-      y[j] = __fma_rn(y[j], r, y[j]);
-    }
-#pragma unroll
-  for (int j = 0; j < NP; ++j) {
-    if (__double_as_longlong(d[j]) == 0x3FFFFFFFFFFFFFFFll) y[j] = __longlong_as_double(0x3FE0000000000001ll);
-    s[j] = __dmul_rn(num[j], y[j]);
-  }
-#pragma unroll
-  for (int it = 0; it < 2; ++it)
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      const double r = __fma_rn(-d[j], s[j], num[j]);
-      s[j] = __fma_rn(r, y[j], s[j]);
-    }
-  // the atanh series (d: z = s^2, y: the polynomial) and log2 a
-#pragma unroll
-  for (int j = 0; j < NP; ++j) {
-    d[j] = __dmul_rn(s[j], s[j]);
-    y[j] = inv_odd[10];
-  }
-#pragma unroll
-  for (int i = 9; i >= 0; --i)
-#pragma unroll
-    for (int j = 0; j < NP; ++j) y[j] = __fma_rn(y[j], d[j], inv_odd[i]);
-#pragma unroll
-  for (int j = 0; j < NP; ++j) t[j] = __dadd_rn((double)e[j], __dmul_rn(__dmul_rn(s[j], y[j]), two_over_ln2));
-  // codes and the exponent of their inverse
-#pragma unroll
-  for (int j = 0; j < NP; ++j) n[j] = (int)rint(__dmul_rn(t[j], c.invd));
-#pragma unroll
-  for (int j = 0; j < NP; ++j) {
-    double tt = __dmul_rn((double)n[j], c.stepd);
-    if (((unsigned long long)__double_as_longlong(tt) & 0x7FFFFFFFFFFFFFFFull) > 0x40A0680000000000ull)
-      tt = __double_as_longlong(tt) < 0 ? -2100.0 : 2100.0;
-    const double nf = rint(tt);
-    e[j] = (int)nf;                               // e: exp2's integer part
-    s[j] = __dmul_rn(__dsub_rn(tt, nf), ln2);     // s: u
-    y[j] = inv_fact[13];
-  }
-  // exp2 (dev_exp2d's series and scalings)
-#pragma unroll
-  for (int i = 12; i >= 0; --i)
-#pragma unroll
-    for (int j = 0; j < NP; ++j) y[j] = __fma_rn(y[j], s[j], inv_fact[i]);
-#pragma unroll
-  for (int j = 0; j < NP; ++j) {
-    const int k = e[j], k1 = k / 3, k2 = (k - k1) / 2, k3 = k - k1 - k2;
-    const double r = __dmul_rn(__dmul_rn(__dmul_rn(y[j], pow2_scale_d(k1)), pow2_scale_d(k2)), pow2_scale_d(k3));
-    const int qq = n[j] + (pos[j] ? c.Kp : c.Kn);
-    const bool cls = code_class(qq, c) == (pos[j] ? 1 : 2);
-    const bool in_bound = fabs(__dsub_rn(r, a[j])) <= __dmul_rd(c.ebdnd, a[j]);
-    const bool ok = zero[j] || (!small[j] && cls && in_bound);
-    q[j] = small[j] ? c.Zq : qq;
-    okm |= (ok ? 1u : 0u) << (bit0 + j);
-  }
-}
-
 
 // ---------------------------------------------------------------------------
 // Stencils.  S7: the 3-D Lorenzo set; S13: every (dz,dy,dx) in {-1,0,1}^3 that
