@@ -269,14 +269,14 @@ def sha_of(*paths):
 TRAFFIC = {
     # (workload, stage, form): (bytes per launch, sha of the sources, profile summary)
     # captured on 256 x 256 x 512 (one quarter of a 512^3 field, same recipe and network shape) and scaled by
-    # the points processed: 68.6 MB read + 74.5 MB written there
-    ("density_velocity_512", "recon", "bf16"): (4 * (68622080 + 74481152), "4c5daf2d675c3a2b",
+    # the points processed: 69.1 MB read + 74.9 MB written there
+    ("density_velocity_512", "recon", "bf16"): (4 * (69058304 + 74940928), "75ff1fa4048c60e2",
                                                 "profiles/k_recon_c3_wmma.md"),
-    # 134.8 MB read + 38.5 MB written on the same quarter-size case
-    ("density_velocity_512", "compress", "bf16"): (4 * (134838272 + 38451968), "17ab68d20eb5a342",
+    # 134.8 MB read + 38.2 MB written on the same quarter-size case
+    ("density_velocity_512", "compress", "bf16"): (4 * (134845440 + 38154496), "5558dd42ecd8e777",
                                                    "profiles/k_compress_c3_tcgen05.md"),
-    # captured on 128 x 384 x 384 (one half of the float64 field, same recipe): 152.0 MB read + 22.0 MB written
-    ("grf256x384x384_f64", "compress", "bf16"): (2 * (152046080 + 21986560), "17ab68d20eb5a342",
+    # captured on 128 x 384 x 384 (one half of the float64 field, same recipe): 151.8 MB read + 23.0 MB written
+    ("grf256x384x384_f64", "compress", "bf16"): (2 * (151760128 + 22973952), "5558dd42ecd8e777",
                                                  "profiles/k_compress_c5_f64.md"),
 }
 STAGE_SOURCES = {
